@@ -1,0 +1,813 @@
+/*
+ * oracle.c -- plain, slow FP64 CPU oracle of subsystem-based ADMM multibody simulation
+ * (Lee, Lee & Lee, "Modular and Parallelizable Multibody Physics Simulation via
+ * Subsystem-Based ADMM", arXiv 2302.14344).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the package's smoke check and the
+ * benchmark's CPU-baseline leg load this file.  It shares no code, header, table or helper
+ * with the CUDA library, and it includes nothing from it.
+ *
+ * What it computes, in the paper's order (Algorithm 1), for one scene:
+ *   construct A_i, b_i                         (Eq. ddyn -> Eq. sdyn; rigid bodies below)
+ *   construct e_j, J_j                         (Sec. II-A: soft, hard, contact rows)
+ *   beta_i = Tr(A_i) / Tr(J_ci^T J_ci)         (Sec. III-D), or a fixed rho
+ *   factorise K_i = A_i + beta_i J_ci^T J_ci   (plain Cholesky, no pivoting)
+ *   loop l = 0 .. l_max-1
+ *     v-step   K_i v_i = b_i + J_ci^T (beta_i z_i - u_i)      (Eq. admm-1i)
+ *              x_i = J_ci v_i,  y_i = beta_i x_i + u_i          (Eq. surrogate)
+ *     theta    = sum_i |y_i^{l+1} - y_i^l|^2                    (Eq. residual)
+ *     z-step   per constraint j: lambda_j from the closed forms of Sec. III-C, then
+ *              beta_i z_ij = y_ij + lambda_j                    (Eq. surrogate)
+ *     u-step   u_i += beta_i (x_i - z_i)                        (Eq. admm-3)
+ *     r_p = max |x - z|, r_d = max beta_i |z^{l+1} - z^l|       (Boyd's residuals)
+ *   update each subsystem state from v-hat                      (Eq. ddyn)
+ *
+ * Readings where the paper is silent or garbled (each is also listed in the design notes):
+ *   - A_i = (2/h) M_i and b_i = (2/h) M_i v_k - C v_k + f: Eq. ddyn with
+ *     v_{k+1} = 2 v-hat - v_k substituted; lambda is in force units.
+ *   - Soft: lambda = -k (e + alpha q) / (1 + s alpha k) with q = sum beta_i^-1 y_i and
+ *     s = sum beta_i^-1 (the printed formula has an unbalanced parenthesis).
+ *   - Contact: with lambda* = -(q + e)/s, lambda_n = max(0, lambda*_n) and the tangent
+ *     lambda*_t scaled onto the disk of radius mu lambda_n: the exact solution of
+ *     Eq. contact12 under the isotropic metric s I (open / stick / slip cases).
+ *   - Stop rule "primal": r_p = max|x - z| <= tol and max|z^{l+1} - z^l| <= tol after the
+ *     u-step (both in constraint-velocity units; tol <= 0: exactly l_max iterations).  The
+ *     second test is Boyd's dual residual divided by beta: without it an open contact seen
+ *     twice in a row has x = z exactly while v is still moving.  Stop rule "theta":
+ *     theta < theta_th after the v-step, from l >= 1.
+ *   - Baumgarte error e = gamma phi / h for joints; contact normal e_n = gap/h for an
+ *     open gap, gamma gap/h for penetration; tangential e = 0.
+ *
+ * Rounding: build with -O2 -ffp-contract=off (no fused multiply-add).
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define MAXSIDES 8
+
+enum { T_EQUALITY = 0, T_HARD = 1, T_SOFT = 2, T_CONTACT = 3 };
+enum { SRC_ROWS = 0, SRC_BALL = 1, SRC_REVOLUTE = 2, SRC_ANGLE_PD = 3, SRC_PLANE = 4 };
+enum { SUB_GENERIC = 0, SUB_RIGID = 1 };
+
+typedef struct {
+    double m, I[3], p[3], q[4], v[3], w[3];
+} body_t;
+
+typedef struct {
+    int kind, n, nb;
+    body_t *bodies;
+    double *A, *b;   /* n*n, n */
+    double *L;       /* Cholesky factor of K (lower, row-major n*n) */
+    double *v;       /* v-hat */
+    double *rhs;
+    double beta;
+} sub_t;
+
+typedef struct {
+    int src, type, rows, ns;
+    int sub[MAXSIDES];
+    double *J[MAXSIDES];  /* rows x n_sub, row-major */
+    double *e;
+    double k, alpha, mu;
+    /* rigid-model parameters */
+    int sa, ba, sb, bb;
+    double anc_a[3], anc_b[3], ax_a[3], ax_b[3], ref_a[3], ref_b[3];
+    double kp, kd, target, plane_z;
+    /* iteration state per side-row, index s*rows + r */
+    double *x, *z, *u, *y, *yold, *zold, *zprev;
+    double *lam, *lamprev;
+    int has_prev;
+} con_t;
+
+typedef struct orc_scene {
+    double h, g[3], gamma, rho, tol, theta_th;
+    int beta_fixed, warm_prev, stop_theta, max_iters;
+    int nsub, ncon, capsub, capcon;
+    sub_t *subs;
+    con_t *cons;
+    /* last solve */
+    int iters, converged, status;
+    double r_p, r_d, theta;
+    double *trace;
+    int trace_cap;
+} orc_scene;
+
+/* ------------------------------------------------------------------------------------ */
+/* small dense helpers                                                                   */
+
+static void *xcalloc(size_t n, size_t sz) { return calloc(n ? n : 1, sz); }
+
+/* plain Cholesky K = L L^T; returns 0 on success, -1 on a pivot <= 0 or non-finite */
+static int cholesky(int n, const double *K, double *L)
+{
+    memset(L, 0, sizeof(double) * (size_t)n * n);
+    for (int i = 0; i < n; i++) {
+        for (int j = 0; j <= i; j++) {
+            double s = K[i * n + j];
+            for (int k = 0; k < j; k++) s -= L[i * n + k] * L[j * n + k];
+            if (i == j) {
+                if (!(s > 0.0) || !isfinite(s)) return -1;
+                L[i * n + i] = sqrt(s);
+            } else {
+                L[i * n + j] = s / L[j * n + j];
+            }
+        }
+    }
+    return 0;
+}
+
+/* solve L L^T x = r in place */
+static void chol_solve(int n, const double *L, double *x)
+{
+    for (int i = 0; i < n; i++) {
+        double s = x[i];
+        for (int k = 0; k < i; k++) s -= L[i * n + k] * x[k];
+        x[i] = s / L[i * n + i];
+    }
+    for (int i = n - 1; i >= 0; i--) {
+        double s = x[i];
+        for (int k = i + 1; k < n; k++) s -= L[k * n + i] * x[k];
+        x[i] = s / L[i * n + i];
+    }
+}
+
+static void quat_to_mat(const double q[4], double R[9])
+{
+    double w = q[0], x = q[1], y = q[2], z = q[3];
+    R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z);     R[2] = 2 * (x * z + w * y);
+    R[3] = 2 * (x * y + w * z);     R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+    R[6] = 2 * (x * z - w * y);     R[7] = 2 * (y * z + w * x);     R[8] = 1 - 2 * (x * x + y * y);
+}
+
+static void matvec3(const double R[9], const double a[3], double out[3])
+{
+    for (int i = 0; i < 3; i++) out[i] = R[3 * i] * a[0] + R[3 * i + 1] * a[1] + R[3 * i + 2] * a[2];
+}
+
+static void cross3(const double a[3], const double b[3], double out[3])
+{
+    out[0] = a[1] * b[2] - a[2] * b[1];
+    out[1] = a[2] * b[0] - a[0] * b[2];
+    out[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+static double dot3(const double a[3], const double b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+/* row vector c^T R (i.e. R^T c) */
+static void rowtimesR(const double c[3], const double R[9], double out[3])
+{
+    for (int j = 0; j < 3; j++) out[j] = c[0] * R[j] + c[1] * R[3 + j] + c[2] * R[6 + j];
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* construction                                                                          */
+
+orc_scene *orc_new(const double *o)
+{
+    orc_scene *S = (orc_scene *)xcalloc(1, sizeof(orc_scene));
+    S->h = o[0]; S->g[0] = o[1]; S->g[1] = o[2]; S->g[2] = o[3];
+    S->gamma = o[4];
+    S->beta_fixed = (int)o[5];
+    S->rho = o[6];
+    S->warm_prev = (int)o[7];
+    S->stop_theta = (int)o[8];
+    S->tol = o[9];
+    S->theta_th = o[10];
+    S->max_iters = (int)o[11];
+    return S;
+}
+
+static sub_t *new_sub(orc_scene *S)
+{
+    if (S->nsub == S->capsub) {
+        S->capsub = S->capsub ? 2 * S->capsub : 8;
+        S->subs = (sub_t *)realloc(S->subs, sizeof(sub_t) * S->capsub);
+    }
+    sub_t *u = &S->subs[S->nsub++];
+    memset(u, 0, sizeof(*u));
+    return u;
+}
+
+static void sub_alloc(sub_t *u)
+{
+    int n = u->n;
+    u->A = (double *)xcalloc((size_t)n * n, sizeof(double));
+    u->b = (double *)xcalloc(n, sizeof(double));
+    u->L = (double *)xcalloc((size_t)n * n, sizeof(double));
+    u->v = (double *)xcalloc(n, sizeof(double));
+    u->rhs = (double *)xcalloc(n, sizeof(double));
+}
+
+int orc_add_generic(orc_scene *S, int n, const double *A, const double *b)
+{
+    if (n <= 0) return -1;
+    sub_t *u = new_sub(S);
+    u->kind = SUB_GENERIC; u->n = n;
+    sub_alloc(u);
+    memcpy(u->A, A, sizeof(double) * (size_t)n * n);
+    memcpy(u->b, b, sizeof(double) * n);
+    return S->nsub - 1;
+}
+
+/* bodies: nb records of 17 doubles: m, I[3], p[3], q[4] (w,x,y,z), v[3], w[3] */
+int orc_add_rigid(orc_scene *S, int nb, const double *rec)
+{
+    if (nb <= 0) return -1;
+    sub_t *u = new_sub(S);
+    u->kind = SUB_RIGID; u->nb = nb; u->n = 6 * nb;
+    u->bodies = (body_t *)xcalloc(nb, sizeof(body_t));
+    for (int k = 0; k < nb; k++) {
+        const double *r = rec + 17 * k;
+        body_t *B = &u->bodies[k];
+        B->m = r[0];
+        memcpy(B->I, r + 1, 3 * sizeof(double));
+        memcpy(B->p, r + 4, 3 * sizeof(double));
+        memcpy(B->q, r + 7, 4 * sizeof(double));
+        memcpy(B->v, r + 11, 3 * sizeof(double));
+        memcpy(B->w, r + 14, 3 * sizeof(double));
+    }
+    sub_alloc(u);
+    return S->nsub - 1;
+}
+
+static con_t *new_con(orc_scene *S)
+{
+    if (S->ncon == S->capcon) {
+        S->capcon = S->capcon ? 2 * S->capcon : 8;
+        S->cons = (con_t *)realloc(S->cons, sizeof(con_t) * S->capcon);
+    }
+    con_t *c = &S->cons[S->ncon++];
+    memset(c, 0, sizeof(*c));
+    return c;
+}
+
+static void con_alloc(orc_scene *S, con_t *c)
+{
+    int nr = c->rows * c->ns;
+    for (int s = 0; s < c->ns; s++)
+        c->J[s] = (double *)xcalloc((size_t)c->rows * S->subs[c->sub[s]].n, sizeof(double));
+    c->e = (double *)xcalloc(c->rows, sizeof(double));
+    c->x = (double *)xcalloc(nr, sizeof(double));
+    c->z = (double *)xcalloc(nr, sizeof(double));
+    c->u = (double *)xcalloc(nr, sizeof(double));
+    c->y = (double *)xcalloc(nr, sizeof(double));
+    c->yold = (double *)xcalloc(nr, sizeof(double));
+    c->zold = (double *)xcalloc(nr, sizeof(double));
+    c->zprev = (double *)xcalloc(nr, sizeof(double));
+    c->lam = (double *)xcalloc(c->rows, sizeof(double));
+    c->lamprev = (double *)xcalloc(c->rows, sizeof(double));
+}
+
+/* explicit rows: J holds, side after side, rows x n_{subs[s]} row-major blocks */
+int orc_add_rows(orc_scene *S, int type, int rows, int ns, const int *subs, const double *J,
+                 const double *e, double k, double alpha, double mu)
+{
+    if (ns < 1 || ns > MAXSIDES || rows < 1) return -1;
+    if (type == T_CONTACT && rows != 3) return -1;
+    for (int s = 0; s < ns; s++) {
+        if (subs[s] < 0 || subs[s] >= S->nsub) return -1;
+        for (int t = 0; t < s; t++) if (subs[t] == subs[s]) return -1;
+    }
+    con_t *c = new_con(S);
+    c->src = SRC_ROWS; c->type = type; c->rows = rows; c->ns = ns;
+    c->k = k; c->alpha = alpha; c->mu = mu;
+    for (int s = 0; s < ns; s++) c->sub[s] = subs[s];
+    con_alloc(S, c);
+    const double *Jp = J;
+    for (int s = 0; s < ns; s++) {
+        size_t cnt = (size_t)rows * S->subs[subs[s]].n;
+        memcpy(c->J[s], Jp, cnt * sizeof(double));
+        Jp += cnt;
+    }
+    memcpy(c->e, e, rows * sizeof(double));
+    return S->ncon - 1;
+}
+
+/* rigid-model constraint.  p: anchor_a[3] anchor_b[3] axis_a[3] axis_b[3] ref_a[3]
+ * ref_b[3] kp kd target plane_z mu   (23 doubles).  sb < 0 means the world. */
+int orc_add_joint(orc_scene *S, int kind, int sa, int ba, int sb, int bb, const double *p)
+{
+    if (sa < 0 || sa >= S->nsub || S->subs[sa].kind != SUB_RIGID) return -1;
+    if (ba < 0 || ba >= S->subs[sa].nb) return -1;
+    if (sb >= 0) {
+        if (sb >= S->nsub || S->subs[sb].kind != SUB_RIGID) return -1;
+        if (bb < 0 || bb >= S->subs[sb].nb) return -1;
+        if (sb == sa && bb == ba) return -1;
+    }
+    if (kind == SRC_PLANE) sb = -1;
+    con_t *c = new_con(S);
+    c->src = kind;
+    c->sa = sa; c->ba = ba; c->sb = sb; c->bb = bb;
+    memcpy(c->anc_a, p + 0, 3 * sizeof(double));
+    memcpy(c->anc_b, p + 3, 3 * sizeof(double));
+    memcpy(c->ax_a, p + 6, 3 * sizeof(double));
+    memcpy(c->ax_b, p + 9, 3 * sizeof(double));
+    memcpy(c->ref_a, p + 12, 3 * sizeof(double));
+    memcpy(c->ref_b, p + 15, 3 * sizeof(double));
+    c->kp = p[18]; c->kd = p[19]; c->target = p[20]; c->plane_z = p[21]; c->mu = p[22];
+    switch (kind) {
+    case SRC_BALL: c->rows = 3; c->type = T_EQUALITY; break;
+    case SRC_REVOLUTE: c->rows = 5; c->type = T_EQUALITY; break;
+    case SRC_ANGLE_PD: c->rows = 1; c->type = T_SOFT; break;
+    case SRC_PLANE: c->rows = 3; c->type = T_CONTACT; break;
+    default: S->ncon--; return -1;
+    }
+    c->ns = 1;
+    c->sub[0] = sa;
+    if (sb >= 0 && sb != sa) { c->ns = 2; c->sub[1] = sb; }
+    con_alloc(S, c);
+    return S->ncon - 1;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* rigid-body model: A_i, b_i (Eq. ddyn) and constraint rows (Sec. II-A)                 */
+
+static void assemble_rigid(orc_scene *S, sub_t *u)
+{
+    int n = u->n;
+    double c2h = 2.0 / S->h;
+    memset(u->A, 0, sizeof(double) * (size_t)n * n);
+    for (int k = 0; k < u->nb; k++) {
+        body_t *B = &u->bodies[k];
+        int o = 6 * k;
+        double mass[6] = {B->m, B->m, B->m, B->I[0], B->I[1], B->I[2]};
+        for (int d = 0; d < 6; d++) u->A[(o + d) * n + (o + d)] = c2h * mass[d];
+        /* b = (2/h) M v_k - C v_k + f ;  C v_k = [0; w x I w] (body frame) ; f = [m g; 0] */
+        double Iw[3] = {B->I[0] * B->w[0], B->I[1] * B->w[1], B->I[2] * B->w[2]};
+        double gyro[3];
+        cross3(B->w, Iw, gyro);
+        for (int d = 0; d < 3; d++) {
+            u->b[o + d] = c2h * B->m * B->v[d] + B->m * S->g[d];
+            u->b[o + 3 + d] = c2h * Iw[d] - gyro[d];
+        }
+    }
+}
+
+/* Row of the velocity of body point P = p + R r along the world direction dir.
+ * dP/dt = v + R (w x r) with w in the body frame, so
+ * dir . dP/dt = dir . v + (R^T dir) . (w x r) = dir . v + w . (r x R^T dir). */
+static void point_row(const double dir[3], const double R[9], const double r[3], double row[6])
+{
+    double Rd[3];
+    rowtimesR(dir, R, Rd);          /* R^T dir */
+    row[0] = dir[0]; row[1] = dir[1]; row[2] = dir[2];
+    cross3(r, Rd, row + 3);
+}
+
+/* phi (rows) and body blocks Ja, Jb (rows x 6) of a rigid-model constraint */
+static void joint_rows(orc_scene *S, con_t *c, double *phi, double *Ja, double *Jb)
+{
+    body_t *A = &S->subs[c->sa].bodies[c->ba];
+    body_t *B = c->sb >= 0 ? &S->subs[c->sb].bodies[c->bb] : NULL;
+    double Ra[9], Rb[9];
+    quat_to_mat(A->q, Ra);
+    if (B) quat_to_mat(B->q, Rb);
+    else { memset(Rb, 0, sizeof Rb); Rb[0] = Rb[4] = Rb[8] = 1.0; }
+    memset(Ja, 0, sizeof(double) * 6 * c->rows);
+    memset(Jb, 0, sizeof(double) * 6 * c->rows);
+    static const double E[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+    if (c->src == SRC_BALL || c->src == SRC_REVOLUTE) {
+        double ra[3], pa[3], pb[3], rb[3];
+        matvec3(Ra, c->anc_a, ra);
+        for (int d = 0; d < 3; d++) pa[d] = A->p[d] + ra[d];
+        if (B) { matvec3(Rb, c->anc_b, rb); for (int d = 0; d < 3; d++) pb[d] = B->p[d] + rb[d]; }
+        else { for (int d = 0; d < 3; d++) pb[d] = c->anc_b[d]; }
+        for (int d = 0; d < 3; d++) {
+            phi[d] = pa[d] - pb[d];
+            point_row(E[d], Ra, c->anc_a, Ja + 6 * d);
+            if (B) {
+                point_row(E[d], Rb, c->anc_b, Jb + 6 * d);
+                for (int q = 0; q < 6; q++) Jb[6 * d + q] = -Jb[6 * d + q];
+            }
+        }
+        if (c->src == SRC_REVOLUTE) {
+            double ua[3], ub[3], t[2][3], tmp[3];
+            matvec3(Ra, c->ax_a, ua);
+            if (B) matvec3(Rb, c->ax_b, ub); else memcpy(ub, c->ax_b, sizeof ub);
+            matvec3(Ra, c->ref_a, t[0]);
+            cross3(c->ax_a, c->ref_a, tmp);
+            matvec3(Ra, tmp, t[1]);
+            (void)ua;
+            for (int k = 0; k < 2; k++) {
+                int r = 3 + k;
+                double txu[3], ja[3], jb[3];
+                phi[r] = dot3(t[k], ub);
+                cross3(t[k], ub, txu);       /* d/dt (t . u_b) = (t x u_b) . (w_a - w_b) */
+                rowtimesR(txu, Ra, ja);
+                for (int q = 0; q < 3; q++) Ja[6 * r + 3 + q] = ja[q];
+                if (B) {
+                    rowtimesR(txu, Rb, jb);
+                    for (int q = 0; q < 3; q++) Jb[6 * r + 3 + q] = -jb[q];
+                }
+            }
+        }
+    } else if (c->src == SRC_ANGLE_PD) {
+        double u[3], na[3], nb[3], cr[3], ja[3], jb[3];
+        matvec3(Ra, c->ax_a, u);
+        matvec3(Ra, c->ref_a, na);
+        if (B) matvec3(Rb, c->ref_b, nb); else memcpy(nb, c->ref_b, sizeof nb);
+        cross3(na, nb, cr);
+        phi[0] = atan2(dot3(cr, u), dot3(na, nb));
+        /* d theta / dt = u . (w_b - w_a) */
+        rowtimesR(u, Ra, ja);
+        for (int q = 0; q < 3; q++) Ja[3 + q] = -ja[q];
+        if (B) {
+            rowtimesR(u, Rb, jb);
+            for (int q = 0; q < 3; q++) Jb[3 + q] = jb[q];
+        }
+    } else if (c->src == SRC_PLANE) {
+        double ra[3];
+        matvec3(Ra, c->anc_a, ra);
+        phi[0] = A->p[2] + ra[2] - c->plane_z;   /* gap along the normal +z */
+        phi[1] = 0.0; phi[2] = 0.0;
+        static const double dirs[3][3] = {{0, 0, 1}, {1, 0, 0}, {0, 1, 0}};
+        for (int d = 0; d < 3; d++) point_row(dirs[d], Ra, c->anc_a, Ja + 6 * d);
+    }
+}
+
+static void assemble_joint(orc_scene *S, con_t *c)
+{
+    double phi[5], Ja[30], Jb[30];
+    joint_rows(S, c, phi, Ja, Jb);
+    int na = S->subs[c->sa].n;
+    for (int s = 0; s < c->ns; s++) memset(c->J[s], 0, sizeof(double) * c->rows * S->subs[c->sub[s]].n);
+    for (int r = 0; r < c->rows; r++)
+        for (int q = 0; q < 6; q++) c->J[0][r * na + 6 * c->ba + q] += Ja[r * 6 + q];
+    if (c->sb >= 0) {
+        int side = (c->sb == c->sa) ? 0 : 1;
+        int nb = S->subs[c->sb].n;
+        for (int r = 0; r < c->rows; r++)
+            for (int q = 0; q < 6; q++) c->J[side][r * nb + 6 * c->bb + q] += Jb[r * 6 + q];
+    }
+    double h = S->h;
+    if (c->src == SRC_BALL || c->src == SRC_REVOLUTE) {
+        for (int r = 0; r < c->rows; r++) c->e[r] = S->gamma * phi[r] / h;
+    } else if (c->src == SRC_ANGLE_PD) {
+        c->e[0] = phi[0] - c->target;
+        c->k = c->kp;
+        c->alpha = c->kd / c->kp + 0.5 * h;
+    } else if (c->src == SRC_PLANE) {
+        double gap = phi[0];
+        c->e[0] = gap >= 0.0 ? gap / h : S->gamma * gap / h;
+        c->e[1] = 0.0; c->e[2] = 0.0;
+    }
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* z-step of one constraint (Sec. III-C, Eq. admm-2j via Eq. surrogate)                   */
+
+/* y: ns x rows, beta: ns.  Writes lambda (rows).  Returns nothing. */
+void orc_project(int type, int rows, int ns, const double *beta, const double *y,
+                 const double *e, double k, double alpha, double mu, double *lam)
+{
+    double s = 0.0;
+    for (int i = 0; i < ns; i++) s += 1.0 / beta[i];
+    double q[8];
+    for (int r = 0; r < rows; r++) {
+        q[r] = 0.0;
+        for (int i = 0; i < ns; i++) q[r] += y[i * rows + r] / beta[i];
+    }
+    if (type == T_EQUALITY) {
+        for (int r = 0; r < rows; r++) lam[r] = -(q[r] + e[r]) / s;
+    } else if (type == T_HARD) {
+        for (int r = 0; r < rows; r++) {
+            double l = -(q[r] + e[r]) / s;
+            lam[r] = l > 0.0 ? l : 0.0;
+        }
+    } else if (type == T_SOFT) {
+        for (int r = 0; r < rows; r++)
+            lam[r] = -k * (e[r] + alpha * q[r]) / (1.0 + s * alpha * k);
+    } else { /* contact: rows (n, t1, t2) */
+        double ln = -(q[0] + e[0]) / s;
+        double l1 = -(q[1] + e[1]) / s;
+        double l2 = -(q[2] + e[2]) / s;
+        if (ln <= 0.0) { lam[0] = 0.0; lam[1] = 0.0; lam[2] = 0.0; return; }
+        double t = sqrt(l1 * l1 + l2 * l2);
+        double lim = mu * ln;
+        lam[0] = ln;
+        if (t > lim) { lam[1] = l1 * (lim / t); lam[2] = l2 * (lim / t); }
+        else { lam[1] = l1; lam[2] = l2; }
+    }
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* one time step (Algorithm 1)                                                            */
+
+static double beta_of(orc_scene *S, int i)
+{
+    return S->subs[i].beta;
+}
+
+int orc_step(orc_scene *S)
+{
+    S->status = 0;
+    /* construct A_i, b_i */
+    for (int i = 0; i < S->nsub; i++)
+        if (S->subs[i].kind == SUB_RIGID) assemble_rigid(S, &S->subs[i]);
+    /* construct e_j, J_j */
+    for (int j = 0; j < S->ncon; j++)
+        if (S->cons[j].src != SRC_ROWS) assemble_joint(S, &S->cons[j]);
+    /* beta_i (Sec. III-D) */
+    for (int i = 0; i < S->nsub; i++) {
+        sub_t *u = &S->subs[i];
+        if (S->beta_fixed) { u->beta = S->rho; continue; }
+        double trA = 0.0, trJ = 0.0;
+        for (int d = 0; d < u->n; d++) trA += u->A[d * u->n + d];
+        for (int j = 0; j < S->ncon; j++) {
+            con_t *c = &S->cons[j];
+            for (int s = 0; s < c->ns; s++) {
+                if (c->sub[s] != i) continue;
+                for (int q = 0; q < c->rows * u->n; q++) trJ += c->J[s][q] * c->J[s][q];
+            }
+        }
+        u->beta = trJ > 0.0 ? trA / trJ : 1.0;
+    }
+    /* factorise K_i = A_i + beta_i J_ci^T J_ci */
+    for (int i = 0; i < S->nsub; i++) {
+        sub_t *u = &S->subs[i];
+        int n = u->n;
+        double *K = (double *)xcalloc((size_t)n * n, sizeof(double));
+        memcpy(K, u->A, sizeof(double) * (size_t)n * n);
+        for (int j = 0; j < S->ncon; j++) {
+            con_t *c = &S->cons[j];
+            for (int s = 0; s < c->ns; s++) {
+                if (c->sub[s] != i) continue;
+                const double *J = c->J[s];
+                for (int r = 0; r < c->rows; r++)
+                    for (int p = 0; p < n; p++)
+                        for (int q = 0; q < n; q++)
+                            K[p * n + q] += u->beta * J[r * n + p] * J[r * n + q];
+            }
+        }
+        int rc = cholesky(n, K, u->L);
+        free(K);
+        if (rc) { S->status = -3; return -3; }
+    }
+    /* initial z, u (cold: zeros; warm: previous step's z and -lambda) */
+    for (int j = 0; j < S->ncon; j++) {
+        con_t *c = &S->cons[j];
+        for (int s = 0; s < c->ns; s++) {
+            double be = beta_of(S, c->sub[s]);
+            for (int r = 0; r < c->rows; r++) {
+                int q = s * c->rows + r;
+                if (S->warm_prev && c->has_prev) {
+                    c->z[q] = c->zprev[q];
+                    c->u[q] = -c->lamprev[r];
+                } else {
+                    c->z[q] = 0.0;
+                    c->u[q] = 0.0;
+                }
+                c->yold[q] = be * c->z[q] + c->u[q];
+            }
+        }
+    }
+    S->iters = 0; S->converged = 0;
+    S->r_p = INFINITY; S->r_d = INFINITY; S->theta = INFINITY;
+    int L = S->max_iters;
+    for (int l = 0; l < L; l++) {
+        /* v-step: rhs_i = b_i + J_ci^T (beta_i z_i - u_i); K_i v_i = rhs_i */
+        for (int i = 0; i < S->nsub; i++) {
+            sub_t *u = &S->subs[i];
+            memcpy(u->rhs, u->b, sizeof(double) * u->n);
+        }
+        for (int j = 0; j < S->ncon; j++) {
+            con_t *c = &S->cons[j];
+            for (int s = 0; s < c->ns; s++) {
+                sub_t *u = &S->subs[c->sub[s]];
+                for (int r = 0; r < c->rows; r++) {
+                    int q = s * c->rows + r;
+                    double w = u->beta * c->z[q] - c->u[q];
+                    for (int p = 0; p < u->n; p++) u->rhs[p] += c->J[s][r * u->n + p] * w;
+                }
+            }
+        }
+        for (int i = 0; i < S->nsub; i++) {
+            sub_t *u = &S->subs[i];
+            memcpy(u->v, u->rhs, sizeof(double) * u->n);
+            chol_solve(u->n, u->L, u->v);
+        }
+        /* x_i = J_ci v_i ; y_i = beta_i x_i + u_i ; theta */
+        double theta = 0.0;
+        for (int j = 0; j < S->ncon; j++) {
+            con_t *c = &S->cons[j];
+            for (int s = 0; s < c->ns; s++) {
+                sub_t *u = &S->subs[c->sub[s]];
+                for (int r = 0; r < c->rows; r++) {
+                    int q = s * c->rows + r;
+                    double acc = 0.0;
+                    for (int p = 0; p < u->n; p++) acc += c->J[s][r * u->n + p] * u->v[p];
+                    c->x[q] = acc;
+                    c->y[q] = u->beta * acc + c->u[q];
+                    double d = c->y[q] - c->yold[q];
+                    theta += d * d;
+                    c->yold[q] = c->y[q];
+                }
+            }
+        }
+        S->theta = theta;
+        S->iters = l + 1;
+        if (S->stop_theta && l >= 1 && theta < S->theta_th) {
+            S->converged = 1;
+            if (S->trace && l < S->trace_cap) {
+                S->trace[3 * l] = theta; S->trace[3 * l + 1] = NAN; S->trace[3 * l + 2] = NAN;
+            }
+            break;
+        }
+        /* z-step per constraint, then u-step, then residuals */
+        double rp = 0.0, rd = 0.0, rz = 0.0;
+        for (int j = 0; j < S->ncon; j++) {
+            con_t *c = &S->cons[j];
+            double beta[MAXSIDES];
+            for (int s = 0; s < c->ns; s++) beta[s] = beta_of(S, c->sub[s]);
+            orc_project(c->type, c->rows, c->ns, beta, c->y, c->e, c->k, c->alpha, c->mu, c->lam);
+            for (int s = 0; s < c->ns; s++) {
+                for (int r = 0; r < c->rows; r++) {
+                    int q = s * c->rows + r;
+                    c->zold[q] = c->z[q];
+                    c->z[q] = (c->y[q] + c->lam[r]) / beta[s];
+                    c->u[q] = c->u[q] + beta[s] * (c->x[q] - c->z[q]);
+                    double a = fabs(c->x[q] - c->z[q]);
+                    if (a > rp) rp = a;
+                    double dz = fabs(c->z[q] - c->zold[q]);
+                    if (dz > rz) rz = dz;
+                    double b = beta[s] * dz;
+                    if (b > rd) rd = b;
+                }
+            }
+        }
+        S->r_p = rp; S->r_d = rd;
+        if (S->trace && l < S->trace_cap) {
+            S->trace[3 * l] = theta; S->trace[3 * l + 1] = rp; S->trace[3 * l + 2] = rd;
+        }
+        if (!S->stop_theta && S->tol > 0.0 && rp <= S->tol && rz <= S->tol) {
+            S->converged = 1;
+            break;
+        }
+        if (!isfinite(rp) || !isfinite(theta)) { S->status = -4; break; }
+    }
+    /* keep lambda and z for the next step's warm start */
+    for (int j = 0; j < S->ncon; j++) {
+        con_t *c = &S->cons[j];
+        memcpy(c->lamprev, c->lam, sizeof(double) * c->rows);
+        memcpy(c->zprev, c->z, sizeof(double) * c->rows * c->ns);
+        c->has_prev = 1;
+    }
+    /* state update from v-hat (Eq. ddyn): v_{k+1} = 2 v-hat - v_k ; p += h v-hat ;
+       R <- R Exp(h w-hat) with the body-frame angular velocity */
+    for (int i = 0; i < S->nsub; i++) {
+        sub_t *u = &S->subs[i];
+        if (u->kind != SUB_RIGID) continue;
+        for (int k = 0; k < u->nb; k++) {
+            body_t *B = &u->bodies[k];
+            const double *vh = u->v + 6 * k;
+            for (int d = 0; d < 3; d++) {
+                B->p[d] += S->h * vh[d];
+                B->v[d] = 2.0 * vh[d] - B->v[d];
+                B->w[d] = 2.0 * vh[3 + d] - B->w[d];
+            }
+            double a[3] = {S->h * vh[3], S->h * vh[4], S->h * vh[5]};
+            double th = sqrt(dot3(a, a));
+            double dq[4];
+            if (th > 0.0) {
+                double sn = sin(0.5 * th) / th;
+                dq[0] = cos(0.5 * th); dq[1] = a[0] * sn; dq[2] = a[1] * sn; dq[3] = a[2] * sn;
+            } else { dq[0] = 1.0; dq[1] = dq[2] = dq[3] = 0.0; }
+            double *q = B->q, nq[4];
+            nq[0] = q[0] * dq[0] - q[1] * dq[1] - q[2] * dq[2] - q[3] * dq[3];
+            nq[1] = q[0] * dq[1] + q[1] * dq[0] + q[2] * dq[3] - q[3] * dq[2];
+            nq[2] = q[0] * dq[2] - q[1] * dq[3] + q[2] * dq[0] + q[3] * dq[1];
+            nq[3] = q[0] * dq[3] + q[1] * dq[2] - q[2] * dq[1] + q[3] * dq[0];
+            double nn = sqrt(nq[0] * nq[0] + nq[1] * nq[1] + nq[2] * nq[2] + nq[3] * nq[3]);
+            for (int d = 0; d < 4; d++) q[d] = nq[d] / nn;
+        }
+    }
+    return S->status;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* accessors                                                                             */
+
+void orc_set_trace(orc_scene *S, double *buf, int cap) { S->trace = buf; S->trace_cap = cap; }
+int orc_nsub(orc_scene *S) { return S->nsub; }
+int orc_ncon(orc_scene *S) { return S->ncon; }
+int orc_n(orc_scene *S, int i) { return S->subs[i].n; }
+int orc_rows(orc_scene *S, int j) { return S->cons[j].rows; }
+int orc_nsides(orc_scene *S, int j) { return S->cons[j].ns; }
+double orc_beta(orc_scene *S, int i) { return S->subs[i].beta; }
+
+void orc_get_vhat(orc_scene *S, int i, double *out) { memcpy(out, S->subs[i].v, sizeof(double) * S->subs[i].n); }
+
+void orc_get_Ab(orc_scene *S, int i, double *A, double *b)
+{
+    sub_t *u = &S->subs[i];
+    if (A) memcpy(A, u->A, sizeof(double) * (size_t)u->n * u->n);
+    if (b) memcpy(b, u->b, sizeof(double) * u->n);
+}
+
+void orc_get_L(orc_scene *S, int i, double *L) { memcpy(L, S->subs[i].L, sizeof(double) * (size_t)S->subs[i].n * S->subs[i].n); }
+
+void orc_get_lambda(orc_scene *S, int j, double *out) { memcpy(out, S->cons[j].lam, sizeof(double) * S->cons[j].rows); }
+
+/* which: 0 x, 1 z, 2 u, 3 y */
+void orc_get_side(orc_scene *S, int j, int which, double *out)
+{
+    con_t *c = &S->cons[j];
+    double *src = which == 0 ? c->x : which == 1 ? c->z : which == 2 ? c->u : c->y;
+    memcpy(out, src, sizeof(double) * c->rows * c->ns);
+}
+
+/* the rows of constraint j as assembled for the last step: e (rows) and J per side */
+void orc_get_rows(orc_scene *S, int j, double *e, double *J)
+{
+    con_t *c = &S->cons[j];
+    if (e) memcpy(e, c->e, sizeof(double) * c->rows);
+    if (J) {
+        double *p = J;
+        for (int s = 0; s < c->ns; s++) {
+            size_t cnt = (size_t)c->rows * S->subs[c->sub[s]].n;
+            memcpy(p, c->J[s], cnt * sizeof(double));
+            p += cnt;
+        }
+    }
+}
+
+int orc_con_sub(orc_scene *S, int j, int s) { return S->cons[j].sub[s]; }
+
+/* assemble (without solving) so tests can read A, b, J, e at the current state */
+void orc_assemble(orc_scene *S)
+{
+    for (int i = 0; i < S->nsub; i++)
+        if (S->subs[i].kind == SUB_RIGID) assemble_rigid(S, &S->subs[i]);
+    for (int j = 0; j < S->ncon; j++)
+        if (S->cons[j].src != SRC_ROWS) assemble_joint(S, &S->cons[j]);
+}
+
+/* position-level value phi of a rigid-model constraint at the current state */
+void orc_joint_phi(orc_scene *S, int j, double *phi)
+{
+    double Ja[30], Jb[30];
+    joint_rows(S, &S->cons[j], phi, Ja, Jb);
+}
+
+void orc_get_body(orc_scene *S, int i, int k, double *out)
+{
+    body_t *B = &S->subs[i].bodies[k];
+    out[0] = B->m;
+    memcpy(out + 1, B->I, 3 * sizeof(double));
+    memcpy(out + 4, B->p, 3 * sizeof(double));
+    memcpy(out + 7, B->q, 4 * sizeof(double));
+    memcpy(out + 11, B->v, 3 * sizeof(double));
+    memcpy(out + 14, B->w, 3 * sizeof(double));
+}
+
+void orc_set_body(orc_scene *S, int i, int k, const double *in)
+{
+    body_t *B = &S->subs[i].bodies[k];
+    B->m = in[0];
+    memcpy(B->I, in + 1, 3 * sizeof(double));
+    memcpy(B->p, in + 4, 3 * sizeof(double));
+    memcpy(B->q, in + 7, 4 * sizeof(double));
+    memcpy(B->v, in + 11, 3 * sizeof(double));
+    memcpy(B->w, in + 14, 3 * sizeof(double));
+}
+
+void orc_set_generic(orc_scene *S, int i, const double *A, const double *b)
+{
+    sub_t *u = &S->subs[i];
+    if (A) memcpy(u->A, A, sizeof(double) * (size_t)u->n * u->n);
+    if (b) memcpy(u->b, b, sizeof(double) * u->n);
+}
+
+/* out: r_p, r_d, theta, iters, converged, status */
+void orc_residuals(orc_scene *S, double *out)
+{
+    out[0] = S->r_p; out[1] = S->r_d; out[2] = S->theta;
+    out[3] = S->iters; out[4] = S->converged; out[5] = S->status;
+}
+
+/* standalone dense SPD solve through the oracle's Cholesky (for pins) */
+int orc_chol_solve(int n, const double *K, const double *r, double *x)
+{
+    double *L = (double *)xcalloc((size_t)n * n, sizeof(double));
+    int rc = cholesky(n, K, L);
+    if (!rc) { memcpy(x, r, sizeof(double) * n); chol_solve(n, L, x); }
+    free(L);
+    return rc;
+}
+
+void orc_free(orc_scene *S)
+{
+    if (!S) return;
+    for (int i = 0; i < S->nsub; i++) {
+        sub_t *u = &S->subs[i];
+        free(u->A); free(u->b); free(u->L); free(u->v); free(u->rhs); free(u->bodies);
+    }
+    for (int j = 0; j < S->ncon; j++) {
+        con_t *c = &S->cons[j];
+        for (int s = 0; s < c->ns; s++) free(c->J[s]);
+        free(c->e); free(c->x); free(c->z); free(c->u); free(c->y); free(c->yold);
+        free(c->zold); free(c->zprev); free(c->lam); free(c->lamprev);
+    }
+    free(S->subs); free(S->cons); free(S);
+}

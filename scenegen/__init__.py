@@ -1,0 +1,408 @@
+"""Seeded synthetic scene generators.
+
+This module only describes scenes: bodies, masses, initial poses, joint anchors and axes,
+generic SPD blocks and random constraint rows.  It holds none of the method's arithmetic
+(no dynamics assembly, no Jacobians, no projections, no ADMM): both the CPU oracle and the
+CUDA library consume the descriptions built here, and each side does all of the method's
+work in its own code.
+
+Scene shapes follow the paper's examples (Sec. IV-A: rigid chains, articulated robots with
+point contacts, split deformable blocks) at the sizes of the workloads this project
+measures; every draw comes from ``numpy.random.default_rng(seed)``.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import List, Optional, Sequence, Tuple
+
+import numpy as np
+
+# Projection types of a constraint (Sec. II-A: soft, hard, contact; hard covers equations
+# and inequalities).
+EQUALITY, HARD, SOFT, CONTACT = 0, 1, 2, 3
+TYPE_NAMES = {EQUALITY: "equality", HARD: "hard", SOFT: "soft", CONTACT: "contact"}
+
+# Interface sources: explicit rows, or a rigid-body model constraint whose rows are built
+# from the bodies' state every step.
+ROWS, BALL, REVOLUTE, ANGLE_PD, PLANE_CONTACT = 0, 1, 2, 3, 4
+
+WORLD = -1
+
+
+@dataclass
+class Body:
+    """A rigid body in maximal coordinates.
+
+    ``q`` is the unit quaternion (w, x, y, z) of the body-to-world rotation, ``v`` the
+    world-frame linear velocity of the centre of mass, ``w`` the body-frame angular
+    velocity.  The inertia is diagonal in the body frame (principal axes).
+    """
+
+    m: float
+    I: np.ndarray
+    p: np.ndarray
+    q: np.ndarray
+    v: np.ndarray
+    w: np.ndarray
+
+
+@dataclass
+class GenericSub:
+    """A subsystem given directly by its SPD block ``A`` (n x n) and vector ``b``."""
+
+    A: np.ndarray
+    b: np.ndarray
+
+    @property
+    def n(self) -> int:
+        return int(self.b.shape[0])
+
+
+@dataclass
+class RigidSub:
+    """A subsystem made of rigid bodies (6 DOF each: [v, w] per body)."""
+
+    bodies: List[Body]
+
+    @property
+    def n(self) -> int:
+        return 6 * len(self.bodies)
+
+
+@dataclass
+class RowsIf:
+    """An interface given by explicit rows.
+
+    ``subs[s]`` is the subsystem of side s; ``J[s]`` is (rows x n_subs[s]); the constraint
+    value is sum_s J[s] v_subs[s] + e.  ``type`` is one of EQUALITY/HARD/SOFT/CONTACT;
+    a contact has 3 rows ordered (normal, tangent 1, tangent 2).
+    """
+
+    type: int
+    subs: List[int]
+    J: List[np.ndarray]
+    e: np.ndarray
+    k: float = 0.0
+    alpha: float = 0.0
+    mu: float = 0.0
+
+    @property
+    def rows(self) -> int:
+        return int(self.e.shape[0])
+
+
+@dataclass
+class JointIf:
+    """A rigid-body model constraint between body ``a`` and body ``b`` (or the world).
+
+    ``a`` and ``b`` are (subsystem, body index) pairs; ``b`` is None for the world, in which
+    case ``anchor_b`` is a world point and ``axis_b``/``ref_b`` are world vectors.
+
+    kind BALL:          anchor_a (a frame), anchor_b (b frame)                    3 rows
+    kind REVOLUTE:      + axis_a, ref_a (a frame, ref_a orthogonal to axis_a),
+                        axis_b (b frame)                                         5 rows
+    kind ANGLE_PD:      axis_a, ref_a (a frame), ref_b (b frame), kp, kd, target 1 soft row
+    kind PLANE_CONTACT: anchor_a = contact point in a's frame, plane_z, mu        3 rows
+    """
+
+    kind: int
+    a: Tuple[int, int]
+    b: Optional[Tuple[int, int]] = None
+    anchor_a: np.ndarray = field(default_factory=lambda: np.zeros(3))
+    anchor_b: np.ndarray = field(default_factory=lambda: np.zeros(3))
+    axis_a: np.ndarray = field(default_factory=lambda: np.array([1.0, 0.0, 0.0]))
+    axis_b: np.ndarray = field(default_factory=lambda: np.array([1.0, 0.0, 0.0]))
+    ref_a: np.ndarray = field(default_factory=lambda: np.array([0.0, 1.0, 0.0]))
+    ref_b: np.ndarray = field(default_factory=lambda: np.array([0.0, 1.0, 0.0]))
+    kp: float = 0.0
+    kd: float = 0.0
+    target: float = 0.0
+    plane_z: float = 0.0
+    mu: float = 0.0
+
+
+@dataclass
+class Scene:
+    subs: list
+    ifs: list
+
+
+@dataclass
+class Options:
+    """Per-run settings shared by both implementations (each parses them itself)."""
+
+    h: float = 1e-3
+    gravity: Tuple[float, float, float] = (0.0, 0.0, -9.81)
+    baumgarte: float = 0.2
+    beta_mode: str = "trace"      # "trace": beta_i = Tr A_i / Tr(J_i^T J_i); "fixed": rho
+    rho: float = 1e3
+    warm: str = "prev"            # "cold" or "prev" (previous step's lambda and z)
+    stop: str = "primal"          # "primal": r_p <= tol_primal; "theta": theta < theta_th
+    tol_primal: float = 1e-6      # <= 0 runs exactly max_iters iterations
+    theta_th: float = 1e-12
+    max_iters: int = 1000
+
+
+@dataclass
+class Problem:
+    scenes: List[Scene]
+    options: Options
+    name: str = ""
+
+
+# ----------------------------------------------------------------------------------------
+# small rotation helpers (input construction only)
+
+def _quat_from_rotvec(r: np.ndarray) -> np.ndarray:
+    th = float(np.linalg.norm(r))
+    if th < 1e-300:
+        return np.array([1.0, 0.0, 0.0, 0.0])
+    a = np.asarray(r, dtype=np.float64) / th
+    return np.concatenate([[np.cos(th / 2)], np.sin(th / 2) * a])
+
+
+def _quat_mul(p: np.ndarray, q: np.ndarray) -> np.ndarray:
+    pw, px, py, pz = p
+    qw, qx, qy, qz = q
+    return np.array([
+        pw * qw - px * qx - py * qy - pz * qz,
+        pw * qx + px * qw + py * qz - pz * qy,
+        pw * qy - px * qz + py * qw + pz * qx,
+        pw * qz + px * qy - py * qx + pz * qw,
+    ])
+
+
+def _quat_to_mat(q: np.ndarray) -> np.ndarray:
+    w, x, y, z = q
+    return np.array([
+        [1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+        [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+        [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)],
+    ])
+
+
+def box_inertia(m: float, a: float, b: float, c: float) -> np.ndarray:
+    """Principal inertia of a solid box with edges a (x), b (y), c (z)."""
+    return np.array([m * (b * b + c * c) / 12.0, m * (a * a + c * c) / 12.0,
+                     m * (a * a + b * b) / 12.0])
+
+
+# ----------------------------------------------------------------------------------------
+# Serial chain of 8 rigid links (shaped like the cable of Sec. IV-A): the 3D chain workload
+
+
+def chain(seed: int = 0, n_links: int = 8, links_per_sub: int = 2, pinned: bool = True,
+          gravity: bool = True, angle: float = 0.5, rho: Optional[float] = 1e3,
+          h: float = 1e-3, max_iters: int = 100, tol_primal: float = -1.0,
+          warm: str = "prev") -> Problem:
+    """8 boxes 0.1 x 0.02 x 0.02 m, density 1000, ball joints at the box ends.
+
+    The first link's -x end is pinned to the world origin (a one-sided ball joint).  The
+    chain is split into subsystems of ``links_per_sub`` consecutive links: joints inside a
+    subsystem are intra-subsystem constraints (|S_j| = 1), joints between subsystems are
+    coupling interfaces (|S_j| = 2).  Initial joint rotation vectors are uniform in
+    [-angle, angle]^3, composed along the chain; all velocities start at zero.
+    """
+    rng = np.random.default_rng(seed)
+    L, wdt = 0.1, 0.02
+    m = L * wdt * wdt * 1000.0
+    I = box_inertia(m, L, wdt, wdt)
+    half = np.array([L / 2, 0.0, 0.0])
+    rv = rng.uniform(-angle, angle, size=(n_links, 3))
+    bodies: List[Body] = []
+    q = np.array([1.0, 0.0, 0.0, 0.0])
+    end = np.zeros(3)
+    for k in range(n_links):
+        q = _quat_mul(q, _quat_from_rotvec(rv[k]))
+        q = q / np.linalg.norm(q)
+        R = _quat_to_mat(q)
+        c = end + R @ half
+        bodies.append(Body(m, I.copy(), c, q.copy(), np.zeros(3), np.zeros(3)))
+        end = c + R @ half
+    assert n_links % links_per_sub == 0
+    n_sub = n_links // links_per_sub
+    subs = [RigidSub(bodies[s * links_per_sub:(s + 1) * links_per_sub]) for s in range(n_sub)]
+
+    def ref(k):
+        return (k // links_per_sub, k % links_per_sub)
+
+    ifs = []
+    if pinned:
+        ifs.append(JointIf(BALL, a=ref(0), b=None, anchor_a=-half, anchor_b=np.zeros(3)))
+    for k in range(1, n_links):
+        ifs.append(JointIf(BALL, a=ref(k - 1), b=ref(k), anchor_a=half.copy(), anchor_b=-half))
+    opts = Options(h=h, gravity=(0.0, 0.0, -9.81) if gravity else (0.0, 0.0, 0.0),
+                   beta_mode="fixed" if rho is not None else "trace",
+                   rho=rho if rho is not None else 0.0, warm=warm,
+                   tol_primal=tol_primal, max_iters=max_iters)
+    return Problem([Scene(subs, ifs)], opts, name="chain8")
+
+
+# ----------------------------------------------------------------------------------------
+# Legged robots with point-foot contacts (articulated-with-contact workload)
+
+
+def _rot_axis(axis: np.ndarray, ang: float) -> np.ndarray:
+    return _quat_from_rotvec(np.asarray(axis, dtype=np.float64) * ang)
+
+
+def legged_robot(rng: np.random.Generator, origin_xy=(0.0, 0.0), kp: float = 50.0,
+                 kd: float = 1.0, mu: float = 0.8, offset: float = 0.2,
+                 drop=(0.3, 0.5)) -> Scene:
+    """A floating trunk plus 4 legs of 3 revolute joints (hip roll x, hip pitch y, knee y).
+
+    One subsystem for the trunk (6 DOF) and one per leg (3 links, 18 DOF).  The hip-roll
+    joint couples trunk and leg (|S_j| = 2); hip pitch and knee are intra-leg.  Every joint
+    has a PD drive (soft row, Sec. II-A) towards its initial offset, drawn uniform in
+    [-offset, offset]; each foot is a point contact with the plane z = 0.  The trunk starts
+    level, with its lowest foot at a height uniform in ``drop`` above the plane.
+    """
+    rho = 1000.0
+    tx, ty, tz = 0.3, 0.2, 0.08
+    mt = tx * ty * tz * rho
+    trunk = Body(mt, box_inertia(mt, tx, ty, tz), np.zeros(3), np.array([1.0, 0, 0, 0]),
+                 np.zeros(3), np.zeros(3))
+    lens = [0.05, 0.15, 0.15]
+    lw = 0.04
+    hips = [np.array([sx * 0.12, sy * 0.07, -tz / 2]) for sx in (1, -1) for sy in (1, -1)]
+    ex, ey = np.array([1.0, 0, 0]), np.array([0, 1.0, 0])
+    refz = np.array([0.0, 0.0, 1.0])
+    legs = []
+    feet_world = []
+    offsets = rng.uniform(-offset, offset, size=(4, 3))
+    for lg in range(4):
+        links = []
+        q_par = trunk.q
+        p_par = trunk.p
+        anchor_par = hips[lg]
+        axes = [ex, ey, ey]
+        for k in range(3):
+            qk = _quat_mul(q_par, _rot_axis(axes[k], offsets[lg, k]))
+            Rk = _quat_to_mat(qk)
+            joint_w = p_par + _quat_to_mat(q_par) @ anchor_par
+            top = np.array([0.0, 0.0, lens[k] / 2])
+            ck = joint_w - Rk @ top
+            mk = lw * lw * lens[k] * rho
+            links.append(Body(mk, box_inertia(mk, lw, lw, lens[k]), ck, qk, np.zeros(3),
+                              np.zeros(3)))
+            q_par, p_par, anchor_par = qk, ck, -top
+        foot = np.array([0.0, 0.0, -lens[2] / 2])
+        feet_world.append(links[2].p + _quat_to_mat(links[2].q) @ foot)
+        legs.append(links)
+    H = rng.uniform(*drop)
+    zmin = min(f[2] for f in feet_world)
+    shift = np.array([origin_xy[0], origin_xy[1], H - zmin])
+    trunk.p = trunk.p + shift
+    for links in legs:
+        for b in links:
+            b.p = b.p + shift
+    subs = [RigidSub([trunk])] + [RigidSub(links) for links in legs]
+    ifs = []
+    for lg in range(4):
+        s = lg + 1
+        parents = [(0, 0), (s, 0), (s, 1)]
+        children = [(s, 0), (s, 1), (s, 2)]
+        axes = [ex, ey, ey]
+        anchors_a = [hips[lg], np.array([0, 0, -lens[0] / 2]), np.array([0, 0, -lens[1] / 2])]
+        for k in range(3):
+            top = np.array([0.0, 0.0, lens[k] / 2])
+            ax = axes[k]
+            rf = refz if k == 0 else ex
+            ifs.append(JointIf(REVOLUTE, a=parents[k], b=children[k], anchor_a=anchors_a[k],
+                               anchor_b=top, axis_a=ax.copy(), axis_b=ax.copy(),
+                               ref_a=rf.copy(), ref_b=rf.copy()))
+            ifs.append(JointIf(ANGLE_PD, a=parents[k], b=children[k], axis_a=ax.copy(),
+                               axis_b=ax.copy(), ref_a=rf.copy(), ref_b=rf.copy(), kp=kp,
+                               kd=kd, target=float(offsets[lg, k])))
+        ifs.append(JointIf(PLANE_CONTACT, a=(s, 2), anchor_a=np.array([0, 0, -lens[2] / 2]),
+                           plane_z=0.0, mu=mu))
+    return Scene(subs, ifs)
+
+
+def robots(seed: int = 0, n_robots: int = 64, h: float = 2e-3, tol_primal: float = 1e-6,
+           max_iters: int = 1000, warm: str = "prev", **kw) -> Problem:
+    """``n_robots`` independent legged robots, one scene each, on a 1 m grid."""
+    rng = np.random.default_rng(seed)
+    side = int(np.ceil(np.sqrt(max(n_robots, 1))))
+    scenes = [legged_robot(rng, origin_xy=(float(r % side), float(r // side)), **kw)
+              for r in range(n_robots)]
+    opts = Options(h=h, beta_mode="trace", warm=warm, tol_primal=tol_primal,
+                   max_iters=max_iters)
+    return Problem(scenes, opts, name=f"robots{n_robots}")
+
+
+# ----------------------------------------------------------------------------------------
+# Generic SPD blocks coupled by random rows (exercises every projection type and |S_j|)
+
+
+def generic_scene(rng: np.random.Generator, n_sub: int = 4, n_range=(1, 12),
+                  types: Sequence[int] = (EQUALITY, HARD, SOFT, CONTACT),
+                  extra: int = 2, max_sides: int = 3, density: float = 1.0) -> Scene:
+    """Random SPD blocks and a random constraint graph.
+
+    Blocks: A = G G^T / n + diag(U[0.5, 2]) scaled by a per-block mass in [0.1, 10].
+    Constraints: a random spanning tree (|S_j| = 2), ``extra`` further constraints on 1..
+    ``max_sides`` distinct subsystems, and one intra constraint (|S_j| = 1) per block.
+    Rows per constraint: 1..3 (contact: 3).  J entries N(0, 1) with the given density.
+    """
+    subs = []
+    for _ in range(n_sub):
+        n = int(rng.integers(n_range[0], n_range[1] + 1))
+        G = rng.standard_normal((n, n))
+        mass = 10.0 ** rng.uniform(-1, 1)
+        A = mass * (G @ G.T / n + np.diag(rng.uniform(0.5, 2.0, n)))
+        b = mass * rng.standard_normal(n)
+        subs.append(GenericSub(A, b))
+    edges: List[List[int]] = []
+    for i in range(1, n_sub):
+        edges.append([int(rng.integers(0, i)), i])
+    for _ in range(extra):
+        ns = int(rng.integers(1, min(max_sides, n_sub) + 1))
+        edges.append([int(x) for x in rng.choice(n_sub, size=ns, replace=False)])
+    for i in range(n_sub):
+        edges.append([i])
+    ifs = []
+    for sides in edges:
+        t = int(types[int(rng.integers(0, len(types)))])
+        rows = 3 if t == CONTACT else int(rng.integers(1, 4))
+        J = []
+        for s in sides:
+            M = rng.standard_normal((rows, subs[s].n))
+            if density < 1.0:
+                M = M * (rng.random(M.shape) < density)
+            J.append(M)
+        e = rng.standard_normal(rows)
+        k = float(10.0 ** rng.uniform(0, 2))
+        alpha = float(10.0 ** rng.uniform(-3, -1))
+        mu = float(rng.uniform(0.2, 1.0))
+        ifs.append(RowsIf(t, list(sides), J, e, k=k, alpha=alpha, mu=mu))
+    return Scene(subs, ifs)
+
+
+def generic(seed: int = 0, n_scenes: int = 4, tol_primal: float = -1.0, max_iters: int = 50,
+            beta_mode: str = "trace", rho: float = 1.0, warm: str = "cold", **kw) -> Problem:
+    rng = np.random.default_rng(seed)
+    scenes = [generic_scene(rng, **kw) for _ in range(n_scenes)]
+    opts = Options(h=1e-3, gravity=(0.0, 0.0, 0.0), beta_mode=beta_mode, rho=rho,
+                   warm=warm, tol_primal=tol_primal, max_iters=max_iters)
+    return Problem(scenes, opts, name="generic")
+
+
+def problem_sizes(p: Problem) -> dict:
+    """Counts of subsystems, DOF, constraints, rows and side-rows (plain bookkeeping)."""
+    n_sub = sum(len(s.subs) for s in p.scenes)
+    dof = sum(sub.n for s in p.scenes for sub in s.subs)
+    n_if = sum(len(s.ifs) for s in p.scenes)
+    rows = 0
+    side_rows = 0
+    for s in p.scenes:
+        for itf in s.ifs:
+            if isinstance(itf, RowsIf):
+                r, ns = itf.rows, len(itf.subs)
+            else:
+                r = {BALL: 3, REVOLUTE: 5, ANGLE_PD: 1, PLANE_CONTACT: 3}[itf.kind]
+                ns = 1 if (itf.b is None or itf.b[0] == itf.a[0]) else 2
+            rows += r
+            side_rows += r * ns
+    return dict(scenes=len(p.scenes), subsystems=n_sub, dof=dof, interfaces=n_if, rows=rows,
+                side_rows=side_rows)
