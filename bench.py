@@ -1,0 +1,346 @@
+"""Benchmark: simulation steps per second of the 64-legged-robot batch, every step iterated
+to primal residual <= 1e-6, on GB300 through libsubadmm (the C ABI in include/subadmm.h).
+
+One benchmark step = one time step of the whole batch: assembly, beta, factorisation, the
+ADMM loop to the stop rule, v-hat and the state update, all in the step kernel.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun every rank simulates its own seeded batch
+(scenes are independent: weak scaling, no data-path collective).  --impl reference times
+the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "sim steps/sec at primal residual ≤1e-6, chosen form vs plain FP64, 1 GB300"
+FP64_NOMINAL_TFLOPS = 1.25     # GB300 FP64 (non-tensor) rate quoted for this pool
+L2_FLUSH_BYTES = 512 << 20     # > 129 MB L2
+
+
+def workload_desc(n_robots: int, h: float) -> str:
+    return (f"{n_robots} independent legged robots (6-DOF trunk + 4 legs x 3 revolute joints, "
+            f"one subsystem per leg and one for the trunk, PD drives as soft rows, 4 point-foot "
+            f"plane contacts mu=0.8), dropped from 0.3-0.5 m; h={h:g} s; each step iterated to "
+            f"r_p<=1e-6 with the previous step's warm start")
+
+
+def algorithmic_work(problem):
+    """Per-scene algorithmic FLOPs of the method (triangular-solve form of Eq. admm-1i):
+    per iteration and subsystem 2 n^2 (two triangular solves) + 4 nnz(J_i) (J^T w and J v)
+    + 20 m_i (projection, updates, residuals); per step and subsystem n^3/3 (Cholesky)
+    + 2 sum_rows nnz(row)^2 (K = A + beta J^T J)."""
+    import numpy as np
+    out = []
+    for sc in problem.scenes:
+        n = [s.n for s in sc.subs]
+        m = [0] * len(n)
+        nnz = [0] * len(n)
+        rowsq = [0] * len(n)
+        for itf in sc.ifs:
+            if hasattr(itf, "J"):
+                for s, Jm in zip(itf.subs, itf.J):
+                    c = (np.asarray(Jm) != 0).sum(1)
+                    m[s] += itf.rows
+                    nnz[s] += int(c.sum())
+                    rowsq[s] += int((c ** 2).sum())
+                continue
+            kind = itf.kind
+            rows_cols = {1: [6, 6, 6], 2: [6, 6, 6, 3, 3], 3: [3], 4: [6, 6, 6]}[kind]
+            same = itf.b is None or itf.b[0] == itf.a[0]
+            nbody = 1 if itf.b is None else 2
+            if same:
+                s = itf.a[0]
+                cols = [c * nbody for c in rows_cols]
+                m[s] += len(cols)
+                nnz[s] += sum(cols)
+                rowsq[s] += sum(c * c for c in cols)
+            else:
+                for s in (itf.a[0], itf.b[0]):
+                    m[s] += len(rows_cols)
+                    nnz[s] += sum(rows_cols)
+                    rowsq[s] += sum(c * c for c in rows_cols)
+        it = sum(2 * ni * ni + 4 * zi + 20 * mi for ni, zi, mi in zip(n, nnz, m))
+        st = sum(ni ** 3 / 3.0 + 2 * q for ni, q in zip(n, rowsq))
+        out.append((it, st))
+    return out
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sms, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sms.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sms:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sms), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sms)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def cpu_baseline(problem, seconds: float):
+    """Time the FP64 CPU oracle, as it stands, on a bounded sample of the same workload:
+    the first steps of every scene of the batch, until ``seconds`` have elapsed."""
+    import oracle
+    scs = [oracle.OracleScene(sc, problem.options) for sc in problem.scenes]
+    t0 = time.perf_counter()
+    steps = 0
+    iters = 0
+    while True:
+        for o in scs:
+            o.step()
+            iters += o.residuals()["iters"]
+        steps += 1
+        if time.perf_counter() - t0 >= seconds or steps >= 500:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": steps / dt, "unit": "steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {steps} steps of all {len(scs)} scenes (whole batch per step), "
+                      f"single-threaded plain C -O2, {iters / max(steps * len(scs), 1):.1f} "
+                      f"iterations per scene-step",
+            "seconds": dt}
+
+
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return 0
+    import scenegen as sg
+    p = sg.robots(seed=0, n_robots=args.robots, h=2e-3, tol_primal=1e-6, max_iters=1000)
+    import oracle
+    scs = [oracle.OracleScene(sc, p.options) for sc in p.scenes]
+    # warm-up steps, then time K steps bounded to a few minutes
+    for _ in range(args.warmup):
+        for o in scs:
+            o.step()
+    t0 = time.perf_counter()
+    k = 0
+    for k in range(1, args.steps + 1):
+        for o in scs:
+            o.step()
+        if time.perf_counter() - t0 > args.reference_seconds:
+            break
+    dt = time.perf_counter() - t0
+    val = k / dt
+    line = {"metric": METRIC, "value": val, "unit": "steps/s", "n_gpus": world, "steps": k,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt / k, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": workload_desc(args.robots, 2e-3), "robots": args.robots,
+                       "form": "FP64 CPU oracle"},
+            "cpu_baseline": {"value": val, "unit": "steps/s", "cores": 1, "kind": "oracle",
+                             "sample": f"steps {args.warmup}..{args.warmup + k} of the batch"},
+            "e2e": {"value": val, "unit": "steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--robots", type=int, default=64)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--reference-seconds", type=float, default=120.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+    import scenegen as sg
+    from paper_2302_14344_gb300 import subadmm
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    h = 2e-3
+    p = sg.robots(seed=rank, n_robots=args.robots, h=h, tol_primal=1e-6, max_iters=1000)
+    sim = subadmm.Simulation(p, stream=stream.cuda_stream, device=local)
+    sizes = sim.sizes()
+    work = algorithmic_work(p)
+    it_flops = work[0][0]
+    st_flops = sum(w[1] for w in work)
+    assert all(w[0] == it_flops for w in work)
+
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    # warm-up steps (untimed)
+    for _ in range(args.warmup):
+        sim.step(1)
+    sim.sync()
+    sim.iteration_stats()   # clear counters
+
+    K = args.steps
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        for k in range(K):
+            flush.zero_()                      # L2 flushed between timed steps
+            ev0[k].record(stream)
+            sim.step(1)
+            ev1[k].record(stream)
+        torch.cuda.synchronize(dev)
+    if dist is not None:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+    t_ms = float(sum(step_ms))
+    stats = sim.iteration_stats()
+    not_conv = stats["not_converged"]
+    if dist is not None:
+        tt = torch.tensor([t_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    value = world * K / (t_ms / 1e3)
+
+    # roofline of the step kernel (the only kernel of a step): FP64 ALU
+    total_iters = stats["total_iters"]
+    flops = it_flops * total_iters + st_flops * K
+    achieved_tflops = flops / (t_ms / 1e3) / 1e12
+    peaks = measured_peaks()
+    roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_NOMINAL_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved_tflops / FP64_NOMINAL_TFLOPS,
+                "traffic": None,
+                "note": "FP64 non-tensor pipe; peak = nominal GB300 FP64 rate (152 SMs x "
+                        "2 FP64 FMA/clk x 2 flops x ~2.06 GHz); algorithmic flops of the "
+                        "triangular-solve form per iteration and per step"}
+
+    # end to end through the C ABI with host buffers: state in from pinned host memory,
+    # one step, state out to pinned host memory, every step
+    nb = sizes["bodies"]
+    hbuf = torch.empty(13 * nb, dtype=torch.float64).pin_memory()
+    subadmm.sim_read_state(sim.h, hbuf.data_ptr())
+    e2e_steps = min(K, 200)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        subadmm.sim_write_state(sim.h, hbuf.data_ptr())
+        sim.step(1)
+        subadmm.sim_read_state(sim.h, hbuf.data_ptr())
+    e2e_dt = time.perf_counter() - t0
+    e2e = {"value": world * e2e_steps / e2e_dt, "unit": "steps/s",
+           "h2d_bytes_per_step": 13 * 8 * nb, "d2h_bytes_per_step": 13 * 8 * nb,
+           "steps": e2e_steps, "timer": "host wall clock"}
+    if dist is not None:
+        tt = torch.tensor([e2e_dt], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e["value"] = world * e2e_steps / float(tt.item())
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": t_ms / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_desc(args.robots, h), "form": "plain FP64",
+                       "robots": args.robots, "scenes_per_gpu": sizes["scenes"],
+                       "subsystems": sizes["subsystems"], "dof": sizes["dof"],
+                       "interfaces": sizes["interfaces"], "rows": sizes["rows"],
+                       "side_rows": sizes["side_rows"], "parallelism": f"scenes x{world}",
+                       "l2": "flushed between timed steps (512 MiB write)",
+                       "launch": "one step kernel per step, one block of 256 threads per scene"},
+            "iterations": {"mean_per_scene_step": total_iters / max(stats["scene_steps"], 1),
+                           "max": stats["max_iters"], "not_converged": not_conv},
+            "interface_updates_per_s": sum(len(sc.ifs) for sc in p.scenes) * total_iters /
+                                       max(len(p.scenes), 1) * world / (t_ms / 1e3),
+            "roofline": roofline,
+            "e2e": e2e,
+            "gpu_launches": K,
+            "clocks": clk.summary(),
+            "kernel_ms": {"mean": statistics.mean(step_ms), "median": statistics.median(step_ms),
+                          "min": min(step_ms), "max": max(step_ms)},
+            "peaks_file": bool(peaks),
+        }
+        if not args.no_cpu_baseline and world == 1:
+            line["cpu_baseline"] = cpu_baseline(sg.robots(seed=0, n_robots=args.robots, h=h,
+                                                          tol_primal=1e-6, max_iters=1000),
+                                                args.cpu_seconds)
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

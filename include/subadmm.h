@@ -1,0 +1,181 @@
+/*
+ * subadmm.h -- C ABI of the GB300 (sm_103a) subsystem-based ADMM multibody solver.
+ *
+ * The method is that of "Modular and Parallelizable Multibody Physics Simulation via
+ * Subsystem-Based ADMM" (Lee, Lee & Lee, arXiv 2302.14344).  One time step (Algorithm 1):
+ *   construct A_i, b_i per subsystem (Eq. sdyn) and e_j, J_j per constraint (Sec. II-A);
+ *   beta_i = Tr(A_i) / Tr(J_ci^T J_ci) (Sec. III-D) or a fixed rho;
+ *   factorise K_i = A_i + beta_i J_ci^T J_ci once per step;
+ *   iterate  v-step  K_i v_i = b_i + J_ci^T (beta_i z_i - u_i),  x_i = J_ci v_i   (Eq. admm-1i)
+ *            z-step  per constraint, closed-form lambda_j, beta_i z_ij = y_ij + lambda_j
+ *                    with y_i = beta_i x_i + u_i                    (Eq. admm-2j, Eq. surrogate)
+ *            u-step  u_i += beta_i (x_i - z_i)                                    (Eq. admm-3)
+ *   until the stop rule holds; then update each subsystem's state from v-hat (Eq. ddyn).
+ *
+ * Every step of that loop runs in CUDA kernels on the device; nothing falls back to the host.
+ *
+ * Conventions for every call:
+ *   - Return value: SIM_OK (0) on success, a positive warning, or a negative error code; the
+ *     message of the last error is in sim_last_error().
+ *   - Ownership: host arrays passed in are copied before the call returns; the library never
+ *     keeps a caller's pointer.  A sim_t owns all device memory it allocates, freed by
+ *     sim_destroy().
+ *   - Topology (subsystems and interfaces) is fixed at the first sim_step(); adding after that
+ *     returns SIM_EINVAL.
+ *   - One host thread per sim_t.  Work is enqueued on the stream given in sim_options;
+ *     sim_step() is asynchronous, the sim_get_* / sim_residuals() calls synchronise it.
+ *   - Matrices are row-major double precision.  Indices are 0-based.
+ *   - Sign convention: constraint j's value is sum_{i in S_j} J_ij v_i + e_j; lambda_j acts on
+ *     subsystem i as J_ij^T lambda_j.
+ */
+#ifndef SUBADMM_H
+#define SUBADMM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define SIM_OK 0
+#define SIM_NOT_CONVERGED 1   /* warning: a scene hit max_iters before its stop rule held */
+#define SIM_EINVAL (-1)       /* bad argument, bad topology, or a scene too large           */
+#define SIM_ENOMEM (-2)       /* device or host allocation failed                           */
+#define SIM_ENOTSPD (-3)      /* K_i = A_i + beta_i J^T J had a pivot <= 0 (not SPD)        */
+#define SIM_ENAN (-4)         /* a residual became NaN or infinite                          */
+#define SIM_ECUDA (-5)        /* a CUDA runtime call failed                                 */
+
+/* subsystem kinds (Sec. III-A: rigid bodies, or any block given by A_i, b_i) */
+#define SIM_SUB_GENERIC 0     /* A_i (n x n, SPD) and b_i given directly                    */
+#define SIM_SUB_RIGID 1       /* rigid bodies in maximal coordinates, 6 DOF each            */
+
+/* interface kinds.  The first four give rows explicitly (J per side, e); the last four are
+ * rigid-body model constraints whose rows are rebuilt from the bodies' state every step. */
+#define SIM_IF_EQUALITY 0     /* sum J v + e = 0                       (hard, Eq. hcon)    */
+#define SIM_IF_HARD 1         /* sum J v + e >= 0, lambda >= 0, per row (Eq. hcon)          */
+#define SIM_IF_SOFT 2         /* lambda = -k (e + alpha sum J v)        (Eq. scon)          */
+#define SIM_IF_CONTACT 3      /* 3 rows (normal, t1, t2), Signorini-Coulomb (Eq. scc)       */
+#define SIM_IF_BALL 4         /* 3 equality rows: point of a == point of b                  */
+#define SIM_IF_REVOLUTE 5     /* 5 equality rows: ball + two axis-alignment rows            */
+#define SIM_IF_ANGLE_PD 6     /* 1 soft row: PD drive of the relative angle about an axis   */
+#define SIM_IF_PLANE_CONTACT 7/* 3 contact rows: body point against the plane z = plane_z  */
+
+/* option values */
+#define SIM_BETA_TRACE 0      /* beta_i = Tr(A_i) / Tr(J_ci^T J_ci)  (Sec. III-D)           */
+#define SIM_BETA_FIXED 1      /* beta_i = rho for every subsystem                           */
+#define SIM_WARM_COLD 0       /* z = u = 0 at the start of every step                       */
+#define SIM_WARM_PREV 1       /* z and u = -lambda of the previous step                     */
+#define SIM_STOP_PRIMAL 0     /* stop when max|x - z| <= tol and max|z^{l+1}-z^l| <= tol    */
+#define SIM_STOP_THETA 1      /* stop when theta < theta_th after the v-step (Eq. residual) */
+#define SIM_FP64 0            /* every step in double precision                             */
+
+/* what sim_get() reads */
+#define SIM_GET_VHAT 0        /* id = subsystem: n doubles, v-hat of the last step          */
+#define SIM_GET_LAMBDA 1      /* id = interface: rows doubles, lambda of the last step      */
+#define SIM_GET_BODIES 2      /* id = subsystem: nb x 17 doubles (body records, see below)  */
+#define SIM_GET_BETA 3        /* id = subsystem: 1 double                                   */
+#define SIM_GET_Z 4           /* id = interface: n_sides x rows doubles, z of the last step */
+
+typedef struct sim_s *sim_t;
+
+typedef struct sim_options {
+    double h;              /* time step (s)                                   default 1e-3  */
+    double gravity[3];     /* gravity acceleration on rigid bodies (m/s^2)  default 0,0,-9.81*/
+    double baumgarte;      /* gamma in e = gamma phi / h for joints       default 0.2       */
+    int beta_mode;         /* SIM_BETA_TRACE or SIM_BETA_FIXED            default TRACE      */
+    double rho;            /* beta for SIM_BETA_FIXED                     default 1e3        */
+    int warm;              /* SIM_WARM_COLD or SIM_WARM_PREV              default PREV       */
+    int stop;              /* SIM_STOP_PRIMAL or SIM_STOP_THETA           default PRIMAL     */
+    double tol_primal;     /* <= 0: run exactly max_iters iterations      default 1e-6       */
+    double theta_th;       /*                                             default 1e-12      */
+    int max_iters;         /* l_max                                       default 1000       */
+    int precision;         /* SIM_FP64                                    default FP64       */
+    int device;            /* CUDA device ordinal                         default 0          */
+    void *stream;          /* cudaStream_t to enqueue on; NULL = default  default NULL       */
+} sim_options;
+
+/* Fills *opt with the defaults listed above. */
+void sim_default_options(sim_options *opt);
+
+/* Creates an empty simulation on opt->device.  *out receives the handle. */
+int sim_create(const sim_options *opt, sim_t *out);
+
+/* Frees every device and host resource of s (NULL is ignored).  Synchronises s's stream. */
+void sim_destroy(sim_t s);
+
+/* Adds a subsystem to scene `scene` (scenes are independent problems solved side by side,
+ * numbered 0..; a new number opens a new scene).  Subsystem ids are global, in call order.
+ *   kind SIM_SUB_GENERIC: count = n >= 1; data = A (n*n, row-major, SPD) then b (n).
+ *   kind SIM_SUB_RIGID:   count = number of bodies >= 1; data = count records of 17 doubles
+ *       m, Ixx, Iyy, Izz (principal inertia in the body frame), p[3] (world position of the
+ *       centre of mass), q[4] (w, x, y, z unit quaternion, body to world), v[3] (world linear
+ *       velocity), w[3] (body-frame angular velocity).  DOF order: [v, w] per body.
+ *       A_i = (2/h) M_i and b_i = (2/h) M_i v_k - C v_k + f with C v_k = [0; w x I w] and
+ *       f = [m g; 0] (Eq. ddyn with v_{k+1} = 2 v-hat - v_k).  */
+int sim_add_subsystem(sim_t s, int scene, int kind, int count, const double *data, int *out_id);
+
+/* Adds an interface (constraint j) to scene `scene`; interface ids are global, in call order.
+ * Explicit-row kinds (SIM_IF_EQUALITY, SIM_IF_HARD, SIM_IF_SOFT, SIM_IF_CONTACT):
+ *   rows >= 1 (3 for a contact), n_sides = |S_j| in 1..8, sides = distinct subsystem ids of
+ *   the same scene; J = for each side in order, a rows x n_side row-major block; e = rows
+ *   values; params = {k, alpha, mu} (k, alpha for SOFT; mu for CONTACT; may be NULL
+ *   otherwise).  J and e are constant for the life of the simulation.
+ * Rigid-model kinds (SIM_IF_BALL, SIM_IF_REVOLUTE, SIM_IF_ANGLE_PD, SIM_IF_PLANE_CONTACT):
+ *   rows and n_sides are ignored; sides = {sub_a, body_a, sub_b, body_b}: (subsystem id, body
+ *   index inside it) of bodies a and b, sub_b = -1 for the world (PLANE_CONTACT uses a only);
+ *   J and e must be NULL; params = 23 doubles:
+ *     anchor_a[3] (a frame), anchor_b[3] (b frame, or a world point), axis_a[3], axis_b[3],
+ *     ref_a[3] (a frame, orthogonal to axis_a), ref_b[3] (b frame), kp, kd, target,
+ *     plane_z, mu.
+ *   BALL: phi = p_a + R_a anchor_a - (p_b + R_b anchor_b), e = baumgarte phi / h.
+ *   REVOLUTE: BALL rows plus t_k . (R_b axis_b) for t_1 = R_a ref_a, t_2 = R_a (axis_a x ref_a).
+ *   ANGLE_PD: angle theta of R_b ref_b from R_a ref_a about R_a axis_a; soft row with
+ *     k = kp, alpha = kd/kp + h/2, e = theta - target.
+ *   PLANE_CONTACT: rows (z, x, y) of the velocity of point anchor_a; e_n = gap/h for
+ *     gap >= 0, baumgarte gap/h otherwise; friction coefficient mu.
+ * Two bodies of the same subsystem give an intra-subsystem constraint (|S_j| = 1). */
+int sim_add_interface(sim_t s, int scene, int kind, int rows, int n_sides, const int *sides,
+                      const double *J, const double *e, const double *params, int *out_id);
+
+/* Replaces A_i and/or b_i of a SIM_SUB_GENERIC subsystem (host arrays; either may be NULL).
+ * Takes effect at the next step. */
+int sim_set_generic(sim_t s, int subsystem, const double *A, const double *b);
+
+/* Runs n_steps >= 1 time steps of every scene, asynchronously on the stream.  The first call
+ * uploads the topology.  Returns SIM_EINVAL if a scene does not fit the on-chip path. */
+int sim_step(sim_t s, int n_steps);
+
+/* Waits for the stream, then writes for scene `scene`'s last step:
+ * out[0] r_p = max|x - z|, out[1] r_d = max beta_i |z^{l+1} - z^l|, out[2] theta,
+ * out[3] iterations, out[4] 1 if the stop rule held, out[5] status (0 or a SIM_E* code).
+ * Returns that status, or SIM_NOT_CONVERGED if out[4] is 0. */
+int sim_residuals(sim_t s, int scene, double out[6]);
+
+/* Waits for the stream, then copies a quantity of the last step into host memory dst. */
+int sim_get(sim_t s, int what, int id, double *dst);
+
+/* Packed state of all rigid bodies, in subsystem then body order: 13 doubles per body
+ * (p[3], q[4], v[3], w[3]).  sim_read_state copies device -> host (dst holds 13 x bodies)
+ * after the stream's work; sim_write_state copies host -> device, enqueued on the stream. */
+int sim_read_state(sim_t s, double *dst);
+int sim_write_state(sim_t s, const double *src);
+
+/* Counts: out[0] scenes, out[1] subsystems, out[2] DOF, out[3] interfaces, out[4] rows,
+ * out[5] side-rows, out[6] rigid bodies, out[7] on-chip bytes of the largest scene. */
+int sim_sizes(sim_t s, long long out[8]);
+
+/* Sum and maximum over scenes of the iterations of all steps since the last call, and the
+ * number of scene-steps that ended without their stop rule holding; then clears them.
+ * out[0] total iterations, out[1] max iterations of a scene-step, out[2] not converged,
+ * out[3] scene-steps counted. */
+int sim_iteration_stats(sim_t s, long long out[4]);
+
+/* Blocks until every call enqueued on s's stream has finished. */
+int sim_sync(sim_t s);
+
+/* Message of the last error on s (or of the last failed sim_create when s is NULL). */
+const char *sim_last_error(sim_t s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SUBADMM_H */

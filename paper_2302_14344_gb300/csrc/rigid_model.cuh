@@ -1,0 +1,194 @@
+// Rigid-body model on the device: the per-step construction of A_i, b_i (Eq. ddyn with
+// v_{k+1} = 2 v-hat - v_k substituted, so A_i = (2/h) M_i, b_i = (2/h) M_i v_k - C v_k + f)
+// and of the rows J_j, e_j of ball, revolute, PD-drive and plane-contact constraints
+// (Sec. II-A), plus the state update of Algorithm 1's last line.
+//
+// Body record (17 doubles): m, I[3] (principal, body frame), p[3], q[4] (w, x, y, z),
+// v[3] (world), w[3] (body frame).  Generalized velocity per body: [v, w].
+#pragma once
+#include "layout.h"
+
+namespace subadmm {
+
+struct Rot { double r[9]; };
+
+__device__ __forceinline__ Rot quat_rot(const double *q)
+{
+    const double w = q[0], x = q[1], y = q[2], z = q[3];
+    Rot R;
+    R.r[0] = 1.0 - 2.0 * (y * y + z * z); R.r[1] = 2.0 * (x * y - w * z); R.r[2] = 2.0 * (x * z + w * y);
+    R.r[3] = 2.0 * (x * y + w * z); R.r[4] = 1.0 - 2.0 * (x * x + z * z); R.r[5] = 2.0 * (y * z - w * x);
+    R.r[6] = 2.0 * (x * z - w * y); R.r[7] = 2.0 * (y * z + w * x); R.r[8] = 1.0 - 2.0 * (x * x + y * y);
+    return R;
+}
+
+__device__ __forceinline__ void mul(const Rot &R, const double *a, double *o)
+{
+    o[0] = R.r[0] * a[0] + R.r[1] * a[1] + R.r[2] * a[2];
+    o[1] = R.r[3] * a[0] + R.r[4] * a[1] + R.r[5] * a[2];
+    o[2] = R.r[6] * a[0] + R.r[7] * a[1] + R.r[8] * a[2];
+}
+
+// R^T c, i.e. the row vector c^T R
+__device__ __forceinline__ void mulT(const Rot &R, const double *c, double *o)
+{
+    o[0] = R.r[0] * c[0] + R.r[3] * c[1] + R.r[6] * c[2];
+    o[1] = R.r[1] * c[0] + R.r[4] * c[1] + R.r[7] * c[2];
+    o[2] = R.r[2] * c[0] + R.r[5] * c[1] + R.r[8] * c[2];
+}
+
+__device__ __forceinline__ void cross(const double *a, const double *b, double *o)
+{
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+__device__ __forceinline__ double dot(const double *a, const double *b)
+{
+    return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+// Row of the velocity of body point p + R r along world direction d:
+// d . (v + R (w x r)) = d . v + w . (r x R^T d)
+__device__ __forceinline__ void point_row(const double *d, const Rot &R, const double *r, double *row)
+{
+    double Rd[3];
+    mulT(R, d, Rd);
+    row[0] = d[0]; row[1] = d[1]; row[2] = d[2];
+    cross(r, Rd, row + 3);
+}
+
+// Rows of a model constraint: Ja, Jb are rows x 6 blocks of bodies a and b, e the error
+// terms; k, alpha (soft) are returned for ANGLE_PD.
+__device__ void model_rows(const ConDesc &c, const double *prm, const double *bodies,
+                           double h, double gamma, double *Ja, double *Jb, double *e,
+                           double *k_out, double *alpha_out)
+{
+    const double *A = bodies + (size_t)c.gb_a * SUBADMM_BODY;
+    const double *B = c.gb_b >= 0 ? bodies + (size_t)c.gb_b * SUBADMM_BODY : nullptr;
+    const Rot Ra = quat_rot(A + 7);
+    Rot Rb;
+    if (B) Rb = quat_rot(B + 7);
+    const double *anc_a = prm + 0, *anc_b = prm + 3, *ax_a = prm + 6, *ax_b = prm + 9;
+    const double *ref_a = prm + 12, *ref_b = prm + 15;
+    for (int q = 0; q < 6 * c.rows; ++q) { Ja[q] = 0.0; Jb[q] = 0.0; }
+    if (c.src == SRC_BALL || c.src == SRC_REVOLUTE) {
+        double ra[3], pa[3], pb[3];
+        mul(Ra, anc_a, ra);
+        for (int d = 0; d < 3; ++d) pa[d] = A[4 + d] + ra[d];
+        if (B) {
+            double rb[3];
+            mul(Rb, anc_b, rb);
+            for (int d = 0; d < 3; ++d) pb[d] = B[4 + d] + rb[d];
+        } else {
+            for (int d = 0; d < 3; ++d) pb[d] = anc_b[d];
+        }
+        for (int d = 0; d < 3; ++d) {
+            const double E[3] = {d == 0 ? 1.0 : 0.0, d == 1 ? 1.0 : 0.0, d == 2 ? 1.0 : 0.0};
+            point_row(E, Ra, anc_a, Ja + 6 * d);
+            if (B) {
+                point_row(E, Rb, anc_b, Jb + 6 * d);
+                for (int q = 0; q < 6; ++q) Jb[6 * d + q] = -Jb[6 * d + q];
+            }
+            e[d] = gamma * (pa[d] - pb[d]) / h;
+        }
+        if (c.src == SRC_REVOLUTE) {
+            double ub[3], t[2][3], axr[3];
+            if (B) mul(Rb, ax_b, ub); else { ub[0] = ax_b[0]; ub[1] = ax_b[1]; ub[2] = ax_b[2]; }
+            mul(Ra, ref_a, t[0]);
+            cross(ax_a, ref_a, axr);
+            mul(Ra, axr, t[1]);
+            for (int kk = 0; kk < 2; ++kk) {
+                const int r = 3 + kk;
+                double txu[3], ja[3];
+                cross(t[kk], ub, txu);          // d/dt (t . u_b) = (t x u_b) . (w_a - w_b)
+                mulT(Ra, txu, ja);
+                for (int q = 0; q < 3; ++q) Ja[6 * r + 3 + q] = ja[q];
+                if (B) {
+                    double jb[3];
+                    mulT(Rb, txu, jb);
+                    for (int q = 0; q < 3; ++q) Jb[6 * r + 3 + q] = -jb[q];
+                }
+                e[r] = gamma * dot(t[kk], ub) / h;
+            }
+        }
+    } else if (c.src == SRC_ANGLE_PD) {
+        double u[3], na[3], nb[3], cr[3], ja[3];
+        mul(Ra, ax_a, u);
+        mul(Ra, ref_a, na);
+        if (B) mul(Rb, ref_b, nb); else { nb[0] = ref_b[0]; nb[1] = ref_b[1]; nb[2] = ref_b[2]; }
+        cross(na, nb, cr);
+        const double theta = atan2(dot(cr, u), dot(na, nb));
+        mulT(Ra, u, ja);                        // d theta / dt = u . (w_b - w_a)
+        for (int q = 0; q < 3; ++q) Ja[3 + q] = -ja[q];
+        if (B) {
+            double jb[3];
+            mulT(Rb, u, jb);
+            for (int q = 0; q < 3; ++q) Jb[3 + q] = jb[q];
+        }
+        const double kp = prm[18], kd = prm[19];
+        e[0] = theta - prm[20];
+        *k_out = kp;
+        *alpha_out = kd / kp + 0.5 * h;
+    } else if (c.src == SRC_PLANE) {
+        double ra[3];
+        mul(Ra, anc_a, ra);
+        const double gap = A[6] + ra[2] - prm[21];
+        const double dirs[3][3] = {{0.0, 0.0, 1.0}, {1.0, 0.0, 0.0}, {0.0, 1.0, 0.0}};
+        for (int d = 0; d < 3; ++d) point_row(dirs[d], Ra, anc_a, Ja + 6 * d);
+        e[0] = gap >= 0.0 ? gap / h : gamma * gap / h;
+        e[1] = 0.0;
+        e[2] = 0.0;
+    }
+}
+
+// Diagonal of A_i = (2/h) M and b_i for one body (6 entries each).
+__device__ __forceinline__ void body_dynamics(const double *B, double h, double g0, double g1,
+                                              double g2, double *Adiag, double *b)
+{
+    const double c2h = 2.0 / h;
+    const double m = B[0];
+    const double *I = B + 1, *v = B + 11, *w = B + 14;
+    const double g[3] = {g0, g1, g2};
+    double Iw[3] = {I[0] * w[0], I[1] * w[1], I[2] * w[2]};
+    double gyro[3];
+    cross(w, Iw, gyro);
+    for (int d = 0; d < 3; ++d) {
+        Adiag[d] = c2h * m;
+        Adiag[3 + d] = c2h * I[d];
+        b[d] = c2h * m * v[d] + m * g[d];
+        b[3 + d] = c2h * Iw[d] - gyro[d];
+    }
+}
+
+// v_{k+1} = 2 v-hat - v_k; p += h v-hat; q <- q (x) Exp(h w-hat), renormalised.
+__device__ __forceinline__ void body_update(double *B, const double *vh, double h)
+{
+    for (int d = 0; d < 3; ++d) {
+        B[4 + d] += h * vh[d];
+        B[11 + d] = 2.0 * vh[d] - B[11 + d];
+        B[14 + d] = 2.0 * vh[3 + d] - B[14 + d];
+    }
+    const double a0 = h * vh[3], a1 = h * vh[4], a2 = h * vh[5];
+    const double th = sqrt(a0 * a0 + a1 * a1 + a2 * a2);
+    double dq[4];
+    if (th > 0.0) {
+        double sn, cs;
+        sincos(0.5 * th, &sn, &cs);
+        sn /= th;
+        dq[0] = cs; dq[1] = a0 * sn; dq[2] = a1 * sn; dq[3] = a2 * sn;
+    } else {
+        dq[0] = 1.0; dq[1] = 0.0; dq[2] = 0.0; dq[3] = 0.0;
+    }
+    double *q = B + 7;
+    double nq[4];
+    nq[0] = q[0] * dq[0] - q[1] * dq[1] - q[2] * dq[2] - q[3] * dq[3];
+    nq[1] = q[0] * dq[1] + q[1] * dq[0] + q[2] * dq[3] - q[3] * dq[2];
+    nq[2] = q[0] * dq[2] - q[1] * dq[3] + q[2] * dq[0] + q[3] * dq[1];
+    nq[3] = q[0] * dq[3] + q[1] * dq[2] - q[2] * dq[1] + q[3] * dq[0];
+    const double inv = 1.0 / sqrt(nq[0] * nq[0] + nq[1] * nq[1] + nq[2] * nq[2] + nq[3] * nq[3]);
+    for (int d = 0; d < 4; ++d) q[d] = nq[d] * inv;
+}
+
+}  // namespace subadmm

@@ -1,0 +1,671 @@
+// libsubadmm: host runtime and C ABI (include/subadmm.h) of the sm_103a subsystem-based
+// ADMM solver.  The runtime lays the scenes out for the step kernel once, when the topology
+// is fixed, and then only enqueues launches and copies on the caller's stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "subadmm.h"
+#include "layout.h"
+#include "step_kernel.cuh"
+
+namespace {
+
+std::string g_create_error;
+
+struct HostSub {
+    int scene = 0, kind = 0, n = 0, nb = 0;
+    std::vector<double> Ab;      // generic: A (n*n) then b (n)
+    std::vector<double> bodies;  // rigid: nb records of 17
+};
+
+struct HostCon {
+    int scene = 0, src = 0, type = 0, rows = 0, ns = 0;
+    int side_sub[SUBADMM_MAXS] = {0};   // global subsystem ids
+    int sa = -1, ba = 0, sb = -1, bb = 0;
+    std::vector<double> data;    // explicit: k, alpha, mu, e[rows], J blocks ; model: 23 params
+};
+
+}  // namespace
+
+struct sim_s {
+    sim_options opt{};
+    std::string err;
+    cudaStream_t stream = nullptr;
+    std::vector<HostSub> subs;
+    std::vector<HostCon> cons;
+    bool finalized = false;
+    // layout (device order) and maps from public ids
+    std::vector<SceneDesc> scenes;
+    std::vector<SubDesc> sdesc;
+    std::vector<ConDesc> cdesc;
+    std::vector<int> sub_dev;      // public subsystem id -> device index
+    std::vector<int> con_dev;      // public interface id -> device index
+    std::vector<int> con_rowg;     // device constraint -> global row of row 0
+    std::vector<int> con_srg;      // device constraint -> global side-row of side 0 row 0 (per side below)
+    std::vector<std::vector<int>> con_sr_global;  // per device constraint, global side-row per side
+    int nscenes = 0;
+    long long dof = 0, nrows = 0, nsr = 0, nbodies = 0;
+    int max_smem = 0;
+    std::vector<int> pool_gen_off; // device subsystem -> pool offset of A,b (generic)
+    // device buffers
+    SceneDesc *d_scenes = nullptr;
+    SubDesc *d_subs = nullptr;
+    ConDesc *d_cons = nullptr;
+    double *d_pool = nullptr, *d_bodies = nullptr, *d_vhat = nullptr, *d_lam = nullptr;
+    double *d_z = nullptr, *d_beta = nullptr, *d_res = nullptr, *d_stage = nullptr;
+    long long *d_stats = nullptr;
+    size_t pool_size = 0;
+};
+
+namespace {
+
+int fail(sim_t s, int code, const std::string &msg)
+{
+    if (s) s->err = msg; else g_create_error = msg;
+    return code;
+}
+
+int cuda_fail(sim_t s, cudaError_t e, const char *what)
+{
+    return fail(s, SIM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                        \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(s, e_, what); \
+    } while (0)
+
+int model_rows_of(int src)
+{
+    switch (src) {
+    case SRC_BALL: return 3;
+    case SRC_REVOLUTE: return 5;
+    case SRC_ANGLE_PD: return 1;
+    case SRC_PLANE: return 3;
+    default: return 0;
+    }
+}
+
+int model_type_of(int src)
+{
+    switch (src) {
+    case SRC_ANGLE_PD: return TYPE_SOFT;
+    case SRC_PLANE: return TYPE_CONTACT;
+    default: return TYPE_EQUALITY;
+    }
+}
+
+// pack / unpack of the 13 state doubles (p, q, v, w) of every body record
+__global__ void pack_state(const double *bodies, double *out, long long nb)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nb * 13;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long b = i / 13, k = i - b * 13;
+        out[i] = bodies[b * SUBADMM_BODY + 4 + k];
+    }
+}
+
+__global__ void unpack_state(double *bodies, const double *in, long long nb)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nb * 13;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long b = i / 13, k = i - b * 13;
+        bodies[b * SUBADMM_BODY + 4 + k] = in[i];
+    }
+}
+
+void free_device(sim_t s)
+{
+    cudaFree(s->d_scenes); cudaFree(s->d_subs); cudaFree(s->d_cons); cudaFree(s->d_pool);
+    cudaFree(s->d_bodies); cudaFree(s->d_vhat); cudaFree(s->d_lam); cudaFree(s->d_z);
+    cudaFree(s->d_beta); cudaFree(s->d_res); cudaFree(s->d_stats); cudaFree(s->d_stage);
+    s->d_scenes = nullptr; s->d_subs = nullptr; s->d_cons = nullptr; s->d_pool = nullptr;
+    s->d_bodies = nullptr; s->d_vhat = nullptr; s->d_lam = nullptr; s->d_z = nullptr;
+    s->d_beta = nullptr; s->d_res = nullptr; s->d_stats = nullptr; s->d_stage = nullptr;
+}
+
+template <typename T>
+int upload(sim_t s, T **dst, const std::vector<T> &src, const char *what)
+{
+    const size_t bytes = std::max<size_t>(src.size(), 1) * sizeof(T);
+    cudaError_t e = cudaMalloc((void **)dst, bytes);
+    if (e != cudaSuccess) return fail(s, SIM_ENOMEM, std::string("cudaMalloc ") + what + ": " + cudaGetErrorString(e));
+    if (!src.empty()) {
+        e = cudaMemcpyAsync(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, s->stream);
+        if (e != cudaSuccess) return cuda_fail(s, e, what);
+    }
+    return SIM_OK;
+}
+
+int zeros(sim_t s, double **dst, size_t count, const char *what)
+{
+    cudaError_t e = cudaMalloc((void **)dst, std::max<size_t>(count, 1) * sizeof(double));
+    if (e != cudaSuccess) return fail(s, SIM_ENOMEM, std::string("cudaMalloc ") + what + ": " + cudaGetErrorString(e));
+    e = cudaMemsetAsync(*dst, 0, std::max<size_t>(count, 1) * sizeof(double), s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, what);
+    return SIM_OK;
+}
+
+// Lays out every scene for the step kernel and uploads it.
+int finalize(sim_t s)
+{
+    if (s->finalized) return SIM_OK;
+    CK(cudaSetDevice(s->opt.device), "cudaSetDevice");
+    const int nsubs = (int)s->subs.size(), ncons = (int)s->cons.size();
+    int nscenes = 0;
+    for (auto &u : s->subs) nscenes = std::max(nscenes, u.scene + 1);
+    for (auto &c : s->cons) nscenes = std::max(nscenes, c.scene + 1);
+    s->nscenes = nscenes;
+    // device order: by scene, stable in call order
+    std::vector<int> sub_order(nsubs), con_order(ncons);
+    for (int i = 0; i < nsubs; ++i) sub_order[i] = i;
+    for (int j = 0; j < ncons; ++j) con_order[j] = j;
+    std::stable_sort(sub_order.begin(), sub_order.end(), [&](int a, int b) { return s->subs[a].scene < s->subs[b].scene; });
+    std::stable_sort(con_order.begin(), con_order.end(), [&](int a, int b) { return s->cons[a].scene < s->cons[b].scene; });
+    s->sub_dev.assign(nsubs, 0);
+    s->con_dev.assign(ncons, 0);
+    for (int k = 0; k < nsubs; ++k) s->sub_dev[sub_order[k]] = k;
+    for (int k = 0; k < ncons; ++k) s->con_dev[con_order[k]] = k;
+
+    std::vector<double> pool;
+    std::vector<double> bodies;
+    s->sdesc.assign(nsubs, SubDesc{});
+    s->cdesc.assign(ncons, ConDesc{});
+    s->scenes.assign(nscenes, SceneDesc{});
+    s->con_sr_global.assign(ncons, std::vector<int>());
+    s->con_rowg.assign(ncons, 0);
+    long long dof = 0, rows_g = 0, sr_g = 0;
+    int max_smem = 0;
+    int si = 0, cj = 0;
+    for (int sc = 0; sc < nscenes; ++sc) {
+        SceneDesc &S = s->scenes[sc];
+        S.sub0 = si;
+        while (si < nsubs && s->subs[sub_order[si]].scene == sc) ++si;
+        S.nsub = si - S.sub0;
+        S.con0 = cj;
+        while (cj < ncons && s->cons[con_order[cj]].scene == sc) ++cj;
+        S.ncon = cj - S.con0;
+        S.sr_g0 = (int)sr_g;
+        S.row_g0 = (int)rows_g;
+        // subsystems of the scene
+        for (int i = 0; i < S.nsub; ++i) {
+            const HostSub &h = s->subs[sub_order[S.sub0 + i]];
+            SubDesc &u = s->sdesc[S.sub0 + i];
+            u.kind = h.kind; u.n = h.n; u.m = 0; u.local = i;
+            u.nb = h.nb;
+            u.body0 = (int)(bodies.size() / SUBADMM_BODY);
+            if (h.kind == KIND_RIGID) bodies.insert(bodies.end(), h.bodies.begin(), h.bodies.end());
+            u.gen_off = (int)pool.size();
+            if (h.kind == KIND_GENERIC) pool.insert(pool.end(), h.Ab.begin(), h.Ab.end());
+            u.v_off = (int)dof;
+            dof += h.n;
+        }
+        // constraints: rows, local sides
+        int row = 0;
+        for (int j = 0; j < S.ncon; ++j) {
+            const HostCon &h = s->cons[con_order[S.con0 + j]];
+            ConDesc &c = s->cdesc[S.con0 + j];
+            c.src = h.src; c.type = h.type; c.rows = h.rows; c.ns = h.ns;
+            c.row0 = row;
+            s->con_rowg[S.con0 + j] = (int)rows_g + row;
+            row += h.rows;
+            c.par_off = (int)pool.size();
+            pool.insert(pool.end(), h.data.begin(), h.data.end());
+            for (int q = 0; q < h.ns; ++q) {
+                const int d = s->sub_dev[h.side_sub[q]];
+                if (d < S.sub0 || d >= S.sub0 + S.nsub)
+                    return fail(s, SIM_EINVAL, "an interface side is a subsystem of another scene");
+                c.sub[q] = d - S.sub0;
+            }
+            c.ba = h.ba; c.bb = h.bb; c.gb_a = -1; c.gb_b = -1; c.side_b = -1;
+        }
+        S.nrow = row;
+        // side-rows, subsystem by subsystem so each subsystem's rows are contiguous
+        int sr = 0;
+        for (int i = 0; i < S.nsub; ++i) {
+            SubDesc &u = s->sdesc[S.sub0 + i];
+            u.sr0 = sr;
+            for (int j = 0; j < S.ncon; ++j) {
+                ConDesc &c = s->cdesc[S.con0 + j];
+                for (int q = 0; q < c.ns; ++q)
+                    if (c.sub[q] == i) { c.sr[q] = sr; sr += c.rows; }
+            }
+            u.m = sr - u.sr0;
+        }
+        S.nsr = sr;
+        for (int j = 0; j < S.ncon; ++j) {
+            const ConDesc &c = s->cdesc[S.con0 + j];
+            std::vector<int> g(c.ns);
+            for (int q = 0; q < c.ns; ++q) g[q] = (int)sr_g + c.sr[q];
+            s->con_sr_global[S.con0 + j] = g;
+        }
+        // model constraints: global bodies
+        for (int j = 0; j < S.ncon; ++j) {
+            const HostCon &h = s->cons[con_order[S.con0 + j]];
+            ConDesc &c = s->cdesc[S.con0 + j];
+            if (h.src <= SRC_CONTACT) continue;
+            const SubDesc &ua = s->sdesc[s->sub_dev[h.sa]];
+            c.gb_a = ua.body0 + h.ba;
+            if (h.sb >= 0) {
+                const SubDesc &ub = s->sdesc[s->sub_dev[h.sb]];
+                c.gb_b = ub.body0 + h.bb;
+                c.side_b = (h.sb == h.sa) ? 0 : 1;
+            }
+        }
+        // shared-memory layout (doubles, then ints)
+        int off = 0;
+        for (int i = 0; i < S.nsub; ++i) {
+            SubDesc &u = s->sdesc[S.sub0 + i];
+            if (u.m > SUBADMM_MAXM)
+                return fail(s, SIM_EINVAL, "a subsystem has more constraint rows than the on-chip path holds");
+            u.o_W = off; off += u.m * u.n;
+            u.o_L = off; off += u.n * u.n;
+            u.o_D = off; off += u.m * u.m;
+            u.o_b = off; off += u.n;
+            u.o_c = off; off += u.m;
+        }
+        S.o_x = off; off += S.nsr;
+        S.o_y = off; off += S.nsr;
+        S.o_z = off; off += S.nsr;
+        S.o_w0 = off; off += S.nsr;
+        S.o_w1 = off; off += S.nsr;
+        S.o_lam = off; off += S.nrow;
+        S.o_e = off; off += S.nrow;
+        S.o_beta = off; off += S.nsub;
+        S.o_int = off;
+        S.smem_bytes = off * (int)sizeof(double) + 6 * S.nsr * (int)sizeof(int);
+        max_smem = std::max(max_smem, S.smem_bytes);
+        sr_g += S.nsr;
+        rows_g += S.nrow;
+    }
+    s->dof = dof; s->nrows = rows_g; s->nsr = sr_g;
+    s->nbodies = (long long)(bodies.size() / SUBADMM_BODY);
+    int dev_max = 0;
+    CK(cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->opt.device), "attribute");
+    const int static_smem = (int)(sizeof(double) * 2 * 4 * SUBADMM_WARPS + 64);
+    if (max_smem + static_smem > dev_max) {
+        char buf[256];
+        snprintf(buf, sizeof buf, "a scene needs %d bytes of shared memory; the on-chip path holds %d",
+                 max_smem, dev_max - static_smem);
+        return fail(s, SIM_EINVAL, buf);
+    }
+    s->max_smem = max_smem;
+    s->pool_gen_off.assign(nsubs, 0);
+    for (int k = 0; k < nsubs; ++k) s->pool_gen_off[k] = s->sdesc[k].gen_off;
+    int rc;
+    if ((rc = upload(s, &s->d_scenes, s->scenes, "scenes"))) return rc;
+    if ((rc = upload(s, &s->d_subs, s->sdesc, "subsystems"))) return rc;
+    if ((rc = upload(s, &s->d_cons, s->cdesc, "interfaces"))) return rc;
+    if ((rc = upload(s, &s->d_pool, pool, "pool"))) return rc;
+    if ((rc = upload(s, &s->d_bodies, bodies, "bodies"))) return rc;
+    s->pool_size = pool.size();
+    if ((rc = zeros(s, &s->d_vhat, (size_t)dof, "vhat"))) return rc;
+    if ((rc = zeros(s, &s->d_lam, (size_t)rows_g, "lambda"))) return rc;
+    if ((rc = zeros(s, &s->d_z, (size_t)sr_g, "z"))) return rc;
+    if ((rc = zeros(s, &s->d_beta, (size_t)nsubs, "beta"))) return rc;
+    if ((rc = zeros(s, &s->d_res, (size_t)6 * nscenes, "residuals"))) return rc;
+    if ((rc = zeros(s, &s->d_stage, (size_t)13 * s->nbodies, "state staging"))) return rc;
+    {
+        cudaError_t e = cudaMalloc((void **)&s->d_stats, std::max(1, 4 * nscenes) * sizeof(long long));
+        if (e != cudaSuccess) return fail(s, SIM_ENOMEM, "cudaMalloc stats");
+        CK(cudaMemsetAsync(s->d_stats, 0, std::max(1, 4 * nscenes) * sizeof(long long), s->stream), "memset stats");
+    }
+    CK(cudaFuncSetAttribute(subadmm::step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            std::max(max_smem, 1)), "shared memory attribute");
+    s->finalized = true;
+    return SIM_OK;
+}
+
+int check_rows_data(sim_t s, int kind, int rows, int n_sides, const int *sides, const double *J,
+                    const double *e, const double *params, HostCon &c)
+{
+    if (rows < 1 || rows > 8) return fail(s, SIM_EINVAL, "rows must be in 1..8");
+    if (kind == SRC_CONTACT && rows != 3) return fail(s, SIM_EINVAL, "a contact has 3 rows");
+    if (n_sides < 1 || n_sides > SUBADMM_MAXS) return fail(s, SIM_EINVAL, "n_sides must be in 1..8");
+    if (!sides || !J || !e) return fail(s, SIM_EINVAL, "sides, J and e are required");
+    if (kind == SRC_SOFT && (!params || !(params[0] > 0.0) || !(params[1] > 0.0)))
+        return fail(s, SIM_EINVAL, "a soft interface needs k > 0 and alpha > 0");
+    if (kind == SRC_CONTACT && (!params || !(params[2] >= 0.0)))
+        return fail(s, SIM_EINVAL, "a contact needs mu >= 0");
+    c.src = kind; c.type = kind; c.rows = rows; c.ns = n_sides;
+    c.data.clear();
+    c.data.push_back(params ? params[0] : 0.0);
+    c.data.push_back(params ? params[1] : 0.0);
+    c.data.push_back(params ? params[2] : 0.0);
+    for (int r = 0; r < rows; ++r) c.data.push_back(e[r]);
+    const double *Jp = J;
+    for (int q = 0; q < n_sides; ++q) {
+        const int id = sides[q];
+        if (id < 0 || id >= (int)s->subs.size()) return fail(s, SIM_EINVAL, "unknown subsystem id");
+        for (int t = 0; t < q; ++t)
+            if (sides[t] == id) return fail(s, SIM_EINVAL, "sides must be distinct subsystems");
+        c.side_sub[q] = id;
+        const int n = s->subs[id].n;
+        c.data.insert(c.data.end(), Jp, Jp + (size_t)rows * n);
+        Jp += (size_t)rows * n;
+    }
+    for (double v : c.data)
+        if (!std::isfinite(v)) return fail(s, SIM_EINVAL, "non-finite value in J, e or params");
+    return SIM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void sim_default_options(sim_options *o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->h = 1e-3;
+    o->gravity[0] = 0.0; o->gravity[1] = 0.0; o->gravity[2] = -9.81;
+    o->baumgarte = 0.2;
+    o->beta_mode = SIM_BETA_TRACE;
+    o->rho = 1e3;
+    o->warm = SIM_WARM_PREV;
+    o->stop = SIM_STOP_PRIMAL;
+    o->tol_primal = 1e-6;
+    o->theta_th = 1e-12;
+    o->max_iters = 1000;
+    o->precision = SIM_FP64;
+    o->device = 0;
+    o->stream = nullptr;
+}
+
+int sim_create(const sim_options *opt, sim_t *out)
+{
+    if (!out) return fail(nullptr, SIM_EINVAL, "out is NULL");
+    *out = nullptr;
+    sim_options o;
+    if (opt) o = *opt; else sim_default_options(&o);
+    if (!(o.h > 0.0) || o.max_iters < 1 || o.precision != SIM_FP64 ||
+        (o.beta_mode != SIM_BETA_TRACE && o.beta_mode != SIM_BETA_FIXED) ||
+        (o.beta_mode == SIM_BETA_FIXED && !(o.rho > 0.0)) ||
+        (o.warm != SIM_WARM_COLD && o.warm != SIM_WARM_PREV) ||
+        (o.stop != SIM_STOP_PRIMAL && o.stop != SIM_STOP_THETA))
+        return fail(nullptr, SIM_EINVAL, "invalid options");
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) return fail(nullptr, SIM_ECUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
+    if (o.device < 0 || o.device >= ndev) return fail(nullptr, SIM_EINVAL, "device ordinal out of range");
+    e = cudaSetDevice(o.device);
+    if (e != cudaSuccess) return fail(nullptr, SIM_ECUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+    sim_t s = new (std::nothrow) sim_s();
+    if (!s) return fail(nullptr, SIM_ENOMEM, "host allocation failed");
+    s->opt = o;
+    s->stream = (cudaStream_t)o.stream;
+    *out = s;
+    return SIM_OK;
+}
+
+void sim_destroy(sim_t s)
+{
+    if (!s) return;
+    cudaSetDevice(s->opt.device);
+    cudaStreamSynchronize(s->stream);
+    free_device(s);
+    delete s;
+}
+
+int sim_add_subsystem(sim_t s, int scene, int kind, int count, const double *data, int *out_id)
+{
+    if (!s) return SIM_EINVAL;
+    if (s->finalized) return fail(s, SIM_EINVAL, "topology is fixed after the first sim_step");
+    if (scene < 0) return fail(s, SIM_EINVAL, "scene must be >= 0");
+    if (count < 1 || !data) return fail(s, SIM_EINVAL, "count >= 1 and data are required");
+    HostSub u;
+    u.scene = scene;
+    if (kind == SIM_SUB_GENERIC) {
+        if (count > SUBADMM_MAXN) return fail(s, SIM_EINVAL, "generic subsystem larger than the on-chip path");
+        u.kind = KIND_GENERIC; u.n = count;
+        u.Ab.assign(data, data + (size_t)count * count + count);
+    } else if (kind == SIM_SUB_RIGID) {
+        if (6 * count > SUBADMM_MAXN) return fail(s, SIM_EINVAL, "rigid subsystem larger than the on-chip path");
+        u.kind = KIND_RIGID; u.nb = count; u.n = 6 * count;
+        u.bodies.assign(data, data + (size_t)count * SUBADMM_BODY);
+        for (int b = 0; b < count; ++b) {
+            const double *r = data + (size_t)b * SUBADMM_BODY;
+            if (!(r[0] > 0.0) || !(r[1] > 0.0) || !(r[2] > 0.0) || !(r[3] > 0.0))
+                return fail(s, SIM_EINVAL, "body mass and inertia must be positive");
+        }
+    } else {
+        return fail(s, SIM_EINVAL, "unknown subsystem kind");
+    }
+    for (double v : u.Ab) if (!std::isfinite(v)) return fail(s, SIM_EINVAL, "non-finite A or b");
+    for (double v : u.bodies) if (!std::isfinite(v)) return fail(s, SIM_EINVAL, "non-finite body record");
+    s->subs.push_back(std::move(u));
+    if (out_id) *out_id = (int)s->subs.size() - 1;
+    return SIM_OK;
+}
+
+int sim_add_interface(sim_t s, int scene, int kind, int rows, int n_sides, const int *sides,
+                      const double *J, const double *e, const double *params, int *out_id)
+{
+    if (!s) return SIM_EINVAL;
+    if (s->finalized) return fail(s, SIM_EINVAL, "topology is fixed after the first sim_step");
+    if (scene < 0) return fail(s, SIM_EINVAL, "scene must be >= 0");
+    HostCon c;
+    c.scene = scene;
+    if (kind >= SIM_IF_EQUALITY && kind <= SIM_IF_CONTACT) {
+        int rc = check_rows_data(s, kind, rows, n_sides, sides, J, e, params, c);
+        if (rc) return rc;
+        for (int q = 0; q < n_sides; ++q)
+            if (s->subs[sides[q]].scene != scene) return fail(s, SIM_EINVAL, "a side belongs to another scene");
+    } else if (kind >= SIM_IF_BALL && kind <= SIM_IF_PLANE_CONTACT) {
+        if (!sides || !params) return fail(s, SIM_EINVAL, "sides and params are required");
+        if (J || e) return fail(s, SIM_EINVAL, "model interfaces take no J or e");
+        const int sa = sides[0], ba = sides[1];
+        int sb = sides[2], bb = sides[3];
+        if (kind == SIM_IF_PLANE_CONTACT) { sb = -1; bb = 0; }
+        if (sa < 0 || sa >= (int)s->subs.size() || s->subs[sa].kind != KIND_RIGID)
+            return fail(s, SIM_EINVAL, "side a must be a rigid subsystem");
+        if (ba < 0 || ba >= s->subs[sa].nb) return fail(s, SIM_EINVAL, "body a out of range");
+        if (s->subs[sa].scene != scene) return fail(s, SIM_EINVAL, "body a belongs to another scene");
+        if (sb >= 0) {
+            if (sb >= (int)s->subs.size() || s->subs[sb].kind != KIND_RIGID)
+                return fail(s, SIM_EINVAL, "side b must be a rigid subsystem or -1");
+            if (bb < 0 || bb >= s->subs[sb].nb) return fail(s, SIM_EINVAL, "body b out of range");
+            if (sb == sa && bb == ba) return fail(s, SIM_EINVAL, "a body cannot be joined to itself");
+            if (s->subs[sb].scene != scene) return fail(s, SIM_EINVAL, "body b belongs to another scene");
+        }
+        for (int q = 0; q < SUBADMM_PARAMS; ++q)
+            if (!std::isfinite(params[q])) return fail(s, SIM_EINVAL, "non-finite parameter");
+        if (kind == SIM_IF_ANGLE_PD && !(params[18] > 0.0))
+            return fail(s, SIM_EINVAL, "ANGLE_PD needs kp > 0");
+        if (kind == SIM_IF_PLANE_CONTACT && !(params[22] >= 0.0))
+            return fail(s, SIM_EINVAL, "PLANE_CONTACT needs mu >= 0");
+        c.src = kind; c.type = model_type_of(kind); c.rows = model_rows_of(kind);
+        c.sa = sa; c.ba = ba; c.sb = sb; c.bb = bb;
+        c.side_sub[0] = sa;
+        c.ns = 1;
+        if (sb >= 0 && sb != sa) { c.ns = 2; c.side_sub[1] = sb; }
+        c.data.assign(params, params + SUBADMM_PARAMS);
+    } else {
+        return fail(s, SIM_EINVAL, "unknown interface kind");
+    }
+    s->cons.push_back(std::move(c));
+    if (out_id) *out_id = (int)s->cons.size() - 1;
+    return SIM_OK;
+}
+
+int sim_set_generic(sim_t s, int sub, const double *A, const double *b)
+{
+    if (!s) return SIM_EINVAL;
+    if (sub < 0 || sub >= (int)s->subs.size() || s->subs[sub].kind != KIND_GENERIC)
+        return fail(s, SIM_EINVAL, "not a generic subsystem");
+    HostSub &u = s->subs[sub];
+    const int n = u.n;
+    if (A) for (int q = 0; q < n * n; ++q) if (!std::isfinite(A[q])) return fail(s, SIM_EINVAL, "non-finite A");
+    if (b) for (int q = 0; q < n; ++q) if (!std::isfinite(b[q])) return fail(s, SIM_EINVAL, "non-finite b");
+    if (A) std::memcpy(u.Ab.data(), A, sizeof(double) * n * n);
+    if (b) std::memcpy(u.Ab.data() + (size_t)n * n, b, sizeof(double) * n);
+    if (s->finalized) {
+        const int off = s->pool_gen_off[s->sub_dev[sub]];
+        CK(cudaMemcpyAsync(s->d_pool + off, u.Ab.data(), sizeof(double) * ((size_t)n * n + n),
+                           cudaMemcpyHostToDevice, s->stream), "set_generic");
+        // the host copy must outlive the async copy: wait for it
+        CK(cudaStreamSynchronize(s->stream), "set_generic sync");
+    }
+    return SIM_OK;
+}
+
+int sim_step(sim_t s, int n_steps)
+{
+    if (!s) return SIM_EINVAL;
+    if (n_steps < 1) return fail(s, SIM_EINVAL, "n_steps must be >= 1");
+    int rc = finalize(s);
+    if (rc) return rc;
+    if (s->nscenes == 0) return SIM_OK;
+    StepParams P;
+    P.scenes = s->d_scenes; P.subs = s->d_subs; P.cons = s->d_cons; P.pool = s->d_pool;
+    P.bodies = s->d_bodies; P.vhat = s->d_vhat; P.lam = s->d_lam; P.z = s->d_z;
+    P.beta = s->d_beta; P.res = s->d_res; P.stats = s->d_stats;
+    P.nscenes = s->nscenes;
+    P.n_steps = n_steps;
+    P.h = s->opt.h; P.g0 = s->opt.gravity[0]; P.g1 = s->opt.gravity[1]; P.g2 = s->opt.gravity[2];
+    P.gamma = s->opt.baumgarte; P.rho = s->opt.rho; P.tol = s->opt.tol_primal;
+    P.theta_th = s->opt.theta_th;
+    P.beta_fixed = s->opt.beta_mode == SIM_BETA_FIXED;
+    P.warm_prev = s->opt.warm == SIM_WARM_PREV;
+    P.stop_theta = s->opt.stop == SIM_STOP_THETA;
+    P.max_iters = s->opt.max_iters;
+    CK(cudaSetDevice(s->opt.device), "cudaSetDevice");
+    // the attribute is per function, shared by every simulation of the process
+    CK(cudaFuncSetAttribute(subadmm::step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            std::max(s->max_smem, 1)), "shared memory attribute");
+    subadmm::step_kernel<<<s->nscenes, SUBADMM_THREADS, s->max_smem, s->stream>>>(P);
+    CK(cudaGetLastError(), "step kernel launch");
+    return SIM_OK;
+}
+
+int sim_sync(sim_t s)
+{
+    if (!s) return SIM_EINVAL;
+    CK(cudaStreamSynchronize(s->stream), "stream synchronize");
+    return SIM_OK;
+}
+
+int sim_residuals(sim_t s, int scene, double out[6])
+{
+    if (!s || !out) return SIM_EINVAL;
+    if (!s->finalized) return fail(s, SIM_EINVAL, "no step has run");
+    if (scene < 0 || scene >= s->nscenes) return fail(s, SIM_EINVAL, "scene out of range");
+    CK(cudaStreamSynchronize(s->stream), "stream synchronize");
+    CK(cudaMemcpy(out, s->d_res + 6 * scene, 6 * sizeof(double), cudaMemcpyDeviceToHost), "residuals");
+    const int st = (int)out[5];
+    if (st != 0) {
+        s->err = st == SIM_ENOTSPD ? "K_i is not positive definite" : "a residual is not finite";
+        return st;
+    }
+    return out[4] != 0.0 ? SIM_OK : SIM_NOT_CONVERGED;
+}
+
+int sim_get(sim_t s, int what, int id, double *dst)
+{
+    if (!s || !dst) return SIM_EINVAL;
+    if (!s->finalized) return fail(s, SIM_EINVAL, "no step has run");
+    CK(cudaStreamSynchronize(s->stream), "stream synchronize");
+    if (what == SIM_GET_VHAT || what == SIM_GET_BODIES || what == SIM_GET_BETA) {
+        if (id < 0 || id >= (int)s->subs.size()) return fail(s, SIM_EINVAL, "subsystem id out of range");
+        const SubDesc &u = s->sdesc[s->sub_dev[id]];
+        if (what == SIM_GET_VHAT)
+            CK(cudaMemcpy(dst, s->d_vhat + u.v_off, sizeof(double) * u.n, cudaMemcpyDeviceToHost), "get");
+        else if (what == SIM_GET_BETA)
+            CK(cudaMemcpy(dst, s->d_beta + s->sub_dev[id], sizeof(double), cudaMemcpyDeviceToHost), "get");
+        else {
+            if (u.kind != KIND_RIGID) return fail(s, SIM_EINVAL, "not a rigid subsystem");
+            CK(cudaMemcpy(dst, s->d_bodies + (size_t)u.body0 * SUBADMM_BODY,
+                          sizeof(double) * SUBADMM_BODY * u.nb, cudaMemcpyDeviceToHost), "get");
+        }
+        return SIM_OK;
+    }
+    if (what == SIM_GET_LAMBDA || what == SIM_GET_Z) {
+        if (id < 0 || id >= (int)s->cons.size()) return fail(s, SIM_EINVAL, "interface id out of range");
+        const int d = s->con_dev[id];
+        const ConDesc &c = s->cdesc[d];
+        if (what == SIM_GET_LAMBDA) {
+            CK(cudaMemcpy(dst, s->d_lam + s->con_rowg[d], sizeof(double) * c.rows, cudaMemcpyDeviceToHost), "get");
+        } else {
+            for (int q = 0; q < c.ns; ++q)
+                CK(cudaMemcpy(dst + q * c.rows, s->d_z + s->con_sr_global[d][q], sizeof(double) * c.rows,
+                              cudaMemcpyDeviceToHost), "get");
+        }
+        return SIM_OK;
+    }
+    return fail(s, SIM_EINVAL, "unknown quantity");
+}
+
+int sim_read_state(sim_t s, double *dst)
+{
+    if (!s || !dst) return SIM_EINVAL;
+    int rc = finalize(s);
+    if (rc) return rc;
+    if (s->nbodies == 0) return SIM_OK;
+    const int grid = (int)std::min<long long>((13 * s->nbodies + 255) / 256, 1024);
+    pack_state<<<grid, 256, 0, s->stream>>>(s->d_bodies, s->d_stage, s->nbodies);
+    CK(cudaGetLastError(), "pack state");
+    CK(cudaMemcpyAsync(dst, s->d_stage, sizeof(double) * 13 * s->nbodies, cudaMemcpyDeviceToHost, s->stream), "read state");
+    CK(cudaStreamSynchronize(s->stream), "read state sync");
+    return SIM_OK;
+}
+
+int sim_write_state(sim_t s, const double *src)
+{
+    if (!s || !src) return SIM_EINVAL;
+    int rc = finalize(s);
+    if (rc) return rc;
+    if (s->nbodies == 0) return SIM_OK;
+    CK(cudaMemcpyAsync(s->d_stage, src, sizeof(double) * 13 * s->nbodies, cudaMemcpyHostToDevice, s->stream), "write state");
+    const int grid = (int)std::min<long long>((13 * s->nbodies + 255) / 256, 1024);
+    unpack_state<<<grid, 256, 0, s->stream>>>(s->d_bodies, s->d_stage, s->nbodies);
+    CK(cudaGetLastError(), "unpack state");
+    return SIM_OK;
+}
+
+int sim_sizes(sim_t s, long long out[8])
+{
+    if (!s || !out) return SIM_EINVAL;
+    int rc = finalize(s);
+    if (rc) return rc;
+    out[0] = s->nscenes;
+    out[1] = (long long)s->subs.size();
+    out[2] = s->dof;
+    out[3] = (long long)s->cons.size();
+    out[4] = s->nrows;
+    out[5] = s->nsr;
+    out[6] = s->nbodies;
+    out[7] = s->max_smem;
+    return SIM_OK;
+}
+
+int sim_iteration_stats(sim_t s, long long out[4])
+{
+    if (!s || !out) return SIM_EINVAL;
+    if (!s->finalized) return fail(s, SIM_EINVAL, "no step has run");
+    CK(cudaStreamSynchronize(s->stream), "stream synchronize");
+    std::vector<long long> st((size_t)4 * std::max(1, s->nscenes));
+    CK(cudaMemcpy(st.data(), s->d_stats, sizeof(long long) * 4 * s->nscenes, cudaMemcpyDeviceToHost), "stats");
+    out[0] = out[1] = out[2] = out[3] = 0;
+    for (int k = 0; k < s->nscenes; ++k) {
+        out[0] += st[4 * k];
+        out[1] = std::max(out[1], st[4 * k + 1]);
+        out[2] += st[4 * k + 2];
+        out[3] += st[4 * k + 3];
+    }
+    CK(cudaMemset(s->d_stats, 0, sizeof(long long) * 4 * s->nscenes), "stats clear");
+    return SIM_OK;
+}
+
+const char *sim_last_error(sim_t s)
+{
+    return s ? s->err.c_str() : g_create_error.c_str();
+}
+
+}  // extern "C"

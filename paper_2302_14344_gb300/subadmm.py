@@ -1,0 +1,344 @@
+"""Python binding of libsubadmm (include/subadmm.h): argument marshalling only.
+
+Every function named ``sim_*`` calls the C function of the same name and raises
+``SimError`` on a negative status.  All of the method's work runs in the library's CUDA
+kernels; this module never computes any of it.  Loading fails loudly when the library has
+not been built (see ``paper_2302_14344_gb300.build``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+SIM_OK, SIM_NOT_CONVERGED = 0, 1
+SIM_EINVAL, SIM_ENOMEM, SIM_ENOTSPD, SIM_ENAN, SIM_ECUDA = -1, -2, -3, -4, -5
+SIM_SUB_GENERIC, SIM_SUB_RIGID = 0, 1
+SIM_IF_EQUALITY, SIM_IF_HARD, SIM_IF_SOFT, SIM_IF_CONTACT = 0, 1, 2, 3
+SIM_IF_BALL, SIM_IF_REVOLUTE, SIM_IF_ANGLE_PD, SIM_IF_PLANE_CONTACT = 4, 5, 6, 7
+SIM_BETA_TRACE, SIM_BETA_FIXED = 0, 1
+SIM_WARM_COLD, SIM_WARM_PREV = 0, 1
+SIM_STOP_PRIMAL, SIM_STOP_THETA = 0, 1
+SIM_FP64 = 0
+SIM_GET_VHAT, SIM_GET_LAMBDA, SIM_GET_BODIES, SIM_GET_BETA, SIM_GET_Z = 0, 1, 2, 3, 4
+
+# exported symbols of include/subadmm.h
+EXPORTS = ("sim_default_options", "sim_create", "sim_destroy", "sim_add_subsystem",
+           "sim_add_interface", "sim_set_generic", "sim_step", "sim_residuals", "sim_get",
+           "sim_read_state", "sim_write_state", "sim_sizes", "sim_iteration_stats", "sim_sync",
+           "sim_last_error")
+
+
+class sim_options(C.Structure):
+    _fields_ = [("h", C.c_double), ("gravity", C.c_double * 3), ("baumgarte", C.c_double),
+                ("beta_mode", C.c_int), ("rho", C.c_double), ("warm", C.c_int),
+                ("stop", C.c_int), ("tol_primal", C.c_double), ("theta_th", C.c_double),
+                ("max_iters", C.c_int), ("precision", C.c_int), ("device", C.c_int),
+                ("stream", C.c_void_p)]
+
+
+class SimError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{msg} (status {code})")
+        self.code = code
+
+
+_lock = threading.Lock()
+_lib = None
+PD = C.POINTER(C.c_double)
+PI = C.POINTER(C.c_int)
+PL = C.POINTER(C.c_longlong)
+VP = C.c_void_p
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libsubadmm.so (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if build_if_missing:
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError(f"libsubadmm.so is not built ({_build.LIB}); run "
+                               "paper_2302_14344_gb300.build.build()")
+        L = C.CDLL(_build.LIB)
+        sig = {
+            "sim_default_options": (None, [C.POINTER(sim_options)]),
+            "sim_create": (C.c_int, [C.POINTER(sim_options), C.POINTER(VP)]),
+            "sim_destroy": (None, [VP]),
+            "sim_add_subsystem": (C.c_int, [VP, C.c_int, C.c_int, C.c_int, PD, PI]),
+            "sim_add_interface": (C.c_int, [VP, C.c_int, C.c_int, C.c_int, C.c_int, PI, PD, PD,
+                                            PD, PI]),
+            "sim_set_generic": (C.c_int, [VP, C.c_int, PD, PD]),
+            "sim_step": (C.c_int, [VP, C.c_int]),
+            "sim_residuals": (C.c_int, [VP, C.c_int, PD]),
+            "sim_get": (C.c_int, [VP, C.c_int, C.c_int, PD]),
+            "sim_read_state": (C.c_int, [VP, VP]),
+            "sim_write_state": (C.c_int, [VP, VP]),
+            "sim_sizes": (C.c_int, [VP, PL]),
+            "sim_iteration_stats": (C.c_int, [VP, PL]),
+            "sim_sync": (C.c_int, [VP]),
+            "sim_last_error": (C.c_char_p, [VP]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+        return L
+
+
+def _check(h, rc: int) -> int:
+    if rc < 0:
+        msg = load().sim_last_error(h)
+        raise SimError(rc, msg.decode() if msg else "error")
+    return rc
+
+
+def _dp(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data_as(PD)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+# --- thin wrappers, one per C function --------------------------------------------------
+
+def sim_default_options() -> sim_options:
+    o = sim_options()
+    load().sim_default_options(C.byref(o))
+    return o
+
+
+def sim_create(opt: sim_options):
+    h = VP()
+    _check(None, load().sim_create(C.byref(opt), C.byref(h)))
+    return h
+
+
+def sim_destroy(h) -> None:
+    load().sim_destroy(h)
+
+
+def sim_add_subsystem(h, scene: int, kind: int, count: int, data) -> int:
+    d = _f64(data)
+    out = C.c_int(-1)
+    _check(h, load().sim_add_subsystem(h, scene, kind, count, _dp(d), C.byref(out)))
+    return out.value
+
+
+def sim_add_interface(h, scene: int, kind: int, rows: int, n_sides: int, sides, J=None, e=None,
+                      params=None) -> int:
+    s = np.ascontiguousarray(np.asarray(sides, dtype=np.int32))
+    Jd = None if J is None else _f64(J)
+    ed = None if e is None else _f64(e)
+    pd = None if params is None else _f64(params)
+    out = C.c_int(-1)
+    _check(h, load().sim_add_interface(h, scene, kind, rows, n_sides, s.ctypes.data_as(PI),
+                                       _dp(Jd), _dp(ed), _dp(pd), C.byref(out)))
+    return out.value
+
+
+def sim_set_generic(h, sub: int, A=None, b=None) -> None:
+    Ad = None if A is None else _f64(A)
+    bd = None if b is None else _f64(b)
+    _check(h, load().sim_set_generic(h, sub, _dp(Ad), _dp(bd)))
+
+
+def sim_step(h, n_steps: int = 1) -> None:
+    _check(h, load().sim_step(h, n_steps))
+
+
+def sim_residuals(h, scene: int) -> dict:
+    out = np.zeros(6)
+    rc = _check(h, load().sim_residuals(h, scene, _dp(out)))
+    return dict(r_p=out[0], r_d=out[1], theta=out[2], iters=int(out[3]),
+                converged=bool(out[4]), status=int(out[5]), rc=rc)
+
+
+def sim_get(h, what: int, id_: int, count: int) -> np.ndarray:
+    out = np.zeros(count)
+    _check(h, load().sim_get(h, what, id_, _dp(out)))
+    return out
+
+
+def sim_read_state(h, dst_ptr: int) -> None:
+    """dst_ptr: address of a host buffer of 13 doubles per body (e.g. a pinned tensor)."""
+    _check(h, load().sim_read_state(h, VP(dst_ptr)))
+
+
+def sim_write_state(h, src_ptr: int) -> None:
+    _check(h, load().sim_write_state(h, VP(src_ptr)))
+
+
+def sim_sizes(h) -> dict:
+    out = (C.c_longlong * 8)()
+    _check(h, load().sim_sizes(h, out))
+    keys = ("scenes", "subsystems", "dof", "interfaces", "rows", "side_rows", "bodies",
+            "smem_bytes")
+    return {k: int(v) for k, v in zip(keys, out)}
+
+
+def sim_iteration_stats(h) -> dict:
+    out = (C.c_longlong * 4)()
+    _check(h, load().sim_iteration_stats(h, out))
+    return dict(total_iters=int(out[0]), max_iters=int(out[1]), not_converged=int(out[2]),
+                scene_steps=int(out[3]))
+
+
+def sim_sync(h) -> None:
+    _check(h, load().sim_sync(h))
+
+
+def sim_last_error(h) -> str:
+    m = load().sim_last_error(h)
+    return m.decode() if m else ""
+
+
+# --- convenience: a simulation built from a scene description ---------------------------
+
+_KIND = {0: SIM_IF_EQUALITY, 1: SIM_IF_HARD, 2: SIM_IF_SOFT, 3: SIM_IF_CONTACT}
+_MODEL = {1: SIM_IF_BALL, 2: SIM_IF_REVOLUTE, 3: SIM_IF_ANGLE_PD, 4: SIM_IF_PLANE_CONTACT}
+
+
+def options_from(o, stream: int = 0, device: int = 0) -> sim_options:
+    """sim_options from an object with the fields of ``scenegen.Options``."""
+    opt = sim_default_options()
+    opt.h = o.h
+    for k in range(3):
+        opt.gravity[k] = o.gravity[k]
+    opt.baumgarte = o.baumgarte
+    opt.beta_mode = SIM_BETA_FIXED if o.beta_mode == "fixed" else SIM_BETA_TRACE
+    opt.rho = o.rho if o.beta_mode == "fixed" else 1e3
+    opt.warm = SIM_WARM_PREV if o.warm == "prev" else SIM_WARM_COLD
+    opt.stop = SIM_STOP_THETA if o.stop == "theta" else SIM_STOP_PRIMAL
+    opt.tol_primal = o.tol_primal
+    opt.theta_th = o.theta_th
+    opt.max_iters = int(o.max_iters)
+    opt.device = device
+    opt.stream = stream or None
+    return opt
+
+
+class Simulation:
+    """A libsubadmm simulation holding every scene of a problem description.
+
+    ``problem`` has ``scenes`` (each with ``subs`` and ``ifs``) and ``options``, shaped like
+    ``scenegen.Problem``.  Subsystem and interface ids are assigned in scene order."""
+
+    def __init__(self, problem, stream: int = 0, device: int = 0):
+        self.h = sim_create(options_from(problem.options, stream, device))
+        self.sub_ids = []     # per scene: list of ids
+        self.if_ids = []
+        self.sub_n = []
+        self.if_rows = []
+        self.if_nsides = []
+        self.rigid_subs = []
+        for sc_i, sc in enumerate(problem.scenes):
+            ids = []
+            for sub in sc.subs:
+                if hasattr(sub, "bodies"):
+                    rec = np.concatenate([np.concatenate([[b.m], b.I, b.p, b.q, b.v, b.w])
+                                          for b in sub.bodies])
+                    sid = sim_add_subsystem(self.h, sc_i, SIM_SUB_RIGID, len(sub.bodies), rec)
+                    self.rigid_subs.append((sid, len(sub.bodies)))
+                else:
+                    data = np.concatenate([np.asarray(sub.A, float).ravel(),
+                                           np.asarray(sub.b, float)])
+                    sid = sim_add_subsystem(self.h, sc_i, SIM_SUB_GENERIC, sub.n, data)
+                ids.append(sid)
+                self.sub_n.append(sub.n)
+            self.sub_ids.append(ids)
+            iids = []
+            for itf in sc.ifs:
+                if hasattr(itf, "J"):
+                    sides = [ids[s] for s in itf.subs]
+                    J = np.concatenate([np.asarray(m, float).ravel() for m in itf.J])
+                    iid = sim_add_interface(self.h, sc_i, _KIND[int(itf.type)], itf.rows,
+                                            len(sides), sides, J, itf.e,
+                                            [itf.k, itf.alpha, itf.mu])
+                    self.if_rows.append(itf.rows)
+                    self.if_nsides.append(len(sides))
+                else:
+                    sb, bb = (ids[itf.b[0]], itf.b[1]) if itf.b is not None else (-1, 0)
+                    prm = np.concatenate([itf.anchor_a, itf.anchor_b, itf.axis_a, itf.axis_b,
+                                          itf.ref_a, itf.ref_b,
+                                          [itf.kp, itf.kd, itf.target, itf.plane_z, itf.mu]])
+                    kind = _MODEL[int(itf.kind)]
+                    iid = sim_add_interface(self.h, sc_i, kind, 0, 0,
+                                            [ids[itf.a[0]], itf.a[1], sb, bb], None, None, prm)
+                    rows = {SIM_IF_BALL: 3, SIM_IF_REVOLUTE: 5, SIM_IF_ANGLE_PD: 1,
+                            SIM_IF_PLANE_CONTACT: 3}[kind]
+                    self.if_rows.append(rows)
+                    same = itf.b is None or itf.b[0] == itf.a[0]
+                    self.if_nsides.append(1 if same else 2)
+                iids.append(iid)
+            self.if_ids.append(iids)
+        self.n_scenes = len(problem.scenes)
+
+    def close(self):
+        if getattr(self, "h", None):
+            sim_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n: int = 1):
+        sim_step(self.h, n)
+
+    def sync(self):
+        sim_sync(self.h)
+
+    def residuals(self, scene: int) -> dict:
+        return sim_residuals(self.h, scene)
+
+    def vhat(self, sid: int) -> np.ndarray:
+        return sim_get(self.h, SIM_GET_VHAT, sid, self.sub_n[sid])
+
+    def lam(self, iid: int) -> np.ndarray:
+        return sim_get(self.h, SIM_GET_LAMBDA, iid, self.if_rows[iid])
+
+    def z(self, iid: int) -> np.ndarray:
+        return sim_get(self.h, SIM_GET_Z, iid, self.if_rows[iid] * self.if_nsides[iid]).reshape(
+            self.if_nsides[iid], self.if_rows[iid])
+
+    def beta(self, sid: int) -> float:
+        return float(sim_get(self.h, SIM_GET_BETA, sid, 1)[0])
+
+    def bodies(self, sid: int, nb: int) -> np.ndarray:
+        return sim_get(self.h, SIM_GET_BODIES, sid, 17 * nb).reshape(nb, 17)
+
+    def scene_vhat(self, scene: int) -> np.ndarray:
+        return np.concatenate([self.vhat(s) for s in self.sub_ids[scene]])
+
+    def scene_lam(self, scene: int) -> np.ndarray:
+        ids = self.if_ids[scene]
+        return np.concatenate([self.lam(i) for i in ids]) if ids else np.zeros(0)
+
+    def scene_bodies(self, scene: int) -> np.ndarray:
+        out = []
+        for sid, nb in self.rigid_subs:
+            if sid in self.sub_ids[scene]:
+                out.append(self.bodies(sid, nb))
+        return np.concatenate(out) if out else np.zeros((0, 17))
+
+    def sizes(self) -> dict:
+        return sim_sizes(self.h)
+
+    def iteration_stats(self) -> dict:
+        return sim_iteration_stats(self.h)

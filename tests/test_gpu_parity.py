@@ -1,0 +1,219 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Both sides get the same seeded scene descriptions.  Tolerance: FP64 results agree to 1e-9
+relative (max-norm difference over max(max-norm of the oracle, 1e-12)); the two sides
+reassociate the same arithmetic (the device evaluates the v-step through the per-step map
+x = c + D w and uses u = -lambda), so they differ by rounding, amplified by cond(K_i)."""
+import numpy as np
+import pytest
+
+import oracle
+import scenegen as sg
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-9
+
+
+def rel(a, b):
+    a, b = np.asarray(a, float), np.asarray(b, float)
+    if a.size == 0 and b.size == 0:
+        return 0.0
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-12))
+
+
+@pytest.fixture(scope="module")
+def sa():
+    from paper_2302_14344_gb300 import subadmm
+    subadmm.load()
+    return subadmm
+
+
+def _compare(sim, orcs, problem, what=("vhat", "lam", "bodies"), tol=TOL):
+    for k, o in enumerate(orcs):
+        if "vhat" in what:
+            assert rel(sim.scene_vhat(k), o.vhat_all()) < tol, ("vhat", k)
+        if "lam" in what:
+            assert rel(sim.scene_lam(k), o.lam_all()) < tol, ("lambda", k)
+        if "bodies" in what and any(hasattr(s, "bodies") for s in problem.scenes[k].subs):
+            gb, ob = sim.scene_bodies(k), o.bodies_all()
+            assert rel(gb[:, 4:], ob[:, 4:]) < tol, ("bodies", k)
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_generic_fixed_iterations(sa, seed):
+    p = sg.generic(seed, n_scenes=6, max_iters=40, tol_primal=-1, n_sub=2 + seed,
+                   max_sides=3)
+    orcs = oracle.run(p)
+    sim = sa.Simulation(p)
+    sim.step(1)
+    _compare(sim, orcs, p, what=("vhat", "lam"))
+    for k, o in enumerate(orcs):
+        r, ro = sim.residuals(k), o.residuals()
+        assert r["iters"] == ro["iters"] == 40
+        assert abs(r["theta"] - ro["theta"]) <= 1e-9 * max(ro["theta"], 1e-300) + 1e-30
+        for j, iid in enumerate(sim.if_ids[k]):
+            assert rel(sim.z(iid), o.side(j, "z")) < TOL
+        for i, sid in enumerate(sim.sub_ids[k]):
+            assert abs(sim.beta(sid) - o.beta(i)) <= 1e-13 * o.beta(i)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_generic_converged_and_warm(sa, seed):
+    p = sg.generic(10 + seed, n_scenes=5, max_iters=20000, tol_primal=1e-9, warm="prev",
+                   n_range=(6, 12), types=(sg.EQUALITY, sg.SOFT, sg.HARD, sg.CONTACT))
+    orcs = oracle.run(p, steps=2)
+    sim = sa.Simulation(p)
+    sim.step(2)
+    for k, o in enumerate(orcs):
+        r, ro = sim.residuals(k), o.residuals()
+        assert r["converged"] == ro["converged"]
+        assert abs(r["iters"] - ro["iters"]) <= 1
+        assert rel(sim.scene_vhat(k), o.vhat_all()) < 1e-6
+
+
+def test_chain_fixed_iterations_several_steps(sa):
+    p = sg.chain(0, max_iters=100, tol_primal=-1, rho=1e3)
+    o = oracle.OracleScene(p.scenes[0], p.options)
+    sim = sa.Simulation(p)
+    for _ in range(5):
+        o.step()
+        sim.step(1)
+        _compare(sim, [o], p)
+
+
+def test_chain_in_one_launch_equals_stepwise(sa):
+    p = sg.chain(1, max_iters=100, tol_primal=-1, rho=1e3)
+    a = sa.Simulation(p)
+    b = sa.Simulation(p)
+    a.step(6)
+    for _ in range(6):
+        b.step(1)
+    assert np.array_equal(a.scene_bodies(0), b.scene_bodies(0))
+
+
+def test_robots_fixed_iterations(sa):
+    p = sg.robots(3, n_robots=4, max_iters=60, tol_primal=-1)
+    orcs = [oracle.OracleScene(sc, p.options) for sc in p.scenes]
+    sim = sa.Simulation(p)
+    for _ in range(4):
+        for o in orcs:
+            o.step()
+        sim.step(1)
+        _compare(sim, orcs, p)
+
+
+def test_robots_converged_iteration_counts(sa):
+    p = sg.robots(4, n_robots=3, tol_primal=1e-6, max_iters=1000)
+    orcs = oracle.run(p, steps=3)
+    sim = sa.Simulation(p)
+    sim.step(3)
+    for k, o in enumerate(orcs):
+        r, ro = sim.residuals(k), o.residuals()
+        assert r["converged"] and ro["converged"]
+        assert abs(r["iters"] - ro["iters"]) <= 1
+        assert rel(sim.scene_bodies(k)[:, 4:], o.bodies_all()[:, 4:]) < 1e-7
+
+
+def test_full_size_robot_batch_sampled(sa):
+    """The 64-robot workload in the benchmark's launch configuration (all scenes in one
+    launch, several steps per launch); scenes 0, 31 and 63 checked against the oracle."""
+    p = sg.robots(0, n_robots=64, tol_primal=1e-6, max_iters=1000)
+    sim = sa.Simulation(p)
+    sim.step(5)
+    for k in (0, 31, 63):
+        o = oracle.OracleScene(p.scenes[k], p.options)
+        for _ in range(5):
+            o.step()
+        assert sim.residuals(k)["converged"]
+        assert abs(sim.residuals(k)["iters"] - o.residuals()["iters"]) <= 1
+        assert rel(sim.scene_bodies(k)[:, 4:], o.bodies_all()[:, 4:]) < 1e-7
+
+
+def test_edge_cases(sa):
+    rng = np.random.default_rng(0)
+    subs = []
+    for n in (1, 2, 64):
+        G = rng.standard_normal((n, n))
+        subs.append(sg.GenericSub(G @ G.T + n * np.eye(n), rng.standard_normal(n)))
+    ifs = [
+        sg.RowsIf(sg.EQUALITY, [0, 1, 2], [rng.standard_normal((1, 1)),
+                                           rng.standard_normal((1, 2)),
+                                           rng.standard_normal((1, 64))], rng.standard_normal(1)),
+        sg.RowsIf(sg.HARD, [2], [rng.standard_normal((8, 64))], rng.standard_normal(8)),
+        sg.RowsIf(sg.CONTACT, [1, 2], [rng.standard_normal((3, 2)), rng.standard_normal((3, 64))],
+                  np.array([0.1, 0.0, 0.0]), mu=0.4),
+        sg.RowsIf(sg.SOFT, [0], [rng.standard_normal((2, 1))], rng.standard_normal(2), k=5.0,
+                  alpha=0.1),
+    ]
+    lone = sg.GenericSub(np.diag([2.0, 3.0]), np.array([1.0, -1.0]))   # no constraints
+    scenes = [sg.Scene(subs, ifs), sg.Scene([lone], [])]
+    p = sg.Problem(scenes, sg.Options(gravity=(0, 0, 0), warm="cold", tol_primal=-1,
+                                      max_iters=25))
+    orcs = oracle.run(p)
+    sim = sa.Simulation(p)
+    sim.step(1)
+    _compare(sim, orcs, p, what=("vhat", "lam"))
+    assert np.allclose(sim.scene_vhat(1), [0.5, -1.0 / 3.0], rtol=1e-15)
+
+
+def test_many_ragged_scenes_in_one_launch(sa):
+    """More scenes than SMs, of uneven sizes (tail scenes share blocks)."""
+    p = sg.generic(21, n_scenes=400, max_iters=12, tol_primal=-1, n_sub=3, n_range=(1, 9))
+    sim = sa.Simulation(p)
+    sim.step(1)
+    for k in (0, 151, 152, 399):
+        o = oracle.OracleScene(p.scenes[k], p.options)
+        o.step()
+        assert rel(sim.scene_vhat(k), o.vhat_all()) < TOL
+        assert rel(sim.scene_lam(k), o.lam_all()) < TOL
+
+
+def test_not_spd_is_reported_not_faulted(sa):
+    A = -np.eye(3)
+    p = sg.Problem([sg.Scene([sg.GenericSub(A, np.ones(3))], [])],
+                   sg.Options(gravity=(0, 0, 0), max_iters=5))
+    sim = sa.Simulation(p)
+    sim.step(1)
+    with pytest.raises(sa.SimError) as ei:
+        sim.residuals(0)
+    assert ei.value.code == sa.SIM_ENOTSPD
+
+
+def test_invalid_topology_is_rejected(sa):
+    p = sg.chain(0)
+    sim = sa.Simulation(p)
+    with pytest.raises(sa.SimError):
+        sa.sim_add_interface(sim.h, 0, sa.SIM_IF_BALL, 0, 0, [0, 5, 1, 0], None, None,
+                             np.zeros(23))
+    with pytest.raises(sa.SimError):
+        sa.sim_add_interface(sim.h, 0, sa.SIM_IF_EQUALITY, 9, 1, [0], np.zeros(9 * 12),
+                             np.zeros(9), None)
+    sim.step(1)
+    with pytest.raises(sa.SimError):
+        sa.sim_add_subsystem(sim.h, 0, sa.SIM_SUB_GENERIC, 1, np.ones(2))
+
+
+def test_bitwise_deterministic(sa):
+    p = sg.robots(7, n_robots=8, tol_primal=1e-6)
+    a, b = sa.Simulation(p), sa.Simulation(p)
+    a.step(3)
+    b.step(3)
+    for k in range(8):
+        assert np.array_equal(a.scene_bodies(k), b.scene_bodies(k))
+        assert np.array_equal(a.scene_lam(k), b.scene_lam(k))
+
+
+def test_state_roundtrip_through_host_buffers(sa):
+    import torch
+    p = sg.robots(1, n_robots=2)
+    sim = sa.Simulation(p)
+    nb = sim.sizes()["bodies"]
+    buf = torch.empty(13 * nb, dtype=torch.float64).pin_memory()
+    sa.sim_read_state(sim.h, buf.data_ptr())
+    ref = np.concatenate([sim.scene_bodies(k)[:, 4:] for k in range(2)]).ravel()
+    assert np.array_equal(buf.numpy(), ref)
+    buf[2] += 1.0
+    sa.sim_write_state(sim.h, buf.data_ptr())
+    sim.sync()
+    assert sim.scene_bodies(0)[0, 6] == ref[2] + 1.0
