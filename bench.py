@@ -27,6 +27,7 @@ if ROOT not in sys.path:
 
 METRIC = "sim steps/sec at primal residual ≤1e-6, chosen form vs plain FP64, 1 GB300"
 FP64_NOMINAL_TFLOPS = 1.25     # GB300 FP64 (non-tensor) rate quoted for this pool
+FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # 152 SMs x 128 FP32 lanes x FMA x clock
 L2_FLUSH_BYTES = 512 << 20     # > 129 MB L2
 
 
@@ -201,6 +202,47 @@ def run_reference(args, rank: int, world: int):
     return 0
 
 
+def time_form(subadmm, p, precision, args, stream, dev, local, dist, flush, sample_clocks):
+    """Warm-up W steps, then K timed steps in launches of ``--steps-per-launch`` steps (the
+    scenes are independent, so one launch advances every scene by that many steps without a
+    device-wide wait per step).  The L2 is flushed before every timed launch."""
+    import torch
+    sim = subadmm.Simulation(p, stream=stream.cuda_stream, device=local, precision=precision)
+    for _ in range(args.warmup):
+        sim.step(1)
+    sim.sync()
+    sim.iteration_stats()   # clear counters
+    K = args.steps
+    spl = max(1, min(args.steps_per_launch, K))
+    chunks = [spl] * (K // spl) + ([K % spl] if K % spl else [])
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in chunks]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in chunks]
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clk = ClockSampler(local) if sample_clocks else None
+    if clk:
+        clk.__enter__()
+    for k, n in enumerate(chunks):
+        flush.zero_()                      # L2 flushed between timed launches
+        ev0[k].record(stream)
+        sim.step(n)
+        ev1[k].record(stream)
+    torch.cuda.synchronize(dev)
+    if clk:
+        clk.__exit__()
+    if dist is not None:
+        dist.barrier()
+    launch_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+    t_ms = float(sum(launch_ms))
+    if dist is not None:
+        tt = torch.tensor([t_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    stats = sim.iteration_stats()
+    return sim, t_ms, launch_ms, stats, (clk.summary() if clk else None)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -211,6 +253,12 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--reference-seconds", type=float, default=120.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--form", default="mixed", choices=["mixed", "fp64"],
+                    help="mixed: FP32 iterations with FP64 setup and residual check (the "
+                         "chosen form); fp64: the plain FP64 form")
+    ap.add_argument("--steps-per-launch", type=int, default=50)
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip timing the plain FP64 form next to the chosen one")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -221,7 +269,6 @@ def main():
     if args.impl == "reference":
         return run_reference(args, rank, world)
 
-    import numpy as np
     import torch
     import scenegen as sg
     from paper_2302_14344_gb300 import subadmm
@@ -235,56 +282,42 @@ def main():
     stream = torch.cuda.current_stream(dev)
     h = 2e-3
     p = sg.robots(seed=rank, n_robots=args.robots, h=h, tol_primal=1e-6, max_iters=1000)
-    sim = subadmm.Simulation(p, stream=stream.cuda_stream, device=local)
-    sizes = sim.sizes()
     work = algorithmic_work(p)
     it_flops = work[0][0]
     st_flops = sum(w[1] for w in work)
     assert all(w[0] == it_flops for w in work)
-
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    # warm-up steps (untimed)
-    for _ in range(args.warmup):
-        sim.step(1)
-    sim.sync()
-    sim.iteration_stats()   # clear counters
+    forms = {"mixed": subadmm.SIM_MIXED, "fp64": subadmm.SIM_FP64}
 
+    sim, t_ms, launch_ms, stats, clocks = time_form(subadmm, p, forms[args.form], args, stream,
+                                                  dev, local, dist, flush, True)
     K = args.steps
-    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
-    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
-    if dist is not None:
-        dist.barrier()
-    torch.cuda.synchronize(dev)
-    with ClockSampler(local) as clk:
-        for k in range(K):
-            flush.zero_()                      # L2 flushed between timed steps
-            ev0[k].record(stream)
-            sim.step(1)
-            ev1[k].record(stream)
-        torch.cuda.synchronize(dev)
-    if dist is not None:
-        dist.barrier()
-    step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
-    t_ms = float(sum(step_ms))
-    stats = sim.iteration_stats()
-    not_conv = stats["not_converged"]
-    if dist is not None:
-        tt = torch.tensor([t_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
+    sizes = sim.sizes()
     value = world * K / (t_ms / 1e3)
-
-    # roofline of the step kernel (the only kernel of a step): FP64 ALU
     total_iters = stats["total_iters"]
     flops = it_flops * total_iters + st_flops * K
-    achieved_tflops = flops / (t_ms / 1e3) / 1e12
-    peaks = measured_peaks()
-    roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_NOMINAL_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved_tflops / FP64_NOMINAL_TFLOPS,
-                "traffic": None,
-                "note": "FP64 non-tensor pipe; peak = nominal GB300 FP64 rate (152 SMs x "
-                        "2 FP64 FMA/clk x 2 flops x ~2.06 GHz); algorithmic flops of the "
-                        "triangular-solve form per iteration and per step"}
+    achieved = flops / (t_ms / 1e3) / 1e12
+    if args.form == "mixed":
+        peak, pipe = FP32_NOMINAL_TFLOPS, "FP32"
+    else:
+        peak, pipe = FP64_NOMINAL_TFLOPS, "FP64"
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "note": f"{pipe} non-tensor pipe (iterations; the mixed form's per-step setup "
+                        f"is FP64); peak = 152 SMs x lanes x 2 flops x 2.07 GHz; algorithmic "
+                        f"flops of the triangular-solve form, "
+                        f"{it_flops} per scene-iteration and {st_flops / len(p.scenes):.0f} "
+                        f"per scene-step"}
+
+    compare = None
+    if not args.no_compare and args.form != "fp64":
+        sim2, t2, sm2, st2, _ = time_form(subadmm, p, subadmm.SIM_FP64, args, stream, dev, local,
+                                          dist, flush, False)
+        compare = {"value": world * K / (t2 / 1e3), "unit": "steps/s", "ms_per_step": t2 / K,
+                   "mean_iterations": st2["total_iters"] / max(st2["scene_steps"], 1),
+                   "not_converged": st2["not_converged"],
+                   "chosen_over_plain": (world * K / (t_ms / 1e3)) / (world * K / (t2 / 1e3))}
+        sim2.close()
 
     # end to end through the C ABI with host buffers: state in from pinned host memory,
     # one step, state out to pinned host memory, every step
@@ -299,37 +332,46 @@ def main():
         sim.step(1)
         subadmm.sim_read_state(sim.h, hbuf.data_ptr())
     e2e_dt = time.perf_counter() - t0
-    e2e = {"value": world * e2e_steps / e2e_dt, "unit": "steps/s",
-           "h2d_bytes_per_step": 13 * 8 * nb, "d2h_bytes_per_step": 13 * 8 * nb,
-           "steps": e2e_steps, "timer": "host wall clock"}
     if dist is not None:
         tt = torch.tensor([e2e_dt], device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e["value"] = world * e2e_steps / float(tt.item())
+        e2e_dt = float(tt.item())
+    e2e = {"value": world * e2e_steps / e2e_dt, "unit": "steps/s",
+           "h2d_bytes_per_step": 13 * 8 * nb, "d2h_bytes_per_step": 13 * 8 * nb,
+           "steps": e2e_steps, "timer": "host wall clock",
+           "segment": f"steps {args.warmup + K}..{args.warmup + K + e2e_steps} of the run"}
 
     if rank == 0:
+        n_if = sum(len(sc.ifs) for sc in p.scenes) / max(len(p.scenes), 1)
         line = {
             "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": t_ms / K, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_desc(args.robots, h), "form": "plain FP64",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.form == "mixed" else "f64", "data": "synthetic",
+            "config": {"workload": workload_desc(args.robots, h),
+                       "form": ("mixed: FP64 assembly, factorisation and residual check, "
+                                "FP32 iterations") if args.form == "mixed" else "plain FP64",
                        "robots": args.robots, "scenes_per_gpu": sizes["scenes"],
                        "subsystems": sizes["subsystems"], "dof": sizes["dof"],
                        "interfaces": sizes["interfaces"], "rows": sizes["rows"],
                        "side_rows": sizes["side_rows"], "parallelism": f"scenes x{world}",
                        "l2": "flushed between timed steps (512 MiB write)",
-                       "launch": "one step kernel per step, one block of 256 threads per scene"},
+                       "launch": f"step kernel, {min(args.steps_per_launch, K)} steps per launch, "
+                                 f"one block of 256 threads per scene",
+                       "timed_segment": f"steps {args.warmup}..{args.warmup + K} of a run from "
+                                        f"the drop"},
             "iterations": {"mean_per_scene_step": total_iters / max(stats["scene_steps"], 1),
-                           "max": stats["max_iters"], "not_converged": not_conv},
-            "interface_updates_per_s": sum(len(sc.ifs) for sc in p.scenes) * total_iters /
-                                       max(len(p.scenes), 1) * world / (t_ms / 1e3),
+                           "max": stats["max_iters"], "not_converged": stats["not_converged"],
+                           "scene_steps": stats["scene_steps"]},
+            "interface_updates_per_s": n_if * total_iters * world / (t_ms / 1e3),
+            "plain_fp64": compare,
             "roofline": roofline,
             "e2e": e2e,
-            "gpu_launches": K,
-            "clocks": clk.summary(),
-            "kernel_ms": {"mean": statistics.mean(step_ms), "median": statistics.median(step_ms),
-                          "min": min(step_ms), "max": max(step_ms)},
-            "peaks_file": bool(peaks),
+            "gpu_launches": len(launch_ms),
+            "clocks": clocks,
+            "launch_ms": {"mean": statistics.mean(launch_ms),
+                          "median": statistics.median(launch_ms),
+                          "min": min(launch_ms), "max": max(launch_ms)},
         }
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(sg.robots(seed=0, n_robots=args.robots, h=h,

@@ -67,6 +67,8 @@ extern "C" {
 #define SIM_STOP_PRIMAL 0     /* stop when max|x - z| <= tol and max|z^{l+1}-z^l| <= tol    */
 #define SIM_STOP_THETA 1      /* stop when theta < theta_th after the v-step (Eq. residual) */
 #define SIM_FP64 0            /* every step in double precision                             */
+#define SIM_MIXED 1           /* FP64 assembly, beta, factorisation and final residual check;
+                                 FP32 iterations (resumed if the FP64 check misses the tol.) */
 
 /* what sim_get() reads */
 #define SIM_GET_VHAT 0        /* id = subsystem: n doubles, v-hat of the last step          */
@@ -88,7 +90,7 @@ typedef struct sim_options {
     double tol_primal;     /* <= 0: run exactly max_iters iterations      default 1e-6       */
     double theta_th;       /*                                             default 1e-12      */
     int max_iters;         /* l_max                                       default 1000       */
-    int precision;         /* SIM_FP64                                    default FP64       */
+    int precision;         /* SIM_FP64 or SIM_MIXED                       default FP64       */
     int device;            /* CUDA device ordinal                         default 0          */
     void *stream;          /* cudaStream_t to enqueue on; NULL = default  default NULL       */
 } sim_options;

@@ -21,25 +21,33 @@ enum { KIND_GENERIC = 0, KIND_RIGID = 1 };
 enum { ST_OK = 0, ST_NOTSPD = -3, ST_NAN = -4 };
 
 // One scene: a set of subsystems and constraints solved by one thread block.  The on-chip
-// working set lives in dynamic shared memory at the offsets below (in doubles, then ints).
+// working set lives in dynamic shared memory: a double region (factors), a region of the
+// iteration type T, and an int region (tables).  Offsets are in elements of each region.
 struct SceneDesc {
     int sub0, nsub;        // global subsystem range
     int con0, ncon;        // global constraint range
     int nsr, nrow;         // side-rows and rows of the scene
+    int nitem, nlist;      // projection items (a row, or a whole contact) and their side lists
+    int item_g0, list_g0;  // global offsets of the scene's item / list tables
     int sr_g0, row_g0;     // global offset of the scene's side-rows / rows (z, lambda state)
-    // shared-memory offsets (doubles)
-    int o_x, o_y, o_z, o_w0, o_w1, o_lam, o_e, o_beta;
-    int o_int;             // first int slot (after all doubles): side-row -> row, -> subsystem
-    int smem_bytes;
+    // double region
+    int od_beta;
+    // T region (element offsets)
+    int ot_x, ot_y, ot_z, ot_yo, ot_zo, ot_w0, ot_w1, ot_invb, ot_b;  // per side-row
+    int ot_lam, ot_e, ot_invs, ot_kf, ot_al, ot_mu;              // per row
+    // byte offsets of the T and int regions; total bytes
+    int t_base, i_base, smem_bytes;
 };
 
 struct SubDesc {
     int kind, n, m;        // DOF, side-rows (rows of J_ci)
-    int sr0;               // scene-local first side-row of this subsystem
+    int mpad;              // m rounded up to a whole 16-byte vector of the iteration type
+    int sr0;               // scene-local first side-row (16-byte aligned in the T region)
     int local;             // index inside its scene
     int body0, nb;         // first global body, body count (rigid)
     int gen_off;           // pool offset of A (n*n) then b (n) (generic)
-    int o_W, o_L, o_D, o_b, o_c;   // shared-memory offsets (doubles)
+    int od_W, od_L, od_b;  // double region: W (m x n), L (n x n), b / g / v (n)
+    int ot_D, ot_c;        // T region: D (m x m), c (m)
     int v_off;             // global offset of v-hat
 };
 
@@ -54,10 +62,18 @@ struct ConDesc {
     int side_b;            // model: side that holds body b (-1 for the world)
 };
 
+// One z-step work item: a row of an equality / hard / soft constraint, or a whole contact.
+// list[lo .. lo+ns) holds the scene-local side-row of each side (row 0 for a contact).
+struct Item {
+    int type, ns, row, lo;
+};
+
 struct StepParams {
     const SceneDesc *scenes;
     const SubDesc *subs;
     const ConDesc *cons;
+    const Item *items;
+    const int *lists;
     const double *pool;    // constant data and generic A, b
     double *bodies;        // 17 doubles per body (state in and out)
     double *vhat;          // per DOF

@@ -7,7 +7,7 @@
 //   factor     K_i = A_i + beta_i J_ci^T J_ci = L_i L_i^T                   (Algorithm 1, factorise)
 //   map        W_i = L_i^-1 J_ci^T, g_i = L_i^-1 b_i,
 //              D_i = W_i^T W_i = J_ci K_i^-1 J_ci^T, c_i = W_i^T g_i = J_ci K_i^-1 b_i
-//   iterate    x_i = c_i + D_i (beta_i z_i - u_i)                           (Eq. admm-1i, then x = J v)
+//   iterate    x_i = c_i + D_i (beta_i z_i - u_i)                           (Eq. admm-1i, x = J v)
 //              y_i = beta_i x_i + u_i ; theta                               (Eq. surrogate, residual)
 //              lambda_j by type, beta_i z_ij = y_ij + lambda_j              (Eq. admm-2j)
 //              u_i = -lambda (the u-step of Eq. admm-3, simplified by Eq. surrogate)
@@ -17,8 +17,14 @@
 // The v-step is evaluated through the per-step affine map x = c + D w instead of two
 // triangular solves and two products with J per iteration: it is the same linear map,
 // reassociated, so every iteration is a small dense mat-vec whose rows run in parallel.
-// The u-step uses the identity u^{l+1} = y^{l+1} - beta z^{l+1} = -lambda^{l+1} (from
-// Eq. admm-3 and Eq. surrogate), so each row keeps one lambda shared by all its sides.
+// The u-step uses u^{l+1} = y^{l+1} - beta z^{l+1} = -lambda^{l+1} (Eq. admm-3 with
+// Eq. surrogate), so each row keeps one lambda shared by its sides and w = y + 2 lambda.
+//
+// T is the iteration type.  T = double: every step in FP64.  T = float (mixed form): the
+// setup (assembly, beta, factor, W, g) stays FP64, D and c are rounded to FP32 for the
+// iterations, and when the FP32 stop test passes the primal residual is re-evaluated in
+// FP64 (x = W^T (g + W w)); if that misses the tolerance the iterations resume with a
+// tighter FP32 test.  v-hat is always recovered in FP64.
 #pragma once
 #include "layout.h"
 #include "rigid_model.cuh"
@@ -41,25 +47,41 @@ __device__ __forceinline__ double warp_max(double v)
     return v;
 }
 
-// per-side-row integer tables kept in shared memory for the whole launch
-struct SrTables {
-    int *row;    // scene row of the side-row (lambda, e index)
-    int *sub;    // scene-local subsystem
-    int *drow;   // shared-memory offset of its row of D
-    int *coff;   // shared-memory offset of its entry of c
-    int *wbase;  // first side-row of its subsystem
-    int *mlen;   // side-rows of its subsystem
+// shared-memory views of one scene
+template <typename T>
+struct View {
+    double *db;          // double region
+    T *tb;               // T region
+    int *row, *sub, *drow, *coff, *wbase, *mlen;   // per side-row tables
+    Item *item;
+    int *list;
 };
 
-__device__ void scene_tables(const StepParams &P, const SceneDesc &S, double *sm, SrTables &T)
+template <typename T>
+__device__ View<T> scene_view(const SceneDesc &S, unsigned char *raw)
 {
-    int *ib = reinterpret_cast<int *>(sm + S.o_int);
-    T.row = ib;
-    T.sub = ib + S.nsr;
-    T.drow = ib + 2 * S.nsr;
-    T.coff = ib + 3 * S.nsr;
-    T.wbase = ib + 4 * S.nsr;
-    T.mlen = ib + 5 * S.nsr;
+    View<T> V;
+    V.db = reinterpret_cast<double *>(raw);
+    V.tb = reinterpret_cast<T *>(raw + S.t_base);
+    int *ib = reinterpret_cast<int *>(raw + S.i_base);
+    V.row = ib;
+    V.sub = ib + S.nsr;
+    V.drow = ib + 2 * S.nsr;
+    V.coff = ib + 3 * S.nsr;
+    V.wbase = ib + 4 * S.nsr;
+    V.mlen = ib + 5 * S.nsr;
+    V.item = reinterpret_cast<Item *>(ib + 6 * S.nsr);
+    V.list = ib + 6 * S.nsr + 4 * S.nitem;
+    return V;
+}
+
+template <typename T>
+__device__ void scene_tables(const StepParams &P, const SceneDesc &S, const View<T> &V)
+{
+    for (int t = threadIdx.x; t < S.nsr; t += blockDim.x) {
+        V.row[t] = 0; V.sub[t] = 0; V.drow[t] = 0; V.coff[t] = 0; V.wbase[t] = 0; V.mlen[t] = 0;
+    }
+    __syncthreads();
     for (int j = threadIdx.x; j < S.ncon; j += blockDim.x) {
         const ConDesc &c = P.cons[S.con0 + j];
         for (int s = 0; s < c.ns; ++s) {
@@ -67,18 +89,20 @@ __device__ void scene_tables(const StepParams &P, const SceneDesc &S, double *sm
             for (int r = 0; r < c.rows; ++r) {
                 const int t = c.sr[s] + r;
                 const int lr = t - u.sr0;
-                T.row[t] = c.row0 + r;
-                T.sub[t] = c.sub[s];
-                T.drow[t] = u.o_D + lr * u.m;
-                T.coff[t] = u.o_c + lr;
-                T.wbase[t] = u.sr0;
-                T.mlen[t] = u.m;
+                V.row[t] = c.row0 + r;
+                V.sub[t] = c.sub[s];
+                V.drow[t] = u.ot_D + lr * u.mpad;
+                V.coff[t] = u.ot_c + lr;
+                V.wbase[t] = u.sr0;
+                V.mlen[t] = u.m;
             }
         }
     }
+    for (int i = threadIdx.x; i < S.nitem; i += blockDim.x) V.item[i] = P.items[S.item_g0 + i];
+    for (int i = threadIdx.x; i < S.nlist; i += blockDim.x) V.list[i] = P.lists[S.list_g0 + i];
 }
 
-// Parameters k, alpha, mu of a constraint (model kinds derive them from their drive gains)
+// k, alpha, mu of a constraint (model kinds derive them from their drive gains)
 __device__ __forceinline__ void con_params(const ConDesc &c, const double *pool, double h,
                                            double &k, double &alpha, double &mu)
 {
@@ -93,22 +117,24 @@ __device__ __forceinline__ void con_params(const ConDesc &c, const double *pool,
     }
 }
 
-// Step (assemble .. factor .. map) for all subsystems of the scene.  Returns via s_status.
-__device__ void scene_setup(const StepParams &P, const SceneDesc &S, double *sm, int *s_status)
+// assemble .. factor .. map, and the per-step constants of the z-step
+template <typename T>
+__device__ void scene_setup(const StepParams &P, const SceneDesc &S, const View<T> &V,
+                            int *s_status)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    // zero W and K of rigid subsystems (their rows only fill body columns); generic blocks
-    // are copied whole
+    double *db = V.db;
+    T *tb = V.tb;
     for (int i = warp; i < S.nsub; i += SUBADMM_WARPS) {
         const SubDesc &u = P.subs[S.sub0 + i];
-        double *W = sm + u.o_W, *K = sm + u.o_L;
+        double *W = db + u.od_W, *K = db + u.od_L;
         if (u.kind == KIND_RIGID) {
             for (int q = lane; q < u.m * u.n; q += 32) W[q] = 0.0;
             for (int q = lane; q < u.n * u.n; q += 32) K[q] = 0.0;
         } else {
             const double *A = P.pool + u.gen_off;
             for (int q = lane; q < u.n * u.n; q += 32) K[q] = A[q];
-            for (int q = lane; q < u.n; q += 32) sm[u.o_b + q] = A[u.n * u.n + q];
+            for (int q = lane; q < u.n; q += 32) db[u.od_b + q] = A[u.n * u.n + q];
         }
     }
     __syncthreads();
@@ -120,26 +146,26 @@ __device__ void scene_setup(const StepParams &P, const SceneDesc &S, double *sm,
             double Ad[6], bb[6];
             body_dynamics(P.bodies + (size_t)(u.body0 + k) * SUBADMM_BODY, P.h, P.g0, P.g1, P.g2,
                           Ad, bb);
-            double *K = sm + u.o_L;
+            double *K = db + u.od_L;
             for (int d = 0; d < 6; ++d) {
                 const int q = 6 * k + d;
                 K[q * u.n + q] = Ad[d];
-                sm[u.o_b + q] = bb[d];
+                db[u.od_b + q] = bb[d];
             }
         }
     }
     // constraint rows into W (as rows of J_ci) and e (thread per constraint)
+    T *E = tb + S.ot_e;
     for (int j = tid; j < S.ncon; j += blockDim.x) {
         const ConDesc &c = P.cons[S.con0 + j];
-        double *e = sm + S.o_e + c.row0;
         if (c.src <= SRC_CONTACT) {
             const double *p = P.pool + c.par_off + 3;
-            for (int r = 0; r < c.rows; ++r) e[r] = p[r];
+            for (int r = 0; r < c.rows; ++r) E[c.row0 + r] = (T)p[r];
             const double *J = p + c.rows;
             for (int s = 0; s < c.ns; ++s) {
                 const SubDesc &u = P.subs[S.sub0 + c.sub[s]];
                 for (int r = 0; r < c.rows; ++r) {
-                    double *Wr = sm + u.o_W + (c.sr[s] + r - u.sr0) * u.n;
+                    double *Wr = db + u.od_W + (c.sr[s] + r - u.sr0) * u.n;
                     for (int q = 0; q < u.n; ++q) Wr[q] = J[r * u.n + q];
                 }
                 J += c.rows * u.n;
@@ -147,18 +173,18 @@ __device__ void scene_setup(const StepParams &P, const SceneDesc &S, double *sm,
         } else {
             double Ja[30], Jb[30], ee[5], kk = 0.0, al = 0.0;
             model_rows(c, P.pool + c.par_off, P.bodies, P.h, P.gamma, Ja, Jb, ee, &kk, &al);
-            for (int r = 0; r < c.rows; ++r) e[r] = ee[r];
+            for (int r = 0; r < c.rows; ++r) E[c.row0 + r] = (T)ee[r];
             {
                 const SubDesc &u = P.subs[S.sub0 + c.sub[0]];
                 for (int r = 0; r < c.rows; ++r) {
-                    double *Wr = sm + u.o_W + (c.sr[0] + r - u.sr0) * u.n + 6 * c.ba;
+                    double *Wr = db + u.od_W + (c.sr[0] + r - u.sr0) * u.n + 6 * c.ba;
                     for (int q = 0; q < 6; ++q) Wr[q] = Ja[6 * r + q];
                 }
             }
             if (c.side_b >= 0) {
                 const SubDesc &u = P.subs[S.sub0 + c.sub[c.side_b]];
                 for (int r = 0; r < c.rows; ++r) {
-                    double *Wr = sm + u.o_W + (c.sr[c.side_b] + r - u.sr0) * u.n + 6 * c.bb;
+                    double *Wr = db + u.od_W + (c.sr[c.side_b] + r - u.sr0) * u.n + 6 * c.bb;
                     for (int q = 0; q < 6; ++q) Wr[q] = Jb[6 * r + q];
                 }
             }
@@ -169,7 +195,8 @@ __device__ void scene_setup(const StepParams &P, const SceneDesc &S, double *sm,
     for (int i = warp; i < S.nsub; i += SUBADMM_WARPS) {
         const SubDesc &u = P.subs[S.sub0 + i];
         const int n = u.n, m = u.m;
-        double *W = sm + u.o_W, *K = sm + u.o_L, *D = sm + u.o_D, *b = sm + u.o_b, *cc = sm + u.o_c;
+        double *W = db + u.od_W, *K = db + u.od_L, *b = db + u.od_b;
+        T *D = tb + u.ot_D, *cc = tb + u.ot_c;
         // beta_i = Tr(A_i) / Tr(J_ci^T J_ci)  (Sec. III-D)
         double trA = 0.0, trJ = 0.0;
         for (int q = lane; q < n; q += 32) trA += K[q * n + q];
@@ -178,7 +205,7 @@ __device__ void scene_setup(const StepParams &P, const SceneDesc &S, double *sm,
         trJ = warp_sum(trJ);
         const double beta = P.beta_fixed ? P.rho : (trJ > 0.0 ? trA / trJ : 1.0);
         if (lane == 0) {
-            sm[S.o_beta + i] = beta;
+            db[S.od_beta + i] = beta;
             P.beta[S.sub0 + i] = beta;
         }
         // K_i = A_i + beta_i J_ci^T J_ci (lower triangle)
@@ -196,8 +223,9 @@ __device__ void scene_setup(const StepParams &P, const SceneDesc &S, double *sm,
             const double d = K[k * n + k];
             if (!(d > 0.0) || !isfinite(d)) { ok = false; break; }
             const double lkk = sqrt(d);
+            const double ilkk = 1.0 / lkk;
             __syncwarp();
-            for (int r = k + lane; r < n; r += 32) K[r * n + k] = (r == k) ? lkk : K[r * n + k] / lkk;
+            for (int r = k + lane; r < n; r += 32) K[r * n + k] = (r == k) ? lkk : K[r * n + k] * ilkk;
             __syncwarp();
             for (int r = k + 1 + lane; r < n; r += 32) {
                 const double lrk = K[r * n + k];
@@ -219,49 +247,161 @@ __device__ void scene_setup(const StepParams &P, const SceneDesc &S, double *sm,
             }
         }
         __syncwarp();
-        // D = W^T W (as rows of W), c = W^T g
-        for (int t = lane; t < m * m + m; t += 32) {
-            if (t < m * m) {
-                const int r = t / m, s = t - r * m;
+        // D = W^T W (as rows of W, symmetric; rows padded with zeros to mpad), c = W^T g,
+        // rounded to T
+        const int mp = u.mpad;
+        for (int t = lane; t < m * mp + m; t += 32) {
+            if (t < m * mp) {
+                const int r = t / mp, s = t - r * mp;
+                if (s >= m) { D[r * mp + s] = (T)0; continue; }
                 if (s > r) continue;
                 double acc = 0.0;
                 for (int p = 0; p < n; ++p) acc += W[r * n + p] * W[s * n + p];
-                D[r * m + s] = acc;
-                D[s * m + r] = acc;
+                D[r * mp + s] = (T)acc;
+                D[s * mp + r] = (T)acc;
             } else {
-                const int r = t - m * m;
+                const int r = t - m * mp;
                 double acc = 0.0;
                 for (int p = 0; p < n; ++p) acc += W[r * n + p] * b[p];
-                cc[r] = acc;
+                cc[r] = (T)acc;
+            }
+        }
+    }
+    __syncthreads();
+    // per-step z-step constants: 1/s, soft gain k/(1 + s alpha k), alpha, mu (per row);
+    // beta and 1/beta per side-row
+    T *INVS = tb + S.ot_invs, *KF = tb + S.ot_kf, *AL = tb + S.ot_al, *MU = tb + S.ot_mu;
+    T *INVB = tb + S.ot_invb, *BT = tb + S.ot_b;
+    const double *BETA = db + S.od_beta;
+    for (int j = tid; j < S.ncon; j += blockDim.x) {
+        const ConDesc &c = P.cons[S.con0 + j];
+        double s = 0.0;
+        for (int q = 0; q < c.ns; ++q) s += 1.0 / BETA[c.sub[q]];
+        double kk, al, mu;
+        con_params(c, P.pool, P.h, kk, al, mu);
+        const double kf = (c.type == TYPE_SOFT) ? kk / (1.0 + s * al * kk) : 0.0;
+        for (int r = 0; r < c.rows; ++r) {
+            INVS[c.row0 + r] = (T)(1.0 / s);
+            KF[c.row0 + r] = (T)kf;
+            AL[c.row0 + r] = (T)al;
+            MU[c.row0 + r] = (T)mu;
+        }
+        for (int q = 0; q < c.ns; ++q) {
+            const double be = BETA[c.sub[q]];
+            for (int r = 0; r < c.rows; ++r) {
+                INVB[c.sr[q] + r] = (T)(1.0 / be);
+                BT[c.sr[q] + r] = (T)be;
             }
         }
     }
     __syncthreads();
 }
 
+// h_i = g_i + W_i w (FP64) for every subsystem (warp per subsystem).  h lives right after
+// g in the double region (the host reserves 2 n doubles at od_b).
+template <typename T>
+__device__ void form_h(const StepParams &P, const SceneDesc &S, const View<T> &V, const T *w)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = warp; i < S.nsub; i += SUBADMM_WARPS) {
+        const SubDesc &u = P.subs[S.sub0 + i];
+        const int n = u.n, m = u.m;
+        const double *W = V.db + u.od_W, *g = V.db + u.od_b;
+        double *h = V.db + u.od_b + n;
+        const T *wi = w + u.sr0;
+        for (int p = lane; p < n; p += 32) {
+            double acc = g[p];
+            for (int r = 0; r < m; ++r) acc += W[r * n + p] * (double)wi[r];
+            h[p] = acc;
+        }
+    }
+}
+
+// 16-byte vectors of the iteration type and residual bit patterns.  Residuals are
+// non-negative, so their IEEE bit patterns order like their values and a NaN (sign bit
+// cleared by fabs) orders above +inf: maxima reduce on the integer pipe.
+template <typename T> struct VecOf;
+template <> struct VecOf<float> { using V = float4; using U = unsigned; static constexpr int N = 4; };
+template <> struct VecOf<double> { using V = double2; using U = unsigned long long; static constexpr int N = 2; };
+
+__device__ __forceinline__ float vdot(const float4 a, const float4 b, float acc)
+{
+    acc = fmaf(a.x, b.x, acc); acc = fmaf(a.y, b.y, acc);
+    acc = fmaf(a.z, b.z, acc); acc = fmaf(a.w, b.w, acc);
+    return acc;
+}
+__device__ __forceinline__ double vdot(const double2 a, const double2 b, double acc)
+{
+    acc = fma(a.x, b.x, acc); acc = fma(a.y, b.y, acc);
+    return acc;
+}
+__device__ __forceinline__ unsigned rbits(float v) { return __float_as_uint(v); }
+__device__ __forceinline__ unsigned long long rbits(double v) { return (unsigned long long)__double_as_longlong(v); }
+__device__ __forceinline__ unsigned umax(unsigned a, unsigned b) { return a > b ? a : b; }
+__device__ __forceinline__ unsigned long long umax(unsigned long long a, unsigned long long b) { return a > b ? a : b; }
+__device__ __forceinline__ unsigned warp_umax(unsigned v) { return __reduce_max_sync(0xffffffffu, v); }
+__device__ __forceinline__ unsigned long long warp_umax(unsigned long long v)
+{
+    const unsigned hi = (unsigned)(v >> 32), lo = (unsigned)v;
+    const unsigned mh = __reduce_max_sync(0xffffffffu, hi);
+    const unsigned ml = __reduce_max_sync(0xffffffffu, hi == mh ? lo : 0u);
+    return ((unsigned long long)mh << 32) | ml;
+}
+__device__ __forceinline__ unsigned tol_bits(float, double tol) { return __float_as_uint(__double2float_rd(tol)); }
+__device__ __forceinline__ unsigned long long tol_bits(double, double tol) { return rbits(tol); }
+__device__ __forceinline__ unsigned inf_bits(float) { return 0x7f800000u; }
+__device__ __forceinline__ unsigned long long inf_bits(double) { return 0x7ff0000000000000ull; }
+
+// Sum (k = 0) and maxima (k = 1, 2) of three per-thread doubles over the block.
+__device__ __forceinline__ void block_reduce3(double (*red)[SUBADMM_WARPS], double &a, double &b,
+                                              double &c)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    a = warp_sum(a); b = warp_max(b); c = warp_max(c);
+    __syncthreads();
+    if (lane == 0) { red[0][warp] = a; red[1][warp] = b; red[2][warp] = c; }
+    __syncthreads();
+    a = 0.0; b = 0.0; c = 0.0;
+    for (int q = 0; q < SUBADMM_WARPS; ++q) {
+        a += red[0][q]; b = nanmax(b, red[1][q]); c = nanmax(c, red[2][q]);
+    }
+    __syncthreads();
+}
+
+template <typename T, int SPLIT>
 __global__ void __launch_bounds__(SUBADMM_THREADS) step_kernel(StepParams P)
 {
-    extern __shared__ __align__(16) double sm[];
-    __shared__ double red[2][4][SUBADMM_WARPS];
+    using VT = typename VecOf<T>::V;
+    using U = typename VecOf<T>::U;
+    constexpr int VN = VecOf<T>::N;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ double red[4][SUBADMM_WARPS];
+    __shared__ U ured[2][SUBADMM_WARPS];
     __shared__ int s_status;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr bool MIXED = sizeof(T) == 4;
 
     for (int sc = blockIdx.x; sc < P.nscenes; sc += gridDim.x) {
         const SceneDesc S = P.scenes[sc];
-        SrTables T;
-        scene_tables(P, S, sm, T);
-        double *X = sm + S.o_x, *Y = sm + S.o_y, *Z = sm + S.o_z, *LAM = sm + S.o_lam;
-        double *E = sm + S.o_e, *BETA = sm + S.o_beta;
-        double *Wv[2] = {sm + S.o_w0, sm + S.o_w1};
+        const View<T> V = scene_view<T>(S, smraw);
+        T *X = V.tb + S.ot_x, *Y = V.tb + S.ot_y, *Z = V.tb + S.ot_z, *LAM = V.tb + S.ot_lam;
+        T *YO = V.tb + S.ot_yo, *ZO = V.tb + S.ot_zo;
+        T *E = V.tb + S.ot_e, *INVB = V.tb + S.ot_invb, *BT = V.tb + S.ot_b;
+        T *INVS = V.tb + S.ot_invs, *KF = V.tb + S.ot_kf, *AL = V.tb + S.ot_al;
+        T *MU = V.tb + S.ot_mu;
+        T *Wv[2] = {V.tb + S.ot_w0, V.tb + S.ot_w1};
+        // per-side-row arrays start zero (padding side-rows between subsystems stay zero)
+        for (int q = tid; q < S.ot_lam - S.ot_x; q += blockDim.x) V.tb[S.ot_x + q] = (T)0;
+        scene_tables<T>(P, S, V);
         __syncthreads();
 
         for (int step = 0; step < P.n_steps; ++step) {
             if (tid == 0) s_status = ST_OK;
             __syncthreads();
-            scene_setup(P, S, sm, &s_status);
+            scene_setup<T>(P, S, V, &s_status);
             const int status0 = s_status;
             if (status0 != ST_OK) {
-                // K_i not SPD: report, leave the state untouched (as the step is undefined)
+                // K_i not SPD: report, leave the state untouched (the step is undefined)
                 if (tid == 0) {
                     double *o = P.res + 6 * sc;
                     o[0] = o[1] = o[2] = __longlong_as_double(0x7ff8000000000000LL);
@@ -272,143 +412,203 @@ __global__ void __launch_bounds__(SUBADMM_THREADS) step_kernel(StepParams P)
             }
             // initial z, u = -lambda (cold: zeros; warm: the previous step's)
             for (int r = tid; r < S.nrow; r += blockDim.x)
-                LAM[r] = P.warm_prev ? P.lam[S.row_g0 + r] : 0.0;
+                LAM[r] = P.warm_prev ? (T)P.lam[S.row_g0 + r] : (T)0;
             for (int t = tid; t < S.nsr; t += blockDim.x) {
-                const double beta = BETA[T.sub[t]];
-                const double z = P.warm_prev ? P.z[S.sr_g0 + t] : 0.0;
-                const double l = P.warm_prev ? P.lam[S.row_g0 + T.row[t]] : 0.0;
+                if (V.mlen[t] == 0) continue;                 // padding side-row
+                const T beta = BT[t];
+                const T z = P.warm_prev ? (T)P.z[S.sr_g0 + t] : (T)0;
+                const T l = P.warm_prev ? (T)P.lam[S.row_g0 + V.row[t]] : (T)0;
                 Z[t] = z;
-                X[t] = 0.0;
+                ZO[t] = z;
+                X[t] = (T)0;
                 Y[t] = beta * z - l;           // y^0 = beta z^0 + u^0
                 Wv[0][t] = beta * z + l;       // w^0 = beta z^0 - u^0
             }
             __syncthreads();
 
             int par = 0, last_par = 0, iters = 0, conv = 0, status = ST_OK;
-            double th = INFINITY, rp = INFINITY, rd = INFINITY, rz = INFINITY;
-            for (int l = 0; l < P.max_iters; ++l) {
-                // v-step through the affine map, then y and the theta partial
-                const double *w = Wv[par];
-                double tpart = 0.0;
-                for (int t = tid; t < S.nsr; t += blockDim.x) {
-                    const double *Dr = sm + T.drow[t];
-                    const double *wb = w + T.wbase[t];
-                    const int m = T.mlen[t];
-                    double acc = sm[T.coff[t]];
-                    for (int s = 0; s < m; ++s) acc += Dr[s] * wb[s];
-                    const double ynew = BETA[T.sub[t]] * acc - LAM[T.row[t]];
-                    const double d = ynew - Y[t];
-                    tpart += d * d;
-                    Y[t] = ynew;
-                    X[t] = acc;
-                }
-                tpart = warp_sum(tpart);
-                if (lane == 0) red[l & 1][0][warp] = tpart;
-                __syncthreads();
-                th = 0.0;
-                for (int q = 0; q < SUBADMM_WARPS; ++q) th += red[l & 1][0][q];
-                last_par = par;
-                iters = l + 1;
-                if (P.stop_theta && l >= 1 && th < P.theta_th) { conv = 1; break; }
-                // z-step per constraint (Sec. III-C), u = -lambda, residual partials
-                double *wn = Wv[par ^ 1];
-                double rpp = 0.0, rzp = 0.0, rdp = 0.0;
-                for (int j = tid; j < S.ncon; j += blockDim.x) {
-                    const ConDesc &c = P.cons[S.con0 + j];
-                    double invb[SUBADMM_MAXS], bet[SUBADMM_MAXS];
-                    double s = 0.0;
-                    for (int si = 0; si < c.ns; ++si) {
-                        bet[si] = BETA[c.sub[si]];
-                        invb[si] = 1.0 / bet[si];
-                        s += invb[si];
-                    }
-                    double kk, al, mu;
-                    con_params(c, P.pool, P.h, kk, al, mu);
-                    double lamv[8];
-                    if (c.type == TYPE_CONTACT) {
-                        double qv[3];
-                        for (int r = 0; r < 3; ++r) {
-                            double q = 0.0;
-                            for (int si = 0; si < c.ns; ++si) q += Y[c.sr[si] + r] * invb[si];
-                            qv[r] = q + E[c.row0 + r];
+            double th = 0.0;
+            double tolc = P.tol;
+            U tolb = tol_bits(T(0), tolc > 0.0 ? tolc : 0.0);
+            int l = 0;
+            for (;;) {
+                for (; l < P.max_iters; ++l) {
+                    // v-step through the affine map x = c + D w; y = beta x - lambda
+                    const T *w = Wv[par];
+                    double tpart = 0.0;
+                    {
+                        constexpr int groups = SUBADMM_THREADS / SPLIT;
+                        const int g = tid / SPLIT, gl = tid - g * SPLIT;
+                        const int trips = (S.nsr + groups - 1) / groups;
+                        for (int k = 0; k < trips; ++k) {
+                            const int t = g + k * groups;
+                            const int m = t < S.nsr ? V.mlen[t] : 0;
+                            T acc = (T)0;
+                            if (m > 0) {
+                                const VT *Dr = reinterpret_cast<const VT *>(V.tb + V.drow[t]);
+                                const VT *wb = reinterpret_cast<const VT *>(w + V.wbase[t]);
+                                const int nv = (m + VN - 1) / VN;
+                                for (int c = gl; c < nv; c += SPLIT) acc = vdot(Dr[c], wb[c], acc);
+                            }
+#pragma unroll
+                            for (int o = SPLIT / 2; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                            if (m > 0 && gl == 0) {
+                                acc += V.tb[V.coff[t]];
+                                const T ynew = BT[t] * acc - LAM[V.row[t]];
+                                if (P.stop_theta) {
+                                    const double d = (double)ynew - (double)Y[t];
+                                    tpart += d * d;
+                                }
+                                YO[t] = Y[t];
+                                Y[t] = ynew;
+                                X[t] = acc;
+                            }
                         }
-                        const double ln = -qv[0] / s, l1 = -qv[1] / s, l2 = -qv[2] / s;
-                        if (ln <= 0.0) {
-                            lamv[0] = lamv[1] = lamv[2] = 0.0;
+                    }
+                    if (P.stop_theta) {
+                        tpart = warp_sum(tpart);
+                        if (lane == 0) red[l & 1][warp] = tpart;
+                    }
+                    __syncthreads();
+                    last_par = par;
+                    iters = l + 1;
+                    if (P.stop_theta) {
+                        th = 0.0;
+                        for (int q = 0; q < SUBADMM_WARPS; ++q) th += red[l & 1][q];
+                        if (l >= 1 && th < P.theta_th) { conv = 1; break; }
+                    }
+                    // z-step per item (Sec. III-C); u = -lambda; max(|x - z|, |dz|) as bits
+                    T *wn = Wv[par ^ 1];
+                    U mloc = 0;
+                    for (int i = tid; i < S.nitem; i += SUBADMM_THREADS) {
+                        const Item it = V.item[i];
+                        const int *ls = V.list + it.lo;
+                        if (it.type == TYPE_CONTACT) {
+                            T q0 = (T)0, q1 = (T)0, q2 = (T)0;
+                            for (int s = 0; s < it.ns; ++s) {
+                                const int t = ls[s];
+                                const T ib = INVB[t];
+                                q0 += Y[t] * ib; q1 += Y[t + 1] * ib; q2 += Y[t + 2] * ib;
+                            }
+                            const T is = INVS[it.row];
+                            const T ln = -(q0 + E[it.row]) * is;
+                            const T l1 = -(q1 + E[it.row + 1]) * is;
+                            const T l2 = -(q2 + E[it.row + 2]) * is;
+                            T lv[3];
+                            if (ln <= (T)0) {
+                                lv[0] = lv[1] = lv[2] = (T)0;
+                            } else {
+                                const T tn = sqrt(l1 * l1 + l2 * l2);
+                                const T lim = MU[it.row] * ln;
+                                lv[0] = ln;
+                                if (tn > lim) { const T f = lim / tn; lv[1] = l1 * f; lv[2] = l2 * f; }
+                                else { lv[1] = l1; lv[2] = l2; }
+                            }
+                            LAM[it.row] = lv[0]; LAM[it.row + 1] = lv[1]; LAM[it.row + 2] = lv[2];
+                            for (int s = 0; s < it.ns; ++s) {
+#pragma unroll
+                                for (int r = 0; r < 3; ++r) {
+                                    const int t = ls[s] + r;
+                                    const T yv = Y[t], zo = Z[t];
+                                    const T zn = (yv + lv[r]) * INVB[t];
+                                    mloc = umax(mloc, umax(rbits(fabs(X[t] - zn)), rbits(fabs(zn - zo))));
+                                    ZO[t] = zo;
+                                    Z[t] = zn;
+                                    wn[t] = yv + (T)2 * lv[r];
+                                }
+                            }
                         } else {
-                            const double tn = sqrt(l1 * l1 + l2 * l2);
-                            const double lim = mu * ln;
-                            lamv[0] = ln;
-                            if (tn > lim) { const double f = lim / tn; lamv[1] = l1 * f; lamv[2] = l2 * f; }
-                            else { lamv[1] = l1; lamv[2] = l2; }
-                        }
-                    } else {
-                        for (int r = 0; r < c.rows; ++r) {
-                            double q = 0.0;
-                            for (int si = 0; si < c.ns; ++si) q += Y[c.sr[si] + r] * invb[si];
-                            const double e = E[c.row0 + r];
-                            double lv;
-                            if (c.type == TYPE_EQUALITY) lv = -(q + e) / s;
-                            else if (c.type == TYPE_HARD) { lv = -(q + e) / s; lv = lv > 0.0 ? lv : 0.0; }
-                            else lv = -kk * (e + al * q) / (1.0 + s * al * kk);
-                            lamv[r] = lv;
-                        }
-                    }
-                    for (int r = 0; r < c.rows; ++r) LAM[c.row0 + r] = lamv[r];
-                    for (int si = 0; si < c.ns; ++si) {
-                        for (int r = 0; r < c.rows; ++r) {
-                            const int t = c.sr[si] + r;
-                            const double zn = (Y[t] + lamv[r]) / bet[si];
-                            const double dz = fabs(zn - Z[t]);
-                            rzp = nanmax(rzp, dz);
-                            rdp = nanmax(rdp, bet[si] * dz);
-                            rpp = nanmax(rpp, fabs(X[t] - zn));
-                            Z[t] = zn;
-                            wn[t] = bet[si] * zn + lamv[r];
+                            T q = (T)0;
+                            for (int s = 0; s < it.ns; ++s) q += Y[ls[s]] * INVB[ls[s]];
+                            const T e = E[it.row];
+                            T lv;
+                            if (it.type == TYPE_EQUALITY) lv = -(q + e) * INVS[it.row];
+                            else if (it.type == TYPE_HARD) { lv = -(q + e) * INVS[it.row]; lv = lv > (T)0 ? lv : (T)0; }
+                            else lv = -(e + AL[it.row] * q) * KF[it.row];
+                            LAM[it.row] = lv;
+                            for (int s = 0; s < it.ns; ++s) {
+                                const int t = ls[s];
+                                const T yv = Y[t], zo = Z[t];
+                                const T zn = (yv + lv) * INVB[t];
+                                mloc = umax(mloc, umax(rbits(fabs(X[t] - zn)), rbits(fabs(zn - zo))));
+                                ZO[t] = zo;
+                                Z[t] = zn;
+                                wn[t] = yv + (T)2 * lv;
+                            }
                         }
                     }
+                    mloc = warp_umax(mloc);
+                    if (lane == 0) ured[l & 1][warp] = mloc;
+                    __syncthreads();
+                    U mx = 0;
+#pragma unroll
+                    for (int q = 0; q < SUBADMM_WARPS; ++q) mx = umax(mx, ured[l & 1][q]);
+                    par ^= 1;
+                    if (mx >= inf_bits(T(0))) { status = ST_NAN; break; }
+                    if (!P.stop_theta && tolc > 0.0 && mx <= tolb) { conv = 1; break; }
                 }
-                rpp = warp_max(rpp);
-                rzp = warp_max(rzp);
-                rdp = warp_max(rdp);
-                if (lane == 0) {
-                    red[l & 1][1][warp] = rpp;
-                    red[l & 1][2][warp] = rzp;
-                    red[l & 1][3][warp] = rdp;
-                }
+                // h = g + W w of the last v-step (FP64)
+                form_h<T>(P, S, V, Wv[last_par]);
                 __syncthreads();
-                rp = 0.0; rz = 0.0; rd = 0.0;
-                for (int q = 0; q < SUBADMM_WARPS; ++q) {
-                    rp = nanmax(rp, red[l & 1][1][q]);
-                    rz = nanmax(rz, red[l & 1][2][q]);
-                    rd = nanmax(rd, red[l & 1][3][q]);
+                if (MIXED && conv && !P.stop_theta && status == ST_OK) {
+                    // FP64 check of the primal residual: x = J v = W^T h
+                    double part = 0.0;
+                    for (int t = tid; t < S.nsr; t += blockDim.x) {
+                        if (V.mlen[t] == 0) continue;
+                        const SubDesc &u = P.subs[S.sub0 + V.sub[t]];
+                        const int lr = t - u.sr0, n = u.n;
+                        const double *Wr = V.db + u.od_W + lr * n;
+                        const double *h = V.db + u.od_b + n;
+                        double x = 0.0;
+                        for (int p = 0; p < n; ++p) x += Wr[p] * h[p];
+                        part = nanmax(part, fabs(x - (double)Z[t]));
+                    }
+                    double d0 = 0.0, d2 = 0.0;
+                    block_reduce3(red, d0, part, d2);
+                    if (part > P.tol && l + 1 < P.max_iters) {
+                        // resume from the current iterate with a tighter FP32 test
+                        tolc *= 0.25;
+                        tolb = tol_bits(T(0), tolc);
+                        conv = 0;
+                        ++l;
+                        continue;
+                    }
+                    if (part > P.tol) conv = 0;
                 }
-                par ^= 1;
-                if (!isfinite(rp) || !isfinite(th) || !isfinite(rz)) { status = ST_NAN; break; }
-                if (!P.stop_theta && P.tol > 0.0 && rp <= P.tol && rz <= P.tol) { conv = 1; break; }
+                break;
+            }
+            // reported residuals of the last iteration: theta, r_p = max|x - z|,
+            // r_d = max beta |z^{l+1} - z^l|
+            double rp, rd;
+            {
+                double tp = 0.0, pp = 0.0, dd = 0.0;
+                for (int t = tid; t < S.nsr; t += blockDim.x) {
+                    if (V.mlen[t] == 0) continue;
+                    const double dy = (double)Y[t] - (double)YO[t];
+                    tp += dy * dy;
+                    pp = nanmax(pp, fabs((double)X[t] - (double)Z[t]));
+                    dd = nanmax(dd, (double)BT[t] * fabs((double)Z[t] - (double)ZO[t]));
+                }
+                block_reduce3(red, tp, pp, dd);
+                if (!P.stop_theta) th = tp;
+                rp = pp;
+                rd = dd;
             }
 
-            // v-hat of the last v-step: v = L^-T (g + W w)  (warp per subsystem)
+            // v-hat = L^-T h (warp per subsystem, in place in h)
             for (int i = warp; i < S.nsub; i += SUBADMM_WARPS) {
                 const SubDesc &u = P.subs[S.sub0 + i];
-                const int n = u.n, m = u.m;
-                const double *W = sm + u.o_W, *Lf = sm + u.o_L;
-                double *g = sm + u.o_b;
-                const double *w = Wv[last_par] + u.sr0;
-                for (int p = lane; p < n; p += 32) {
-                    double acc = g[p];
-                    for (int r = 0; r < m; ++r) acc += W[r * n + p] * w[r];
-                    g[p] = acc;
-                }
-                __syncwarp();
+                const int n = u.n;
+                const double *Lf = V.db + u.od_L;
+                double *h = V.db + u.od_b + n;
                 for (int p = n - 1; p >= 0; --p) {
-                    const double vp = g[p] / Lf[p * n + p];
+                    const double vp = h[p] / Lf[p * n + p];
                     __syncwarp();
-                    if (lane == 0) g[p] = vp;
-                    for (int q = lane; q < p; q += 32) g[q] -= Lf[p * n + q] * vp;
+                    if (lane == 0) h[p] = vp;
+                    for (int q = lane; q < p; q += 32) h[q] -= Lf[p * n + q] * vp;
                     __syncwarp();
                 }
-                for (int p = lane; p < n; p += 32) P.vhat[u.v_off + p] = g[p];
+                for (int p = lane; p < n; p += 32) P.vhat[u.v_off + p] = h[p];
             }
             __syncthreads();
             // state update of rigid bodies (Algorithm 1, last line)
@@ -416,11 +616,12 @@ __global__ void __launch_bounds__(SUBADMM_THREADS) step_kernel(StepParams P)
                 const SubDesc &u = P.subs[S.sub0 + i];
                 if (u.kind != KIND_RIGID) continue;
                 for (int k = lane; k < u.nb; k += 32)
-                    body_update(P.bodies + (size_t)(u.body0 + k) * SUBADMM_BODY, sm + u.o_b + 6 * k, P.h);
+                    body_update(P.bodies + (size_t)(u.body0 + k) * SUBADMM_BODY,
+                                V.db + u.od_b + u.n + 6 * k, P.h);
             }
             // warm-start state and reports
-            for (int r = tid; r < S.nrow; r += blockDim.x) P.lam[S.row_g0 + r] = LAM[r];
-            for (int t = tid; t < S.nsr; t += blockDim.x) P.z[S.sr_g0 + t] = Z[t];
+            for (int r = tid; r < S.nrow; r += blockDim.x) P.lam[S.row_g0 + r] = (double)LAM[r];
+            for (int t = tid; t < S.nsr; t += blockDim.x) P.z[S.sr_g0 + t] = (double)Z[t];
             if (tid == 0) {
                 double *o = P.res + 6 * sc;
                 o[0] = rp; o[1] = rd; o[2] = th; o[3] = (double)iters; o[4] = (double)conv;

@@ -57,6 +57,9 @@ struct sim_s {
     SceneDesc *d_scenes = nullptr;
     SubDesc *d_subs = nullptr;
     ConDesc *d_cons = nullptr;
+    Item *d_items = nullptr;
+    int *d_lists = nullptr;
+    int split = 1;                 // lanes per side-row in the v-step mat-vec
     double *d_pool = nullptr, *d_bodies = nullptr, *d_vhat = nullptr, *d_lam = nullptr;
     double *d_z = nullptr, *d_beta = nullptr, *d_res = nullptr, *d_stage = nullptr;
     long long *d_stats = nullptr;
@@ -124,6 +127,8 @@ __global__ void unpack_state(double *bodies, const double *in, long long nb)
 void free_device(sim_t s)
 {
     cudaFree(s->d_scenes); cudaFree(s->d_subs); cudaFree(s->d_cons); cudaFree(s->d_pool);
+    cudaFree(s->d_items); cudaFree(s->d_lists);
+    s->d_items = nullptr; s->d_lists = nullptr;
     cudaFree(s->d_bodies); cudaFree(s->d_vhat); cudaFree(s->d_lam); cudaFree(s->d_z);
     cudaFree(s->d_beta); cudaFree(s->d_res); cudaFree(s->d_stats); cudaFree(s->d_stage);
     s->d_scenes = nullptr; s->d_subs = nullptr; s->d_cons = nullptr; s->d_pool = nullptr;
@@ -176,6 +181,9 @@ int finalize(sim_t s)
 
     std::vector<double> pool;
     std::vector<double> bodies;
+    std::vector<Item> items;
+    std::vector<int> lists;
+    int max_nsr = 0;
     s->sdesc.assign(nsubs, SubDesc{});
     s->cdesc.assign(ncons, ConDesc{});
     s->scenes.assign(nscenes, SceneDesc{});
@@ -227,10 +235,14 @@ int finalize(sim_t s)
             c.ba = h.ba; c.bb = h.bb; c.gb_a = -1; c.gb_b = -1; c.side_b = -1;
         }
         S.nrow = row;
-        // side-rows, subsystem by subsystem so each subsystem's rows are contiguous
+        // side-rows, subsystem by subsystem so each subsystem's rows are contiguous; each
+        // subsystem's block starts on a 16-byte boundary of the iteration type (padding
+        // side-rows between blocks belong to no constraint and stay zero)
+        const int vn = s->opt.precision == SIM_MIXED ? 4 : 2;
         int sr = 0;
         for (int i = 0; i < S.nsub; ++i) {
             SubDesc &u = s->sdesc[S.sub0 + i];
+            sr = (sr + vn - 1) / vn * vn;
             u.sr0 = sr;
             for (int j = 0; j < S.ncon; ++j) {
                 ConDesc &c = s->cdesc[S.con0 + j];
@@ -238,7 +250,9 @@ int finalize(sim_t s)
                     if (c.sub[q] == i) { c.sr[q] = sr; sr += c.rows; }
             }
             u.m = sr - u.sr0;
+            u.mpad = (u.m + vn - 1) / vn * vn;
         }
+        sr = (sr + vn - 1) / vn * vn;
         S.nsr = sr;
         for (int j = 0; j < S.ncon; ++j) {
             const ConDesc &c = s->cdesc[S.con0 + j];
@@ -259,29 +273,64 @@ int finalize(sim_t s)
                 c.side_b = (h.sb == h.sa) ? 0 : 1;
             }
         }
-        // shared-memory layout (doubles, then ints)
-        int off = 0;
+        // z-step items: one per row of an equality / hard / soft constraint, one per contact
+        S.item_g0 = (int)items.size();
+        S.list_g0 = (int)lists.size();
+        for (int j = 0; j < S.ncon; ++j) {
+            const ConDesc &c = s->cdesc[S.con0 + j];
+            if (c.type == TYPE_CONTACT) {
+                items.push_back(Item{c.type, c.ns, c.row0, (int)lists.size() - S.list_g0});
+                for (int q = 0; q < c.ns; ++q) lists.push_back(c.sr[q]);
+            } else {
+                for (int r = 0; r < c.rows; ++r) {
+                    items.push_back(Item{c.type, c.ns, c.row0 + r, (int)lists.size() - S.list_g0});
+                    for (int q = 0; q < c.ns; ++q) lists.push_back(c.sr[q] + r);
+                }
+            }
+        }
+        S.nitem = (int)items.size() - S.item_g0;
+        S.nlist = (int)lists.size() - S.list_g0;
+        // shared-memory layout: doubles (factors), then T (iteration arrays), then ints.
+        // T offsets are whole 16-byte vectors so D rows and w segments load as vectors.
+        int od = 0, ot = 0;
+        auto tal = [&](int v) { return (v + vn - 1) / vn * vn; };
         for (int i = 0; i < S.nsub; ++i) {
             SubDesc &u = s->sdesc[S.sub0 + i];
             if (u.m > SUBADMM_MAXM)
                 return fail(s, SIM_EINVAL, "a subsystem has more constraint rows than the on-chip path holds");
-            u.o_W = off; off += u.m * u.n;
-            u.o_L = off; off += u.n * u.n;
-            u.o_D = off; off += u.m * u.m;
-            u.o_b = off; off += u.n;
-            u.o_c = off; off += u.m;
+            u.od_W = od; od += u.m * u.n;
+            u.od_L = od; od += u.n * u.n;
+            u.od_b = od; od += 2 * u.n;          // g, then h = g + W w
+            u.ot_D = ot; ot = tal(ot + u.m * u.mpad);
+            u.ot_c = ot; ot = tal(ot + u.m);
         }
-        S.o_x = off; off += S.nsr;
-        S.o_y = off; off += S.nsr;
-        S.o_z = off; off += S.nsr;
-        S.o_w0 = off; off += S.nsr;
-        S.o_w1 = off; off += S.nsr;
-        S.o_lam = off; off += S.nrow;
-        S.o_e = off; off += S.nrow;
-        S.o_beta = off; off += S.nsub;
-        S.o_int = off;
-        S.smem_bytes = off * (int)sizeof(double) + 6 * S.nsr * (int)sizeof(int);
+        S.od_beta = od; od += S.nsub;
+        // per-side-row arrays are contiguous from ot_x up to ot_lam (zeroed together)
+        S.ot_x = ot; ot = tal(ot + S.nsr);
+        S.ot_y = ot; ot = tal(ot + S.nsr);
+        S.ot_z = ot; ot = tal(ot + S.nsr);
+        S.ot_yo = ot; ot = tal(ot + S.nsr);
+        S.ot_zo = ot; ot = tal(ot + S.nsr);
+        S.ot_w0 = ot; ot = tal(ot + S.nsr);
+        S.ot_w1 = ot; ot = tal(ot + S.nsr);
+        S.ot_invb = ot; ot = tal(ot + S.nsr);
+        S.ot_b = ot; ot = tal(ot + S.nsr);
+        S.ot_lam = ot; ot += S.nrow;
+        S.ot_e = ot; ot += S.nrow;
+        S.ot_invs = ot; ot += S.nrow;
+        S.ot_kf = ot; ot += S.nrow;
+        S.ot_al = ot; ot += S.nrow;
+        S.ot_mu = ot; ot += S.nrow;
+        const int tsize = s->opt.precision == SIM_MIXED ? 4 : 8;
+        const long long t_base = ((long long)od * 8 + 15) / 16 * 16;
+        const long long i_base = (t_base + (long long)ot * tsize + 15) / 16 * 16;
+        const long long bytes = i_base + 4LL * (6LL * S.nsr + 4LL * S.nitem + S.nlist);
+        if (bytes > (1LL << 30)) return fail(s, SIM_EINVAL, "scene too large");
+        S.t_base = (int)t_base;
+        S.i_base = (int)i_base;
+        S.smem_bytes = (int)bytes;
         max_smem = std::max(max_smem, S.smem_bytes);
+        max_nsr = std::max(max_nsr, S.nsr);
         sr_g += S.nsr;
         rows_g += S.nrow;
     }
@@ -290,6 +339,7 @@ int finalize(sim_t s)
     int dev_max = 0;
     CK(cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->opt.device), "attribute");
     const int static_smem = (int)(sizeof(double) * 2 * 4 * SUBADMM_WARPS + 64);
+    // (checked again at launch against the kernel's own static shared memory)
     if (max_smem + static_smem > dev_max) {
         char buf[256];
         snprintf(buf, sizeof buf, "a scene needs %d bytes of shared memory; the on-chip path holds %d",
@@ -304,6 +354,10 @@ int finalize(sim_t s)
     if ((rc = upload(s, &s->d_subs, s->sdesc, "subsystems"))) return rc;
     if ((rc = upload(s, &s->d_cons, s->cdesc, "interfaces"))) return rc;
     if ((rc = upload(s, &s->d_pool, pool, "pool"))) return rc;
+    if ((rc = upload(s, &s->d_items, items, "items"))) return rc;
+    if ((rc = upload(s, &s->d_lists, lists, "lists"))) return rc;
+    s->split = 1;
+    while (s->split < 4 && 2 * s->split * std::max(max_nsr, 1) <= SUBADMM_THREADS) s->split *= 2;
     if ((rc = upload(s, &s->d_bodies, bodies, "bodies"))) return rc;
     s->pool_size = pool.size();
     if ((rc = zeros(s, &s->d_vhat, (size_t)dof, "vhat"))) return rc;
@@ -317,8 +371,6 @@ int finalize(sim_t s)
         if (e != cudaSuccess) return fail(s, SIM_ENOMEM, "cudaMalloc stats");
         CK(cudaMemsetAsync(s->d_stats, 0, std::max(1, 4 * nscenes) * sizeof(long long), s->stream), "memset stats");
     }
-    CK(cudaFuncSetAttribute(subadmm::step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                            std::max(max_smem, 1)), "shared memory attribute");
     s->finalized = true;
     return SIM_OK;
 }
@@ -385,7 +437,7 @@ int sim_create(const sim_options *opt, sim_t *out)
     *out = nullptr;
     sim_options o;
     if (opt) o = *opt; else sim_default_options(&o);
-    if (!(o.h > 0.0) || o.max_iters < 1 || o.precision != SIM_FP64 ||
+    if (!(o.h > 0.0) || o.max_iters < 1 || (o.precision != SIM_FP64 && o.precision != SIM_MIXED) ||
         (o.beta_mode != SIM_BETA_TRACE && o.beta_mode != SIM_BETA_FIXED) ||
         (o.beta_mode == SIM_BETA_FIXED && !(o.rho > 0.0)) ||
         (o.warm != SIM_WARM_COLD && o.warm != SIM_WARM_PREV) ||
@@ -537,10 +589,16 @@ int sim_step(sim_t s, int n_steps)
     P.stop_theta = s->opt.stop == SIM_STOP_THETA;
     P.max_iters = s->opt.max_iters;
     CK(cudaSetDevice(s->opt.device), "cudaSetDevice");
+    P.items = s->d_items;
+    P.lists = s->d_lists;
+    const bool mixed = s->opt.precision == SIM_MIXED;
+    void (*kern)(StepParams) = nullptr;
+    if (mixed) kern = s->split == 4 ? subadmm::step_kernel<float, 4> : s->split == 2 ? subadmm::step_kernel<float, 2> : subadmm::step_kernel<float, 1>;
+    else kern = s->split == 4 ? subadmm::step_kernel<double, 4> : s->split == 2 ? subadmm::step_kernel<double, 2> : subadmm::step_kernel<double, 1>;
     // the attribute is per function, shared by every simulation of the process
-    CK(cudaFuncSetAttribute(subadmm::step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                            std::max(s->max_smem, 1)), "shared memory attribute");
-    subadmm::step_kernel<<<s->nscenes, SUBADMM_THREADS, s->max_smem, s->stream>>>(P);
+    CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, std::max(s->max_smem, 1)),
+       "shared memory attribute");
+    kern<<<s->nscenes, SUBADMM_THREADS, s->max_smem, s->stream>>>(P);
     CK(cudaGetLastError(), "step kernel launch");
     return SIM_OK;
 }

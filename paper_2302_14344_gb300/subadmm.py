@@ -24,7 +24,7 @@ SIM_IF_BALL, SIM_IF_REVOLUTE, SIM_IF_ANGLE_PD, SIM_IF_PLANE_CONTACT = 4, 5, 6, 7
 SIM_BETA_TRACE, SIM_BETA_FIXED = 0, 1
 SIM_WARM_COLD, SIM_WARM_PREV = 0, 1
 SIM_STOP_PRIMAL, SIM_STOP_THETA = 0, 1
-SIM_FP64 = 0
+SIM_FP64, SIM_MIXED = 0, 1
 SIM_GET_VHAT, SIM_GET_LAMBDA, SIM_GET_BODIES, SIM_GET_BETA, SIM_GET_Z = 0, 1, 2, 3, 4
 
 # exported symbols of include/subadmm.h
@@ -212,7 +212,7 @@ _KIND = {0: SIM_IF_EQUALITY, 1: SIM_IF_HARD, 2: SIM_IF_SOFT, 3: SIM_IF_CONTACT}
 _MODEL = {1: SIM_IF_BALL, 2: SIM_IF_REVOLUTE, 3: SIM_IF_ANGLE_PD, 4: SIM_IF_PLANE_CONTACT}
 
 
-def options_from(o, stream: int = 0, device: int = 0) -> sim_options:
+def options_from(o, stream: int = 0, device: int = 0, precision: int = SIM_FP64) -> sim_options:
     """sim_options from an object with the fields of ``scenegen.Options``."""
     opt = sim_default_options()
     opt.h = o.h
@@ -226,6 +226,7 @@ def options_from(o, stream: int = 0, device: int = 0) -> sim_options:
     opt.tol_primal = o.tol_primal
     opt.theta_th = o.theta_th
     opt.max_iters = int(o.max_iters)
+    opt.precision = precision
     opt.device = device
     opt.stream = stream or None
     return opt
@@ -237,8 +238,8 @@ class Simulation:
     ``problem`` has ``scenes`` (each with ``subs`` and ``ifs``) and ``options``, shaped like
     ``scenegen.Problem``.  Subsystem and interface ids are assigned in scene order."""
 
-    def __init__(self, problem, stream: int = 0, device: int = 0):
-        self.h = sim_create(options_from(problem.options, stream, device))
+    def __init__(self, problem, stream: int = 0, device: int = 0, precision: int = SIM_FP64):
+        self.h = sim_create(options_from(problem.options, stream, device, precision))
         self.sub_ids = []     # per scene: list of ids
         self.if_ids = []
         self.sub_n = []
