@@ -171,6 +171,16 @@ int sim_sizes(sim_t s, long long out[8]);
  * out[3] scene-steps counted. */
 int sim_iteration_stats(sim_t s, long long out[4]);
 
+/* Device-side phase tracer.  Reads the counters accumulated since the last call into out
+ * (if out is not NULL; zeros when tracing was off), then turns tracing on (enable != 0, the
+ * counters restart at zero) or off.  Counters, summed over scenes, are SM clock cycles seen
+ * by the first thread of each scene's block: out[0] assembly and start of the iterations,
+ * out[1] beta and factorisation, out[2] v-steps (Eq. admm-1i) including their barrier,
+ * out[3] z-steps and u-steps (Eqs. admm-2j, admm-3) including their barrier, out[4] exit
+ * checks and residuals, out[5] v-hat recovery and state update; out[6] iterations,
+ * out[7] scene-steps.  Tracing adds a few clock reads per iteration. */
+int sim_phase_trace(sim_t s, int enable, long long out[8]);
+
 /* Blocks until every call enqueued on s's stream has finished. */
 int sim_sync(sim_t s);
 

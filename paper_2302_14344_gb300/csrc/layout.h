@@ -17,6 +17,9 @@ enum { SRC_EQUALITY = 0, SRC_HARD = 1, SRC_SOFT = 2, SRC_CONTACT = 3, SRC_BALL =
 enum { TYPE_EQUALITY = 0, TYPE_HARD = 1, TYPE_SOFT = 2, TYPE_CONTACT = 3 };
 // subsystem kinds
 enum { KIND_GENERIC = 0, KIND_RIGID = 1 };
+// phase counters (clock64 cycles seen by thread 0 of a scene's block)
+enum { PHASE_ASSEMBLE = 0, PHASE_FACTOR = 1, PHASE_VSTEP = 2, PHASE_ZSTEP = 3, PHASE_EXIT = 4,
+       PHASE_RECOVER = 5, PHASE_ITERS = 6, PHASE_STEPS = 7 };
 // per-scene status words
 enum { ST_OK = 0, ST_NOTSPD = -3, ST_NAN = -4 };
 
@@ -82,6 +85,7 @@ struct StepParams {
     double *beta;          // per subsystem
     double *res;           // 6 per scene
     long long *stats;      // 4 per scene: sum iters, max iters, not converged, steps
+    long long *phase;      // 8 per scene (or null): SM clock cycles per phase, see PHASE_*
     int nscenes;
     int n_steps;
     double h, g0, g1, g2, gamma, rho, tol, theta_th;

@@ -118,9 +118,27 @@ __device__ __forceinline__ void con_params(const ConDesc &c, const double *pool,
 }
 
 // assemble .. factor .. map, and the per-step constants of the z-step
+// Phase tracer: thread 0 of a scene's block adds clock64 deltas to P.phase when enabled.
+struct PhaseClock {
+    long long *acc;
+    long long t;
+    __device__ __forceinline__ PhaseClock(long long *a) : acc(threadIdx.x == 0 ? a : nullptr), t(0)
+    {
+        if (acc) t = clock64();
+    }
+    __device__ __forceinline__ void mark(int phase)
+    {
+        if (acc) {
+            const long long n = clock64();
+            acc[phase] += n - t;
+            t = n;
+        }
+    }
+};
+
 template <typename T>
 __device__ void scene_setup(const StepParams &P, const SceneDesc &S, const View<T> &V,
-                            int *s_status)
+                            int *s_status, PhaseClock &pc)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     double *db = V.db;
@@ -191,6 +209,7 @@ __device__ void scene_setup(const StepParams &P, const SceneDesc &S, const View<
         }
     }
     __syncthreads();
+    pc.mark(PHASE_ASSEMBLE);
     // per subsystem (one warp each): beta, K += beta J^T J, Cholesky, W, g, D, c
     for (int i = warp; i < S.nsub; i += SUBADMM_WARPS) {
         const SubDesc &u = P.subs[S.sub0 + i];
@@ -273,6 +292,7 @@ __device__ void scene_setup(const StepParams &P, const SceneDesc &S, const View<
     T *INVS = tb + S.ot_invs, *KF = tb + S.ot_kf, *AL = tb + S.ot_al, *MU = tb + S.ot_mu;
     T *INVB = tb + S.ot_invb, *BT = tb + S.ot_b;
     const double *BETA = db + S.od_beta;
+    pc.mark(PHASE_FACTOR);
     for (int j = tid; j < S.ncon; j += blockDim.x) {
         const ConDesc &c = P.cons[S.con0 + j];
         double s = 0.0;
@@ -398,7 +418,8 @@ __global__ void __launch_bounds__(SUBADMM_THREADS) step_kernel(StepParams P)
         for (int step = 0; step < P.n_steps; ++step) {
             if (tid == 0) s_status = ST_OK;
             __syncthreads();
-            scene_setup<T>(P, S, V, &s_status);
+            PhaseClock pc(P.phase ? P.phase + 8 * sc : nullptr);
+            scene_setup<T>(P, S, V, &s_status, pc);
             const int status0 = s_status;
             if (status0 != ST_OK) {
                 // K_i not SPD: report, leave the state untouched (the step is undefined)
@@ -425,11 +446,13 @@ __global__ void __launch_bounds__(SUBADMM_THREADS) step_kernel(StepParams P)
                 Wv[0][t] = beta * z + l;       // w^0 = beta z^0 - u^0
             }
             __syncthreads();
+            pc.mark(PHASE_ASSEMBLE);
 
             int par = 0, last_par = 0, iters = 0, conv = 0, status = ST_OK;
             double th = 0.0;
             double tolc = P.tol;
             U tolb = tol_bits(T(0), tolc > 0.0 ? tolc : 0.0);
+            const bool primal_stop = !P.stop_theta && P.tol > 0.0;
             int l = 0;
             for (;;) {
                 for (; l < P.max_iters; ++l) {
@@ -470,6 +493,7 @@ __global__ void __launch_bounds__(SUBADMM_THREADS) step_kernel(StepParams P)
                         if (lane == 0) red[l & 1][warp] = tpart;
                     }
                     __syncthreads();
+                    pc.mark(PHASE_VSTEP);
                     last_par = par;
                     iters = l + 1;
                     if (P.stop_theta) {
@@ -544,8 +568,9 @@ __global__ void __launch_bounds__(SUBADMM_THREADS) step_kernel(StepParams P)
 #pragma unroll
                     for (int q = 0; q < SUBADMM_WARPS; ++q) mx = umax(mx, ured[l & 1][q]);
                     par ^= 1;
+                    pc.mark(PHASE_ZSTEP);
                     if (mx >= inf_bits(T(0))) { status = ST_NAN; break; }
-                    if (!P.stop_theta && tolc > 0.0 && mx <= tolb) { conv = 1; break; }
+                    if (primal_stop && mx <= tolb) { conv = 1; break; }
                 }
                 // h = g + W w of the last v-step (FP64)
                 form_h<T>(P, S, V, Wv[last_par]);
@@ -594,6 +619,7 @@ __global__ void __launch_bounds__(SUBADMM_THREADS) step_kernel(StepParams P)
                 rp = pp;
                 rd = dd;
             }
+            pc.mark(PHASE_EXIT);
 
             // v-hat = L^-T h (warp per subsystem, in place in h)
             for (int i = warp; i < S.nsub; i += SUBADMM_WARPS) {
@@ -619,6 +645,9 @@ __global__ void __launch_bounds__(SUBADMM_THREADS) step_kernel(StepParams P)
                     body_update(P.bodies + (size_t)(u.body0 + k) * SUBADMM_BODY,
                                 V.db + u.od_b + u.n + 6 * k, P.h);
             }
+            __syncthreads();
+            pc.mark(PHASE_RECOVER);
+            if (pc.acc) { pc.acc[PHASE_ITERS] += iters; pc.acc[PHASE_STEPS] += 1; }
             // warm-start state and reports
             for (int r = tid; r < S.nrow; r += blockDim.x) P.lam[S.row_g0 + r] = (double)LAM[r];
             for (int t = tid; t < S.nsr; t += blockDim.x) P.z[S.sr_g0 + t] = (double)Z[t];

@@ -63,6 +63,7 @@ struct sim_s {
     double *d_pool = nullptr, *d_bodies = nullptr, *d_vhat = nullptr, *d_lam = nullptr;
     double *d_z = nullptr, *d_beta = nullptr, *d_res = nullptr, *d_stage = nullptr;
     long long *d_stats = nullptr;
+    long long *d_phase = nullptr;  // phase tracer counters (8 per scene) when enabled
     size_t pool_size = 0;
 };
 
@@ -131,6 +132,8 @@ void free_device(sim_t s)
     s->d_items = nullptr; s->d_lists = nullptr;
     cudaFree(s->d_bodies); cudaFree(s->d_vhat); cudaFree(s->d_lam); cudaFree(s->d_z);
     cudaFree(s->d_beta); cudaFree(s->d_res); cudaFree(s->d_stats); cudaFree(s->d_stage);
+    cudaFree(s->d_phase);
+    s->d_phase = nullptr;
     s->d_scenes = nullptr; s->d_subs = nullptr; s->d_cons = nullptr; s->d_pool = nullptr;
     s->d_bodies = nullptr; s->d_vhat = nullptr; s->d_lam = nullptr; s->d_z = nullptr;
     s->d_beta = nullptr; s->d_res = nullptr; s->d_stats = nullptr; s->d_stage = nullptr;
@@ -578,7 +581,7 @@ int sim_step(sim_t s, int n_steps)
     StepParams P;
     P.scenes = s->d_scenes; P.subs = s->d_subs; P.cons = s->d_cons; P.pool = s->d_pool;
     P.bodies = s->d_bodies; P.vhat = s->d_vhat; P.lam = s->d_lam; P.z = s->d_z;
-    P.beta = s->d_beta; P.res = s->d_res; P.stats = s->d_stats;
+    P.beta = s->d_beta; P.res = s->d_res; P.stats = s->d_stats; P.phase = s->d_phase;
     P.nscenes = s->nscenes;
     P.n_steps = n_steps;
     P.h = s->opt.h; P.g0 = s->opt.gravity[0]; P.g1 = s->opt.gravity[1]; P.g2 = s->opt.gravity[2];
@@ -718,6 +721,36 @@ int sim_iteration_stats(sim_t s, long long out[4])
         out[3] += st[4 * k + 3];
     }
     CK(cudaMemset(s->d_stats, 0, sizeof(long long) * 4 * s->nscenes), "stats clear");
+    return SIM_OK;
+}
+
+int sim_phase_trace(sim_t s, int enable, long long out[8])
+{
+    if (!s) return SIM_EINVAL;
+    int rc = finalize(s);
+    if (rc) return rc;
+    const size_t bytes = sizeof(long long) * 8 * std::max(1, s->nscenes);
+    if (out) {
+        for (int k = 0; k < 8; ++k) out[k] = 0;
+        if (s->d_phase) {
+            CK(cudaStreamSynchronize(s->stream), "stream synchronize");
+            std::vector<long long> v((size_t)8 * std::max(1, s->nscenes));
+            CK(cudaMemcpy(v.data(), s->d_phase, bytes, cudaMemcpyDeviceToHost), "phase trace");
+            for (int sc = 0; sc < s->nscenes; ++sc)
+                for (int k = 0; k < 8; ++k) out[k] += v[(size_t)8 * sc + k];
+        }
+    }
+    if (enable && !s->d_phase) {
+        cudaError_t e = cudaMalloc((void **)&s->d_phase, bytes);
+        if (e != cudaSuccess) return fail(s, SIM_ENOMEM, "cudaMalloc phase trace");
+    }
+    if (enable) {
+        CK(cudaMemsetAsync(s->d_phase, 0, bytes, s->stream), "phase trace clear");
+    } else if (s->d_phase) {
+        CK(cudaStreamSynchronize(s->stream), "stream synchronize");
+        cudaFree(s->d_phase);
+        s->d_phase = nullptr;
+    }
     return SIM_OK;
 }
 

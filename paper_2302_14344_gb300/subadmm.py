@@ -30,8 +30,8 @@ SIM_GET_VHAT, SIM_GET_LAMBDA, SIM_GET_BODIES, SIM_GET_BETA, SIM_GET_Z = 0, 1, 2,
 # exported symbols of include/subadmm.h
 EXPORTS = ("sim_default_options", "sim_create", "sim_destroy", "sim_add_subsystem",
            "sim_add_interface", "sim_set_generic", "sim_step", "sim_residuals", "sim_get",
-           "sim_read_state", "sim_write_state", "sim_sizes", "sim_iteration_stats", "sim_sync",
-           "sim_last_error")
+           "sim_read_state", "sim_write_state", "sim_sizes", "sim_iteration_stats",
+           "sim_phase_trace", "sim_sync", "sim_last_error")
 
 
 class sim_options(C.Structure):
@@ -87,6 +87,7 @@ def load(build_if_missing: bool = True):
             "sim_write_state": (C.c_int, [VP, VP]),
             "sim_sizes": (C.c_int, [VP, PL]),
             "sim_iteration_stats": (C.c_int, [VP, PL]),
+            "sim_phase_trace": (C.c_int, [VP, C.c_int, PL]),
             "sim_sync": (C.c_int, [VP]),
             "sim_last_error": (C.c_char_p, [VP]),
         }
@@ -195,6 +196,18 @@ def sim_iteration_stats(h) -> dict:
     _check(h, load().sim_iteration_stats(h, out))
     return dict(total_iters=int(out[0]), max_iters=int(out[1]), not_converged=int(out[2]),
                 scene_steps=int(out[3]))
+
+
+PHASES = ("assemble", "factor", "v_step", "z_step", "exit", "recover", "iterations",
+          "scene_steps")
+
+
+def sim_phase_trace(h, enable: bool) -> dict:
+    """Counters since the last call (cycles per phase, iterations, scene-steps), then turn
+    the device phase tracer on or off."""
+    out = (C.c_longlong * 8)()
+    _check(h, load().sim_phase_trace(h, 1 if enable else 0, out))
+    return {k: int(v) for k, v in zip(PHASES, out)}
 
 
 def sim_sync(h) -> None:

@@ -319,3 +319,15 @@ def test_mixed_fixed_iterations_close_to_oracle(sa, capsys):
         print(f"\n[mixed vs FP64 oracle, chain 3 x 100 it] state rel err {e:.3e}, "
               f"v-hat rel err {ev:.3e}")
     assert e < 1e-6 and ev < 1e-4
+
+
+def test_phase_trace_counts_match_iteration_stats(sa):
+    p = sg.robots(3, n_robots=4, tol_primal=1e-6, max_iters=1000)
+    sim = sa.Simulation(p, precision=sa.SIM_MIXED)
+    sa.sim_phase_trace(sim.h, True)
+    sim.iteration_stats()
+    sim.step(3)
+    tr = sa.sim_phase_trace(sim.h, False)
+    st = sim.iteration_stats()
+    assert tr["iterations"] == st["total_iters"] and tr["scene_steps"] == 12
+    assert all(tr[k] > 0 for k in ("assemble", "factor", "v_step", "z_step", "exit", "recover"))
