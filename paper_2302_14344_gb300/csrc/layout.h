@@ -32,6 +32,7 @@ struct SceneDesc {
     int nsr, nrow;         // side-rows and rows of the scene
     int nitem, nlist;      // projection items (a row, or a whole contact) and their side lists
     int item_g0, list_g0;  // global offsets of the scene's item / list tables
+    int nasm, asm_g0;      // assembly slots (constraint indices grouped by kind, -1 = idle)
     int sr_g0, row_g0;     // global offset of the scene's side-rows / rows (z, lambda state)
     // double region
     int od_beta;
@@ -49,8 +50,10 @@ struct SubDesc {
     int local;             // index inside its scene
     int body0, nb;         // first global body, body count (rigid)
     int gen_off;           // pool offset of A (n*n) then b (n) (generic)
-    int od_W, od_L, od_b;  // double region: W (m x n), L (n x n), b / g / v (n)
-    int ot_D, ot_c;        // T region: D (m x m), c (m)
+    int od_J, od_L, od_b;  // double region: J_ci rows (m x n), K then its factor L (n x n), b (n)
+    int od_v, od_id;       // double region: right-hand side then v-hat (n), 1 / L_pp (n)
+    int ot_L, ot_W, ot_g;  // T region: L (n x n, 1/L_pp on the diagonal), W rows (m x n), g (n)
+    int ot_D, ot_c;        // T region: D (m x mpad), c (m)
     int v_off;             // global offset of v-hat
 };
 
@@ -77,6 +80,7 @@ struct StepParams {
     const ConDesc *cons;
     const Item *items;
     const int *lists;
+    const int *asm_order;  // per scene: constraint index of each assembly slot
     const double *pool;    // constant data and generic A, b
     double *bodies;        // 17 doubles per body (state in and out)
     double *vhat;          // per DOF

@@ -4,14 +4,14 @@
 // Per step and scene:
 //   assemble   A_i, b_i, J_ci, e (rigid model or generic blocks)           (Eq. sdyn, Sec. II-A)
 //   beta_i     Tr(A_i)/Tr(J_ci^T J_ci) or rho                               (Sec. III-D)
-//   factor     K_i = A_i + beta_i J_ci^T J_ci = L_i L_i^T                   (Algorithm 1, factorise)
+//   factor     K_i = A_i + beta_i J_ci^T J_ci = L_i L_i^T in FP64          (Algorithm 1, factorise)
 //   map        W_i = L_i^-1 J_ci^T, g_i = L_i^-1 b_i,
 //              D_i = W_i^T W_i = J_ci K_i^-1 J_ci^T, c_i = W_i^T g_i = J_ci K_i^-1 b_i
 //   iterate    x_i = c_i + D_i (beta_i z_i - u_i)                           (Eq. admm-1i, x = J v)
-//              y_i = beta_i x_i + u_i ; theta                               (Eq. surrogate, residual)
+//              y_i = beta_i x_i + u_i                                       (Eq. surrogate)
 //              lambda_j by type, beta_i z_ij = y_ij + lambda_j              (Eq. admm-2j)
 //              u_i = -lambda (the u-step of Eq. admm-3, simplified by Eq. surrogate)
-//   recover    v_i = L_i^-T (g_i + W_i (beta_i z_i - u_i)) for the last iterate (Eq. admm-1i)
+//   recover    v_i = K_i^-1 (b_i + J_ci^T (beta_i z_i - u_i)) in FP64 for the last v-step
 //   update     rigid state from v-hat                                       (Eq. ddyn)
 //
 // The v-step is evaluated through the per-step affine map x = c + D w instead of two
@@ -20,11 +20,16 @@
 // The u-step uses u^{l+1} = y^{l+1} - beta z^{l+1} = -lambda^{l+1} (Eq. admm-3 with
 // Eq. surrogate), so each row keeps one lambda shared by its sides and w = y + 2 lambda.
 //
-// T is the iteration type.  T = double: every step in FP64.  T = float (mixed form): the
-// setup (assembly, beta, factor, W, g) stays FP64, D and c are rounded to FP32 for the
-// iterations, and when the FP32 stop test passes the primal residual is re-evaluated in
-// FP64 (x = W^T (g + W w)); if that misses the tolerance the iterations resume with a
-// tighter FP32 test.  v-hat is always recovered in FP64.
+// T is the iteration type.  T = double: the map and the iterations in FP64.  T = float (the
+// mixed form): assembly, beta, K and its Cholesky factor stay FP64; W, g, D, c are formed
+// in FP32 from the rounded factor and the iterations run in FP32.  When the FP32 stop test
+// passes, v-hat is recovered in FP64 and the primal residual re-evaluated as
+// max |J v-hat - z| in FP64; if that misses the tolerance, c is corrected by the FP64 - FP32
+// difference of x at the current iterate (iterative refinement) and the iterations resume.
+//
+// On GB300 an FP64 warp instruction costs about 64 issue cycles of a sub-partition however
+// few lanes are active, so FP64 work is kept out of the loop of the mixed form and the loop
+// keeps each thread's coefficients, y and z in registers for the whole step.
 #pragma once
 #include "layout.h"
 #include "rigid_model.cuh"
@@ -46,6 +51,77 @@ __device__ __forceinline__ double warp_max(double v)
     for (int o = 16; o; o >>= 1) v = nanmax(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
 }
+
+// 16-byte vectors of the iteration type and residual bit patterns.  Residuals are
+// non-negative, so their IEEE bit patterns order like their values and a NaN (sign bit
+// cleared by fabs) orders above +inf: maxima reduce on the integer pipe.
+template <typename T> struct VecOf;
+template <> struct VecOf<float> { using V = float4; using U = unsigned; static constexpr int N = 4; };
+template <> struct VecOf<double> { using V = double2; using U = unsigned long long; static constexpr int N = 2; };
+
+__device__ __forceinline__ float vdot(const float4 a, const float4 b, float acc)
+{
+    acc = fmaf(a.x, b.x, acc); acc = fmaf(a.y, b.y, acc);
+    acc = fmaf(a.z, b.z, acc); acc = fmaf(a.w, b.w, acc);
+    return acc;
+}
+__device__ __forceinline__ double vdot(const double2 a, const double2 b, double acc)
+{
+    acc = fma(a.x, b.x, acc); acc = fma(a.y, b.y, acc);
+    return acc;
+}
+__device__ __forceinline__ unsigned rbits(float v) { return __float_as_uint(v); }
+__device__ __forceinline__ unsigned long long rbits(double v) { return (unsigned long long)__double_as_longlong(v); }
+__device__ __forceinline__ unsigned umax(unsigned a, unsigned b) { return a > b ? a : b; }
+__device__ __forceinline__ unsigned long long umax(unsigned long long a, unsigned long long b) { return a > b ? a : b; }
+__device__ __forceinline__ unsigned warp_umax(unsigned v) { return __reduce_max_sync(0xffffffffu, v); }
+__device__ __forceinline__ unsigned long long warp_umax(unsigned long long v)
+{
+    const unsigned hi = (unsigned)(v >> 32), lo = (unsigned)v;
+    const unsigned mh = __reduce_max_sync(0xffffffffu, hi);
+    const unsigned ml = __reduce_max_sync(0xffffffffu, hi == mh ? lo : 0u);
+    return ((unsigned long long)mh << 32) | ml;
+}
+__device__ __forceinline__ unsigned tol_bits(float, double tol) { return __float_as_uint(__double2float_rd(tol)); }
+__device__ __forceinline__ unsigned long long tol_bits(double, double tol) { return rbits(tol); }
+__device__ __forceinline__ unsigned inf_bits(float) { return 0x7f800000u; }
+__device__ __forceinline__ unsigned long long inf_bits(double) { return 0x7ff0000000000000ull; }
+__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
+
+// Sum (a) and maxima (b, c) of three per-thread doubles over the block.
+__device__ __forceinline__ void block_reduce3(double (*red)[SUBADMM_WARPS], double &a, double &b,
+                                              double &c)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    a = warp_sum(a); b = warp_max(b); c = warp_max(c);
+    __syncthreads();
+    if (lane == 0) { red[0][warp] = a; red[1][warp] = b; red[2][warp] = c; }
+    __syncthreads();
+    a = 0.0; b = 0.0; c = 0.0;
+    for (int q = 0; q < SUBADMM_WARPS; ++q) {
+        a += red[0][q]; b = nanmax(b, red[1][q]); c = nanmax(c, red[2][q]);
+    }
+    __syncthreads();
+}
+
+// Phase tracer: thread 0 of a scene's block adds clock64 deltas to P.phase when enabled.
+struct PhaseClock {
+    long long *acc;
+    long long t;
+    __device__ __forceinline__ PhaseClock(long long *a) : acc(threadIdx.x == 0 ? a : nullptr), t(0)
+    {
+        if (acc) t = clock64();
+    }
+    __device__ __forceinline__ void mark(int phase)
+    {
+        if (acc) {
+            const long long n = clock64();
+            acc[phase] += n - t;
+            t = n;
+        }
+    }
+};
 
 // shared-memory views of one scene
 template <typename T>
@@ -117,25 +193,16 @@ __device__ __forceinline__ void con_params(const ConDesc &c, const double *pool,
     }
 }
 
-// assemble .. factor .. map, and the per-step constants of the z-step
-// Phase tracer: thread 0 of a scene's block adds clock64 deltas to P.phase when enabled.
-struct PhaseClock {
-    long long *acc;
-    long long t;
-    __device__ __forceinline__ PhaseClock(long long *a) : acc(threadIdx.x == 0 ? a : nullptr), t(0)
-    {
-        if (acc) t = clock64();
-    }
-    __device__ __forceinline__ void mark(int phase)
-    {
-        if (acc) {
-            const long long n = clock64();
-            acc[phase] += n - t;
-            t = n;
-        }
-    }
-};
+// index (r, s), s <= r, of entry t of a lower triangle stored row by row
+__device__ __forceinline__ void tri_index(int t, int &r, int &s)
+{
+    r = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+    while ((r + 1) * (r + 2) / 2 <= t) ++r;
+    while (r * (r + 1) / 2 > t) --r;
+    s = t - r * (r + 1) / 2;
+}
 
+// assemble .. factor .. map, and the per-step constants of the z-step
 template <typename T>
 __device__ void scene_setup(const StepParams &P, const SceneDesc &S, const View<T> &V,
                             int *s_status, PhaseClock &pc)
@@ -145,9 +212,9 @@ __device__ void scene_setup(const StepParams &P, const SceneDesc &S, const View<
     T *tb = V.tb;
     for (int i = warp; i < S.nsub; i += SUBADMM_WARPS) {
         const SubDesc &u = P.subs[S.sub0 + i];
-        double *W = db + u.od_W, *K = db + u.od_L;
+        double *J = db + u.od_J, *K = db + u.od_L;
         if (u.kind == KIND_RIGID) {
-            for (int q = lane; q < u.m * u.n; q += 32) W[q] = 0.0;
+            for (int q = lane; q < u.m * u.n; q += 32) J[q] = 0.0;
             for (int q = lane; q < u.n * u.n; q += 32) K[q] = 0.0;
         } else {
             const double *A = P.pool + u.gen_off;
@@ -172,21 +239,24 @@ __device__ void scene_setup(const StepParams &P, const SceneDesc &S, const View<
             }
         }
     }
-    // constraint rows into W (as rows of J_ci) and e (thread per constraint)
+    // constraint rows into J (FP64) and e; constraints in the host's assembly order, which
+    // groups kinds by warp so a warp runs one kind's code path
     T *E = tb + S.ot_e;
-    for (int j = tid; j < S.ncon; j += blockDim.x) {
+    for (int a = tid; a < S.nasm; a += blockDim.x) {
+        const int j = P.asm_order[S.asm_g0 + a];
+        if (j < 0) continue;
         const ConDesc &c = P.cons[S.con0 + j];
         if (c.src <= SRC_CONTACT) {
             const double *p = P.pool + c.par_off + 3;
             for (int r = 0; r < c.rows; ++r) E[c.row0 + r] = (T)p[r];
-            const double *J = p + c.rows;
+            const double *Jp = p + c.rows;
             for (int s = 0; s < c.ns; ++s) {
                 const SubDesc &u = P.subs[S.sub0 + c.sub[s]];
                 for (int r = 0; r < c.rows; ++r) {
-                    double *Wr = db + u.od_W + (c.sr[s] + r - u.sr0) * u.n;
-                    for (int q = 0; q < u.n; ++q) Wr[q] = J[r * u.n + q];
+                    double *Jr = db + u.od_J + (c.sr[s] + r - u.sr0) * u.n;
+                    for (int q = 0; q < u.n; ++q) Jr[q] = Jp[r * u.n + q];
                 }
-                J += c.rows * u.n;
+                Jp += c.rows * u.n;
             }
         } else {
             double Ja[30], Jb[30], ee[5], kk = 0.0, al = 0.0;
@@ -195,31 +265,31 @@ __device__ void scene_setup(const StepParams &P, const SceneDesc &S, const View<
             {
                 const SubDesc &u = P.subs[S.sub0 + c.sub[0]];
                 for (int r = 0; r < c.rows; ++r) {
-                    double *Wr = db + u.od_W + (c.sr[0] + r - u.sr0) * u.n + 6 * c.ba;
-                    for (int q = 0; q < 6; ++q) Wr[q] = Ja[6 * r + q];
+                    double *Jr = db + u.od_J + (c.sr[0] + r - u.sr0) * u.n + 6 * c.ba;
+                    for (int q = 0; q < 6; ++q) Jr[q] = Ja[6 * r + q];
                 }
             }
             if (c.side_b >= 0) {
                 const SubDesc &u = P.subs[S.sub0 + c.sub[c.side_b]];
                 for (int r = 0; r < c.rows; ++r) {
-                    double *Wr = db + u.od_W + (c.sr[c.side_b] + r - u.sr0) * u.n + 6 * c.bb;
-                    for (int q = 0; q < 6; ++q) Wr[q] = Jb[6 * r + q];
+                    double *Jr = db + u.od_J + (c.sr[c.side_b] + r - u.sr0) * u.n + 6 * c.bb;
+                    for (int q = 0; q < 6; ++q) Jr[q] = Jb[6 * r + q];
                 }
             }
         }
     }
     __syncthreads();
     pc.mark(PHASE_ASSEMBLE);
-    // per subsystem (one warp each): beta, K += beta J^T J, Cholesky, W, g, D, c
+    // per subsystem (one warp each): beta, K += beta J^T J, FP64 Cholesky, then the map in T
     for (int i = warp; i < S.nsub; i += SUBADMM_WARPS) {
         const SubDesc &u = P.subs[S.sub0 + i];
-        const int n = u.n, m = u.m;
-        double *W = db + u.od_W, *K = db + u.od_L, *b = db + u.od_b;
-        T *D = tb + u.ot_D, *cc = tb + u.ot_c;
+        const int n = u.n, m = u.m, mp = u.mpad;
+        double *J = db + u.od_J, *K = db + u.od_L, *b = db + u.od_b, *idg = db + u.od_id;
+        T *LT = tb + u.ot_L, *W = tb + u.ot_W, *g = tb + u.ot_g, *D = tb + u.ot_D, *cc = tb + u.ot_c;
         // beta_i = Tr(A_i) / Tr(J_ci^T J_ci)  (Sec. III-D)
         double trA = 0.0, trJ = 0.0;
         for (int q = lane; q < n; q += 32) trA += K[q * n + q];
-        for (int q = lane; q < m * n; q += 32) trJ += W[q] * W[q];
+        for (int q = lane; q < m * n; q += 32) trJ += J[q] * J[q];
         trA = warp_sum(trA);
         trJ = warp_sum(trJ);
         const double beta = P.beta_fixed ? P.rho : (trJ > 0.0 ? trA / trJ : 1.0);
@@ -228,23 +298,23 @@ __device__ void scene_setup(const StepParams &P, const SceneDesc &S, const View<
             P.beta[S.sub0 + i] = beta;
         }
         // K_i = A_i + beta_i J_ci^T J_ci (lower triangle)
-        for (int t = lane; t < n * n; t += 32) {
-            const int p = t / n, q = t - p * n;
-            if (q > p) continue;
+        for (int t = lane; t < n * (n + 1) / 2; t += 32) {
+            int p, q;
+            tri_index(t, p, q);
             double acc = 0.0;
-            for (int r = 0; r < m; ++r) acc += W[r * n + p] * W[r * n + q];
-            K[t] += beta * acc;
+            for (int r = 0; r < m; ++r) acc += J[r * n + p] * J[r * n + q];
+            K[p * n + q] += beta * acc;
         }
         __syncwarp();
-        // right-looking Cholesky, in place (lower triangle)
+        // right-looking Cholesky in FP64, in place (lower triangle); 1/L_kk kept in idg
         bool ok = true;
         for (int k = 0; k < n; ++k) {
             const double d = K[k * n + k];
             if (!(d > 0.0) || !isfinite(d)) { ok = false; break; }
-            const double lkk = sqrt(d);
-            const double ilkk = 1.0 / lkk;
+            const double ilkk = rsqrt(d);
             __syncwarp();
-            for (int r = k + lane; r < n; r += 32) K[r * n + k] = (r == k) ? lkk : K[r * n + k] * ilkk;
+            for (int r = k + lane; r < n; r += 32) K[r * n + k] = (r == k) ? d * ilkk : K[r * n + k] * ilkk;
+            if (lane == 0) idg[k] = ilkk;
             __syncwarp();
             for (int r = k + 1 + lane; r < n; r += 32) {
                 const double lrk = K[r * n + k];
@@ -256,43 +326,52 @@ __device__ void scene_setup(const StepParams &P, const SceneDesc &S, const View<
             if (lane == 0) *s_status = ST_NOTSPD;
             continue;
         }
-        // W rows <- L^-1 J rows ; g = L^-1 b (forward substitution, lane per right-hand side)
+        // the map in T: LT = L (with 1/L_pp on its diagonal), W rows = J rows, g = b
+        for (int q = lane; q < n * n; q += 32) {
+            const int p = q / n, r = q - p * n;
+            LT[q] = (r == p) ? (T)idg[p] : (T)K[q];
+        }
+        for (int q = lane; q < m * n; q += 32) W[q] = (T)J[q];
+        for (int q = lane; q < n; q += 32) g[q] = (T)b[q];
+        __syncwarp();
+        // W rows <- L^-1 J rows, g <- L^-1 b (forward substitution, lane per right-hand side)
         for (int t = lane; t <= m; t += 32) {
-            double *x = (t < m) ? W + t * n : b;
+            T *x = (t < m) ? W + t * n : g;
             for (int p = 0; p < n; ++p) {
-                double s = x[p];
-                for (int q = 0; q < p; ++q) s -= K[p * n + q] * x[q];
-                x[p] = s / K[p * n + p];
+                T s = x[p];
+                for (int q = 0; q < p; ++q) s -= LT[p * n + q] * x[q];
+                x[p] = s * LT[p * n + p];
             }
         }
         __syncwarp();
-        // D = W^T W (as rows of W, symmetric; rows padded with zeros to mpad), c = W^T g,
-        // rounded to T
-        const int mp = u.mpad;
-        for (int t = lane; t < m * mp + m; t += 32) {
-            if (t < m * mp) {
-                const int r = t / mp, s = t - r * mp;
-                if (s >= m) { D[r * mp + s] = (T)0; continue; }
-                if (s > r) continue;
-                double acc = 0.0;
-                for (int p = 0; p < n; ++p) acc += W[r * n + p] * W[s * n + p];
-                D[r * mp + s] = (T)acc;
-                D[s * mp + r] = (T)acc;
-            } else {
-                const int r = t - m * mp;
-                double acc = 0.0;
-                for (int p = 0; p < n; ++p) acc += W[r * n + p] * b[p];
-                cc[r] = (T)acc;
+        // D = W^T W (symmetric, rows padded with zeros to mpad), c = W^T g
+        for (int t = lane; t < m * (m + 1) / 2; t += 32) {
+            int r, s;
+            tri_index(t, r, s);
+            T acc = (T)0;
+            for (int p = 0; p < n; ++p) acc += W[r * n + p] * W[s * n + p];
+            D[r * mp + s] = acc;
+            D[s * mp + r] = acc;
+        }
+        if (mp > m) {
+            for (int t = lane; t < m * (mp - m); t += 32) {
+                const int r = t / (mp - m);
+                D[r * mp + m + (t - r * (mp - m))] = (T)0;
             }
+        }
+        for (int r = lane; r < m; r += 32) {
+            T acc = (T)0;
+            for (int p = 0; p < n; ++p) acc += W[r * n + p] * g[p];
+            cc[r] = acc;
         }
     }
     __syncthreads();
+    pc.mark(PHASE_FACTOR);
     // per-step z-step constants: 1/s, soft gain k/(1 + s alpha k), alpha, mu (per row);
     // beta and 1/beta per side-row
     T *INVS = tb + S.ot_invs, *KF = tb + S.ot_kf, *AL = tb + S.ot_al, *MU = tb + S.ot_mu;
     T *INVB = tb + S.ot_invb, *BT = tb + S.ot_b;
     const double *BETA = db + S.od_beta;
-    pc.mark(PHASE_FACTOR);
     for (int j = tid; j < S.ncon; j += blockDim.x) {
         const ConDesc &c = P.cons[S.con0 + j];
         double s = 0.0;
@@ -317,79 +396,43 @@ __device__ void scene_setup(const StepParams &P, const SceneDesc &S, const View<
     __syncthreads();
 }
 
-// h_i = g_i + W_i w (FP64) for every subsystem (warp per subsystem).  h lives right after
-// g in the double region (the host reserves 2 n doubles at od_b).
+// v-hat of the last v-step in FP64: v = L^-T L^-1 (b + J^T w) into od_v (warp per subsystem)
 template <typename T>
-__device__ void form_h(const StepParams &P, const SceneDesc &S, const View<T> &V, const T *w)
+__device__ void recover_v(const StepParams &P, const SceneDesc &S, const View<T> &V, const T *w)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int i = warp; i < S.nsub; i += SUBADMM_WARPS) {
         const SubDesc &u = P.subs[S.sub0 + i];
         const int n = u.n, m = u.m;
-        const double *W = V.db + u.od_W, *g = V.db + u.od_b;
-        double *h = V.db + u.od_b + n;
+        const double *J = V.db + u.od_J, *Lf = V.db + u.od_L, *b = V.db + u.od_b;
+        const double *idg = V.db + u.od_id;
+        double *v = V.db + u.od_v;
         const T *wi = w + u.sr0;
         for (int p = lane; p < n; p += 32) {
-            double acc = g[p];
-            for (int r = 0; r < m; ++r) acc += W[r * n + p] * (double)wi[r];
-            h[p] = acc;
+            double acc = b[p];
+            for (int r = 0; r < m; ++r) acc += J[r * n + p] * (double)wi[r];
+            v[p] = acc;
+        }
+        __syncwarp();
+        for (int p = 0; p < n; ++p) {          // L y = rhs (column-oriented)
+            const double yp = v[p] * idg[p];
+            __syncwarp();
+            if (lane == 0) v[p] = yp;
+            for (int q = p + 1 + lane; q < n; q += 32) v[q] -= Lf[q * n + p] * yp;
+            __syncwarp();
+        }
+        for (int p = n - 1; p >= 0; --p) {     // L^T v = y
+            const double vp = v[p] * idg[p];
+            __syncwarp();
+            if (lane == 0) v[p] = vp;
+            for (int q = lane; q < p; q += 32) v[q] -= Lf[p * n + q] * vp;
+            __syncwarp();
         }
     }
 }
 
-// 16-byte vectors of the iteration type and residual bit patterns.  Residuals are
-// non-negative, so their IEEE bit patterns order like their values and a NaN (sign bit
-// cleared by fabs) orders above +inf: maxima reduce on the integer pipe.
-template <typename T> struct VecOf;
-template <> struct VecOf<float> { using V = float4; using U = unsigned; static constexpr int N = 4; };
-template <> struct VecOf<double> { using V = double2; using U = unsigned long long; static constexpr int N = 2; };
-
-__device__ __forceinline__ float vdot(const float4 a, const float4 b, float acc)
-{
-    acc = fmaf(a.x, b.x, acc); acc = fmaf(a.y, b.y, acc);
-    acc = fmaf(a.z, b.z, acc); acc = fmaf(a.w, b.w, acc);
-    return acc;
-}
-__device__ __forceinline__ double vdot(const double2 a, const double2 b, double acc)
-{
-    acc = fma(a.x, b.x, acc); acc = fma(a.y, b.y, acc);
-    return acc;
-}
-__device__ __forceinline__ unsigned rbits(float v) { return __float_as_uint(v); }
-__device__ __forceinline__ unsigned long long rbits(double v) { return (unsigned long long)__double_as_longlong(v); }
-__device__ __forceinline__ unsigned umax(unsigned a, unsigned b) { return a > b ? a : b; }
-__device__ __forceinline__ unsigned long long umax(unsigned long long a, unsigned long long b) { return a > b ? a : b; }
-__device__ __forceinline__ unsigned warp_umax(unsigned v) { return __reduce_max_sync(0xffffffffu, v); }
-__device__ __forceinline__ unsigned long long warp_umax(unsigned long long v)
-{
-    const unsigned hi = (unsigned)(v >> 32), lo = (unsigned)v;
-    const unsigned mh = __reduce_max_sync(0xffffffffu, hi);
-    const unsigned ml = __reduce_max_sync(0xffffffffu, hi == mh ? lo : 0u);
-    return ((unsigned long long)mh << 32) | ml;
-}
-__device__ __forceinline__ unsigned tol_bits(float, double tol) { return __float_as_uint(__double2float_rd(tol)); }
-__device__ __forceinline__ unsigned long long tol_bits(double, double tol) { return rbits(tol); }
-__device__ __forceinline__ unsigned inf_bits(float) { return 0x7f800000u; }
-__device__ __forceinline__ unsigned long long inf_bits(double) { return 0x7ff0000000000000ull; }
-
-// Sum (k = 0) and maxima (k = 1, 2) of three per-thread doubles over the block.
-__device__ __forceinline__ void block_reduce3(double (*red)[SUBADMM_WARPS], double &a, double &b,
-                                              double &c)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    a = warp_sum(a); b = warp_max(b); c = warp_max(c);
-    __syncthreads();
-    if (lane == 0) { red[0][warp] = a; red[1][warp] = b; red[2][warp] = c; }
-    __syncthreads();
-    a = 0.0; b = 0.0; c = 0.0;
-    for (int q = 0; q < SUBADMM_WARPS; ++q) {
-        a += red[0][q]; b = nanmax(b, red[1][q]); c = nanmax(c, red[2][q]);
-    }
-    __syncthreads();
-}
-
-template <typename T, int SPLIT>
-__global__ void __launch_bounds__(SUBADMM_THREADS) step_kernel(StepParams P)
+template <typename T, int SPLIT, bool CACHED>
+__global__ void __launch_bounds__(SUBADMM_THREADS, 1) step_kernel(StepParams P)
 {
     using VT = typename VecOf<T>::V;
     using U = typename VecOf<T>::U;
@@ -443,10 +486,60 @@ __global__ void __launch_bounds__(SUBADMM_THREADS) step_kernel(StepParams P)
                 ZO[t] = z;
                 X[t] = (T)0;
                 Y[t] = beta * z - l;           // y^0 = beta z^0 + u^0
+                YO[t] = Y[t];
                 Wv[0][t] = beta * z + l;       // w^0 = beta z^0 - u^0
             }
             __syncthreads();
-            pc.mark(PHASE_ASSEMBLE);
+
+            // ---- per-thread cache of the step's coefficients (CACHED: one side-row group
+            // and one z-step item per thread, items with at most two sides)
+            const int xg = tid / SPLIT, xgl = tid - xg * SPLIT;
+            const int xt = xg;
+            bool xv = false;
+            int xdro = 0, xwbo = 0, xnv = 0, xrow = 0;
+            T xc = (T)0, xbt = (T)0, yreg = (T)0, yprev = (T)0;
+            bool pv = false;
+            int ptype = 0, prow = 0, pt0 = 0, pt1 = -1, pnr = 1;
+            T ib0 = (T)0, ib1 = (T)0, pe0 = (T)0, pe1 = (T)0, pe2 = (T)0;
+            T pis = (T)0, pkf = (T)0, pal = (T)0, pmu = (T)0;
+            T zr[6] = {(T)0, (T)0, (T)0, (T)0, (T)0, (T)0};
+            T zq[6] = {(T)0, (T)0, (T)0, (T)0, (T)0, (T)0};
+            if (CACHED) {
+                if (xt < S.nsr && V.mlen[xt] > 0) {
+                    xv = true;
+                    xdro = V.drow[xt];
+                    xwbo = V.wbase[xt];
+                    xnv = (V.mlen[xt] + VN - 1) / VN;
+                    xrow = V.row[xt];
+                    xc = V.tb[V.coff[xt]];
+                    xbt = BT[xt];
+                    yreg = Y[xt];
+                    yprev = yreg;
+                }
+                if (tid < S.nitem) {
+                    pv = true;
+                    const Item it = V.item[tid];
+                    ptype = it.type;
+                    prow = it.row;
+                    pt0 = V.list[it.lo];
+                    pt1 = it.ns > 1 ? V.list[it.lo + 1] : -1;
+                    pnr = ptype == TYPE_CONTACT ? 3 : 1;
+                    ib0 = INVB[pt0];
+                    if (pt1 >= 0) ib1 = INVB[pt1];
+                    pe0 = E[prow];
+                    if (pnr == 3) { pe1 = E[prow + 1]; pe2 = E[prow + 2]; }
+                    pis = INVS[prow]; pkf = KF[prow]; pal = AL[prow]; pmu = MU[prow];
+#pragma unroll
+                    for (int r = 0; r < 3; ++r) {
+                        if (r < pnr) {
+                            zr[r] = Z[pt0 + r];
+                            if (pt1 >= 0) zr[3 + r] = Z[pt1 + r];
+                        }
+                    }
+#pragma unroll
+                    for (int r = 0; r < 6; ++r) zq[r] = zr[r];
+                }
+            }
 
             int par = 0, last_par = 0, iters = 0, conv = 0, status = ST_OK;
             double th = 0.0;
@@ -454,28 +547,49 @@ __global__ void __launch_bounds__(SUBADMM_THREADS) step_kernel(StepParams P)
             U tolb = tol_bits(T(0), tolc > 0.0 ? tolc : 0.0);
             const bool primal_stop = !P.stop_theta && P.tol > 0.0;
             int l = 0;
+            pc.mark(PHASE_ASSEMBLE);
             for (;;) {
                 for (; l < P.max_iters; ++l) {
-                    // v-step through the affine map x = c + D w; y = beta x - lambda
+                    // ---- v-step through the affine map x = c + D w; y = beta x - lambda
                     const T *w = Wv[par];
                     double tpart = 0.0;
-                    {
+                    if (CACHED) {
+                        T acc = (T)0;
+                        if (xv) {
+                            const VT *Dr = reinterpret_cast<const VT *>(V.tb + xdro);
+                            const VT *wb = reinterpret_cast<const VT *>(w + xwbo);
+                            for (int c = xgl; c < xnv; c += SPLIT) acc = vdot(Dr[c], wb[c], acc);
+                        }
+#pragma unroll
+                        for (int o = SPLIT / 2; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                        if (xv && xgl == 0) {
+                            acc += xc;
+                            const T ynew = xbt * acc - LAM[xrow];
+                            if (P.stop_theta) {
+                                const double d = (double)ynew - (double)yreg;
+                                tpart += d * d;
+                            }
+                            yprev = yreg;
+                            yreg = ynew;
+                            Y[xt] = ynew;
+                            X[xt] = acc;
+                        }
+                    } else {
                         constexpr int groups = SUBADMM_THREADS / SPLIT;
-                        const int g = tid / SPLIT, gl = tid - g * SPLIT;
                         const int trips = (S.nsr + groups - 1) / groups;
                         for (int k = 0; k < trips; ++k) {
-                            const int t = g + k * groups;
+                            const int t = xg + k * groups;
                             const int m = t < S.nsr ? V.mlen[t] : 0;
                             T acc = (T)0;
                             if (m > 0) {
                                 const VT *Dr = reinterpret_cast<const VT *>(V.tb + V.drow[t]);
                                 const VT *wb = reinterpret_cast<const VT *>(w + V.wbase[t]);
                                 const int nv = (m + VN - 1) / VN;
-                                for (int c = gl; c < nv; c += SPLIT) acc = vdot(Dr[c], wb[c], acc);
+                                for (int c = xgl; c < nv; c += SPLIT) acc = vdot(Dr[c], wb[c], acc);
                             }
 #pragma unroll
                             for (int o = SPLIT / 2; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-                            if (m > 0 && gl == 0) {
+                            if (m > 0 && xgl == 0) {
                                 acc += V.tb[V.coff[t]];
                                 const T ynew = BT[t] * acc - LAM[V.row[t]];
                                 if (P.stop_theta) {
@@ -501,63 +615,132 @@ __global__ void __launch_bounds__(SUBADMM_THREADS) step_kernel(StepParams P)
                         for (int q = 0; q < SUBADMM_WARPS; ++q) th += red[l & 1][q];
                         if (l >= 1 && th < P.theta_th) { conv = 1; break; }
                     }
-                    // z-step per item (Sec. III-C); u = -lambda; max(|x - z|, |dz|) as bits
+                    // ---- z-step (Sec. III-C); u = -lambda; max(|x - z|, |dz|) as bits
                     T *wn = Wv[par ^ 1];
                     U mloc = 0;
-                    for (int i = tid; i < S.nitem; i += SUBADMM_THREADS) {
-                        const Item it = V.item[i];
-                        const int *ls = V.list + it.lo;
-                        if (it.type == TYPE_CONTACT) {
-                            T q0 = (T)0, q1 = (T)0, q2 = (T)0;
-                            for (int s = 0; s < it.ns; ++s) {
-                                const int t = ls[s];
-                                const T ib = INVB[t];
-                                q0 += Y[t] * ib; q1 += Y[t + 1] * ib; q2 += Y[t + 2] * ib;
-                            }
-                            const T is = INVS[it.row];
-                            const T ln = -(q0 + E[it.row]) * is;
-                            const T l1 = -(q1 + E[it.row + 1]) * is;
-                            const T l2 = -(q2 + E[it.row + 2]) * is;
-                            T lv[3];
-                            if (ln <= (T)0) {
-                                lv[0] = lv[1] = lv[2] = (T)0;
-                            } else {
-                                const T tn = sqrt(l1 * l1 + l2 * l2);
-                                const T lim = MU[it.row] * ln;
-                                lv[0] = ln;
-                                if (tn > lim) { const T f = lim / tn; lv[1] = l1 * f; lv[2] = l2 * f; }
-                                else { lv[1] = l1; lv[2] = l2; }
-                            }
-                            LAM[it.row] = lv[0]; LAM[it.row + 1] = lv[1]; LAM[it.row + 2] = lv[2];
-                            for (int s = 0; s < it.ns; ++s) {
+                    if (CACHED) {
+                        if (pv) {
+                            if (ptype == TYPE_CONTACT) {
+                                T ya[3], yb[3] = {(T)0, (T)0, (T)0};
+#pragma unroll
+                                for (int r = 0; r < 3; ++r) ya[r] = Y[pt0 + r];
+                                if (pt1 >= 0) {
+#pragma unroll
+                                    for (int r = 0; r < 3; ++r) yb[r] = Y[pt1 + r];
+                                }
+                                const T ln = -(ya[0] * ib0 + yb[0] * ib1 + pe0) * pis;
+                                const T l1 = -(ya[1] * ib0 + yb[1] * ib1 + pe1) * pis;
+                                const T l2 = -(ya[2] * ib0 + yb[2] * ib1 + pe2) * pis;
+                                T lv[3];
+                                if (ln <= (T)0) {
+                                    lv[0] = lv[1] = lv[2] = (T)0;
+                                } else {
+                                    const T t2 = l1 * l1 + l2 * l2;
+                                    const T lim = pmu * ln;
+                                    lv[0] = ln;
+                                    if (t2 > lim * lim) { const T f = lim * rsq(t2); lv[1] = l1 * f; lv[2] = l2 * f; }
+                                    else { lv[1] = l1; lv[2] = l2; }
+                                }
 #pragma unroll
                                 for (int r = 0; r < 3; ++r) {
-                                    const int t = ls[s] + r;
+                                    LAM[prow + r] = lv[r];
+                                    const T zn = (ya[r] + lv[r]) * ib0;
+                                    mloc = umax(mloc, umax(rbits(fabs(X[pt0 + r] - zn)), rbits(fabs(zn - zr[r]))));
+                                    zq[r] = zr[r];
+                                    zr[r] = zn;
+                                    wn[pt0 + r] = ya[r] + (T)2 * lv[r];
+                                }
+                                if (pt1 >= 0) {
+#pragma unroll
+                                    for (int r = 0; r < 3; ++r) {
+                                        const T zn = (yb[r] + lv[r]) * ib1;
+                                        mloc = umax(mloc, umax(rbits(fabs(X[pt1 + r] - zn)), rbits(fabs(zn - zr[3 + r]))));
+                                        zq[3 + r] = zr[3 + r];
+                                        zr[3 + r] = zn;
+                                        wn[pt1 + r] = yb[r] + (T)2 * lv[r];
+                                    }
+                                }
+                            } else {
+                                const T y0 = Y[pt0];
+                                const T y1 = pt1 >= 0 ? Y[pt1] : (T)0;
+                                const T q = y0 * ib0 + y1 * ib1;
+                                T lv;
+                                if (ptype == TYPE_SOFT) lv = -(pe0 + pal * q) * pkf;
+                                else {
+                                    lv = -(q + pe0) * pis;
+                                    if (ptype == TYPE_HARD) lv = lv > (T)0 ? lv : (T)0;
+                                }
+                                LAM[prow] = lv;
+                                const T zn0 = (y0 + lv) * ib0;
+                                mloc = umax(mloc, umax(rbits(fabs(X[pt0] - zn0)), rbits(fabs(zn0 - zr[0]))));
+                                zq[0] = zr[0];
+                                zr[0] = zn0;
+                                wn[pt0] = y0 + (T)2 * lv;
+                                if (pt1 >= 0) {
+                                    const T zn1 = (y1 + lv) * ib1;
+                                    mloc = umax(mloc, umax(rbits(fabs(X[pt1] - zn1)), rbits(fabs(zn1 - zr[3]))));
+                                    zq[3] = zr[3];
+                                    zr[3] = zn1;
+                                    wn[pt1] = y1 + (T)2 * lv;
+                                }
+                            }
+                        }
+                    } else {
+                        for (int i = tid; i < S.nitem; i += SUBADMM_THREADS) {
+                            const Item it = V.item[i];
+                            const int *ls = V.list + it.lo;
+                            if (it.type == TYPE_CONTACT) {
+                                T q0 = (T)0, q1 = (T)0, q2 = (T)0;
+                                for (int s = 0; s < it.ns; ++s) {
+                                    const int t = ls[s];
+                                    const T ib = INVB[t];
+                                    q0 += Y[t] * ib; q1 += Y[t + 1] * ib; q2 += Y[t + 2] * ib;
+                                }
+                                const T is = INVS[it.row];
+                                const T ln = -(q0 + E[it.row]) * is;
+                                const T l1 = -(q1 + E[it.row + 1]) * is;
+                                const T l2 = -(q2 + E[it.row + 2]) * is;
+                                T lv[3];
+                                if (ln <= (T)0) {
+                                    lv[0] = lv[1] = lv[2] = (T)0;
+                                } else {
+                                    const T t2 = l1 * l1 + l2 * l2;
+                                    const T lim = MU[it.row] * ln;
+                                    lv[0] = ln;
+                                    if (t2 > lim * lim) { const T f = lim * rsq(t2); lv[1] = l1 * f; lv[2] = l2 * f; }
+                                    else { lv[1] = l1; lv[2] = l2; }
+                                }
+                                LAM[it.row] = lv[0]; LAM[it.row + 1] = lv[1]; LAM[it.row + 2] = lv[2];
+                                for (int s = 0; s < it.ns; ++s) {
+#pragma unroll
+                                    for (int r = 0; r < 3; ++r) {
+                                        const int t = ls[s] + r;
+                                        const T yv = Y[t], zo = Z[t];
+                                        const T zn = (yv + lv[r]) * INVB[t];
+                                        mloc = umax(mloc, umax(rbits(fabs(X[t] - zn)), rbits(fabs(zn - zo))));
+                                        ZO[t] = zo;
+                                        Z[t] = zn;
+                                        wn[t] = yv + (T)2 * lv[r];
+                                    }
+                                }
+                            } else {
+                                T q = (T)0;
+                                for (int s = 0; s < it.ns; ++s) q += Y[ls[s]] * INVB[ls[s]];
+                                const T e = E[it.row];
+                                T lv;
+                                if (it.type == TYPE_EQUALITY) lv = -(q + e) * INVS[it.row];
+                                else if (it.type == TYPE_HARD) { lv = -(q + e) * INVS[it.row]; lv = lv > (T)0 ? lv : (T)0; }
+                                else lv = -(e + AL[it.row] * q) * KF[it.row];
+                                LAM[it.row] = lv;
+                                for (int s = 0; s < it.ns; ++s) {
+                                    const int t = ls[s];
                                     const T yv = Y[t], zo = Z[t];
-                                    const T zn = (yv + lv[r]) * INVB[t];
+                                    const T zn = (yv + lv) * INVB[t];
                                     mloc = umax(mloc, umax(rbits(fabs(X[t] - zn)), rbits(fabs(zn - zo))));
                                     ZO[t] = zo;
                                     Z[t] = zn;
-                                    wn[t] = yv + (T)2 * lv[r];
+                                    wn[t] = yv + (T)2 * lv;
                                 }
-                            }
-                        } else {
-                            T q = (T)0;
-                            for (int s = 0; s < it.ns; ++s) q += Y[ls[s]] * INVB[ls[s]];
-                            const T e = E[it.row];
-                            T lv;
-                            if (it.type == TYPE_EQUALITY) lv = -(q + e) * INVS[it.row];
-                            else if (it.type == TYPE_HARD) { lv = -(q + e) * INVS[it.row]; lv = lv > (T)0 ? lv : (T)0; }
-                            else lv = -(e + AL[it.row] * q) * KF[it.row];
-                            LAM[it.row] = lv;
-                            for (int s = 0; s < it.ns; ++s) {
-                                const int t = ls[s];
-                                const T yv = Y[t], zo = Z[t];
-                                const T zn = (yv + lv) * INVB[t];
-                                mloc = umax(mloc, umax(rbits(fabs(X[t] - zn)), rbits(fabs(zn - zo))));
-                                ZO[t] = zo;
-                                Z[t] = zn;
-                                wn[t] = yv + (T)2 * lv;
                             }
                         }
                     }
@@ -572,28 +755,41 @@ __global__ void __launch_bounds__(SUBADMM_THREADS) step_kernel(StepParams P)
                     if (mx >= inf_bits(T(0))) { status = ST_NAN; break; }
                     if (primal_stop && mx <= tolb) { conv = 1; break; }
                 }
-                // h = g + W w of the last v-step (FP64)
-                form_h<T>(P, S, V, Wv[last_par]);
+                // the cached z live in registers: publish them (and the previous ones)
+                if (CACHED && pv) {
+#pragma unroll
+                    for (int r = 0; r < 3; ++r) {
+                        if (r < pnr) {
+                            Z[pt0 + r] = zr[r]; ZO[pt0 + r] = zq[r];
+                            if (pt1 >= 0) { Z[pt1 + r] = zr[3 + r]; ZO[pt1 + r] = zq[3 + r]; }
+                        }
+                    }
+                }
+                if (CACHED && xv && xgl == 0) YO[xt] = yprev;
                 __syncthreads();
-                if (MIXED && conv && !P.stop_theta && status == ST_OK) {
-                    // FP64 check of the primal residual: x = J v = W^T h
+                recover_v<T>(P, S, V, Wv[last_par]);
+                __syncthreads();
+                if (MIXED && conv && primal_stop && status == ST_OK) {
+                    // FP64 primal residual max |J v - z|; on a miss, refine c by the FP64 - FP32
+                    // difference of x at this iterate and resume
                     double part = 0.0;
                     for (int t = tid; t < S.nsr; t += blockDim.x) {
                         if (V.mlen[t] == 0) continue;
                         const SubDesc &u = P.subs[S.sub0 + V.sub[t]];
                         const int lr = t - u.sr0, n = u.n;
-                        const double *Wr = V.db + u.od_W + lr * n;
-                        const double *h = V.db + u.od_b + n;
+                        const double *Jr = V.db + u.od_J + lr * n;
+                        const double *v = V.db + u.od_v;
                         double x = 0.0;
-                        for (int p = 0; p < n; ++p) x += Wr[p] * h[p];
+                        for (int p = 0; p < n; ++p) x += Jr[p] * v[p];
                         part = nanmax(part, fabs(x - (double)Z[t]));
+                        V.tb[V.coff[t]] += (T)(x - (double)X[t]);
                     }
                     double d0 = 0.0, d2 = 0.0;
                     block_reduce3(red, d0, part, d2);
                     if (part > P.tol && l + 1 < P.max_iters) {
-                        // resume from the current iterate with a tighter FP32 test
-                        tolc *= 0.25;
+                        tolc *= 0.5;
                         tolb = tol_bits(T(0), tolc);
+                        if (CACHED && xv) xc = V.tb[V.coff[xt]];
                         conv = 0;
                         ++l;
                         continue;
@@ -620,30 +816,14 @@ __global__ void __launch_bounds__(SUBADMM_THREADS) step_kernel(StepParams P)
                 rd = dd;
             }
             pc.mark(PHASE_EXIT);
-
-            // v-hat = L^-T h (warp per subsystem, in place in h)
+            // v-hat out and state update of rigid bodies (Algorithm 1, last line)
             for (int i = warp; i < S.nsub; i += SUBADMM_WARPS) {
                 const SubDesc &u = P.subs[S.sub0 + i];
-                const int n = u.n;
-                const double *Lf = V.db + u.od_L;
-                double *h = V.db + u.od_b + n;
-                for (int p = n - 1; p >= 0; --p) {
-                    const double vp = h[p] / Lf[p * n + p];
-                    __syncwarp();
-                    if (lane == 0) h[p] = vp;
-                    for (int q = lane; q < p; q += 32) h[q] -= Lf[p * n + q] * vp;
-                    __syncwarp();
-                }
-                for (int p = lane; p < n; p += 32) P.vhat[u.v_off + p] = h[p];
-            }
-            __syncthreads();
-            // state update of rigid bodies (Algorithm 1, last line)
-            for (int i = warp; i < S.nsub; i += SUBADMM_WARPS) {
-                const SubDesc &u = P.subs[S.sub0 + i];
+                const double *v = V.db + u.od_v;
+                for (int p = lane; p < u.n; p += 32) P.vhat[u.v_off + p] = v[p];
                 if (u.kind != KIND_RIGID) continue;
                 for (int k = lane; k < u.nb; k += 32)
-                    body_update(P.bodies + (size_t)(u.body0 + k) * SUBADMM_BODY,
-                                V.db + u.od_b + u.n + 6 * k, P.h);
+                    body_update(P.bodies + (size_t)(u.body0 + k) * SUBADMM_BODY, v + 6 * k, P.h);
             }
             __syncthreads();
             pc.mark(PHASE_RECOVER);

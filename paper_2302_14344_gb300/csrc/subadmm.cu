@@ -59,6 +59,8 @@ struct sim_s {
     ConDesc *d_cons = nullptr;
     Item *d_items = nullptr;
     int *d_lists = nullptr;
+    int *d_asm = nullptr;
+    bool cached = false;           // every scene fits the register-cached iteration
     int split = 1;                 // lanes per side-row in the v-step mat-vec
     double *d_pool = nullptr, *d_bodies = nullptr, *d_vhat = nullptr, *d_lam = nullptr;
     double *d_z = nullptr, *d_beta = nullptr, *d_res = nullptr, *d_stage = nullptr;
@@ -128,8 +130,8 @@ __global__ void unpack_state(double *bodies, const double *in, long long nb)
 void free_device(sim_t s)
 {
     cudaFree(s->d_scenes); cudaFree(s->d_subs); cudaFree(s->d_cons); cudaFree(s->d_pool);
-    cudaFree(s->d_items); cudaFree(s->d_lists);
-    s->d_items = nullptr; s->d_lists = nullptr;
+    cudaFree(s->d_items); cudaFree(s->d_lists); cudaFree(s->d_asm);
+    s->d_items = nullptr; s->d_lists = nullptr; s->d_asm = nullptr;
     cudaFree(s->d_bodies); cudaFree(s->d_vhat); cudaFree(s->d_lam); cudaFree(s->d_z);
     cudaFree(s->d_beta); cudaFree(s->d_res); cudaFree(s->d_stats); cudaFree(s->d_stage);
     cudaFree(s->d_phase);
@@ -186,7 +188,8 @@ int finalize(sim_t s)
     std::vector<double> bodies;
     std::vector<Item> items;
     std::vector<int> lists;
-    int max_nsr = 0;
+    std::vector<int> asm_order;
+    int max_nsr = 0, max_items = 0, max_sides = 0;
     s->sdesc.assign(nsubs, SubDesc{});
     s->cdesc.assign(ncons, ConDesc{});
     s->scenes.assign(nscenes, SceneDesc{});
@@ -276,23 +279,44 @@ int finalize(sim_t s)
                 c.side_b = (h.sb == h.sa) ? 0 : 1;
             }
         }
-        // z-step items: one per row of an equality / hard / soft constraint, one per contact
+        // z-step items: one per row of an equality / hard / soft constraint, one per contact;
+        // ordered by type so that neighbouring threads run the same projection
         S.item_g0 = (int)items.size();
         S.list_g0 = (int)lists.size();
-        for (int j = 0; j < S.ncon; ++j) {
-            const ConDesc &c = s->cdesc[S.con0 + j];
-            if (c.type == TYPE_CONTACT) {
-                items.push_back(Item{c.type, c.ns, c.row0, (int)lists.size() - S.list_g0});
-                for (int q = 0; q < c.ns; ++q) lists.push_back(c.sr[q]);
-            } else {
-                for (int r = 0; r < c.rows; ++r) {
-                    items.push_back(Item{c.type, c.ns, c.row0 + r, (int)lists.size() - S.list_g0});
-                    for (int q = 0; q < c.ns; ++q) lists.push_back(c.sr[q] + r);
+        for (int type = 0; type < 4; ++type) {
+            for (int j = 0; j < S.ncon; ++j) {
+                const ConDesc &c = s->cdesc[S.con0 + j];
+                if (c.type != type) continue;
+                max_sides = std::max(max_sides, c.ns);
+                if (c.type == TYPE_CONTACT) {
+                    items.push_back(Item{c.type, c.ns, c.row0, (int)lists.size() - S.list_g0});
+                    for (int q = 0; q < c.ns; ++q) lists.push_back(c.sr[q]);
+                } else {
+                    for (int r = 0; r < c.rows; ++r) {
+                        items.push_back(Item{c.type, c.ns, c.row0 + r, (int)lists.size() - S.list_g0});
+                        for (int q = 0; q < c.ns; ++q) lists.push_back(c.sr[q] + r);
+                    }
                 }
             }
         }
+        // assembly slots: constraints grouped by how their rows are built (explicit rows, or
+        // one model kind), each group padded to whole warps
+        S.asm_g0 = (int)asm_order.size();
+        for (int grp = 0; grp < 5; ++grp) {
+            int cnt = 0;
+            for (int j = 0; j < S.ncon; ++j) {
+                const int src = s->cdesc[S.con0 + j].src;
+                const int g = src <= SRC_CONTACT ? 0 : src - SRC_CONTACT;
+                if (g != grp) continue;
+                asm_order.push_back(j);
+                ++cnt;
+            }
+            while (cnt % 32) { asm_order.push_back(-1); ++cnt; }
+        }
+        S.nasm = (int)asm_order.size() - S.asm_g0;
         S.nitem = (int)items.size() - S.item_g0;
         S.nlist = (int)lists.size() - S.list_g0;
+        max_items = std::max(max_items, S.nitem);
         // shared-memory layout: doubles (factors), then T (iteration arrays), then ints.
         // T offsets are whole 16-byte vectors so D rows and w segments load as vectors.
         int od = 0, ot = 0;
@@ -301,9 +325,14 @@ int finalize(sim_t s)
             SubDesc &u = s->sdesc[S.sub0 + i];
             if (u.m > SUBADMM_MAXM)
                 return fail(s, SIM_EINVAL, "a subsystem has more constraint rows than the on-chip path holds");
-            u.od_W = od; od += u.m * u.n;
+            u.od_J = od; od += u.m * u.n;
             u.od_L = od; od += u.n * u.n;
-            u.od_b = od; od += 2 * u.n;          // g, then h = g + W w
+            u.od_b = od; od += u.n;
+            u.od_v = od; od += u.n;
+            u.od_id = od; od += u.n;
+            u.ot_L = ot; ot += u.n * u.n;
+            u.ot_W = ot; ot += u.m * u.n;
+            u.ot_g = ot; ot = tal(ot + u.n);
             u.ot_D = ot; ot = tal(ot + u.m * u.mpad);
             u.ot_c = ot; ot = tal(ot + u.m);
         }
@@ -359,8 +388,11 @@ int finalize(sim_t s)
     if ((rc = upload(s, &s->d_pool, pool, "pool"))) return rc;
     if ((rc = upload(s, &s->d_items, items, "items"))) return rc;
     if ((rc = upload(s, &s->d_lists, lists, "lists"))) return rc;
+    if ((rc = upload(s, &s->d_asm, asm_order, "assembly order"))) return rc;
     s->split = 1;
     while (s->split < 4 && 2 * s->split * std::max(max_nsr, 1) <= SUBADMM_THREADS) s->split *= 2;
+    // the register-cached iteration holds one side-row group and one item per thread
+    s->cached = max_nsr * s->split <= SUBADMM_THREADS && max_items <= SUBADMM_THREADS && max_sides <= 2;
     if ((rc = upload(s, &s->d_bodies, bodies, "bodies"))) return rc;
     s->pool_size = pool.size();
     if ((rc = zeros(s, &s->d_vhat, (size_t)dof, "vhat"))) return rc;
@@ -594,10 +626,17 @@ int sim_step(sim_t s, int n_steps)
     CK(cudaSetDevice(s->opt.device), "cudaSetDevice");
     P.items = s->d_items;
     P.lists = s->d_lists;
+    P.asm_order = s->d_asm;
     const bool mixed = s->opt.precision == SIM_MIXED;
     void (*kern)(StepParams) = nullptr;
-    if (mixed) kern = s->split == 4 ? subadmm::step_kernel<float, 4> : s->split == 2 ? subadmm::step_kernel<float, 2> : subadmm::step_kernel<float, 1>;
-    else kern = s->split == 4 ? subadmm::step_kernel<double, 4> : s->split == 2 ? subadmm::step_kernel<double, 2> : subadmm::step_kernel<double, 1>;
+    using namespace subadmm;
+    if (mixed) {
+        if (s->cached) kern = s->split == 4 ? step_kernel<float, 4, true> : s->split == 2 ? step_kernel<float, 2, true> : step_kernel<float, 1, true>;
+        else kern = s->split == 4 ? step_kernel<float, 4, false> : s->split == 2 ? step_kernel<float, 2, false> : step_kernel<float, 1, false>;
+    } else {
+        if (s->cached) kern = s->split == 4 ? step_kernel<double, 4, true> : s->split == 2 ? step_kernel<double, 2, true> : step_kernel<double, 1, true>;
+        else kern = s->split == 4 ? step_kernel<double, 4, false> : s->split == 2 ? step_kernel<double, 2, false> : step_kernel<double, 1, false>;
+    }
     // the attribute is per function, shared by every simulation of the process
     CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, std::max(s->max_smem, 1)),
        "shared memory attribute");
