@@ -86,6 +86,13 @@ __device__ __forceinline__ unsigned tol_bits(float, double tol) { return __float
 __device__ __forceinline__ unsigned long long tol_bits(double, double tol) { return rbits(tol); }
 __device__ __forceinline__ unsigned inf_bits(float) { return 0x7f800000u; }
 __device__ __forceinline__ unsigned long long inf_bits(double) { return 0x7ff0000000000000ull; }
+// D chunks (16-byte vectors) a lane keeps in registers in the cached iteration
+template <typename T> struct CachedChunks;
+template <> struct CachedChunks<float> { static constexpr int value = 4; };
+template <> struct CachedChunks<double> { static constexpr int value = 6; };
+template <typename T> struct VecZero;
+template <> struct VecZero<float> { __device__ static float4 get() { return make_float4(0.f, 0.f, 0.f, 0.f); } };
+template <> struct VecZero<double> { __device__ static double2 get() { return make_double2(0.0, 0.0); } };
 __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
 
@@ -105,20 +112,34 @@ __device__ __forceinline__ void block_reduce3(double (*red)[SUBADMM_WARPS], doub
     __syncthreads();
 }
 
-// Phase tracer: thread 0 of a scene's block adds clock64 deltas to P.phase when enabled.
+// Phase tracer: thread 0 of a scene's block accumulates clock64 deltas per phase in
+// registers and adds them to P.phase once per step (flush), so tracing stays off the
+// critical path of the iterations.
 struct PhaseClock {
-    long long *acc;
+    long long *out;
     long long t;
-    __device__ __forceinline__ PhaseClock(long long *a) : acc(threadIdx.x == 0 ? a : nullptr), t(0)
+    long long a[8];
+    __device__ __forceinline__ PhaseClock(long long *o) : out(threadIdx.x == 0 ? o : nullptr), t(0)
     {
-        if (acc) t = clock64();
+#pragma unroll
+        for (int q = 0; q < 8; ++q) a[q] = 0;
+        if (out) t = clock64();
     }
     __device__ __forceinline__ void mark(int phase)
     {
-        if (acc) {
+        if (out) {
             const long long n = clock64();
-            acc[phase] += n - t;
+            a[phase] += n - t;
             t = n;
+        }
+    }
+    __device__ __forceinline__ void flush(int iters)
+    {
+        if (out) {
+            a[PHASE_ITERS] = iters;
+            a[PHASE_STEPS] = 1;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) out[q] += a[q];
         }
     }
 };
@@ -493,8 +514,12 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 1) step_kernel(StepParams P)
 
             // ---- per-thread cache of the step's coefficients (CACHED: one side-row group
             // and one z-step item per thread, items with at most two sides)
+            constexpr int MAXC = CachedChunks<T>::value;   // D chunks a lane keeps in registers
             const int xg = tid / SPLIT, xgl = tid - xg * SPLIT;
             const int xt = xg;
+            VT dreg[MAXC];
+#pragma unroll
+            for (int q = 0; q < MAXC; ++q) dreg[q] = VecZero<T>::get();
             bool xv = false;
             int xdro = 0, xwbo = 0, xnv = 0, xrow = 0;
             T xc = (T)0, xbt = (T)0, yreg = (T)0, yprev = (T)0;
@@ -515,6 +540,10 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 1) step_kernel(StepParams P)
                     xbt = BT[xt];
                     yreg = Y[xt];
                     yprev = yreg;
+                    const VT *Dr = reinterpret_cast<const VT *>(V.tb + xdro);
+#pragma unroll
+                    for (int q = 0; q < MAXC; ++q)
+                        if (xgl + q * SPLIT < xnv) dreg[q] = Dr[xgl + q * SPLIT];
                 }
                 if (tid < S.nitem) {
                     pv = true;
@@ -556,9 +585,17 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 1) step_kernel(StepParams P)
                     if (CACHED) {
                         T acc = (T)0;
                         if (xv) {
-                            const VT *Dr = reinterpret_cast<const VT *>(V.tb + xdro);
                             const VT *wb = reinterpret_cast<const VT *>(w + xwbo);
-                            for (int c = xgl; c < xnv; c += SPLIT) acc = vdot(Dr[c], wb[c], acc);
+                            T a1 = (T)0;
+#pragma unroll
+                            for (int q = 0; q < MAXC; ++q) {
+                                if (xgl + q * SPLIT < xnv) {
+                                    const VT wq = wb[xgl + q * SPLIT];
+                                    if (q & 1) a1 = vdot(dreg[q], wq, a1);
+                                    else acc = vdot(dreg[q], wq, acc);
+                                }
+                            }
+                            acc += a1;
                         }
 #pragma unroll
                         for (int o = SPLIT / 2; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -827,7 +864,7 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 1) step_kernel(StepParams P)
             }
             __syncthreads();
             pc.mark(PHASE_RECOVER);
-            if (pc.acc) { pc.acc[PHASE_ITERS] += iters; pc.acc[PHASE_STEPS] += 1; }
+            pc.flush(iters);
             // warm-start state and reports
             for (int r = tid; r < S.nrow; r += blockDim.x) P.lam[S.row_g0 + r] = (double)LAM[r];
             for (int t = tid; t < S.nsr; t += blockDim.x) P.z[S.sr_g0 + t] = (double)Z[t];

@@ -189,7 +189,7 @@ int finalize(sim_t s)
     std::vector<Item> items;
     std::vector<int> lists;
     std::vector<int> asm_order;
-    int max_nsr = 0, max_items = 0, max_sides = 0;
+    int max_nsr = 0, max_items = 0, max_sides = 0, max_mpad = 0;
     s->sdesc.assign(nsubs, SubDesc{});
     s->cdesc.assign(ncons, ConDesc{});
     s->scenes.assign(nscenes, SceneDesc{});
@@ -257,6 +257,7 @@ int finalize(sim_t s)
             }
             u.m = sr - u.sr0;
             u.mpad = (u.m + vn - 1) / vn * vn;
+            max_mpad = std::max(max_mpad, u.mpad);
         }
         sr = (sr + vn - 1) / vn * vn;
         S.nsr = sr;
@@ -392,7 +393,13 @@ int finalize(sim_t s)
     s->split = 1;
     while (s->split < 4 && 2 * s->split * std::max(max_nsr, 1) <= SUBADMM_THREADS) s->split *= 2;
     // the register-cached iteration holds one side-row group and one item per thread
-    s->cached = max_nsr * s->split <= SUBADMM_THREADS && max_items <= SUBADMM_THREADS && max_sides <= 2;
+    // (and at most 4 float4 / 6 double2 chunks of a D row per lane)
+    {
+        const int vn = s->opt.precision == SIM_MIXED ? 4 : 2;
+        const int chunks = s->opt.precision == SIM_MIXED ? 4 : 6;
+        s->cached = max_nsr * s->split <= SUBADMM_THREADS && max_items <= SUBADMM_THREADS &&
+                    max_sides <= 2 && (max_mpad + vn - 1) / vn <= chunks * s->split;
+    }
     if ((rc = upload(s, &s->d_bodies, bodies, "bodies"))) return rc;
     s->pool_size = pool.size();
     if ((rc = zeros(s, &s->d_vhat, (size_t)dof, "vhat"))) return rc;
