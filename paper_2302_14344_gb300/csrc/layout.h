@@ -68,7 +68,8 @@ struct ConDesc {
     int side_b;            // model: side that holds body b (-1 for the world)
 };
 
-// One z-step work item: a row of an equality / hard / soft constraint, or a whole contact.
+// One z-step work item: a row of an equality / hard / soft constraint, or a whole contact
+// (type -1: an idle slot that aligns the next type's items to a warp).
 // list[lo .. lo+ns) holds the scene-local side-row of each side (row 0 for a contact).
 struct Item {
     int type, ns, row, lo;

@@ -473,7 +473,7 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 1) step_kernel(StepParams P)
         T *E = V.tb + S.ot_e, *INVB = V.tb + S.ot_invb, *BT = V.tb + S.ot_b;
         T *INVS = V.tb + S.ot_invs, *KF = V.tb + S.ot_kf, *AL = V.tb + S.ot_al;
         T *MU = V.tb + S.ot_mu;
-        T *Wv[2] = {V.tb + S.ot_w0, V.tb + S.ot_w1};
+        T *const W0 = V.tb + S.ot_w0, *const W1 = V.tb + S.ot_w1;
         // per-side-row arrays start zero (padding side-rows between subsystems stay zero)
         for (int q = tid; q < S.ot_lam - S.ot_x; q += blockDim.x) V.tb[S.ot_x + q] = (T)0;
         scene_tables<T>(P, S, V);
@@ -508,7 +508,7 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 1) step_kernel(StepParams P)
                 X[t] = (T)0;
                 Y[t] = beta * z - l;           // y^0 = beta z^0 + u^0
                 YO[t] = Y[t];
-                Wv[0][t] = beta * z + l;       // w^0 = beta z^0 - u^0
+                W0[t] = beta * z + l;          // w^0 = beta z^0 - u^0
             }
             __syncthreads();
 
@@ -545,7 +545,7 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 1) step_kernel(StepParams P)
                     for (int q = 0; q < MAXC; ++q)
                         if (xgl + q * SPLIT < xnv) dreg[q] = Dr[xgl + q * SPLIT];
                 }
-                if (tid < S.nitem) {
+                if (tid < S.nitem && V.item[tid].type >= 0) {
                     pv = true;
                     const Item it = V.item[tid];
                     ptype = it.type;
@@ -580,7 +580,7 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 1) step_kernel(StepParams P)
             for (;;) {
                 for (; l < P.max_iters; ++l) {
                     // ---- v-step through the affine map x = c + D w; y = beta x - lambda
-                    const T *w = Wv[par];
+                    const T *w = par ? W1 : W0;
                     double tpart = 0.0;
                     if (CACHED) {
                         T acc = (T)0;
@@ -653,7 +653,7 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 1) step_kernel(StepParams P)
                         if (l >= 1 && th < P.theta_th) { conv = 1; break; }
                     }
                     // ---- z-step (Sec. III-C); u = -lambda; max(|x - z|, |dz|) as bits
-                    T *wn = Wv[par ^ 1];
+                    T *wn = par ? W0 : W1;
                     U mloc = 0;
                     if (CACHED) {
                         if (pv) {
@@ -725,6 +725,7 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 1) step_kernel(StepParams P)
                     } else {
                         for (int i = tid; i < S.nitem; i += SUBADMM_THREADS) {
                             const Item it = V.item[i];
+                            if (it.type < 0) continue;
                             const int *ls = V.list + it.lo;
                             if (it.type == TYPE_CONTACT) {
                                 T q0 = (T)0, q1 = (T)0, q2 = (T)0;
@@ -804,7 +805,7 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 1) step_kernel(StepParams P)
                 }
                 if (CACHED && xv && xgl == 0) YO[xt] = yprev;
                 __syncthreads();
-                recover_v<T>(P, S, V, Wv[last_par]);
+                recover_v<T>(P, S, V, last_par ? W1 : W0);
                 __syncthreads();
                 if (MIXED && conv && primal_stop && status == ST_OK) {
                     // FP64 primal residual max |J v - z|; on a miss, refine c by the FP64 - FP32

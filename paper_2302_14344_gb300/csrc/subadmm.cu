@@ -285,6 +285,9 @@ int finalize(sim_t s)
         S.item_g0 = (int)items.size();
         S.list_g0 = (int)lists.size();
         for (int type = 0; type < 4; ++type) {
+            // each type starts on a warp boundary (idle items, type -1, fill the gap) so a
+            // warp runs a single projection's code path
+            while ((items.size() - S.item_g0) % 32) items.push_back(Item{-1, 0, 0, 0});
             for (int j = 0; j < S.ncon; ++j) {
                 const ConDesc &c = s->cdesc[S.con0 + j];
                 if (c.type != type) continue;
