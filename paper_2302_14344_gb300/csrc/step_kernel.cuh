@@ -461,6 +461,7 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 1) step_kernel(StepParams P)
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ double red[4][SUBADMM_WARPS];
     __shared__ U ured[2][SUBADMM_WARPS];
+    __shared__ T tred[2][SUBADMM_WARPS];
     __shared__ int s_status;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr bool MIXED = sizeof(T) == 4;
@@ -575,13 +576,16 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 1) step_kernel(StepParams P)
             double tolc = P.tol;
             U tolb = tol_bits(T(0), tolc > 0.0 ? tolc : 0.0);
             const bool primal_stop = !P.stop_theta && P.tol > 0.0;
+            // the loop holds no FP64 instruction in the mixed form, not even a predicated one
+            // (an FP64 warp instruction issues for ~64 cycles on GB300 whatever its predicate)
+            const T theta_thT = (T)P.theta_th;
             int l = 0;
             pc.mark(PHASE_ASSEMBLE);
             for (;;) {
                 for (; l < P.max_iters; ++l) {
                     // ---- v-step through the affine map x = c + D w; y = beta x - lambda
                     const T *w = par ? W1 : W0;
-                    double tpart = 0.0;
+                    T tpart = (T)0;
                     if (CACHED) {
                         T acc = (T)0;
                         if (xv) {
@@ -603,7 +607,7 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 1) step_kernel(StepParams P)
                             acc += xc;
                             const T ynew = xbt * acc - LAM[xrow];
                             if (P.stop_theta) {
-                                const double d = (double)ynew - (double)yreg;
+                                const T d = ynew - yreg;
                                 tpart += d * d;
                             }
                             yprev = yreg;
@@ -630,7 +634,7 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 1) step_kernel(StepParams P)
                                 acc += V.tb[V.coff[t]];
                                 const T ynew = BT[t] * acc - LAM[V.row[t]];
                                 if (P.stop_theta) {
-                                    const double d = (double)ynew - (double)Y[t];
+                                    const T d = ynew - Y[t];
                                     tpart += d * d;
                                 }
                                 YO[t] = Y[t];
@@ -640,17 +644,18 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 1) step_kernel(StepParams P)
                         }
                     }
                     if (P.stop_theta) {
-                        tpart = warp_sum(tpart);
-                        if (lane == 0) red[l & 1][warp] = tpart;
+#pragma unroll
+                        for (int o = 16; o; o >>= 1) tpart += __shfl_xor_sync(0xffffffffu, tpart, o);
+                        if (lane == 0) tred[l & 1][warp] = tpart;
                     }
                     __syncthreads();
                     pc.mark(PHASE_VSTEP);
                     last_par = par;
                     iters = l + 1;
                     if (P.stop_theta) {
-                        th = 0.0;
-                        for (int q = 0; q < SUBADMM_WARPS; ++q) th += red[l & 1][q];
-                        if (l >= 1 && th < P.theta_th) { conv = 1; break; }
+                        T ths = (T)0;
+                        for (int q = 0; q < SUBADMM_WARPS; ++q) ths += tred[l & 1][q];
+                        if (l >= 1 && ths < theta_thT) { th = (double)ths; conv = 1; break; }
                     }
                     // ---- z-step (Sec. III-C); u = -lambda; max(|x - z|, |dz|) as bits
                     T *wn = par ? W0 : W1;
