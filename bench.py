@@ -137,6 +137,38 @@ class ClockSampler:
                 "samples": len(sms)}
 
 
+KERNEL_SOURCES = ("layout.h", "rigid_model.cuh", "step_kernel.cuh", "subadmm.cu")
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2302_14344_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def recorded_traffic(steps_per_launch: int):
+    """DRAM bytes per launch from the committed ncu summary, scaled to this launch length
+    (the per-step traffic is constant: descriptors and states are re-read every step), or
+    None when the kernel sources changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "step_kernel_robots64_traffic.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    vals = {}
+    for line in txt.splitlines():
+        if ":" in line and line.split(":")[0] in ("traffic_bytes_per_launch", "steps_per_launch",
+                                                 "source_sha256"):
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("source_sha256") != kernel_source_hash():
+        return None
+    return float(vals["traffic_bytes_per_launch"]) / float(vals["steps_per_launch"]) * steps_per_launch
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -200,6 +232,18 @@ def run_reference(args, rank: int, world: int):
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def batch_for_rank(rank: int, n_robots: int, h: float):
+    """The scenes a rank simulates: an independent seeded batch per rank (weak scaling; the
+    scenes never exchange data, so the ranks share no data-path collective)."""
+    import scenegen as sg
+    return sg.robots(seed=rank, n_robots=n_robots, h=h, tol_primal=1e-6, max_iters=1000)
+
+
+def whole_job_rate(world: int, steps: int, t_ms_max: float) -> float:
+    """Steps of every rank's batch per second over the slowest rank's time."""
+    return world * steps / (t_ms_max / 1e3)
 
 
 def time_form(subadmm, p, precision, args, stream, dev, local, dist, flush, sample_clocks):
@@ -281,7 +325,7 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     h = 2e-3
-    p = sg.robots(seed=rank, n_robots=args.robots, h=h, tol_primal=1e-6, max_iters=1000)
+    p = batch_for_rank(rank, args.robots, h)
     work = algorithmic_work(p)
     it_flops = work[0][0]
     st_flops = sum(w[1] for w in work)
@@ -293,7 +337,7 @@ def main():
                                                   dev, local, dist, flush, True)
     K = args.steps
     sizes = sim.sizes()
-    value = world * K / (t_ms / 1e3)
+    value = whole_job_rate(world, K, t_ms)
     total_iters = stats["total_iters"]
     flops = it_flops * total_iters + st_flops * K
     achieved = flops / (t_ms / 1e3) / 1e12
@@ -301,8 +345,9 @@ def main():
         peak, pipe = FP32_NOMINAL_TFLOPS, "FP32"
     else:
         peak, pipe = FP64_NOMINAL_TFLOPS, "FP64"
+    spl = max(1, min(args.steps_per_launch, K))
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": recorded_traffic(spl),
                 "note": f"{pipe} non-tensor pipe (iterations; the mixed form's per-step setup "
                         f"is FP64); peak = 152 SMs x lanes x 2 flops x 2.07 GHz; algorithmic "
                         f"flops of the triangular-solve form, "

@@ -22,7 +22,7 @@
  *     r_p = max |x - z|, r_d = max beta_i |z^{l+1} - z^l|       (Boyd's residuals)
  *   update each subsystem state from v-hat                      (Eq. ddyn)
  *
- * Readings where the paper is silent or garbled (each is also listed in the design notes):
+ * Readings where the paper is silent or garbled:
  *   - A_i = (2/h) M_i and b_i = (2/h) M_i v_k - C v_k + f: Eq. ddyn with
  *     v_{k+1} = 2 v-hat - v_k substituted; lambda is in force units.
  *   - Soft: lambda = -k (e + alpha q) / (1 + s alpha k) with q = sum beta_i^-1 y_i and

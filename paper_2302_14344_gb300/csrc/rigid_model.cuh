@@ -1,7 +1,7 @@
 // Rigid-body model on the device: the per-step construction of A_i, b_i (Eq. ddyn with
 // v_{k+1} = 2 v-hat - v_k substituted, so A_i = (2/h) M_i, b_i = (2/h) M_i v_k - C v_k + f)
 // and of the rows J_j, e_j of ball, revolute, PD-drive and plane-contact constraints
-// (Sec. II-A), plus the state update of Algorithm 1's last line.
+// (Sec. II-A), plus the state update that ends each step of Algorithm 1.
 //
 // Body record (17 doubles): m, I[3] (principal, body frame), p[3], q[4] (w, x, y, z),
 // v[3] (world), w[3] (body frame).  Generalized velocity per body: [v, w].

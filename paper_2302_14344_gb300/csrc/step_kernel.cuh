@@ -859,7 +859,7 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 1) step_kernel(StepParams P)
                 rd = dd;
             }
             pc.mark(PHASE_EXIT);
-            // v-hat out and state update of rigid bodies (Algorithm 1, last line)
+            // v-hat out and state update of rigid bodies (Algorithm 1, after the loop)
             for (int i = warp; i < S.nsub; i += SUBADMM_WARPS) {
                 const SubDesc &u = P.subs[S.sub0 + i];
                 const double *v = V.db + u.od_v;
