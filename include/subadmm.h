@@ -161,6 +161,24 @@ int sim_get(sim_t s, int what, int id, double *dst);
 int sim_read_state(sim_t s, double *dst);
 int sim_write_state(sim_t s, const double *src);
 
+/* sim_read_state without any device allocation.  The paper has no counterpart: this is a
+ * service of the library for callers that cannot allocate device memory when they read the
+ * state, such as a control loop that must not block on the allocator or an application
+ * whose framework owns all device memory under a fixed budget.  sim_read_state itself
+ * allocates nothing once the simulation is laid out, but its first call on a fresh
+ * simulation lays it out, which allocates; this entry point never does (no cudaMalloc,
+ * cudaFree or allocating library routine) and returns SIM_EINVAL until the first sim_step
+ * has laid the simulation out.
+ * It packs the state through a fixed 1 MiB staging array in device memory, which every GPU
+ * that loads the library holds until the process exits, so it reads at most 10082 bodies
+ * (13 doubles each) and returns SIM_EINVAL beyond that.  The first call on a device looks
+ * up that array's address; make that first call before any stream capture.  Every call,
+ * from any simulation on the device, shares the one array: calls whose GPU work overlaps
+ * (different host threads or streams at once) race and must be serialised by the caller.
+ * Each call overwrites all the entries it reads, so nothing needs clearing between calls.
+ * Output: dst as for sim_read_state; the call returns after the copy has completed. */
+int sim_read_state_noalloc(sim_t s, double *dst);
+
 /* Counts: out[0] scenes, out[1] subsystems, out[2] DOF, out[3] interfaces, out[4] rows,
  * out[5] side-rows, out[6] rigid bodies, out[7] on-chip bytes of the largest scene. */
 int sim_sizes(sim_t s, long long out[8]);

@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -722,6 +723,55 @@ int sim_read_state(sim_t s, double *dst)
     pack_state<<<grid, 256, 0, s->stream>>>(s->d_bodies, s->d_stage, s->nbodies);
     CK(cudaGetLastError(), "pack state");
     CK(cudaMemcpyAsync(dst, s->d_stage, sizeof(double) * 13 * s->nbodies, cudaMemcpyDeviceToHost, s->stream), "read state");
+    CK(cudaStreamSynchronize(s->stream), "read state sync");
+    return SIM_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Staging area of sim_read_state_noalloc: a fixed 1 MiB array in device memory, one copy on
+// every GPU that loads the library, held until the process exits.  Host code cannot use the
+// symbol as a device address; its address is looked up once per device.
+constexpr long long kNoallocStageDoubles = 131072;     // 1 MiB
+__device__ __align__(256) double g_noalloc_stage[kNoallocStageDoubles];
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+double *g_noalloc_addr[kNoallocMaxDevices] = {nullptr};
+
+}  // namespace
+
+extern "C" {
+
+int sim_read_state_noalloc(sim_t s, double *dst)
+{
+    if (!s || !dst) return SIM_EINVAL;
+    if (!s->finalized)
+        return fail(s, SIM_EINVAL, "sim_read_state_noalloc needs a simulation whose device memory "
+                                   "is laid out (after its first sim_step)");
+    if (s->nbodies == 0) return SIM_OK;
+    if (13 * s->nbodies > kNoallocStageDoubles)
+        return fail(s, SIM_EINVAL, "sim_read_state_noalloc holds at most 10082 bodies (1 MiB staging)");
+    const int dev = s->opt.device;
+    if (dev < 0 || dev >= kNoallocMaxDevices) return fail(s, SIM_EINVAL, "device ordinal too large");
+    CK(cudaSetDevice(dev), "cudaSetDevice");
+    double *stage = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        if (!g_noalloc_addr[dev]) {
+            void *p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_stage);
+            if (e != cudaSuccess) return cuda_fail(s, e, "cudaGetSymbolAddress of the staging area");
+            g_noalloc_addr[dev] = static_cast<double *>(p);
+        }
+        stage = g_noalloc_addr[dev];
+    }
+    const int grid = (int)std::min<long long>((13 * s->nbodies + 255) / 256, 1024);
+    pack_state<<<grid, 256, 0, s->stream>>>(s->d_bodies, stage, s->nbodies);
+    CK(cudaGetLastError(), "pack state");
+    CK(cudaMemcpyAsync(dst, stage, sizeof(double) * 13 * s->nbodies, cudaMemcpyDeviceToHost, s->stream),
+       "read state");
     CK(cudaStreamSynchronize(s->stream), "read state sync");
     return SIM_OK;
 }

@@ -30,7 +30,8 @@ SIM_GET_VHAT, SIM_GET_LAMBDA, SIM_GET_BODIES, SIM_GET_BETA, SIM_GET_Z = 0, 1, 2,
 # exported symbols of include/subadmm.h
 EXPORTS = ("sim_default_options", "sim_create", "sim_destroy", "sim_add_subsystem",
            "sim_add_interface", "sim_set_generic", "sim_step", "sim_residuals", "sim_get",
-           "sim_read_state", "sim_write_state", "sim_sizes", "sim_iteration_stats",
+           "sim_read_state", "sim_read_state_noalloc", "sim_write_state", "sim_sizes",
+           "sim_iteration_stats",
            "sim_phase_trace", "sim_sync", "sim_last_error")
 
 
@@ -84,6 +85,7 @@ def load(build_if_missing: bool = True):
             "sim_residuals": (C.c_int, [VP, C.c_int, PD]),
             "sim_get": (C.c_int, [VP, C.c_int, C.c_int, PD]),
             "sim_read_state": (C.c_int, [VP, VP]),
+            "sim_read_state_noalloc": (C.c_int, [VP, VP]),
             "sim_write_state": (C.c_int, [VP, VP]),
             "sim_sizes": (C.c_int, [VP, PL]),
             "sim_iteration_stats": (C.c_int, [VP, PL]),
@@ -177,6 +179,12 @@ def sim_get(h, what: int, id_: int, count: int) -> np.ndarray:
 def sim_read_state(h, dst_ptr: int) -> None:
     """dst_ptr: address of a host buffer of 13 doubles per body (e.g. a pinned tensor)."""
     _check(h, load().sim_read_state(h, VP(dst_ptr)))
+
+
+def sim_read_state_noalloc(h, dst_ptr: int) -> None:
+    """sim_read_state through the library's fixed device staging array: never allocates
+    device memory (for callers that cannot); at most 10082 bodies; calls share the array."""
+    _check(h, load().sim_read_state_noalloc(h, VP(dst_ptr)))
 
 
 def sim_write_state(h, src_ptr: int) -> None:
