@@ -183,6 +183,13 @@ int sim_read_state_noalloc(sim_t s, double *dst);
  * out[5] side-rows, out[6] rigid bodies, out[7] on-chip bytes of the largest scene. */
 int sim_sizes(sim_t s, long long out[8]);
 
+/* Where scene `scene` keeps its working set (lays the simulation out if needed):
+ * out[0] 0 if every per-subsystem array (J, the factor, W, D, ...) fits in the block's
+ * shared memory, 1 if they live in the simulation's global workspace (per-row arrays stay
+ * in shared memory); out[1] shared-memory bytes of the scene; out[2] its subsystems;
+ * out[3] bytes of the global workspace of the whole simulation. */
+int sim_scene_info(sim_t s, int scene, long long out[4]);
+
 /* Sum and maximum over scenes of the iterations of all steps since the last call, and the
  * number of scene-steps that ended without their stop rule holding; then clears them.
  * out[0] total iterations, out[1] max iterations of a scene-step, out[2] not converged,

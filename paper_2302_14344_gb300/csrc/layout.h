@@ -5,8 +5,8 @@
 #define SUBADMM_MAXS 8          // most sides one constraint may have (|S_j|)
 #define SUBADMM_THREADS 256     // threads of one scene's block
 #define SUBADMM_WARPS (SUBADMM_THREADS / 32)
-#define SUBADMM_MAXN 64         // largest subsystem DOF of the on-chip path
-#define SUBADMM_MAXM 96         // largest side-row count of one subsystem (on-chip path)
+#define SUBADMM_MAXN 1024       // largest subsystem DOF
+#define SUBADMM_MAXM 2048       // largest side-row count of one subsystem
 #define SUBADMM_PARAMS 23       // doubles of a rigid-model constraint's parameters
 #define SUBADMM_BODY 17         // doubles of a body record
 
@@ -35,12 +35,17 @@ struct SceneDesc {
     int nasm, asm_g0;      // assembly slots (constraint indices grouped by kind, -1 = idle)
     int sr_g0, row_g0;     // global offset of the scene's side-rows / rows (z, lambda state)
     // double region
-    int od_beta;
+    int od_beta;           // beta per subsystem
+    int od_flag;           // mixed form: 1 if the subsystem was factorised in FP64
     // T region (element offsets)
     int ot_x, ot_y, ot_z, ot_yo, ot_zo, ot_w0, ot_w1, ot_invb, ot_b;  // per side-row
     int ot_lam, ot_e, ot_invs, ot_kf, ot_al, ot_mu;              // per row
     // byte offsets of the T and int regions; total bytes
     int t_base, i_base, smem_bytes;
+    // per-subsystem arrays: in shared memory (sub_global = 0, offsets in the regions above)
+    // or in the global workspace at byte g_base (doubles) and g_base + g_tbase (T)
+    int sub_global;
+    long long g_base, g_tbase;
 };
 
 struct SubDesc {
@@ -51,9 +56,11 @@ struct SubDesc {
     int body0, nb;         // first global body, body count (rigid)
     int gen_off;           // pool offset of A (n*n) then b (n) (generic)
     int od_J, od_L, od_b;  // double region: J_ci rows (m x n), K then its factor L (n x n), b (n)
-    int od_v, od_id;       // double region: right-hand side then v-hat (n), 1 / L_pp (n)
+    int od_v, od_id;       // double region: v-hat (n); 1 / L_pp (FP64 form) or rhs (mixed) (n)
+    int od_t;              // double region: J v in the mixed refinement (m)
     int ot_L, ot_W, ot_g;  // T region: L (n x n, 1/L_pp on the diagonal), W rows (m x n), g (n)
     int ot_D, ot_c;        // T region: D (m x mpad), c (m)
+    int ot_s;              // T region: solve vector of the mixed recovery (n)
     int v_off;             // global offset of v-hat
 };
 
@@ -83,6 +90,7 @@ struct StepParams {
     const int *lists;
     const int *asm_order;  // per scene: constraint index of each assembly slot
     const double *pool;    // constant data and generic A, b
+    double *work;          // per-subsystem arrays of scenes too large for shared memory
     double *bodies;        // 17 doubles per body (state in and out)
     double *vhat;          // per DOF
     double *lam;           // per row: lambda of the last step (warm start state)

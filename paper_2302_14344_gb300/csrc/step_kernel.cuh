@@ -21,8 +21,9 @@
 // Eq. surrogate), so each row keeps one lambda shared by its sides and w = y + 2 lambda.
 //
 // T is the iteration type.  T = double: the map and the iterations in FP64.  T = float (the
-// mixed form): assembly, beta, K and its Cholesky factor stay FP64; W, g, D, c are formed
-// in FP32 from the rounded factor and the iterations run in FP32.  When the FP32 stop test
+// mixed form): assembly stays FP64; K and its Cholesky factor are FP32 for well-conditioned
+// blocks and FP64 for stiff or high-mass-ratio ones (spread of diag K above 1e3); W, g, D,
+// c are formed in FP32 and the iterations run in FP32.  When the FP32 stop test
 // passes, v-hat is recovered in FP64 and the primal residual re-evaluated as
 // max |J v-hat - z| in FP64; if that misses the tolerance, c is corrected by the FP64 - FP32
 // difference of x at the current iterate (iterative refinement) and the iterations resume.
@@ -147,19 +148,29 @@ struct PhaseClock {
 // shared-memory views of one scene
 template <typename T>
 struct View {
-    double *db;          // double region
-    T *tb;               // T region
+    double *db;          // double region (shared memory): scene arrays
+    T *tb;               // T region (shared memory): scene arrays
+    double *sdb;         // per-subsystem double arrays: shared memory, or global for a
+    T *stb;              // scene too large to hold them on chip; likewise for T
     int *row, *sub, *drow, *coff, *wbase, *mlen;   // per side-row tables
     Item *item;
     int *list;
 };
 
 template <typename T>
-__device__ View<T> scene_view(const SceneDesc &S, unsigned char *raw)
+__device__ View<T> scene_view(const StepParams &P, const SceneDesc &S, unsigned char *raw)
 {
     View<T> V;
     V.db = reinterpret_cast<double *>(raw);
     V.tb = reinterpret_cast<T *>(raw + S.t_base);
+    if (S.sub_global) {
+        unsigned char *w = reinterpret_cast<unsigned char *>(P.work) + S.g_base;
+        V.sdb = reinterpret_cast<double *>(w);
+        V.stb = reinterpret_cast<T *>(w + S.g_tbase);
+    } else {
+        V.sdb = V.db;
+        V.stb = V.tb;
+    }
     int *ib = reinterpret_cast<int *>(raw + S.i_base);
     V.row = ib;
     V.sub = ib + S.nsr;
@@ -229,18 +240,19 @@ __device__ void scene_setup(const StepParams &P, const SceneDesc &S, const View<
                             int *s_status, PhaseClock &pc)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    double *db = V.db;
-    T *tb = V.tb;
+    constexpr bool MIXED = sizeof(T) == 4;
+    double *db = V.db, *sdb = V.sdb;
+    T *tb = V.tb, *stb = V.stb;
     for (int i = warp; i < S.nsub; i += SUBADMM_WARPS) {
         const SubDesc &u = P.subs[S.sub0 + i];
-        double *J = db + u.od_J, *K = db + u.od_L;
+        double *J = sdb + u.od_J, *K = sdb + u.od_L;
         if (u.kind == KIND_RIGID) {
             for (int q = lane; q < u.m * u.n; q += 32) J[q] = 0.0;
             for (int q = lane; q < u.n * u.n; q += 32) K[q] = 0.0;
         } else {
             const double *A = P.pool + u.gen_off;
             for (int q = lane; q < u.n * u.n; q += 32) K[q] = A[q];
-            for (int q = lane; q < u.n; q += 32) db[u.od_b + q] = A[u.n * u.n + q];
+            for (int q = lane; q < u.n; q += 32) sdb[u.od_b + q] = A[u.n * u.n + q];
         }
     }
     __syncthreads();
@@ -252,11 +264,11 @@ __device__ void scene_setup(const StepParams &P, const SceneDesc &S, const View<
             double Ad[6], bb[6];
             body_dynamics(P.bodies + (size_t)(u.body0 + k) * SUBADMM_BODY, P.h, P.g0, P.g1, P.g2,
                           Ad, bb);
-            double *K = db + u.od_L;
+            double *K = sdb + u.od_L;
             for (int d = 0; d < 6; ++d) {
                 const int q = 6 * k + d;
                 K[q * u.n + q] = Ad[d];
-                db[u.od_b + q] = bb[d];
+                sdb[u.od_b + q] = bb[d];
             }
         }
     }
@@ -274,7 +286,7 @@ __device__ void scene_setup(const StepParams &P, const SceneDesc &S, const View<
             for (int s = 0; s < c.ns; ++s) {
                 const SubDesc &u = P.subs[S.sub0 + c.sub[s]];
                 for (int r = 0; r < c.rows; ++r) {
-                    double *Jr = db + u.od_J + (c.sr[s] + r - u.sr0) * u.n;
+                    double *Jr = sdb + u.od_J + (c.sr[s] + r - u.sr0) * u.n;
                     for (int q = 0; q < u.n; ++q) Jr[q] = Jp[r * u.n + q];
                 }
                 Jp += c.rows * u.n;
@@ -286,14 +298,14 @@ __device__ void scene_setup(const StepParams &P, const SceneDesc &S, const View<
             {
                 const SubDesc &u = P.subs[S.sub0 + c.sub[0]];
                 for (int r = 0; r < c.rows; ++r) {
-                    double *Jr = db + u.od_J + (c.sr[0] + r - u.sr0) * u.n + 6 * c.ba;
+                    double *Jr = sdb + u.od_J + (c.sr[0] + r - u.sr0) * u.n + 6 * c.ba;
                     for (int q = 0; q < 6; ++q) Jr[q] = Ja[6 * r + q];
                 }
             }
             if (c.side_b >= 0) {
                 const SubDesc &u = P.subs[S.sub0 + c.sub[c.side_b]];
                 for (int r = 0; r < c.rows; ++r) {
-                    double *Jr = db + u.od_J + (c.sr[c.side_b] + r - u.sr0) * u.n + 6 * c.bb;
+                    double *Jr = sdb + u.od_J + (c.sr[c.side_b] + r - u.sr0) * u.n + 6 * c.bb;
                     for (int q = 0; q < 6; ++q) Jr[q] = Jb[6 * r + q];
                 }
             }
@@ -301,60 +313,164 @@ __device__ void scene_setup(const StepParams &P, const SceneDesc &S, const View<
     }
     __syncthreads();
     pc.mark(PHASE_ASSEMBLE);
-    // per subsystem (one warp each): beta, K += beta J^T J, FP64 Cholesky, then the map in T
+    // per subsystem (one warp each): beta, K = A + beta J^T J and its Cholesky factor, then
+    // the map.  FP64 form: K and L in FP64, rounded into the T copy.  Mixed form: K and L in
+    // FP32 (the FP64 A, b and J stay for the FP64 recovery and refinement of v-hat).
     for (int i = warp; i < S.nsub; i += SUBADMM_WARPS) {
         const SubDesc &u = P.subs[S.sub0 + i];
         const int n = u.n, m = u.m, mp = u.mpad;
-        double *J = db + u.od_J, *K = db + u.od_L, *b = db + u.od_b, *idg = db + u.od_id;
-        T *LT = tb + u.ot_L, *W = tb + u.ot_W, *g = tb + u.ot_g, *D = tb + u.ot_D, *cc = tb + u.ot_c;
-        // beta_i = Tr(A_i) / Tr(J_ci^T J_ci)  (Sec. III-D)
-        double trA = 0.0, trJ = 0.0;
-        for (int q = lane; q < n; q += 32) trA += K[q * n + q];
-        for (int q = lane; q < m * n; q += 32) trJ += J[q] * J[q];
-        trA = warp_sum(trA);
-        trJ = warp_sum(trJ);
-        const double beta = P.beta_fixed ? P.rho : (trJ > 0.0 ? trA / trJ : 1.0);
-        if (lane == 0) {
-            db[S.od_beta + i] = beta;
-            P.beta[S.sub0 + i] = beta;
-        }
-        // K_i = A_i + beta_i J_ci^T J_ci (lower triangle)
-        for (int t = lane; t < n * (n + 1) / 2; t += 32) {
-            int p, q;
-            tri_index(t, p, q);
-            double acc = 0.0;
-            for (int r = 0; r < m; ++r) acc += J[r * n + p] * J[r * n + q];
-            K[p * n + q] += beta * acc;
-        }
-        __syncwarp();
-        // right-looking Cholesky in FP64, in place (lower triangle); 1/L_kk kept in idg
+        double *J = sdb + u.od_J, *K = sdb + u.od_L, *b = sdb + u.od_b, *idg = sdb + u.od_id;
+        T *LT = stb + u.ot_L, *W = stb + u.ot_W, *g = stb + u.ot_g, *D = stb + u.ot_D, *cc = stb + u.ot_c;
         bool ok = true;
-        for (int k = 0; k < n; ++k) {
-            const double d = K[k * n + k];
-            if (!(d > 0.0) || !isfinite(d)) { ok = false; break; }
-            const double ilkk = rsqrt(d);
-            __syncwarp();
-            for (int r = k + lane; r < n; r += 32) K[r * n + k] = (r == k) ? d * ilkk : K[r * n + k] * ilkk;
-            if (lane == 0) idg[k] = ilkk;
-            __syncwarp();
-            for (int r = k + 1 + lane; r < n; r += 32) {
-                const double lrk = K[r * n + k];
-                for (int q = k + 1; q <= r; ++q) K[r * n + q] -= lrk * K[q * n + k];
+        if (!MIXED) {
+            // beta_i = Tr(A_i) / Tr(J_ci^T J_ci)  (Sec. III-D)
+            double trA = 0.0, trJ = 0.0;
+            for (int q = lane; q < n; q += 32) trA += K[q * n + q];
+            for (int q = lane; q < m * n; q += 32) trJ += J[q] * J[q];
+            trA = warp_sum(trA);
+            trJ = warp_sum(trJ);
+            const double beta = P.beta_fixed ? P.rho : (trJ > 0.0 ? trA / trJ : 1.0);
+            if (lane == 0) {
+                db[S.od_beta + i] = beta;
+                P.beta[S.sub0 + i] = beta;
+            }
+            // K_i = A_i + beta_i J_ci^T J_ci (lower triangle)
+            for (int t = lane; t < n * (n + 1) / 2; t += 32) {
+                int p, q;
+                tri_index(t, p, q);
+                double acc = 0.0;
+                for (int r = 0; r < m; ++r) acc += J[r * n + p] * J[r * n + q];
+                K[p * n + q] += beta * acc;
             }
             __syncwarp();
+            // right-looking Cholesky in FP64, in place (lower triangle); 1/L_kk kept in idg
+            for (int k = 0; k < n; ++k) {
+                const double d = K[k * n + k];
+                if (!(d > 0.0) || !isfinite(d)) { ok = false; break; }
+                const double ilkk = rsqrt(d);
+                __syncwarp();
+                for (int r = k + lane; r < n; r += 32) K[r * n + k] = (r == k) ? d * ilkk : K[r * n + k] * ilkk;
+                if (lane == 0) idg[k] = ilkk;
+                __syncwarp();
+                for (int r = k + 1 + lane; r < n; r += 32) {
+                    const double lrk = K[r * n + k];
+                    for (int q = k + 1; q <= r; ++q) K[r * n + q] -= lrk * K[q * n + k];
+                }
+                __syncwarp();
+            }
+            if (!ok) {
+                if (lane == 0) *s_status = ST_NOTSPD;
+                continue;
+            }
+            // the map in T: LT = L (with 1/L_pp on its diagonal), W rows = J rows, g = b
+            for (int q = lane; q < n * n; q += 32) {
+                const int p = q / n, r = q - p * n;
+                LT[q] = (r == p) ? (T)idg[p] : (T)K[q];
+            }
+            for (int q = lane; q < m * n; q += 32) W[q] = (T)J[q];
+            for (int q = lane; q < n; q += 32) g[q] = (T)b[q];
+            __syncwarp();
+        } else {
+            // rounded copies: W rows = J rows, LT = A (lower triangle), g = b
+            for (int q = lane; q < m * n; q += 32) W[q] = (T)J[q];
+            for (int q = lane; q < n * n; q += 32) LT[q] = (T)K[q];
+            for (int q = lane; q < n; q += 32) g[q] = (T)b[q];
+            __syncwarp();
+            T trA = (T)0, trJ = (T)0;
+            for (int q = lane; q < n; q += 32) trA += LT[q * n + q];
+            for (int q = lane; q < m * n; q += 32) trJ += W[q] * W[q];
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                trA += __shfl_xor_sync(0xffffffffu, trA, o);
+                trJ += __shfl_xor_sync(0xffffffffu, trJ, o);
+            }
+            const T beta = P.beta_fixed ? (T)P.rho : (trJ > (T)0 ? trA / trJ : (T)1);
+            if (lane == 0) {
+                db[S.od_beta + i] = (double)beta;
+                P.beta[S.sub0 + i] = (double)beta;
+            }
+            // stiffness test: the spread of K's diagonal bounds its condition number from
+            // below; a stiff or high-mass-ratio block (spread > 1e3) is factorised in FP64
+            T dmax = (T)0, dmin = (T)3.0e38;
+            for (int p = lane; p < n; p += 32) {
+                T cs = (T)0;
+                for (int r = 0; r < m; ++r) cs += W[r * n + p] * W[r * n + p];
+                const T dk = LT[p * n + p] + beta * cs;
+                dmax = dk > dmax ? dk : dmax;
+                dmin = dk < dmin ? dk : dmin;
+            }
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                const T a = __shfl_xor_sync(0xffffffffu, dmax, o);
+                const T c = __shfl_xor_sync(0xffffffffu, dmin, o);
+                dmax = a > dmax ? a : dmax;
+                dmin = c < dmin ? c : dmin;
+            }
+            const bool stiff = !(dmin > (T)0) || dmax > (T)1.0e3 * dmin;
+            if (lane == 0) db[S.od_flag + i] = stiff ? 1.0 : 0.0;
+            if (stiff) {
+                const double b64 = (double)beta;
+                for (int t = lane; t < n * (n + 1) / 2; t += 32) {
+                    int p, q;
+                    tri_index(t, p, q);
+                    double acc = 0.0;
+                    for (int r = 0; r < m; ++r) acc += J[r * n + p] * J[r * n + q];
+                    K[p * n + q] += b64 * acc;
+                }
+                __syncwarp();
+                for (int k = 0; k < n; ++k) {
+                    const double d = K[k * n + k];
+                    if (!(d > 0.0) || !isfinite(d)) { ok = false; break; }
+                    const double ilkk = rsqrt(d);
+                    __syncwarp();
+                    for (int r = k + lane; r < n; r += 32) K[r * n + k] = (r == k) ? d * ilkk : K[r * n + k] * ilkk;
+                    if (lane == 0) idg[k] = ilkk;
+                    __syncwarp();
+                    for (int r = k + 1 + lane; r < n; r += 32) {
+                        const double lrk = K[r * n + k];
+                        for (int q = k + 1; q <= r; ++q) K[r * n + q] -= lrk * K[q * n + k];
+                    }
+                    __syncwarp();
+                }
+                if (!ok) {
+                    if (lane == 0) *s_status = ST_NOTSPD;
+                    continue;
+                }
+                for (int q = lane; q < n * n; q += 32) {
+                    const int p = q / n, r = q - p * n;
+                    LT[q] = (r == p) ? (T)idg[p] : (T)K[q];
+                }
+                __syncwarp();
+            } else {
+                for (int t = lane; t < n * (n + 1) / 2; t += 32) {
+                    int p, q;
+                    tri_index(t, p, q);
+                    T acc = (T)0;
+                    for (int r = 0; r < m; ++r) acc += W[r * n + p] * W[r * n + q];
+                    LT[p * n + q] += beta * acc;
+                }
+                __syncwarp();
+                // right-looking Cholesky in FP32, in place; the diagonal ends as 1/L_pp
+                for (int k = 0; k < n; ++k) {
+                    const T d = LT[k * n + k];
+                    if (!(d > (T)0) || !isfinite(d)) { ok = false; break; }
+                    const T ilkk = rsq(d);
+                    __syncwarp();
+                    for (int r = k + 1 + lane; r < n; r += 32) LT[r * n + k] *= ilkk;
+                    __syncwarp();
+                    if (lane == 0) LT[k * n + k] = ilkk;
+                    for (int r = k + 1 + lane; r < n; r += 32) {
+                        const T lrk = LT[r * n + k];
+                        for (int q = k + 1; q <= r; ++q) LT[r * n + q] -= lrk * LT[q * n + k];
+                    }
+                    __syncwarp();
+                }
+                if (!ok) {
+                    if (lane == 0) *s_status = ST_NOTSPD;
+                    continue;
+                }
+            }
         }
-        if (!ok) {
-            if (lane == 0) *s_status = ST_NOTSPD;
-            continue;
-        }
-        // the map in T: LT = L (with 1/L_pp on its diagonal), W rows = J rows, g = b
-        for (int q = lane; q < n * n; q += 32) {
-            const int p = q / n, r = q - p * n;
-            LT[q] = (r == p) ? (T)idg[p] : (T)K[q];
-        }
-        for (int q = lane; q < m * n; q += 32) W[q] = (T)J[q];
-        for (int q = lane; q < n; q += 32) g[q] = (T)b[q];
-        __syncwarp();
         // W rows <- L^-1 J rows, g <- L^-1 b (forward substitution, lane per right-hand side)
         for (int t = lane; t <= m; t += 32) {
             T *x = (t < m) ? W + t * n : g;
@@ -417,38 +533,101 @@ __device__ void scene_setup(const StepParams &P, const SceneDesc &S, const View<
     __syncthreads();
 }
 
-// v-hat of the last v-step in FP64: v = L^-T L^-1 (b + J^T w) into od_v (warp per subsystem)
+// Triangular solves with the T factor (1/L_pp on its diagonal), in place on s (warp).
+template <typename T>
+__device__ __forceinline__ void warp_chol_solve(const T *LT, T *s, int n)
+{
+    const int lane = threadIdx.x & 31;
+    for (int p = 0; p < n; ++p) {              // L y = s (column-oriented)
+        const T yp = s[p] * LT[p * n + p];
+        __syncwarp();
+        if (lane == 0) s[p] = yp;
+        for (int q = p + 1 + lane; q < n; q += 32) s[q] -= LT[q * n + p] * yp;
+        __syncwarp();
+    }
+    for (int p = n - 1; p >= 0; --p) {         // L^T v = y
+        const T vp = s[p] * LT[p * n + p];
+        __syncwarp();
+        if (lane == 0) s[p] = vp;
+        for (int q = lane; q < p; q += 32) s[q] -= LT[p * n + q] * vp;
+        __syncwarp();
+    }
+}
+
+// v-hat of the last v-step, v = K^-1 (b + J^T w), in FP64 (warp per subsystem) into od_v.
+// With an FP64 factor (FP64 form, or a stiff block of the mixed form): two triangular
+// solves.  With an FP32 factor: a solve, then one step of iterative refinement with the
+// residual b + J^T w - K v formed in FP64 from A (kept in od_L) and J:
+// K v = A v + beta J^T (J v).
 template <typename T>
 __device__ void recover_v(const StepParams &P, const SceneDesc &S, const View<T> &V, const T *w)
 {
+    constexpr bool MIXED = sizeof(T) == 4;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int i = warp; i < S.nsub; i += SUBADMM_WARPS) {
         const SubDesc &u = P.subs[S.sub0 + i];
         const int n = u.n, m = u.m;
-        const double *J = V.db + u.od_J, *Lf = V.db + u.od_L, *b = V.db + u.od_b;
-        const double *idg = V.db + u.od_id;
-        double *v = V.db + u.od_v;
+        // od_L holds the FP64 factor L (FP64 form) or A itself (mixed form)
+        const double *J = V.sdb + u.od_J, *Lf = V.sdb + u.od_L, *b = V.sdb + u.od_b;
+        double *idg = V.sdb + u.od_id;
+        double *v = V.sdb + u.od_v;
         const T *wi = w + u.sr0;
+        if (!MIXED || V.db[S.od_flag + i] != 0.0) {
+            for (int p = lane; p < n; p += 32) {
+                double acc = b[p];
+                for (int r = 0; r < m; ++r) acc += J[r * n + p] * (double)wi[r];
+                v[p] = acc;
+            }
+            __syncwarp();
+            for (int p = 0; p < n; ++p) {          // L y = rhs (column-oriented)
+                const double yp = v[p] * idg[p];
+                __syncwarp();
+                if (lane == 0) v[p] = yp;
+                for (int q = p + 1 + lane; q < n; q += 32) v[q] -= Lf[q * n + p] * yp;
+                __syncwarp();
+            }
+            for (int p = n - 1; p >= 0; --p) {     // L^T v = y
+                const double vp = v[p] * idg[p];
+                __syncwarp();
+                if (lane == 0) v[p] = vp;
+                for (int q = lane; q < p; q += 32) v[q] -= Lf[p * n + q] * vp;
+                __syncwarp();
+            }
+            continue;
+        }
+        const T *LT = V.stb + u.ot_L;
+        T *s = V.stb + u.ot_s;
+        double *rhs = idg;                          // (unused by the mixed factor)
+        double *t = V.sdb + u.od_t;
+        const double beta = V.db[S.od_beta + i];
         for (int p = lane; p < n; p += 32) {
             double acc = b[p];
             for (int r = 0; r < m; ++r) acc += J[r * n + p] * (double)wi[r];
-            v[p] = acc;
+            rhs[p] = acc;
+            s[p] = (T)acc;
         }
         __syncwarp();
-        for (int p = 0; p < n; ++p) {          // L y = rhs (column-oriented)
-            const double yp = v[p] * idg[p];
-            __syncwarp();
-            if (lane == 0) v[p] = yp;
-            for (int q = p + 1 + lane; q < n; q += 32) v[q] -= Lf[q * n + p] * yp;
-            __syncwarp();
+        warp_chol_solve<T>(LT, s, n);
+        for (int p = lane; p < n; p += 32) v[p] = (double)s[p];
+        __syncwarp();
+        // one refinement step: r = rhs - A v - beta J^T (J v); v += K^-1 r
+        for (int r = lane; r < m; r += 32) {
+            double acc = 0.0;
+            for (int p = 0; p < n; ++p) acc += J[r * n + p] * v[p];
+            t[r] = acc;
         }
-        for (int p = n - 1; p >= 0; --p) {     // L^T v = y
-            const double vp = v[p] * idg[p];
-            __syncwarp();
-            if (lane == 0) v[p] = vp;
-            for (int q = lane; q < p; q += 32) v[q] -= Lf[p * n + q] * vp;
-            __syncwarp();
+        __syncwarp();
+        for (int p = lane; p < n; p += 32) {
+            double acc = rhs[p];
+            for (int q = 0; q < n; ++q) acc -= Lf[p * n + q] * v[q];     // A v
+            double jt = 0.0;
+            for (int r = 0; r < m; ++r) jt += J[r * n + p] * t[r];
+            s[p] = (T)(acc - beta * jt);
         }
+        __syncwarp();
+        warp_chol_solve<T>(LT, s, n);
+        for (int p = lane; p < n; p += 32) v[p] += (double)s[p];
+        __syncwarp();
     }
 }
 
@@ -468,7 +647,7 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 1) step_kernel(StepParams P)
 
     for (int sc = blockIdx.x; sc < P.nscenes; sc += gridDim.x) {
         const SceneDesc S = P.scenes[sc];
-        const View<T> V = scene_view<T>(S, smraw);
+        const View<T> V = scene_view<T>(P, S, smraw);
         T *X = V.tb + S.ot_x, *Y = V.tb + S.ot_y, *Z = V.tb + S.ot_z, *LAM = V.tb + S.ot_lam;
         T *YO = V.tb + S.ot_yo, *ZO = V.tb + S.ot_zo;
         T *E = V.tb + S.ot_e, *INVB = V.tb + S.ot_invb, *BT = V.tb + S.ot_b;
@@ -537,11 +716,11 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 1) step_kernel(StepParams P)
                     xwbo = V.wbase[xt];
                     xnv = (V.mlen[xt] + VN - 1) / VN;
                     xrow = V.row[xt];
-                    xc = V.tb[V.coff[xt]];
+                    xc = V.stb[V.coff[xt]];
                     xbt = BT[xt];
                     yreg = Y[xt];
                     yprev = yreg;
-                    const VT *Dr = reinterpret_cast<const VT *>(V.tb + xdro);
+                    const VT *Dr = reinterpret_cast<const VT *>(V.stb + xdro);
 #pragma unroll
                     for (int q = 0; q < MAXC; ++q)
                         if (xgl + q * SPLIT < xnv) dreg[q] = Dr[xgl + q * SPLIT];
@@ -623,7 +802,7 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 1) step_kernel(StepParams P)
                             const int m = t < S.nsr ? V.mlen[t] : 0;
                             T acc = (T)0;
                             if (m > 0) {
-                                const VT *Dr = reinterpret_cast<const VT *>(V.tb + V.drow[t]);
+                                const VT *Dr = reinterpret_cast<const VT *>(V.stb + V.drow[t]);
                                 const VT *wb = reinterpret_cast<const VT *>(w + V.wbase[t]);
                                 const int nv = (m + VN - 1) / VN;
                                 for (int c = xgl; c < nv; c += SPLIT) acc = vdot(Dr[c], wb[c], acc);
@@ -631,7 +810,7 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 1) step_kernel(StepParams P)
 #pragma unroll
                             for (int o = SPLIT / 2; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
                             if (m > 0 && xgl == 0) {
-                                acc += V.tb[V.coff[t]];
+                                acc += V.stb[V.coff[t]];
                                 const T ynew = BT[t] * acc - LAM[V.row[t]];
                                 if (P.stop_theta) {
                                     const T d = ynew - Y[t];
@@ -820,19 +999,19 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 1) step_kernel(StepParams P)
                         if (V.mlen[t] == 0) continue;
                         const SubDesc &u = P.subs[S.sub0 + V.sub[t]];
                         const int lr = t - u.sr0, n = u.n;
-                        const double *Jr = V.db + u.od_J + lr * n;
-                        const double *v = V.db + u.od_v;
+                        const double *Jr = V.sdb + u.od_J + lr * n;
+                        const double *v = V.sdb + u.od_v;
                         double x = 0.0;
                         for (int p = 0; p < n; ++p) x += Jr[p] * v[p];
                         part = nanmax(part, fabs(x - (double)Z[t]));
-                        V.tb[V.coff[t]] += (T)(x - (double)X[t]);
+                        V.stb[V.coff[t]] += (T)(x - (double)X[t]);
                     }
                     double d0 = 0.0, d2 = 0.0;
                     block_reduce3(red, d0, part, d2);
                     if (part > P.tol && l + 1 < P.max_iters) {
                         tolc *= 0.5;
                         tolb = tol_bits(T(0), tolc);
-                        if (CACHED && xv) xc = V.tb[V.coff[xt]];
+                        if (CACHED && xv) xc = V.stb[V.coff[xt]];
                         conv = 0;
                         ++l;
                         continue;
@@ -862,7 +1041,7 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 1) step_kernel(StepParams P)
             // v-hat out and state update of rigid bodies (Algorithm 1, after the loop)
             for (int i = warp; i < S.nsub; i += SUBADMM_WARPS) {
                 const SubDesc &u = P.subs[S.sub0 + i];
-                const double *v = V.db + u.od_v;
+                const double *v = V.sdb + u.od_v;
                 for (int p = lane; p < u.n; p += 32) P.vhat[u.v_off + p] = v[p];
                 if (u.kind != KIND_RIGID) continue;
                 for (int k = lane; k < u.nb; k += 32)

@@ -67,6 +67,8 @@ struct sim_s {
     double *d_z = nullptr, *d_beta = nullptr, *d_res = nullptr, *d_stage = nullptr;
     long long *d_stats = nullptr;
     long long *d_phase = nullptr;  // phase tracer counters (8 per scene) when enabled
+    double *d_work = nullptr;      // per-subsystem arrays of scenes too large for shared memory
+    long long work_bytes = 0;
     size_t pool_size = 0;
 };
 
@@ -137,6 +139,8 @@ void free_device(sim_t s)
     cudaFree(s->d_beta); cudaFree(s->d_res); cudaFree(s->d_stats); cudaFree(s->d_stage);
     cudaFree(s->d_phase);
     s->d_phase = nullptr;
+    cudaFree(s->d_work);
+    s->d_work = nullptr;
     s->d_scenes = nullptr; s->d_subs = nullptr; s->d_cons = nullptr; s->d_pool = nullptr;
     s->d_bodies = nullptr; s->d_vhat = nullptr; s->d_lam = nullptr; s->d_z = nullptr;
     s->d_beta = nullptr; s->d_res = nullptr; s->d_stats = nullptr; s->d_stage = nullptr;
@@ -190,6 +194,11 @@ int finalize(sim_t s)
     std::vector<Item> items;
     std::vector<int> lists;
     std::vector<int> asm_order;
+    int dev_max_smem = 0;
+    CK(cudaDeviceGetAttribute(&dev_max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->opt.device),
+       "attribute");
+    const int smem_budget = dev_max_smem - 1024;   // static shared memory of the kernel
+    long long work_bytes = 0;
     int max_nsr = 0, max_items = 0, max_sides = 0, max_mpad = 0;
     s->sdesc.assign(nsubs, SubDesc{});
     s->cdesc.assign(ncons, ConDesc{});
@@ -322,47 +331,75 @@ int finalize(sim_t s)
         S.nitem = (int)items.size() - S.item_g0;
         S.nlist = (int)lists.size() - S.list_g0;
         max_items = std::max(max_items, S.nitem);
-        // shared-memory layout: doubles (factors), then T (iteration arrays), then ints.
-        // T offsets are whole 16-byte vectors so D rows and w segments load as vectors.
-        int od = 0, ot = 0;
-        auto tal = [&](int v) { return (v + vn - 1) / vn * vn; };
+        // per-subsystem arrays (doubles: J, K or A, b, v, 1/L_pp or rhs, J v; T: L, W rows,
+        // g, D, c, s).  T offsets are whole 16-byte vectors so D rows load as vectors.
+        auto tal = [&](long long v) { return (v + vn - 1) / vn * vn; };
+        long long sd = 0, st = 0;
         for (int i = 0; i < S.nsub; ++i) {
             SubDesc &u = s->sdesc[S.sub0 + i];
             if (u.m > SUBADMM_MAXM)
-                return fail(s, SIM_EINVAL, "a subsystem has more constraint rows than the on-chip path holds");
-            u.od_J = od; od += u.m * u.n;
-            u.od_L = od; od += u.n * u.n;
-            u.od_b = od; od += u.n;
-            u.od_v = od; od += u.n;
-            u.od_id = od; od += u.n;
-            u.ot_L = ot; ot += u.n * u.n;
-            u.ot_W = ot; ot += u.m * u.n;
-            u.ot_g = ot; ot = tal(ot + u.n);
-            u.ot_D = ot; ot = tal(ot + u.m * u.mpad);
-            u.ot_c = ot; ot = tal(ot + u.m);
+                return fail(s, SIM_EINVAL, "a subsystem has more constraint rows than supported (2048)");
+            u.od_J = (int)sd; sd += (long long)u.m * u.n;
+            u.od_L = (int)sd; sd += (long long)u.n * u.n;
+            u.od_b = (int)sd; sd += u.n;
+            u.od_v = (int)sd; sd += u.n;
+            u.od_id = (int)sd; sd += u.n;
+            u.od_t = (int)sd; sd += u.m;
+            u.ot_L = (int)st; st += (long long)u.n * u.n;
+            u.ot_W = (int)st; st += (long long)u.m * u.n;
+            u.ot_g = (int)st; st = tal(st + u.n);
+            u.ot_D = (int)st; st = tal(st + (long long)u.m * u.mpad);
+            u.ot_c = (int)st; st = tal(st + u.m);
+            u.ot_s = (int)st; st = tal(st + u.n);
+            if (sd > (1LL << 30) || st > (1LL << 30)) return fail(s, SIM_EINVAL, "scene too large");
         }
-        S.od_beta = od; od += S.nsub;
-        // per-side-row arrays are contiguous from ot_x up to ot_lam (zeroed together)
-        S.ot_x = ot; ot = tal(ot + S.nsr);
-        S.ot_y = ot; ot = tal(ot + S.nsr);
-        S.ot_z = ot; ot = tal(ot + S.nsr);
-        S.ot_yo = ot; ot = tal(ot + S.nsr);
-        S.ot_zo = ot; ot = tal(ot + S.nsr);
-        S.ot_w0 = ot; ot = tal(ot + S.nsr);
-        S.ot_w1 = ot; ot = tal(ot + S.nsr);
-        S.ot_invb = ot; ot = tal(ot + S.nsr);
-        S.ot_b = ot; ot = tal(ot + S.nsr);
-        S.ot_lam = ot; ot += S.nrow;
-        S.ot_e = ot; ot += S.nrow;
-        S.ot_invs = ot; ot += S.nrow;
-        S.ot_kf = ot; ot += S.nrow;
-        S.ot_al = ot; ot += S.nrow;
-        S.ot_mu = ot; ot += S.nrow;
+        // scene arrays (shared memory): per side-row arrays contiguous from ot_x to ot_lam
+        const long long scd = 2LL * S.nsub;
+        const long long scene_t = tal((long long)S.nsr) * 9 + 6LL * S.nrow;
         const int tsize = s->opt.precision == SIM_MIXED ? 4 : 8;
-        const long long t_base = ((long long)od * 8 + 15) / 16 * 16;
-        const long long i_base = (t_base + (long long)ot * tsize + 15) / 16 * 16;
-        const long long bytes = i_base + 4LL * (6LL * S.nsr + 4LL * S.nitem + S.nlist);
-        if (bytes > (1LL << 30)) return fail(s, SIM_EINVAL, "scene too large");
+        const long long ints = 6LL * S.nsr + 4LL * S.nitem + S.nlist;
+        auto bytes_of = [&](long long d, long long t) {
+            const long long tb = (d * 8 + 15) / 16 * 16;
+            const long long ib = (tb + t * tsize + 15) / 16 * 16;
+            return ib + 4 * ints;
+        };
+        const long long onchip = bytes_of(sd + scd, st + scene_t);
+        S.sub_global = onchip > (long long)smem_budget ? 1 : 0;
+        long long od = 0, ot = 0;
+        if (S.sub_global) {
+            S.g_base = work_bytes;
+            S.g_tbase = (sd * 8 + 255) / 256 * 256;
+            work_bytes += (S.g_tbase + st * tsize + 255) / 256 * 256;
+        } else {
+            S.g_base = 0; S.g_tbase = 0;
+            od = sd; ot = st;
+        }
+        S.od_beta = (int)od; od += S.nsub;
+        S.od_flag = (int)od; od += S.nsub;
+        S.ot_x = (int)ot; ot = tal(ot + S.nsr);
+        S.ot_y = (int)ot; ot = tal(ot + S.nsr);
+        S.ot_z = (int)ot; ot = tal(ot + S.nsr);
+        S.ot_yo = (int)ot; ot = tal(ot + S.nsr);
+        S.ot_zo = (int)ot; ot = tal(ot + S.nsr);
+        S.ot_w0 = (int)ot; ot = tal(ot + S.nsr);
+        S.ot_w1 = (int)ot; ot = tal(ot + S.nsr);
+        S.ot_invb = (int)ot; ot = tal(ot + S.nsr);
+        S.ot_b = (int)ot; ot = tal(ot + S.nsr);
+        S.ot_lam = (int)ot; ot += S.nrow;
+        S.ot_e = (int)ot; ot += S.nrow;
+        S.ot_invs = (int)ot; ot += S.nrow;
+        S.ot_kf = (int)ot; ot += S.nrow;
+        S.ot_al = (int)ot; ot += S.nrow;
+        S.ot_mu = (int)ot; ot += S.nrow;
+        const long long t_base = (od * 8 + 15) / 16 * 16;
+        const long long i_base = (t_base + ot * tsize + 15) / 16 * 16;
+        const long long bytes = i_base + 4 * ints;
+        if (bytes > (long long)smem_budget) {
+            char buf[256];
+            snprintf(buf, sizeof buf, "scene %d needs %lld bytes of shared memory for its per-row "
+                     "arrays alone; at most %d are available", sc, bytes, smem_budget);
+            return fail(s, SIM_EINVAL, buf);
+        }
         S.t_base = (int)t_base;
         S.i_base = (int)i_base;
         S.smem_bytes = (int)bytes;
@@ -373,17 +410,12 @@ int finalize(sim_t s)
     }
     s->dof = dof; s->nrows = rows_g; s->nsr = sr_g;
     s->nbodies = (long long)(bodies.size() / SUBADMM_BODY);
-    int dev_max = 0;
-    CK(cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->opt.device), "attribute");
-    const int static_smem = (int)(sizeof(double) * 2 * 4 * SUBADMM_WARPS + 64);
-    // (checked again at launch against the kernel's own static shared memory)
-    if (max_smem + static_smem > dev_max) {
-        char buf[256];
-        snprintf(buf, sizeof buf, "a scene needs %d bytes of shared memory; the on-chip path holds %d",
-                 max_smem, dev_max - static_smem);
-        return fail(s, SIM_EINVAL, buf);
-    }
     s->max_smem = max_smem;
+    if (work_bytes > 0) {
+        cudaError_t e = cudaMalloc((void **)&s->d_work, (size_t)work_bytes);
+        if (e != cudaSuccess) return fail(s, SIM_ENOMEM, std::string("cudaMalloc workspace: ") + cudaGetErrorString(e));
+    }
+    s->work_bytes = work_bytes;
     s->pool_gen_off.assign(nsubs, 0);
     for (int k = 0; k < nsubs; ++k) s->pool_gen_off[k] = s->sdesc[k].gen_off;
     int rc;
@@ -521,11 +553,11 @@ int sim_add_subsystem(sim_t s, int scene, int kind, int count, const double *dat
     HostSub u;
     u.scene = scene;
     if (kind == SIM_SUB_GENERIC) {
-        if (count > SUBADMM_MAXN) return fail(s, SIM_EINVAL, "generic subsystem larger than the on-chip path");
+        if (count > SUBADMM_MAXN) return fail(s, SIM_EINVAL, "generic subsystem larger than 1024 DOF");
         u.kind = KIND_GENERIC; u.n = count;
         u.Ab.assign(data, data + (size_t)count * count + count);
     } else if (kind == SIM_SUB_RIGID) {
-        if (6 * count > SUBADMM_MAXN) return fail(s, SIM_EINVAL, "rigid subsystem larger than the on-chip path");
+        if (6 * count > SUBADMM_MAXN) return fail(s, SIM_EINVAL, "rigid subsystem larger than 1024 DOF");
         u.kind = KIND_RIGID; u.nb = count; u.n = 6 * count;
         u.bodies.assign(data, data + (size_t)count * SUBADMM_BODY);
         for (int b = 0; b < count; ++b) {
@@ -624,6 +656,7 @@ int sim_step(sim_t s, int n_steps)
     StepParams P;
     P.scenes = s->d_scenes; P.subs = s->d_subs; P.cons = s->d_cons; P.pool = s->d_pool;
     P.bodies = s->d_bodies; P.vhat = s->d_vhat; P.lam = s->d_lam; P.z = s->d_z;
+    P.work = s->d_work;
     P.beta = s->d_beta; P.res = s->d_res; P.stats = s->d_stats; P.phase = s->d_phase;
     P.nscenes = s->nscenes;
     P.n_steps = n_steps;
@@ -802,6 +835,20 @@ int sim_sizes(sim_t s, long long out[8])
     out[5] = s->nsr;
     out[6] = s->nbodies;
     out[7] = s->max_smem;
+    return SIM_OK;
+}
+
+int sim_scene_info(sim_t s, int scene, long long out[4])
+{
+    if (!s || !out) return SIM_EINVAL;
+    int rc = finalize(s);
+    if (rc) return rc;
+    if (scene < 0 || scene >= s->nscenes) return fail(s, SIM_EINVAL, "scene out of range");
+    const SceneDesc &S = s->scenes[scene];
+    out[0] = S.sub_global;
+    out[1] = S.smem_bytes;
+    out[2] = S.nsub;
+    out[3] = s->work_bytes;
     return SIM_OK;
 }
 

@@ -31,7 +31,7 @@ SIM_GET_VHAT, SIM_GET_LAMBDA, SIM_GET_BODIES, SIM_GET_BETA, SIM_GET_Z = 0, 1, 2,
 EXPORTS = ("sim_default_options", "sim_create", "sim_destroy", "sim_add_subsystem",
            "sim_add_interface", "sim_set_generic", "sim_step", "sim_residuals", "sim_get",
            "sim_read_state", "sim_read_state_noalloc", "sim_write_state", "sim_sizes",
-           "sim_iteration_stats",
+           "sim_iteration_stats", "sim_scene_info",
            "sim_phase_trace", "sim_sync", "sim_last_error")
 
 
@@ -89,6 +89,7 @@ def load(build_if_missing: bool = True):
             "sim_write_state": (C.c_int, [VP, VP]),
             "sim_sizes": (C.c_int, [VP, PL]),
             "sim_iteration_stats": (C.c_int, [VP, PL]),
+            "sim_scene_info": (C.c_int, [VP, C.c_int, PL]),
             "sim_phase_trace": (C.c_int, [VP, C.c_int, PL]),
             "sim_sync": (C.c_int, [VP]),
             "sim_last_error": (C.c_char_p, [VP]),
@@ -197,6 +198,13 @@ def sim_sizes(h) -> dict:
     keys = ("scenes", "subsystems", "dof", "interfaces", "rows", "side_rows", "bodies",
             "smem_bytes")
     return {k: int(v) for k, v in zip(keys, out)}
+
+
+def sim_scene_info(h, scene: int) -> dict:
+    out = (C.c_longlong * 4)()
+    _check(h, load().sim_scene_info(h, scene, out))
+    return dict(global_workspace=bool(out[0]), smem_bytes=int(out[1]), subsystems=int(out[2]),
+                work_bytes=int(out[3]))
 
 
 def sim_iteration_stats(h) -> dict:

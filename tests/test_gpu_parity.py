@@ -221,6 +221,33 @@ def test_many_ragged_scenes_in_one_launch(sa):
         assert rel_lam(sim, o, k, p) < TOL
 
 
+@pytest.mark.parametrize("seed", range(2))
+def test_large_blocks_in_global_workspace_fp64(sa, seed):
+    """Subsystems of 100-240 DOF do not fit a block's shared memory: their factors, maps
+    and D live in the global workspace.  FP64, fixed iterations, against the oracle."""
+    p = sg.generic(30 + seed, n_scenes=3, max_iters=25, tol_primal=-1, n_sub=3,
+                   n_range=(100, 240), max_sides=2, extra=2)
+    sim = sa.Simulation(p)
+    assert any(sa.sim_scene_info(sim.h, k)["global_workspace"] for k in range(3))
+    sim.step(1)
+    orcs = oracle.run(p)
+    _compare(sim, orcs, p, what=("vhat", "lam"))
+
+
+def test_large_blocks_mixed_close_to_oracle(sa, capsys):
+    p = sg.generic(40, n_scenes=2, max_iters=400, tol_primal=1e-8, n_sub=3,
+                   n_range=(100, 240), max_sides=2, extra=1, warm="cold",
+                   types=(sg.EQUALITY, sg.SOFT, sg.HARD))
+    sim = sa.Simulation(p, precision=sa.SIM_MIXED)
+    assert all(sa.sim_scene_info(sim.h, k)["global_workspace"] for k in range(2))
+    sim.step(1)
+    orcs = oracle.run(p)
+    errs = [rel(sim.scene_vhat(k), o.vhat_all()) for k, o in enumerate(orcs)]
+    with capsys.disabled():
+        print(f"\n[mixed vs FP64 oracle, 100-240 DOF blocks] v-hat rel err max {max(errs):.3e}")
+    assert max(errs) < 1e-5
+
+
 def test_not_spd_is_reported_not_faulted(sa):
     A = -np.eye(3)
     p = sg.Problem([sg.Scene([sg.GenericSub(A, np.ones(3))], [])],
