@@ -47,6 +47,7 @@ extern "C" {
 /* subsystem kinds (Sec. III-A: rigid bodies, or any block given by A_i, b_i) */
 #define SIM_SUB_GENERIC 0     /* A_i (n x n, SPD) and b_i given directly                    */
 #define SIM_SUB_RIGID 1       /* rigid bodies in maximal coordinates, 6 DOF each            */
+#define SIM_SUB_LINEAR 2      /* linear elastic block of nodes (3 DOF each), e.g. linear FEM */
 
 /* interface kinds.  The first four give rows explicitly (J per side, e); the last four are
  * rigid-body model constraints whose rows are rebuilt from the bodies' state every step. */
@@ -76,6 +77,7 @@ extern "C" {
 #define SIM_GET_BODIES 2      /* id = subsystem: nb x 17 doubles (body records, see below)  */
 #define SIM_GET_BETA 3        /* id = subsystem: 1 double                                   */
 #define SIM_GET_Z 4           /* id = interface: n_sides x rows doubles, z of the last step */
+#define SIM_GET_NODES 5       /* id = linear subsystem: nodes x 6 doubles (x[3], v[3])      */
 
 typedef struct sim_s *sim_t;
 
@@ -112,7 +114,14 @@ void sim_destroy(sim_t s);
  *       centre of mass), q[4] (w, x, y, z unit quaternion, body to world), v[3] (world linear
  *       velocity), w[3] (body-frame angular velocity).  DOF order: [v, w] per body.
  *       A_i = (2/h) M_i and b_i = (2/h) M_i v_k - C v_k + f with C v_k = [0; w x I w] and
- *       f = [m g; 0] (Eq. ddyn with v_{k+1} = 2 v-hat - v_k).  */
+ *       f = [m g; 0] (Eq. ddyn with v_{k+1} = 2 v-hat - v_k).
+ *   kind SIM_SUB_LINEAR:  count = nodes nn >= 1, n = 3 nn DOF (node velocities); data =
+ *       mass (nn, lumped per node), f (n, constant force), X0 (n, rest positions),
+ *       x (n, positions), v (n, velocities), nnz, then nnz triplets (row, col, value) of the
+ *       symmetric stiffness K (indices as exact doubles).  With the elastic force
+ *       at the midpoint of the step (Eq. ddyn): A_i = (2/h) M + (h/2) K,
+ *       b_i = (2/h) M v_k - K (x_k - X0) + f + M g; then x += h v-hat, v = 2 v-hat - v_k.
+ *       K is kept sparse.  */
 int sim_add_subsystem(sim_t s, int scene, int kind, int count, const double *data, int *out_id);
 
 /* Adds an interface (constraint j) to scene `scene`; interface ids are global, in call order.
@@ -124,6 +133,8 @@ int sim_add_subsystem(sim_t s, int scene, int kind, int count, const double *dat
  * Rigid-model kinds (SIM_IF_BALL, SIM_IF_REVOLUTE, SIM_IF_ANGLE_PD, SIM_IF_PLANE_CONTACT):
  *   rows and n_sides are ignored; sides = {sub_a, body_a, sub_b, body_b}: (subsystem id, body
  *   index inside it) of bodies a and b, sub_b = -1 for the world (PLANE_CONTACT uses a only);
+ *   for BALL and PLANE_CONTACT a side may also be (linear subsystem id, node index): the
+ *   node's position takes the place of the anchored body point;
  *   J and e must be NULL; params = 23 doubles:
  *     anchor_a[3] (a frame), anchor_b[3] (b frame, or a world point), axis_a[3], axis_b[3],
  *     ref_a[3] (a frame, orthogonal to axis_a), ref_b[3] (b frame), kp, kd, target,
@@ -155,9 +166,12 @@ int sim_residuals(sim_t s, int scene, double out[6]);
 /* Waits for the stream, then copies a quantity of the last step into host memory dst. */
 int sim_get(sim_t s, int what, int id, double *dst);
 
-/* Packed state of all rigid bodies, in subsystem then body order: 13 doubles per body
- * (p[3], q[4], v[3], w[3]).  sim_read_state copies device -> host (dst holds 13 x bodies)
- * after the stream's work; sim_write_state copies host -> device, enqueued on the stream. */
+/* Packed state: all rigid bodies ordered by scene, then subsystem in the order added, then
+ * body, 13 doubles per body (p[3], q[4], v[3], w[3]), followed by all nodes of the linear
+ * blocks in the same order, 6 doubles per node (x[3], v[3]); 13 x bodies + 6 x nodes doubles in all (sim_sizes
+ * out[6] and out[8]).  sim_read_state copies device -> host after the stream's work;
+ * sim_write_state copies host -> device, enqueued on the stream.  dst/src are host memory
+ * owned by the caller (pinned memory makes the copies asynchronous to the host). */
 int sim_read_state(sim_t s, double *dst);
 int sim_write_state(sim_t s, const double *src);
 
@@ -170,8 +184,8 @@ int sim_write_state(sim_t s, const double *src);
  * cudaFree or allocating library routine) and returns SIM_EINVAL until the first sim_step
  * has laid the simulation out.
  * It packs the state through a fixed 1 MiB staging array in device memory, which every GPU
- * that loads the library holds until the process exits, so it reads at most 10082 bodies
- * (13 doubles each) and returns SIM_EINVAL beyond that.  The first call on a device looks
+ * that loads the library holds until the process exits, so it reads a state of at most
+ * 131072 doubles (10082 bodies without nodes) and returns SIM_EINVAL beyond that.  The first call on a device looks
  * up that array's address; make that first call before any stream capture.  Every call,
  * from any simulation on the device, shares the one array: calls whose GPU work overlaps
  * (different host threads or streams at once) race and must be serialised by the caller.
@@ -180,8 +194,9 @@ int sim_write_state(sim_t s, const double *src);
 int sim_read_state_noalloc(sim_t s, double *dst);
 
 /* Counts: out[0] scenes, out[1] subsystems, out[2] DOF, out[3] interfaces, out[4] rows,
- * out[5] side-rows, out[6] rigid bodies, out[7] on-chip bytes of the largest scene. */
-int sim_sizes(sim_t s, long long out[8]);
+ * out[5] side-rows, out[6] rigid bodies, out[7] on-chip bytes of the largest scene,
+ * out[8] nodes of the linear blocks. */
+int sim_sizes(sim_t s, long long out[9]);
 
 /* Where scene `scene` keeps its working set (lays the simulation out if needed):
  * out[0] 0 if every per-subsystem array (J, the factor, W, D, ...) fits in the block's

@@ -50,6 +50,9 @@ def lib():
                 "orc_new": (VP, [PD]),
                 "orc_add_generic": (C.c_int, [VP, C.c_int, PD, PD]),
                 "orc_add_rigid": (C.c_int, [VP, C.c_int, PD]),
+                "orc_add_linear": (C.c_int, [VP, C.c_int, PD]),
+                "orc_get_node": (None, [VP, C.c_int, C.c_int, PD]),
+                "orc_set_node": (None, [VP, C.c_int, C.c_int, PD]),
                 "orc_add_rows": (C.c_int, [VP, C.c_int, C.c_int, C.c_int, PI, PD, PD, D, D, D]),
                 "orc_add_joint": (C.c_int, [VP, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, PD]),
                 "orc_step": (C.c_int, [VP]),
@@ -123,6 +126,10 @@ class OracleScene:
             if hasattr(sub, "bodies"):
                 rec = _f64(np.concatenate([body_record(b) for b in sub.bodies]))
                 rc = L.orc_add_rigid(self.h, len(sub.bodies), _p(rec))
+            elif hasattr(sub, "Kv"):
+                data = _f64(np.concatenate([sub.mass, sub.K_dense().ravel(), sub.f, sub.X0,
+                                            sub.x, sub.v]))
+                rc = L.orc_add_linear(self.h, sub.nodes, _p(data))
             else:
                 A, b = _f64(sub.A), _f64(sub.b)
                 rc = L.orc_add_generic(self.h, sub.n, _p(A), _p(b))
@@ -239,6 +246,19 @@ class OracleScene:
         out = np.zeros(17)
         self.L.orc_get_body(self.h, i, k, _p(out))
         return out
+
+    def node(self, i, k) -> np.ndarray:
+        out = np.zeros(6)
+        self.L.orc_get_node(self.h, i, k, _p(out))
+        return out
+
+    def nodes_all(self) -> np.ndarray:
+        out = []
+        for i, sub in enumerate(self.scene.subs):
+            if hasattr(sub, "Kv"):
+                for k in range(sub.nodes):
+                    out.append(self.node(i, k))
+        return np.array(out).reshape(-1, 6)
 
     def set_body(self, i, k, rec):
         rec = _f64(rec)

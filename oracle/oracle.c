@@ -48,15 +48,17 @@
 
 enum { T_EQUALITY = 0, T_HARD = 1, T_SOFT = 2, T_CONTACT = 3 };
 enum { SRC_ROWS = 0, SRC_BALL = 1, SRC_REVOLUTE = 2, SRC_ANGLE_PD = 3, SRC_PLANE = 4 };
-enum { SUB_GENERIC = 0, SUB_RIGID = 1 };
+enum { SUB_GENERIC = 0, SUB_RIGID = 1, SUB_LINEAR = 2 };
 
 typedef struct {
     double m, I[3], p[3], q[4], v[3], w[3];
 } body_t;
 
 typedef struct {
-    int kind, n, nb;
+    int kind, n, nb;           /* nb: bodies (rigid) or nodes (linear) */
     body_t *bodies;
+    double *mass, *Kel, *fext, *X0, *x, *vel;   /* linear: per node mass, K (n x n), f,
+                                                   rest, position, velocity (n each) */
     double *A, *b;   /* n*n, n */
     double *L;       /* Cholesky factor of K (lower, row-major n*n) */
     double *v;       /* v-hat */
@@ -231,6 +233,31 @@ int orc_add_rigid(orc_scene *S, int nb, const double *rec)
     return S->nsub - 1;
 }
 
+/* linear elastic block of nn nodes (3 DOF each): data = mass (nn), K (n x n row-major),
+ * f (n), rest positions X0 (n), positions x (n), velocities v (n), n = 3 nn */
+int orc_add_linear(orc_scene *S, int nn, const double *data)
+{
+    if (nn <= 0) return -1;
+    sub_t *u = new_sub(S);
+    u->kind = SUB_LINEAR; u->nb = nn; u->n = 3 * nn;
+    int n = u->n;
+    u->mass = (double *)xcalloc(nn, sizeof(double));
+    u->Kel = (double *)xcalloc((size_t)n * n, sizeof(double));
+    u->fext = (double *)xcalloc(n, sizeof(double));
+    u->X0 = (double *)xcalloc(n, sizeof(double));
+    u->x = (double *)xcalloc(n, sizeof(double));
+    u->vel = (double *)xcalloc(n, sizeof(double));
+    const double *p = data;
+    memcpy(u->mass, p, nn * sizeof(double)); p += nn;
+    memcpy(u->Kel, p, (size_t)n * n * sizeof(double)); p += (size_t)n * n;
+    memcpy(u->fext, p, n * sizeof(double)); p += n;
+    memcpy(u->X0, p, n * sizeof(double)); p += n;
+    memcpy(u->x, p, n * sizeof(double)); p += n;
+    memcpy(u->vel, p, n * sizeof(double));
+    sub_alloc(u);
+    return S->nsub - 1;
+}
+
 static con_t *new_con(orc_scene *S)
 {
     if (S->ncon == S->capcon) {
@@ -288,10 +315,15 @@ int orc_add_rows(orc_scene *S, int type, int rows, int ns, const int *subs, cons
  * ref_b[3] kp kd target plane_z mu   (23 doubles).  sb < 0 means the world. */
 int orc_add_joint(orc_scene *S, int kind, int sa, int ba, int sb, int bb, const double *p)
 {
-    if (sa < 0 || sa >= S->nsub || S->subs[sa].kind != SUB_RIGID) return -1;
+    /* a node of a linear block may be a side of a ball joint or a plane contact */
+    const int node_ok = (kind == SRC_BALL || kind == SRC_PLANE);
+    if (sa < 0 || sa >= S->nsub || S->subs[sa].kind == SUB_GENERIC) return -1;
+    if (S->subs[sa].kind == SUB_LINEAR && !node_ok) return -1;
     if (ba < 0 || ba >= S->subs[sa].nb) return -1;
+    if (kind == SRC_PLANE) sb = -1;
     if (sb >= 0) {
-        if (sb >= S->nsub || S->subs[sb].kind != SUB_RIGID) return -1;
+        if (sb >= S->nsub || S->subs[sb].kind == SUB_GENERIC) return -1;
+        if (S->subs[sb].kind == SUB_LINEAR && !node_ok) return -1;
         if (bb < 0 || bb >= S->subs[sb].nb) return -1;
         if (sb == sa && bb == ba) return -1;
     }
@@ -344,6 +376,21 @@ static void assemble_rigid(orc_scene *S, sub_t *u)
     }
 }
 
+/* Linear elastic block (Eq. ddyn with the elastic force at the midpoint):
+ * A = (2/h) M + (h/2) K ;  b = (2/h) M v_k - K (x_k - X0) + f + M g */
+static void assemble_linear(orc_scene *S, sub_t *u)
+{
+    int n = u->n;
+    double c2h = 2.0 / S->h;
+    for (int p = 0; p < n; p++) {
+        for (int q = 0; q < n; q++) u->A[p * n + q] = 0.5 * S->h * u->Kel[p * n + q];
+        u->A[p * n + p] += c2h * u->mass[p / 3];
+        double kx = 0.0;
+        for (int q = 0; q < n; q++) kx += u->Kel[p * n + q] * (u->x[q] - u->X0[q]);
+        u->b[p] = c2h * u->mass[p / 3] * u->vel[p] - kx + u->fext[p] + u->mass[p / 3] * S->g[p % 3];
+    }
+}
+
 /* Row of the velocity of body point P = p + R r along the world direction dir.
  * dP/dt = v + R (w x r) with w in the body frame, so
  * dir . dP/dt = dir . v + (R^T dir) . (w x r) = dir . v + w . (r x R^T dir). */
@@ -355,40 +402,72 @@ static void point_row(const double dir[3], const double R[9], const double r[3],
     cross3(r, Rd, row + 3);
 }
 
-/* phi (rows) and body blocks Ja, Jb (rows x 6) of a rigid-model constraint */
+/* A side of a model constraint: a rigid body (6 columns from 6 idx: [v, w]) or a node of a
+ * linear block (3 columns from 3 idx: its velocity). */
+typedef struct { int node; const double *p; double R[9]; } side_t;
+
+static void side_of(orc_scene *S, int sub, int idx, side_t *sd)
+{
+    if (S->subs[sub].kind == SUB_LINEAR) {
+        sd->node = 1;
+        sd->p = S->subs[sub].x + 3 * idx;
+        memset(sd->R, 0, sizeof sd->R);
+        sd->R[0] = sd->R[4] = sd->R[8] = 1.0;
+    } else {
+        body_t *B = &S->subs[sub].bodies[idx];
+        sd->node = 0;
+        sd->p = B->p;
+        quat_to_mat(B->q, sd->R);
+    }
+}
+
+/* world point of a side (a node ignores the anchor) and its velocity row along dir */
+static void side_point(const side_t *sd, const double anc[3], double P[3])
+{
+    if (sd->node) { P[0] = sd->p[0]; P[1] = sd->p[1]; P[2] = sd->p[2]; return; }
+    double ra[3];
+    matvec3(sd->R, anc, ra);
+    for (int d = 0; d < 3; d++) P[d] = sd->p[d] + ra[d];
+}
+
+static void side_row(const side_t *sd, const double dir[3], const double anc[3], double *row)
+{
+    if (sd->node) { row[0] = dir[0]; row[1] = dir[1]; row[2] = dir[2]; return; }
+    point_row(dir, sd->R, anc, row);
+}
+
+/* phi (rows) and the blocks Ja, Jb (rows x 6, of which the first 3 columns are used for a
+ * node side) of a model constraint */
 static void joint_rows(orc_scene *S, con_t *c, double *phi, double *Ja, double *Jb)
 {
-    body_t *A = &S->subs[c->sa].bodies[c->ba];
-    body_t *B = c->sb >= 0 ? &S->subs[c->sb].bodies[c->bb] : NULL;
-    double Ra[9], Rb[9];
-    quat_to_mat(A->q, Ra);
-    if (B) quat_to_mat(B->q, Rb);
-    else { memset(Rb, 0, sizeof Rb); Rb[0] = Rb[4] = Rb[8] = 1.0; }
+    side_t sa, sbd;
+    side_of(S, c->sa, c->ba, &sa);
+    const int hasb = c->sb >= 0;
+    if (hasb) side_of(S, c->sb, c->bb, &sbd);
+    const double *Ra = sa.R, *Rb = hasb ? sbd.R : NULL;
+    body_t *B = (hasb && !sbd.node) ? &S->subs[c->sb].bodies[c->bb] : NULL;
     memset(Ja, 0, sizeof(double) * 6 * c->rows);
     memset(Jb, 0, sizeof(double) * 6 * c->rows);
     static const double E[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
     if (c->src == SRC_BALL || c->src == SRC_REVOLUTE) {
-        double ra[3], pa[3], pb[3], rb[3];
-        matvec3(Ra, c->anc_a, ra);
-        for (int d = 0; d < 3; d++) pa[d] = A->p[d] + ra[d];
-        if (B) { matvec3(Rb, c->anc_b, rb); for (int d = 0; d < 3; d++) pb[d] = B->p[d] + rb[d]; }
+        double pa[3], pb[3];
+        side_point(&sa, c->anc_a, pa);
+        if (hasb) side_point(&sbd, c->anc_b, pb);
         else { for (int d = 0; d < 3; d++) pb[d] = c->anc_b[d]; }
         for (int d = 0; d < 3; d++) {
             phi[d] = pa[d] - pb[d];
-            point_row(E[d], Ra, c->anc_a, Ja + 6 * d);
-            if (B) {
-                point_row(E[d], Rb, c->anc_b, Jb + 6 * d);
+            side_row(&sa, E[d], c->anc_a, Ja + 6 * d);
+            if (hasb) {
+                side_row(&sbd, E[d], c->anc_b, Jb + 6 * d);
                 for (int q = 0; q < 6; q++) Jb[6 * d + q] = -Jb[6 * d + q];
             }
         }
         if (c->src == SRC_REVOLUTE) {
-            double ua[3], ub[3], t[2][3], tmp[3];
-            matvec3(Ra, c->ax_a, ua);
+            double ub[3], t[2][3], tmp[3];
             if (B) matvec3(Rb, c->ax_b, ub); else memcpy(ub, c->ax_b, sizeof ub);
             matvec3(Ra, c->ref_a, t[0]);
             cross3(c->ax_a, c->ref_a, tmp);
             matvec3(Ra, tmp, t[1]);
-            (void)ua;
             for (int k = 0; k < 2; k++) {
                 int r = 3 + k;
                 double txu[3], ja[3], jb[3];
@@ -417,12 +496,12 @@ static void joint_rows(orc_scene *S, con_t *c, double *phi, double *Ja, double *
             for (int q = 0; q < 3; q++) Jb[3 + q] = jb[q];
         }
     } else if (c->src == SRC_PLANE) {
-        double ra[3];
-        matvec3(Ra, c->anc_a, ra);
-        phi[0] = A->p[2] + ra[2] - c->plane_z;   /* gap along the normal +z */
+        double pa[3];
+        side_point(&sa, c->anc_a, pa);
+        phi[0] = pa[2] - c->plane_z;   /* gap along the normal +z */
         phi[1] = 0.0; phi[2] = 0.0;
         static const double dirs[3][3] = {{0, 0, 1}, {1, 0, 0}, {0, 1, 0}};
-        for (int d = 0; d < 3; d++) point_row(dirs[d], Ra, c->anc_a, Ja + 6 * d);
+        for (int d = 0; d < 3; d++) side_row(&sa, dirs[d], c->anc_a, Ja + 6 * d);
     }
 }
 
@@ -431,14 +510,17 @@ static void assemble_joint(orc_scene *S, con_t *c)
     double phi[5], Ja[30], Jb[30];
     joint_rows(S, c, phi, Ja, Jb);
     int na = S->subs[c->sa].n;
+    /* a body side fills 6 columns at 6 * index, a node side 3 columns at 3 * index */
+    int wa = S->subs[c->sa].kind == SUB_LINEAR ? 3 : 6;
     for (int s = 0; s < c->ns; s++) memset(c->J[s], 0, sizeof(double) * c->rows * S->subs[c->sub[s]].n);
     for (int r = 0; r < c->rows; r++)
-        for (int q = 0; q < 6; q++) c->J[0][r * na + 6 * c->ba + q] += Ja[r * 6 + q];
+        for (int q = 0; q < wa; q++) c->J[0][r * na + wa * c->ba + q] += Ja[r * 6 + q];
     if (c->sb >= 0) {
         int side = (c->sb == c->sa) ? 0 : 1;
         int nb = S->subs[c->sb].n;
+        int wb = S->subs[c->sb].kind == SUB_LINEAR ? 3 : 6;
         for (int r = 0; r < c->rows; r++)
-            for (int q = 0; q < 6; q++) c->J[side][r * nb + 6 * c->bb + q] += Jb[r * 6 + q];
+            for (int q = 0; q < wb; q++) c->J[side][r * nb + wb * c->bb + q] += Jb[r * 6 + q];
     }
     double h = S->h;
     if (c->src == SRC_BALL || c->src == SRC_REVOLUTE) {
@@ -503,8 +585,10 @@ int orc_step(orc_scene *S)
 {
     S->status = 0;
     /* construct A_i, b_i */
-    for (int i = 0; i < S->nsub; i++)
+    for (int i = 0; i < S->nsub; i++) {
         if (S->subs[i].kind == SUB_RIGID) assemble_rigid(S, &S->subs[i]);
+        else if (S->subs[i].kind == SUB_LINEAR) assemble_linear(S, &S->subs[i]);
+    }
     /* construct e_j, J_j */
     for (int j = 0; j < S->ncon; j++)
         if (S->cons[j].src != SRC_ROWS) assemble_joint(S, &S->cons[j]);
@@ -657,6 +741,13 @@ int orc_step(orc_scene *S)
        R <- R Exp(h w-hat) with the body-frame angular velocity */
     for (int i = 0; i < S->nsub; i++) {
         sub_t *u = &S->subs[i];
+        if (u->kind == SUB_LINEAR) {
+            for (int p = 0; p < u->n; p++) {
+                u->x[p] += S->h * u->v[p];
+                u->vel[p] = 2.0 * u->v[p] - u->vel[p];
+            }
+            continue;
+        }
         if (u->kind != SUB_RIGID) continue;
         for (int k = 0; k < u->nb; k++) {
             body_t *B = &u->bodies[k];
@@ -737,8 +828,10 @@ int orc_con_sub(orc_scene *S, int j, int s) { return S->cons[j].sub[s]; }
 /* assemble (without solving) so tests can read A, b, J, e at the current state */
 void orc_assemble(orc_scene *S)
 {
-    for (int i = 0; i < S->nsub; i++)
+    for (int i = 0; i < S->nsub; i++) {
         if (S->subs[i].kind == SUB_RIGID) assemble_rigid(S, &S->subs[i]);
+        else if (S->subs[i].kind == SUB_LINEAR) assemble_linear(S, &S->subs[i]);
+    }
     for (int j = 0; j < S->ncon; j++)
         if (S->cons[j].src != SRC_ROWS) assemble_joint(S, &S->cons[j]);
 }
@@ -748,6 +841,21 @@ void orc_joint_phi(orc_scene *S, int j, double *phi)
 {
     double Ja[30], Jb[30];
     joint_rows(S, &S->cons[j], phi, Ja, Jb);
+}
+
+/* node k of linear block i: x[3], v[3] */
+void orc_get_node(orc_scene *S, int i, int k, double *out)
+{
+    sub_t *u = &S->subs[i];
+    memcpy(out, u->x + 3 * k, 3 * sizeof(double));
+    memcpy(out + 3, u->vel + 3 * k, 3 * sizeof(double));
+}
+
+void orc_set_node(orc_scene *S, int i, int k, const double *in)
+{
+    sub_t *u = &S->subs[i];
+    memcpy(u->x + 3 * k, in, 3 * sizeof(double));
+    memcpy(u->vel + 3 * k, in + 3, 3 * sizeof(double));
 }
 
 void orc_get_body(orc_scene *S, int i, int k, double *out)
@@ -802,6 +910,7 @@ void orc_free(orc_scene *S)
     for (int i = 0; i < S->nsub; i++) {
         sub_t *u = &S->subs[i];
         free(u->A); free(u->b); free(u->L); free(u->v); free(u->rhs); free(u->bodies);
+        free(u->mass); free(u->Kel); free(u->fext); free(u->X0); free(u->x); free(u->vel);
     }
     for (int j = 0; j < S->ncon; j++) {
         con_t *c = &S->cons[j];

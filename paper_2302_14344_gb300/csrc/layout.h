@@ -16,7 +16,8 @@ enum { SRC_EQUALITY = 0, SRC_HARD = 1, SRC_SOFT = 2, SRC_CONTACT = 3, SRC_BALL =
 // projection types (Sec. III-C)
 enum { TYPE_EQUALITY = 0, TYPE_HARD = 1, TYPE_SOFT = 2, TYPE_CONTACT = 3 };
 // subsystem kinds
-enum { KIND_GENERIC = 0, KIND_RIGID = 1 };
+enum { KIND_GENERIC = 0, KIND_RIGID = 1, KIND_LINEAR = 2 };
+#define SUBADMM_NODE 6          // doubles of a node state record: x[3], v[3]
 // phase counters (clock64 cycles seen by thread 0 of a scene's block)
 enum { PHASE_ASSEMBLE = 0, PHASE_FACTOR = 1, PHASE_VSTEP = 2, PHASE_ZSTEP = 3, PHASE_EXIT = 4,
        PHASE_RECOVER = 5, PHASE_ITERS = 6, PHASE_STEPS = 7 };
@@ -53,8 +54,10 @@ struct SubDesc {
     int mpad;              // m rounded up to a whole 16-byte vector of the iteration type
     int sr0;               // scene-local first side-row (16-byte aligned in the T region)
     int local;             // index inside its scene
-    int body0, nb;         // first global body, body count (rigid)
-    int gen_off;           // pool offset of A (n*n) then b (n) (generic)
+    int body0, nb;         // first global body (rigid) or node (linear), and their count
+    int gen_off;           // pool offset of A (n*n) then b (n) (generic); of mass (nb), f (n),
+                           // X0 (n), K values (linear)
+    int csr_off;           // linear: ipool offset of the K row pointers (n+1), then columns
     int od_J, od_L, od_b;  // double region: J_ci rows (m x n), K then its factor L (n x n), b (n)
     int od_v, od_id;       // double region: v-hat (n); 1 / L_pp (FP64 form) or rhs (mixed) (n)
     int od_t;              // double region: J v in the mixed refinement (m)
@@ -71,7 +74,8 @@ struct ConDesc {
     int sub[SUBADMM_MAXS]; // scene-local subsystem of each side
     int sr[SUBADMM_MAXS];  // scene-local side-row of row 0 of each side
     int ba, bb;            // model: body index inside its subsystem (column block 6*ba)
-    int gb_a, gb_b;        // model: global body index of a and b (-1: the world)
+    int gb_a, gb_b;        // model: global body or node index of a and b (-1: the world)
+    int node_a, node_b;    // model: 1 if that side is a node of a linear block
     int side_b;            // model: side that holds body b (-1 for the world)
 };
 
@@ -92,6 +96,8 @@ struct StepParams {
     const double *pool;    // constant data and generic A, b
     double *work;          // per-subsystem arrays of scenes too large for shared memory
     double *bodies;        // 17 doubles per body (state in and out)
+    double *nodes;         // 6 doubles per node of linear blocks (state in and out)
+    const int *ipool;      // integer constant data (sparse K of linear blocks)
     double *vhat;          // per DOF
     double *lam;           // per row: lambda of the last step (warm start state)
     double *z;             // per side-row: z of the last step (warm start state)

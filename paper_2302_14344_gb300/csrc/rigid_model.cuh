@@ -59,43 +59,78 @@ __device__ __forceinline__ void point_row(const double *d, const Rot &R, const d
     cross(r, Rd, row + 3);
 }
 
-// Rows of a model constraint: Ja, Jb are rows x 6 blocks of bodies a and b, e the error
-// terms; k, alpha (soft) are returned for ANGLE_PD.
-__device__ void model_rows(const ConDesc &c, const double *prm, const double *bodies,
-                           double h, double gamma, double *Ja, double *Jb, double *e,
-                           double *k_out, double *alpha_out)
+// A side of a model constraint: a rigid body (its point p + R anchor, rows of 6 columns
+// [v, w]) or a node of a linear block (its position, rows of 3 columns: its velocity).
+struct Side {
+    bool node;
+    const double *p;
+    Rot R;
+};
+
+__device__ __forceinline__ Side make_side(bool node, const double *rec)
 {
-    const double *A = bodies + (size_t)c.gb_a * SUBADMM_BODY;
-    const double *B = c.gb_b >= 0 ? bodies + (size_t)c.gb_b * SUBADMM_BODY : nullptr;
-    const Rot Ra = quat_rot(A + 7);
-    Rot Rb;
-    if (B) Rb = quat_rot(B + 7);
+    Side s;
+    s.node = node;
+    if (node) {
+        s.p = rec;                                  // x[3], then v[3]
+        for (int q = 0; q < 9; ++q) s.R.r[q] = (q % 4 == 0) ? 1.0 : 0.0;
+    } else {
+        s.p = rec + 4;
+        s.R = quat_rot(rec + 7);
+    }
+    return s;
+}
+
+__device__ __forceinline__ void side_point(const Side &s, const double *anc, double *P)
+{
+    if (s.node) { P[0] = s.p[0]; P[1] = s.p[1]; P[2] = s.p[2]; return; }
+    double r[3];
+    mul(s.R, anc, r);
+    for (int d = 0; d < 3; ++d) P[d] = s.p[d] + r[d];
+}
+
+__device__ __forceinline__ void side_row(const Side &s, const double *dir, const double *anc, double *row)
+{
+    if (s.node) { row[0] = dir[0]; row[1] = dir[1]; row[2] = dir[2]; return; }
+    point_row(dir, s.R, anc, row);
+}
+
+// Rows of a model constraint: Ja, Jb are rows x 6 blocks of sides a and b (a node side
+// uses the first 3 columns), e the error terms; k, alpha (soft) are returned for ANGLE_PD.
+__device__ void model_rows(const ConDesc &c, const double *prm, const double *bodies,
+                           const double *nodes, double h, double gamma, double *Ja, double *Jb,
+                           double *e, double *k_out, double *alpha_out)
+{
+    const double ih = 1.0 / h;
+    const Side sa = make_side(c.node_a, c.node_a ? nodes + (size_t)c.gb_a * SUBADMM_NODE
+                                                 : bodies + (size_t)c.gb_a * SUBADMM_BODY);
+    const bool hasb = c.gb_b >= 0;
+    Side sb;
+    if (hasb)
+        sb = make_side(c.node_b, c.node_b ? nodes + (size_t)c.gb_b * SUBADMM_NODE
+                                          : bodies + (size_t)c.gb_b * SUBADMM_BODY);
+    const Rot &Ra = sa.R;
     const double *anc_a = prm + 0, *anc_b = prm + 3, *ax_a = prm + 6, *ax_b = prm + 9;
     const double *ref_a = prm + 12, *ref_b = prm + 15;
     for (int q = 0; q < 6 * c.rows; ++q) { Ja[q] = 0.0; Jb[q] = 0.0; }
     if (c.src == SRC_BALL || c.src == SRC_REVOLUTE) {
-        double ra[3], pa[3], pb[3];
-        mul(Ra, anc_a, ra);
-        for (int d = 0; d < 3; ++d) pa[d] = A[4 + d] + ra[d];
-        if (B) {
-            double rb[3];
-            mul(Rb, anc_b, rb);
-            for (int d = 0; d < 3; ++d) pb[d] = B[4 + d] + rb[d];
-        } else {
-            for (int d = 0; d < 3; ++d) pb[d] = anc_b[d];
-        }
+        double pa[3], pb[3];
+        side_point(sa, anc_a, pa);
+        if (hasb) side_point(sb, anc_b, pb);
+        else { pb[0] = anc_b[0]; pb[1] = anc_b[1]; pb[2] = anc_b[2]; }
         for (int d = 0; d < 3; ++d) {
             const double E[3] = {d == 0 ? 1.0 : 0.0, d == 1 ? 1.0 : 0.0, d == 2 ? 1.0 : 0.0};
-            point_row(E, Ra, anc_a, Ja + 6 * d);
-            if (B) {
-                point_row(E, Rb, anc_b, Jb + 6 * d);
+            side_row(sa, E, anc_a, Ja + 6 * d);
+            if (hasb) {
+                side_row(sb, E, anc_b, Jb + 6 * d);
                 for (int q = 0; q < 6; ++q) Jb[6 * d + q] = -Jb[6 * d + q];
             }
-            e[d] = gamma * (pa[d] - pb[d]) / h;
+            e[d] = gamma * (pa[d] - pb[d]) * ih;
         }
         if (c.src == SRC_REVOLUTE) {
+            // revolute joints join rigid bodies only (the host rejects node sides)
             double ub[3], t[2][3], axr[3];
-            if (B) mul(Rb, ax_b, ub); else { ub[0] = ax_b[0]; ub[1] = ax_b[1]; ub[2] = ax_b[2]; }
+            if (hasb) mul(sb.R, ax_b, ub); else { ub[0] = ax_b[0]; ub[1] = ax_b[1]; ub[2] = ax_b[2]; }
             mul(Ra, ref_a, t[0]);
             cross(ax_a, ref_a, axr);
             mul(Ra, axr, t[1]);
@@ -105,26 +140,26 @@ __device__ void model_rows(const ConDesc &c, const double *prm, const double *bo
                 cross(t[kk], ub, txu);          // d/dt (t . u_b) = (t x u_b) . (w_a - w_b)
                 mulT(Ra, txu, ja);
                 for (int q = 0; q < 3; ++q) Ja[6 * r + 3 + q] = ja[q];
-                if (B) {
+                if (hasb) {
                     double jb[3];
-                    mulT(Rb, txu, jb);
+                    mulT(sb.R, txu, jb);
                     for (int q = 0; q < 3; ++q) Jb[6 * r + 3 + q] = -jb[q];
                 }
-                e[r] = gamma * dot(t[kk], ub) / h;
+                e[r] = gamma * dot(t[kk], ub) * ih;
             }
         }
     } else if (c.src == SRC_ANGLE_PD) {
         double u[3], na[3], nb[3], cr[3], ja[3];
         mul(Ra, ax_a, u);
         mul(Ra, ref_a, na);
-        if (B) mul(Rb, ref_b, nb); else { nb[0] = ref_b[0]; nb[1] = ref_b[1]; nb[2] = ref_b[2]; }
+        if (hasb) mul(sb.R, ref_b, nb); else { nb[0] = ref_b[0]; nb[1] = ref_b[1]; nb[2] = ref_b[2]; }
         cross(na, nb, cr);
         const double theta = atan2(dot(cr, u), dot(na, nb));
         mulT(Ra, u, ja);                        // d theta / dt = u . (w_b - w_a)
         for (int q = 0; q < 3; ++q) Ja[3 + q] = -ja[q];
-        if (B) {
+        if (hasb) {
             double jb[3];
-            mulT(Rb, u, jb);
+            mulT(sb.R, u, jb);
             for (int q = 0; q < 3; ++q) Jb[3 + q] = jb[q];
         }
         const double kp = prm[18], kd = prm[19];
@@ -132,12 +167,12 @@ __device__ void model_rows(const ConDesc &c, const double *prm, const double *bo
         *k_out = kp;
         *alpha_out = kd / kp + 0.5 * h;
     } else if (c.src == SRC_PLANE) {
-        double ra[3];
-        mul(Ra, anc_a, ra);
-        const double gap = A[6] + ra[2] - prm[21];
+        double pa[3];
+        side_point(sa, anc_a, pa);
+        const double gap = pa[2] - prm[21];
         const double dirs[3][3] = {{0.0, 0.0, 1.0}, {1.0, 0.0, 0.0}, {0.0, 1.0, 0.0}};
-        for (int d = 0; d < 3; ++d) point_row(dirs[d], Ra, anc_a, Ja + 6 * d);
-        e[0] = gap >= 0.0 ? gap / h : gamma * gap / h;
+        for (int d = 0; d < 3; ++d) side_row(sa, dirs[d], anc_a, Ja + 6 * d);
+        e[0] = gap >= 0.0 ? gap * ih : gamma * gap * ih;
         e[1] = 0.0;
         e[2] = 0.0;
     }
@@ -160,6 +195,22 @@ __device__ __forceinline__ void body_dynamics(const double *B, double h, double 
         b[d] = c2h * m * v[d] + m * g[d];
         b[3 + d] = c2h * Iw[d] - gyro[d];
     }
+}
+
+// Linear elastic block (Eq. ddyn with the elastic force at the midpoint): the diagonal part
+// (2/h) m of A and b_p = (2/h) m v_p - (K (x - X0))_p + f_p + m g_p (K sparse, CSR).
+__device__ __forceinline__ double linear_b(int p, const double *mass, const double *f,
+                                           const double *X0, const double *Kval, const int *rowp,
+                                           const int *col, const double *nodes, double h,
+                                           const double *g)
+{
+    double kx = 0.0;
+    for (int q = rowp[p]; q < rowp[p + 1]; ++q) {
+        const int cq = col[q];
+        kx += Kval[q] * (nodes[(cq / 3) * SUBADMM_NODE + cq % 3] - X0[cq]);
+    }
+    const double m = mass[p / 3];
+    return (2.0 / h) * m * nodes[(p / 3) * SUBADMM_NODE + 3 + p % 3] - kx + f[p] + m * g[p % 3];
 }
 
 // v_{k+1} = 2 v-hat - v_k; p += h v-hat; q <- q (x) Exp(h w-hat), renormalised.

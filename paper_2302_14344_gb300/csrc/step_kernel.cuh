@@ -249,6 +249,22 @@ __device__ void scene_setup(const StepParams &P, const SceneDesc &S, const View<
         if (u.kind == KIND_RIGID) {
             for (int q = lane; q < u.m * u.n; q += 32) J[q] = 0.0;
             for (int q = lane; q < u.n * u.n; q += 32) K[q] = 0.0;
+        } else if (u.kind == KIND_LINEAR) {
+            // A = (2/h) M + (h/2) K_el (K_el sparse, scattered into the dense block);
+            // b from the node state (Eq. ddyn, elastic force at the midpoint)
+            for (int q = lane; q < u.m * u.n; q += 32) J[q] = 0.0;
+            for (int q = lane; q < u.n * u.n; q += 32) K[q] = 0.0;
+            __syncwarp();
+            const double *mass = P.pool + u.gen_off;
+            const double *f = mass + u.nb, *X0 = f + u.n, *Kval = X0 + u.n;
+            const int *rowp = P.ipool + u.csr_off, *col = rowp + u.n + 1;
+            const double gv[3] = {P.g0, P.g1, P.g2};
+            const double *nodes = P.nodes + (size_t)u.body0 * SUBADMM_NODE;
+            for (int p = lane; p < u.n; p += 32) {
+                for (int q = rowp[p]; q < rowp[p + 1]; ++q) K[p * u.n + col[q]] = 0.5 * P.h * Kval[q];
+                K[p * u.n + p] += (2.0 / P.h) * mass[p / 3];
+                sdb[u.od_b + p] = linear_b(p, mass, f, X0, Kval, rowp, col, nodes, P.h, gv);
+            }
         } else {
             const double *A = P.pool + u.gen_off;
             for (int q = lane; q < u.n * u.n; q += 32) K[q] = A[q];
@@ -293,20 +309,23 @@ __device__ void scene_setup(const StepParams &P, const SceneDesc &S, const View<
             }
         } else {
             double Ja[30], Jb[30], ee[5], kk = 0.0, al = 0.0;
-            model_rows(c, P.pool + c.par_off, P.bodies, P.h, P.gamma, Ja, Jb, ee, &kk, &al);
+            model_rows(c, P.pool + c.par_off, P.bodies, P.nodes, P.h, P.gamma, Ja, Jb, ee, &kk, &al);
             for (int r = 0; r < c.rows; ++r) E[c.row0 + r] = (T)ee[r];
             {
+                // a body side fills 6 columns at 6 * index, a node side 3 columns at 3 * index
                 const SubDesc &u = P.subs[S.sub0 + c.sub[0]];
+                const int wa = c.node_a ? 3 : 6;
                 for (int r = 0; r < c.rows; ++r) {
-                    double *Jr = sdb + u.od_J + (c.sr[0] + r - u.sr0) * u.n + 6 * c.ba;
-                    for (int q = 0; q < 6; ++q) Jr[q] = Ja[6 * r + q];
+                    double *Jr = sdb + u.od_J + (c.sr[0] + r - u.sr0) * u.n + wa * c.ba;
+                    for (int q = 0; q < wa; ++q) Jr[q] = Ja[6 * r + q];
                 }
             }
             if (c.side_b >= 0) {
                 const SubDesc &u = P.subs[S.sub0 + c.sub[c.side_b]];
+                const int wb = c.node_b ? 3 : 6;
                 for (int r = 0; r < c.rows; ++r) {
-                    double *Jr = sdb + u.od_J + (c.sr[c.side_b] + r - u.sr0) * u.n + 6 * c.bb;
-                    for (int q = 0; q < 6; ++q) Jr[q] = Jb[6 * r + q];
+                    double *Jr = sdb + u.od_J + (c.sr[c.side_b] + r - u.sr0) * u.n + wb * c.bb;
+                    for (int q = 0; q < wb; ++q) Jr[q] += Jb[6 * r + q];
                 }
             }
         }
@@ -632,7 +651,7 @@ __device__ void recover_v(const StepParams &P, const SceneDesc &S, const View<T>
 }
 
 template <typename T, int SPLIT, bool CACHED>
-__global__ void __launch_bounds__(SUBADMM_THREADS, 1) step_kernel(StepParams P)
+__global__ void __launch_bounds__(SUBADMM_THREADS, CACHED ? 1 : 2) step_kernel(StepParams P)
 {
     using VT = typename VecOf<T>::V;
     using U = typename VecOf<T>::U;
@@ -1043,6 +1062,15 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 1) step_kernel(StepParams P)
                 const SubDesc &u = P.subs[S.sub0 + i];
                 const double *v = V.sdb + u.od_v;
                 for (int p = lane; p < u.n; p += 32) P.vhat[u.v_off + p] = v[p];
+                if (u.kind == KIND_LINEAR) {
+                    double *nd = P.nodes + (size_t)u.body0 * SUBADMM_NODE;
+                    for (int p = lane; p < u.n; p += 32) {
+                        nd[(p / 3) * SUBADMM_NODE + p % 3] += P.h * v[p];
+                        double &vel = nd[(p / 3) * SUBADMM_NODE + 3 + p % 3];
+                        vel = 2.0 * v[p] - vel;
+                    }
+                    continue;
+                }
                 if (u.kind != KIND_RIGID) continue;
                 for (int k = lane; k < u.nb; k += 32)
                     body_update(P.bodies + (size_t)(u.body0 + k) * SUBADMM_BODY, v + 6 * k, P.h);

@@ -23,6 +23,9 @@ struct HostSub {
     int scene = 0, kind = 0, n = 0, nb = 0;
     std::vector<double> Ab;      // generic: A (n*n) then b (n)
     std::vector<double> bodies;  // rigid: nb records of 17
+    std::vector<double> lin;     // linear: mass (nb), f (n), X0 (n), K values (CSR)
+    std::vector<int> csr;        // linear: K row pointers (n+1), then column indices
+    std::vector<double> nodes;   // linear: nb records of 6 (x[3], v[3])
 };
 
 struct HostCon {
@@ -68,6 +71,9 @@ struct sim_s {
     long long *d_stats = nullptr;
     long long *d_phase = nullptr;  // phase tracer counters (8 per scene) when enabled
     double *d_work = nullptr;      // per-subsystem arrays of scenes too large for shared memory
+    double *d_nodes = nullptr;     // node states of linear blocks
+    int *d_ipool = nullptr;        // integer constant data
+    long long nnodes = 0;
     long long work_bytes = 0;
     size_t pool_size = 0;
 };
@@ -112,23 +118,39 @@ int model_type_of(int src)
 }
 
 // pack / unpack of the 13 state doubles (p, q, v, w) of every body record
-__global__ void pack_state(const double *bodies, double *out, long long nb)
+// Packed state: 13 doubles per rigid body (p, q, v, w), then 6 per node of the linear blocks
+// (x, v; the node records are stored in exactly that layout).
+__global__ void pack_state(const double *bodies, const double *nodes, double *out, long long nb,
+                           long long nn)
 {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nb * 13;
+    const long long nbd = nb * 13, total = nbd + nn * SUBADMM_NODE;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
-        const long long b = i / 13, k = i - b * 13;
-        out[i] = bodies[b * SUBADMM_BODY + 4 + k];
+        if (i < nbd) {
+            const long long b = i / 13, k = i - b * 13;
+            out[i] = bodies[b * SUBADMM_BODY + 4 + k];
+        } else {
+            out[i] = nodes[i - nbd];
+        }
     }
 }
 
-__global__ void unpack_state(double *bodies, const double *in, long long nb)
+__global__ void unpack_state(double *bodies, double *nodes, const double *in, long long nb,
+                             long long nn)
 {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nb * 13;
+    const long long nbd = nb * 13, total = nbd + nn * SUBADMM_NODE;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
-        const long long b = i / 13, k = i - b * 13;
-        bodies[b * SUBADMM_BODY + 4 + k] = in[i];
+        if (i < nbd) {
+            const long long b = i / 13, k = i - b * 13;
+            bodies[b * SUBADMM_BODY + 4 + k] = in[i];
+        } else {
+            nodes[i - nbd] = in[i];
+        }
     }
 }
+
+long long state_doubles(const sim_t s) { return 13 * s->nbodies + SUBADMM_NODE * s->nnodes; }
 
 void free_device(sim_t s)
 {
@@ -141,6 +163,8 @@ void free_device(sim_t s)
     s->d_phase = nullptr;
     cudaFree(s->d_work);
     s->d_work = nullptr;
+    cudaFree(s->d_nodes); cudaFree(s->d_ipool);
+    s->d_nodes = nullptr; s->d_ipool = nullptr;
     s->d_scenes = nullptr; s->d_subs = nullptr; s->d_cons = nullptr; s->d_pool = nullptr;
     s->d_bodies = nullptr; s->d_vhat = nullptr; s->d_lam = nullptr; s->d_z = nullptr;
     s->d_beta = nullptr; s->d_res = nullptr; s->d_stats = nullptr; s->d_stage = nullptr;
@@ -191,6 +215,8 @@ int finalize(sim_t s)
 
     std::vector<double> pool;
     std::vector<double> bodies;
+    std::vector<double> nodes;
+    std::vector<int> ipool;
     std::vector<Item> items;
     std::vector<int> lists;
     std::vector<int> asm_order;
@@ -226,8 +252,15 @@ int finalize(sim_t s)
             u.nb = h.nb;
             u.body0 = (int)(bodies.size() / SUBADMM_BODY);
             if (h.kind == KIND_RIGID) bodies.insert(bodies.end(), h.bodies.begin(), h.bodies.end());
+            if (h.kind == KIND_LINEAR) {
+                u.body0 = (int)(nodes.size() / SUBADMM_NODE);
+                nodes.insert(nodes.end(), h.nodes.begin(), h.nodes.end());
+                u.csr_off = (int)ipool.size();
+                ipool.insert(ipool.end(), h.csr.begin(), h.csr.end());
+            }
             u.gen_off = (int)pool.size();
             if (h.kind == KIND_GENERIC) pool.insert(pool.end(), h.Ab.begin(), h.Ab.end());
+            if (h.kind == KIND_LINEAR) pool.insert(pool.end(), h.lin.begin(), h.lin.end());
             u.v_off = (int)dof;
             dof += h.n;
         }
@@ -249,6 +282,7 @@ int finalize(sim_t s)
                 c.sub[q] = d - S.sub0;
             }
             c.ba = h.ba; c.bb = h.bb; c.gb_a = -1; c.gb_b = -1; c.side_b = -1;
+            c.node_a = 0; c.node_b = 0;
         }
         S.nrow = row;
         // side-rows, subsystem by subsystem so each subsystem's rows are contiguous; each
@@ -284,9 +318,12 @@ int finalize(sim_t s)
             if (h.src <= SRC_CONTACT) continue;
             const SubDesc &ua = s->sdesc[s->sub_dev[h.sa]];
             c.gb_a = ua.body0 + h.ba;
+            c.node_a = ua.kind == KIND_LINEAR ? 1 : 0;
+            c.node_b = 0;
             if (h.sb >= 0) {
                 const SubDesc &ub = s->sdesc[s->sub_dev[h.sb]];
                 c.gb_b = ub.body0 + h.bb;
+                c.node_b = ub.kind == KIND_LINEAR ? 1 : 0;
                 c.side_b = (h.sb == h.sa) ? 0 : 1;
             }
         }
@@ -437,13 +474,16 @@ int finalize(sim_t s)
                     max_sides <= 2 && (max_mpad + vn - 1) / vn <= chunks * s->split;
     }
     if ((rc = upload(s, &s->d_bodies, bodies, "bodies"))) return rc;
+    if ((rc = upload(s, &s->d_nodes, nodes, "nodes"))) return rc;
+    if ((rc = upload(s, &s->d_ipool, ipool, "integer pool"))) return rc;
+    s->nnodes = (long long)(nodes.size() / SUBADMM_NODE);
     s->pool_size = pool.size();
     if ((rc = zeros(s, &s->d_vhat, (size_t)dof, "vhat"))) return rc;
     if ((rc = zeros(s, &s->d_lam, (size_t)rows_g, "lambda"))) return rc;
     if ((rc = zeros(s, &s->d_z, (size_t)sr_g, "z"))) return rc;
     if ((rc = zeros(s, &s->d_beta, (size_t)nsubs, "beta"))) return rc;
     if ((rc = zeros(s, &s->d_res, (size_t)6 * nscenes, "residuals"))) return rc;
-    if ((rc = zeros(s, &s->d_stage, (size_t)13 * s->nbodies, "state staging"))) return rc;
+    if ((rc = zeros(s, &s->d_stage, (size_t)state_doubles(s), "state staging"))) return rc;
     {
         cudaError_t e = cudaMalloc((void **)&s->d_stats, std::max(1, 4 * nscenes) * sizeof(long long));
         if (e != cudaSuccess) return fail(s, SIM_ENOMEM, "cudaMalloc stats");
@@ -565,6 +605,49 @@ int sim_add_subsystem(sim_t s, int scene, int kind, int count, const double *dat
             if (!(r[0] > 0.0) || !(r[1] > 0.0) || !(r[2] > 0.0) || !(r[3] > 0.0))
                 return fail(s, SIM_EINVAL, "body mass and inertia must be positive");
         }
+    } else if (kind == SIM_SUB_LINEAR) {
+        // data: mass (nn), f (n), X0 (n), x (n), v (n), nnz, then nnz triplets (row, col,
+        // value) of the symmetric stiffness K, indices stored exactly as doubles
+        const int nn = count, n = 3 * count;
+        if (n > SUBADMM_MAXN) return fail(s, SIM_EINVAL, "linear subsystem larger than 1024 DOF");
+        u.kind = KIND_LINEAR; u.nb = nn; u.n = n;
+        const double *mass = data, *f = data + nn, *X0 = f + n, *x = X0 + n, *v = x + n;
+        const double nnzd = v[n];
+        if (!(nnzd >= 0.0) || nnzd > (double)n * n || nnzd != (double)(long long)nnzd)
+            return fail(s, SIM_EINVAL, "bad non-zero count of K");
+        const long long nnz = (long long)nnzd;
+        const double *trip = v + n + 1;
+        for (int q = 0; q < nn; ++q)
+            if (!(mass[q] > 0.0)) return fail(s, SIM_EINVAL, "node masses must be positive");
+        for (long long q = 0; q < (long long)nn + 4LL * n + 3 * nnz; ++q)
+            if (!std::isfinite(data[q])) return fail(s, SIM_EINVAL, "non-finite linear block data");
+        std::vector<std::vector<std::pair<int, double>>> rows(n);
+        for (long long t = 0; t < nnz; ++t) {
+            const double rd = trip[3 * t], cd = trip[3 * t + 1];
+            if (rd < 0 || rd >= n || cd < 0 || cd >= n || rd != (double)(int)rd || cd != (double)(int)cd)
+                return fail(s, SIM_EINVAL, "K index out of range");
+            rows[(int)rd].push_back({(int)cd, trip[3 * t + 2]});
+        }
+        u.lin.assign(mass, mass + nn);
+        u.lin.insert(u.lin.end(), f, f + n);
+        u.lin.insert(u.lin.end(), X0, X0 + n);
+        u.csr.assign(1, 0);
+        std::vector<int> cols;
+        for (int p = 0; p < n; ++p) {
+            std::sort(rows[p].begin(), rows[p].end());
+            for (size_t q = 0; q < rows[p].size(); ++q) {
+                if (q + 1 < rows[p].size() && rows[p][q + 1].first == rows[p][q].first)
+                    return fail(s, SIM_EINVAL, "duplicate K entry");
+                cols.push_back(rows[p][q].first);
+                u.lin.push_back(rows[p][q].second);
+            }
+            u.csr.push_back((int)cols.size());
+        }
+        u.csr.insert(u.csr.end(), cols.begin(), cols.end());
+        for (int q = 0; q < nn; ++q) {
+            for (int d = 0; d < 3; ++d) u.nodes.push_back(x[3 * q + d]);
+            for (int d = 0; d < 3; ++d) u.nodes.push_back(v[3 * q + d]);
+        }
     } else {
         return fail(s, SIM_EINVAL, "unknown subsystem kind");
     }
@@ -594,13 +677,19 @@ int sim_add_interface(sim_t s, int scene, int kind, int rows, int n_sides, const
         const int sa = sides[0], ba = sides[1];
         int sb = sides[2], bb = sides[3];
         if (kind == SIM_IF_PLANE_CONTACT) { sb = -1; bb = 0; }
-        if (sa < 0 || sa >= (int)s->subs.size() || s->subs[sa].kind != KIND_RIGID)
-            return fail(s, SIM_EINVAL, "side a must be a rigid subsystem");
+        // a node of a linear block may be a side of a ball joint or a plane contact
+        const bool node_ok = kind == SIM_IF_BALL || kind == SIM_IF_PLANE_CONTACT;
+        auto side_kind_ok = [&](int sub) {
+            const int kd = s->subs[sub].kind;
+            return kd == KIND_RIGID || (kd == KIND_LINEAR && node_ok);
+        };
+        if (sa < 0 || sa >= (int)s->subs.size() || !side_kind_ok(sa))
+            return fail(s, SIM_EINVAL, "side a must be a rigid subsystem (or a linear one for BALL / PLANE_CONTACT)");
         if (ba < 0 || ba >= s->subs[sa].nb) return fail(s, SIM_EINVAL, "body a out of range");
         if (s->subs[sa].scene != scene) return fail(s, SIM_EINVAL, "body a belongs to another scene");
         if (sb >= 0) {
-            if (sb >= (int)s->subs.size() || s->subs[sb].kind != KIND_RIGID)
-                return fail(s, SIM_EINVAL, "side b must be a rigid subsystem or -1");
+            if (sb >= (int)s->subs.size() || !side_kind_ok(sb))
+                return fail(s, SIM_EINVAL, "side b must be a rigid subsystem (or a linear one for BALL), or -1");
             if (bb < 0 || bb >= s->subs[sb].nb) return fail(s, SIM_EINVAL, "body b out of range");
             if (sb == sa && bb == ba) return fail(s, SIM_EINVAL, "a body cannot be joined to itself");
             if (s->subs[sb].scene != scene) return fail(s, SIM_EINVAL, "body b belongs to another scene");
@@ -657,6 +746,8 @@ int sim_step(sim_t s, int n_steps)
     P.scenes = s->d_scenes; P.subs = s->d_subs; P.cons = s->d_cons; P.pool = s->d_pool;
     P.bodies = s->d_bodies; P.vhat = s->d_vhat; P.lam = s->d_lam; P.z = s->d_z;
     P.work = s->d_work;
+    P.nodes = s->d_nodes;
+    P.ipool = s->d_ipool;
     P.beta = s->d_beta; P.res = s->d_res; P.stats = s->d_stats; P.phase = s->d_phase;
     P.nscenes = s->nscenes;
     P.n_steps = n_steps;
@@ -730,6 +821,14 @@ int sim_get(sim_t s, int what, int id, double *dst)
         }
         return SIM_OK;
     }
+    if (what == SIM_GET_NODES) {
+        if (id < 0 || id >= (int)s->subs.size()) return fail(s, SIM_EINVAL, "subsystem id out of range");
+        const SubDesc &u = s->sdesc[s->sub_dev[id]];
+        if (u.kind != KIND_LINEAR) return fail(s, SIM_EINVAL, "not a linear subsystem");
+        CK(cudaMemcpy(dst, s->d_nodes + (size_t)u.body0 * SUBADMM_NODE,
+                      sizeof(double) * SUBADMM_NODE * u.nb, cudaMemcpyDeviceToHost), "get");
+        return SIM_OK;
+    }
     if (what == SIM_GET_LAMBDA || what == SIM_GET_Z) {
         if (id < 0 || id >= (int)s->cons.size()) return fail(s, SIM_EINVAL, "interface id out of range");
         const int d = s->con_dev[id];
@@ -751,11 +850,12 @@ int sim_read_state(sim_t s, double *dst)
     if (!s || !dst) return SIM_EINVAL;
     int rc = finalize(s);
     if (rc) return rc;
-    if (s->nbodies == 0) return SIM_OK;
-    const int grid = (int)std::min<long long>((13 * s->nbodies + 255) / 256, 1024);
-    pack_state<<<grid, 256, 0, s->stream>>>(s->d_bodies, s->d_stage, s->nbodies);
+    const long long nd = state_doubles(s);
+    if (nd == 0) return SIM_OK;
+    const int grid = (int)std::min<long long>((nd + 255) / 256, 1024);
+    pack_state<<<grid, 256, 0, s->stream>>>(s->d_bodies, s->d_nodes, s->d_stage, s->nbodies, s->nnodes);
     CK(cudaGetLastError(), "pack state");
-    CK(cudaMemcpyAsync(dst, s->d_stage, sizeof(double) * 13 * s->nbodies, cudaMemcpyDeviceToHost, s->stream), "read state");
+    CK(cudaMemcpyAsync(dst, s->d_stage, sizeof(double) * nd, cudaMemcpyDeviceToHost, s->stream), "read state");
     CK(cudaStreamSynchronize(s->stream), "read state sync");
     return SIM_OK;
 }
@@ -783,9 +883,11 @@ int sim_read_state_noalloc(sim_t s, double *dst)
     if (!s->finalized)
         return fail(s, SIM_EINVAL, "sim_read_state_noalloc needs a simulation whose device memory "
                                    "is laid out (after its first sim_step)");
-    if (s->nbodies == 0) return SIM_OK;
-    if (13 * s->nbodies > kNoallocStageDoubles)
-        return fail(s, SIM_EINVAL, "sim_read_state_noalloc holds at most 10082 bodies (1 MiB staging)");
+    const long long nd = state_doubles(s);
+    if (nd == 0) return SIM_OK;
+    if (nd > kNoallocStageDoubles)
+        return fail(s, SIM_EINVAL, "sim_read_state_noalloc holds at most 131072 state doubles "
+                                   "(1 MiB staging)");
     const int dev = s->opt.device;
     if (dev < 0 || dev >= kNoallocMaxDevices) return fail(s, SIM_EINVAL, "device ordinal too large");
     CK(cudaSetDevice(dev), "cudaSetDevice");
@@ -800,11 +902,10 @@ int sim_read_state_noalloc(sim_t s, double *dst)
         }
         stage = g_noalloc_addr[dev];
     }
-    const int grid = (int)std::min<long long>((13 * s->nbodies + 255) / 256, 1024);
-    pack_state<<<grid, 256, 0, s->stream>>>(s->d_bodies, stage, s->nbodies);
+    const int grid = (int)std::min<long long>((nd + 255) / 256, 1024);
+    pack_state<<<grid, 256, 0, s->stream>>>(s->d_bodies, s->d_nodes, stage, s->nbodies, s->nnodes);
     CK(cudaGetLastError(), "pack state");
-    CK(cudaMemcpyAsync(dst, stage, sizeof(double) * 13 * s->nbodies, cudaMemcpyDeviceToHost, s->stream),
-       "read state");
+    CK(cudaMemcpyAsync(dst, stage, sizeof(double) * nd, cudaMemcpyDeviceToHost, s->stream), "read state");
     CK(cudaStreamSynchronize(s->stream), "read state sync");
     return SIM_OK;
 }
@@ -814,15 +915,16 @@ int sim_write_state(sim_t s, const double *src)
     if (!s || !src) return SIM_EINVAL;
     int rc = finalize(s);
     if (rc) return rc;
-    if (s->nbodies == 0) return SIM_OK;
-    CK(cudaMemcpyAsync(s->d_stage, src, sizeof(double) * 13 * s->nbodies, cudaMemcpyHostToDevice, s->stream), "write state");
-    const int grid = (int)std::min<long long>((13 * s->nbodies + 255) / 256, 1024);
-    unpack_state<<<grid, 256, 0, s->stream>>>(s->d_bodies, s->d_stage, s->nbodies);
+    const long long nd = state_doubles(s);
+    if (nd == 0) return SIM_OK;
+    CK(cudaMemcpyAsync(s->d_stage, src, sizeof(double) * nd, cudaMemcpyHostToDevice, s->stream), "write state");
+    const int grid = (int)std::min<long long>((nd + 255) / 256, 1024);
+    unpack_state<<<grid, 256, 0, s->stream>>>(s->d_bodies, s->d_nodes, s->d_stage, s->nbodies, s->nnodes);
     CK(cudaGetLastError(), "unpack state");
     return SIM_OK;
 }
 
-int sim_sizes(sim_t s, long long out[8])
+int sim_sizes(sim_t s, long long out[9])
 {
     if (!s || !out) return SIM_EINVAL;
     int rc = finalize(s);
@@ -835,6 +937,7 @@ int sim_sizes(sim_t s, long long out[8])
     out[5] = s->nsr;
     out[6] = s->nbodies;
     out[7] = s->max_smem;
+    out[8] = s->nnodes;
     return SIM_OK;
 }
 

@@ -18,14 +18,14 @@ from . import build as _build
 
 SIM_OK, SIM_NOT_CONVERGED = 0, 1
 SIM_EINVAL, SIM_ENOMEM, SIM_ENOTSPD, SIM_ENAN, SIM_ECUDA = -1, -2, -3, -4, -5
-SIM_SUB_GENERIC, SIM_SUB_RIGID = 0, 1
+SIM_SUB_GENERIC, SIM_SUB_RIGID, SIM_SUB_LINEAR = 0, 1, 2
 SIM_IF_EQUALITY, SIM_IF_HARD, SIM_IF_SOFT, SIM_IF_CONTACT = 0, 1, 2, 3
 SIM_IF_BALL, SIM_IF_REVOLUTE, SIM_IF_ANGLE_PD, SIM_IF_PLANE_CONTACT = 4, 5, 6, 7
 SIM_BETA_TRACE, SIM_BETA_FIXED = 0, 1
 SIM_WARM_COLD, SIM_WARM_PREV = 0, 1
 SIM_STOP_PRIMAL, SIM_STOP_THETA = 0, 1
 SIM_FP64, SIM_MIXED = 0, 1
-SIM_GET_VHAT, SIM_GET_LAMBDA, SIM_GET_BODIES, SIM_GET_BETA, SIM_GET_Z = 0, 1, 2, 3, 4
+SIM_GET_VHAT, SIM_GET_LAMBDA, SIM_GET_BODIES, SIM_GET_BETA, SIM_GET_Z, SIM_GET_NODES = range(6)
 
 # exported symbols of include/subadmm.h
 EXPORTS = ("sim_default_options", "sim_create", "sim_destroy", "sim_add_subsystem",
@@ -178,7 +178,8 @@ def sim_get(h, what: int, id_: int, count: int) -> np.ndarray:
 
 
 def sim_read_state(h, dst_ptr: int) -> None:
-    """dst_ptr: address of a host buffer of 13 doubles per body (e.g. a pinned tensor)."""
+    """dst_ptr: address of a host buffer of 13 doubles per body followed by 6 per node (e.g.
+    a pinned tensor)."""
     _check(h, load().sim_read_state(h, VP(dst_ptr)))
 
 
@@ -193,10 +194,10 @@ def sim_write_state(h, src_ptr: int) -> None:
 
 
 def sim_sizes(h) -> dict:
-    out = (C.c_longlong * 8)()
+    out = (C.c_longlong * 9)()
     _check(h, load().sim_sizes(h, out))
     keys = ("scenes", "subsystems", "dof", "interfaces", "rows", "side_rows", "bodies",
-            "smem_bytes")
+            "smem_bytes", "nodes")
     return {k: int(v) for k, v in zip(keys, out)}
 
 
@@ -275,6 +276,7 @@ class Simulation:
         self.if_rows = []
         self.if_nsides = []
         self.rigid_subs = []
+        self.linear_subs = []
         for sc_i, sc in enumerate(problem.scenes):
             ids = []
             for sub in sc.subs:
@@ -283,6 +285,13 @@ class Simulation:
                                           for b in sub.bodies])
                     sid = sim_add_subsystem(self.h, sc_i, SIM_SUB_RIGID, len(sub.bodies), rec)
                     self.rigid_subs.append((sid, len(sub.bodies)))
+                elif hasattr(sub, "Kv"):
+                    trip = np.stack([np.asarray(sub.Ki, float), np.asarray(sub.Kj, float),
+                                     np.asarray(sub.Kv, float)], axis=1).ravel()
+                    data = np.concatenate([sub.mass, sub.f, sub.X0, sub.x, sub.v,
+                                           [float(len(sub.Kv))], trip])
+                    sid = sim_add_subsystem(self.h, sc_i, SIM_SUB_LINEAR, sub.nodes, data)
+                    self.linear_subs.append((sid, sub.nodes))
                 else:
                     data = np.concatenate([np.asarray(sub.A, float).ravel(),
                                            np.asarray(sub.b, float)])
@@ -352,6 +361,16 @@ class Simulation:
 
     def bodies(self, sid: int, nb: int) -> np.ndarray:
         return sim_get(self.h, SIM_GET_BODIES, sid, 17 * nb).reshape(nb, 17)
+
+    def nodes(self, sid: int, nn: int) -> np.ndarray:
+        return sim_get(self.h, SIM_GET_NODES, sid, 6 * nn).reshape(nn, 6)
+
+    def scene_nodes(self, scene: int) -> np.ndarray:
+        out = []
+        for sid, nn in self.linear_subs:
+            if sid in self.sub_ids[scene]:
+                out.append(self.nodes(sid, nn))
+        return np.concatenate(out) if out else np.zeros((0, 6))
 
     def scene_vhat(self, scene: int) -> np.ndarray:
         return np.concatenate([self.vhat(s) for s in self.sub_ids[scene]])

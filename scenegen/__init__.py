@@ -70,6 +70,83 @@ class RigidSub:
 
 
 @dataclass
+class LinearSub:
+    """A linear elastic block of nodes (3 DOF each): lumped node masses, a symmetric
+    stiffness K given by triplets (Ki, Kj, Kv), a constant force f, rest positions X0,
+    positions x and velocities v (each 3 * nodes long)."""
+
+    mass: np.ndarray
+    Ki: np.ndarray
+    Kj: np.ndarray
+    Kv: np.ndarray
+    f: np.ndarray
+    X0: np.ndarray
+    x: np.ndarray
+    v: np.ndarray
+
+    @property
+    def nodes(self) -> int:
+        return int(self.mass.shape[0])
+
+    @property
+    def n(self) -> int:
+        return 3 * self.nodes
+
+    def K_dense(self) -> np.ndarray:
+        K = np.zeros((self.n, self.n))
+        np.add.at(K, (self.Ki.astype(int), self.Kj.astype(int)), self.Kv)
+        return K
+
+
+def spring_stiffness(X: np.ndarray, edges, k: float):
+    """Stiffness triplets of linear springs (stiffness k) along the rest directions of the
+    given node pairs: each spring adds k d d^T to the (a,a), (b,b) blocks and -k d d^T to the
+    (a,b), (b,a) blocks, d the unit rest direction."""
+    acc = {}
+    for a, b in edges:
+        d = X[b] - X[a]
+        d = d / np.linalg.norm(d)
+        blk = k * np.outer(d, d)
+        for (p, q, s) in ((a, a, 1.0), (b, b, 1.0), (a, b, -1.0), (b, a, -1.0)):
+            for i in range(3):
+                for j in range(3):
+                    key = (3 * p + i, 3 * q + j)
+                    acc[key] = acc.get(key, 0.0) + s * blk[i, j]
+    keys = sorted(k_ for k_, v_ in acc.items() if v_ != 0.0)
+    Ki = np.array([k_[0] for k_ in keys], dtype=np.int64)
+    Kj = np.array([k_[1] for k_ in keys], dtype=np.int64)
+    Kv = np.array([acc[k_] for k_ in keys])
+    return Ki, Kj, Kv
+
+
+_LATTICE_CACHE: dict = {}
+
+
+def _lattice_stiffness(dims, spacing, k):
+    key = (tuple(dims), float(spacing), float(k))
+    if key not in _LATTICE_CACHE:
+        nx, ny, nz = dims
+        X = np.array([[i * spacing, j * spacing, l * spacing] for l in range(nz)
+                      for j in range(ny) for i in range(nx)], dtype=np.float64)
+        d = np.linalg.norm(X[None, :, :] - X[:, None, :], axis=2)
+        a, b = np.nonzero(np.triu(d < 1.8 * spacing, 1))
+        _LATTICE_CACHE[key] = (X, spring_stiffness(X, list(zip(a.tolist(), b.tolist())), k))
+    return _LATTICE_CACHE[key]
+
+
+def lattice_block(dims=(2, 2, 3), spacing=0.02, origin=(0.0, 0.0, 0.0), density=1000.0,
+                  k=500.0, v=None) -> LinearSub:
+    """Nodes on a dims grid joined by springs to their neighbours within one cell diagonal
+    (a stand-in for a small linear FEM block); lumped mass = density * spacing^3 per node."""
+    X, (Ki, Kj, Kv) = _lattice_stiffness(dims, spacing, k)
+    X = X + np.asarray(origin, dtype=np.float64)
+    nn = X.shape[0]
+    mass = np.full(nn, density * spacing ** 3)
+    vv = np.zeros(3 * nn) if v is None else np.tile(np.asarray(v, dtype=np.float64), nn)
+    return LinearSub(mass, Ki, Kj, Kv, np.zeros(3 * nn), X.ravel().copy(), X.ravel().copy(), vv)
+
+
+@dataclass
 class RowsIf:
     """An interface given by explicit rows.
 
@@ -388,6 +465,144 @@ def generic(seed: int = 0, n_scenes: int = 4, tol_primal: float = -1.0, max_iter
     return Problem(scenes, opts, name="generic")
 
 
+def hanging_scene(rng: np.random.Generator, n_blocks: int = 2, dims=(2, 2, 3),
+                  with_body: bool = True, drop: float = 0.004) -> Scene:
+    """Spring blocks pinned at two top nodes, one above the plane z = 0 with node contacts,
+    and a rigid box hung from the first block by a ball joint (mixed rigid / linear scene)."""
+    subs, ifs = [], []
+    for b in range(n_blocks):
+        blk = lattice_block(dims=dims, spacing=0.02, origin=(0.1 * b, 0.0, drop), k=400.0,
+                            v=rng.uniform(-0.05, 0.05, 3))
+        subs.append(blk)
+    nn = subs[0].nodes
+    top = nn - dims[0] * dims[1]
+    for b in range(1, n_blocks):
+        X = subs[b].X0
+        ifs.append(JointIf(BALL, a=(b, top), b=None, anchor_b=X[3 * top:3 * top + 3].copy()))
+        ifs.append(JointIf(BALL, a=(b, top + 1), b=None,
+                           anchor_b=X[3 * (top + 1):3 * (top + 1) + 3].copy()))
+    for k in range(dims[0] * dims[1]):        # the bottom layer of block 0 touches the plane
+        ifs.append(JointIf(PLANE_CONTACT, a=(0, k), plane_z=0.0,
+                           mu=float(rng.uniform(0.3, 1.0))))
+    if with_body:
+        X = subs[-1].X0
+        pin = X[0:3]
+        box = Body(0.05, box_inertia(0.05, 0.02, 0.02, 0.02), pin + np.array([0.0, 0.0, -0.03]),
+                   np.array([1.0, 0.0, 0.0, 0.0]), np.zeros(3), np.zeros(3))
+        subs.append(RigidSub([box]))
+        ifs.append(JointIf(BALL, a=(len(subs) - 1, 0), b=(n_blocks - 1, 0),
+                           anchor_a=np.array([0.0, 0.0, 0.03])))
+    return Scene(subs, ifs)
+
+
+def _random_rotation(rng) -> np.ndarray:
+    return _quat_from_rotvec(rng.uniform(-np.pi, np.pi, 3) * 0.3)
+
+
+def _floating_chain(rng, links: int, L=0.05, w=0.01) -> RigidSub:
+    """A straight chain of `links` boxes along a random direction (joined by ball joints at
+    their ends, added by the caller)."""
+    m = L * w * w * 1000.0
+    I = box_inertia(m, L, w, w)
+    q = _random_rotation(rng)
+    R = _quat_to_mat(q)
+    ax = R @ np.array([L, 0.0, 0.0])
+    bodies = [Body(m, I.copy(), ax * k, q.copy(), np.zeros(3), np.zeros(3)) for k in range(links)]
+    return RigidSub(bodies)
+
+
+def _point_of(sub, idx, rng):
+    """(anchor in the body frame or None for a node, world point) of an attachment site."""
+    if isinstance(sub, RigidSub):
+        b = sub.bodies[idx]
+        anc = np.array([rng.choice([-0.025, 0.025]), 0.0, 0.0])
+        return anc, b.p + _quat_to_mat(b.q) @ anc
+    return None, sub.x[3 * idx:3 * idx + 3].copy()
+
+
+def _shift(sub, d):
+    if isinstance(sub, RigidSub):
+        for b in sub.bodies:
+            b.p = b.p + d
+    else:
+        sub.x = sub.x + np.tile(d, sub.nodes)
+        sub.X0 = sub.X0 + np.tile(d, sub.nodes)
+
+
+def _sites(sub) -> int:
+    return len(sub.bodies) if isinstance(sub, RigidSub) else sub.nodes
+
+
+def batched_scene(rng: np.random.Generator, n_sub=(2, 32), n_range=(6, 240), contacts=(0, 64),
+                  mu=(0.3, 1.0)) -> Scene:
+    """One scene of the batched workload: U{n_sub} subsystems with DOF log-uniform in
+    n_range, half rigid floating chains (6 DOF per link, links joined by ball joints) and half
+    spring blocks of 2 x 2 x k nodes (12 DOF per node layer); a random spanning tree of ball
+    joints plus floor(N/4) chords, each anchored at points that coincide at t = 0; U{contacts}
+    point contacts with the plane z = 0, friction uniform in mu."""
+    N = int(rng.integers(n_sub[0], n_sub[1] + 1))
+    subs, ifs = [], []
+    for i in range(N):
+        n_t = float(np.exp(rng.uniform(np.log(n_range[0]), np.log(n_range[1]))))
+        if rng.random() < 0.5:
+            links = int(np.clip(round(n_t / 6), 1, n_range[1] // 6))
+            sub = _floating_chain(rng, links)
+            for k in range(1, links):
+                ifs.append(JointIf(BALL, a=(i, k - 1), b=(i, k), anchor_a=np.array([0.025, 0, 0]),
+                                   anchor_b=np.array([-0.025, 0, 0])))
+        else:
+            layers = int(np.clip(round(n_t / 12), 1, n_range[1] // 12))
+            sub = lattice_block(dims=(2, 2, layers), spacing=0.02, k=400.0)
+        subs.append(sub)
+        if i > 0:
+            parent = int(rng.integers(0, i))
+            ip = int(rng.integers(0, _sites(subs[parent])))
+            anc_p, P = _point_of(subs[parent], ip, rng)
+            ic = int(rng.integers(0, _sites(sub)))
+            anc_c, Pc = _point_of(sub, ic, rng)
+            _shift(sub, P - Pc)
+            ifs.append(JointIf(BALL, a=(i, ic), b=(parent, ip),
+                               anchor_a=anc_c if anc_c is not None else np.zeros(3),
+                               anchor_b=anc_p if anc_p is not None else np.zeros(3)))
+    for _ in range(N // 4):
+        a, b = (int(v) for v in rng.choice(N, size=2, replace=False))
+        if not isinstance(subs[a], RigidSub):
+            a, b = b, a
+        if not isinstance(subs[a], RigidSub):
+            continue                         # node-node chords would start violated
+        ib = int(rng.integers(0, _sites(subs[b])))
+        anc_b, P = _point_of(subs[b], ib, rng)
+        ia = int(rng.integers(0, _sites(subs[a])))
+        body = subs[a].bodies[ia]
+        anc_a = _quat_to_mat(body.q).T @ (P - body.p)
+        ifs.append(JointIf(BALL, a=(a, ia), b=(b, ib), anchor_a=anc_a,
+                           anchor_b=anc_b if anc_b is not None else np.zeros(3)))
+    # rest the scene just above the plane, then the contact sites
+    zmin = min(min(b.p[2] for b in s.bodies) if isinstance(s, RigidSub) else s.x[2::3].min()
+               for s in subs)
+    lift = np.array([0.0, 0.0, -zmin + 0.03 + rng.uniform(0.0, 0.01)])
+    for s in subs:
+        _shift(s, lift)
+    for _ in range(int(rng.integers(contacts[0], contacts[1] + 1))):
+        i = int(rng.integers(0, N))
+        k = int(rng.integers(0, _sites(subs[i])))
+        anc = np.array([rng.choice([-0.025, 0.025]), 0.0, 0.0]) if isinstance(subs[i], RigidSub) \
+            else np.zeros(3)
+        ifs.append(JointIf(PLANE_CONTACT, a=(i, k), anchor_a=anc, plane_z=0.0,
+                           mu=float(rng.uniform(*mu))))
+    return Scene(subs, ifs)
+
+
+def batched(seed: int = 0, n_scenes: int = 4096, h: float = 1e-3, tol_primal: float = 1e-6,
+            max_iters: int = 1000, **kw) -> Problem:
+    """The batched workload: many independent uneven scenes solved in one launch."""
+    rng = np.random.default_rng(seed)
+    scenes = [batched_scene(rng, **kw) for _ in range(n_scenes)]
+    opts = Options(h=h, beta_mode="trace", warm="prev", tol_primal=tol_primal,
+                   max_iters=max_iters)
+    return Problem(scenes, opts, name=f"batched{n_scenes}")
+
+
 def problem_sizes(p: Problem) -> dict:
     """Counts of subsystems, DOF, constraints, rows and side-rows (plain bookkeeping)."""
     n_sub = sum(len(s.subs) for s in p.scenes)
@@ -400,7 +615,7 @@ def problem_sizes(p: Problem) -> dict:
             if isinstance(itf, RowsIf):
                 r, ns = itf.rows, len(itf.subs)
             else:
-                r = {BALL: 3, REVOLUTE: 5, ANGLE_PD: 1, PLANE_CONTACT: 3}[itf.kind]
+                r = {BALL: 3, REVOLUTE: 5, ANGLE_PD: 1, PLANE_CONTACT: 3}[itf.kind]  # noqa
                 ns = 1 if (itf.b is None or itf.b[0] == itf.a[0]) else 2
             rows += r
             side_rows += r * ns

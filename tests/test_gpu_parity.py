@@ -248,6 +248,80 @@ def test_large_blocks_mixed_close_to_oracle(sa, capsys):
     assert max(errs) < 1e-5
 
 
+def test_linear_blocks_with_contacts_and_a_body_fp64(sa):
+    """Spring blocks (linear kind), node contacts, node-world pins, a node-body ball joint:
+    several steps at a fixed iteration count, FP64, against the oracle."""
+    rng = np.random.default_rng(3)
+    scenes = [sg.hanging_scene(rng, n_blocks=2 + k % 2) for k in range(3)]
+    p = sg.Problem(scenes, sg.Options(h=1e-3, warm="prev", tol_primal=-1, max_iters=60))
+    orcs = [oracle.OracleScene(sc, p.options) for sc in p.scenes]
+    sim = sa.Simulation(p)
+    for _ in range(4):
+        for o in orcs:
+            o.step()
+        sim.step(1)
+        _compare(sim, orcs, p)
+        for k, o in enumerate(orcs):
+            assert rel(sim.scene_nodes(k), o.nodes_all()) < TOL
+
+
+def test_linear_blocks_converged_mixed(sa, capsys):
+    rng = np.random.default_rng(4)
+    scenes = [sg.hanging_scene(rng, n_blocks=2) for _ in range(3)]
+    p = sg.Problem(scenes, sg.Options(h=1e-3, warm="prev", tol_primal=1e-6, max_iters=3000))
+    orcs = oracle.run(p, steps=10)
+    sim = sa.Simulation(p, precision=sa.SIM_MIXED)
+    sim.step(10)
+    errs = [rel(sim.scene_nodes(k), o.nodes_all()) for k, o in enumerate(orcs)]
+    with capsys.disabled():
+        print(f"\n[mixed vs FP64 oracle, spring blocks 10 steps] node state rel err max "
+              f"{max(errs):.3e}")
+    assert max(errs) < 1e-5
+    for k in range(3):
+        r = sim.residuals(k)
+        assert r["converged"] and r["r_p"] <= 1e-6
+
+
+def _compare_states(sim, orcs, tol):
+    for k, o in enumerate(orcs):
+        if o.bodies_all().size:
+            assert rel(sim.scene_bodies(k)[:, 4:], o.bodies_all()[:, 4:]) < tol, ("bodies", k)
+        if o.nodes_all().size:
+            assert rel(sim.scene_nodes(k), o.nodes_all()) < tol, ("nodes", k)
+
+
+def test_batched_uneven_scenes_fp64_fixed_iterations(sa):
+    """Scenes of the batched workload (2-32 subsystems of 6-240 DOF: rigid chains and
+    spring blocks, tree + chord ball joints, plane contacts); scenes too large for shared
+    memory run from the global workspace.  FP64, fixed iterations, two steps."""
+    p = sg.batched(1, n_scenes=6, tol_primal=-1, max_iters=40)
+    orcs = [oracle.OracleScene(sc, p.options) for sc in p.scenes]
+    sim = sa.Simulation(p)
+    assert any(sa.sim_scene_info(sim.h, k)["global_workspace"] for k in range(6))
+    for _ in range(2):
+        for o in orcs:
+            o.step()
+        sim.step(1)
+        _compare(sim, orcs, p, what=("vhat", "lam"))
+        _compare_states(sim, orcs, TOL)
+
+
+def test_batched_uneven_scenes_mixed_converged(sa, capsys):
+    p = sg.batched(2, n_scenes=8, tol_primal=1e-6, max_iters=3000)
+    orcs = oracle.run(p, steps=3)
+    sim = sa.Simulation(p, precision=sa.SIM_MIXED)
+    sim.step(3)
+    errs = []
+    for k, o in enumerate(orcs):
+        r = sim.residuals(k)
+        assert r["converged"] and r["r_p"] <= 1e-6, (k, r)
+        errs.append(rel(sim.scene_vhat(k), o.vhat_all()))
+    with capsys.disabled():
+        print(f"\n[mixed vs FP64 oracle, batched scenes 3 steps] v-hat rel err max {max(errs):.3e}")
+    assert max(errs) < 1e-4
+    _compare_states(sim, orcs, 1e-5)
+
+
 def test_not_spd_is_reported_not_faulted(sa):
     A = -np.eye(3)
     p = sg.Problem([sg.Scene([sg.GenericSub(A, np.ones(3))], [])],
@@ -296,6 +370,29 @@ def test_state_roundtrip_through_host_buffers(sa):
     sa.sim_write_state(sim.h, buf.data_ptr())
     sim.sync()
     assert sim.scene_bodies(0)[0, 6] == ref[2] + 1.0
+
+
+def test_state_roundtrip_with_nodes_of_linear_blocks(sa):
+    """The packed state holds the bodies, then the nodes of the linear blocks."""
+    import torch
+    p = sg.batched(3, n_scenes=3)
+    sim = sa.Simulation(p)
+    sim.step(1)
+    sz = sim.sizes()
+    nb, nn = sz["bodies"], sz["nodes"]
+    assert nb > 0 and nn > 0
+    buf = torch.empty(13 * nb + 6 * nn, dtype=torch.float64).pin_memory()
+    sa.sim_read_state(sim.h, buf.data_ptr())
+    bodies = np.concatenate([sim.scene_bodies(k)[:, 4:] for k in range(3)
+                             if sim.scene_bodies(k).size]).ravel()
+    nodes = np.concatenate([sim.scene_nodes(k) for k in range(3)
+                            if sim.scene_nodes(k).size]).ravel()
+    assert np.array_equal(buf.numpy(), np.concatenate([bodies, nodes]))
+    buf[13 * nb + 4] += 0.5        # v_y of the first node
+    sa.sim_write_state(sim.h, buf.data_ptr())
+    sim.sync()
+    k0 = next(k for k in range(3) if sim.scene_nodes(k).size)
+    assert sim.scene_nodes(k0).ravel()[4] == nodes[4] + 0.5
 
 
 # ---------------------------------------------------------------------------------------
