@@ -199,17 +199,20 @@ int sim_read_state_noalloc(sim_t s, double *dst);
 int sim_sizes(sim_t s, long long out[9]);
 
 /* Where scene `scene` keeps its working set (lays the simulation out if needed):
- * out[0] 0 if every per-subsystem array (J, the factor, W, D, ...) fits in the block's
- * shared memory, 1 if they live in the simulation's global workspace (per-row arrays stay
- * in shared memory); out[1] shared-memory bytes of the scene; out[2] its subsystems;
- * out[3] bytes of the global workspace of the whole simulation. */
+ * out[0] 0 if every per-subsystem array fits in the block's shared memory; 1 if the setup
+ * arrays (J, K, the factor, W: O(n^2) per subsystem) live in the simulation's global
+ * workspace while the iteration arrays (D, c: O(m^2)) and the per-row arrays stay in shared
+ * memory; 2 if the iteration arrays are in the workspace too.  out[1] shared-memory bytes of
+ * the scene; out[2] its subsystems; out[3] bytes of the global workspace of the whole
+ * simulation. */
 int sim_scene_info(sim_t s, int scene, long long out[4]);
 
 /* Sum and maximum over scenes of the iterations of all steps since the last call, and the
  * number of scene-steps that ended without their stop rule holding; then clears them.
  * out[0] total iterations, out[1] max iterations of a scene-step, out[2] not converged,
- * out[3] scene-steps counted. */
-int sim_iteration_stats(sim_t s, long long out[4]);
+ * out[3] scene-steps counted.  per_scene (host memory, may be NULL) receives the same four
+ * counts for each scene: 4 x scenes entries, scene k at 4k (its maximum at 4k + 1). */
+int sim_iteration_stats(sim_t s, long long out[4], long long *per_scene);
 
 /* Device-side phase tracer.  Reads the counters accumulated since the last call into out
  * (if out is not NULL; zeros when tracing was off), then turns tracing on (enable != 0, the

@@ -44,8 +44,10 @@ struct SceneDesc {
     // byte offsets of the T and int regions; total bytes
     int t_base, i_base, smem_bytes;
     // per-subsystem arrays: in shared memory (sub_global = 0, offsets in the regions above)
-    // or in the global workspace at byte g_base (doubles) and g_base + g_tbase (T)
-    int sub_global;
+    // or in the global workspace at byte g_base (doubles) and g_base + g_tbase (T).  The
+    // iteration arrays D and c stay in the T region of shared memory unless hot_global, when
+    // they follow the others in the workspace.
+    int sub_global, hot_global;
     long long g_base, g_tbase;
 };
 
@@ -58,12 +60,15 @@ struct SubDesc {
     int gen_off;           // pool offset of A (n*n) then b (n) (generic); of mass (nb), f (n),
                            // X0 (n), K values (linear)
     int csr_off;           // linear: ipool offset of the K row pointers (n+1), then columns
+    int env_off;           // ipool offset of the profile of K_i: env (n), lastr (n), jlo (m), jhi (m)
+    int cst;               // 1 if K_i is the same at every step (its factor may be kept)
     int od_J, od_L, od_b;  // double region: J_ci rows (m x n), K then its factor L (n x n), b (n)
-    int od_v, od_id;       // double region: v-hat (n); 1 / L_pp (FP64 form) or rhs (mixed) (n)
+    int od_v, od_id;       // double region: v-hat (n); 1 / L_pp (FP64 factor) or rhs (mixed) (n)
     int od_t;              // double region: J v in the mixed refinement (m)
-    int ot_L, ot_W, ot_g;  // T region: L (n x n, 1/L_pp on the diagonal), W rows (m x n), g (n)
-    int ot_D, ot_c;        // T region: D (m x mpad), c (m)
+    int ot_L, ot_W;        // T region: L (n x n, 1/L_pp on the diagonal); W = L^-1 [J^T b]
+                           // (n x (m + 1), column-major: W[p (m + 1) + t], column m = g)
     int ot_s;              // T region: solve vector of the mixed recovery (n)
+    int ot_D, ot_c;        // iteration region: D (m x mpad), c (m)
     int v_off;             // global offset of v-hat
 };
 
@@ -97,7 +102,8 @@ struct StepParams {
     double *work;          // per-subsystem arrays of scenes too large for shared memory
     double *bodies;        // 17 doubles per body (state in and out)
     double *nodes;         // 6 doubles per node of linear blocks (state in and out)
-    const int *ipool;      // integer constant data (sparse K of linear blocks)
+    const int *ipool;      // integer constant data (sparse K of linear blocks, profiles)
+    int *subflag;          // per subsystem: bit 0 its kept factor is valid, bit 1 it is FP64
     double *vhat;          // per DOF
     double *lam;           // per row: lambda of the last step (warm start state)
     double *z;             // per side-row: z of the last step (warm start state)

@@ -152,6 +152,8 @@ struct View {
     T *tb;               // T region (shared memory): scene arrays
     double *sdb;         // per-subsystem double arrays: shared memory, or global for a
     T *stb;              // scene too large to hold them on chip; likewise for T
+    T *htb;              // per-subsystem iteration arrays (D, c): shared memory unless the
+                         // scene cannot hold even those
     int *row, *sub, *drow, *coff, *wbase, *mlen;   // per side-row tables
     Item *item;
     int *list;
@@ -171,6 +173,7 @@ __device__ View<T> scene_view(const StepParams &P, const SceneDesc &S, unsigned 
         V.sdb = V.db;
         V.stb = V.tb;
     }
+    V.htb = S.hot_global ? V.stb : V.tb;
     int *ib = reinterpret_cast<int *>(raw + S.i_base);
     V.row = ib;
     V.sub = ib + S.nsr;
@@ -234,26 +237,201 @@ __device__ __forceinline__ void tri_index(int t, int &r, int &s)
     s = t - r * (r + 1) / 2;
 }
 
+// Profile of a subsystem's K_i and the column spans of its J rows (built by the host from
+// the structure of A_i and J_i): env[p] first column of row p inside the envelope, lastr[k]
+// last row whose envelope reaches column k, [jlo[t], jhi[t]) the columns of J row t.
+struct SubEnv {
+    const int *env, *lastr, *jlo, *jhi;
+};
+
+__device__ __forceinline__ SubEnv sub_env(const StepParams &P, const SubDesc &u)
+{
+    SubEnv e;
+    e.env = P.ipool + u.env_off;
+    e.lastr = e.env + u.n;
+    e.jlo = e.lastr + u.n;
+    e.jhi = e.jlo + u.m;
+    return e;
+}
+
+// A constant K_i whose factor from an earlier step is still held: in the workspace (it
+// outlives the launch) or in shared memory from an earlier step of this launch.
+__device__ __forceinline__ bool factor_kept(const StepParams &P, const SceneDesc &S,
+                                            const SubDesc &u, int gsub, int step)
+{
+    return u.cst && (step > 0 || S.sub_global) && (P.subflag[gsub] & 1);
+}
+
+// K += beta J^T J on the lower triangle (row-major n x n), one J row at a time over the
+// row's column span (rows share entries, so they are added in turn)
+template <typename F>
+__device__ void add_jtj(F *K, int n, const double *J, int m, const SubEnv &e, F beta)
+{
+    const int lane = threadIdx.x & 31;
+    for (int t = 0; t < m; ++t) {
+        const int lo = e.jlo[t], w = e.jhi[t] - lo;
+        const double *Jr = J + (size_t)t * n + lo;
+        for (int k = lane; k < w * (w + 1) / 2; k += 32) {
+            int a, b;
+            tri_index(k, a, b);
+            K[(lo + a) * n + lo + b] += beta * (F)Jr[a] * (F)Jr[b];
+        }
+        __syncwarp();
+    }
+}
+
+// Right-looking Cholesky inside the envelope, in place on the lower triangle of K (one
+// warp).  Column k below the diagonal is scaled, then the rows it reaches are updated a row
+// at a time, lanes across the columns (coalesced).  INV_DIAG: the diagonal ends as 1/L_kk
+// (the T factor); otherwise as L_kk with 1/L_kk in idg.  False on a non-positive pivot.
+template <typename F, bool INV_DIAG>
+__device__ bool env_cholesky(F *K, int n, const SubEnv &e, double *idg)
+{
+    const int lane = threadIdx.x & 31;
+    for (int k = 0; k < n; ++k) {
+        const F d = K[k * n + k];
+        if (!(d > (F)0) || !isfinite(d)) return false;
+        const F ilkk = rsq(d);
+        const int R = e.lastr[k];
+        __syncwarp();
+        for (int q = k + 1 + lane; q <= R; q += 32) K[q * n + k] *= ilkk;
+        if (lane == 0) {
+            if (INV_DIAG) {
+                K[k * n + k] = ilkk;
+            } else {
+                K[k * n + k] = d * ilkk;
+                idg[k] = (double)ilkk;
+            }
+        }
+        __syncwarp();
+        for (int c0 = k + 1; c0 <= R; c0 += 32) {
+            const int q = c0 + lane;
+            const F lq = q <= R ? K[q * n + k] : (F)0;
+            F *Kq = K + q;
+#pragma unroll 4
+            for (int r = c0; r <= R; ++r) {
+                const F lrk = (r - c0 < 32) ? __shfl_sync(0xffffffffu, lq, r - c0) : K[r * n + k];
+                if (q <= r) Kq[r * n] -= lrk * lq;
+            }
+        }
+        __syncwarp();
+    }
+    return true;
+}
+
+// X <- L^-1 X for the nrhs columns of X (column t at X[p ldx + t]), a lane per column, each
+// row inside the envelope; the diagonal of LT holds 1/L_pp
+template <typename F>
+__device__ void env_forward_cols(const F *LT, F *X, int n, int ldx, int nrhs, const int *env)
+{
+    const int lane = threadIdx.x & 31;
+    for (int t0 = 0; t0 < nrhs; t0 += 32) {
+        const int t = t0 + lane;
+        const bool act = t < nrhs;
+        F *x = X + (act ? t : nrhs - 1);
+        for (int p = 0; p < n; ++p) {
+            const F *Lp = LT + (size_t)p * n;
+            F s0 = x[p * ldx], s1 = (F)0, s2 = (F)0, s3 = (F)0;
+            int q = env[p];
+            for (; q + 3 < p; q += 4) {
+                s0 -= Lp[q] * x[q * ldx];
+                s1 -= Lp[q + 1] * x[(q + 1) * ldx];
+                s2 -= Lp[q + 2] * x[(q + 2) * ldx];
+                s3 -= Lp[q + 3] * x[(q + 3) * ldx];
+            }
+            for (; q < p; ++q) s0 -= Lp[q] * x[q * ldx];
+            if (act) x[p * ldx] = ((s0 + s1) + (s2 + s3)) * Lp[p];
+        }
+    }
+}
+
+// y <- L^-1 y for one vector (stride ldy), column by column: lanes update the rows below p
+template <typename F>
+__device__ void env_forward_vec(const F *LT, F *y, int n, int ldy, const int *lastr)
+{
+    const int lane = threadIdx.x & 31;
+    for (int p = 0; p < n; ++p) {
+        const F yp = y[p * ldy] * LT[p * n + p];
+        __syncwarp();
+        if (lane == 0) y[p * ldy] = yp;
+        for (int q = p + 1 + lane; q <= lastr[p]; q += 32) y[q * ldy] -= LT[q * n + p] * yp;
+        __syncwarp();
+    }
+}
+
+// D = W^T W over the m columns of W (rows padded with zeros to mp); W column t is zero above
+// row jlo[t]
+template <typename F>
+__device__ void form_D(const F *W, int n, int m, int mp, int ldw, const int *jlo, F *D)
+{
+    const int lane = threadIdx.x & 31;
+    for (int k = lane; k < m * (m + 1) / 2; k += 32) {
+        int r, s;
+        tri_index(k, r, s);
+        int p = max(jlo[r], jlo[s]);
+        F a0 = (F)0, a1 = (F)0;
+        for (; p + 1 < n; p += 2) {
+            a0 += W[p * ldw + r] * W[p * ldw + s];
+            a1 += W[(p + 1) * ldw + r] * W[(p + 1) * ldw + s];
+        }
+        if (p < n) a0 += W[p * ldw + r] * W[p * ldw + s];
+        D[r * mp + s] = a0 + a1;
+        D[s * mp + r] = a0 + a1;
+    }
+    if (mp > m) {
+        for (int t = lane; t < m * (mp - m); t += 32) {
+            const int r = t / (mp - m);
+            D[r * mp + m + (t - r * (mp - m))] = (F)0;
+        }
+    }
+}
+
+// c = W^T g, g = column m of W
+template <typename F>
+__device__ void form_c(const F *W, int n, int m, int ldw, const int *jlo, F *cc)
+{
+    const int lane = threadIdx.x & 31;
+    for (int r = lane; r < m; r += 32) {
+        F a0 = (F)0, a1 = (F)0;
+        int p = jlo[r];
+        for (; p + 1 < n; p += 2) {
+            a0 += W[p * ldw + r] * W[p * ldw + m];
+            a1 += W[(p + 1) * ldw + r] * W[(p + 1) * ldw + m];
+        }
+        if (p < n) a0 += W[p * ldw + r] * W[p * ldw + m];
+        cc[r] = a0 + a1;
+    }
+}
+
 // assemble .. factor .. map, and the per-step constants of the z-step
 template <typename T>
 __device__ void scene_setup(const StepParams &P, const SceneDesc &S, const View<T> &V,
-                            int *s_status, PhaseClock &pc)
+                            int *s_status, PhaseClock &pc, int step)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr bool MIXED = sizeof(T) == 4;
     double *db = V.db, *sdb = V.sdb;
-    T *tb = V.tb, *stb = V.stb;
+    T *tb = V.tb, *stb = V.stb, *htb = V.htb;
     for (int i = warp; i < S.nsub; i += SUBADMM_WARPS) {
         const SubDesc &u = P.subs[S.sub0 + i];
+        const SubEnv e = sub_env(P, u);
+        const bool keep = factor_kept(P, S, u, S.sub0 + i, step);
         double *J = sdb + u.od_J, *K = sdb + u.od_L;
-        if (u.kind == KIND_RIGID) {
-            for (int q = lane; q < u.m * u.n; q += 32) J[q] = 0.0;
-            for (int q = lane; q < u.n * u.n; q += 32) K[q] = 0.0;
-        } else if (u.kind == KIND_LINEAR) {
-            // A = (2/h) M + (h/2) K_el (K_el sparse, scattered into the dense block);
+        for (int q = lane; q < u.m * u.n; q += 32) J[q] = 0.0;
+        if (u.kind == KIND_GENERIC) {
+            const double *A = P.pool + u.gen_off;
+            for (int q = lane; q < u.n * u.n; q += 32) K[q] = A[q];
+            for (int q = lane; q < u.n; q += 32) sdb[u.od_b + q] = A[u.n * u.n + q];
+            continue;
+        }
+        if (!keep) {
+            // the band [env[p], lastr[p]] of every row holds A (both triangles)
+            for (int p = 0; p < u.n; ++p)
+                for (int q = e.env[p] + lane; q <= e.lastr[p]; q += 32) K[p * u.n + q] = 0.0;
+        }
+        if (u.kind == KIND_LINEAR) {
+            // A = (2/h) M + (h/2) K_el (K_el sparse, scattered into the band);
             // b from the node state (Eq. ddyn, elastic force at the midpoint)
-            for (int q = lane; q < u.m * u.n; q += 32) J[q] = 0.0;
-            for (int q = lane; q < u.n * u.n; q += 32) K[q] = 0.0;
             __syncwarp();
             const double *mass = P.pool + u.gen_off;
             const double *f = mass + u.nb, *X0 = f + u.n, *Kval = X0 + u.n;
@@ -261,14 +439,12 @@ __device__ void scene_setup(const StepParams &P, const SceneDesc &S, const View<
             const double gv[3] = {P.g0, P.g1, P.g2};
             const double *nodes = P.nodes + (size_t)u.body0 * SUBADMM_NODE;
             for (int p = lane; p < u.n; p += 32) {
-                for (int q = rowp[p]; q < rowp[p + 1]; ++q) K[p * u.n + col[q]] = 0.5 * P.h * Kval[q];
-                K[p * u.n + p] += (2.0 / P.h) * mass[p / 3];
+                if (!keep) {
+                    for (int q = rowp[p]; q < rowp[p + 1]; ++q) K[p * u.n + col[q]] = 0.5 * P.h * Kval[q];
+                    K[p * u.n + p] += (2.0 / P.h) * mass[p / 3];
+                }
                 sdb[u.od_b + p] = linear_b(p, mass, f, X0, Kval, rowp, col, nodes, P.h, gv);
             }
-        } else {
-            const double *A = P.pool + u.gen_off;
-            for (int q = lane; q < u.n * u.n; q += 32) K[q] = A[q];
-            for (int q = lane; q < u.n; q += 32) sdb[u.od_b + q] = A[u.n * u.n + q];
         }
     }
     __syncthreads();
@@ -333,88 +509,64 @@ __device__ void scene_setup(const StepParams &P, const SceneDesc &S, const View<
     __syncthreads();
     pc.mark(PHASE_ASSEMBLE);
     // per subsystem (one warp each): beta, K = A + beta J^T J and its Cholesky factor, then
-    // the map.  FP64 form: K and L in FP64, rounded into the T copy.  Mixed form: K and L in
-    // FP32 (the FP64 A, b and J stay for the FP64 recovery and refinement of v-hat).
+    // the map W = L^-1 [J^T b], D = W^T W, c.  The FP64 form and the stiff blocks of the mixed
+    // form factorise K in FP64 (rounded into the T copy); the other mixed blocks factorise in
+    // FP32, keeping the FP64 A, b and J for the recovery and refinement of v-hat.
     for (int i = warp; i < S.nsub; i += SUBADMM_WARPS) {
         const SubDesc &u = P.subs[S.sub0 + i];
-        const int n = u.n, m = u.m, mp = u.mpad;
+        const int gsub = S.sub0 + i;
+        const int n = u.n, m = u.m, mp = u.mpad, ldw = m + 1;
+        const SubEnv e = sub_env(P, u);
         double *J = sdb + u.od_J, *K = sdb + u.od_L, *b = sdb + u.od_b, *idg = sdb + u.od_id;
-        T *LT = stb + u.ot_L, *W = stb + u.ot_W, *g = stb + u.ot_g, *D = stb + u.ot_D, *cc = stb + u.ot_c;
-        bool ok = true;
+        T *LT = stb + u.ot_L, *W = stb + u.ot_W, *D = htb + u.ot_D, *cc = htb + u.ot_c;
+        if (factor_kept(P, S, u, gsub, step)) {
+            // constant K_i: only g = L^-1 b and c change (and D when the launch lost it)
+            if (step == 0 && lane == 0) {
+                db[S.od_beta + i] = P.beta[gsub];
+                db[S.od_flag + i] = (P.subflag[gsub] & 2) ? 1.0 : 0.0;
+            }
+            for (int p = lane; p < n; p += 32) W[p * ldw + m] = (T)b[p];
+            __syncwarp();
+            env_forward_vec<T>(LT, W + m, n, ldw, e.lastr);
+            if (step == 0 && !S.hot_global) form_D<T>(W, n, m, mp, ldw, e.jlo, D);
+            form_c<T>(W, n, m, ldw, e.jlo, cc);
+            __syncwarp();
+            continue;
+        }
+        // beta_i = Tr(A_i) / Tr(J_ci^T J_ci)  (Sec. III-D)
+        double beta;
         if (!MIXED) {
-            // beta_i = Tr(A_i) / Tr(J_ci^T J_ci)  (Sec. III-D)
             double trA = 0.0, trJ = 0.0;
             for (int q = lane; q < n; q += 32) trA += K[q * n + q];
             for (int q = lane; q < m * n; q += 32) trJ += J[q] * J[q];
             trA = warp_sum(trA);
             trJ = warp_sum(trJ);
-            const double beta = P.beta_fixed ? P.rho : (trJ > 0.0 ? trA / trJ : 1.0);
-            if (lane == 0) {
-                db[S.od_beta + i] = beta;
-                P.beta[S.sub0 + i] = beta;
-            }
-            // K_i = A_i + beta_i J_ci^T J_ci (lower triangle)
-            for (int t = lane; t < n * (n + 1) / 2; t += 32) {
-                int p, q;
-                tri_index(t, p, q);
-                double acc = 0.0;
-                for (int r = 0; r < m; ++r) acc += J[r * n + p] * J[r * n + q];
-                K[p * n + q] += beta * acc;
-            }
-            __syncwarp();
-            // right-looking Cholesky in FP64, in place (lower triangle); 1/L_kk kept in idg
-            for (int k = 0; k < n; ++k) {
-                const double d = K[k * n + k];
-                if (!(d > 0.0) || !isfinite(d)) { ok = false; break; }
-                const double ilkk = rsqrt(d);
-                __syncwarp();
-                for (int r = k + lane; r < n; r += 32) K[r * n + k] = (r == k) ? d * ilkk : K[r * n + k] * ilkk;
-                if (lane == 0) idg[k] = ilkk;
-                __syncwarp();
-                for (int r = k + 1 + lane; r < n; r += 32) {
-                    const double lrk = K[r * n + k];
-                    for (int q = k + 1; q <= r; ++q) K[r * n + q] -= lrk * K[q * n + k];
-                }
-                __syncwarp();
-            }
-            if (!ok) {
-                if (lane == 0) *s_status = ST_NOTSPD;
-                continue;
-            }
-            // the map in T: LT = L (with 1/L_pp on its diagonal), W rows = J rows, g = b
-            for (int q = lane; q < n * n; q += 32) {
-                const int p = q / n, r = q - p * n;
-                LT[q] = (r == p) ? (T)idg[p] : (T)K[q];
-            }
-            for (int q = lane; q < m * n; q += 32) W[q] = (T)J[q];
-            for (int q = lane; q < n; q += 32) g[q] = (T)b[q];
-            __syncwarp();
+            beta = P.beta_fixed ? P.rho : (trJ > 0.0 ? trA / trJ : 1.0);
         } else {
-            // rounded copies: W rows = J rows, LT = A (lower triangle), g = b
-            for (int q = lane; q < m * n; q += 32) W[q] = (T)J[q];
-            for (int q = lane; q < n * n; q += 32) LT[q] = (T)K[q];
-            for (int q = lane; q < n; q += 32) g[q] = (T)b[q];
-            __syncwarp();
             T trA = (T)0, trJ = (T)0;
-            for (int q = lane; q < n; q += 32) trA += LT[q * n + q];
-            for (int q = lane; q < m * n; q += 32) trJ += W[q] * W[q];
+            for (int q = lane; q < n; q += 32) trA += (T)K[q * n + q];
+            for (int q = lane; q < m * n; q += 32) { const T jq = (T)J[q]; trJ += jq * jq; }
 #pragma unroll
             for (int o = 16; o; o >>= 1) {
                 trA += __shfl_xor_sync(0xffffffffu, trA, o);
                 trJ += __shfl_xor_sync(0xffffffffu, trJ, o);
             }
-            const T beta = P.beta_fixed ? (T)P.rho : (trJ > (T)0 ? trA / trJ : (T)1);
-            if (lane == 0) {
-                db[S.od_beta + i] = (double)beta;
-                P.beta[S.sub0 + i] = (double)beta;
-            }
+            beta = (double)(P.beta_fixed ? (T)P.rho : (trJ > (T)0 ? trA / trJ : (T)1));
+        }
+        if (lane == 0) {
+            db[S.od_beta + i] = beta;
+            P.beta[gsub] = beta;
+        }
+        bool stiff = true;
+        if (MIXED) {
             // stiffness test: the spread of K's diagonal bounds its condition number from
             // below; a stiff or high-mass-ratio block (spread > 1e3) is factorised in FP64
+            const T bt = (T)beta;
             T dmax = (T)0, dmin = (T)3.0e38;
             for (int p = lane; p < n; p += 32) {
                 T cs = (T)0;
-                for (int r = 0; r < m; ++r) cs += W[r * n + p] * W[r * n + p];
-                const T dk = LT[p * n + p] + beta * cs;
+                for (int r = 0; r < m; ++r) { const T jr = (T)J[r * n + p]; cs += jr * jr; }
+                const T dk = (T)K[p * n + p] + bt * cs;
                 dmax = dk > dmax ? dk : dmax;
                 dmin = dk < dmin ? dk : dmin;
             }
@@ -425,101 +577,41 @@ __device__ void scene_setup(const StepParams &P, const SceneDesc &S, const View<
                 dmax = a > dmax ? a : dmax;
                 dmin = c < dmin ? c : dmin;
             }
-            const bool stiff = !(dmin > (T)0) || dmax > (T)1.0e3 * dmin;
+            stiff = !(dmin > (T)0) || dmax > (T)1.0e3 * dmin;
             if (lane == 0) db[S.od_flag + i] = stiff ? 1.0 : 0.0;
-            if (stiff) {
-                const double b64 = (double)beta;
-                for (int t = lane; t < n * (n + 1) / 2; t += 32) {
-                    int p, q;
-                    tri_index(t, p, q);
-                    double acc = 0.0;
-                    for (int r = 0; r < m; ++r) acc += J[r * n + p] * J[r * n + q];
-                    K[p * n + q] += b64 * acc;
-                }
-                __syncwarp();
-                for (int k = 0; k < n; ++k) {
-                    const double d = K[k * n + k];
-                    if (!(d > 0.0) || !isfinite(d)) { ok = false; break; }
-                    const double ilkk = rsqrt(d);
-                    __syncwarp();
-                    for (int r = k + lane; r < n; r += 32) K[r * n + k] = (r == k) ? d * ilkk : K[r * n + k] * ilkk;
-                    if (lane == 0) idg[k] = ilkk;
-                    __syncwarp();
-                    for (int r = k + 1 + lane; r < n; r += 32) {
-                        const double lrk = K[r * n + k];
-                        for (int q = k + 1; q <= r; ++q) K[r * n + q] -= lrk * K[q * n + k];
-                    }
-                    __syncwarp();
-                }
-                if (!ok) {
-                    if (lane == 0) *s_status = ST_NOTSPD;
-                    continue;
-                }
-                for (int q = lane; q < n * n; q += 32) {
-                    const int p = q / n, r = q - p * n;
-                    LT[q] = (r == p) ? (T)idg[p] : (T)K[q];
-                }
-                __syncwarp();
-            } else {
-                for (int t = lane; t < n * (n + 1) / 2; t += 32) {
-                    int p, q;
-                    tri_index(t, p, q);
-                    T acc = (T)0;
-                    for (int r = 0; r < m; ++r) acc += W[r * n + p] * W[r * n + q];
-                    LT[p * n + q] += beta * acc;
-                }
-                __syncwarp();
-                // right-looking Cholesky in FP32, in place; the diagonal ends as 1/L_pp
-                for (int k = 0; k < n; ++k) {
-                    const T d = LT[k * n + k];
-                    if (!(d > (T)0) || !isfinite(d)) { ok = false; break; }
-                    const T ilkk = rsq(d);
-                    __syncwarp();
-                    for (int r = k + 1 + lane; r < n; r += 32) LT[r * n + k] *= ilkk;
-                    __syncwarp();
-                    if (lane == 0) LT[k * n + k] = ilkk;
-                    for (int r = k + 1 + lane; r < n; r += 32) {
-                        const T lrk = LT[r * n + k];
-                        for (int q = k + 1; q <= r; ++q) LT[r * n + q] -= lrk * LT[q * n + k];
-                    }
-                    __syncwarp();
-                }
-                if (!ok) {
-                    if (lane == 0) *s_status = ST_NOTSPD;
-                    continue;
-                }
-            }
         }
-        // W rows <- L^-1 J rows, g <- L^-1 b (forward substitution, lane per right-hand side)
-        for (int t = lane; t <= m; t += 32) {
-            T *x = (t < m) ? W + t * n : g;
-            for (int p = 0; p < n; ++p) {
-                T s = x[p];
-                for (int q = 0; q < p; ++q) s -= LT[p * n + q] * x[q];
-                x[p] = s * LT[p * n + p];
+        bool ok;
+        if (stiff) {
+            add_jtj<double>(K, n, J, m, e, beta);
+            ok = env_cholesky<double, false>(K, n, e, idg);
+            if (ok) {
+                for (int p = 0; p < n; ++p)
+                    for (int q = e.env[p] + lane; q <= p; q += 32)
+                        LT[p * n + q] = (q == p) ? (T)idg[p] : (T)K[p * n + q];
             }
+        } else {
+            for (int p = 0; p < n; ++p)
+                for (int q = e.env[p] + lane; q <= p; q += 32) LT[p * n + q] = (T)K[p * n + q];
+            __syncwarp();
+            add_jtj<T>(LT, n, J, m, e, (T)beta);
+            ok = env_cholesky<T, true>(LT, n, e, nullptr);
+        }
+        if (u.cst && lane == 0) P.subflag[gsub] = ok ? (1 | (stiff ? 2 : 0)) : 0;
+        if (!ok) {
+            if (lane == 0) *s_status = ST_NOTSPD;
+            continue;
+        }
+        // W = [J^T b] in T (column-major), then W <- L^-1 W; D = W^T W, c = W^T g
+        for (int q = lane; q < n * ldw; q += 32) {
+            const int p = q / ldw, t = q - p * ldw;
+            W[q] = t < m ? (T)J[t * n + p] : (T)b[p];
         }
         __syncwarp();
-        // D = W^T W (symmetric, rows padded with zeros to mpad), c = W^T g
-        for (int t = lane; t < m * (m + 1) / 2; t += 32) {
-            int r, s;
-            tri_index(t, r, s);
-            T acc = (T)0;
-            for (int p = 0; p < n; ++p) acc += W[r * n + p] * W[s * n + p];
-            D[r * mp + s] = acc;
-            D[s * mp + r] = acc;
-        }
-        if (mp > m) {
-            for (int t = lane; t < m * (mp - m); t += 32) {
-                const int r = t / (mp - m);
-                D[r * mp + m + (t - r * (mp - m))] = (T)0;
-            }
-        }
-        for (int r = lane; r < m; r += 32) {
-            T acc = (T)0;
-            for (int p = 0; p < n; ++p) acc += W[r * n + p] * g[p];
-            cc[r] = acc;
-        }
+        env_forward_cols<T>(LT, W, n, ldw, m + 1, e.env);
+        __syncwarp();
+        form_D<T>(W, n, m, mp, ldw, e.jlo, D);
+        form_c<T>(W, n, m, ldw, e.jlo, cc);
+        __syncwarp();
     }
     __syncthreads();
     pc.mark(PHASE_FACTOR);
@@ -552,23 +644,24 @@ __device__ void scene_setup(const StepParams &P, const SceneDesc &S, const View<
     __syncthreads();
 }
 
-// Triangular solves with the T factor (1/L_pp on its diagonal), in place on s (warp).
+// Triangular solves with the T factor (1/L_pp on its diagonal), in place on s (warp),
+// inside the envelope.
 template <typename T>
-__device__ __forceinline__ void warp_chol_solve(const T *LT, T *s, int n)
+__device__ __forceinline__ void warp_chol_solve(const T *LT, T *s, int n, const SubEnv &e)
 {
     const int lane = threadIdx.x & 31;
     for (int p = 0; p < n; ++p) {              // L y = s (column-oriented)
         const T yp = s[p] * LT[p * n + p];
         __syncwarp();
         if (lane == 0) s[p] = yp;
-        for (int q = p + 1 + lane; q < n; q += 32) s[q] -= LT[q * n + p] * yp;
+        for (int q = p + 1 + lane; q <= e.lastr[p]; q += 32) s[q] -= LT[q * n + p] * yp;
         __syncwarp();
     }
     for (int p = n - 1; p >= 0; --p) {         // L^T v = y
         const T vp = s[p] * LT[p * n + p];
         __syncwarp();
         if (lane == 0) s[p] = vp;
-        for (int q = lane; q < p; q += 32) s[q] -= LT[p * n + q] * vp;
+        for (int q = e.env[p] + lane; q < p; q += 32) s[q] -= LT[p * n + q] * vp;
         __syncwarp();
     }
 }
@@ -586,6 +679,7 @@ __device__ void recover_v(const StepParams &P, const SceneDesc &S, const View<T>
     for (int i = warp; i < S.nsub; i += SUBADMM_WARPS) {
         const SubDesc &u = P.subs[S.sub0 + i];
         const int n = u.n, m = u.m;
+        const SubEnv e = sub_env(P, u);
         // od_L holds the FP64 factor L (FP64 form) or A itself (mixed form)
         const double *J = V.sdb + u.od_J, *Lf = V.sdb + u.od_L, *b = V.sdb + u.od_b;
         double *idg = V.sdb + u.od_id;
@@ -602,14 +696,14 @@ __device__ void recover_v(const StepParams &P, const SceneDesc &S, const View<T>
                 const double yp = v[p] * idg[p];
                 __syncwarp();
                 if (lane == 0) v[p] = yp;
-                for (int q = p + 1 + lane; q < n; q += 32) v[q] -= Lf[q * n + p] * yp;
+                for (int q = p + 1 + lane; q <= e.lastr[p]; q += 32) v[q] -= Lf[q * n + p] * yp;
                 __syncwarp();
             }
             for (int p = n - 1; p >= 0; --p) {     // L^T v = y
                 const double vp = v[p] * idg[p];
                 __syncwarp();
                 if (lane == 0) v[p] = vp;
-                for (int q = lane; q < p; q += 32) v[q] -= Lf[p * n + q] * vp;
+                for (int q = e.env[p] + lane; q < p; q += 32) v[q] -= Lf[p * n + q] * vp;
                 __syncwarp();
             }
             continue;
@@ -626,25 +720,26 @@ __device__ void recover_v(const StepParams &P, const SceneDesc &S, const View<T>
             s[p] = (T)acc;
         }
         __syncwarp();
-        warp_chol_solve<T>(LT, s, n);
+        warp_chol_solve<T>(LT, s, n, e);
         for (int p = lane; p < n; p += 32) v[p] = (double)s[p];
         __syncwarp();
-        // one refinement step: r = rhs - A v - beta J^T (J v); v += K^-1 r
+        // one refinement step: r = rhs - A v - beta J^T (J v); v += K^-1 r.  Row p of A lies
+        // inside the band [env[p], lastr[p]]
         for (int r = lane; r < m; r += 32) {
             double acc = 0.0;
-            for (int p = 0; p < n; ++p) acc += J[r * n + p] * v[p];
+            for (int p = e.jlo[r]; p < e.jhi[r]; ++p) acc += J[r * n + p] * v[p];
             t[r] = acc;
         }
         __syncwarp();
         for (int p = lane; p < n; p += 32) {
             double acc = rhs[p];
-            for (int q = 0; q < n; ++q) acc -= Lf[p * n + q] * v[q];     // A v
+            for (int q = e.env[p]; q <= e.lastr[p]; ++q) acc -= Lf[p * n + q] * v[q];     // A v
             double jt = 0.0;
             for (int r = 0; r < m; ++r) jt += J[r * n + p] * t[r];
             s[p] = (T)(acc - beta * jt);
         }
         __syncwarp();
-        warp_chol_solve<T>(LT, s, n);
+        warp_chol_solve<T>(LT, s, n, e);
         for (int p = lane; p < n; p += 32) v[p] += (double)s[p];
         __syncwarp();
     }
@@ -682,7 +777,7 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, CACHED ? 1 : 2) step_kernel(S
             if (tid == 0) s_status = ST_OK;
             __syncthreads();
             PhaseClock pc(P.phase ? P.phase + 8 * sc : nullptr);
-            scene_setup<T>(P, S, V, &s_status, pc);
+            scene_setup<T>(P, S, V, &s_status, pc, step);
             const int status0 = s_status;
             if (status0 != ST_OK) {
                 // K_i not SPD: report, leave the state untouched (the step is undefined)
@@ -735,11 +830,11 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, CACHED ? 1 : 2) step_kernel(S
                     xwbo = V.wbase[xt];
                     xnv = (V.mlen[xt] + VN - 1) / VN;
                     xrow = V.row[xt];
-                    xc = V.stb[V.coff[xt]];
+                    xc = V.htb[V.coff[xt]];
                     xbt = BT[xt];
                     yreg = Y[xt];
                     yprev = yreg;
-                    const VT *Dr = reinterpret_cast<const VT *>(V.stb + xdro);
+                    const VT *Dr = reinterpret_cast<const VT *>(V.htb + xdro);
 #pragma unroll
                     for (int q = 0; q < MAXC; ++q)
                         if (xgl + q * SPLIT < xnv) dreg[q] = Dr[xgl + q * SPLIT];
@@ -821,7 +916,7 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, CACHED ? 1 : 2) step_kernel(S
                             const int m = t < S.nsr ? V.mlen[t] : 0;
                             T acc = (T)0;
                             if (m > 0) {
-                                const VT *Dr = reinterpret_cast<const VT *>(V.stb + V.drow[t]);
+                                const VT *Dr = reinterpret_cast<const VT *>(V.htb + V.drow[t]);
                                 const VT *wb = reinterpret_cast<const VT *>(w + V.wbase[t]);
                                 const int nv = (m + VN - 1) / VN;
                                 for (int c = xgl; c < nv; c += SPLIT) acc = vdot(Dr[c], wb[c], acc);
@@ -829,7 +924,7 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, CACHED ? 1 : 2) step_kernel(S
 #pragma unroll
                             for (int o = SPLIT / 2; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
                             if (m > 0 && xgl == 0) {
-                                acc += V.stb[V.coff[t]];
+                                acc += V.htb[V.coff[t]];
                                 const T ynew = BT[t] * acc - LAM[V.row[t]];
                                 if (P.stop_theta) {
                                     const T d = ynew - Y[t];
@@ -1020,17 +1115,18 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, CACHED ? 1 : 2) step_kernel(S
                         const int lr = t - u.sr0, n = u.n;
                         const double *Jr = V.sdb + u.od_J + lr * n;
                         const double *v = V.sdb + u.od_v;
+                        const int *jl = P.ipool + u.env_off + 2 * n;
                         double x = 0.0;
-                        for (int p = 0; p < n; ++p) x += Jr[p] * v[p];
+                        for (int p = jl[lr]; p < jl[u.m + lr]; ++p) x += Jr[p] * v[p];
                         part = nanmax(part, fabs(x - (double)Z[t]));
-                        V.stb[V.coff[t]] += (T)(x - (double)X[t]);
+                        V.htb[V.coff[t]] += (T)(x - (double)X[t]);
                     }
                     double d0 = 0.0, d2 = 0.0;
                     block_reduce3(red, d0, part, d2);
                     if (part > P.tol && l + 1 < P.max_iters) {
                         tolc *= 0.5;
                         tolb = tol_bits(T(0), tolc);
-                        if (CACHED && xv) xc = V.stb[V.coff[xt]];
+                        if (CACHED && xv) xc = V.htb[V.coff[xt]];
                         conv = 0;
                         ++l;
                         continue;

@@ -73,6 +73,7 @@ struct sim_s {
     double *d_work = nullptr;      // per-subsystem arrays of scenes too large for shared memory
     double *d_nodes = nullptr;     // node states of linear blocks
     int *d_ipool = nullptr;        // integer constant data
+    int *d_subflag = nullptr;      // per subsystem: kept-factor flags
     long long nnodes = 0;
     long long work_bytes = 0;
     size_t pool_size = 0;
@@ -163,8 +164,8 @@ void free_device(sim_t s)
     s->d_phase = nullptr;
     cudaFree(s->d_work);
     s->d_work = nullptr;
-    cudaFree(s->d_nodes); cudaFree(s->d_ipool);
-    s->d_nodes = nullptr; s->d_ipool = nullptr;
+    cudaFree(s->d_nodes); cudaFree(s->d_ipool); cudaFree(s->d_subflag);
+    s->d_nodes = nullptr; s->d_ipool = nullptr; s->d_subflag = nullptr;
     s->d_scenes = nullptr; s->d_subs = nullptr; s->d_cons = nullptr; s->d_pool = nullptr;
     s->d_bodies = nullptr; s->d_vhat = nullptr; s->d_lam = nullptr; s->d_z = nullptr;
     s->d_beta = nullptr; s->d_res = nullptr; s->d_stats = nullptr; s->d_stage = nullptr;
@@ -327,6 +328,73 @@ int finalize(sim_t s)
                 c.side_b = (h.sb == h.sa) ? 0 : 1;
             }
         }
+        // profile of every K_i = A_i + beta_i J_i^T J_i: env[p] = first column of row p inside
+        // the envelope, lastr[k] = last row whose envelope reaches column k; and the column
+        // span [jlo, jhi) of every J row (empty rows: jlo = jhi = n).  Cholesky fill stays
+        // inside the envelope, so the factorisation and the solves skip everything outside.
+        for (int i = 0; i < S.nsub; ++i) {
+            SubDesc &u = s->sdesc[S.sub0 + i];
+            const HostSub &hs = s->subs[sub_order[S.sub0 + i]];
+            const int n = u.n, m = u.m;
+            std::vector<int> env(n), lastr(n), jlo(m, n), jhi(m, n);
+            for (int p = 0; p < n; ++p) env[p] = u.kind == KIND_GENERIC ? 0 : p;
+            if (u.kind == KIND_LINEAR) {
+                const int *rowp = hs.csr.data(), *col = rowp + n + 1;
+                for (int p = 0; p < n; ++p)
+                    for (int q = rowp[p]; q < rowp[p + 1]; ++q) {
+                        const int hi = std::max(p, col[q]), lo = std::min(p, col[q]);
+                        env[hi] = std::min(env[hi], lo);
+                    }
+            }
+            // A of a linear block is constant, and every row on it is a constant selector or
+            // an explicit row, so its K_i (and factor) is the same at every step
+            u.cst = u.kind == KIND_LINEAR ? 1 : 0;
+            auto span = [&](int lr, int a, int b) {
+                if (b <= a) return;
+                if (jlo[lr] == n) { jlo[lr] = a; jhi[lr] = b; }
+                else { jlo[lr] = std::min(jlo[lr], a); jhi[lr] = std::max(jhi[lr], b); }
+            };
+            for (int j = 0; j < S.ncon; ++j) {
+                const HostCon &h = s->cons[con_order[S.con0 + j]];
+                const ConDesc &c = s->cdesc[S.con0 + j];
+                if (h.src <= SRC_CONTACT) {
+                    size_t off = 3 + (size_t)c.rows;
+                    for (int q = 0; q < c.ns; ++q) {
+                        const int nq = s->sdesc[S.sub0 + c.sub[q]].n;
+                        if (c.sub[q] == i) {
+                            for (int r = 0; r < c.rows; ++r) {
+                                int a = n, b = 0;
+                                for (int p = 0; p < n; ++p)
+                                    if (h.data[off + (size_t)r * n + p] != 0.0) { a = std::min(a, p); b = p + 1; }
+                                span(c.sr[q] + r - u.sr0, a, b);
+                            }
+                        }
+                        off += (size_t)c.rows * nq;
+                    }
+                    continue;
+                }
+                const int wa = c.node_a ? 3 : 6, wb = c.node_b ? 3 : 6;
+                for (int r = 0; r < c.rows; ++r) {
+                    if (c.sub[0] == i) span(c.sr[0] + r - u.sr0, wa * c.ba, wa * c.ba + wa);
+                    if (c.side_b >= 0 && c.sub[c.side_b] == i)
+                        span(c.sr[c.side_b] + r - u.sr0, wb * c.bb, wb * c.bb + wb);
+                }
+            }
+            for (int t = 0; t < m; ++t)
+                for (int p = jlo[t]; p < jhi[t]; ++p) env[p] = std::min(env[p], jlo[t]);
+            // make the envelope monotone (suffix minimum), so that every row a column reaches,
+            // (k, lastr[k]], holds its column-k entry inside its own band (assembled and
+            // zeroed there; entries outside any band are never read)
+            for (int p = n - 2; p >= 0; --p) env[p] = std::min(env[p], env[p + 1]);
+            for (int k = 0; k < n; ++k) lastr[k] = k;
+            for (int r = 0; r < n; ++r)
+                for (int k = env[r]; k < r; ++k) lastr[k] = std::max(lastr[k], r);
+            u.env_off = (int)ipool.size();
+            ipool.insert(ipool.end(), env.begin(), env.end());
+            ipool.insert(ipool.end(), lastr.begin(), lastr.end());
+            ipool.insert(ipool.end(), jlo.begin(), jlo.end());
+            ipool.insert(ipool.end(), jhi.begin(), jhi.end());
+        }
         // z-step items: one per row of an equality / hard / soft constraint, one per contact;
         // ordered by type so that neighbouring threads run the same projection
         S.item_g0 = (int)items.size();
@@ -368,10 +436,11 @@ int finalize(sim_t s)
         S.nitem = (int)items.size() - S.item_g0;
         S.nlist = (int)lists.size() - S.list_g0;
         max_items = std::max(max_items, S.nitem);
-        // per-subsystem arrays (doubles: J, K or A, b, v, 1/L_pp or rhs, J v; T: L, W rows,
-        // g, D, c, s).  T offsets are whole 16-byte vectors so D rows load as vectors.
+        // per-subsystem arrays (doubles: J, K or A, b, v, 1/L_pp or rhs, J v; T: L, W, s;
+        // iteration T arrays: D, c).  T offsets are whole 16-byte vectors so D rows load as
+        // vectors.
         auto tal = [&](long long v) { return (v + vn - 1) / vn * vn; };
-        long long sd = 0, st = 0;
+        long long sd = 0, st = 0, sh = 0;
         for (int i = 0; i < S.nsub; ++i) {
             SubDesc &u = s->sdesc[S.sub0 + i];
             if (u.m > SUBADMM_MAXM)
@@ -383,12 +452,11 @@ int finalize(sim_t s)
             u.od_id = (int)sd; sd += u.n;
             u.od_t = (int)sd; sd += u.m;
             u.ot_L = (int)st; st += (long long)u.n * u.n;
-            u.ot_W = (int)st; st += (long long)u.m * u.n;
-            u.ot_g = (int)st; st = tal(st + u.n);
-            u.ot_D = (int)st; st = tal(st + (long long)u.m * u.mpad);
-            u.ot_c = (int)st; st = tal(st + u.m);
+            u.ot_W = (int)st; st = tal(st + (long long)(u.m + 1) * u.n);
             u.ot_s = (int)st; st = tal(st + u.n);
-            if (sd > (1LL << 30) || st > (1LL << 30)) return fail(s, SIM_EINVAL, "scene too large");
+            u.ot_D = (int)sh; sh = tal(sh + (long long)u.m * u.mpad);
+            u.ot_c = (int)sh; sh = tal(sh + u.m);
+            if (sd > (1LL << 30) || st + sh > (1LL << 30)) return fail(s, SIM_EINVAL, "scene too large");
         }
         // scene arrays (shared memory): per side-row arrays contiguous from ot_x to ot_lam
         const long long scd = 2LL * S.nsub;
@@ -400,16 +468,31 @@ int finalize(sim_t s)
             const long long ib = (tb + t * tsize + 15) / 16 * 16;
             return ib + 4 * ints;
         };
-        const long long onchip = bytes_of(sd + scd, st + scene_t);
-        S.sub_global = onchip > (long long)smem_budget ? 1 : 0;
+        // everything on chip if it fits; else the setup arrays (J, K, L, W: O(n^2)) in the
+        // workspace and the iteration arrays (D, c: O(m^2)) on chip; else all in the workspace
         long long od = 0, ot = 0;
-        if (S.sub_global) {
+        if (bytes_of(sd + scd, st + sh + scene_t) <= (long long)smem_budget) {
+            S.sub_global = 0; S.hot_global = 0; S.g_base = 0; S.g_tbase = 0;
+            od = sd; ot = st + sh;
+            for (int i = 0; i < S.nsub; ++i) {
+                s->sdesc[S.sub0 + i].ot_D += (int)st;
+                s->sdesc[S.sub0 + i].ot_c += (int)st;
+            }
+        } else if (bytes_of(scd, sh + scene_t) <= (long long)smem_budget) {
+            S.sub_global = 1; S.hot_global = 0;
             S.g_base = work_bytes;
             S.g_tbase = (sd * 8 + 255) / 256 * 256;
             work_bytes += (S.g_tbase + st * tsize + 255) / 256 * 256;
+            ot = sh;
         } else {
-            S.g_base = 0; S.g_tbase = 0;
-            od = sd; ot = st;
+            S.sub_global = 1; S.hot_global = 1;
+            S.g_base = work_bytes;
+            S.g_tbase = (sd * 8 + 255) / 256 * 256;
+            work_bytes += (S.g_tbase + (st + sh) * tsize + 255) / 256 * 256;
+            for (int i = 0; i < S.nsub; ++i) {
+                s->sdesc[S.sub0 + i].ot_D += (int)st;
+                s->sdesc[S.sub0 + i].ot_c += (int)st;
+            }
         }
         S.od_beta = (int)od; od += S.nsub;
         S.od_flag = (int)od; od += S.nsub;
@@ -476,6 +559,11 @@ int finalize(sim_t s)
     if ((rc = upload(s, &s->d_bodies, bodies, "bodies"))) return rc;
     if ((rc = upload(s, &s->d_nodes, nodes, "nodes"))) return rc;
     if ((rc = upload(s, &s->d_ipool, ipool, "integer pool"))) return rc;
+    {
+        cudaError_t e = cudaMalloc((void **)&s->d_subflag, std::max(1, nsubs) * sizeof(int));
+        if (e != cudaSuccess) return fail(s, SIM_ENOMEM, "cudaMalloc subsystem flags");
+        CK(cudaMemsetAsync(s->d_subflag, 0, std::max(1, nsubs) * sizeof(int), s->stream), "memset flags");
+    }
     s->nnodes = (long long)(nodes.size() / SUBADMM_NODE);
     s->pool_size = pool.size();
     if ((rc = zeros(s, &s->d_vhat, (size_t)dof, "vhat"))) return rc;
@@ -748,6 +836,7 @@ int sim_step(sim_t s, int n_steps)
     P.work = s->d_work;
     P.nodes = s->d_nodes;
     P.ipool = s->d_ipool;
+    P.subflag = s->d_subflag;
     P.beta = s->d_beta; P.res = s->d_res; P.stats = s->d_stats; P.phase = s->d_phase;
     P.nscenes = s->nscenes;
     P.n_steps = n_steps;
@@ -948,14 +1037,14 @@ int sim_scene_info(sim_t s, int scene, long long out[4])
     if (rc) return rc;
     if (scene < 0 || scene >= s->nscenes) return fail(s, SIM_EINVAL, "scene out of range");
     const SceneDesc &S = s->scenes[scene];
-    out[0] = S.sub_global;
+    out[0] = S.sub_global + S.hot_global;
     out[1] = S.smem_bytes;
     out[2] = S.nsub;
     out[3] = s->work_bytes;
     return SIM_OK;
 }
 
-int sim_iteration_stats(sim_t s, long long out[4])
+int sim_iteration_stats(sim_t s, long long out[4], long long *per_scene)
 {
     if (!s || !out) return SIM_EINVAL;
     if (!s->finalized) return fail(s, SIM_EINVAL, "no step has run");
@@ -969,6 +1058,7 @@ int sim_iteration_stats(sim_t s, long long out[4])
         out[2] += st[4 * k + 2];
         out[3] += st[4 * k + 3];
     }
+    if (per_scene) std::copy(st.begin(), st.begin() + 4 * (size_t)s->nscenes, per_scene);
     CK(cudaMemset(s->d_stats, 0, sizeof(long long) * 4 * s->nscenes), "stats clear");
     return SIM_OK;
 }

@@ -88,7 +88,7 @@ def load(build_if_missing: bool = True):
             "sim_read_state_noalloc": (C.c_int, [VP, VP]),
             "sim_write_state": (C.c_int, [VP, VP]),
             "sim_sizes": (C.c_int, [VP, PL]),
-            "sim_iteration_stats": (C.c_int, [VP, PL]),
+            "sim_iteration_stats": (C.c_int, [VP, PL, PL]),
             "sim_scene_info": (C.c_int, [VP, C.c_int, PL]),
             "sim_phase_trace": (C.c_int, [VP, C.c_int, PL]),
             "sim_sync": (C.c_int, [VP]),
@@ -185,7 +185,8 @@ def sim_read_state(h, dst_ptr: int) -> None:
 
 def sim_read_state_noalloc(h, dst_ptr: int) -> None:
     """sim_read_state through the library's fixed device staging array: never allocates
-    device memory (for callers that cannot); at most 10082 bodies; calls share the array."""
+    device memory (for callers that cannot); at most 131072 state doubles (10082 bodies);
+    calls share the array."""
     _check(h, load().sim_read_state_noalloc(h, VP(dst_ptr)))
 
 
@@ -204,15 +205,24 @@ def sim_sizes(h) -> dict:
 def sim_scene_info(h, scene: int) -> dict:
     out = (C.c_longlong * 4)()
     _check(h, load().sim_scene_info(h, scene, out))
-    return dict(global_workspace=bool(out[0]), smem_bytes=int(out[1]), subsystems=int(out[2]),
-                work_bytes=int(out[3]))
+    return dict(global_workspace=bool(out[0]), placement=int(out[0]), smem_bytes=int(out[1]),
+                subsystems=int(out[2]), work_bytes=int(out[3]))
 
 
-def sim_iteration_stats(h) -> dict:
+def sim_iteration_stats(h, per_scene: bool = False) -> dict:
+    """Totals since the last call (then cleared); with per_scene, also "per_scene": an
+    array (scenes, 4) of [iterations, max iterations, not converged, scene-steps]."""
     out = (C.c_longlong * 4)()
-    _check(h, load().sim_iteration_stats(h, out))
-    return dict(total_iters=int(out[0]), max_iters=int(out[1]), not_converged=int(out[2]),
-                scene_steps=int(out[3]))
+    ps = None
+    if per_scene:
+        ps = np.zeros((sim_sizes(h)["scenes"], 4), dtype=np.int64)
+    _check(h, load().sim_iteration_stats(h, out, None if ps is None else
+                                         ps.ctypes.data_as(C.POINTER(C.c_longlong))))
+    d = dict(total_iters=int(out[0]), max_iters=int(out[1]), not_converged=int(out[2]),
+             scene_steps=int(out[3]))
+    if ps is not None:
+        d["per_scene"] = ps
+    return d
 
 
 PHASES = ("assemble", "factor", "v_step", "z_step", "exit", "recover", "iterations",
@@ -389,5 +399,5 @@ class Simulation:
     def sizes(self) -> dict:
         return sim_sizes(self.h)
 
-    def iteration_stats(self) -> dict:
-        return sim_iteration_stats(self.h)
+    def iteration_stats(self, per_scene: bool = False) -> dict:
+        return sim_iteration_stats(self.h, per_scene)
