@@ -271,7 +271,11 @@ def time_form(subadmm, p, precision, args, stream, dev, local, dist, flush, samp
     device-wide wait per step).  The L2 is flushed before every timed launch."""
     import torch
     sim = subadmm.Simulation(p, stream=stream.cuda_stream, device=local, precision=precision)
-    for _ in range(args.warmup):
+    sim.step(1)
+    tuned = sim.launch_classes() if args.no_autotune else sim.autotune(steps=3)
+    if not args.no_graph:
+        sim.use_graph(True)
+    for _ in range(args.warmup - 1):
         sim.step(1)
     sim.sync()
     sim.iteration_stats()   # clear counters
@@ -303,6 +307,7 @@ def time_form(subadmm, p, precision, args, stream, dev, local, dist, flush, samp
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_ms = float(tt.item())
     stats = sim.iteration_stats(per_scene=True)
+    stats["classes"] = tuned
     return sim, t_ms, launch_ms, stats, (clk.summary() if clk else None)
 
 
@@ -326,6 +331,9 @@ def main():
                     help="mixed: FP32 iterations with FP64 setup and residual check (the "
                          "chosen form); fp64: the plain FP64 form")
     ap.add_argument("--steps-per-launch", type=int, default=50)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the heuristic kernel variants instead of timing them first")
+    ap.add_argument("--no-graph", action="store_true", help="launch directly, not by graph replay")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip timing the plain FP64 form next to the chosen one")
     args = ap.parse_args()
@@ -426,7 +434,12 @@ def main():
                        "side_rows": sizes["side_rows"], "parallelism": f"scenes x{world}",
                        "l2": "flushed between timed steps (512 MiB write)",
                        "launch": f"step kernel, {min(args.steps_per_launch, K)} steps per launch, "
-                                 f"one block of 256 threads per scene",
+                                 f"one block of 256 threads per scene, one launch per class of "
+                                 f"scenes (classes on forked streams)"
+                                 + ("" if args.no_graph else ", replayed as a CUDA graph"),
+                       "launch_classes": stats["classes"],
+                       "kernel_variants": "heuristic" if args.no_autotune else
+                                          "autotuned (sim_autotune, 3 steps per variant)",
                        "timed_segment": f"steps {args.warmup}..{args.warmup + K} of a run from "
                                         f"the drop"},
             "iterations": {"mean_per_scene_step": total_iters / max(stats["scene_steps"], 1),
@@ -436,7 +449,7 @@ def main():
             "plain_fp64": compare,
             "roofline": roofline,
             "e2e": e2e,
-            "gpu_launches": len(launch_ms),
+            "gpu_launches": len(launch_ms) * len(stats["classes"]),
             "clocks": clocks,
             "launch_ms": {"mean": statistics.mean(launch_ms),
                           "median": statistics.median(launch_ms),

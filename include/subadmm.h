@@ -157,6 +157,34 @@ int sim_set_generic(sim_t s, int subsystem, const double *A, const double *b);
  * uploads the topology.  Returns SIM_EINVAL if a scene does not fit the on-chip path. */
 int sim_step(sim_t s, int n_steps);
 
+/* Launch classes.  The scenes are grouped into classes that share a kernel variant (the
+ * register-cached iteration, which holds each thread's D row chunks and projection item in
+ * registers, or the generic one) and a shared-memory budget (a whole SM, or half of one for
+ * generic scenes that fit, so that two blocks share an SM).  sim_step enqueues one launch per
+ * class; classes after the first run on streams of their own forked from the simulation's
+ * stream and joined back to it, so the classes overlap.
+ * sim_launch_classes lays the simulation out if needed and writes, for each class k <
+ * max_classes, five counts at out[5k]: scenes, 1 if the register-cached kernel runs it, lanes
+ * per side-row (1, 2 or 4), dynamic shared memory per block in bytes, 0.  Returns the number
+ * of classes, or a negative SIM_E* code.
+ * sim_autotune times, for each class on its own, every kernel variant that is valid for all
+ * its scenes (generic with 1, 2 or 4 lanes per side-row, register-cached where the scenes
+ * fit) over `steps` steps from the current state, keeps the fastest, and restores the state
+ * (bodies, nodes, warm-start duals, outputs, counters) so that tuning leaves no trace.  It
+ * waits for the stream, allocates a temporary snapshot, and writes the same rows as
+ * sim_launch_classes with out[5k + 4] the chosen variant's time per step in nanoseconds.
+ * Returns the number of classes or a negative SIM_E* code. */
+int sim_launch_classes(sim_t s, int max_classes, long long *out);
+int sim_autotune(sim_t s, int steps, int max_classes, long long *out);
+
+/* CUDA-graph replay of sim_step (off by default).  When enabled, the first sim_step with a
+ * given n_steps captures its launches (one per launch class of scenes, forked across streams
+ * and joined back to the simulation's stream) into a graph, and later calls with the same
+ * n_steps replay it with a single cudaGraphLaunch on the stream.  A call on a stream that the
+ * caller is already capturing enqueues the launches into the caller's capture instead.
+ * Disabling frees the graph.  Returns SIM_OK, or SIM_EINVAL for a null handle. */
+int sim_use_graph(sim_t s, int enable);
+
 /* Waits for the stream, then writes for scene `scene`'s last step:
  * out[0] r_p = max|x - z|, out[1] r_d = max beta_i |z^{l+1} - z^l|, out[2] theta,
  * out[3] iterations, out[4] 1 if the stop rule held, out[5] status (0 or a SIM_E* code).

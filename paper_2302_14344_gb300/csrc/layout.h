@@ -54,6 +54,7 @@ struct SceneDesc {
 struct SubDesc {
     int kind, n, m;        // DOF, side-rows (rows of J_ci)
     int mpad;              // m rounded up to a whole 16-byte vector of the iteration type
+    int ldd;               // row stride of D (mpad, or mpad + one vector to keep it odd)
     int sr0;               // scene-local first side-row (16-byte aligned in the T region)
     int local;             // index inside its scene
     int body0, nb;         // first global body (rigid) or node (linear), and their count
@@ -68,7 +69,7 @@ struct SubDesc {
     int ot_L, ot_W;        // T region: L (n x n, 1/L_pp on the diagonal); W = L^-1 [J^T b]
                            // (n x (m + 1), column-major: W[p (m + 1) + t], column m = g)
     int ot_s;              // T region: solve vector of the mixed recovery (n)
-    int ot_D, ot_c;        // iteration region: D (m x mpad), c (m)
+    int ot_D, ot_c;        // iteration region: D (m rows of mpad, ldd apart), c (m)
     int v_off;             // global offset of v-hat
 };
 
@@ -93,6 +94,7 @@ struct Item {
 
 struct StepParams {
     const SceneDesc *scenes;
+    const int *scene_ids;  // the scenes of this launch (indices into scenes)
     const SubDesc *subs;
     const ConDesc *cons;
     const Item *items;
@@ -111,7 +113,7 @@ struct StepParams {
     double *res;           // 6 per scene
     long long *stats;      // 4 per scene: sum iters, max iters, not converged, steps
     long long *phase;      // 8 per scene (or null): SM clock cycles per phase, see PHASE_*
-    int nscenes;
+    int nscenes;           // scenes of this launch
     int n_steps;
     double h, g0, g1, g2, gamma, rho, tol, theta_th;
     int beta_fixed, warm_prev, stop_theta, max_iters;

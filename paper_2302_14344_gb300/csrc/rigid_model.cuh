@@ -198,19 +198,23 @@ __device__ __forceinline__ void body_dynamics(const double *B, double h, double 
 }
 
 // Linear elastic block (Eq. ddyn with the elastic force at the midpoint): the diagonal part
-// (2/h) m of A and b_p = (2/h) m v_p - (K (x - X0))_p + f_p + m g_p (K sparse, CSR).
+// (2/h) m of A and b_p = (2/h) m v_p - (K (x - X0))_p + f_p + m g_p (K sparse, CSR), a lane
+// per row; ux = x - X0 staged by the caller.  Two partial sums keep two gathers in flight.
 __device__ __forceinline__ double linear_b(int p, const double *mass, const double *f,
-                                           const double *X0, const double *Kval, const int *rowp,
+                                           const double *ux, const double *Kval, const int *rowp,
                                            const int *col, const double *nodes, double h,
                                            const double *g)
 {
-    double kx = 0.0;
-    for (int q = rowp[p]; q < rowp[p + 1]; ++q) {
-        const int cq = col[q];
-        kx += Kval[q] * (nodes[(cq / 3) * SUBADMM_NODE + cq % 3] - X0[cq]);
+    double k0 = 0.0, k1 = 0.0;
+    int q = rowp[p];
+    const int q1 = rowp[p + 1];
+    for (; q + 1 < q1; q += 2) {
+        k0 += Kval[q] * ux[col[q]];
+        k1 += Kval[q + 1] * ux[col[q + 1]];
     }
+    if (q < q1) k0 += Kval[q] * ux[col[q]];
     const double m = mass[p / 3];
-    return (2.0 / h) * m * nodes[(p / 3) * SUBADMM_NODE + 3 + p % 3] - kx + f[p] + m * g[p % 3];
+    return (2.0 / h) * m * nodes[(p / 3) * SUBADMM_NODE + 3 + p % 3] - (k0 + k1) + f[p] + m * g[p % 3];
 }
 
 // v_{k+1} = 2 v-hat - v_k; p += h v-hat; q <- q (x) Exp(h w-hat), renormalised.

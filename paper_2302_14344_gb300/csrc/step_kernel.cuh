@@ -202,7 +202,7 @@ __device__ void scene_tables(const StepParams &P, const SceneDesc &S, const View
                 const int lr = t - u.sr0;
                 V.row[t] = c.row0 + r;
                 V.sub[t] = c.sub[s];
-                V.drow[t] = u.ot_D + lr * u.mpad;
+                V.drow[t] = u.ot_D + lr * u.ldd;
                 V.coff[t] = u.ot_c + lr;
                 V.wbase[t] = u.sr0;
                 V.mlen[t] = u.m;
@@ -359,10 +359,10 @@ __device__ void env_forward_vec(const F *LT, F *y, int n, int ldy, const int *la
     }
 }
 
-// D = W^T W over the m columns of W (rows padded with zeros to mp); W column t is zero above
-// row jlo[t]
+// D = W^T W over the m columns of W (rows ldd apart, padded with zeros to mp); W column t
+// is zero above row jlo[t]
 template <typename F>
-__device__ void form_D(const F *W, int n, int m, int mp, int ldw, const int *jlo, F *D)
+__device__ void form_D(const F *W, int n, int m, int mp, int ldd, int ldw, const int *jlo, F *D)
 {
     const int lane = threadIdx.x & 31;
     for (int k = lane; k < m * (m + 1) / 2; k += 32) {
@@ -375,13 +375,13 @@ __device__ void form_D(const F *W, int n, int m, int mp, int ldw, const int *jlo
             a1 += W[(p + 1) * ldw + r] * W[(p + 1) * ldw + s];
         }
         if (p < n) a0 += W[p * ldw + r] * W[p * ldw + s];
-        D[r * mp + s] = a0 + a1;
-        D[s * mp + r] = a0 + a1;
+        D[r * ldd + s] = a0 + a1;
+        D[s * ldd + r] = a0 + a1;
     }
     if (mp > m) {
         for (int t = lane; t < m * (mp - m); t += 32) {
             const int r = t / (mp - m);
-            D[r * mp + m + (t - r * (mp - m))] = (F)0;
+            D[r * ldd + m + (t - r * (mp - m))] = (F)0;
         }
     }
 }
@@ -438,13 +438,20 @@ __device__ void scene_setup(const StepParams &P, const SceneDesc &S, const View<
             const int *rowp = P.ipool + u.csr_off, *col = rowp + u.n + 1;
             const double gv[3] = {P.g0, P.g1, P.g2};
             const double *nodes = P.nodes + (size_t)u.body0 * SUBADMM_NODE;
-            for (int p = lane; p < u.n; p += 32) {
-                if (!keep) {
-                    for (int q = rowp[p]; q < rowp[p + 1]; ++q) K[p * u.n + col[q]] = 0.5 * P.h * Kval[q];
-                    K[p * u.n + p] += (2.0 / P.h) * mass[p / 3];
+            double *ux = sdb + u.od_v;               // x - X0 (v-hat is rewritten later)
+            for (int p = lane; p < u.n; p += 32) ux[p] = nodes[(p / 3) * SUBADMM_NODE + p % 3] - X0[p];
+            if (!keep) {
+                for (int p = lane; p < u.n; p += 32) {
+                    const int q1 = rowp[p + 1];
+#pragma unroll 4
+                    for (int q = rowp[p]; q < q1; ++q) K[p * u.n + col[q]] = 0.5 * P.h * Kval[q];
                 }
-                sdb[u.od_b + p] = linear_b(p, mass, f, X0, Kval, rowp, col, nodes, P.h, gv);
+                __syncwarp();
+                for (int p = lane; p < u.n; p += 32) K[p * u.n + p] += (2.0 / P.h) * mass[p / 3];
             }
+            __syncwarp();
+            for (int p = lane; p < u.n; p += 32)
+                sdb[u.od_b + p] = linear_b(p, mass, f, ux, Kval, rowp, col, nodes, P.h, gv);
         }
     }
     __syncthreads();
@@ -528,7 +535,7 @@ __device__ void scene_setup(const StepParams &P, const SceneDesc &S, const View<
             for (int p = lane; p < n; p += 32) W[p * ldw + m] = (T)b[p];
             __syncwarp();
             env_forward_vec<T>(LT, W + m, n, ldw, e.lastr);
-            if (step == 0 && !S.hot_global) form_D<T>(W, n, m, mp, ldw, e.jlo, D);
+            if (step == 0 && !S.hot_global) form_D<T>(W, n, m, mp, u.ldd, ldw, e.jlo, D);
             form_c<T>(W, n, m, ldw, e.jlo, cc);
             __syncwarp();
             continue;
@@ -609,7 +616,7 @@ __device__ void scene_setup(const StepParams &P, const SceneDesc &S, const View<
         __syncwarp();
         env_forward_cols<T>(LT, W, n, ldw, m + 1, e.env);
         __syncwarp();
-        form_D<T>(W, n, m, mp, ldw, e.jlo, D);
+        form_D<T>(W, n, m, mp, u.ldd, ldw, e.jlo, D);
         form_c<T>(W, n, m, ldw, e.jlo, cc);
         __syncwarp();
     }
@@ -759,7 +766,8 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, CACHED ? 1 : 2) step_kernel(S
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr bool MIXED = sizeof(T) == 4;
 
-    for (int sc = blockIdx.x; sc < P.nscenes; sc += gridDim.x) {
+    for (int k = blockIdx.x; k < P.nscenes; k += gridDim.x) {
+        const int sc = P.scene_ids[k];
         const SceneDesc S = P.scenes[sc];
         const View<T> V = scene_view<T>(P, S, smraw);
         T *X = V.tb + S.ot_x, *Y = V.tb + S.ot_y, *Z = V.tb + S.ot_z, *LAM = V.tb + S.ot_lam;
@@ -909,30 +917,50 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, CACHED ? 1 : 2) step_kernel(S
                             X[xt] = acc;
                         }
                     } else {
+                        // two side-rows per trip, two accumulators per row: independent
+                        // load and FMA chains overlap
                         constexpr int groups = SUBADMM_THREADS / SPLIT;
                         const int trips = (S.nsr + groups - 1) / groups;
-                        for (int k = 0; k < trips; ++k) {
-                            const int t = xg + k * groups;
-                            const int m = t < S.nsr ? V.mlen[t] : 0;
-                            T acc = (T)0;
-                            if (m > 0) {
-                                const VT *Dr = reinterpret_cast<const VT *>(V.htb + V.drow[t]);
-                                const VT *wb = reinterpret_cast<const VT *>(w + V.wbase[t]);
-                                const int nv = (m + VN - 1) / VN;
-                                for (int c = xgl; c < nv; c += SPLIT) acc = vdot(Dr[c], wb[c], acc);
+                        for (int k = 0; k < trips; k += 2) {
+                            int tt[2], mm[2];
+                            T acc[2];
+#pragma unroll
+                            for (int h = 0; h < 2; ++h) {
+                                tt[h] = xg + (k + h) * groups;
+                                mm[h] = (k + h < trips && tt[h] < S.nsr) ? V.mlen[tt[h]] : 0;
+                                T a0 = (T)0, a1 = (T)0;
+                                if (mm[h] > 0) {
+                                    const VT *Dr = reinterpret_cast<const VT *>(V.htb + V.drow[tt[h]]);
+                                    const VT *wb = reinterpret_cast<const VT *>(w + V.wbase[tt[h]]);
+                                    const int nv = (mm[h] + VN - 1) / VN;
+                                    int c = xgl;
+                                    for (; c + SPLIT < nv; c += 2 * SPLIT) {
+                                        a0 = vdot(Dr[c], wb[c], a0);
+                                        a1 = vdot(Dr[c + SPLIT], wb[c + SPLIT], a1);
+                                    }
+                                    if (c < nv) a0 = vdot(Dr[c], wb[c], a0);
+                                }
+                                acc[h] = a0 + a1;
                             }
 #pragma unroll
-                            for (int o = SPLIT / 2; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-                            if (m > 0 && xgl == 0) {
-                                acc += V.htb[V.coff[t]];
-                                const T ynew = BT[t] * acc - LAM[V.row[t]];
-                                if (P.stop_theta) {
-                                    const T d = ynew - Y[t];
-                                    tpart += d * d;
+                            for (int o = SPLIT / 2; o; o >>= 1) {
+                                acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], o);
+                                acc[1] += __shfl_xor_sync(0xffffffffu, acc[1], o);
+                            }
+#pragma unroll
+                            for (int h = 0; h < 2; ++h) {
+                                const int t = tt[h];
+                                if (mm[h] > 0 && xgl == 0) {
+                                    const T a = acc[h] + V.htb[V.coff[t]];
+                                    const T ynew = BT[t] * a - LAM[V.row[t]];
+                                    if (P.stop_theta) {
+                                        const T d = ynew - Y[t];
+                                        tpart += d * d;
+                                    }
+                                    YO[t] = Y[t];
+                                    Y[t] = ynew;
+                                    X[t] = a;
                                 }
-                                YO[t] = Y[t];
-                                Y[t] = ynew;
-                                X[t] = acc;
                             }
                         }
                     }

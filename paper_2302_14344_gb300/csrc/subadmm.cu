@@ -28,6 +28,17 @@ struct HostSub {
     std::vector<double> nodes;   // linear: nb records of 6 (x[3], v[3])
 };
 
+struct LaunchClass {
+    bool cached = false;           // register-cached iteration
+    int split = 1;                 // lanes per side-row in the v-step mat-vec
+    bool half = false;             // placed within half an SM's shared memory (two blocks/SM)
+    std::vector<int> scenes;
+    int ids_off = 0;               // offset of the scene list in d_scene_ids
+    int max_smem = 0;
+    cudaStream_t stream = nullptr; // class 0 runs on the simulation's stream
+    cudaEvent_t done = nullptr;
+};
+
 struct HostCon {
     int scene = 0, src = 0, type = 0, rows = 0, ns = 0;
     int side_sub[SUBADMM_MAXS] = {0};   // global subsystem ids
@@ -64,8 +75,21 @@ struct sim_s {
     Item *d_items = nullptr;
     int *d_lists = nullptr;
     int *d_asm = nullptr;
-    bool cached = false;           // every scene fits the register-cached iteration
-    int split = 1;                 // lanes per side-row in the v-step mat-vec
+    // launch classes: scenes that share a kernel variant (register-cached or generic, lanes
+    // per side-row) and a shared-memory budget; each class is one launch, the classes run
+    // concurrently on forked streams
+    std::vector<LaunchClass> classes;
+    int *d_scene_ids = nullptr;    // every class's scene list, concatenated
+    cudaEvent_t ev_fork = nullptr;
+    int split_override = 0;        // tuning: force the split of every class (0: heuristic)
+    std::vector<int> sc_nsr, sc_items, sc_sides, sc_mpad;   // per scene: register-cache limits
+    int smem_full = 0;             // dynamic shared memory a block may use
+    // graph replay of sim_step
+    bool use_graph = false;
+    int graph_steps = 0;
+    cudaGraphExec_t graph = nullptr;
+    cudaStream_t graph_stream = nullptr;   // capture and replay stream when the simulation's
+                                           // stream is the legacy default stream
     double *d_pool = nullptr, *d_bodies = nullptr, *d_vhat = nullptr, *d_lam = nullptr;
     double *d_z = nullptr, *d_beta = nullptr, *d_res = nullptr, *d_stage = nullptr;
     long long *d_stats = nullptr;
@@ -165,6 +189,20 @@ void free_device(sim_t s)
     cudaFree(s->d_work);
     s->d_work = nullptr;
     cudaFree(s->d_nodes); cudaFree(s->d_ipool); cudaFree(s->d_subflag);
+    cudaFree(s->d_scene_ids);
+    s->d_scene_ids = nullptr;
+    for (auto &c : s->classes) {
+        if (c.stream) cudaStreamDestroy(c.stream);
+        if (c.done) cudaEventDestroy(c.done);
+    }
+    s->classes.clear();
+    if (s->ev_fork) cudaEventDestroy(s->ev_fork);
+    s->ev_fork = nullptr;
+    if (s->graph) cudaGraphExecDestroy(s->graph);
+    s->graph = nullptr;
+    s->graph_steps = 0;
+    if (s->graph_stream) cudaStreamDestroy(s->graph_stream);
+    s->graph_stream = nullptr;
     s->d_nodes = nullptr; s->d_ipool = nullptr; s->d_subflag = nullptr;
     s->d_scenes = nullptr; s->d_subs = nullptr; s->d_cons = nullptr; s->d_pool = nullptr;
     s->d_bodies = nullptr; s->d_vhat = nullptr; s->d_lam = nullptr; s->d_z = nullptr;
@@ -225,8 +263,15 @@ int finalize(sim_t s)
     CK(cudaDeviceGetAttribute(&dev_max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->opt.device),
        "attribute");
     const int smem_budget = dev_max_smem - 1024;   // static shared memory of the kernel
+    s->smem_full = smem_budget;
+    int sm_smem = 0;
+    CK(cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, s->opt.device),
+       "attribute");
     long long work_bytes = 0;
     int max_nsr = 0, max_items = 0, max_sides = 0, max_mpad = 0;
+    struct Place { long long sd, st, sh, scd, scene_t, ints; };
+    std::vector<Place> place(nscenes);
+    std::vector<int> sc_mpad(nscenes, 0), sc_sides(nscenes, 0);
     s->sdesc.assign(nsubs, SubDesc{});
     s->cdesc.assign(ncons, ConDesc{});
     s->scenes.assign(nscenes, SceneDesc{});
@@ -303,6 +348,7 @@ int finalize(sim_t s)
             u.m = sr - u.sr0;
             u.mpad = (u.m + vn - 1) / vn * vn;
             max_mpad = std::max(max_mpad, u.mpad);
+            sc_mpad[sc] = std::max(sc_mpad[sc], u.mpad);
         }
         sr = (sr + vn - 1) / vn * vn;
         S.nsr = sr;
@@ -407,6 +453,7 @@ int finalize(sim_t s)
                 const ConDesc &c = s->cdesc[S.con0 + j];
                 if (c.type != type) continue;
                 max_sides = std::max(max_sides, c.ns);
+                sc_sides[sc] = std::max(sc_sides[sc], c.ns);
                 if (c.type == TYPE_CONTACT) {
                     items.push_back(Item{c.type, c.ns, c.row0, (int)lists.size() - S.list_g0});
                     for (int q = 0; q < c.ns; ++q) lists.push_back(c.sr[q]);
@@ -454,44 +501,99 @@ int finalize(sim_t s)
             u.ot_L = (int)st; st += (long long)u.n * u.n;
             u.ot_W = (int)st; st = tal(st + (long long)(u.m + 1) * u.n);
             u.ot_s = (int)st; st = tal(st + u.n);
-            u.ot_D = (int)sh; sh = tal(sh + (long long)u.m * u.mpad);
+            // D rows are ldd apart: an odd number of 16-byte vectors, so the rows that the
+            // lanes of a warp read at once fall in different shared-memory banks
+            u.ldd = ((u.mpad / vn) % 2 == 0) ? u.mpad + vn : u.mpad;
+            u.ot_D = (int)sh; sh = tal(sh + (long long)u.m * u.ldd);
             u.ot_c = (int)sh; sh = tal(sh + u.m);
             if (sd > (1LL << 30) || st + sh > (1LL << 30)) return fail(s, SIM_EINVAL, "scene too large");
         }
         // scene arrays (shared memory): per side-row arrays contiguous from ot_x to ot_lam
-        const long long scd = 2LL * S.nsub;
-        const long long scene_t = tal((long long)S.nsr) * 9 + 6LL * S.nrow;
-        const int tsize = s->opt.precision == SIM_MIXED ? 4 : 8;
-        const long long ints = 6LL * S.nsr + 4LL * S.nitem + S.nlist;
-        auto bytes_of = [&](long long d, long long t) {
-            const long long tb = (d * 8 + 15) / 16 * 16;
-            const long long ib = (tb + t * tsize + 15) / 16 * 16;
-            return ib + 4 * ints;
-        };
+        place[sc] = Place{sd, st, sh, 2LL * S.nsub, tal((long long)S.nsr) * 9 + 6LL * S.nrow,
+                          6LL * S.nsr + 4LL * S.nitem + S.nlist};
+        max_nsr = std::max(max_nsr, S.nsr);
+        sr_g += S.nsr;
+        rows_g += S.nrow;
+    }
+    s->dof = dof; s->nrows = rows_g; s->nsr = sr_g;
+    s->nbodies = (long long)(bodies.size() / SUBADMM_BODY);
+    // launch classes.  Per scene: lanes per side-row of the v-step mat-vec (the largest of
+    // 1, 2, 4 whose groups still cover the side-rows twice), and whether it fits the
+    // register-cached iteration (one side-row group and one item per thread, at most 4
+    // float4 / 6 double2 chunks of a D row per lane).  The register-cached kernel runs one
+    // block per SM and may take all of its shared memory; the generic kernel runs two blocks
+    // per SM, so a generic scene whose per-row and iteration arrays fit within half an SM is
+    // placed there, and the others get the whole budget in a class of their own.
+    const int tsize = s->opt.precision == SIM_MIXED ? 4 : 8;
+    const int vn = s->opt.precision == SIM_MIXED ? 4 : 2;
+    const int chunks = s->opt.precision == SIM_MIXED ? 4 : 6;
+    auto tal = [&](long long v) { return (v + vn - 1) / vn * vn; };
+    const int half_budget = std::min(smem_budget, sm_smem / 2 - 2048);
+    auto bytes_with = [&](const Place &q, long long d, long long tt) {
+        const long long tb = (d * 8 + 15) / 16 * 16;
+        const long long ib = (tb + tt * tsize + 15) / 16 * 16;
+        return ib + 4 * q.ints;
+    };
+    std::vector<int> sc_budget(nscenes, smem_budget), sc_class(nscenes, 0);
+    s->sc_nsr.assign(nscenes, 0);
+    s->sc_items.assign(nscenes, 0);
+    for (int sc = 0; sc < nscenes; ++sc) {
+        s->sc_nsr[sc] = s->scenes[sc].nsr;
+        s->sc_items[sc] = s->scenes[sc].nitem;
+    }
+    s->sc_sides = sc_sides;
+    s->sc_mpad = sc_mpad;
+    s->classes.clear();
+    for (int sc = 0; sc < nscenes; ++sc) {
+        const SceneDesc &S = s->scenes[sc];
+        const Place &q = place[sc];
+        int split = 1;
+        while (split < 4 && 2 * split * std::max(S.nsr, 1) <= SUBADMM_THREADS) split *= 2;
+        if (s->split_override > 0) split = s->split_override;
+        const bool cached = S.nsr * split <= SUBADMM_THREADS && S.nitem <= SUBADMM_THREADS &&
+                            sc_sides[sc] <= 2 && (sc_mpad[sc] + vn - 1) / vn <= chunks * split;
+        const bool half = !cached && bytes_with(q, q.scd, q.sh + q.scene_t) <= half_budget;
+        sc_budget[sc] = half ? half_budget : smem_budget;
+        int k = 0;
+        while (k < (int)s->classes.size() && !(s->classes[k].cached == cached &&
+               s->classes[k].split == split && s->classes[k].half == half)) ++k;
+        if (k == (int)s->classes.size()) {
+            LaunchClass c;
+            c.cached = cached; c.split = split; c.half = half;
+            s->classes.push_back(c);
+        }
+        s->classes[k].scenes.push_back(sc);
+        sc_class[sc] = k;
+    }
+    for (int sc = 0; sc < nscenes; ++sc) {
+        SceneDesc &S = s->scenes[sc];
+        const Place &q = place[sc];
+        const int budget = sc_budget[sc];
+        auto bytes_of = [&](long long d, long long tt) { return bytes_with(q, d, tt); };
         // everything on chip if it fits; else the setup arrays (J, K, L, W: O(n^2)) in the
         // workspace and the iteration arrays (D, c: O(m^2)) on chip; else all in the workspace
         long long od = 0, ot = 0;
-        if (bytes_of(sd + scd, st + sh + scene_t) <= (long long)smem_budget) {
+        if (bytes_of(q.sd + q.scd, q.st + q.sh + q.scene_t) <= (long long)budget) {
             S.sub_global = 0; S.hot_global = 0; S.g_base = 0; S.g_tbase = 0;
-            od = sd; ot = st + sh;
+            od = q.sd; ot = q.st + q.sh;
             for (int i = 0; i < S.nsub; ++i) {
-                s->sdesc[S.sub0 + i].ot_D += (int)st;
-                s->sdesc[S.sub0 + i].ot_c += (int)st;
+                s->sdesc[S.sub0 + i].ot_D += (int)q.st;
+                s->sdesc[S.sub0 + i].ot_c += (int)q.st;
             }
-        } else if (bytes_of(scd, sh + scene_t) <= (long long)smem_budget) {
+        } else if (bytes_of(q.scd, q.sh + q.scene_t) <= (long long)budget) {
             S.sub_global = 1; S.hot_global = 0;
             S.g_base = work_bytes;
-            S.g_tbase = (sd * 8 + 255) / 256 * 256;
-            work_bytes += (S.g_tbase + st * tsize + 255) / 256 * 256;
-            ot = sh;
+            S.g_tbase = (q.sd * 8 + 255) / 256 * 256;
+            work_bytes += (S.g_tbase + q.st * tsize + 255) / 256 * 256;
+            ot = q.sh;
         } else {
             S.sub_global = 1; S.hot_global = 1;
             S.g_base = work_bytes;
-            S.g_tbase = (sd * 8 + 255) / 256 * 256;
-            work_bytes += (S.g_tbase + (st + sh) * tsize + 255) / 256 * 256;
+            S.g_tbase = (q.sd * 8 + 255) / 256 * 256;
+            work_bytes += (S.g_tbase + (q.st + q.sh) * tsize + 255) / 256 * 256;
             for (int i = 0; i < S.nsub; ++i) {
-                s->sdesc[S.sub0 + i].ot_D += (int)st;
-                s->sdesc[S.sub0 + i].ot_c += (int)st;
+                s->sdesc[S.sub0 + i].ot_D += (int)q.st;
+                s->sdesc[S.sub0 + i].ot_c += (int)q.st;
             }
         }
         S.od_beta = (int)od; od += S.nsub;
@@ -513,24 +615,37 @@ int finalize(sim_t s)
         S.ot_mu = (int)ot; ot += S.nrow;
         const long long t_base = (od * 8 + 15) / 16 * 16;
         const long long i_base = (t_base + ot * tsize + 15) / 16 * 16;
-        const long long bytes = i_base + 4 * ints;
-        if (bytes > (long long)smem_budget) {
+        const long long bytes = i_base + 4 * q.ints;
+        if (bytes > (long long)budget) {
             char buf[256];
             snprintf(buf, sizeof buf, "scene %d needs %lld bytes of shared memory for its per-row "
-                     "arrays alone; at most %d are available", sc, bytes, smem_budget);
+                     "arrays alone; at most %d are available", sc, bytes, budget);
             return fail(s, SIM_EINVAL, buf);
         }
         S.t_base = (int)t_base;
         S.i_base = (int)i_base;
         S.smem_bytes = (int)bytes;
         max_smem = std::max(max_smem, S.smem_bytes);
-        max_nsr = std::max(max_nsr, S.nsr);
-        sr_g += S.nsr;
-        rows_g += S.nrow;
+        LaunchClass &cl = s->classes[sc_class[sc]];
+        cl.max_smem = std::max(cl.max_smem, S.smem_bytes);
     }
-    s->dof = dof; s->nrows = rows_g; s->nsr = sr_g;
-    s->nbodies = (long long)(bodies.size() / SUBADMM_BODY);
     s->max_smem = max_smem;
+    {
+        // scene lists, streams and events of the classes (class 0 uses the simulation's stream)
+        std::vector<int> ids;
+        for (auto &c : s->classes) {
+            c.ids_off = (int)ids.size();
+            ids.insert(ids.end(), c.scenes.begin(), c.scenes.end());
+        }
+        int rc2 = upload(s, &s->d_scene_ids, ids, "scene lists");
+        if (rc2) return rc2;
+        CK(cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming), "event");
+        for (size_t k = 0; k < s->classes.size(); ++k) {
+            LaunchClass &c = s->classes[k];
+            if (k > 0) CK(cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking), "class stream");
+            CK(cudaEventCreateWithFlags(&c.done, cudaEventDisableTiming), "event");
+        }
+    }
     if (work_bytes > 0) {
         cudaError_t e = cudaMalloc((void **)&s->d_work, (size_t)work_bytes);
         if (e != cudaSuccess) return fail(s, SIM_ENOMEM, std::string("cudaMalloc workspace: ") + cudaGetErrorString(e));
@@ -546,16 +661,6 @@ int finalize(sim_t s)
     if ((rc = upload(s, &s->d_items, items, "items"))) return rc;
     if ((rc = upload(s, &s->d_lists, lists, "lists"))) return rc;
     if ((rc = upload(s, &s->d_asm, asm_order, "assembly order"))) return rc;
-    s->split = 1;
-    while (s->split < 4 && 2 * s->split * std::max(max_nsr, 1) <= SUBADMM_THREADS) s->split *= 2;
-    // the register-cached iteration holds one side-row group and one item per thread
-    // (and at most 4 float4 / 6 double2 chunks of a D row per lane)
-    {
-        const int vn = s->opt.precision == SIM_MIXED ? 4 : 2;
-        const int chunks = s->opt.precision == SIM_MIXED ? 4 : 6;
-        s->cached = max_nsr * s->split <= SUBADMM_THREADS && max_items <= SUBADMM_THREADS &&
-                    max_sides <= 2 && (max_mpad + vn - 1) / vn <= chunks * s->split;
-    }
     if ((rc = upload(s, &s->d_bodies, bodies, "bodies"))) return rc;
     if ((rc = upload(s, &s->d_nodes, nodes, "nodes"))) return rc;
     if ((rc = upload(s, &s->d_ipool, ipool, "integer pool"))) return rc;
@@ -823,13 +928,15 @@ int sim_set_generic(sim_t s, int sub, const double *A, const double *b)
     return SIM_OK;
 }
 
-int sim_step(sim_t s, int n_steps)
+}  // extern "C"
+
+namespace {
+
+using KernFn = void (*)(StepParams);
+
+// kernel parameters of a step launch (scene list filled in per class)
+StepParams step_params(const sim_t s, int n_steps)
 {
-    if (!s) return SIM_EINVAL;
-    if (n_steps < 1) return fail(s, SIM_EINVAL, "n_steps must be >= 1");
-    int rc = finalize(s);
-    if (rc) return rc;
-    if (s->nscenes == 0) return SIM_OK;
     StepParams P;
     P.scenes = s->d_scenes; P.subs = s->d_subs; P.cons = s->d_cons; P.pool = s->d_pool;
     P.bodies = s->d_bodies; P.vhat = s->d_vhat; P.lam = s->d_lam; P.z = s->d_z;
@@ -847,26 +954,247 @@ int sim_step(sim_t s, int n_steps)
     P.warm_prev = s->opt.warm == SIM_WARM_PREV;
     P.stop_theta = s->opt.stop == SIM_STOP_THETA;
     P.max_iters = s->opt.max_iters;
-    CK(cudaSetDevice(s->opt.device), "cudaSetDevice");
     P.items = s->d_items;
     P.lists = s->d_lists;
     P.asm_order = s->d_asm;
-    const bool mixed = s->opt.precision == SIM_MIXED;
-    void (*kern)(StepParams) = nullptr;
+    P.scene_ids = s->d_scene_ids;
+    return P;
+}
+
+KernFn kernel_for(bool mixed, bool cached, int split)
+{
     using namespace subadmm;
     if (mixed) {
-        if (s->cached) kern = s->split == 4 ? step_kernel<float, 4, true> : s->split == 2 ? step_kernel<float, 2, true> : step_kernel<float, 1, true>;
-        else kern = s->split == 4 ? step_kernel<float, 4, false> : s->split == 2 ? step_kernel<float, 2, false> : step_kernel<float, 1, false>;
-    } else {
-        if (s->cached) kern = s->split == 4 ? step_kernel<double, 4, true> : s->split == 2 ? step_kernel<double, 2, true> : step_kernel<double, 1, true>;
-        else kern = s->split == 4 ? step_kernel<double, 4, false> : s->split == 2 ? step_kernel<double, 2, false> : step_kernel<double, 1, false>;
+        if (cached) return split == 4 ? step_kernel<float, 4, true> : split == 2 ? step_kernel<float, 2, true> : step_kernel<float, 1, true>;
+        return split == 4 ? step_kernel<float, 4, false> : split == 2 ? step_kernel<float, 2, false> : step_kernel<float, 1, false>;
     }
-    // the attribute is per function, shared by every simulation of the process
-    CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, std::max(s->max_smem, 1)),
-       "shared memory attribute");
-    kern<<<s->nscenes, SUBADMM_THREADS, s->max_smem, s->stream>>>(P);
-    CK(cudaGetLastError(), "step kernel launch");
+    if (cached) return split == 4 ? step_kernel<double, 4, true> : split == 2 ? step_kernel<double, 2, true> : step_kernel<double, 1, true>;
+    return split == 4 ? step_kernel<double, 4, false> : split == 2 ? step_kernel<double, 2, false> : step_kernel<double, 1, false>;
+}
+
+// Enqueue one launch per class: class 0 on the simulation's stream, the others on their
+// own streams forked from it and joined back, so the classes run concurrently.
+int launch_classes(sim_t s, StepParams P, cudaStream_t base)
+{
+    const bool mixed = s->opt.precision == SIM_MIXED;
+    const int nc = (int)s->classes.size();
+    if (nc > 1) CK(cudaEventRecord(s->ev_fork, base), "fork");
+    for (int k = 0; k < nc; ++k) {
+        const LaunchClass &c = s->classes[k];
+        cudaStream_t st = k == 0 ? base : c.stream;
+        if (k > 0) CK(cudaStreamWaitEvent(st, s->ev_fork, 0), "fork wait");
+        P.scene_ids = s->d_scene_ids + c.ids_off;
+        P.nscenes = (int)c.scenes.size();
+        kernel_for(mixed, c.cached, c.split)<<<P.nscenes, SUBADMM_THREADS, c.max_smem, st>>>(P);
+        CK(cudaGetLastError(), "step kernel launch");
+        if (k > 0) {
+            CK(cudaEventRecord(c.done, st), "join");
+            CK(cudaStreamWaitEvent(base, c.done, 0), "join wait");
+        }
+    }
     return SIM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sim_step(sim_t s, int n_steps)
+{
+    if (!s) return SIM_EINVAL;
+    if (n_steps < 1) return fail(s, SIM_EINVAL, "n_steps must be >= 1");
+    int rc = finalize(s);
+    if (rc) return rc;
+    if (s->nscenes == 0) return SIM_OK;
+    CK(cudaSetDevice(s->opt.device), "cudaSetDevice");
+    StepParams P = step_params(s, n_steps);
+    // the attribute is per function (shared by every simulation of the process): allow the
+    // full budget; each launch requests its class's own size, which sets its occupancy
+    for (const LaunchClass &c : s->classes)
+        CK(cudaFuncSetAttribute(kernel_for(s->opt.precision == SIM_MIXED, c.cached, c.split),
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, s->smem_full),
+           "shared memory attribute");
+    if (s->use_graph) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        CK(cudaStreamIsCapturing(s->stream, &cs), "capture status");
+        if (cs == cudaStreamCaptureStatusNone) {
+            // the legacy default stream cannot be captured: capture on and replay from a
+            // private blocking stream, which the legacy stream orders implicitly
+            cudaStream_t gs = s->stream;
+            if (!gs) {
+                if (!s->graph_stream) CK(cudaStreamCreate(&s->graph_stream), "graph stream");
+                gs = s->graph_stream;
+            }
+            // replay the captured launches of this step count (captured on first use)
+            if (!s->graph || s->graph_steps != n_steps) {
+                if (s->graph) cudaGraphExecDestroy(s->graph);
+                s->graph = nullptr;
+                cudaGraph_t g = nullptr;
+                CK(cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal), "begin capture");
+                const int lrc = launch_classes(s, P, gs);
+                cudaError_t ec = cudaStreamEndCapture(gs, &g);
+                if (lrc) { if (g) cudaGraphDestroy(g); return lrc; }
+                CK(ec, "end capture");
+                cudaError_t ei = cudaGraphInstantiate(&s->graph, g, 0);
+                cudaGraphDestroy(g);
+                CK(ei, "graph instantiate");
+                s->graph_steps = n_steps;
+            }
+            CK(cudaGraphLaunch(s->graph, gs), "graph launch");
+            if (gs != s->stream) {
+                // an explicit join, so that waits on the simulation's stream cover the replay
+                CK(cudaEventRecord(s->ev_fork, gs), "graph join");
+                CK(cudaStreamWaitEvent(s->stream, s->ev_fork, 0), "graph join wait");
+            }
+            return SIM_OK;
+        }
+    }
+    return launch_classes(s, P, s->stream);
+}
+
+int sim_use_graph(sim_t s, int enable)
+{
+    if (!s) return SIM_EINVAL;
+    s->use_graph = enable != 0;
+    if (!s->use_graph && s->graph) {
+        cudaGraphExecDestroy(s->graph);
+        s->graph = nullptr;
+        s->graph_steps = 0;
+    }
+    return SIM_OK;
+}
+
+namespace {
+
+// a scene fits the register-cached iteration with `split` lanes per side-row
+bool cache_fits(const sim_t s, int sc, int split)
+{
+    const int vn = s->opt.precision == SIM_MIXED ? 4 : 2;
+    const int chunks = s->opt.precision == SIM_MIXED ? 4 : 6;
+    return s->sc_nsr[sc] * split <= SUBADMM_THREADS && s->sc_items[sc] <= SUBADMM_THREADS &&
+           s->sc_sides[sc] <= 2 && (s->sc_mpad[sc] + vn - 1) / vn <= chunks * split;
+}
+
+void class_rows(const sim_t s, int max_classes, long long *out, const std::vector<double> *ns)
+{
+    for (int k = 0; k < (int)s->classes.size() && k < max_classes; ++k) {
+        const LaunchClass &c = s->classes[k];
+        out[5 * k + 0] = (long long)c.scenes.size();
+        out[5 * k + 1] = c.cached ? 1 : 0;
+        out[5 * k + 2] = c.split;
+        out[5 * k + 3] = c.max_smem;
+        out[5 * k + 4] = ns ? (long long)(*ns)[k] : 0;
+    }
+}
+
+}  // namespace
+
+int sim_launch_classes(sim_t s, int max_classes, long long *out)
+{
+    if (!s || (max_classes > 0 && !out)) return SIM_EINVAL;
+    int rc = finalize(s);
+    if (rc) return rc;
+    class_rows(s, max_classes, out, nullptr);
+    return (int)s->classes.size();
+}
+
+int sim_autotune(sim_t s, int steps, int max_classes, long long *out)
+{
+    if (!s || steps < 1 || (max_classes > 0 && !out)) return SIM_EINVAL;
+    int rc = finalize(s);
+    if (rc) return rc;
+    if (s->nscenes == 0) return 0;
+    CK(cudaSetDevice(s->opt.device), "cudaSetDevice");
+    CK(cudaStreamSynchronize(s->stream), "stream synchronize");
+    // snapshot of everything a step writes
+    struct Arr { void *p; size_t bytes; };
+    const size_t nsub = s->sdesc.size();
+    std::vector<Arr> arrs = {
+        {s->d_bodies, sizeof(double) * SUBADMM_BODY * (size_t)s->nbodies},
+        {s->d_nodes, sizeof(double) * SUBADMM_NODE * (size_t)s->nnodes},
+        {s->d_vhat, sizeof(double) * (size_t)s->dof},
+        {s->d_lam, sizeof(double) * (size_t)s->nrows},
+        {s->d_z, sizeof(double) * (size_t)s->nsr},
+        {s->d_beta, sizeof(double) * nsub},
+        {s->d_res, sizeof(double) * 6 * (size_t)s->nscenes},
+        {s->d_stats, sizeof(long long) * 4 * (size_t)s->nscenes},
+        {s->d_subflag, sizeof(int) * nsub},
+        {s->d_phase, s->d_phase ? sizeof(long long) * 8 * (size_t)s->nscenes : 0}};
+    size_t total = 0;
+    for (auto &a : arrs) total += (a.p ? (a.bytes + 255) / 256 * 256 : 0);
+    unsigned char *snap = nullptr;
+    if (total) {
+        cudaError_t e = cudaMalloc((void **)&snap, total);
+        if (e != cudaSuccess) return fail(s, SIM_ENOMEM, "cudaMalloc autotune snapshot");
+    }
+    auto copy_all = [&](bool save) -> cudaError_t {
+        size_t off = 0;
+        for (auto &a : arrs) {
+            if (!a.p || !a.bytes) continue;
+            cudaError_t e = save ? cudaMemcpyAsync(snap + off, a.p, a.bytes, cudaMemcpyDeviceToDevice, s->stream)
+                                 : cudaMemcpyAsync(a.p, snap + off, a.bytes, cudaMemcpyDeviceToDevice, s->stream);
+            if (e != cudaSuccess) return e;
+            off += (a.bytes + 255) / 256 * 256;
+        }
+        return cudaSuccess;
+    };
+    StepParams P = step_params(s, steps);
+    for (int cached = 0; cached < 2; ++cached)
+        for (int split = 1; split <= 4; split *= 2)
+            CK(cudaFuncSetAttribute(kernel_for(s->opt.precision == SIM_MIXED, cached, split),
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, s->smem_full),
+               "shared memory attribute");
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    std::vector<double> best_ns(s->classes.size(), 0.0);
+    cudaError_t err = copy_all(true);
+    for (size_t k = 0; k < s->classes.size() && err == cudaSuccess; ++k) {
+        LaunchClass &c = s->classes[k];
+        P.scene_ids = s->d_scene_ids + c.ids_off;
+        P.nscenes = (int)c.scenes.size();
+        double best = 1e300;
+        bool bc = c.cached;
+        int bs = c.split;
+        for (int cached = 0; cached < 2 && err == cudaSuccess; ++cached) {
+            for (int split = 1; split <= 4 && err == cudaSuccess; split *= 2) {
+                if (cached) {
+                    bool ok = true;
+                    for (int sc : c.scenes) ok = ok && cache_fits(s, sc, split);
+                    if (!ok) continue;
+                }
+                KernFn kf = kernel_for(s->opt.precision == SIM_MIXED, cached, split);
+                float ms = 0.0f;
+                for (int rep = 0; rep < 2 && err == cudaSuccess; ++rep) {   // warm, then timed
+                    err = copy_all(false);
+                    if (err != cudaSuccess) break;
+                    cudaEventRecord(e0, s->stream);
+                    kf<<<P.nscenes, SUBADMM_THREADS, c.max_smem, s->stream>>>(P);
+                    err = cudaGetLastError();
+                    cudaEventRecord(e1, s->stream);
+                    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+                    if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+                }
+                if (err == cudaSuccess && ms < best) { best = ms; bc = cached; bs = split; }
+            }
+        }
+        c.cached = bc;
+        c.split = bs;
+        best_ns[k] = best * 1e6 / steps;
+    }
+    if (err == cudaSuccess) err = copy_all(false);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(s->stream);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(snap);
+    if (err != cudaSuccess) return cuda_fail(s, err, "autotune");
+    if (s->graph) {            // the captured launches used the old variants
+        cudaGraphExecDestroy(s->graph);
+        s->graph = nullptr;
+        s->graph_steps = 0;
+    }
+    class_rows(s, max_classes, out, &best_ns);
+    return (int)s->classes.size();
 }
 
 int sim_sync(sim_t s)
@@ -1078,6 +1406,13 @@ int sim_phase_trace(sim_t s, int enable, long long out[8])
             for (int sc = 0; sc < s->nscenes; ++sc)
                 for (int k = 0; k < 8; ++k) out[k] += v[(size_t)8 * sc + k];
         }
+    }
+    // a captured graph holds the tracer pointer of its capture: capture again
+    if (s->graph) {
+        CK(cudaStreamSynchronize(s->stream), "stream synchronize");
+        cudaGraphExecDestroy(s->graph);
+        s->graph = nullptr;
+        s->graph_steps = 0;
     }
     if (enable && !s->d_phase) {
         cudaError_t e = cudaMalloc((void **)&s->d_phase, bytes);

@@ -31,7 +31,8 @@ SIM_GET_VHAT, SIM_GET_LAMBDA, SIM_GET_BODIES, SIM_GET_BETA, SIM_GET_Z, SIM_GET_N
 EXPORTS = ("sim_default_options", "sim_create", "sim_destroy", "sim_add_subsystem",
            "sim_add_interface", "sim_set_generic", "sim_step", "sim_residuals", "sim_get",
            "sim_read_state", "sim_read_state_noalloc", "sim_write_state", "sim_sizes",
-           "sim_iteration_stats", "sim_scene_info",
+           "sim_iteration_stats", "sim_scene_info", "sim_use_graph", "sim_launch_classes",
+           "sim_autotune",
            "sim_phase_trace", "sim_sync", "sim_last_error")
 
 
@@ -90,6 +91,9 @@ def load(build_if_missing: bool = True):
             "sim_sizes": (C.c_int, [VP, PL]),
             "sim_iteration_stats": (C.c_int, [VP, PL, PL]),
             "sim_scene_info": (C.c_int, [VP, C.c_int, PL]),
+            "sim_use_graph": (C.c_int, [VP, C.c_int]),
+            "sim_launch_classes": (C.c_int, [VP, C.c_int, PL]),
+            "sim_autotune": (C.c_int, [VP, C.c_int, C.c_int, PL]),
             "sim_phase_trace": (C.c_int, [VP, C.c_int, PL]),
             "sim_sync": (C.c_int, [VP]),
             "sim_last_error": (C.c_char_p, [VP]),
@@ -192,6 +196,27 @@ def sim_read_state_noalloc(h, dst_ptr: int) -> None:
 
 def sim_write_state(h, src_ptr: int) -> None:
     _check(h, load().sim_write_state(h, VP(src_ptr)))
+
+
+def _class_rows(out, n: int) -> list:
+    keys = ("scenes", "cached", "split", "smem_bytes", "ns_per_step")
+    return [dict(zip(keys, (int(v) for v in out[5 * k:5 * k + 5]))) for k in range(n)]
+
+
+def sim_launch_classes(h, max_classes: int = 64) -> list:
+    out = (C.c_longlong * (5 * max_classes))()
+    n = _check(h, load().sim_launch_classes(h, max_classes, out))
+    return _class_rows(out, min(n, max_classes))
+
+
+def sim_autotune(h, steps: int = 5, max_classes: int = 64) -> list:
+    out = (C.c_longlong * (5 * max_classes))()
+    n = _check(h, load().sim_autotune(h, steps, max_classes, out))
+    return _class_rows(out, min(n, max_classes))
+
+
+def sim_use_graph(h, enable: bool) -> None:
+    _check(h, load().sim_use_graph(h, 1 if enable else 0))
 
 
 def sim_sizes(h) -> dict:
@@ -349,6 +374,15 @@ class Simulation:
 
     def step(self, n: int = 1):
         sim_step(self.h, n)
+
+    def launch_classes(self) -> list:
+        return sim_launch_classes(self.h)
+
+    def autotune(self, steps: int = 5) -> list:
+        return sim_autotune(self.h, steps)
+
+    def use_graph(self, enable: bool = True) -> None:
+        sim_use_graph(self.h, enable)
 
     def sync(self):
         sim_sync(self.h)

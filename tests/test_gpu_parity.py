@@ -308,6 +308,8 @@ def test_batched_uneven_scenes_fp64_fixed_iterations(sa):
     orcs = [oracle.OracleScene(sc, p.options) for sc in p.scenes]
     sim = sa.Simulation(p)
     assert any(sa.sim_scene_info(sim.h, k)["global_workspace"] for k in range(6))
+    classes = sim.launch_classes()
+    assert sum(c["scenes"] for c in classes) == 6
     for _ in range(2):
         for o in orcs:
             o.step()
@@ -344,6 +346,77 @@ def test_batched_uneven_scenes_mixed_converged(sa, capsys, tol):
     for k in range(8):
         assert errs[k] <= 3 * spreads[k] + 0.1 * max(spreads), (k, errs[k], spreads[k])
     assert max(errs) <= 2 * max(spreads)
+
+
+def _batch_state(sim, n):
+    return (np.concatenate([sim.scene_vhat(k) for k in range(n)]),
+            np.concatenate([sim.scene_lam(k) for k in range(n)]),
+            np.concatenate([sim.scene_nodes(k).ravel() for k in range(n)]),
+            np.concatenate([sim.scene_bodies(k).ravel() for k in range(n)]))
+
+
+def test_scenes_of_different_sizes_run_in_concurrent_launch_classes(sa):
+    """Small scenes (the register-cached kernel) and large ones (the generic kernel) of one
+    batch are separate launches on forked streams; results match the oracle per scene."""
+    small = sg.robots(11, n_robots=3).scenes
+    large = sg.batched(5, n_scenes=3, tol_primal=-1, max_iters=30).scenes
+    p = sg.Problem(small + large, sg.Options(h=1e-3, warm="prev", tol_primal=-1, max_iters=30,
+                                             beta_mode="trace"))
+    orcs = [oracle.OracleScene(sc, p.options) for sc in p.scenes]
+    sim = sa.Simulation(p)
+    classes = sim.launch_classes()
+    assert len(classes) >= 2 and sum(c["scenes"] for c in classes) == 6
+    assert any(c["cached"] for c in classes) and not all(c["cached"] for c in classes)
+    for _ in range(2):
+        for o in orcs:
+            o.step()
+        sim.step(1)
+        _compare(sim, orcs, p, what=("vhat", "lam"))
+
+
+def test_graph_replay_equals_direct_launches(sa):
+    p = sg.batched(6, n_scenes=5, max_iters=200)
+    a = sa.Simulation(p, precision=sa.SIM_MIXED)
+    b = sa.Simulation(p, precision=sa.SIM_MIXED)
+    b.use_graph(True)
+    for n in (2, 2, 3):
+        a.step(n)
+        b.step(n)
+    for x, y in zip(_batch_state(a, 5), _batch_state(b, 5)):
+        assert np.array_equal(x, y)
+    b.use_graph(False)
+    b.step(1)
+    a.step(1)
+    for x, y in zip(_batch_state(a, 5), _batch_state(b, 5)):
+        assert np.array_equal(x, y)
+
+
+def test_autotune_leaves_no_trace_and_keeps_parity(sa):
+    """Tuning times kernel variants on a snapshot and restores it: the state after tuning is
+    the state before, bit for bit; stepping on with the tuned variants matches the oracle."""
+    import torch
+    p = sg.batched(7, n_scenes=6, tol_primal=-1, max_iters=25)
+    orcs = [oracle.OracleScene(sc, p.options) for sc in p.scenes]
+    sim = sa.Simulation(p)
+    for o in orcs:
+        o.step()
+    sim.step(1)
+    sz = sim.sizes()
+    before = torch.empty(13 * sz["bodies"] + 6 * sz["nodes"], dtype=torch.float64).pin_memory()
+    after = torch.empty_like(before).pin_memory()
+    sa.sim_read_state(sim.h, before.data_ptr())
+    lam0 = np.concatenate([sim.scene_lam(k) for k in range(6)])
+    rows = sim.autotune(steps=2)
+    assert sum(r["scenes"] for r in rows) == 6 and all(r["ns_per_step"] > 0 for r in rows)
+    sa.sim_read_state(sim.h, after.data_ptr())
+    assert np.array_equal(before.numpy(), after.numpy())
+    assert np.array_equal(lam0, np.concatenate([sim.scene_lam(k) for k in range(6)]))
+    assert sim.iteration_stats()["scene_steps"] == 6          # only the real step counted
+    for _ in range(2):
+        for o in orcs:
+            o.step()
+        sim.step(1)
+        _compare(sim, orcs, p, what=("vhat", "lam"))
 
 
 def test_not_spd_is_reported_not_faulted(sa):
