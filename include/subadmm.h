@@ -43,6 +43,8 @@ extern "C" {
 #define SIM_ENOTSPD (-3)      /* K_i = A_i + beta_i J^T J had a pivot <= 0 (not SPD)        */
 #define SIM_ENAN (-4)         /* a residual became NaN or infinite                          */
 #define SIM_ECUDA (-5)        /* a CUDA runtime call failed                                 */
+#define SIM_ETIMEOUT (-6)     /* a grid-wide barrier (one scene over the whole GPU) waited
+                                 over 20 s: the kernel ended early, results are undefined  */
 
 /* subsystem kinds (Sec. III-A: rigid bodies, or any block given by A_i, b_i) */
 #define SIM_SUB_GENERIC 0     /* A_i (n x n, SPD) and b_i given directly                    */
@@ -163,19 +165,36 @@ int sim_step(sim_t s, int n_steps);
  * generic scenes that fit, so that two blocks share an SM).  sim_step enqueues one launch per
  * class; classes after the first run on streams of their own forked from the simulation's
  * stream and joined back to it, so the classes overlap.
+ * A scene with at least 8192 side-rows runs alone over the whole GPU instead (the grid
+ * kernel: a cooperative launch whose blocks share the scene's rows, items and subsystems,
+ * with two bounded grid barriers per iteration); grid classes run before the others, one
+ * scene at a time, and are never captured into a graph.
  * sim_launch_classes lays the simulation out if needed and writes, for each class k <
- * max_classes, five counts at out[5k]: scenes, 1 if the register-cached kernel runs it, lanes
- * per side-row (1, 2 or 4), dynamic shared memory per block in bytes, 0.  Returns the number
+ * max_classes, five counts at out[5k]: scenes, kernel (0 generic, 1 register-cached, 2
+ * grid), lanes per side-row (1, 2 or 4; 8, 16 or 32 for the grid kernel), dynamic shared
+ * memory per block in bytes, 0.  Returns the number
  * of classes, or a negative SIM_E* code.
  * sim_autotune times, for each class on its own, every kernel variant that is valid for all
  * its scenes (generic with 1, 2 or 4 lanes per side-row, register-cached where the scenes
- * fit) over `steps` steps from the current state, keeps the fastest, and restores the state
+ * fit; the grid kernel with 8, 16 or 32) over `steps` steps from the current state, keeps the fastest, and restores the state
  * (bodies, nodes, warm-start duals, outputs, counters) so that tuning leaves no trace.  It
  * waits for the stream, allocates a temporary snapshot, and writes the same rows as
  * sim_launch_classes with out[5k + 4] the chosen variant's time per step in nanoseconds.
  * Returns the number of classes or a negative SIM_E* code. */
 int sim_launch_classes(sim_t s, int max_classes, long long *out);
 int sim_autotune(sim_t s, int steps, int max_classes, long long *out);
+
+/* Scenes with at least `side_rows` side-rows run on the grid kernel (default 8192).  Must be
+ * called before the first sim_step (SIM_EINVAL after it, or for side_rows < 1). */
+int sim_grid_threshold(sim_t s, int side_rows);
+
+/* Self-test of the grid barrier's time limit (failure detection without a fault): a
+ * cooperative launch of `blocks` blocks (all resident, else SIM_EINVAL) in which every block
+ * waits once at a barrier that needs `expected` arrivals, for at most limit_s seconds
+ * (0 < limit_s <= 10).  With expected > blocks nothing completes the barrier: every wait runs
+ * out, raises the error flag and returns.  Writes out[0] the error flag (1 if a wait ran
+ * out), out[1] the blocks that left the barrier.  Synchronises the device. */
+int sim_probe_barrier(int device, int blocks, int expected, double limit_s, int out[2]);
 
 /* CUDA-graph replay of sim_step (off by default).  When enabled, the first sim_step with a
  * given n_steps captures its launches (one per launch class of scenes, forked across streams
@@ -230,7 +249,8 @@ int sim_sizes(sim_t s, long long out[9]);
  * out[0] 0 if every per-subsystem array fits in the block's shared memory; 1 if the setup
  * arrays (J, K, the factor, W: O(n^2) per subsystem) live in the simulation's global
  * workspace while the iteration arrays (D, c: O(m^2)) and the per-row arrays stay in shared
- * memory; 2 if the iteration arrays are in the workspace too.  out[1] shared-memory bytes of
+ * memory; 2 if the iteration arrays are in the workspace too; 3 if the scene runs on the
+ * grid kernel (everything in the workspace).  out[1] shared-memory bytes of
  * the scene; out[2] its subsystems; out[3] bytes of the global workspace of the whole
  * simulation. */
 int sim_scene_info(sim_t s, int scene, long long out[4]);

@@ -5,7 +5,7 @@
 #define SUBADMM_MAXS 8          // most sides one constraint may have (|S_j|)
 #define SUBADMM_THREADS 256     // threads of one scene's block
 #define SUBADMM_WARPS (SUBADMM_THREADS / 32)
-#define SUBADMM_MAXN 1024       // largest subsystem DOF
+#define SUBADMM_MAXN 2048       // largest subsystem DOF
 #define SUBADMM_MAXM 2048       // largest side-row count of one subsystem
 #define SUBADMM_PARAMS 23       // doubles of a rigid-model constraint's parameters
 #define SUBADMM_BODY 17         // doubles of a body record
@@ -22,7 +22,7 @@ enum { KIND_GENERIC = 0, KIND_RIGID = 1, KIND_LINEAR = 2 };
 enum { PHASE_ASSEMBLE = 0, PHASE_FACTOR = 1, PHASE_VSTEP = 2, PHASE_ZSTEP = 3, PHASE_EXIT = 4,
        PHASE_RECOVER = 5, PHASE_ITERS = 6, PHASE_STEPS = 7 };
 // per-scene status words
-enum { ST_OK = 0, ST_NOTSPD = -3, ST_NAN = -4 };
+enum { ST_OK = 0, ST_NOTSPD = -3, ST_NAN = -4, ST_TIMEOUT = -6 };
 
 // One scene: a set of subsystems and constraints solved by one thread block.  The on-chip
 // working set lives in dynamic shared memory: a double region (factors), a region of the
@@ -32,6 +32,7 @@ struct SceneDesc {
     int con0, ncon;        // global constraint range
     int nsr, nrow;         // side-rows and rows of the scene
     int nitem, nlist;      // projection items (a row, or a whole contact) and their side lists
+    int max_sides;         // most sides of one constraint of the scene
     int item_g0, list_g0;  // global offsets of the scene's item / list tables
     int nasm, asm_g0;      // assembly slots (constraint indices grouped by kind, -1 = idle)
     int sr_g0, row_g0;     // global offset of the scene's side-rows / rows (z, lambda state)
@@ -49,6 +50,9 @@ struct SceneDesc {
     // they follow the others in the workspace.
     int sub_global, hot_global;
     long long g_base, g_tbase;
+    // grid kernel: the scene arrays and tables (shared memory in the block kernel) live in
+    // the workspace at byte g_scene (-1: block kernel)
+    long long g_scene;
 };
 
 struct SubDesc {
@@ -92,6 +96,19 @@ struct Item {
     int type, ns, row, lo;
 };
 
+// Scratch of the grid kernel (one scene over the whole grid) in global memory, zeroed
+// before every launch: the barrier, the scene status, and the reduction slots.
+struct GridScratch {
+    unsigned count, gen;           // grid barrier
+    int err;                       // a barrier wait timed out
+    int status;                    // ST_* of the step
+    unsigned long long umax[3];    // per iteration: max(|x - z|, |dz|) bits (rotating slots)
+    double theta[3];               // per iteration: theta (rotating slots)
+    double tsum;                   // exit residuals: theta, max |x - z|, max beta |dz| (bits)
+    unsigned long long pmax, dmax;
+    unsigned long long chk;        // mixed form: FP64 max |J v - z| (bits)
+};
+
 struct StepParams {
     const SceneDesc *scenes;
     const int *scene_ids;  // the scenes of this launch (indices into scenes)
@@ -113,6 +130,7 @@ struct StepParams {
     double *res;           // 6 per scene
     long long *stats;      // 4 per scene: sum iters, max iters, not converged, steps
     long long *phase;      // 8 per scene (or null): SM clock cycles per phase, see PHASE_*
+    GridScratch *grid;     // grid kernel scratch
     int nscenes;           // scenes of this launch
     int n_steps;
     double h, g0, g1, g2, gamma, rho, tol, theta_th;

@@ -186,14 +186,80 @@ __device__ View<T> scene_view(const StepParams &P, const SceneDesc &S, unsigned 
     return V;
 }
 
-template <typename T>
-__device__ void scene_tables(const StepParams &P, const SceneDesc &S, const View<T> &V)
+// Work distribution of one scene's step: the threads of a block (block kernel: one block
+// per scene) or of the whole grid (grid kernel: one scene over every SM).  Loops over
+// subsystems take a warp each, loops over rows and constraints a thread each; sync() is a
+// barrier over all of them.
+struct BlockDist {
+    int tid, nthreads, warp, nwarps;
+    __device__ __forceinline__ BlockDist()
+        : tid(threadIdx.x), nthreads(blockDim.x), warp(threadIdx.x >> 5), nwarps(blockDim.x >> 5) {}
+    __device__ __forceinline__ void sync() const { __syncthreads(); }
+};
+
+__device__ __forceinline__ unsigned long long global_ns()
 {
-    for (int t = threadIdx.x; t < S.nsr; t += blockDim.x) {
-        V.row[t] = 0; V.sub[t] = 0; V.drow[t] = 0; V.coff[t] = 0; V.wbase[t] = 0; V.mlen[t] = 0;
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Barrier over the `expected` blocks of a cooperative launch.  Thread 0 of each block
+// arrives on a counter; the last arrival resets it and advances the generation the others
+// wait on.  A wait longer than limit_ns, or an error raised by another block, sets / sees
+// the error flag and returns at once, here and at every later barrier, so the grid always
+// runs to its end.
+__device__ __noinline__ void grid_barrier(unsigned *count, unsigned *gen, int *err,
+                                          unsigned expected, unsigned long long limit_ns)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *vgen = gen;
+        volatile int *verr = err;
+        if (!*verr) {
+            const unsigned my = *vgen;
+            __threadfence();
+            if (atomicAdd(count, 1u) == expected - 1) {
+                atomicExch(count, 0u);
+                __threadfence();
+                atomicAdd(gen, 1u);
+            } else {
+                const unsigned long long t0 = global_ns();
+                while (*vgen == my) {
+                    if (*verr) break;
+                    if (global_ns() - t0 > limit_ns) { atomicExch(err, 1); break; }
+                    __nanosleep(64);
+                }
+            }
+            __threadfence();
+        }
     }
     __syncthreads();
-    for (int j = threadIdx.x; j < S.ncon; j += blockDim.x) {
+}
+
+struct GridDist {
+    int tid, nthreads, warp, nwarps;
+    unsigned *count, *gen;
+    int *err;
+    __device__ __forceinline__ GridDist(unsigned *c, unsigned *g, int *e)
+        : tid(blockIdx.x * blockDim.x + threadIdx.x), nthreads(gridDim.x * blockDim.x),
+          warp((blockIdx.x * blockDim.x + threadIdx.x) >> 5), nwarps((gridDim.x * blockDim.x) >> 5),
+          count(c), gen(g), err(e) {}
+    __device__ __forceinline__ void sync() const
+    {
+        grid_barrier(count, gen, err, gridDim.x, 20000000000ull);
+    }
+};
+
+template <typename T, typename Dist>
+__device__ void scene_tables(const StepParams &P, const SceneDesc &S, const View<T> &V,
+                             const Dist &d)
+{
+    for (int t = d.tid; t < S.nsr; t += d.nthreads) {
+        V.row[t] = 0; V.sub[t] = 0; V.drow[t] = 0; V.coff[t] = 0; V.wbase[t] = 0; V.mlen[t] = 0;
+    }
+    d.sync();
+    for (int j = d.tid; j < S.ncon; j += d.nthreads) {
         const ConDesc &c = P.cons[S.con0 + j];
         for (int s = 0; s < c.ns; ++s) {
             const SubDesc &u = P.subs[S.sub0 + c.sub[s]];
@@ -209,8 +275,8 @@ __device__ void scene_tables(const StepParams &P, const SceneDesc &S, const View
             }
         }
     }
-    for (int i = threadIdx.x; i < S.nitem; i += blockDim.x) V.item[i] = P.items[S.item_g0 + i];
-    for (int i = threadIdx.x; i < S.nlist; i += blockDim.x) V.list[i] = P.lists[S.list_g0 + i];
+    for (int i = d.tid; i < S.nitem; i += d.nthreads) V.item[i] = P.items[S.item_g0 + i];
+    for (int i = d.tid; i < S.nlist; i += d.nthreads) V.list[i] = P.lists[S.list_g0 + i];
 }
 
 // k, alpha, mu of a constraint (model kinds derive them from their drive gains)
@@ -404,15 +470,15 @@ __device__ void form_c(const F *W, int n, int m, int ldw, const int *jlo, F *cc)
 }
 
 // assemble .. factor .. map, and the per-step constants of the z-step
-template <typename T>
+template <typename T, typename Dist>
 __device__ void scene_setup(const StepParams &P, const SceneDesc &S, const View<T> &V,
-                            int *s_status, PhaseClock &pc, int step)
+                            int *s_status, PhaseClock &pc, int step, const Dist &d)
 {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int lane = threadIdx.x & 31;
     constexpr bool MIXED = sizeof(T) == 4;
     double *db = V.db, *sdb = V.sdb;
     T *tb = V.tb, *stb = V.stb, *htb = V.htb;
-    for (int i = warp; i < S.nsub; i += SUBADMM_WARPS) {
+    for (int i = d.warp; i < S.nsub; i += d.nwarps) {
         const SubDesc &u = P.subs[S.sub0 + i];
         const SubEnv e = sub_env(P, u);
         const bool keep = factor_kept(P, S, u, S.sub0 + i, step);
@@ -454,9 +520,9 @@ __device__ void scene_setup(const StepParams &P, const SceneDesc &S, const View<
                 sdb[u.od_b + p] = linear_b(p, mass, f, ux, Kval, rowp, col, nodes, P.h, gv);
         }
     }
-    __syncthreads();
+    d.sync();
     // rigid bodies: diagonal A = (2/h) M and b (lane per body)
-    for (int i = warp; i < S.nsub; i += SUBADMM_WARPS) {
+    for (int i = d.warp; i < S.nsub; i += d.nwarps) {
         const SubDesc &u = P.subs[S.sub0 + i];
         if (u.kind != KIND_RIGID) continue;
         for (int k = lane; k < u.nb; k += 32) {
@@ -474,7 +540,7 @@ __device__ void scene_setup(const StepParams &P, const SceneDesc &S, const View<
     // constraint rows into J (FP64) and e; constraints in the host's assembly order, which
     // groups kinds by warp so a warp runs one kind's code path
     T *E = tb + S.ot_e;
-    for (int a = tid; a < S.nasm; a += blockDim.x) {
+    for (int a = d.tid; a < S.nasm; a += d.nthreads) {
         const int j = P.asm_order[S.asm_g0 + a];
         if (j < 0) continue;
         const ConDesc &c = P.cons[S.con0 + j];
@@ -513,13 +579,13 @@ __device__ void scene_setup(const StepParams &P, const SceneDesc &S, const View<
             }
         }
     }
-    __syncthreads();
+    d.sync();
     pc.mark(PHASE_ASSEMBLE);
     // per subsystem (one warp each): beta, K = A + beta J^T J and its Cholesky factor, then
     // the map W = L^-1 [J^T b], D = W^T W, c.  The FP64 form and the stiff blocks of the mixed
     // form factorise K in FP64 (rounded into the T copy); the other mixed blocks factorise in
     // FP32, keeping the FP64 A, b and J for the recovery and refinement of v-hat.
-    for (int i = warp; i < S.nsub; i += SUBADMM_WARPS) {
+    for (int i = d.warp; i < S.nsub; i += d.nwarps) {
         const SubDesc &u = P.subs[S.sub0 + i];
         const int gsub = S.sub0 + i;
         const int n = u.n, m = u.m, mp = u.mpad, ldw = m + 1;
@@ -620,14 +686,14 @@ __device__ void scene_setup(const StepParams &P, const SceneDesc &S, const View<
         form_c<T>(W, n, m, ldw, e.jlo, cc);
         __syncwarp();
     }
-    __syncthreads();
+    d.sync();
     pc.mark(PHASE_FACTOR);
     // per-step z-step constants: 1/s, soft gain k/(1 + s alpha k), alpha, mu (per row);
     // beta and 1/beta per side-row
     T *INVS = tb + S.ot_invs, *KF = tb + S.ot_kf, *AL = tb + S.ot_al, *MU = tb + S.ot_mu;
     T *INVB = tb + S.ot_invb, *BT = tb + S.ot_b;
     const double *BETA = db + S.od_beta;
-    for (int j = tid; j < S.ncon; j += blockDim.x) {
+    for (int j = d.tid; j < S.ncon; j += d.nthreads) {
         const ConDesc &c = P.cons[S.con0 + j];
         double s = 0.0;
         for (int q = 0; q < c.ns; ++q) s += 1.0 / BETA[c.sub[q]];
@@ -648,7 +714,22 @@ __device__ void scene_setup(const StepParams &P, const SceneDesc &S, const View<
             }
         }
     }
-    __syncthreads();
+    d.sync();
+}
+
+// out += J^T w (FP64) over the column span of each J row, a row at a time (lanes across the
+// span), in row order: deterministic, and O(sum of spans) instead of O(m n)
+template <typename W>
+__device__ __forceinline__ void add_jt(double *out, const double *J, int n, int m,
+                                       const SubEnv &e, const W *w)
+{
+    const int lane = threadIdx.x & 31;
+    for (int r = 0; r < m; ++r) {
+        const double wr = (double)w[r];
+        const double *Jr = J + (size_t)r * n;
+        for (int p = e.jlo[r] + lane; p < e.jhi[r]; p += 32) out[p] += Jr[p] * wr;
+        __syncwarp();
+    }
 }
 
 // Triangular solves with the T factor (1/L_pp on its diagonal), in place on s (warp),
@@ -678,12 +759,13 @@ __device__ __forceinline__ void warp_chol_solve(const T *LT, T *s, int n, const 
 // solves.  With an FP32 factor: a solve, then one step of iterative refinement with the
 // residual b + J^T w - K v formed in FP64 from A (kept in od_L) and J:
 // K v = A v + beta J^T (J v).
-template <typename T>
-__device__ void recover_v(const StepParams &P, const SceneDesc &S, const View<T> &V, const T *w)
+template <typename T, typename Dist>
+__device__ void recover_v(const StepParams &P, const SceneDesc &S, const View<T> &V, const T *w,
+                          const Dist &d)
 {
     constexpr bool MIXED = sizeof(T) == 4;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int i = warp; i < S.nsub; i += SUBADMM_WARPS) {
+    const int lane = threadIdx.x & 31;
+    for (int i = d.warp; i < S.nsub; i += d.nwarps) {
         const SubDesc &u = P.subs[S.sub0 + i];
         const int n = u.n, m = u.m;
         const SubEnv e = sub_env(P, u);
@@ -693,12 +775,9 @@ __device__ void recover_v(const StepParams &P, const SceneDesc &S, const View<T>
         double *v = V.sdb + u.od_v;
         const T *wi = w + u.sr0;
         if (!MIXED || V.db[S.od_flag + i] != 0.0) {
-            for (int p = lane; p < n; p += 32) {
-                double acc = b[p];
-                for (int r = 0; r < m; ++r) acc += J[r * n + p] * (double)wi[r];
-                v[p] = acc;
-            }
+            for (int p = lane; p < n; p += 32) v[p] = b[p];
             __syncwarp();
+            add_jt(v, J, n, m, e, wi);
             for (int p = 0; p < n; ++p) {          // L y = rhs (column-oriented)
                 const double yp = v[p] * idg[p];
                 __syncwarp();
@@ -720,12 +799,10 @@ __device__ void recover_v(const StepParams &P, const SceneDesc &S, const View<T>
         double *rhs = idg;                          // (unused by the mixed factor)
         double *t = V.sdb + u.od_t;
         const double beta = V.db[S.od_beta + i];
-        for (int p = lane; p < n; p += 32) {
-            double acc = b[p];
-            for (int r = 0; r < m; ++r) acc += J[r * n + p] * (double)wi[r];
-            rhs[p] = acc;
-            s[p] = (T)acc;
-        }
+        for (int p = lane; p < n; p += 32) rhs[p] = b[p];
+        __syncwarp();
+        add_jt(rhs, J, n, m, e, wi);
+        for (int p = lane; p < n; p += 32) s[p] = (T)rhs[p];
         __syncwarp();
         warp_chol_solve<T>(LT, s, n, e);
         for (int p = lane; p < n; p += 32) v[p] = (double)s[p];
@@ -738,12 +815,14 @@ __device__ void recover_v(const StepParams &P, const SceneDesc &S, const View<T>
             t[r] = acc;
         }
         __syncwarp();
+        for (int r = lane; r < m; r += 32) t[r] *= -beta;
+        __syncwarp();
+        // s = rhs - A v - beta J^T t, with J^T (-beta t) added into the FP64 rhs copy
+        add_jt(rhs, J, n, m, e, t);
         for (int p = lane; p < n; p += 32) {
             double acc = rhs[p];
             for (int q = e.env[p]; q <= e.lastr[p]; ++q) acc -= Lf[p * n + q] * v[q];     // A v
-            double jt = 0.0;
-            for (int r = 0; r < m; ++r) jt += J[r * n + p] * t[r];
-            s[p] = (T)(acc - beta * jt);
+            s[p] = (T)acc;
         }
         __syncwarp();
         warp_chol_solve<T>(LT, s, n, e);
@@ -751,6 +830,153 @@ __device__ void recover_v(const StepParams &P, const SceneDesc &S, const View<T>
         __syncwarp();
     }
 }
+
+// One z-step item held in a thread's registers for a whole step (items with at most two
+// sides): its type, row, side-rows and the step's constants.  KEEP_Z: the z of its
+// side-rows (the item is their only writer) and the previous z stay in registers until
+// published; otherwise they are read and written in memory each iteration (fewer
+// registers).
+template <typename T, bool KEEP_Z = true>
+struct RegItem {
+    using U = typename VecOf<T>::U;
+    static constexpr int NZ = KEEP_Z ? 6 : 1;
+    bool valid = false;
+    int type = 0, row = 0, t0 = 0, t1 = -1, nr = 1;
+    T ib0 = (T)0, ib1 = (T)0, e0 = (T)0, e1 = (T)0, e2 = (T)0;
+    T is = (T)0, kf = (T)0, al = (T)0, mu = (T)0;
+    T zr[NZ] = {(T)0};
+    T zq[NZ] = {(T)0};
+
+    __device__ __forceinline__ void load(const Item *items, const int *list, int i, const T *INVB,
+                                         const T *E, const T *INVS, const T *KF, const T *AL,
+                                         const T *MU, const T *Z)
+    {
+        const Item it = items[i];
+        if (it.type < 0) return;
+        valid = true;
+        type = it.type;
+        row = it.row;
+        t0 = list[it.lo];
+        t1 = it.ns > 1 ? list[it.lo + 1] : -1;
+        nr = type == TYPE_CONTACT ? 3 : 1;
+        ib0 = INVB[t0];
+        if (t1 >= 0) ib1 = INVB[t1];
+        e0 = E[row];
+        if (nr == 3) { e1 = E[row + 1]; e2 = E[row + 2]; }
+        is = INVS[row]; kf = KF[row]; al = AL[row]; mu = MU[row];
+        if constexpr (KEEP_Z) {
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                if (r < nr) {
+                    zr[r] = Z[t0 + r];
+                    if (t1 >= 0) zr[3 + r] = Z[t1 + r];
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < 6; ++r) zq[r] = zr[r];
+        }
+    }
+
+    // z of side-row t (k: its slot), replaced by zn; returns the old z
+    __device__ __forceinline__ T swap_z(T *Z, T *ZO, int t, int k, T zn)
+    {
+        if constexpr (KEEP_Z) {
+            const T zo = zr[k];
+            zq[k] = zo;
+            zr[k] = zn;
+            return zo;
+        } else {
+            const T zo = Z[t];
+            ZO[t] = zo;
+            Z[t] = zn;
+            return zo;
+        }
+    }
+
+    // the item's projection (Sec. III-C): lambda, z, w of the next v-step; returns the bits
+    // of max(|x - z|, |dz|) over its side-rows
+    __device__ __forceinline__ U project(const T *Y, const T *X, T *LAM, T *wn, T *Z, T *ZO)
+    {
+        U mloc = 0;
+        if (!valid) return mloc;
+        if (type == TYPE_CONTACT) {
+            T ya[3], yb[3] = {(T)0, (T)0, (T)0};
+#pragma unroll
+            for (int r = 0; r < 3; ++r) ya[r] = Y[t0 + r];
+            if (t1 >= 0) {
+#pragma unroll
+                for (int r = 0; r < 3; ++r) yb[r] = Y[t1 + r];
+            }
+            const T ln = -(ya[0] * ib0 + yb[0] * ib1 + e0) * is;
+            const T l1 = -(ya[1] * ib0 + yb[1] * ib1 + e1) * is;
+            const T l2 = -(ya[2] * ib0 + yb[2] * ib1 + e2) * is;
+            T lv[3];
+            if (ln <= (T)0) {
+                lv[0] = lv[1] = lv[2] = (T)0;
+            } else {
+                const T t2 = l1 * l1 + l2 * l2;
+                const T lim = mu * ln;
+                lv[0] = ln;
+                if (t2 > lim * lim) { const T f = lim * rsq(t2); lv[1] = l1 * f; lv[2] = l2 * f; }
+                else { lv[1] = l1; lv[2] = l2; }
+            }
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                LAM[row + r] = lv[r];
+                const T zn = (ya[r] + lv[r]) * ib0;
+                const T zo = swap_z(Z, ZO, t0 + r, r, zn);
+                mloc = umax(mloc, umax(rbits(fabs(X[t0 + r] - zn)), rbits(fabs(zn - zo))));
+                wn[t0 + r] = ya[r] + (T)2 * lv[r];
+            }
+            if (t1 >= 0) {
+#pragma unroll
+                for (int r = 0; r < 3; ++r) {
+                    const T zn = (yb[r] + lv[r]) * ib1;
+                    const T zo = swap_z(Z, ZO, t1 + r, 3 + r, zn);
+                    mloc = umax(mloc, umax(rbits(fabs(X[t1 + r] - zn)), rbits(fabs(zn - zo))));
+                    wn[t1 + r] = yb[r] + (T)2 * lv[r];
+                }
+            }
+        } else {
+            const T y0 = Y[t0];
+            const T y1 = t1 >= 0 ? Y[t1] : (T)0;
+            const T q = y0 * ib0 + y1 * ib1;
+            T lv;
+            if (type == TYPE_SOFT) lv = -(e0 + al * q) * kf;
+            else {
+                lv = -(q + e0) * is;
+                if (type == TYPE_HARD) lv = lv > (T)0 ? lv : (T)0;
+            }
+            LAM[row] = lv;
+            const T zn0 = (y0 + lv) * ib0;
+            const T zo0 = swap_z(Z, ZO, t0, 0, zn0);
+            mloc = umax(mloc, umax(rbits(fabs(X[t0] - zn0)), rbits(fabs(zn0 - zo0))));
+            wn[t0] = y0 + (T)2 * lv;
+            if (t1 >= 0) {
+                const T zn1 = (y1 + lv) * ib1;
+                const T zo1 = swap_z(Z, ZO, t1, 3, zn1);
+                mloc = umax(mloc, umax(rbits(fabs(X[t1] - zn1)), rbits(fabs(zn1 - zo1))));
+                wn[t1] = y1 + (T)2 * lv;
+            }
+        }
+        return mloc;
+    }
+
+    // write the z (and the previous z) held in registers back to the scene arrays
+    __device__ __forceinline__ void publish(T *Z, T *ZO) const
+    {
+        if constexpr (KEEP_Z) {
+            if (!valid) return;
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                if (r < nr) {
+                    Z[t0 + r] = zr[r]; ZO[t0 + r] = zq[r];
+                    if (t1 >= 0) { Z[t1 + r] = zr[3 + r]; ZO[t1 + r] = zq[3 + r]; }
+                }
+            }
+        }
+    }
+};
 
 template <typename T, int SPLIT, bool CACHED>
 __global__ void __launch_bounds__(SUBADMM_THREADS, CACHED ? 1 : 2) step_kernel(StepParams P)
@@ -778,14 +1004,14 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, CACHED ? 1 : 2) step_kernel(S
         T *const W0 = V.tb + S.ot_w0, *const W1 = V.tb + S.ot_w1;
         // per-side-row arrays start zero (padding side-rows between subsystems stay zero)
         for (int q = tid; q < S.ot_lam - S.ot_x; q += blockDim.x) V.tb[S.ot_x + q] = (T)0;
-        scene_tables<T>(P, S, V);
+        scene_tables<T>(P, S, V, BlockDist());
         __syncthreads();
 
         for (int step = 0; step < P.n_steps; ++step) {
             if (tid == 0) s_status = ST_OK;
             __syncthreads();
             PhaseClock pc(P.phase ? P.phase + 8 * sc : nullptr);
-            scene_setup<T>(P, S, V, &s_status, pc, step);
+            scene_setup<T>(P, S, V, &s_status, pc, step, BlockDist());
             const int status0 = s_status;
             if (status0 != ST_OK) {
                 // K_i not SPD: report, leave the state untouched (the step is undefined)
@@ -825,12 +1051,7 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, CACHED ? 1 : 2) step_kernel(S
             bool xv = false;
             int xdro = 0, xwbo = 0, xnv = 0, xrow = 0;
             T xc = (T)0, xbt = (T)0, yreg = (T)0, yprev = (T)0;
-            bool pv = false;
-            int ptype = 0, prow = 0, pt0 = 0, pt1 = -1, pnr = 1;
-            T ib0 = (T)0, ib1 = (T)0, pe0 = (T)0, pe1 = (T)0, pe2 = (T)0;
-            T pis = (T)0, pkf = (T)0, pal = (T)0, pmu = (T)0;
-            T zr[6] = {(T)0, (T)0, (T)0, (T)0, (T)0, (T)0};
-            T zq[6] = {(T)0, (T)0, (T)0, (T)0, (T)0, (T)0};
+            RegItem<T> ri;
             if (CACHED) {
                 if (xt < S.nsr && V.mlen[xt] > 0) {
                     xv = true;
@@ -847,29 +1068,7 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, CACHED ? 1 : 2) step_kernel(S
                     for (int q = 0; q < MAXC; ++q)
                         if (xgl + q * SPLIT < xnv) dreg[q] = Dr[xgl + q * SPLIT];
                 }
-                if (tid < S.nitem && V.item[tid].type >= 0) {
-                    pv = true;
-                    const Item it = V.item[tid];
-                    ptype = it.type;
-                    prow = it.row;
-                    pt0 = V.list[it.lo];
-                    pt1 = it.ns > 1 ? V.list[it.lo + 1] : -1;
-                    pnr = ptype == TYPE_CONTACT ? 3 : 1;
-                    ib0 = INVB[pt0];
-                    if (pt1 >= 0) ib1 = INVB[pt1];
-                    pe0 = E[prow];
-                    if (pnr == 3) { pe1 = E[prow + 1]; pe2 = E[prow + 2]; }
-                    pis = INVS[prow]; pkf = KF[prow]; pal = AL[prow]; pmu = MU[prow];
-#pragma unroll
-                    for (int r = 0; r < 3; ++r) {
-                        if (r < pnr) {
-                            zr[r] = Z[pt0 + r];
-                            if (pt1 >= 0) zr[3 + r] = Z[pt1 + r];
-                        }
-                    }
-#pragma unroll
-                    for (int r = 0; r < 6; ++r) zq[r] = zr[r];
-                }
+                if (tid < S.nitem) ri.load(V.item, V.list, tid, INVB, E, INVS, KF, AL, MU, Z);
             }
 
             int par = 0, last_par = 0, iters = 0, conv = 0, status = ST_OK;
@@ -982,72 +1181,7 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, CACHED ? 1 : 2) step_kernel(S
                     T *wn = par ? W0 : W1;
                     U mloc = 0;
                     if (CACHED) {
-                        if (pv) {
-                            if (ptype == TYPE_CONTACT) {
-                                T ya[3], yb[3] = {(T)0, (T)0, (T)0};
-#pragma unroll
-                                for (int r = 0; r < 3; ++r) ya[r] = Y[pt0 + r];
-                                if (pt1 >= 0) {
-#pragma unroll
-                                    for (int r = 0; r < 3; ++r) yb[r] = Y[pt1 + r];
-                                }
-                                const T ln = -(ya[0] * ib0 + yb[0] * ib1 + pe0) * pis;
-                                const T l1 = -(ya[1] * ib0 + yb[1] * ib1 + pe1) * pis;
-                                const T l2 = -(ya[2] * ib0 + yb[2] * ib1 + pe2) * pis;
-                                T lv[3];
-                                if (ln <= (T)0) {
-                                    lv[0] = lv[1] = lv[2] = (T)0;
-                                } else {
-                                    const T t2 = l1 * l1 + l2 * l2;
-                                    const T lim = pmu * ln;
-                                    lv[0] = ln;
-                                    if (t2 > lim * lim) { const T f = lim * rsq(t2); lv[1] = l1 * f; lv[2] = l2 * f; }
-                                    else { lv[1] = l1; lv[2] = l2; }
-                                }
-#pragma unroll
-                                for (int r = 0; r < 3; ++r) {
-                                    LAM[prow + r] = lv[r];
-                                    const T zn = (ya[r] + lv[r]) * ib0;
-                                    mloc = umax(mloc, umax(rbits(fabs(X[pt0 + r] - zn)), rbits(fabs(zn - zr[r]))));
-                                    zq[r] = zr[r];
-                                    zr[r] = zn;
-                                    wn[pt0 + r] = ya[r] + (T)2 * lv[r];
-                                }
-                                if (pt1 >= 0) {
-#pragma unroll
-                                    for (int r = 0; r < 3; ++r) {
-                                        const T zn = (yb[r] + lv[r]) * ib1;
-                                        mloc = umax(mloc, umax(rbits(fabs(X[pt1 + r] - zn)), rbits(fabs(zn - zr[3 + r]))));
-                                        zq[3 + r] = zr[3 + r];
-                                        zr[3 + r] = zn;
-                                        wn[pt1 + r] = yb[r] + (T)2 * lv[r];
-                                    }
-                                }
-                            } else {
-                                const T y0 = Y[pt0];
-                                const T y1 = pt1 >= 0 ? Y[pt1] : (T)0;
-                                const T q = y0 * ib0 + y1 * ib1;
-                                T lv;
-                                if (ptype == TYPE_SOFT) lv = -(pe0 + pal * q) * pkf;
-                                else {
-                                    lv = -(q + pe0) * pis;
-                                    if (ptype == TYPE_HARD) lv = lv > (T)0 ? lv : (T)0;
-                                }
-                                LAM[prow] = lv;
-                                const T zn0 = (y0 + lv) * ib0;
-                                mloc = umax(mloc, umax(rbits(fabs(X[pt0] - zn0)), rbits(fabs(zn0 - zr[0]))));
-                                zq[0] = zr[0];
-                                zr[0] = zn0;
-                                wn[pt0] = y0 + (T)2 * lv;
-                                if (pt1 >= 0) {
-                                    const T zn1 = (y1 + lv) * ib1;
-                                    mloc = umax(mloc, umax(rbits(fabs(X[pt1] - zn1)), rbits(fabs(zn1 - zr[3]))));
-                                    zq[3] = zr[3];
-                                    zr[3] = zn1;
-                                    wn[pt1] = y1 + (T)2 * lv;
-                                }
-                            }
-                        }
+                        mloc = ri.project(Y, X, LAM, wn, Z, ZO);
                     } else {
                         for (int i = tid; i < S.nitem; i += SUBADMM_THREADS) {
                             const Item it = V.item[i];
@@ -1120,18 +1254,10 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, CACHED ? 1 : 2) step_kernel(S
                     if (primal_stop && mx <= tolb) { conv = 1; break; }
                 }
                 // the cached z live in registers: publish them (and the previous ones)
-                if (CACHED && pv) {
-#pragma unroll
-                    for (int r = 0; r < 3; ++r) {
-                        if (r < pnr) {
-                            Z[pt0 + r] = zr[r]; ZO[pt0 + r] = zq[r];
-                            if (pt1 >= 0) { Z[pt1 + r] = zr[3 + r]; ZO[pt1 + r] = zq[3 + r]; }
-                        }
-                    }
-                }
+                if (CACHED) ri.publish(Z, ZO);
                 if (CACHED && xv && xgl == 0) YO[xt] = yprev;
                 __syncthreads();
-                recover_v<T>(P, S, V, last_par ? W1 : W0);
+                recover_v<T>(P, S, V, last_par ? W1 : W0, BlockDist());
                 __syncthreads();
                 if (MIXED && conv && primal_stop && status == ST_OK) {
                     // FP64 primal residual max |J v - z|; on a miss, refine c by the FP64 - FP32

@@ -14,10 +14,13 @@
 #include "subadmm.h"
 #include "layout.h"
 #include "step_kernel.cuh"
+#include "grid_kernel.cuh"
 
 namespace {
 
 std::string g_create_error;
+constexpr int kGridSideRows = 8192;   // default: scenes with at least this many side-rows use
+                                      // the grid kernel
 
 struct HostSub {
     int scene = 0, kind = 0, n = 0, nb = 0;
@@ -32,6 +35,8 @@ struct LaunchClass {
     bool cached = false;           // register-cached iteration
     int split = 1;                 // lanes per side-row in the v-step mat-vec
     bool half = false;             // placed within half an SM's shared memory (two blocks/SM)
+    bool grid = false;             // one scene at a time over the whole GPU (cooperative launch)
+    int blocks = 0;                // grid class: blocks of the cooperative launch
     std::vector<int> scenes;
     int ids_off = 0;               // offset of the scene list in d_scene_ids
     int max_smem = 0;
@@ -80,10 +85,12 @@ struct sim_s {
     // concurrently on forked streams
     std::vector<LaunchClass> classes;
     int *d_scene_ids = nullptr;    // every class's scene list, concatenated
+    GridScratch *d_grid = nullptr; // grid kernel scratch
     cudaEvent_t ev_fork = nullptr;
     int split_override = 0;        // tuning: force the split of every class (0: heuristic)
     std::vector<int> sc_nsr, sc_items, sc_sides, sc_mpad;   // per scene: register-cache limits
     int smem_full = 0;             // dynamic shared memory a block may use
+    int grid_side_rows = kGridSideRows;
     // graph replay of sim_step
     bool use_graph = false;
     int graph_steps = 0;
@@ -191,6 +198,8 @@ void free_device(sim_t s)
     cudaFree(s->d_nodes); cudaFree(s->d_ipool); cudaFree(s->d_subflag);
     cudaFree(s->d_scene_ids);
     s->d_scene_ids = nullptr;
+    cudaFree(s->d_grid);
+    s->d_grid = nullptr;
     for (auto &c : s->classes) {
         if (c.stream) cudaStreamDestroy(c.stream);
         if (c.done) cudaEventDestroy(c.done);
@@ -543,23 +552,33 @@ int finalize(sim_t s)
     }
     s->sc_sides = sc_sides;
     s->sc_mpad = sc_mpad;
+    for (int sc = 0; sc < nscenes; ++sc) s->scenes[sc].max_sides = sc_sides[sc];
     s->classes.clear();
     for (int sc = 0; sc < nscenes; ++sc) {
         const SceneDesc &S = s->scenes[sc];
         const Place &q = place[sc];
+        // a scene with many side-rows runs alone over the whole GPU (grid kernel, lanes per
+        // side-row 8 / 16 / 32 by the mean row length of D)
+        const bool grid = S.nsr >= s->grid_side_rows;
         int split = 1;
-        while (split < 4 && 2 * split * std::max(S.nsr, 1) <= SUBADMM_THREADS) split *= 2;
+        if (grid) {
+            const double mean_m = (double)S.nsr / std::max(S.nsub, 1);
+            split = mean_m >= 256 ? 32 : mean_m >= 64 ? 16 : 8;
+        } else {
+            while (split < 4 && 2 * split * std::max(S.nsr, 1) <= SUBADMM_THREADS) split *= 2;
+        }
         if (s->split_override > 0) split = s->split_override;
-        const bool cached = S.nsr * split <= SUBADMM_THREADS && S.nitem <= SUBADMM_THREADS &&
+        const bool cached = !grid && S.nsr * split <= SUBADMM_THREADS && S.nitem <= SUBADMM_THREADS &&
                             sc_sides[sc] <= 2 && (sc_mpad[sc] + vn - 1) / vn <= chunks * split;
-        const bool half = !cached && bytes_with(q, q.scd, q.sh + q.scene_t) <= half_budget;
+        const bool half = !grid && !cached && bytes_with(q, q.scd, q.sh + q.scene_t) <= half_budget;
         sc_budget[sc] = half ? half_budget : smem_budget;
         int k = 0;
         while (k < (int)s->classes.size() && !(s->classes[k].cached == cached &&
-               s->classes[k].split == split && s->classes[k].half == half)) ++k;
+               s->classes[k].split == split && s->classes[k].half == half &&
+               s->classes[k].grid == grid)) ++k;
         if (k == (int)s->classes.size()) {
             LaunchClass c;
-            c.cached = cached; c.split = split; c.half = half;
+            c.cached = cached; c.split = split; c.half = half; c.grid = grid;
             s->classes.push_back(c);
         }
         s->classes[k].scenes.push_back(sc);
@@ -573,7 +592,20 @@ int finalize(sim_t s)
         // everything on chip if it fits; else the setup arrays (J, K, L, W: O(n^2)) in the
         // workspace and the iteration arrays (D, c: O(m^2)) on chip; else all in the workspace
         long long od = 0, ot = 0;
-        if (bytes_of(q.sd + q.scd, q.st + q.sh + q.scene_t) <= (long long)budget) {
+        S.g_scene = -1;
+        const bool grid_scene = s->classes[sc_class[sc]].grid;
+        if (grid_scene) {
+            // everything in the workspace: the per-subsystem arrays, then the scene arrays
+            S.sub_global = 1; S.hot_global = 1;
+            S.g_base = work_bytes;
+            S.g_tbase = (q.sd * 8 + 255) / 256 * 256;
+            work_bytes += (S.g_tbase + (q.st + q.sh) * tsize + 255) / 256 * 256;
+            for (int i = 0; i < S.nsub; ++i) {
+                s->sdesc[S.sub0 + i].ot_D += (int)q.st;
+                s->sdesc[S.sub0 + i].ot_c += (int)q.st;
+            }
+            S.g_scene = work_bytes;
+        } else if (bytes_of(q.sd + q.scd, q.st + q.sh + q.scene_t) <= (long long)budget) {
             S.sub_global = 0; S.hot_global = 0; S.g_base = 0; S.g_tbase = 0;
             od = q.sd; ot = q.st + q.sh;
             for (int i = 0; i < S.nsub; ++i) {
@@ -616,6 +648,13 @@ int finalize(sim_t s)
         const long long t_base = (od * 8 + 15) / 16 * 16;
         const long long i_base = (t_base + ot * tsize + 15) / 16 * 16;
         const long long bytes = i_base + 4 * q.ints;
+        if (grid_scene) {
+            work_bytes += (bytes + 255) / 256 * 256;
+            S.t_base = (int)t_base;
+            S.i_base = (int)i_base;
+            S.smem_bytes = 0;
+            continue;
+        }
         if (bytes > (long long)budget) {
             char buf[256];
             snprintf(buf, sizeof buf, "scene %d needs %lld bytes of shared memory for its per-row "
@@ -639,6 +678,8 @@ int finalize(sim_t s)
         }
         int rc2 = upload(s, &s->d_scene_ids, ids, "scene lists");
         if (rc2) return rc2;
+        cudaError_t e = cudaMalloc((void **)&s->d_grid, sizeof(GridScratch));
+        if (e != cudaSuccess) return fail(s, SIM_ENOMEM, "cudaMalloc grid scratch");
         CK(cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming), "event");
         for (size_t k = 0; k < s->classes.size(); ++k) {
             LaunchClass &c = s->classes[k];
@@ -786,11 +827,11 @@ int sim_add_subsystem(sim_t s, int scene, int kind, int count, const double *dat
     HostSub u;
     u.scene = scene;
     if (kind == SIM_SUB_GENERIC) {
-        if (count > SUBADMM_MAXN) return fail(s, SIM_EINVAL, "generic subsystem larger than 1024 DOF");
+        if (count > SUBADMM_MAXN) return fail(s, SIM_EINVAL, "generic subsystem larger than 2048 DOF");
         u.kind = KIND_GENERIC; u.n = count;
         u.Ab.assign(data, data + (size_t)count * count + count);
     } else if (kind == SIM_SUB_RIGID) {
-        if (6 * count > SUBADMM_MAXN) return fail(s, SIM_EINVAL, "rigid subsystem larger than 1024 DOF");
+        if (6 * count > SUBADMM_MAXN) return fail(s, SIM_EINVAL, "rigid subsystem larger than 2048 DOF");
         u.kind = KIND_RIGID; u.nb = count; u.n = 6 * count;
         u.bodies.assign(data, data + (size_t)count * SUBADMM_BODY);
         for (int b = 0; b < count; ++b) {
@@ -802,7 +843,7 @@ int sim_add_subsystem(sim_t s, int scene, int kind, int count, const double *dat
         // data: mass (nn), f (n), X0 (n), x (n), v (n), nnz, then nnz triplets (row, col,
         // value) of the symmetric stiffness K, indices stored exactly as doubles
         const int nn = count, n = 3 * count;
-        if (n > SUBADMM_MAXN) return fail(s, SIM_EINVAL, "linear subsystem larger than 1024 DOF");
+        if (n > SUBADMM_MAXN) return fail(s, SIM_EINVAL, "linear subsystem larger than 2048 DOF");
         u.kind = KIND_LINEAR; u.nb = nn; u.n = n;
         const double *mass = data, *f = data + nn, *X0 = f + n, *x = X0 + n, *v = x + n;
         const double nnzd = v[n];
@@ -958,6 +999,7 @@ StepParams step_params(const sim_t s, int n_steps)
     P.lists = s->d_lists;
     P.asm_order = s->d_asm;
     P.scene_ids = s->d_scene_ids;
+    P.grid = s->d_grid;
     return P;
 }
 
@@ -972,22 +1014,60 @@ KernFn kernel_for(bool mixed, bool cached, int split)
     return split == 4 ? step_kernel<double, 4, false> : split == 2 ? step_kernel<double, 2, false> : step_kernel<double, 1, false>;
 }
 
+KernFn grid_kernel_for(bool mixed, int split)
+{
+    using namespace subadmm;
+    if (mixed) return split == 32 ? grid_step_kernel<float, 32> : split == 16 ? grid_step_kernel<float, 16> : grid_step_kernel<float, 8>;
+    return split == 32 ? grid_step_kernel<double, 32> : split == 16 ? grid_step_kernel<double, 16> : grid_step_kernel<double, 8>;
+}
+
+// One cooperative launch per scene of a grid class, in turn on `st`, each after zeroing the
+// grid scratch; as many blocks as fit on the GPU at once.
+int launch_grid_class(sim_t s, const LaunchClass &c, StepParams P, cudaStream_t st, int split)
+{
+    KernFn kf = grid_kernel_for(s->opt.precision == SIM_MIXED, split);
+    int per_sm = 0, sms = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kf, SUBADMM_THREADS, 0), "occupancy");
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->opt.device), "attribute");
+    const int blocks = std::max(1, per_sm * sms);
+    for (size_t i = 0; i < c.scenes.size(); ++i) {
+        CK(cudaMemsetAsync(s->d_grid, 0, sizeof(GridScratch), st), "grid scratch");
+        P.scene_ids = s->d_scene_ids + c.ids_off + (int)i;
+        P.nscenes = 1;
+        void *args[] = {&P};
+        CK(cudaLaunchCooperativeKernel((const void *)kf, dim3(blocks), dim3(SUBADMM_THREADS), args, 0, st),
+           "grid kernel launch");
+    }
+    return SIM_OK;
+}
+
 // Enqueue one launch per class: class 0 on the simulation's stream, the others on their
 // own streams forked from it and joined back, so the classes run concurrently.
 int launch_classes(sim_t s, StepParams P, cudaStream_t base)
 {
     const bool mixed = s->opt.precision == SIM_MIXED;
-    const int nc = (int)s->classes.size();
-    if (nc > 1) CK(cudaEventRecord(s->ev_fork, base), "fork");
-    for (int k = 0; k < nc; ++k) {
+    // grid classes first, alone on the GPU (their blocks must all be resident at once)
+    std::vector<int> block_classes;
+    for (int k = 0; k < (int)s->classes.size(); ++k) {
         const LaunchClass &c = s->classes[k];
-        cudaStream_t st = k == 0 ? base : c.stream;
-        if (k > 0) CK(cudaStreamWaitEvent(st, s->ev_fork, 0), "fork wait");
+        if (c.grid) {
+            const int rc = launch_grid_class(s, c, P, base, c.split);
+            if (rc) return rc;
+        } else {
+            block_classes.push_back(k);
+        }
+    }
+    const int nc = (int)block_classes.size();
+    if (nc > 1) CK(cudaEventRecord(s->ev_fork, base), "fork");
+    for (int j = 0; j < nc; ++j) {
+        const LaunchClass &c = s->classes[block_classes[j]];
+        cudaStream_t st = j == 0 ? base : c.stream;
+        if (j > 0) CK(cudaStreamWaitEvent(st, s->ev_fork, 0), "fork wait");
         P.scene_ids = s->d_scene_ids + c.ids_off;
         P.nscenes = (int)c.scenes.size();
         kernel_for(mixed, c.cached, c.split)<<<P.nscenes, SUBADMM_THREADS, c.max_smem, st>>>(P);
         CK(cudaGetLastError(), "step kernel launch");
-        if (k > 0) {
+        if (j > 0) {
             CK(cudaEventRecord(c.done, st), "join");
             CK(cudaStreamWaitEvent(base, c.done, 0), "join wait");
         }
@@ -1014,7 +1094,10 @@ int sim_step(sim_t s, int n_steps)
         CK(cudaFuncSetAttribute(kernel_for(s->opt.precision == SIM_MIXED, c.cached, c.split),
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, s->smem_full),
            "shared memory attribute");
-    if (s->use_graph) {
+    bool has_grid = false;
+    for (const LaunchClass &c : s->classes) has_grid = has_grid || c.grid;
+    // (cooperative launches of the grid kernel are issued directly, not captured)
+    if (s->use_graph && !has_grid) {
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
         CK(cudaStreamIsCapturing(s->stream, &cs), "capture status");
         if (cs == cudaStreamCaptureStatusNone) {
@@ -1080,7 +1163,7 @@ void class_rows(const sim_t s, int max_classes, long long *out, const std::vecto
     for (int k = 0; k < (int)s->classes.size() && k < max_classes; ++k) {
         const LaunchClass &c = s->classes[k];
         out[5 * k + 0] = (long long)c.scenes.size();
-        out[5 * k + 1] = c.cached ? 1 : 0;
+        out[5 * k + 1] = c.grid ? 2 : c.cached ? 1 : 0;
         out[5 * k + 2] = c.split;
         out[5 * k + 3] = c.max_smem;
         out[5 * k + 4] = ns ? (long long)(*ns)[k] : 0;
@@ -1156,6 +1239,25 @@ int sim_autotune(sim_t s, int steps, int max_classes, long long *out)
         double best = 1e300;
         bool bc = c.cached;
         int bs = c.split;
+        if (c.grid) {
+            for (int split = 8; split <= 32 && err == cudaSuccess; split *= 2) {
+                float ms = 0.0f;
+                for (int rep = 0; rep < 2 && err == cudaSuccess; ++rep) {   // warm, then timed
+                    err = copy_all(false);
+                    if (err != cudaSuccess) break;
+                    cudaEventRecord(e0, s->stream);
+                    const int lrc = launch_grid_class(s, c, P, s->stream, split);
+                    cudaEventRecord(e1, s->stream);
+                    if (lrc) { err = cudaErrorLaunchFailure; break; }
+                    err = cudaEventSynchronize(e1);
+                    if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+                }
+                if (err == cudaSuccess && ms < best) { best = ms; bs = split; }
+            }
+            c.split = bs;
+            best_ns[k] = best * 1e6 / steps;
+            continue;
+        }
         for (int cached = 0; cached < 2 && err == cudaSuccess; ++cached) {
             for (int split = 1; split <= 4 && err == cudaSuccess; split *= 2) {
                 if (cached) {
@@ -1195,6 +1297,44 @@ int sim_autotune(sim_t s, int steps, int max_classes, long long *out)
     }
     class_rows(s, max_classes, out, &best_ns);
     return (int)s->classes.size();
+}
+
+int sim_grid_threshold(sim_t s, int side_rows)
+{
+    if (!s) return SIM_EINVAL;
+    if (s->finalized) return fail(s, SIM_EINVAL, "the layout is fixed after the first sim_step");
+    if (side_rows < 1) return fail(s, SIM_EINVAL, "side_rows must be >= 1");
+    s->grid_side_rows = side_rows;
+    return SIM_OK;
+}
+
+int sim_probe_barrier(int device, int blocks, int expected, double limit_s, int out[2])
+{
+    if (!out || blocks < 1 || expected < 1 || !(limit_s > 0.0) || limit_s > 10.0) return SIM_EINVAL;
+    if (cudaSetDevice(device) != cudaSuccess) return SIM_ECUDA;
+    int per_sm = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, subadmm::barrier_probe_kernel, 32, 0) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
+        return SIM_ECUDA;
+    if (blocks > per_sm * sms) return SIM_EINVAL;          // must all be resident
+    unsigned *w = nullptr;
+    if (cudaMalloc((void **)&w, 4 * sizeof(unsigned)) != cudaSuccess) return SIM_ENOMEM;
+    cudaMemset(w, 0, 4 * sizeof(unsigned));
+    unsigned *count = w, *gen = w + 1;
+    int *err = reinterpret_cast<int *>(w + 2), *passed = reinterpret_cast<int *>(w + 3);
+    unsigned ex = (unsigned)expected;
+    unsigned long long lim = (unsigned long long)(limit_s * 1e9);
+    void *args[] = {&count, &gen, &err, &ex, &lim, &passed};
+    cudaError_t e = cudaLaunchCooperativeKernel((const void *)subadmm::barrier_probe_kernel,
+                                                dim3(blocks), dim3(32), args, 0, nullptr);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    int host[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpy(host, w + 2, sizeof host, cudaMemcpyDeviceToHost);
+    cudaFree(w);
+    if (e != cudaSuccess) return SIM_ECUDA;
+    out[0] = host[0];
+    out[1] = host[1];
+    return SIM_OK;
 }
 
 int sim_sync(sim_t s)
@@ -1365,7 +1505,7 @@ int sim_scene_info(sim_t s, int scene, long long out[4])
     if (rc) return rc;
     if (scene < 0 || scene >= s->nscenes) return fail(s, SIM_EINVAL, "scene out of range");
     const SceneDesc &S = s->scenes[scene];
-    out[0] = S.sub_global + S.hot_global;
+    out[0] = S.g_scene >= 0 ? 3 : S.sub_global + S.hot_global;
     out[1] = S.smem_bytes;
     out[2] = S.nsub;
     out[3] = s->work_bytes;

@@ -32,7 +32,7 @@ EXPORTS = ("sim_default_options", "sim_create", "sim_destroy", "sim_add_subsyste
            "sim_add_interface", "sim_set_generic", "sim_step", "sim_residuals", "sim_get",
            "sim_read_state", "sim_read_state_noalloc", "sim_write_state", "sim_sizes",
            "sim_iteration_stats", "sim_scene_info", "sim_use_graph", "sim_launch_classes",
-           "sim_autotune",
+           "sim_autotune", "sim_grid_threshold", "sim_probe_barrier",
            "sim_phase_trace", "sim_sync", "sim_last_error")
 
 
@@ -94,6 +94,8 @@ def load(build_if_missing: bool = True):
             "sim_use_graph": (C.c_int, [VP, C.c_int]),
             "sim_launch_classes": (C.c_int, [VP, C.c_int, PL]),
             "sim_autotune": (C.c_int, [VP, C.c_int, C.c_int, PL]),
+            "sim_grid_threshold": (C.c_int, [VP, C.c_int]),
+            "sim_probe_barrier": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_double, PI]),
             "sim_phase_trace": (C.c_int, [VP, C.c_int, PL]),
             "sim_sync": (C.c_int, [VP]),
             "sim_last_error": (C.c_char_p, [VP]),
@@ -215,6 +217,18 @@ def sim_autotune(h, steps: int = 5, max_classes: int = 64) -> list:
     return _class_rows(out, min(n, max_classes))
 
 
+def sim_grid_threshold(h, side_rows: int) -> None:
+    _check(h, load().sim_grid_threshold(h, side_rows))
+
+
+def sim_probe_barrier(device: int, blocks: int, expected: int, limit_s: float) -> dict:
+    out = (C.c_int * 2)()
+    rc = load().sim_probe_barrier(device, blocks, expected, limit_s, out)
+    if rc < 0:
+        raise SimError(rc, "sim_probe_barrier failed")
+    return dict(timed_out=bool(out[0]), passed=int(out[1]))
+
+
 def sim_use_graph(h, enable: bool) -> None:
     _check(h, load().sim_use_graph(h, 1 if enable else 0))
 
@@ -303,8 +317,11 @@ class Simulation:
     ``problem`` has ``scenes`` (each with ``subs`` and ``ifs``) and ``options``, shaped like
     ``scenegen.Problem``.  Subsystem and interface ids are assigned in scene order."""
 
-    def __init__(self, problem, stream: int = 0, device: int = 0, precision: int = SIM_FP64):
+    def __init__(self, problem, stream: int = 0, device: int = 0, precision: int = SIM_FP64,
+                 grid_side_rows: Optional[int] = None):
         self.h = sim_create(options_from(problem.options, stream, device, precision))
+        if grid_side_rows is not None:
+            sim_grid_threshold(self.h, grid_side_rows)
         self.sub_ids = []     # per scene: list of ids
         self.if_ids = []
         self.sub_n = []

@@ -495,6 +495,213 @@ def hanging_scene(rng: np.random.Generator, n_blocks: int = 2, dims=(2, 2, 3),
     return Scene(subs, ifs)
 
 
+# ----------------------------------------------------------------------------------------
+# Linear tetrahedral FEM beam cut into slabs (rigid-deformable workload)
+
+def lame(E: float, nu: float):
+    """Lame parameters (lambda, mu) of an isotropic material."""
+    return E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu)), E / (2.0 * (1.0 + nu))
+
+
+def tet_stiffness(X: np.ndarray, tets: np.ndarray, E: float, nu: float):
+    """Element stiffness matrices (T x 12 x 12) and volumes of linear (constant-strain)
+    tetrahedra: K_e = V B^T C B with the strain-displacement matrix B of the barycentric
+    shape functions and the isotropic elasticity matrix C in Voigt order
+    (xx, yy, zz, 2yz, 2xz, 2xy)."""
+    P = X[tets]                                    # T x 4 x 3
+    Dm = np.stack([P[:, 1] - P[:, 0], P[:, 2] - P[:, 0], P[:, 3] - P[:, 0]], axis=2)
+    vol = np.abs(np.linalg.det(Dm)) / 6.0
+    Gi = np.linalg.inv(Dm)                         # rows: gradients of N1..N3
+    grads = np.concatenate([-Gi.sum(axis=1, keepdims=True), Gi], axis=1)   # T x 4 x 3
+    T = tets.shape[0]
+    B = np.zeros((T, 6, 12))
+    for a in range(4):
+        bx, by, bz = grads[:, a, 0], grads[:, a, 1], grads[:, a, 2]
+        c = 3 * a
+        B[:, 0, c] = bx
+        B[:, 1, c + 1] = by
+        B[:, 2, c + 2] = bz
+        B[:, 3, c + 1] = bz
+        B[:, 3, c + 2] = by
+        B[:, 4, c] = bz
+        B[:, 4, c + 2] = bx
+        B[:, 5, c] = by
+        B[:, 5, c + 1] = bx
+    lam, mu = lame(E, nu)
+    C = np.zeros((6, 6))
+    C[:3, :3] = lam
+    C[np.arange(3), np.arange(3)] += 2.0 * mu
+    C[np.arange(3, 6), np.arange(3, 6)] = mu
+    Ke = vol[:, None, None] * np.einsum("tji,jk,tkl->til", B, C, B)
+    return Ke, vol
+
+
+def kuhn_tets(cell_corners: np.ndarray) -> np.ndarray:
+    """Split hexahedral cells (C x 8 corner ids, corner index = 4 i + 2 j + k for offsets
+    (i, j, k) in {0, 1}^3) into 6 tetrahedra each around the 000-111 diagonal (Kuhn); the
+    split is the same in every cell, so neighbouring cells share conforming faces."""
+    tets = []
+    for perm in ((0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)):
+        off = np.zeros(3, int)
+        path = [0]
+        for axis in perm:
+            off[axis] = 1
+            path.append(4 * off[0] + 2 * off[1] + off[2])
+        tets.append(cell_corners[:, path])
+    return np.concatenate(tets, axis=0)
+
+
+def fem_slab(planes_x: np.ndarray, ny: int, nz: int, width: float, height: float,
+             E: float, nu: float, rho: float, z0: float = 0.0):
+    """One slab of the beam: node planes at x = planes_x, an ny x nz grid per plane over
+    [0, width] x [z0, z0 + height].  Nodes are numbered plane-fastest,
+    node = (iy nz + iz) k + p, which keeps the stiffness envelope narrow (slabs are only a
+    few planes thick).  Returns the LinearSub (lumped mass, stiffness triplets) and the
+    node index function."""
+    k = len(planes_x)
+    ys = np.linspace(0.0, width, ny)
+    zs = np.linspace(z0, z0 + height, nz)
+
+    def nid(p, iy, iz):
+        return (iy * nz + iz) * k + p
+
+    X = np.zeros((k * ny * nz, 3))
+    for p in range(k):
+        for iy in range(ny):
+            for iz in range(nz):
+                X[nid(p, iy, iz)] = (planes_x[p], ys[iy], zs[iz])
+    cells = []
+    for p in range(k - 1):
+        for iy in range(ny - 1):
+            for iz in range(nz - 1):
+                cells.append([nid(p + i, iy + j, iz + l) for i in (0, 1) for j in (0, 1)
+                              for l in (0, 1)])
+    tets = kuhn_tets(np.array(cells, dtype=int))
+    Ke, vol = tet_stiffness(X, tets, E, nu)
+    dof = (3 * tets[:, :, None] + np.arange(3)[None, None, :]).reshape(-1, 12)
+    Ki = np.repeat(dof, 12, axis=1).ravel()
+    Kj = np.tile(dof, (1, 12)).ravel()
+    Kv = Ke.reshape(-1)
+    # sum duplicate entries
+    key = Ki.astype(np.int64) * (3 * X.shape[0]) + Kj
+    uk, inv = np.unique(key, return_inverse=True)
+    vals = np.zeros(uk.shape[0])
+    np.add.at(vals, inv, Kv)
+    Ki, Kj = (uk // (3 * X.shape[0])).astype(np.int64), (uk % (3 * X.shape[0])).astype(np.int64)
+    mass = np.zeros(X.shape[0])
+    np.add.at(mass, tets.ravel(), np.repeat(rho * vol / 4.0, 4))
+    nn = X.shape[0]
+    sub = LinearSub(mass, Ki, Kj, vals, np.zeros(3 * nn), X.ravel().copy(), X.ravel().copy(),
+                    np.zeros(3 * nn))
+    return sub, nid, tets
+
+
+def gripper(anchor_w: np.ndarray, reach: float = 0.12, rho: float = 1000.0):
+    """A 7-R arm in maximal coordinates (one subsystem of 7 boxes): a base turning about z
+    on a world pivot above ``anchor_w``, a vertical chain of 4 links turning about y, and
+    two paddles turning about x at the end, hanging down to ``anchor_w``.  Returns the
+    subsystem, its joint and PD interfaces (joint i joins body i-1, or the world, to body
+    i), and the paddles' body indices."""
+    lw = 0.012
+    lens = [0.02, reach / 4, reach / 4, reach / 4, reach / 4 - 0.02]
+    top = np.asarray(anchor_w, float) + np.array([0.0, 0.0, sum(lens) + 0.02])
+    bodies, joints = [], []
+    ez, ey, ex = np.array([0.0, 0, 1]), np.array([0.0, 1, 0]), np.array([1.0, 0, 0])
+    q0 = np.array([1.0, 0, 0, 0])
+    z = top[2]
+    axes = [ez, ey, ey, ey, ey]
+    for k, L in enumerate(lens):
+        c = np.array([top[0], top[1], z - L / 2])
+        m = lw * lw * L * rho
+        bodies.append(Body(m, box_inertia(m, lw, lw, L), c, q0.copy(), np.zeros(3), np.zeros(3)))
+        joint_w = np.array([top[0], top[1], z])
+        joints.append((k - 1, k, joint_w, axes[k]))
+        z -= L
+    # paddles: thin plates hanging either side of the anchor, hinged about x at the wrist
+    pl = 0.02
+    wrist = np.array([top[0], top[1], z])
+    paddles = []
+    for side in (-1, 1):
+        c = wrist + np.array([0.0, side * 0.01, -pl / 2])
+        m = 0.004 * 0.02 * pl * rho
+        bodies.append(Body(m, box_inertia(m, 0.02, 0.004, pl), c, q0.copy(), np.zeros(3),
+                           np.zeros(3)))
+        joints.append((len(lens) - 1, len(bodies) - 1, wrist + np.array([0.0, side * 0.01, 0.0]), ex))
+        paddles.append(len(bodies) - 1)
+    return bodies, joints, paddles
+
+
+def fem_beam(seed: int = 0, ny: int = 10, nz: int = 10, planes: int = 137, slabs: int = 64,
+             length: float = 0.5, width: float = 0.05, height: float = 0.05, E: float = 1e5,
+             nu: float = 0.45, rho: float = 1000.0, mu: float = 0.5, drop: float = 0.002,
+             with_gripper: bool = True, h: float = 1e-3, tol_primal: float = 1e-6,
+             max_iters: int = 1000, warm: str = "prev", kp: float = 50.0, kd: float = 1.0):
+    """A linear-elastic tetrahedral beam (planes x ny x nz nodes, Kuhn split of every grid
+    cell) cut into ``slabs`` subsystems: slab g holds 4 node planes when g is a multiple of
+    8 and 3 otherwise, neighbouring slabs duplicate the cut plane, and each duplicated node
+    pair is a node-node ball interface (equality, 3 rows).  Every node of the bottom face
+    has a speculative contact with the plane z = 0 (friction mu); the beam starts ``drop``
+    above it.  With the gripper, a 7-R arm (one rigid subsystem, PD drives holding its
+    pose) holds the beam's x = 0 end by ball joints between its two paddles and the
+    nearest side-face nodes."""
+    rng = np.random.default_rng(seed)
+    ks = [4 if g % 8 == 0 else 3 for g in range(slabs)]
+    if sum(k - 1 for k in ks) != planes - 1:
+        raise ValueError("slab plane counts do not tile the beam")
+    xs = np.linspace(0.0, length, planes)
+    subs, ifs, nids = [], [], []
+    p0 = 0
+    for g in range(slabs):
+        sub, nid, _ = fem_slab(xs[p0:p0 + ks[g]], ny, nz, width, height, E, nu, rho, z0=drop)
+        subs.append(sub)
+        nids.append(nid)
+        if g > 0:
+            kp_prev = ks[g - 1]
+            for iy in range(ny):
+                for iz in range(nz):
+                    ifs.append(JointIf(BALL, a=(g - 1, nids[g - 1](kp_prev - 1, iy, iz)),
+                                       b=(g, nid(0, iy, iz))))
+        for p in range(ks[g]):
+            for iy in range(ny):
+                ifs.append(JointIf(PLANE_CONTACT, a=(g, nid(p, iy, 0)), plane_z=0.0, mu=mu))
+        p0 += ks[g] - 1
+    if with_gripper:
+        # hold the x = 0 end by its side faces, half-way up
+        iz = nz // 2
+        grip = [(0, nids[0](0, 0, iz)), (0, nids[0](1, 0, iz)),
+                (0, nids[0](0, ny - 1, iz)), (0, nids[0](1, ny - 1, iz))]
+        Xn = subs[0].X0.reshape(-1, 3)
+        centre = 0.5 * (Xn[grip[0][1]] + Xn[grip[2][1]])
+        bodies, joints, paddles = gripper(centre + np.array([0.0, 0.0, 0.015]))
+        # paddles move to the side faces (y = -0.002 and y = width + 0.002)
+        for pb, side_y in zip(paddles, (-0.002, width + 0.002)):
+            bodies[pb].p = np.array([Xn[grip[0][1]][0] + 0.002, side_y, Xn[grip[0][1]][2]])
+        gs = len(subs)
+        subs.append(RigidSub(bodies))
+        ex = np.array([1.0, 0, 0])
+        for (pa, ch, jw, ax) in joints:
+            ref = np.array([0.0, 0, 1.0]) if abs(ax[2]) < 0.5 else ex
+            bc = bodies[ch]
+            anchor_b = jw - bc.p
+            if pa < 0:
+                ifs.append(JointIf(REVOLUTE, a=(gs, ch), b=None, anchor_a=anchor_b,
+                                   anchor_b=jw.copy(), axis_a=ax.copy(), axis_b=ax.copy(),
+                                   ref_a=ref.copy(), ref_b=ref.copy()))
+                continue
+            bp = bodies[pa]
+            ifs.append(JointIf(REVOLUTE, a=(gs, pa), b=(gs, ch), anchor_a=jw - bp.p,
+                               anchor_b=anchor_b, axis_a=ax.copy(), axis_b=ax.copy(),
+                               ref_a=ref.copy(), ref_b=ref.copy()))
+            ifs.append(JointIf(ANGLE_PD, a=(gs, pa), b=(gs, ch), axis_a=ax.copy(),
+                               axis_b=ax.copy(), ref_a=ref.copy(), ref_b=ref.copy(), kp=kp,
+                               kd=kd, target=0.0))
+        for j, (sg_, node) in enumerate(grip):
+            pb = paddles[0] if j < 2 else paddles[1]
+            ifs.append(JointIf(BALL, a=(gs, pb), b=(sg_, node), anchor_a=Xn[node] - bodies[pb].p))
+    opts = Options(h=h, beta_mode="trace", warm=warm, tol_primal=tol_primal, max_iters=max_iters)
+    return Problem([Scene(subs, ifs)], opts, name=f"fem_beam{slabs}")
+
+
 def _random_rotation(rng) -> np.ndarray:
     return _quat_from_rotvec(rng.uniform(-np.pi, np.pi, 3) * 0.3)
 

@@ -419,6 +419,74 @@ def test_autotune_leaves_no_trace_and_keeps_parity(sa):
         _compare(sim, orcs, p, what=("vhat", "lam"))
 
 
+# ---------------------------------------------------------------------------------------
+# grid kernel: one scene over the whole GPU
+
+
+def test_grid_barrier_time_limit_raises_the_error_flag(sa):
+    """The grid barrier's bounded wait: with one arrival missing nothing completes the
+    barrier, every wait runs out after 50 ms and the flag is raised; with all arrivals the
+    barrier passes without it."""
+    r = sa.sim_probe_barrier(0, 4, 5, 0.05)
+    assert r["timed_out"] and r["passed"] == 4
+    r = sa.sim_probe_barrier(0, 4, 4, 0.05)
+    assert not r["timed_out"] and r["passed"] == 4
+
+
+def _small_beam(**kw):
+    base = dict(ny=3, nz=3, planes=8, slabs=3, length=0.03, width=0.01, height=0.01)
+    base.update(kw)
+    return sg.fem_beam(0, **base)
+
+
+@pytest.mark.parametrize("grid", [False, True])
+def test_small_fem_beam_fp64_fixed_iterations(sa, grid):
+    """Tetrahedral slabs coupled by node-node equality, ground contacts on the bottom nodes
+    and a 7-R arm holding one end: FP64 at a fixed iteration count, block kernel and grid
+    kernel, against the oracle over three steps."""
+    p = _small_beam(tol_primal=-1, max_iters=40)
+    orcs = [oracle.OracleScene(sc, p.options) for sc in p.scenes]
+    sim = sa.Simulation(p, grid_side_rows=1 if grid else None)
+    kinds = {c["cached"] for c in sim.launch_classes()}
+    assert kinds == ({2} if grid else kinds - {2})
+    for _ in range(3):
+        for o in orcs:
+            o.step()
+        sim.step(1)
+        _compare(sim, orcs, p)
+        _compare_states(sim, orcs, TOL)
+
+
+def test_grid_kernel_batched_scenes_fp64(sa):
+    """Several uneven scenes, each run over the whole GPU in turn (the grid kernel forced
+    for every scene), against the oracle; two steps in one call."""
+    p = sg.batched(8, n_scenes=3, tol_primal=-1, max_iters=30)
+    orcs = oracle.run(p, steps=2)
+    sim = sa.Simulation(p, grid_side_rows=1)
+    assert all(c["cached"] == 2 for c in sim.launch_classes())
+    sim.step(2)
+    _compare(sim, orcs, p, what=("vhat", "lam"))
+    _compare_states(sim, orcs, TOL)
+
+
+def test_grid_kernel_mixed_converged_small_beam(sa, capsys):
+    def problem(tol):
+        return _small_beam(tol_primal=tol, max_iters=200000)
+    steps = 3
+    same = oracle.run(problem(1e-6), steps=steps)
+    tight = oracle.run(problem(1e-11), steps=steps)
+    sim = sa.Simulation(problem(1e-6), precision=sa.SIM_MIXED, grid_side_rows=1)
+    sim.step(steps)
+    r = sim.residuals(0)
+    assert r["converged"] and r["r_p"] <= 1e-6
+    err = rel(sim.scene_vhat(0), tight[0].vhat_all())
+    spread = rel(same[0].vhat_all(), tight[0].vhat_all())
+    with capsys.disabled():
+        print(f"\n[mixed grid kernel vs FP64 oracle, small FEM beam, r_p<=1e-6] v-hat rel err "
+              f"to the exact step {err:.3e}; oracle at the same tolerance {spread:.3e}")
+    assert err <= 3 * spread + 1e-6
+
+
 def test_not_spd_is_reported_not_faulted(sa):
     A = -np.eye(3)
     p = sg.Problem([sg.Scene([sg.GenericSub(A, np.ones(3))], [])],
