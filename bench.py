@@ -34,6 +34,13 @@ L2_FLUSH_BYTES = 512 << 20     # > 129 MB L2
 
 
 def workload_desc(n_robots: int, h: float, workload: str = "robots", scenes: int = 0) -> str:
+    if workload == "fem_beam":
+        return (f"one linear-elastic tetrahedral beam 0.5 x 0.05 x 0.05 m (10 x 10 nodes x 137 "
+                f"planes, Kuhn split, E=1e5 Pa, nu=0.45, rho=1000) cut into 64 slabs of 900/1200 "
+                f"DOF joined by node-node equality (18,900 rows), 2,000 speculative ground "
+                f"contacts mu=0.5, a 7-R arm (one rigid subsystem, PD drives) holding one end by "
+                f"ball joints; h={h:g} s; each step iterated to r_p<=1e-6 with the previous "
+                f"step's warm start")
     if workload == "batched":
         return (f"{scenes} independent uneven scenes of 2-32 subsystems each: rigid chains of "
                 f"1-8 bodies and linear spring-lattice blocks of 6-240 DOF, tree + chord ball "
@@ -77,8 +84,10 @@ def algorithmic_work(problem):
                 nnz[s] += sum(cols)
                 rowsq[s] += sum(c * c for c in cols)
         it = sum(2 * ni * ni + 4 * zi + 20 * mi for ni, zi, mi in zip(n, nnz, m))
-        st = sum(ni ** 3 / 3.0 + 2 * q for ni, q in zip(n, rowsq))
-        out.append((it, st))
+        # a linear block's K_i is constant: its factorisation is per run, not per step
+        lin = [hasattr(s, "Ki") for s in sc.subs]
+        st = sum((0.0 if li else ni ** 3 / 3.0) + 2 * q for ni, q, li in zip(n, rowsq, lin))
+        out.append((it, st, sum(mi * mi for mi in m)))
     return out
 
 
@@ -140,7 +149,7 @@ class ClockSampler:
                 "samples": len(sms)}
 
 
-KERNEL_SOURCES = ("layout.h", "rigid_model.cuh", "step_kernel.cuh", "subadmm.cu")
+KERNEL_SOURCES = ("layout.h", "rigid_model.cuh", "step_kernel.cuh", "grid_kernel.cuh", "subadmm.cu")
 
 
 def kernel_source_hash() -> str:
@@ -209,6 +218,31 @@ def cpu_baseline(problem, seconds: float, sample_scenes: int = 64):
             "seconds": dt}
 
 
+def cpu_baseline_one_scene(args, h: float, mean_iters: float):
+    """The FP64 CPU oracle, as it stands, on one large scene: one step takes minutes, so the
+    first step is timed at 1 and at 4 ADMM iterations; their difference gives the time per
+    iteration, the rest the per-step assembly and factorisation; the rate is extrapolated
+    to the GPU run's mean iterations per step."""
+    import oracle
+    import scenegen as sg
+    times = {}
+    for k in (1, 4):
+        p = sg.fem_beam(seed=0, h=h, tol_primal=-1, max_iters=k)
+        o = oracle.OracleScene(p.scenes[0], p.options)
+        t0 = time.perf_counter()
+        o.step()
+        times[k] = time.perf_counter() - t0
+    per_iter = (times[4] - times[1]) / 3.0
+    setup = times[1] - per_iter
+    step_s = setup + per_iter * mean_iters
+    return {"value": 1.0 / step_s, "unit": "steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"first step at 1 and 4 iterations ({times[1]:.1f} s, {times[4]:.1f} s): "
+                      f"{setup:.1f} s assembly and factorisation + {per_iter * 1e3:.0f} ms per "
+                      f"iteration, extrapolated to {mean_iters:.0f} iterations per step; "
+                      f"single-threaded plain C -O2",
+            "seconds": times[1] + times[4]}
+
+
 def run_reference(args, rank: int, world: int):
     """The reference arm: the FP64 CPU oracle, as it stands, on the same workload (rank 0
     only); for a batch larger than ``--reference-scenes`` a prefix of that many scenes is
@@ -217,6 +251,19 @@ def run_reference(args, rank: int, world: int):
         return 0
     import oracle
     h = 2e-3 if args.workload == "robots" else 1e-3
+    if args.workload == "fem_beam":
+        cb = cpu_baseline_one_scene(args, h, 500.0)
+        line = {"metric": METRIC, "value": cb["value"], "unit": "steps/s", "n_gpus": world,
+                "steps": 1, "warmup": 0, "ms_per_step": 1e3 / cb["value"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "impl": "reference",
+                "config": {"workload": workload_desc(args.robots, h, args.workload),
+                           "form": "FP64 CPU oracle"},
+                "cpu_baseline": cb,
+                "e2e": {"value": cb["value"], "unit": "steps/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return 0
     p = batch_for_rank(0, args.robots, h, args.workload, args.scenes)
     n_all = len(p.scenes)
     scs = [oracle.OracleScene(sc, p.options) for sc in p.scenes[:args.reference_scenes]]
@@ -257,6 +304,8 @@ def batch_for_rank(rank: int, n_robots: int, h: float, workload: str = "robots",
     import scenegen as sg
     if workload == "batched":
         return sg.batched(seed=rank, n_scenes=scenes, h=h, tol_primal=1e-6, max_iters=1000)
+    if workload == "fem_beam":
+        return sg.fem_beam(seed=rank, h=h, tol_primal=1e-6, max_iters=1000)
     return sg.robots(seed=rank, n_robots=n_robots, h=h, tol_primal=1e-6, max_iters=1000)
 
 
@@ -318,9 +367,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--robots", type=int, default=64)
-    ap.add_argument("--workload", default="robots", choices=["robots", "batched"],
+    ap.add_argument("--workload", default="robots", choices=["robots", "batched", "fem_beam"],
                     help="robots: 64 legged robots (the headline workload); batched: many "
-                         "uneven scenes of rigid chains and spring blocks in one launch")
+                         "uneven scenes of rigid chains and spring blocks in one launch; "
+                         "fem_beam: one tetrahedral FEM beam of 64 slabs held by a 7-R arm")
     ap.add_argument("--scenes", type=int, default=4096, help="scenes of the batched workload")
     ap.add_argument("--reference-scenes", type=int, default=64,
                     help="scenes the reference arm steps (a prefix of the batch)")
@@ -378,13 +428,28 @@ def main():
     else:
         peak, pipe = FP64_NOMINAL_TFLOPS, "FP64"
     spl = max(1, min(args.steps_per_launch, K))
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": recorded_traffic(spl),
-                "note": f"{pipe} non-tensor pipe (iterations; the mixed form's per-step setup "
-                        f"is FP64); peak = 152 SMs x lanes x 2 flops x 2.07 GHz; algorithmic "
-                        f"flops of the triangular-solve form, "
-                        f"{it_flops.mean():.0f} per scene-iteration (mean over scenes) and "
-                        f"{st_flops / len(p.scenes):.0f} per scene-step"}
+    if args.workload == "fem_beam":
+        # one scene over the whole GPU: every iteration streams each subsystem's D (m_i x m_i)
+        # from HBM (125 MB in FP32, more than L2 holds), so the bound is HBM bandwidth
+        tsize = 4 if args.form == "mixed" else 8
+        d_bytes = float(sum(w[2] for w in work)) * tsize
+        hbm = measured_peaks().get("hbm_gbs")
+        achieved_gbs = d_bytes * total_iters / (t_ms / 1e3) / 1e9
+        roofline = {"bound": "hbm", "achieved": achieved_gbs,
+                    "peak": hbm if hbm else 6800.0, "unit": "GB/s",
+                    "frac": achieved_gbs / (hbm if hbm else 6800.0), "traffic": None,
+                    "note": f"algorithmic bytes: D of every subsystem once per iteration "
+                            f"({d_bytes / 1e6:.1f} MB) x iterations / whole-step time (setup and "
+                            f"exit included, so a lower bound on the stream rate); peak = "
+                            f"{'measured copy bandwidth' if hbm else 'fallback'}"}
+    else:
+        roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": recorded_traffic(spl),
+                    "note": f"{pipe} non-tensor pipe (iterations; the mixed form's per-step "
+                            f"setup is FP64); peak = 152 SMs x lanes x 2 flops x 2.07 GHz; "
+                            f"algorithmic flops of the triangular-solve form, "
+                            f"{it_flops.mean():.0f} per scene-iteration (mean over scenes) and "
+                            f"{st_flops / len(p.scenes):.0f} per scene-step"}
 
     compare = None
     if not args.no_compare and args.form != "fp64":
@@ -456,8 +521,13 @@ def main():
                           "min": min(launch_ms), "max": max(launch_ms)},
         }
         if not args.no_cpu_baseline and world == 1:
-            line["cpu_baseline"] = cpu_baseline(batch_for_rank(0, args.robots, h, args.workload,
-                                                               args.scenes), args.cpu_seconds)
+            if args.workload == "fem_beam":
+                line["cpu_baseline"] = cpu_baseline_one_scene(
+                    args, h, total_iters / max(stats["scene_steps"], 1))
+            else:
+                line["cpu_baseline"] = cpu_baseline(batch_for_rank(0, args.robots, h,
+                                                                   args.workload, args.scenes),
+                                                    args.cpu_seconds)
         print(json.dumps(line), flush=True)
     sim.close()
     if dist is not None:
