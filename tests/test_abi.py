@@ -1,4 +1,4 @@
-"""The C-ABI library builds, loads and exports every function include/subadmm.h declares.
+"""The C-ABI library builds, loads and exports every function include/*.h declares.
 No compute call is made here (CPU only)."""
 import os
 import re
@@ -27,6 +27,17 @@ def test_library_exports_every_declared_symbol():
     for name in _declared():
         assert hasattr(L, name), name
     assert set(_declared()) == set(subadmm.EXPORTS)
+
+
+def test_library_exports_every_warm_start_network_symbol():
+    from paper_2302_14344_gb300 import subadmm, warmstart
+    txt = open(os.path.join(ROOT, "include", "warmstart.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    names = sorted(set(re.findall(r"\b(wsn_[a-z_]+)\s*\(", txt)))
+    L = subadmm.load()
+    for name in names:
+        assert hasattr(L, name), name
+    assert set(names) == set(warmstart.EXPORTS)
 
 
 def test_default_options_are_the_documented_ones():
