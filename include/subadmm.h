@@ -184,6 +184,44 @@ int sim_step(sim_t s, int n_steps);
 int sim_launch_classes(sim_t s, int max_classes, long long *out);
 int sim_autotune(sim_t s, int steps, int max_classes, long long *out);
 
+/* Learned warm start (a learned counterpart of the previous-step duals of Sec. III-D).
+ * Interfaces are numbered by their public ids (sim_add_interface order); x_dev, t_dev and
+ * mask_dev are device arrays of float, ordered on the simulation's stream.
+ *
+ * sim_interface_features writes 32 features per interface from the current state (the
+ * state a next sim_step starts from): [0:4] projection type one-hot (equality, hard, soft,
+ * contact); [4:7] anchor point of side a minus that of side b (world; the world side is
+ * its anchor, a plane contact's the point's projection on the plane); [7:11] relative
+ * orientation q_a^-1 q_b (w, x, y, z; identity for nodes and the world); [11:14] and
+ * [14:17] anchor velocity and angular velocity of a minus those of b (world); [17:23] the
+ * last step's lambda (first 6 rows); [23:26] the error terms e (first 3 rows); [26] mu;
+ * [27] s = sum of 1/beta over its sides (last step's beta; 0 before the first step); [28]
+ * the contact gap; [29] beta_a / beta_b (1 for one side or before the first step); [30:32]
+ * zero; a non-finite feature is written as 0.  x_dev holds 32 x interfaces floats.
+ *
+ * sim_interface_targets, after a sim_step whose start features are in x_dev, writes the
+ * training targets of each interface: t_dev[7 i + r] = lambda*_r - lambda_prev,r for its
+ * first 6 rows (lambda* the step's final duals, lambda_prev read from the features), 0
+ * elsewhere; mask_dev 1 on those rows and 0 elsewhere (column 6, the network's seventh
+ * output, is unused: beta stays the trace rule of Sec. III-D).
+ *
+ * sim_step_learned runs n_steps steps, each as: features, the network (32 inputs, 7
+ * outputs; see warmstart.h), lambda^0 = lambda_prev + output (first 6 rows of each
+ * interface), and one step started from lambda^0 (z^0 from the previous step).  After 10
+ * iterations a scene compares its residual max(|x - z|, |dz|) with the one its last plain
+ * (previous-step) start had after 10 iterations; if the learned start is behind, the scene
+ * restarts the step from the plain start and records that run's residual as the new
+ * reference; it then starts plain for the next 2^f - 1 steps, f its run of consecutive
+ * fallbacks (at most 5); a kept learned start ends the run.  The iterations of abandoned
+ * learned starts count in sim_iteration_stats.
+ * With sim_use_graph on (and no grid scene), one learned step is captured as a graph after
+ * a first direct step (once per network handle) and replayed n times; the network's
+ * parameters are read at replay time, so training between calls needs no recapture. */
+struct wsn_s;
+int sim_interface_features(sim_t s, float *x_dev);
+int sim_interface_targets(sim_t s, const float *x_dev, float *t_dev, float *mask_dev);
+int sim_step_learned(sim_t s, struct wsn_s *net, int n_steps);
+
 /* Scenes with at least `side_rows` side-rows run on the grid kernel (default 8192).  Must be
  * called before the first sim_step (SIM_EINVAL after it, or for side_rows < 1). */
 int sim_grid_threshold(sim_t s, int side_rows);
@@ -257,10 +295,12 @@ int sim_scene_info(sim_t s, int scene, long long out[4]);
 
 /* Sum and maximum over scenes of the iterations of all steps since the last call, and the
  * number of scene-steps that ended without their stop rule holding; then clears them.
- * out[0] total iterations, out[1] max iterations of a scene-step, out[2] not converged,
- * out[3] scene-steps counted.  per_scene (host memory, may be NULL) receives the same four
- * counts for each scene: 4 x scenes entries, scene k at 4k (its maximum at 4k + 1). */
-int sim_iteration_stats(sim_t s, long long out[4], long long *per_scene);
+ * out[0] total iterations (with those of learned starts that fell back), out[1] max
+ * iterations of a scene-step, out[2] not converged, out[3] scene-steps counted, out[4]
+ * learned starts that fell back to the plain start.  per_scene (host memory, may be NULL)
+ * receives the same five counts for each scene: 5 x scenes entries, scene k at 5k (its
+ * maximum at 5k + 1). */
+int sim_iteration_stats(sim_t s, long long out[5], long long *per_scene);
 
 /* Device-side phase tracer.  Reads the counters accumulated since the last call into out
  * (if out is not NULL; zeros when tracing was off), then turns tracing on (enable != 0, the

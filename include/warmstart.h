@@ -30,6 +30,14 @@ const char *wsn_last_error(wsn_t w);
 /* Number of parameters: sum over layers of in x out + out. */
 long long wsn_num_params(wsn_t w);
 
+/* shape[0] the input width, shape[1] the output width. */
+int wsn_shape(wsn_t w, int shape[2]);
+
+/* Identifies the network's current activation workspace: unique within the process, it
+ * changes whenever a call with a larger batch than before reallocates the workspace.  A
+ * caller that captured wsn_forward into a CUDA graph must recapture when it changes. */
+long long wsn_workspace_generation(wsn_t w);
+
 /* Parameters in layer order: W_1 (in x out, row-major: W[i * out + j] maps input i to
  * output j), b_1, W_2, b_2, ...  Setting also refreshes the BF16 copies and resets Adam. */
 int wsn_set_params(wsn_t w, const float *params);

@@ -69,22 +69,16 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 2) grid_step_kernel(StepParam
             d.sync();
             continue;
         }
-        // initial z, u = -lambda (cold: zeros; warm: the previous step's)
-        for (int r = d.tid; r < S.nrow; r += d.nthreads)
-            LAM[r] = P.warm_prev ? (T)P.lam[S.row_g0 + r] : (T)0;
-        for (int t = d.tid; t < S.nsr; t += d.nthreads) {
-            if (V.mlen[t] == 0) continue;
-            const T beta = BT[t];
-            const T z = P.warm_prev ? (T)P.z[S.sr_g0 + t] : (T)0;
-            const T l = P.warm_prev ? (T)P.lam[S.row_g0 + V.row[t]] : (T)0;
-            Z[t] = z;
-            ZO[t] = z;
-            X[t] = (T)0;
-            Y[t] = beta * z - l;
-            YO[t] = Y[t];
-            W0[t] = beta * z + l;
-        }
+        // initial z, u = -lambda; a learned start is checked after 10 iterations against the
+        // plain start's residual there, and replaced by the plain start if worse
+        const bool learned_mode = P.lam0 != nullptr;
+        const int skip0 = learned_mode ? vload(&P.learn_skip[2 * sc]) : 0;
+        bool learned = learned_mode && skip0 == 0;
+        const unsigned long long ref10 = learned_mode ? vload(&P.ref10[sc]) : 0ull;
+        int wasted = 0, fallbacks = 0;
         d.sync();
+        if (learned_mode && lead && skip0 > 0) P.learn_skip[2 * sc] = skip0 - 1;
+        init_duals<T>(P, S, V, LAM, Z, ZO, X, Y, YO, W0, BT, learned, d);
         pc.mark(PHASE_ASSEMBLE);
 
         constexpr int groups_per_block = SUBADMM_THREADS / SPLIT;
@@ -229,18 +223,20 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 2) grid_step_kernel(StepParam
                 if (P.stop_theta) {
 #pragma unroll
                     for (int o = 16; o; o >>= 1) tpart += __shfl_xor_sync(0xffffffffu, tpart, o);
-                    if (lane == 0 && tpart != (T)0) atomicAdd(&G->theta[l % 3], (double)tpart);
+                    if (lane == 0 && tpart != (T)0) atomicAdd(&G->theta[(l + wasted) % 3], (double)tpart);
                 }
                 d.sync();
                 pc.mark(PHASE_VSTEP);
-                if (lead) {            // the next iteration's slots (last read two iterations ago)
-                    G->umax[(l + 1) % 3] = 0ull;
-                    G->theta[(l + 1) % 3] = 0.0;
+                // slots rotate with the iterations run in this step, restarts included: the
+                // next iteration's slot was last read two barriers ago
+                if (lead) {
+                    G->umax[(l + wasted + 1) % 3] = 0ull;
+                    G->theta[(l + wasted + 1) % 3] = 0.0;
                 }
                 last_par = par;
                 iters = l + 1;
                 if (P.stop_theta) {
-                    const double ths = vload(&G->theta[l % 3]);
+                    const double ths = vload(&G->theta[(l + wasted) % 3]);
                     if (l >= 1 && (T)ths < theta_thT) { th = ths; conv = 1; break; }
                 }
                 // ---- z-step (Sec. III-C); u = -lambda; max(|x - z|, |dz|) as bits
@@ -305,11 +301,29 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 2) grid_step_kernel(StepParam
                     }
                 }
                 mloc = warp_umax(mloc);
-                if (lane == 0 && mloc) atomicMax(&G->umax[l % 3], (unsigned long long)mloc);
+                if (lane == 0 && mloc) atomicMax(&G->umax[(l + wasted) % 3], (unsigned long long)mloc);
                 d.sync();
-                const U mx = (U)vload(&G->umax[l % 3]);
+                const U mx = (U)vload(&G->umax[(l + wasted) % 3]);
                 par ^= 1;
                 pc.mark(PHASE_ZSTEP);
+                if (learned_mode && l == 9) {
+                    if (learned && (unsigned long long)mx > ref10) {
+                        if (lead) {
+                            const int streak = min(P.learn_skip[2 * sc + 1] + 1, 5);
+                            P.learn_skip[2 * sc + 1] = streak;
+                            P.learn_skip[2 * sc] = (1 << streak) - 1;
+                        }
+                        learned = false;
+                        ++fallbacks;
+                        wasted += l + 1;
+                        init_duals<T>(P, S, V, LAM, Z, ZO, X, Y, YO, W0, BT, false, d);
+                        par = 0;
+                        l = -1;
+                        continue;
+                    }
+                    if (!learned && lead) P.ref10[sc] = (unsigned long long)mx;
+                    if (learned && lead) P.learn_skip[2 * sc + 1] = 0;
+                }
                 if (mx >= inf_bits(T(0))) { status = ST_NAN; break; }
                 if (primal_stop && mx <= tolb) { conv = 1; break; }
             }
@@ -401,11 +415,12 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 2) grid_step_kernel(StepParam
             double *o = P.res + 6 * sc;
             o[0] = rp; o[1] = rd; o[2] = th; o[3] = (double)iters; o[4] = (double)conv;
             o[5] = (double)status;
-            long long *st = P.stats + 4 * sc;
-            st[0] += iters;
-            if (iters > st[1]) st[1] = iters;
+            long long *st = P.stats + 5 * sc;
+            st[0] += iters + wasted;
+            if (iters + wasted > st[1]) st[1] = iters + wasted;
             st[2] += conv ? 0 : 1;
             st[3] += 1;
+            st[4] += fallbacks;
         }
     }
 }

@@ -125,10 +125,15 @@ struct StepParams {
     int *subflag;          // per subsystem: bit 0 its kept factor is valid, bit 1 it is FP64
     double *vhat;          // per DOF
     double *lam;           // per row: lambda of the last step (warm start state)
+    const double *lam0;    // per row: learned initial lambda of this step (NULL: not learned)
+    unsigned long long *ref10;   // per scene: bits of the residual after 10 iterations of the
+                                 // last plain start (the learned start's reference)
+    int *learn_skip;       // per scene: steps left to start plain, and the fallback streak
     double *z;             // per side-row: z of the last step (warm start state)
     double *beta;          // per subsystem
     double *res;           // 6 per scene
-    long long *stats;      // 4 per scene: sum iters, max iters, not converged, steps
+    long long *stats;      // 5 per scene: sum iters, max iters, not converged, steps,
+                           // fallbacks of the learned start
     long long *phase;      // 8 per scene (or null): SM clock cycles per phase, see PHASE_*
     GridScratch *grid;     // grid kernel scratch
     int nscenes;           // scenes of this launch

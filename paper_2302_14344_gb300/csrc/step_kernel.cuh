@@ -831,6 +831,32 @@ __device__ void recover_v(const StepParams &P, const SceneDesc &S, const View<T>
     }
 }
 
+// Initial z and u = -lambda of a step (Algorithm 1, before the loop): cold (zeros), warm
+// from the previous step's lambda and z, or from the learned initial lambda (z from the
+// previous step); y^0 = beta z^0 + u^0 and w^0 = beta z^0 - u^0.
+template <typename T, typename Dist>
+__device__ void init_duals(const StepParams &P, const SceneDesc &S, const View<T> &V, T *LAM,
+                           T *Z, T *ZO, T *X, T *Y, T *YO, T *W0, const T *BT, bool learned,
+                           const Dist &d)
+{
+    const double *lam = learned ? P.lam0 : P.lam;
+    const bool warm = learned || P.warm_prev;
+    for (int r = d.tid; r < S.nrow; r += d.nthreads) LAM[r] = warm ? (T)lam[S.row_g0 + r] : (T)0;
+    for (int t = d.tid; t < S.nsr; t += d.nthreads) {
+        if (V.mlen[t] == 0) continue;                 // padding side-row
+        const T beta = BT[t];
+        const T z = warm ? (T)P.z[S.sr_g0 + t] : (T)0;
+        const T l = warm ? (T)lam[S.row_g0 + V.row[t]] : (T)0;
+        Z[t] = z;
+        ZO[t] = z;
+        X[t] = (T)0;
+        Y[t] = beta * z - l;
+        YO[t] = Y[t];
+        W0[t] = beta * z + l;
+    }
+    d.sync();
+}
+
 // One z-step item held in a thread's registers for a whole step (items with at most two
 // sides): its type, row, side-rows and the step's constants.  KEEP_Z: the z of its
 // side-rows (the item is their only writer) and the previous z stay in registers until
@@ -1023,22 +1049,16 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, CACHED ? 1 : 2) step_kernel(S
                 __syncthreads();
                 continue;
             }
-            // initial z, u = -lambda (cold: zeros; warm: the previous step's)
-            for (int r = tid; r < S.nrow; r += blockDim.x)
-                LAM[r] = P.warm_prev ? (T)P.lam[S.row_g0 + r] : (T)0;
-            for (int t = tid; t < S.nsr; t += blockDim.x) {
-                if (V.mlen[t] == 0) continue;                 // padding side-row
-                const T beta = BT[t];
-                const T z = P.warm_prev ? (T)P.z[S.sr_g0 + t] : (T)0;
-                const T l = P.warm_prev ? (T)P.lam[S.row_g0 + V.row[t]] : (T)0;
-                Z[t] = z;
-                ZO[t] = z;
-                X[t] = (T)0;
-                Y[t] = beta * z - l;           // y^0 = beta z^0 + u^0
-                YO[t] = Y[t];
-                W0[t] = beta * z + l;          // w^0 = beta z^0 - u^0
-            }
+            // initial z, u = -lambda; a learned start is checked after 10 iterations against
+            // the plain start's residual there, and replaced by the plain start if worse
+            const bool learned_mode = P.lam0 != nullptr;
+            const int skip0 = learned_mode ? P.learn_skip[2 * sc] : 0;
+            bool learned = learned_mode && skip0 == 0;
+            const unsigned long long ref10 = learned_mode ? P.ref10[sc] : 0ull;
+            int wasted = 0, fallbacks = 0;
             __syncthreads();
+            if (learned_mode && tid == 0 && skip0 > 0) P.learn_skip[2 * sc] = skip0 - 1;
+            init_duals<T>(P, S, V, LAM, Z, ZO, X, Y, YO, W0, BT, learned, BlockDist());
 
             // ---- per-thread cache of the step's coefficients (CACHED: one side-row group
             // and one z-step item per thread, items with at most two sides)
@@ -1052,24 +1072,28 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, CACHED ? 1 : 2) step_kernel(S
             int xdro = 0, xwbo = 0, xnv = 0, xrow = 0;
             T xc = (T)0, xbt = (T)0, yreg = (T)0, yprev = (T)0;
             RegItem<T> ri;
-            if (CACHED) {
-                if (xt < S.nsr && V.mlen[xt] > 0) {
-                    xv = true;
-                    xdro = V.drow[xt];
-                    xwbo = V.wbase[xt];
-                    xnv = (V.mlen[xt] + VN - 1) / VN;
-                    xrow = V.row[xt];
-                    xc = V.htb[V.coff[xt]];
-                    xbt = BT[xt];
-                    yreg = Y[xt];
-                    yprev = yreg;
-                    const VT *Dr = reinterpret_cast<const VT *>(V.htb + xdro);
+            auto load_cache = [&]() {
+                if (CACHED) {
+                    if (xt < S.nsr && V.mlen[xt] > 0) {
+                        xv = true;
+                        xdro = V.drow[xt];
+                        xwbo = V.wbase[xt];
+                        xnv = (V.mlen[xt] + VN - 1) / VN;
+                        xrow = V.row[xt];
+                        xc = V.htb[V.coff[xt]];
+                        xbt = BT[xt];
+                        yreg = Y[xt];
+                        yprev = yreg;
+                        const VT *Dr = reinterpret_cast<const VT *>(V.htb + xdro);
 #pragma unroll
-                    for (int q = 0; q < MAXC; ++q)
-                        if (xgl + q * SPLIT < xnv) dreg[q] = Dr[xgl + q * SPLIT];
+                        for (int q = 0; q < MAXC; ++q)
+                            if (xgl + q * SPLIT < xnv) dreg[q] = Dr[xgl + q * SPLIT];
+                    }
+                    ri = RegItem<T>();
+                    if (tid < S.nitem) ri.load(V.item, V.list, tid, INVB, E, INVS, KF, AL, MU, Z);
                 }
-                if (tid < S.nitem) ri.load(V.item, V.list, tid, INVB, E, INVS, KF, AL, MU, Z);
-            }
+            };
+            load_cache();
 
             int par = 0, last_par = 0, iters = 0, conv = 0, status = ST_OK;
             double th = 0.0;
@@ -1250,6 +1274,27 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, CACHED ? 1 : 2) step_kernel(S
                     for (int q = 0; q < SUBADMM_WARPS; ++q) mx = umax(mx, ured[l & 1][q]);
                     par ^= 1;
                     pc.mark(PHASE_ZSTEP);
+                    if (learned_mode && l == 9) {
+                        if (learned && (unsigned long long)mx > ref10) {
+                            // the learned start trails the plain one: restart from the plain,
+                            // and start plain for the next 2^streak - 1 steps
+                            if (tid == 0) {
+                                const int streak = min(P.learn_skip[2 * sc + 1] + 1, 5);
+                                P.learn_skip[2 * sc + 1] = streak;
+                                P.learn_skip[2 * sc] = (1 << streak) - 1;
+                            }
+                            learned = false;
+                            ++fallbacks;
+                            wasted += l + 1;
+                            init_duals<T>(P, S, V, LAM, Z, ZO, X, Y, YO, W0, BT, false, BlockDist());
+                            load_cache();
+                            par = 0;
+                            l = -1;
+                            continue;
+                        }
+                        if (!learned && tid == 0) P.ref10[sc] = (unsigned long long)mx;
+                        if (learned && tid == 0) P.learn_skip[2 * sc + 1] = 0;   // kept: streak ends
+                    }
                     if (mx >= inf_bits(T(0))) { status = ST_NAN; break; }
                     if (primal_stop && mx <= tolb) { conv = 1; break; }
                 }
@@ -1335,11 +1380,12 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, CACHED ? 1 : 2) step_kernel(S
                 double *o = P.res + 6 * sc;
                 o[0] = rp; o[1] = rd; o[2] = th; o[3] = (double)iters; o[4] = (double)conv;
                 o[5] = (double)status;
-                long long *st = P.stats + 4 * sc;
-                st[0] += iters;
-                if (iters > st[1]) st[1] = iters;
+                long long *st = P.stats + 5 * sc;
+                st[0] += iters + wasted;
+                if (iters + wasted > st[1]) st[1] = iters + wasted;
                 st[2] += conv ? 0 : 1;
                 st[3] += 1;
+                st[4] += fallbacks;
             }
             __syncthreads();
         }

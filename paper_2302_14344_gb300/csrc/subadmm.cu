@@ -15,6 +15,8 @@
 #include "layout.h"
 #include "step_kernel.cuh"
 #include "grid_kernel.cuh"
+#include "features.cuh"
+#include "warmstart.h"
 
 namespace {
 
@@ -86,6 +88,13 @@ struct sim_s {
     std::vector<LaunchClass> classes;
     int *d_scene_ids = nullptr;    // every class's scene list, concatenated
     GridScratch *d_grid = nullptr; // grid kernel scratch
+    // learned warm start: interface maps, the residual reference per scene, buffers
+    int *d_pub2dev = nullptr;      // public interface id -> device constraint
+    int *d_con_scene = nullptr;    // device constraint -> scene
+    unsigned long long *d_ref10 = nullptr;
+    int *d_learn_skip = nullptr;   // per scene: plain steps left, fallback streak
+    double *d_lam0 = nullptr;      // learned initial lambda per row
+    float *d_feat = nullptr, *d_netout = nullptr;
     cudaEvent_t ev_fork = nullptr;
     int split_override = 0;        // tuning: force the split of every class (0: heuristic)
     std::vector<int> sc_nsr, sc_items, sc_sides, sc_mpad;   // per scene: register-cache limits
@@ -95,6 +104,9 @@ struct sim_s {
     bool use_graph = false;
     int graph_steps = 0;
     cudaGraphExec_t graph = nullptr;
+    cudaGraphExec_t graph_learned = nullptr;   // one learned step, captured for one network
+    void *graph_learned_net = nullptr;
+    long long graph_learned_ws = -1;           // the network workspace it was captured with
     cudaStream_t graph_stream = nullptr;   // capture and replay stream when the simulation's
                                            // stream is the legacy default stream
     double *d_pool = nullptr, *d_bodies = nullptr, *d_vhat = nullptr, *d_lam = nullptr;
@@ -200,6 +212,11 @@ void free_device(sim_t s)
     s->d_scene_ids = nullptr;
     cudaFree(s->d_grid);
     s->d_grid = nullptr;
+    cudaFree(s->d_pub2dev); cudaFree(s->d_con_scene); cudaFree(s->d_ref10); cudaFree(s->d_learn_skip);
+    s->d_learn_skip = nullptr;
+    cudaFree(s->d_lam0); cudaFree(s->d_feat); cudaFree(s->d_netout);
+    s->d_pub2dev = nullptr; s->d_con_scene = nullptr; s->d_ref10 = nullptr;
+    s->d_lam0 = nullptr; s->d_feat = nullptr; s->d_netout = nullptr;
     for (auto &c : s->classes) {
         if (c.stream) cudaStreamDestroy(c.stream);
         if (c.done) cudaEventDestroy(c.done);
@@ -210,6 +227,9 @@ void free_device(sim_t s)
     if (s->graph) cudaGraphExecDestroy(s->graph);
     s->graph = nullptr;
     s->graph_steps = 0;
+    if (s->graph_learned) cudaGraphExecDestroy(s->graph_learned);
+    s->graph_learned = nullptr;
+    s->graph_learned_net = nullptr;
     if (s->graph_stream) cudaStreamDestroy(s->graph_stream);
     s->graph_stream = nullptr;
     s->d_nodes = nullptr; s->d_ipool = nullptr; s->d_subflag = nullptr;
@@ -680,6 +700,21 @@ int finalize(sim_t s)
         if (rc2) return rc2;
         cudaError_t e = cudaMalloc((void **)&s->d_grid, sizeof(GridScratch));
         if (e != cudaSuccess) return fail(s, SIM_ENOMEM, "cudaMalloc grid scratch");
+        std::vector<int> con_scene(std::max(ncons, 1), 0);
+        for (int sc = 0; sc < nscenes; ++sc)
+            for (int j = 0; j < s->scenes[sc].ncon; ++j) con_scene[s->scenes[sc].con0 + j] = sc;
+        std::vector<int> pub2dev(s->con_dev.begin(), s->con_dev.end());
+        if (pub2dev.empty()) pub2dev.push_back(0);
+        if ((rc2 = upload(s, &s->d_con_scene, con_scene, "interface scenes"))) return rc2;
+        if ((rc2 = upload(s, &s->d_pub2dev, pub2dev, "interface map"))) return rc2;
+        e = cudaMalloc((void **)&s->d_ref10, sizeof(unsigned long long) * std::max(1, nscenes));
+        if (e != cudaSuccess) return fail(s, SIM_ENOMEM, "cudaMalloc residual references");
+        CK(cudaMemsetAsync(s->d_ref10, 0, sizeof(unsigned long long) * std::max(1, nscenes), s->stream),
+           "memset references");
+        e = cudaMalloc((void **)&s->d_learn_skip, sizeof(int) * 2 * std::max(1, nscenes));
+        if (e != cudaSuccess) return fail(s, SIM_ENOMEM, "cudaMalloc learned-start state");
+        CK(cudaMemsetAsync(s->d_learn_skip, 0, sizeof(int) * 2 * std::max(1, nscenes), s->stream),
+           "memset learned-start state");
         CK(cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming), "event");
         for (size_t k = 0; k < s->classes.size(); ++k) {
             LaunchClass &c = s->classes[k];
@@ -719,9 +754,9 @@ int finalize(sim_t s)
     if ((rc = zeros(s, &s->d_res, (size_t)6 * nscenes, "residuals"))) return rc;
     if ((rc = zeros(s, &s->d_stage, (size_t)state_doubles(s), "state staging"))) return rc;
     {
-        cudaError_t e = cudaMalloc((void **)&s->d_stats, std::max(1, 4 * nscenes) * sizeof(long long));
+        cudaError_t e = cudaMalloc((void **)&s->d_stats, std::max(1, 5 * nscenes) * sizeof(long long));
         if (e != cudaSuccess) return fail(s, SIM_ENOMEM, "cudaMalloc stats");
-        CK(cudaMemsetAsync(s->d_stats, 0, std::max(1, 4 * nscenes) * sizeof(long long), s->stream), "memset stats");
+        CK(cudaMemsetAsync(s->d_stats, 0, std::max(1, 5 * nscenes) * sizeof(long long), s->stream), "memset stats");
     }
     s->finalized = true;
     return SIM_OK;
@@ -1000,6 +1035,9 @@ StepParams step_params(const sim_t s, int n_steps)
     P.asm_order = s->d_asm;
     P.scene_ids = s->d_scene_ids;
     P.grid = s->d_grid;
+    P.lam0 = nullptr;
+    P.ref10 = s->d_ref10;
+    P.learn_skip = s->d_learn_skip;
     return P;
 }
 
@@ -1144,6 +1182,11 @@ int sim_use_graph(sim_t s, int enable)
         s->graph = nullptr;
         s->graph_steps = 0;
     }
+    if (!s->use_graph && s->graph_learned) {
+        cudaGraphExecDestroy(s->graph_learned);
+        s->graph_learned = nullptr;
+        s->graph_learned_net = nullptr;
+    }
     return SIM_OK;
 }
 
@@ -1200,7 +1243,9 @@ int sim_autotune(sim_t s, int steps, int max_classes, long long *out)
         {s->d_z, sizeof(double) * (size_t)s->nsr},
         {s->d_beta, sizeof(double) * nsub},
         {s->d_res, sizeof(double) * 6 * (size_t)s->nscenes},
-        {s->d_stats, sizeof(long long) * 4 * (size_t)s->nscenes},
+        {s->d_stats, sizeof(long long) * 5 * (size_t)s->nscenes},
+        {s->d_ref10, sizeof(unsigned long long) * (size_t)s->nscenes},
+        {s->d_learn_skip, sizeof(int) * 2 * (size_t)s->nscenes},
         {s->d_subflag, sizeof(int) * nsub},
         {s->d_phase, s->d_phase ? sizeof(long long) * 8 * (size_t)s->nscenes : 0}};
     size_t total = 0;
@@ -1295,8 +1340,143 @@ int sim_autotune(sim_t s, int steps, int max_classes, long long *out)
         s->graph = nullptr;
         s->graph_steps = 0;
     }
+    if (s->graph_learned) {
+        cudaGraphExecDestroy(s->graph_learned);
+        s->graph_learned = nullptr;
+        s->graph_learned_net = nullptr;
+    }
     class_rows(s, max_classes, out, &best_ns);
     return (int)s->classes.size();
+}
+
+namespace {
+
+int interface_buffers(sim_t s)
+{
+    const size_t nif = std::max<size_t>(1, s->cons.size());
+    if (!s->d_feat) {
+        cudaError_t e = cudaMalloc((void **)&s->d_feat, sizeof(float) * nif * subadmm::kFeatures);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&s->d_netout, sizeof(float) * nif * subadmm::kDualOut);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&s->d_lam0, sizeof(double) * std::max<long long>(1, s->nrows));
+        if (e != cudaSuccess) return fail(s, SIM_ENOMEM, "cudaMalloc warm-start buffers");
+    }
+    return SIM_OK;
+}
+
+int grid_of(size_t n) { return (int)std::max<size_t>(1, std::min<size_t>((n + 127) / 128, 4096)); }
+
+}  // namespace
+
+int sim_interface_features(sim_t s, float *x_dev)
+{
+    if (!s || !x_dev) return SIM_EINVAL;
+    int rc = finalize(s);
+    if (rc) return rc;
+    const int nif = (int)s->cons.size();
+    if (nif == 0) return SIM_OK;
+    CK(cudaSetDevice(s->opt.device), "cudaSetDevice");
+    subadmm::interface_features_kernel<<<grid_of(nif), 128, 0, s->stream>>>(
+        step_params(s, 1), s->d_pub2dev, s->d_con_scene, nif, x_dev);
+    CK(cudaGetLastError(), "features launch");
+    return SIM_OK;
+}
+
+int sim_interface_targets(sim_t s, const float *x_dev, float *t_dev, float *mask_dev)
+{
+    if (!s || !x_dev || !t_dev || !mask_dev) return SIM_EINVAL;
+    if (!s->finalized) return fail(s, SIM_EINVAL, "no step has run");
+    const int nif = (int)s->cons.size();
+    if (nif == 0) return SIM_OK;
+    CK(cudaSetDevice(s->opt.device), "cudaSetDevice");
+    subadmm::interface_targets_kernel<<<grid_of(nif), 128, 0, s->stream>>>(
+        step_params(s, 1), s->d_pub2dev, s->d_con_scene, nif, x_dev, t_dev, mask_dev);
+    CK(cudaGetLastError(), "targets launch");
+    return SIM_OK;
+}
+
+int sim_step_learned(sim_t s, wsn_t net, int n_steps)
+{
+    if (!s || !net) return SIM_EINVAL;
+    if (n_steps < 1) return fail(s, SIM_EINVAL, "n_steps must be >= 1");
+    int shape[2] = {0, 0};
+    if (wsn_shape(net, shape) || shape[0] != subadmm::kFeatures || shape[1] != subadmm::kDualOut)
+        return fail(s, SIM_EINVAL, "the network must map 32 features to 7 outputs");
+    int rc = finalize(s);
+    if (rc) return rc;
+    if (s->nscenes == 0) return SIM_OK;
+    if ((rc = interface_buffers(s))) return rc;
+    CK(cudaSetDevice(s->opt.device), "cudaSetDevice");
+    const int nif = (int)s->cons.size();
+    StepParams P = step_params(s, 1);
+    for (const LaunchClass &c : s->classes)
+        CK(cudaFuncSetAttribute(kernel_for(s->opt.precision == SIM_MIXED, c.cached, c.split),
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, s->smem_full),
+           "shared memory attribute");
+    // one learned step: features, the network, lambda^0, the step's launches
+    auto enqueue = [&](cudaStream_t st) -> int {
+        if (nif > 0) {
+            subadmm::interface_features_kernel<<<grid_of(nif), 128, 0, st>>>(
+                P, s->d_pub2dev, s->d_con_scene, nif, s->d_feat);
+            CK(cudaGetLastError(), "features launch");
+            const int r = wsn_forward(net, s->d_feat, subadmm::kFeatures, nif, s->d_netout, st);
+            if (r) return fail(s, r, std::string("network: ") + wsn_last_error(net));
+            subadmm::learned_duals_kernel<<<grid_of(nif), 128, 0, st>>>(
+                P, s->d_pub2dev, s->d_con_scene, nif, s->d_netout, s->d_lam0);
+            CK(cudaGetLastError(), "learned duals launch");
+        }
+        StepParams Q = P;
+        Q.lam0 = nif > 0 ? s->d_lam0 : nullptr;
+        return launch_classes(s, Q, st);
+    };
+    bool has_grid = false;
+    for (const LaunchClass &c : s->classes) has_grid = has_grid || c.grid;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(s->stream, &cs), "capture status");
+    if (!s->use_graph || has_grid || cs != cudaStreamCaptureStatusNone) {
+        for (int k = 0; k < n_steps; ++k)
+            if ((rc = enqueue(s->stream))) return rc;
+        return SIM_OK;
+    }
+    // graph replay: capture one learned step once per network (the network's workspace is
+    // reserved by a first direct step, so the capture allocates nothing)
+    cudaStream_t gs = s->stream;
+    if (!gs) {
+        if (!s->graph_stream) CK(cudaStreamCreate(&s->graph_stream), "graph stream");
+        gs = s->graph_stream;
+    }
+    int k = 0;
+    // the direct first step reserves the network's workspace for this batch
+    if (!s->graph_learned || s->graph_learned_net != (void *)net ||
+        s->graph_learned_ws != wsn_workspace_generation(net)) {
+        if (s->graph_learned) cudaGraphExecDestroy(s->graph_learned);
+        s->graph_learned = nullptr;
+        if ((rc = enqueue(s->stream))) return rc;
+        ++k;
+        if (gs != s->stream) {
+            CK(cudaEventRecord(s->ev_fork, s->stream), "graph fork");
+            CK(cudaStreamWaitEvent(gs, s->ev_fork, 0), "graph fork wait");
+        }
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal), "begin capture");
+        const int lrc = enqueue(gs);
+        cudaError_t ec = cudaStreamEndCapture(gs, &g);
+        if (lrc) { if (g) cudaGraphDestroy(g); return lrc; }
+        CK(ec, "end capture");
+        cudaError_t ei = cudaGraphInstantiate(&s->graph_learned, g, 0);
+        cudaGraphDestroy(g);
+        CK(ei, "graph instantiate");
+        s->graph_learned_net = (void *)net;
+        s->graph_learned_ws = wsn_workspace_generation(net);
+    } else if (gs != s->stream) {
+        CK(cudaEventRecord(s->ev_fork, s->stream), "graph fork");
+        CK(cudaStreamWaitEvent(gs, s->ev_fork, 0), "graph fork wait");
+    }
+    for (; k < n_steps; ++k) CK(cudaGraphLaunch(s->graph_learned, gs), "graph launch");
+    if (gs != s->stream) {
+        CK(cudaEventRecord(s->ev_fork, gs), "graph join");
+        CK(cudaStreamWaitEvent(s->stream, s->ev_fork, 0), "graph join wait");
+    }
+    return SIM_OK;
 }
 
 int sim_grid_threshold(sim_t s, int side_rows)
@@ -1512,22 +1692,23 @@ int sim_scene_info(sim_t s, int scene, long long out[4])
     return SIM_OK;
 }
 
-int sim_iteration_stats(sim_t s, long long out[4], long long *per_scene)
+int sim_iteration_stats(sim_t s, long long out[5], long long *per_scene)
 {
     if (!s || !out) return SIM_EINVAL;
     if (!s->finalized) return fail(s, SIM_EINVAL, "no step has run");
     CK(cudaStreamSynchronize(s->stream), "stream synchronize");
-    std::vector<long long> st((size_t)4 * std::max(1, s->nscenes));
-    CK(cudaMemcpy(st.data(), s->d_stats, sizeof(long long) * 4 * s->nscenes, cudaMemcpyDeviceToHost), "stats");
-    out[0] = out[1] = out[2] = out[3] = 0;
+    std::vector<long long> st((size_t)5 * std::max(1, s->nscenes));
+    CK(cudaMemcpy(st.data(), s->d_stats, sizeof(long long) * 5 * s->nscenes, cudaMemcpyDeviceToHost), "stats");
+    out[0] = out[1] = out[2] = out[3] = out[4] = 0;
     for (int k = 0; k < s->nscenes; ++k) {
-        out[0] += st[4 * k];
-        out[1] = std::max(out[1], st[4 * k + 1]);
-        out[2] += st[4 * k + 2];
-        out[3] += st[4 * k + 3];
+        out[0] += st[5 * k];
+        out[1] = std::max(out[1], st[5 * k + 1]);
+        out[2] += st[5 * k + 2];
+        out[3] += st[5 * k + 3];
+        out[4] += st[5 * k + 4];
     }
-    if (per_scene) std::copy(st.begin(), st.begin() + 4 * (size_t)s->nscenes, per_scene);
-    CK(cudaMemset(s->d_stats, 0, sizeof(long long) * 4 * s->nscenes), "stats clear");
+    if (per_scene) std::copy(st.begin(), st.begin() + 5 * (size_t)s->nscenes, per_scene);
+    CK(cudaMemset(s->d_stats, 0, sizeof(long long) * 5 * s->nscenes), "stats clear");
     return SIM_OK;
 }
 
@@ -1548,11 +1729,14 @@ int sim_phase_trace(sim_t s, int enable, long long out[8])
         }
     }
     // a captured graph holds the tracer pointer of its capture: capture again
-    if (s->graph) {
+    if (s->graph || s->graph_learned) {
         CK(cudaStreamSynchronize(s->stream), "stream synchronize");
-        cudaGraphExecDestroy(s->graph);
+        if (s->graph) cudaGraphExecDestroy(s->graph);
+        if (s->graph_learned) cudaGraphExecDestroy(s->graph_learned);
         s->graph = nullptr;
         s->graph_steps = 0;
+        s->graph_learned = nullptr;
+        s->graph_learned_net = nullptr;
     }
     if (enable && !s->d_phase) {
         cudaError_t e = cudaMalloc((void **)&s->d_phase, bytes);

@@ -4,6 +4,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <string>
 #include <vector>
@@ -21,8 +22,10 @@ struct wsn_s {
     __nv_bfloat16 *pb = nullptr;       // BF16 copy of the params
     float *mean = nullptr, *inv_std = nullptr, *scale = nullptr;
     int step = 0;
-    // workspace for `cap` rows
+    // workspace for `cap` rows; its generation is unique in the process and changes with
+    // every reallocation (captured graphs that use the workspace check it)
     int cap = 0;
+    long long ws_gen = 0;
     std::vector<__nv_bfloat16 *> act;  // act[l]: input of layer l (B x sizes[l])
     std::vector<float *> pre;          // pre[l]: pre-activation of hidden layer l (B x sizes[l+1])
     float *y = nullptr;                // network output (B x out)
@@ -31,6 +34,8 @@ struct wsn_s {
 };
 
 namespace {
+
+std::atomic<long long> g_ws_generation{0};
 
 int werr(wsn_t w, int code, const std::string &msg)
 {
@@ -76,6 +81,7 @@ int reserve(wsn_t w, int batch)
     WCK(cudaMalloc((void **)&w->g0, sizeof(__nv_bfloat16) * (size_t)cap * wmax), "cudaMalloc");
     WCK(cudaMalloc((void **)&w->g1, sizeof(__nv_bfloat16) * (size_t)cap * wmax), "cudaMalloc");
     w->cap = cap;
+    w->ws_gen = ++g_ws_generation;
     return SIM_OK;
 }
 
@@ -210,6 +216,16 @@ void wsn_destroy(wsn_t w)
 const char *wsn_last_error(wsn_t w) { return w ? w->err.c_str() : ""; }
 
 long long wsn_num_params(wsn_t w) { return w ? w->nparams : -1; }
+
+long long wsn_workspace_generation(wsn_t w) { return w ? w->ws_gen : -1; }
+
+int wsn_shape(wsn_t w, int shape[2])
+{
+    if (!w || !shape) return SIM_EINVAL;
+    shape[0] = w->sizes.front();
+    shape[1] = w->sizes.back();
+    return SIM_OK;
+}
 
 int wsn_set_params(wsn_t w, const float *params)
 {

@@ -32,7 +32,8 @@ EXPORTS = ("sim_default_options", "sim_create", "sim_destroy", "sim_add_subsyste
            "sim_add_interface", "sim_set_generic", "sim_step", "sim_residuals", "sim_get",
            "sim_read_state", "sim_read_state_noalloc", "sim_write_state", "sim_sizes",
            "sim_iteration_stats", "sim_scene_info", "sim_use_graph", "sim_launch_classes",
-           "sim_autotune", "sim_grid_threshold", "sim_probe_barrier",
+           "sim_autotune", "sim_grid_threshold", "sim_probe_barrier", "sim_interface_features",
+           "sim_interface_targets", "sim_step_learned",
            "sim_phase_trace", "sim_sync", "sim_last_error")
 
 
@@ -95,6 +96,9 @@ def load(build_if_missing: bool = True):
             "sim_launch_classes": (C.c_int, [VP, C.c_int, PL]),
             "sim_autotune": (C.c_int, [VP, C.c_int, C.c_int, PL]),
             "sim_grid_threshold": (C.c_int, [VP, C.c_int]),
+            "sim_interface_features": (C.c_int, [VP, VP]),
+            "sim_interface_targets": (C.c_int, [VP, VP, VP, VP]),
+            "sim_step_learned": (C.c_int, [VP, VP, C.c_int]),
             "sim_probe_barrier": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_double, PI]),
             "sim_phase_trace": (C.c_int, [VP, C.c_int, PL]),
             "sim_sync": (C.c_int, [VP]),
@@ -250,18 +254,31 @@ def sim_scene_info(h, scene: int) -> dict:
 
 def sim_iteration_stats(h, per_scene: bool = False) -> dict:
     """Totals since the last call (then cleared); with per_scene, also "per_scene": an
-    array (scenes, 4) of [iterations, max iterations, not converged, scene-steps]."""
-    out = (C.c_longlong * 4)()
+    array (scenes, 5) of [iterations, max iterations, not converged, scene-steps,
+    fallbacks]."""
+    out = (C.c_longlong * 5)()
     ps = None
     if per_scene:
-        ps = np.zeros((sim_sizes(h)["scenes"], 4), dtype=np.int64)
+        ps = np.zeros((sim_sizes(h)["scenes"], 5), dtype=np.int64)
     _check(h, load().sim_iteration_stats(h, out, None if ps is None else
                                          ps.ctypes.data_as(C.POINTER(C.c_longlong))))
     d = dict(total_iters=int(out[0]), max_iters=int(out[1]), not_converged=int(out[2]),
-             scene_steps=int(out[3]))
+             scene_steps=int(out[3]), fallbacks=int(out[4]))
     if ps is not None:
         d["per_scene"] = ps
     return d
+
+
+def sim_interface_features(h, x_ptr: int) -> None:
+    _check(h, load().sim_interface_features(h, VP(x_ptr)))
+
+
+def sim_interface_targets(h, x_ptr: int, t_ptr: int, mask_ptr: int) -> None:
+    _check(h, load().sim_interface_targets(h, VP(x_ptr), VP(t_ptr), VP(mask_ptr)))
+
+
+def sim_step_learned(h, net_handle, n_steps: int = 1) -> None:
+    _check(h, load().sim_step_learned(h, net_handle, n_steps))
 
 
 PHASES = ("assemble", "factor", "v_step", "z_step", "exit", "recover", "iterations",
@@ -400,6 +417,10 @@ class Simulation:
 
     def use_graph(self, enable: bool = True) -> None:
         sim_use_graph(self.h, enable)
+
+    def step_learned(self, net, n: int = 1) -> None:
+        """n steps with the learned warm start of `net` (a warmstart.Network)."""
+        sim_step_learned(self.h, net.h, n)
 
     def sync(self):
         sim_sync(self.h)

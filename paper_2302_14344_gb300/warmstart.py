@@ -17,7 +17,9 @@ VP = C.c_void_p
 PF = C.POINTER(C.c_float)
 PI = C.POINTER(C.c_int)
 
-EXPORTS = ("wsn_create", "wsn_destroy", "wsn_last_error", "wsn_num_params", "wsn_set_params",
+EXPORTS = ("wsn_create", "wsn_destroy", "wsn_last_error", "wsn_num_params", "wsn_shape",
+           "wsn_workspace_generation",
+           "wsn_set_params",
            "wsn_get_params", "wsn_set_normalization", "wsn_get_normalization",
            "wsn_fit_normalization", "wsn_forward", "wsn_gradients", "wsn_train_step")
 
@@ -26,6 +28,8 @@ _sigs = {
     "wsn_destroy": (None, [VP]),
     "wsn_last_error": (C.c_char_p, [VP]),
     "wsn_num_params": (C.c_longlong, [VP]),
+    "wsn_shape": (C.c_int, [VP, PI]),
+    "wsn_workspace_generation": (C.c_longlong, [VP]),
     "wsn_set_params": (C.c_int, [VP, PF]),
     "wsn_get_params": (C.c_int, [VP, PF]),
     "wsn_set_normalization": (C.c_int, [VP, PF, PF, PF]),

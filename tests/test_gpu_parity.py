@@ -528,9 +528,9 @@ def test_per_scene_iteration_counts_match_the_residuals(sa):
     sim.step(1)
     st = sim.iteration_stats(per_scene=True)
     ps = st["per_scene"]
-    assert ps.shape == (5, 4)
+    assert ps.shape == (5, 5)
     assert ps[:, 0].sum() == st["total_iters"] and ps[:, 1].max() == st["max_iters"]
-    assert (ps[:, 3] == 1).all()
+    assert (ps[:, 3] == 1).all() and (ps[:, 4] == 0).all()
     for k in range(5):
         r = sim.residuals(k)
         assert ps[k, 0] == ps[k, 1] == r["iters"]
