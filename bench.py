@@ -297,6 +297,37 @@ def run_reference(args, rank: int, world: int):
     return 0
 
 
+def learned_comparison(args, p) -> dict:
+    """The learned warm start against the previous-step warm start on this workload: the
+    network is trained on robots of two other seeds after landing (steps 200-400), then
+    both starts run the timed segment (mixed form, one launch per step, graph replay)."""
+    import scenegen as sg
+    import torch
+    from paper_2302_14344_gb300 import learned as lr
+    t0 = time.perf_counter()
+    parts = [lr.collect(sg.robots(s, n_robots=args.robots), steps=200, warmup=200)
+             for s in (101, 102)]
+    X = torch.cat([q[0] for q in parts]); T = torch.cat([q[1] for q in parts])
+    M = torch.cat([q[2] for q in parts])
+    net = lr.init_network(seed=1)
+    losses = lr.train(net, X, T, M, epochs=8)
+    train_s = time.perf_counter() - t0
+    res = lr.compare(p, net, steps=args.steps, warmup=args.warmup)
+    pl, le = res["plain"], res["learned"]
+    return {"value": 1e3 / le["ms_per_step"], "unit": "steps/s",
+            "previous_step_start": 1e3 / pl["ms_per_step"],
+            "learned_over_previous": pl["ms_per_step"] / le["ms_per_step"],
+            "iterations_per_scene_step": {"learned": le["iters_per_scene_step"],
+                                          "previous_step": pl["iters_per_scene_step"]},
+            "fallbacks": le["fallbacks"], "scene_steps": args.steps * len(p.scenes),
+            "training": {"samples": int(X.shape[0]), "epochs": 8,
+                         "loss_first_last": [losses[0], losses[-1]],
+                         "seconds": round(train_s, 1)},
+            "note": "both starts stepped one launch per step (graph replay), timed segment "
+                    "of this run; the network adds features + a 32-256-256-256-7 BF16 MLP "
+                    "per step"}
+
+
 def batch_for_rank(rank: int, n_robots: int, h: float, workload: str = "robots",
                    scenes: int = 4096):
     """The scenes a rank simulates: an independent seeded batch per rank (weak scaling; the
@@ -384,6 +415,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the heuristic kernel variants instead of timing them first")
     ap.add_argument("--no-graph", action="store_true", help="launch directly, not by graph replay")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="skip the learned warm start comparison (robots workload)")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip timing the plain FP64 form next to the chosen one")
     args = ap.parse_args()
@@ -461,6 +494,10 @@ def main():
                    "chosen_over_plain": (world * K / (t_ms / 1e3)) / (world * K / (t2 / 1e3))}
         sim2.close()
 
+    learned_line = None
+    if args.workload == "robots" and not args.no_learned and world == 1:
+        learned_line = learned_comparison(args, p)
+
     # end to end through the C ABI with host buffers: state in from pinned host memory,
     # one step, state out to pinned host memory, every step
     nstate = 13 * sizes["bodies"] + 6 * sizes["nodes"]
@@ -512,6 +549,7 @@ def main():
                            "scene_steps": stats["scene_steps"]},
             "interface_updates_per_s": n_if * total_iters * world / (t_ms / 1e3),
             "plain_fp64": compare,
+            "learned_warm_start": learned_line,
             "roofline": roofline,
             "e2e": e2e,
             "gpu_launches": len(launch_ms) * len(stats["classes"]),

@@ -58,7 +58,8 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 2) grid_step_kernel(StepParam
         }
         d.sync();
         PhaseClock pc((P.phase && blockIdx.x == 0) ? P.phase + 8 * sc : nullptr);
-        scene_setup<T>(P, S, V, &G->status, pc, step, d);
+        pc.mark_at(PHASE_ASSEMBLE, scene_setup<T>(P, S, V, &G->status, step, d));
+        pc.mark(PHASE_FACTOR);
         const int status0 = vload(&G->status);
         if (status0 != ST_OK) {
             if (lead) {
@@ -98,6 +99,7 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 2) grid_step_kernel(StepParam
             }
         }
         int par = 0, last_par = 0, iters = 0, conv = 0, status = ST_OK;
+        bool restart = false;
         double th = 0.0;
         double tolc = P.tol;
         U tolb = tol_bits(T(0), tolc > 0.0 ? tolc : 0.0);
@@ -307,25 +309,29 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 2) grid_step_kernel(StepParam
                 par ^= 1;
                 pc.mark(PHASE_ZSTEP);
                 if (learned_mode && l == 9) {
-                    if (learned && (unsigned long long)mx > ref10) {
-                        if (lead) {
-                            const int streak = min(P.learn_skip[2 * sc + 1] + 1, 5);
-                            P.learn_skip[2 * sc + 1] = streak;
-                            P.learn_skip[2 * sc] = (1 << streak) - 1;
-                        }
-                        learned = false;
-                        ++fallbacks;
-                        wasted += l + 1;
-                        init_duals<T>(P, S, V, LAM, Z, ZO, X, Y, YO, W0, BT, false, d);
-                        par = 0;
-                        l = -1;
-                        continue;
-                    }
+                    if (learned && (unsigned long long)mx > ref10) { restart = true; break; }
                     if (!learned && lead) P.ref10[sc] = (unsigned long long)mx;
                     if (learned && lead) P.learn_skip[2 * sc + 1] = 0;
                 }
                 if (mx >= inf_bits(T(0))) { status = ST_NAN; break; }
                 if (primal_stop && mx <= tolb) { conv = 1; break; }
+            }
+            if (restart) {
+                // the learned start trails the plain one after 10 iterations: restart the step
+                // from the plain start, and start plain for the next 2^streak - 1 steps
+                if (lead) {
+                    const int streak = min(P.learn_skip[2 * sc + 1] + 1, 5);
+                    P.learn_skip[2 * sc + 1] = streak;
+                    P.learn_skip[2 * sc] = (1 << streak) - 1;
+                }
+                restart = false;
+                learned = false;
+                ++fallbacks;
+                wasted += l + 1;
+                init_duals<T>(P, S, V, LAM, Z, ZO, X, Y, YO, W0, BT, false, d);
+                par = 0;
+                l = 0;
+                continue;
             }
             if (lead) G->chk = 0ull;
             recover_v<T>(P, S, V, last_par ? W1 : W0, d);

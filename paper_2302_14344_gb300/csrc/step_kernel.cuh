@@ -134,6 +134,14 @@ struct PhaseClock {
             t = n;
         }
     }
+    // attribute the time up to `when` (a clock64 value) to `phase`
+    __device__ __forceinline__ void mark_at(int phase, long long when)
+    {
+        if (out) {
+            a[phase] += when - t;
+            t = when;
+        }
+    }
     __device__ __forceinline__ void flush(int iters)
     {
         if (out) {
@@ -471,8 +479,8 @@ __device__ void form_c(const F *W, int n, int m, int ldw, const int *jlo, F *cc)
 
 // assemble .. factor .. map, and the per-step constants of the z-step
 template <typename T, typename Dist>
-__device__ void scene_setup(const StepParams &P, const SceneDesc &S, const View<T> &V,
-                            int *s_status, PhaseClock &pc, int step, const Dist &d)
+__device__ long long scene_setup(const StepParams &P, const SceneDesc &S, const View<T> &V,
+                                 int *s_status, int step, const Dist &d)
 {
     const int lane = threadIdx.x & 31;
     constexpr bool MIXED = sizeof(T) == 4;
@@ -580,7 +588,7 @@ __device__ void scene_setup(const StepParams &P, const SceneDesc &S, const View<
         }
     }
     d.sync();
-    pc.mark(PHASE_ASSEMBLE);
+    const long long t_asm = clock64();
     // per subsystem (one warp each): beta, K = A + beta J^T J and its Cholesky factor, then
     // the map W = L^-1 [J^T b], D = W^T W, c.  The FP64 form and the stiff blocks of the mixed
     // form factorise K in FP64 (rounded into the T copy); the other mixed blocks factorise in
@@ -687,7 +695,6 @@ __device__ void scene_setup(const StepParams &P, const SceneDesc &S, const View<
         __syncwarp();
     }
     d.sync();
-    pc.mark(PHASE_FACTOR);
     // per-step z-step constants: 1/s, soft gain k/(1 + s alpha k), alpha, mu (per row);
     // beta and 1/beta per side-row
     T *INVS = tb + S.ot_invs, *KF = tb + S.ot_kf, *AL = tb + S.ot_al, *MU = tb + S.ot_mu;
@@ -715,6 +722,7 @@ __device__ void scene_setup(const StepParams &P, const SceneDesc &S, const View<
         }
     }
     d.sync();
+    return t_asm;
 }
 
 // out += J^T w (FP64) over the column span of each J row, a row at a time (lanes across the
@@ -829,6 +837,21 @@ __device__ void recover_v(const StepParams &P, const SceneDesc &S, const View<T>
         for (int p = lane; p < n; p += 32) v[p] += (double)s[p];
         __syncwarp();
     }
+}
+
+// The block kernel's once-per-step phases as calls (arguments by value), so that the
+// register allocation of its iteration loop is not shaped by the setup code's.
+template <typename T>
+__device__ __noinline__ long long block_setup(StepParams P, SceneDesc S, View<T> V, int *status,
+                                              int step)
+{
+    return scene_setup<T>(P, S, V, status, step, BlockDist());
+}
+
+template <typename T>
+__device__ __noinline__ void block_recover(StepParams P, SceneDesc S, View<T> V, const T *w)
+{
+    recover_v<T>(P, S, V, w, BlockDist());
 }
 
 // Initial z and u = -lambda of a step (Algorithm 1, before the loop): cold (zeros), warm
@@ -1037,7 +1060,8 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, CACHED ? 1 : 2) step_kernel(S
             if (tid == 0) s_status = ST_OK;
             __syncthreads();
             PhaseClock pc(P.phase ? P.phase + 8 * sc : nullptr);
-            scene_setup<T>(P, S, V, &s_status, pc, step, BlockDist());
+            pc.mark_at(PHASE_ASSEMBLE, block_setup<T>(P, S, V, &s_status, step));
+            pc.mark(PHASE_FACTOR);
             const int status0 = s_status;
             if (status0 != ST_OK) {
                 // K_i not SPD: report, leave the state untouched (the step is undefined)
@@ -1096,6 +1120,7 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, CACHED ? 1 : 2) step_kernel(S
             load_cache();
 
             int par = 0, last_par = 0, iters = 0, conv = 0, status = ST_OK;
+            bool restart = false;
             double th = 0.0;
             double tolc = P.tol;
             U tolb = tol_bits(T(0), tolc > 0.0 ? tolc : 0.0);
@@ -1275,34 +1300,36 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, CACHED ? 1 : 2) step_kernel(S
                     par ^= 1;
                     pc.mark(PHASE_ZSTEP);
                     if (learned_mode && l == 9) {
-                        if (learned && (unsigned long long)mx > ref10) {
-                            // the learned start trails the plain one: restart from the plain,
-                            // and start plain for the next 2^streak - 1 steps
-                            if (tid == 0) {
-                                const int streak = min(P.learn_skip[2 * sc + 1] + 1, 5);
-                                P.learn_skip[2 * sc + 1] = streak;
-                                P.learn_skip[2 * sc] = (1 << streak) - 1;
-                            }
-                            learned = false;
-                            ++fallbacks;
-                            wasted += l + 1;
-                            init_duals<T>(P, S, V, LAM, Z, ZO, X, Y, YO, W0, BT, false, BlockDist());
-                            load_cache();
-                            par = 0;
-                            l = -1;
-                            continue;
-                        }
+                        if (learned && (unsigned long long)mx > ref10) { restart = true; break; }
                         if (!learned && tid == 0) P.ref10[sc] = (unsigned long long)mx;
                         if (learned && tid == 0) P.learn_skip[2 * sc + 1] = 0;   // kept: streak ends
                     }
                     if (mx >= inf_bits(T(0))) { status = ST_NAN; break; }
                     if (primal_stop && mx <= tolb) { conv = 1; break; }
                 }
+                if (restart) {
+                    // the learned start trails the plain one after 10 iterations: restart the
+                    // step from the plain start, and start plain for the next 2^streak - 1 steps
+                    if (tid == 0) {
+                        const int streak = min(P.learn_skip[2 * sc + 1] + 1, 5);
+                        P.learn_skip[2 * sc + 1] = streak;
+                        P.learn_skip[2 * sc] = (1 << streak) - 1;
+                    }
+                    restart = false;
+                    learned = false;
+                    ++fallbacks;
+                    wasted += l + 1;
+                    init_duals<T>(P, S, V, LAM, Z, ZO, X, Y, YO, W0, BT, false, BlockDist());
+                    load_cache();
+                    par = 0;
+                    l = 0;
+                    continue;
+                }
                 // the cached z live in registers: publish them (and the previous ones)
                 if (CACHED) ri.publish(Z, ZO);
                 if (CACHED && xv && xgl == 0) YO[xt] = yprev;
                 __syncthreads();
-                recover_v<T>(P, S, V, last_par ? W1 : W0, BlockDist());
+                block_recover<T>(P, S, V, last_par ? W1 : W0);
                 __syncthreads();
                 if (MIXED && conv && primal_stop && status == ST_OK) {
                     // FP64 primal residual max |J v - z|; on a miss, refine c by the FP64 - FP32
