@@ -33,6 +33,11 @@ struct SceneDesc {
     int nsr, nrow;         // side-rows and rows of the scene
     int nitem, nlist;      // projection items (a row, or a whole contact) and their side lists
     int max_sides;         // most sides of one constraint of the scene
+    // register-cached iteration: ipool offset of the thread map for 1, 2 and 4 lanes per
+    // side-row (-1: the scene's items do not pack into one block that way).  Entry of
+    // thread k: int2 {side-row (-1: idle), leader lane | slot << 5 | group lane << 8 |
+    // item << 11}
+    int fmap_off[3];
     int item_g0, list_g0;  // global offsets of the scene's item / list tables
     int nasm, asm_g0;      // assembly slots (constraint indices grouped by kind, -1 = idle)
     int sr_g0, row_g0;     // global offset of the scene's side-rows / rows (z, lambda state)

@@ -434,28 +434,54 @@ __device__ void env_forward_vec(const F *LT, F *y, int n, int ldy, const int *la
 }
 
 // D = W^T W over the m columns of W (rows ldd apart, padded with zeros to mp); W column t
-// is zero above row jlo[t]
+// is zero above row jlo[t].  A lane computes a 4 x 4 block of D (lower triangle of blocks,
+// mirrored): per row p of W it loads 4 + 4 values for 16 FMAs.  ldw is a multiple of 4 and
+// the columns of W past m are zero, so a block never reads past its row of W.
 template <typename F>
 __device__ void form_D(const F *W, int n, int m, int mp, int ldd, int ldw, const int *jlo, F *D)
 {
     const int lane = threadIdx.x & 31;
-    for (int k = lane; k < m * (m + 1) / 2; k += 32) {
-        int r, s;
-        tri_index(k, r, s);
-        int p = max(jlo[r], jlo[s]);
-        F a0 = (F)0, a1 = (F)0;
-        for (; p + 1 < n; p += 2) {
-            a0 += W[p * ldw + r] * W[p * ldw + s];
-            a1 += W[(p + 1) * ldw + r] * W[(p + 1) * ldw + s];
+    const int nb = (m + 3) / 4;
+    for (int k = lane; k < nb * (nb + 1) / 2; k += 32) {
+        int bi, bj;
+        tri_index(k, bi, bj);
+        const int r0 = 4 * bi, s0 = 4 * bj;
+        int pr = n, ps = n;
+        for (int q = 0; q < 4; ++q) {
+            if (r0 + q < m) pr = min(pr, jlo[r0 + q]);
+            if (s0 + q < m) ps = min(ps, jlo[s0 + q]);
         }
-        if (p < n) a0 += W[p * ldw + r] * W[p * ldw + s];
-        D[r * ldd + s] = a0 + a1;
-        D[s * ldd + r] = a0 + a1;
+        F acc[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] = (F)0;
+        for (int p = max(pr, ps); p < n; ++p) {
+            const F *Wp = W + (size_t)p * ldw;
+            F wr[4], ws[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) { wr[q] = Wp[r0 + q]; ws[q] = Wp[s0 + q]; }
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] += wr[a] * ws[b];
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const int r = r0 + a, s = s0 + b;
+                if (r < m && s < m && s <= r) {
+                    D[r * ldd + s] = acc[a][b];
+                    D[s * ldd + r] = acc[a][b];
+                }
+            }
+        }
     }
     if (mp > m) {
-        for (int t = lane; t < m * (mp - m); t += 32) {
-            const int r = t / (mp - m);
-            D[r * ldd + m + (t - r * (mp - m))] = (F)0;
+        for (int q = lane; q < m * (mp - m); q += 32) {
+            const int r = q / (mp - m);
+            D[r * ldd + m + (q - r * (mp - m))] = (F)0;
         }
     }
 }
@@ -596,7 +622,8 @@ __device__ long long scene_setup(const StepParams &P, const SceneDesc &S, const 
     for (int i = d.warp; i < S.nsub; i += d.nwarps) {
         const SubDesc &u = P.subs[S.sub0 + i];
         const int gsub = S.sub0 + i;
-        const int n = u.n, m = u.m, mp = u.mpad, ldw = m + 1;
+        // W's leading dimension: m + 1 columns rounded up to 4 (form_D reads 4-column blocks)
+        const int n = u.n, m = u.m, mp = u.mpad, ldw = (m + 1 + 3) / 4 * 4;
         const SubEnv e = sub_env(P, u);
         double *J = sdb + u.od_J, *K = sdb + u.od_L, *b = sdb + u.od_b, *idg = sdb + u.od_id;
         T *LT = stb + u.ot_L, *W = stb + u.ot_W, *D = htb + u.ot_D, *cc = htb + u.ot_c;
@@ -685,7 +712,7 @@ __device__ long long scene_setup(const StepParams &P, const SceneDesc &S, const 
         // W = [J^T b] in T (column-major), then W <- L^-1 W; D = W^T W, c = W^T g
         for (int q = lane; q < n * ldw; q += 32) {
             const int p = q / ldw, t = q - p * ldw;
-            W[q] = t < m ? (T)J[t * n + p] : (T)b[p];
+            W[q] = t < m ? (T)J[t * n + p] : t == m ? (T)b[p] : (T)0;
         }
         __syncwarp();
         env_forward_cols<T>(LT, W, n, ldw, m + 1, e.env);
@@ -1011,6 +1038,36 @@ struct RegItem {
         return mloc;
     }
 
+    // lambda of the item (Sec. III-C) from the y of its side-rows, slot s * rows + r
+    __device__ __forceinline__ void lambda_of(const T *ys, T *lv) const
+    {
+        lv[0] = lv[1] = lv[2] = (T)0;
+        if (!valid) return;
+        if (type == TYPE_CONTACT) {
+            const T ya0 = ys[0], ya1 = ys[1], ya2 = ys[2];
+            const T yb0 = t1 >= 0 ? ys[3] : (T)0, yb1 = t1 >= 0 ? ys[4] : (T)0, yb2 = t1 >= 0 ? ys[5] : (T)0;
+            const T ln = -(ya0 * ib0 + yb0 * ib1 + e0) * is;
+            const T l1 = -(ya1 * ib0 + yb1 * ib1 + e1) * is;
+            const T l2 = -(ya2 * ib0 + yb2 * ib1 + e2) * is;
+            if (ln > (T)0) {
+                const T t2 = l1 * l1 + l2 * l2;
+                const T lim = mu * ln;
+                lv[0] = ln;
+                if (t2 > lim * lim) { const T f = lim * rsq(t2); lv[1] = l1 * f; lv[2] = l2 * f; }
+                else { lv[1] = l1; lv[2] = l2; }
+            }
+        } else {
+            const T q = ys[0] * ib0 + (t1 >= 0 ? ys[1] : (T)0) * ib1;
+            T l;
+            if (type == TYPE_SOFT) l = -(e0 + al * q) * kf;
+            else {
+                l = -(q + e0) * is;
+                if (type == TYPE_HARD) l = l > (T)0 ? l : (T)0;
+            }
+            lv[0] = l;
+        }
+    }
+
     // write the z (and the previous z) held in registers back to the scene arrays
     __device__ __forceinline__ void publish(T *Z, T *ZO) const
     {
@@ -1084,37 +1141,57 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, CACHED ? 1 : 2) step_kernel(S
             if (learned_mode && tid == 0 && skip0 > 0) P.learn_skip[2 * sc] = skip0 - 1;
             init_duals<T>(P, S, V, LAM, Z, ZO, X, Y, YO, W0, BT, learned, BlockDist());
 
-            // ---- per-thread cache of the step's coefficients (CACHED: one side-row group
-            // and one z-step item per thread, items with at most two sides)
+            // ---- per-thread state of the register-cached iteration (CACHED).  The host's
+            // thread map gives each thread a side-row (its lane group of SPLIT lanes) and puts
+            // every projection item's side-rows on adjacent groups of one warp.  A thread keeps
+            // its side-row's D chunks, c, beta, 1/beta, x, y, z and lambda in registers and the
+            // constants of its item: the warp forms the items' y, and every lane of an item
+            // projects it (Sec. III-C) from y gathered by shuffles, so an iteration needs one
+            // block barrier (the new w) instead of two.
             constexpr int MAXC = CachedChunks<T>::value;   // D chunks a lane keeps in registers
-            const int xg = tid / SPLIT, xgl = tid - xg * SPLIT;
-            const int xt = xg;
+            constexpr int FSI = SPLIT == 4 ? 2 : SPLIT == 2 ? 1 : 0;
+            const int xg = tid / SPLIT;
+            int xt = -1, xgl = tid - xg * SPLIT, flead = 0, fslot = 0, fitem = 0;
+            if (CACHED) {
+                const int2 fm = reinterpret_cast<const int2 *>(P.ipool + S.fmap_off[FSI])[tid];
+                xt = fm.x;
+                flead = fm.y & 31;
+                fslot = (fm.y >> 5) & 7;
+                xgl = (fm.y >> 8) & 7;
+                fitem = fm.y >> 11;
+            }
             VT dreg[MAXC];
-#pragma unroll
-            for (int q = 0; q < MAXC; ++q) dreg[q] = VecZero<T>::get();
             bool xv = false;
-            int xdro = 0, xwbo = 0, xnv = 0, xrow = 0;
-            T xc = (T)0, xbt = (T)0, yreg = (T)0, yprev = (T)0;
-            RegItem<T> ri;
+            int xwbo = 0, xnv = 0, xrow = 0, fr = 0;
+            T xc = (T)0, xbt = (T)0, xib = (T)0, xx = (T)0, yreg = (T)0, yprev = (T)0;
+            T zreg = (T)0, zprev = (T)0, lreg = (T)0;
+            RegItem<T, false> ri;
             auto load_cache = [&]() {
                 if (CACHED) {
-                    if (xt < S.nsr && V.mlen[xt] > 0) {
-                        xv = true;
-                        xdro = V.drow[xt];
+#pragma unroll
+                    for (int q = 0; q < MAXC; ++q) dreg[q] = VecZero<T>::get();
+                    xv = xt >= 0 && V.mlen[xt] > 0;
+                    if (xv) {
                         xwbo = V.wbase[xt];
                         xnv = (V.mlen[xt] + VN - 1) / VN;
                         xrow = V.row[xt];
                         xc = V.htb[V.coff[xt]];
                         xbt = BT[xt];
+                        xib = INVB[xt];
+                        xx = X[xt];
                         yreg = Y[xt];
                         yprev = yreg;
-                        const VT *Dr = reinterpret_cast<const VT *>(V.htb + xdro);
+                        zreg = Z[xt];
+                        zprev = zreg;
+                        lreg = LAM[xrow];
+                        const VT *Dr = reinterpret_cast<const VT *>(V.htb + V.drow[xt]);
 #pragma unroll
                         for (int q = 0; q < MAXC; ++q)
                             if (xgl + q * SPLIT < xnv) dreg[q] = Dr[xgl + q * SPLIT];
                     }
-                    ri = RegItem<T>();
-                    if (tid < S.nitem) ri.load(V.item, V.list, tid, INVB, E, INVS, KF, AL, MU, Z);
+                    ri = RegItem<T, false>();
+                    if (xt >= 0) ri.load(V.item, V.list, fitem, INVB, E, INVS, KF, AL, MU, Z);
+                    fr = ri.nr == 3 ? fslot % 3 : 0;
                 }
             };
             load_cache();
@@ -1135,7 +1212,10 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, CACHED ? 1 : 2) step_kernel(S
                     // ---- v-step through the affine map x = c + D w; y = beta x - lambda
                     const T *w = par ? W1 : W0;
                     T tpart = (T)0;
+                    T *wn = par ? W0 : W1;
+                    U mfused = 0;
                     if (CACHED) {
+                        // x = c + D w of this side-row over its lane group
                         T acc = (T)0;
                         if (xv) {
                             const VT *wb = reinterpret_cast<const VT *>(w + xwbo);
@@ -1152,17 +1232,27 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, CACHED ? 1 : 2) step_kernel(S
                         }
 #pragma unroll
                         for (int o = SPLIT / 2; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-                        if (xv && xgl == 0) {
-                            acc += xc;
-                            const T ynew = xbt * acc - LAM[xrow];
-                            if (P.stop_theta) {
-                                const T d = ynew - yreg;
-                                tpart += d * d;
+                        const T xn = acc + xc;
+                        const T yn = xbt * xn - lreg;
+                        // the item's y (slot k on the group at lane flead + k SPLIT), its lambda,
+                        // then z, w and the residual of this side-row
+                        T ys[6], lv[3];
+#pragma unroll
+                        for (int k = 0; k < 6; ++k) ys[k] = __shfl_sync(0xffffffffu, yn, (flead + k * SPLIT) & 31);
+                        ri.lambda_of(ys, lv);
+                        const T ln = fr == 0 ? lv[0] : fr == 1 ? lv[1] : lv[2];
+                        if (xv) {
+                            const T zn = (yn + ln) * xib;
+                            if (xgl == 0) {
+                                mfused = umax(rbits(fabs(xn - zn)), rbits(fabs(zn - zreg)));
+                                wn[xt] = yn + (T)2 * ln;
                             }
+                            zprev = zreg;
+                            zreg = zn;
                             yprev = yreg;
-                            yreg = ynew;
-                            Y[xt] = ynew;
-                            X[xt] = acc;
+                            yreg = yn;
+                            xx = xn;
+                            lreg = ln;
                         }
                     } else {
                         // two side-rows per trip, two accumulators per row: independent
@@ -1212,25 +1302,26 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, CACHED ? 1 : 2) step_kernel(S
                             }
                         }
                     }
-                    if (P.stop_theta) {
+                    if (!CACHED) {
+                        if (P.stop_theta) {
 #pragma unroll
-                        for (int o = 16; o; o >>= 1) tpart += __shfl_xor_sync(0xffffffffu, tpart, o);
-                        if (lane == 0) tred[l & 1][warp] = tpart;
+                            for (int o = 16; o; o >>= 1) tpart += __shfl_xor_sync(0xffffffffu, tpart, o);
+                            if (lane == 0) tred[l & 1][warp] = tpart;
+                        }
+                        __syncthreads();
                     }
-                    __syncthreads();
                     pc.mark(PHASE_VSTEP);
                     last_par = par;
                     iters = l + 1;
-                    if (P.stop_theta) {
+                    if (!CACHED && P.stop_theta) {
                         T ths = (T)0;
                         for (int q = 0; q < SUBADMM_WARPS; ++q) ths += tred[l & 1][q];
                         if (l >= 1 && ths < theta_thT) { th = (double)ths; conv = 1; break; }
                     }
                     // ---- z-step (Sec. III-C); u = -lambda; max(|x - z|, |dz|) as bits
-                    T *wn = par ? W0 : W1;
                     U mloc = 0;
                     if (CACHED) {
-                        mloc = ri.project(Y, X, LAM, wn, Z, ZO);
+                        mloc = mfused;
                     } else {
                         for (int i = tid; i < S.nitem; i += SUBADMM_THREADS) {
                             const Item it = V.item[i];
@@ -1325,9 +1416,15 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, CACHED ? 1 : 2) step_kernel(S
                     l = 0;
                     continue;
                 }
-                // the cached z live in registers: publish them (and the previous ones)
-                if (CACHED) ri.publish(Z, ZO);
-                if (CACHED && xv && xgl == 0) YO[xt] = yprev;
+                // the register-cached iterate: publish x, y, z, lambda (and the previous y, z)
+                if (CACHED && xv && xgl == 0) {
+                    X[xt] = xx;
+                    Y[xt] = yreg;
+                    YO[xt] = yprev;
+                    Z[xt] = zreg;
+                    ZO[xt] = zprev;
+                    LAM[xrow] = lreg;
+                }
                 __syncthreads();
                 block_recover<T>(P, S, V, last_par ? W1 : W0);
                 __syncthreads();

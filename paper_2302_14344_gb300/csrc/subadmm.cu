@@ -98,6 +98,7 @@ struct sim_s {
     cudaEvent_t ev_fork = nullptr;
     int split_override = 0;        // tuning: force the split of every class (0: heuristic)
     std::vector<int> sc_nsr, sc_items, sc_sides, sc_mpad;   // per scene: register-cache limits
+    std::vector<int> sc_fmap_ok;   // per scene: bit si set if the thread map for 2^si lanes exists
     int smem_full = 0;             // dynamic shared memory a block may use
     int grid_side_rows = kGridSideRows;
     // graph replay of sim_step
@@ -300,7 +301,7 @@ int finalize(sim_t s)
     int max_nsr = 0, max_items = 0, max_sides = 0, max_mpad = 0;
     struct Place { long long sd, st, sh, scd, scene_t, ints; };
     std::vector<Place> place(nscenes);
-    std::vector<int> sc_mpad(nscenes, 0), sc_sides(nscenes, 0);
+    std::vector<int> sc_mpad(nscenes, 0), sc_sides(nscenes, 0), sc_fmap_ok(nscenes, 0);
     s->sdesc.assign(nsubs, SubDesc{});
     s->cdesc.assign(ncons, ConDesc{});
     s->scenes.assign(nscenes, SceneDesc{});
@@ -512,6 +513,54 @@ int finalize(sim_t s)
         S.nitem = (int)items.size() - S.item_g0;
         S.nlist = (int)lists.size() - S.list_g0;
         max_items = std::max(max_items, S.nitem);
+        // thread maps of the register-cached iteration: every item's side-rows on adjacent
+        // lane groups of one warp (SPLIT lanes per side-row, groups aligned to SPLIT), so a
+        // warp both forms the items' y and projects them; slot s * rows + r is side s, row r
+        for (int si = 0; si < 3; ++si) {
+            const int split = 1 << si;
+            S.fmap_off[si] = -1;
+            std::vector<int> map(2 * SUBADMM_THREADS, 0);
+            for (int k = 0; k < SUBADMM_THREADS; ++k) map[2 * k] = -1;
+            int cursor = 0;
+            bool ok = true;
+            for (int it = 0; it < S.nitem && ok; ++it) {
+                const Item &I = items[S.item_g0 + it];
+                if (I.type < 0) continue;
+                const int nr = I.type == TYPE_CONTACT ? 3 : 1;
+                const int lanes = I.ns * nr * split;
+                if (I.ns > 2 || lanes > 32) { ok = false; break; }
+                if (cursor % 32 + lanes > 32) cursor = (cursor + 31) / 32 * 32;
+                if (cursor + lanes > SUBADMM_THREADS) { ok = false; break; }
+                const int leader = cursor % 32;
+                for (int sd = 0; sd < I.ns; ++sd)
+                    for (int r = 0; r < nr; ++r)
+                        for (int g = 0; g < split; ++g) {
+                            const int slot = sd * nr + r;
+                            const int th = cursor + slot * split + g;
+                            map[2 * th] = lists[S.list_g0 + I.lo + sd] + r;
+                            map[2 * th + 1] = leader | (slot << 5) | (g << 8) | (it << 11);
+                        }
+                cursor += lanes;
+            }
+            // every real side-row on exactly one lane group
+            std::vector<int> seen(S.nsr, 0);
+            for (int k = 0; ok && k < SUBADMM_THREADS; ++k) {
+                const int t = map[2 * k];
+                if (t < 0) continue;
+                if (t >= S.nsr) ok = false;
+                else if ((map[2 * k + 1] >> 8 & 7) == 0) ++seen[t];
+            }
+            for (int i = 0; ok && i < S.nsub; ++i) {
+                const SubDesc &u = s->sdesc[S.sub0 + i];
+                for (int r = 0; r < u.m; ++r)
+                    if (seen[u.sr0 + r] != 1) { ok = false; break; }
+            }
+            if (!ok) continue;
+            if (ipool.size() & 1) ipool.push_back(0);       // read as int2: 8-byte aligned
+            S.fmap_off[si] = (int)ipool.size();
+            ipool.insert(ipool.end(), map.begin(), map.end());
+        }
+        sc_fmap_ok[sc] = (S.fmap_off[0] >= 0 ? 1 : 0) | (S.fmap_off[1] >= 0 ? 2 : 0) | (S.fmap_off[2] >= 0 ? 4 : 0);
         // per-subsystem arrays (doubles: J, K or A, b, v, 1/L_pp or rhs, J v; T: L, W, s;
         // iteration T arrays: D, c).  T offsets are whole 16-byte vectors so D rows load as
         // vectors.
@@ -528,7 +577,8 @@ int finalize(sim_t s)
             u.od_id = (int)sd; sd += u.n;
             u.od_t = (int)sd; sd += u.m;
             u.ot_L = (int)st; st += (long long)u.n * u.n;
-            u.ot_W = (int)st; st = tal(st + (long long)(u.m + 1) * u.n);
+            u.ot_W = (int)st; st = tal(st + (long long)((u.m + 4) / 4 * 4) * u.n);   // W: n rows
+                                                                     // of m + 1 rounded up to 4
             u.ot_s = (int)st; st = tal(st + u.n);
             // D rows are ldd apart: an odd number of 16-byte vectors, so the rows that the
             // lanes of a warp read at once fall in different shared-memory banks
@@ -572,6 +622,7 @@ int finalize(sim_t s)
     }
     s->sc_sides = sc_sides;
     s->sc_mpad = sc_mpad;
+    s->sc_fmap_ok = sc_fmap_ok;
     for (int sc = 0; sc < nscenes; ++sc) s->scenes[sc].max_sides = sc_sides[sc];
     s->classes.clear();
     for (int sc = 0; sc < nscenes; ++sc) {
@@ -588,7 +639,8 @@ int finalize(sim_t s)
             while (split < 4 && 2 * split * std::max(S.nsr, 1) <= SUBADMM_THREADS) split *= 2;
         }
         if (s->split_override > 0) split = s->split_override;
-        const bool cached = !grid && S.nsr * split <= SUBADMM_THREADS && S.nitem <= SUBADMM_THREADS &&
+        const int si = split == 4 ? 2 : split == 2 ? 1 : 0;
+        const bool cached = !grid && s->opt.stop != SIM_STOP_THETA && (sc_fmap_ok[sc] >> si & 1) &&
                             sc_sides[sc] <= 2 && (sc_mpad[sc] + vn - 1) / vn <= chunks * split;
         const bool half = !grid && !cached && bytes_with(q, q.scd, q.sh + q.scene_t) <= half_budget;
         sc_budget[sc] = half ? half_budget : smem_budget;
@@ -1197,7 +1249,8 @@ bool cache_fits(const sim_t s, int sc, int split)
 {
     const int vn = s->opt.precision == SIM_MIXED ? 4 : 2;
     const int chunks = s->opt.precision == SIM_MIXED ? 4 : 6;
-    return s->sc_nsr[sc] * split <= SUBADMM_THREADS && s->sc_items[sc] <= SUBADMM_THREADS &&
+    const int si = split == 4 ? 2 : split == 2 ? 1 : 0;
+    return s->opt.stop != SIM_STOP_THETA && (s->sc_fmap_ok[sc] >> si & 1) &&
            s->sc_sides[sc] <= 2 && (s->sc_mpad[sc] + vn - 1) / vn <= chunks * split;
 }
 
