@@ -1095,6 +1095,7 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, CACHED ? 1 : 2) step_kernel(S
     __shared__ U ured[2][SUBADMM_WARPS];
     __shared__ T tred[2][SUBADMM_WARPS];
     __shared__ int s_status;
+    __shared__ int s_nan;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr bool MIXED = sizeof(T) == 4;
 
@@ -1114,7 +1115,7 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, CACHED ? 1 : 2) step_kernel(S
         __syncthreads();
 
         for (int step = 0; step < P.n_steps; ++step) {
-            if (tid == 0) s_status = ST_OK;
+            if (tid == 0) { s_status = ST_OK; s_nan = 0; }
             __syncthreads();
             PhaseClock pc(P.phase ? P.phase + 8 * sc : nullptr);
             pc.mark_at(PHASE_ASSEMBLE, block_setup<T>(P, S, V, &s_status, step));
@@ -1382,6 +1383,17 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, CACHED ? 1 : 2) step_kernel(S
                             }
                         }
                     }
+                    if (!(learned_mode && l == 9)) {
+                        // the stop test rides on the barrier: the number of threads whose
+                        // residual is above the tolerance; a non-finite residual raises s_nan
+                        if (mloc >= inf_bits(T(0))) s_nan = 1;
+                        const int over = __syncthreads_count(primal_stop && mloc > tolb);
+                        par ^= 1;
+                        pc.mark(PHASE_ZSTEP);
+                        if (s_nan) { status = ST_NAN; break; }
+                        if (primal_stop && over == 0) { conv = 1; break; }
+                        continue;
+                    }
                     mloc = warp_umax(mloc);
                     if (lane == 0) ured[l & 1][warp] = mloc;
                     __syncthreads();
@@ -1390,7 +1402,7 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, CACHED ? 1 : 2) step_kernel(S
                     for (int q = 0; q < SUBADMM_WARPS; ++q) mx = umax(mx, ured[l & 1][q]);
                     par ^= 1;
                     pc.mark(PHASE_ZSTEP);
-                    if (learned_mode && l == 9) {
+                    {
                         if (learned && (unsigned long long)mx > ref10) { restart = true; break; }
                         if (!learned && tid == 0) P.ref10[sc] = (unsigned long long)mx;
                         if (learned && tid == 0) P.learn_skip[2 * sc + 1] = 0;   // kept: streak ends
