@@ -1038,33 +1038,57 @@ struct RegItem {
         return mloc;
     }
 
-    // lambda of the item (Sec. III-C) from the y of its side-rows, slot s * rows + r
+    // lambda of the item (Sec. III-C) from the y of its side-rows, slot s * rows + r.  In
+    // FP32 one instruction stream serves every type (a warp holds items of several types):
+    // the first row is -(a q + e) s with (a, s) = (alpha, k) for soft rows and
+    // (1, 1 / sum 1/beta) otherwise, clamped at 0 for hard and contact rows; contact rows 1, 2
+    // are then scaled into the friction cone.  In FP64, where every instruction is costly,
+    // each type runs only its own formula.
     __device__ __forceinline__ void lambda_of(const T *ys, T *lv) const
     {
-        lv[0] = lv[1] = lv[2] = (T)0;
-        if (!valid) return;
-        if (type == TYPE_CONTACT) {
-            const T ya0 = ys[0], ya1 = ys[1], ya2 = ys[2];
-            const T yb0 = t1 >= 0 ? ys[3] : (T)0, yb1 = t1 >= 0 ? ys[4] : (T)0, yb2 = t1 >= 0 ? ys[5] : (T)0;
-            const T ln = -(ya0 * ib0 + yb0 * ib1 + e0) * is;
-            const T l1 = -(ya1 * ib0 + yb1 * ib1 + e1) * is;
-            const T l2 = -(ya2 * ib0 + yb2 * ib1 + e2) * is;
-            if (ln > (T)0) {
-                const T t2 = l1 * l1 + l2 * l2;
-                const T lim = mu * ln;
-                lv[0] = ln;
-                if (t2 > lim * lim) { const T f = lim * rsq(t2); lv[1] = l1 * f; lv[2] = l2 * f; }
-                else { lv[1] = l1; lv[2] = l2; }
-            }
+        const bool two = t1 >= 0, con = nr == 3;
+        if constexpr (sizeof(T) == 4) {
+            const T yb0 = two ? (con ? ys[3] : ys[1]) : (T)0;
+            const T q0 = ys[0] * ib0 + yb0 * ib1;
+            const T a0 = type == TYPE_SOFT ? al : (T)1;
+            const T s0 = type == TYPE_SOFT ? kf : is;
+            T l0 = -(q0 * a0 + e0) * s0;
+            if (type == TYPE_HARD || con) l0 = l0 > (T)0 ? l0 : (T)0;
+            const T yb1 = two ? ys[4] : (T)0, yb2 = two ? ys[5] : (T)0;
+            const T l1 = -(ys[1] * ib0 + yb1 * ib1 + e1) * is;
+            const T l2 = -(ys[2] * ib0 + yb2 * ib1 + e2) * is;
+            const T t2 = l1 * l1 + l2 * l2;
+            const T lim = mu * l0;
+            const T f = t2 > lim * lim ? lim * rsq(t2) : (T)1;
+            const bool on = valid && con && l0 > (T)0;
+            lv[0] = valid ? l0 : (T)0;
+            lv[1] = on ? l1 * f : (T)0;
+            lv[2] = on ? l2 * f : (T)0;
         } else {
-            const T q = ys[0] * ib0 + (t1 >= 0 ? ys[1] : (T)0) * ib1;
-            T l;
-            if (type == TYPE_SOFT) l = -(e0 + al * q) * kf;
-            else {
-                l = -(q + e0) * is;
-                if (type == TYPE_HARD) l = l > (T)0 ? l : (T)0;
+            lv[0] = lv[1] = lv[2] = (T)0;
+            if (!valid) return;
+            if (con) {
+                const T yb0 = two ? ys[3] : (T)0, yb1 = two ? ys[4] : (T)0, yb2 = two ? ys[5] : (T)0;
+                const T ln = -(ys[0] * ib0 + yb0 * ib1 + e0) * is;
+                if (ln > (T)0) {
+                    const T l1 = -(ys[1] * ib0 + yb1 * ib1 + e1) * is;
+                    const T l2 = -(ys[2] * ib0 + yb2 * ib1 + e2) * is;
+                    const T t2 = l1 * l1 + l2 * l2;
+                    const T lim = mu * ln;
+                    lv[0] = ln;
+                    if (t2 > lim * lim) { const T f = lim * rsq(t2); lv[1] = l1 * f; lv[2] = l2 * f; }
+                    else { lv[1] = l1; lv[2] = l2; }
+                }
+            } else {
+                const T q = ys[0] * ib0 + (two ? ys[1] : (T)0) * ib1;
+                T l;
+                if (type == TYPE_SOFT) l = -(e0 + al * q) * kf;
+                else {
+                    l = -(q + e0) * is;
+                    if (type == TYPE_HARD) l = l > (T)0 ? l : (T)0;
+                }
+                lv[0] = l;
             }
-            lv[0] = l;
         }
     }
 
