@@ -1119,7 +1119,6 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, CACHED ? 1 : 2) step_kernel(S
     __shared__ U ured[2][SUBADMM_WARPS];
     __shared__ T tred[2][SUBADMM_WARPS];
     __shared__ int s_status;
-    __shared__ int s_nan;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr bool MIXED = sizeof(T) == 4;
 
@@ -1139,7 +1138,7 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, CACHED ? 1 : 2) step_kernel(S
         __syncthreads();
 
         for (int step = 0; step < P.n_steps; ++step) {
-            if (tid == 0) { s_status = ST_OK; s_nan = 0; }
+            if (tid == 0) s_status = ST_OK;
             __syncthreads();
             PhaseClock pc(P.phase ? P.phase + 8 * sc : nullptr);
             pc.mark_at(PHASE_ASSEMBLE, block_setup<T>(P, S, V, &s_status, step));
@@ -1409,12 +1408,14 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, CACHED ? 1 : 2) step_kernel(S
                     }
                     if (!(learned_mode && l == 9)) {
                         // the stop test rides on the barrier: the number of threads whose
-                        // residual is above the tolerance; a non-finite residual raises s_nan
-                        if (mloc >= inf_bits(T(0))) s_nan = 1;
-                        const int over = __syncthreads_count(primal_stop && mloc > tolb);
+                        // residual is finite and above the tolerance.  A non-finite iterate
+                        // stays non-finite (c is fixed for the step and w carries it to every
+                        // coupled side-row), so the count drops to 0 or the limit ends the
+                        // loop, and the step's FP64 residuals below report it
+                        const int over = __syncthreads_count(primal_stop && mloc > tolb &&
+                                                             mloc < inf_bits(T(0)));
                         par ^= 1;
                         pc.mark(PHASE_ZSTEP);
-                        if (s_nan) { status = ST_NAN; break; }
                         if (primal_stop && over == 0) { conv = 1; break; }
                         continue;
                     }
@@ -1511,6 +1512,8 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, CACHED ? 1 : 2) step_kernel(S
                 rp = pp;
                 rd = dd;
             }
+            // a non-finite iterate (the loop itself does not stop on one)
+            if (status == ST_OK && !(isfinite(rp) && isfinite(rd))) { status = ST_NAN; conv = 0; }
             pc.mark(PHASE_EXIT);
             // v-hat out and state update of rigid bodies (Algorithm 1, after the loop)
             for (int i = warp; i < S.nsub; i += SUBADMM_WARPS) {

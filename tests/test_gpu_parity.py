@@ -498,6 +498,39 @@ def test_not_spd_is_reported_not_faulted(sa):
     assert ei.value.code == sa.SIM_ENOTSPD
 
 
+def test_non_finite_residual_is_reported_by_both_kernels(sa):
+    """A NaN planted in one body's velocity (it enters b_i only, so K_i stays SPD) makes that
+    scene's iterates non-finite: its step reports SIM_ENAN, in the register-cached kernel (a
+    robot) and in the generic kernel (a large batched scene) alike, and the other scenes of
+    the launch step on with finite residuals."""
+    import torch
+    small = sg.robots(11, n_robots=3).scenes
+    large = sg.batched(5, n_scenes=3, tol_primal=-1, max_iters=30).scenes
+    p = sg.Problem(small + large, sg.Options(h=1e-3, warm="prev", tol_primal=1e-6, max_iters=300,
+                                             beta_mode="trace"))
+    sim = sa.Simulation(p, precision=sa.SIM_MIXED)
+    classes = sim.launch_classes()
+    assert any(c["cached"] for c in classes) and not all(c["cached"] for c in classes)
+    sim.step(1)
+    nb = [len(sim.scene_bodies(k)) for k in range(6)]
+    big = next(k for k in range(3, 6) if nb[k] > 0)
+    sz = sim.sizes()
+    st = torch.empty(13 * sz["bodies"] + 6 * sz["nodes"], dtype=torch.float64).pin_memory()
+    sa.sim_read_state(sim.h, st.data_ptr())
+    for k in (0, big):
+        st[13 * sum(nb[:k]) + 7] = float("nan")          # v_x of the scene's first body
+    sa.sim_write_state(sim.h, st.data_ptr())
+    sim.step(1)
+    for k in range(6):
+        if k in (0, big):
+            with pytest.raises(sa.SimError) as ei:
+                sim.residuals(k)
+            assert ei.value.code == sa.SIM_ENAN, k
+        else:
+            r = sim.residuals(k)
+            assert np.isfinite(r["r_p"]) and r["status"] == 0, k
+
+
 def test_invalid_topology_is_rejected(sa):
     p = sg.chain(0)
     sim = sa.Simulation(p)
