@@ -189,15 +189,25 @@ __global__ void column_stats_kernel(const float *x, long long ld, int B, int D, 
     }
 }
 
-// column sums of a B x N BF16 matrix into FP32 (bias gradients), one thread per column
-// block, rows in a fixed order (deterministic)
-__global__ void column_sum_kernel(const __nv_bfloat16 *g, int B, int N, float *out)
+// column sums of a B x N BF16 matrix into FP32 (bias gradients).  A block of 32 x 8 threads
+// takes 32 columns: each of its 8 row groups sums rows g, g + 8, ... in order, then the 8
+// partial sums are added in group order (a fixed order: deterministic).
+__global__ void __launch_bounds__(256) column_sum_kernel(const __nv_bfloat16 *g, int B, int N, float *out)
 {
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= N) return;
+    __shared__ float part[8][33];
+    const int c = threadIdx.x & 31, r = threadIdx.x >> 5;
+    const int n = blockIdx.x * 32 + c;
     float s = 0.0f;
-    for (int b = 0; b < B; ++b) s += __bfloat162float(g[(long long)b * N + n]);
-    out[n] = s;
+    if (n < N)
+        for (int b = r; b < B; b += 8) s += __bfloat162float(g[(long long)b * N + n]);
+    part[r][c] = s;
+    __syncthreads();
+    if (r == 0 && n < N) {
+        float t = 0.0f;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) t += part[q][c];
+        out[n] = t;
+    }
 }
 
 // Adam (bias-corrected) on the FP32 master parameters; refreshes their BF16 copies

@@ -142,7 +142,7 @@ int backward(wsn_t w, const float *t, const float *mask, int batch, float *grad,
         gw.M = in; gw.N = out; gw.K = batch;
         gw.out = grad + w->w_off[l];
         if ((rc = gemm<wsn::EPI_STORE>(w, gw, st))) return rc;
-        wsn::column_sum_kernel<<<(out + 127) / 128, 128, 0, st>>>(gcur, batch, out, grad + w->b_off[l]);
+        wsn::column_sum_kernel<<<(out + 31) / 32, 256, 0, st>>>(gcur, batch, out, grad + w->b_off[l]);
         WCK(cudaGetLastError(), "column sum launch");
         if (l > 0) {                            // g_prev = (g W^T) * GELU'(pre)
             wsn::Gemm ga{};
