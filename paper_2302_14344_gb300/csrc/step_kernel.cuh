@@ -245,14 +245,17 @@ __device__ __noinline__ void grid_barrier(unsigned *count, unsigned *gen, int *e
     __syncthreads();
 }
 
+// Warps are numbered block-interleaved (warp k of block b is k * blocks + b): per-subsystem
+// work (one warp each, FP64-bound in the setup and the recovery) then spreads over one warp
+// per block, i.e. over the SMs and their FP64 pipes, instead of filling the first blocks.
 struct GridDist {
     int tid, nthreads, warp, nwarps;
     unsigned *count, *gen;
     int *err;
     __device__ __forceinline__ GridDist(unsigned *c, unsigned *g, int *e)
         : tid(blockIdx.x * blockDim.x + threadIdx.x), nthreads(gridDim.x * blockDim.x),
-          warp((blockIdx.x * blockDim.x + threadIdx.x) >> 5), nwarps((gridDim.x * blockDim.x) >> 5),
-          count(c), gen(g), err(e) {}
+          warp((int)(threadIdx.x >> 5) * (int)gridDim.x + (int)blockIdx.x),
+          nwarps((gridDim.x * blockDim.x) >> 5), count(c), gen(g), err(e) {}
     __device__ __forceinline__ void sync() const
     {
         grid_barrier(count, gen, err, gridDim.x, 20000000000ull);
