@@ -172,7 +172,8 @@ int sim_step(sim_t s, int n_steps);
  * sim_launch_classes lays the simulation out if needed and writes, for each class k <
  * max_classes, five counts at out[5k]: scenes, kernel (0 generic, 1 register-cached, 2
  * grid), lanes per side-row (1, 2 or 4; 8, 16 or 32 for the grid kernel), dynamic shared
- * memory per block in bytes, 0.  Returns the number
+ * memory per block in bytes (for a grid class: its staged D-row buffers at its last launch,
+ * 0 before the first or without staging, see sim_grid_staging), 0.  Returns the number
  * of classes, or a negative SIM_E* code.
  * sim_autotune times, for each class on its own, every kernel variant that is valid for all
  * its scenes (generic with 1, 2 or 4 lanes per side-row, register-cached where the scenes
@@ -225,6 +226,14 @@ int sim_step_learned(sim_t s, struct wsn_s *net, int n_steps);
 /* Scenes with at least `side_rows` side-rows run on the grid kernel (default 8192).  Must be
  * called before the first sim_step (SIM_EINVAL after it, or for side_rows < 1). */
 int sim_grid_threshold(sim_t s, int side_rows);
+
+/* Grid kernel: with enable != 0 (the default) each warp of the warp-per-side-row v-step
+ * stages its D rows in shared memory by bulk asynchronous copies (two stages per warp, the
+ * next row in flight while the current one is used), when that leaves the launch its
+ * blocks per SM; with 0 the rows are read from global memory directly.  The results are
+ * the same either way (the same products in the same order).  Takes effect at the next
+ * sim_step. */
+int sim_grid_staging(sim_t s, int enable);
 
 /* Self-test of the grid barrier's time limit (failure detection without a fault): a
  * cooperative launch of `blocks` blocks (all resident, else SIM_EINVAL) in which every block

@@ -23,6 +23,62 @@ __device__ __forceinline__ F vload(const F *p)
     return *reinterpret_cast<const volatile F *>(p);
 }
 
+// ---- bulk asynchronous copies global -> shared with an mbarrier transaction count
+__device__ __forceinline__ unsigned smem_u32(const void *p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long *b, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_init_fence()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// generic-proxy writes (D of this step) made visible to later bulk copies of this thread
+__device__ __forceinline__ void proxy_fence_global()
+{
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+// one arrival that also expects `bytes`, then the copy of `bytes` (a multiple of 16, both
+// addresses 16-byte aligned) that completes them
+__device__ __forceinline__ void bulk_row_load(void *dst, const void *src, unsigned bytes,
+                                              unsigned long long *bar)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(unsigned long long *bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+
+// wait for the phase `parity` of the barrier to complete; false after limit_ns
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity,
+                                          unsigned long long limit_ns)
+{
+    if (mbar_test(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        for (int k = 0; k < 64; ++k)
+            if (mbar_test(bar, parity)) return true;
+        if (global_ns() - t0 > limit_ns) return false;
+    }
+}
+
 template <typename T, int SPLIT>
 __global__ void __launch_bounds__(SUBADMM_THREADS, 2) grid_step_kernel(StepParams P)
 {
@@ -44,6 +100,19 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 2) grid_step_kernel(StepParam
     T *INVS = V.tb + S.ot_invs, *KF = V.tb + S.ot_kf, *AL = V.tb + S.ot_al;
     T *MU = V.tb + S.ot_mu;
     T *const W0 = V.tb + S.ot_w0, *const W1 = V.tb + S.ot_w1;
+    // staged D rows: two row buffers per warp (dynamic shared memory), each with an mbarrier
+    // that completes when its bulk copy has landed
+    extern __shared__ __align__(128) unsigned char stage_raw[];
+    __shared__ __align__(8) unsigned long long stage_bar[SUBADMM_WARPS][2];
+    const int wl = threadIdx.x >> 5;
+    if (P.grid_stage > 0 && lane == 0) {
+        mbar_init(&stage_bar[wl][0], 1);
+        mbar_init(&stage_bar[wl][1], 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    unsigned ph = 0;            // parity of the next completion of each stage's barrier
+    bool stage_ok = true;       // false after a copy that did not complete in time
     for (int q = d.tid; q < S.ot_lam - S.ot_x; q += d.nthreads) V.tb[S.ot_x + q] = (T)0;
     scene_tables<T>(P, S, V, d);
     d.sync();
@@ -98,6 +167,16 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 2) grid_step_kernel(StepParam
                 r_row = V.row[t]; r_bt = BT[t];
             }
         }
+        // staged rows: every row of the warp starts 16-byte aligned and fits a stage
+        unsigned char *const stg = stage_raw + (size_t)wl * 2 * (size_t)P.grid_stage;
+        bool staged = false;
+        if (P.grid_stage > 0 && rowcache && stage_ok) {
+            const bool fits = r_len == 0 ||
+                              (((size_t)(V.htb + r_drow) & 15) == 0 &&
+                               (r_len + VN - 1) / VN * 16 <= P.grid_stage);
+            staged = __all_sync(0xffffffffu, fits);
+            if (staged && lane == 0) proxy_fence_global();   // D of this step's setup
+        }
         int par = 0, last_par = 0, iters = 0, conv = 0, status = ST_OK;
         bool restart = false;
         double th = 0.0;
@@ -111,7 +190,79 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 2) grid_step_kernel(StepParam
                 // ---- v-step through the affine map x = c + D w; y = beta x - lambda
                 const T *w = par ? W1 : W0;
                 T tpart = (T)0;
-                if (rowcache) {
+                constexpr int CH = VN == 4 ? 6 : 8;     // chunks per lane per pass
+                if (staged) {
+                    // warp per row, the warp's rows in order through two shared-memory stages:
+                    // row k + 2 is copied into row k's stage once the warp has read it, so a
+                    // copy is in flight while a row is used
+                    T own_c = (T)0, own_lam = (T)0, own_y = (T)0;
+                    if (r_len > 0) {
+                        own_c = V.htb[r_coff];
+                        own_lam = LAM[r_row];
+                        own_y = Y[xg + lane * groups];
+                    }
+                    for (int k = 0; k < 2 && k < trips; ++k) {
+                        const int len = __shfl_sync(0xffffffffu, r_len, k);
+                        const int drow = __shfl_sync(0xffffffffu, r_drow, k);
+                        if (lane == 0 && len > 0)
+                            bulk_row_load(stg + (size_t)k * P.grid_stage, V.htb + drow,
+                                          (unsigned)((len + VN - 1) / VN * 16), &stage_bar[wl][k]);
+                    }
+                    for (int k = 0; k < trips; ++k) {
+                        const int s = k & 1;
+                        const int len = __shfl_sync(0xffffffffu, r_len, k);
+                        const int wbk = __shfl_sync(0xffffffffu, r_wb, k);
+                        T acc = (T)0;
+                        if (len > 0 && staged) {
+                            const bool got = __all_sync(0xffffffffu,
+                                                        mbar_wait(&stage_bar[wl][s], (ph >> s) & 1u, 2000000000ull));
+                            ph ^= 1u << s;
+                            if (!got) {
+                                // the copy did not complete: flag the launch (as a barrier
+                                // time-out does, so the grid runs to its end and the step
+                                // reports it) and stop staging rows
+                                if (lane == 0) atomicExch(&G->err, 1);
+                                staged = false;
+                                stage_ok = false;
+                            }
+                            const VT *Ds = reinterpret_cast<const VT *>(stg + (size_t)s * P.grid_stage);
+                            const VT *wv = reinterpret_cast<const VT *>(w + wbk);
+                            // the products and sums of the direct path below, in its order
+                            const int nv = got ? (len + VN - 1) / VN : 0;
+                            for (int base = 0; base < nv; base += CH * 32) {
+                                T a0 = (T)0;
+#pragma unroll
+                                for (int q = 0; q < CH; ++q) {
+                                    const int c = base + lane + 32 * q;
+                                    if (c < nv) a0 = vdot(Ds[c], wv[c], a0);
+                                }
+                                acc += a0;
+                            }
+                        }
+                        __syncwarp();
+                        if (k + 2 < trips) {
+                            const int len2 = __shfl_sync(0xffffffffu, r_len, k + 2);
+                            const int drow2 = __shfl_sync(0xffffffffu, r_drow, k + 2);
+                            if (staged && lane == 0 && len2 > 0)
+                                bulk_row_load(stg + (size_t)s * P.grid_stage, V.htb + drow2,
+                                              (unsigned)((len2 + VN - 1) / VN * 16), &stage_bar[wl][s]);
+                        }
+#pragma unroll
+                        for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                        if (lane == k && r_len > 0) {
+                            const int t = xg + lane * groups;
+                            const T a = acc + own_c;
+                            const T ynew = r_bt * a - own_lam;
+                            if (P.stop_theta) {
+                                const T dy = ynew - own_y;
+                                tpart += dy * dy;
+                            }
+                            YO[t] = own_y;
+                            Y[t] = ynew;
+                            X[t] = a;
+                        }
+                    }
+                } else if (rowcache) {
                     // each lane's own row: c, lambda and the old y, fetched before the sweep
                     T own_c = (T)0, own_lam = (T)0, own_y = (T)0;
                     if (r_len > 0) {
@@ -120,7 +271,6 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 2) grid_step_kernel(StepParam
                         own_y = Y[xg + lane * groups];
                     }
                     // two rows at a time, every D chunk of a pass loaded before any FMA
-                    constexpr int CH = VN == 4 ? 6 : 8;     // chunks per lane per pass
                     for (int k = 0; k < trips; k += 2) {
                         int len[2], drow[2], wb[2];
                         T acc[2];
@@ -180,7 +330,7 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 2) grid_step_kernel(StepParam
                         }
                     }
                 }
-                for (int k = 0; k < (rowcache ? 0 : trips); k += 2) {
+                for (int k = 0; k < (rowcache || staged ? 0 : trips); k += 2) {
                     int tt[2], mm[2];
                     T acc[2];
 #pragma unroll

@@ -38,6 +38,8 @@ struct SceneDesc {
     // thread k: int2 {side-row (-1: idle), leader lane | slot << 5 | group lane << 8 |
     // item << 11}
     int fmap_off[3];
+    // grid kernel: bytes of one staged D row (the longest row, whole 16-byte vectors)
+    int row_bytes;
     int item_g0, list_g0;  // global offsets of the scene's item / list tables
     int nasm, asm_g0;      // assembly slots (constraint indices grouped by kind, -1 = idle)
     int sr_g0, row_g0;     // global offset of the scene's side-rows / rows (z, lambda state)
@@ -141,6 +143,8 @@ struct StepParams {
                            // fallbacks of the learned start
     long long *phase;      // 8 per scene (or null): SM clock cycles per phase, see PHASE_*
     GridScratch *grid;     // grid kernel scratch
+    int grid_stage;        // grid kernel: bytes per staged D row in shared memory (two
+                           // stages per warp, filled by bulk copies), 0: rows read directly
     int nscenes;           // scenes of this launch
     int n_steps;
     double h, g0, g1, g2, gamma, rho, tol, theta_th;

@@ -101,6 +101,7 @@ struct sim_s {
     std::vector<int> sc_fmap_ok;   // per scene: bit si set if the thread map for 2^si lanes exists
     int smem_full = 0;             // dynamic shared memory a block may use
     int grid_side_rows = kGridSideRows;
+    int grid_staging = 1;          // grid kernel: stage D rows in shared memory by bulk copies
     // graph replay of sim_step
     bool use_graph = false;
     int graph_steps = 0;
@@ -566,6 +567,7 @@ int finalize(sim_t s)
         // vectors.
         auto tal = [&](long long v) { return (v + vn - 1) / vn * vn; };
         long long sd = 0, st = 0, sh = 0;
+        S.row_bytes = 0;
         for (int i = 0; i < S.nsub; ++i) {
             SubDesc &u = s->sdesc[S.sub0 + i];
             if (u.m > SUBADMM_MAXM)
@@ -584,6 +586,7 @@ int finalize(sim_t s)
             // lanes of a warp read at once fall in different shared-memory banks
             u.ldd = ((u.mpad / vn) % 2 == 0) ? u.mpad + vn : u.mpad;
             u.ot_D = (int)sh; sh = tal(sh + (long long)u.m * u.ldd);
+            S.row_bytes = std::max(S.row_bytes, (u.m + vn - 1) / vn * 16);
             u.ot_c = (int)sh; sh = tal(sh + u.m);
             if (sd > (1LL << 30) || st + sh > (1LL << 30)) return fail(s, SIM_EINVAL, "scene too large");
         }
@@ -1113,19 +1116,39 @@ KernFn grid_kernel_for(bool mixed, int split)
 
 // One cooperative launch per scene of a grid class, in turn on `st`, each after zeroing the
 // grid scratch; as many blocks as fit on the GPU at once.
-int launch_grid_class(sim_t s, const LaunchClass &c, StepParams P, cudaStream_t st, int split)
+int launch_grid_class(sim_t s, LaunchClass &c, StepParams P, cudaStream_t st, int split)
 {
     KernFn kf = grid_kernel_for(s->opt.precision == SIM_MIXED, split);
     int per_sm = 0, sms = 0;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kf, SUBADMM_THREADS, 0), "occupancy");
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->opt.device), "attribute");
     const int blocks = std::max(1, per_sm * sms);
+    c.max_smem = 0;                 // reported: the largest stage buffers of the class's launches
     for (size_t i = 0; i < c.scenes.size(); ++i) {
+        // D rows staged in shared memory by bulk copies (two stages per warp, the warp-per-row
+        // v-step only) when that keeps the blocks per SM of the launch without it
+        const SceneDesc &S = s->scenes[c.scenes[i]];
+        int stage = (s->grid_staging && split == 32) ? S.row_bytes : 0;
+        size_t dyn = (size_t)stage * 2 * SUBADMM_WARPS;
+        if (stage > 0) {
+            int per_sm_dyn = 0;
+            if (cudaFuncSetAttribute((const void *)kf, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)dyn) != cudaSuccess ||
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_dyn, kf, SUBADMM_THREADS, dyn) !=
+                    cudaSuccess ||
+                per_sm_dyn < per_sm) {
+                cudaGetLastError();
+                stage = 0;
+                dyn = 0;
+            }
+        }
         CK(cudaMemsetAsync(s->d_grid, 0, sizeof(GridScratch), st), "grid scratch");
         P.scene_ids = s->d_scene_ids + c.ids_off + (int)i;
         P.nscenes = 1;
+        P.grid_stage = stage;
+        c.max_smem = std::max(c.max_smem, (int)dyn);
         void *args[] = {&P};
-        CK(cudaLaunchCooperativeKernel((const void *)kf, dim3(blocks), dim3(SUBADMM_THREADS), args, 0, st),
+        CK(cudaLaunchCooperativeKernel((const void *)kf, dim3(blocks), dim3(SUBADMM_THREADS), args, dyn, st),
            "grid kernel launch");
     }
     return SIM_OK;
@@ -1139,7 +1162,7 @@ int launch_classes(sim_t s, StepParams P, cudaStream_t base)
     // grid classes first, alone on the GPU (their blocks must all be resident at once)
     std::vector<int> block_classes;
     for (int k = 0; k < (int)s->classes.size(); ++k) {
-        const LaunchClass &c = s->classes[k];
+        LaunchClass &c = s->classes[k];
         if (c.grid) {
             const int rc = launch_grid_class(s, c, P, base, c.split);
             if (rc) return rc;
@@ -1538,6 +1561,13 @@ int sim_grid_threshold(sim_t s, int side_rows)
     if (s->finalized) return fail(s, SIM_EINVAL, "the layout is fixed after the first sim_step");
     if (side_rows < 1) return fail(s, SIM_EINVAL, "side_rows must be >= 1");
     s->grid_side_rows = side_rows;
+    return SIM_OK;
+}
+
+int sim_grid_staging(sim_t s, int enable)
+{
+    if (!s) return SIM_EINVAL;
+    s->grid_staging = enable ? 1 : 0;
     return SIM_OK;
 }
 

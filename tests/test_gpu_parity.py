@@ -457,6 +457,58 @@ def test_small_fem_beam_fp64_fixed_iterations(sa, grid):
         _compare_states(sim, orcs, TOL)
 
 
+def _staged_and_direct(sa, p, prec):
+    a = sa.Simulation(p, precision=prec, grid_side_rows=1)
+    b = sa.Simulation(p, precision=prec, grid_side_rows=1)
+    b.grid_staging(False)
+    (ca,), (cb,) = a.launch_classes(), b.launch_classes()
+    assert ca["cached"] == 2 and ca["split"] == 32 and cb["split"] == 32   # warp per side-row
+    return a, b
+
+
+def _assert_staged(a, b):
+    (ca,), (cb,) = a.launch_classes(), b.launch_classes()
+    assert ca["smem_bytes"] > 0 and cb["smem_bytes"] == 0      # staged / direct
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_grid_staged_rows_equal_direct_rows(sa, precision):
+    """The grid kernel's v-step with D rows staged in shared memory by bulk copies gives the
+    same bits as the direct reads (same products, same order) over three steps of a beam of
+    three slabs without the arm (warp per side-row), and matches the oracle (FP64)."""
+    prec = sa.SIM_FP64 if precision == "fp64" else sa.SIM_MIXED
+    p = _small_beam(ny=8, nz=8, with_gripper=False, tol_primal=-1, max_iters=40)
+    a, b = _staged_and_direct(sa, p, prec)
+    orcs = [oracle.OracleScene(sc, p.options) for sc in p.scenes] if precision == "fp64" else []
+    for _ in range(3):
+        a.step(1)
+        b.step(1)
+        for x, y in zip(_batch_state(a, 1), _batch_state(b, 1)):
+            assert np.array_equal(x, y)
+        for o in orcs:
+            o.step()
+        if orcs:
+            _compare(a, orcs, p)
+    _assert_staged(a, b)
+
+
+def test_grid_staged_rows_several_per_warp(sa):
+    """Nine slabs of 10 x 10 nodes: more side-rows than warps in the grid, so a warp stages
+    several rows per iteration through its two buffers (each reused, its barrier phase
+    flipping every use); staged and direct reads give the same bits over two steps."""
+    p = _small_beam(ny=10, nz=10, planes=21, slabs=9, with_gripper=False, tol_primal=-1,
+                    max_iters=30)
+    a, b = _staged_and_direct(sa, p, sa.SIM_MIXED)
+    # more than two rows for some warps: 8 warps x 2 blocks x 152 SMs = 2432 warps
+    assert a.sizes()["side_rows"] > 2 * 2432
+    for _ in range(2):
+        a.step(1)
+        b.step(1)
+        for x, y in zip(_batch_state(a, 1), _batch_state(b, 1)):
+            assert np.array_equal(x, y)
+    _assert_staged(a, b)
+
+
 def test_grid_kernel_batched_scenes_fp64(sa):
     """Several uneven scenes, each run over the whole GPU in turn (the grid kernel forced
     for every scene), against the oracle; two steps in one call."""
