@@ -484,7 +484,10 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 2) grid_step_kernel(StepParam
                 continue;
             }
             if (lead) G->chk = 0ull;
-            recover_v<T>(P, S, V, last_par ? W1 : W0, d);
+            // the warp's stage buffers (idle outside the v-step) hold the solves' vector
+            recover_v<T>(P, S, V, last_par ? W1 : W0, d,
+                         P.grid_stage > 0 ? reinterpret_cast<T *>(stg) : nullptr,
+                         P.grid_stage > 0 ? 2 * P.grid_stage / (int)sizeof(T) : 0);
             d.sync();
             if (MIXED && conv && primal_stop && status == ST_OK) {
                 // FP64 primal residual max |J v - z|; on a miss, refine c by the FP64 - FP32

@@ -422,6 +422,52 @@ __device__ void env_forward_cols(const F *LT, F *X, int n, int ldx, int nrhs, co
     }
 }
 
+// x[q ldx] -= a[q lda] f for q0 <= q < q1 (warp, lanes across q).  Whole passes of 8 x 32
+// entries load their a and x before writing any x (x and a may share a type, so the
+// compiler could not move a load of a above a store to x, and each entry would cost a
+// round trip); the remainder takes one more such pass if it is long, else one pass of 2 x 32
+// or 32.  The passes are warp-uniform: a short range issues no predicated-off
+// instructions (an FP64 one occupies its pipe all the same).
+template <int K, typename F, typename G>
+__device__ __forceinline__ void axpy_pass(F *x, int ldx, const G *a, int lda, int q, int q1, F f)
+{
+    G av[K];
+    F xv[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int qq = q + 32 * k;
+        av[k] = qq < q1 ? a[qq * lda] : (G)0;
+        xv[k] = qq < q1 ? x[qq * ldx] : (F)0;
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int qq = q + 32 * k;
+        if (qq < q1) x[qq * ldx] = xv[k] - (F)av[k] * f;
+    }
+}
+
+// (indices: q lda and q ldx stay below 2^31 for the supported sizes, n, m <= 2048)
+template <typename F, typename G>
+__device__ __forceinline__ void warp_axpy_neg(F *x, int ldx, const G *a, int lda, int q0, int q1,
+                                              F f)
+{
+    const int lane = threadIdx.x & 31;
+    if (q1 - q0 <= 32) {                     // one entry per lane at most
+        const int q = q0 + lane;
+        if (q < q1) x[q * ldx] -= (F)a[q * lda] * f;
+        return;
+    }
+    int base = q0;
+    for (; base + 256 <= q1; base += 256) axpy_pass<8>(x, ldx, a, lda, base + lane, q1, f);
+    if (q1 - base > 64) {                    // a long range's remainder in one pass
+        axpy_pass<8>(x, ldx, a, lda, base + lane, q1, f);
+        return;
+    }
+    // at most 64 entries left
+    if (q1 - base > 32) axpy_pass<2>(x, ldx, a, lda, base + lane, q1, f);
+    else if (q1 > base) axpy_pass<1>(x, ldx, a, lda, base + lane, q1, f);
+}
+
 // y <- L^-1 y for one vector (stride ldy), column by column: lanes update the rows below p
 template <typename F>
 __device__ void env_forward_vec(const F *LT, F *y, int n, int ldy, const int *lastr)
@@ -431,7 +477,7 @@ __device__ void env_forward_vec(const F *LT, F *y, int n, int ldy, const int *la
         const F yp = y[p * ldy] * LT[p * n + p];
         __syncwarp();
         if (lane == 0) y[p * ldy] = yp;
-        for (int q = p + 1 + lane; q <= lastr[p]; q += 32) y[q * ldy] -= LT[q * n + p] * yp;
+        warp_axpy_neg(y, ldy, LT + p, n, p + 1, lastr[p] + 1, yp);
         __syncwarp();
     }
 }
@@ -780,14 +826,14 @@ __device__ __forceinline__ void warp_chol_solve(const T *LT, T *s, int n, const 
         const T yp = s[p] * LT[p * n + p];
         __syncwarp();
         if (lane == 0) s[p] = yp;
-        for (int q = p + 1 + lane; q <= e.lastr[p]; q += 32) s[q] -= LT[q * n + p] * yp;
+        warp_axpy_neg(s, 1, LT + p, n, p + 1, e.lastr[p] + 1, yp);
         __syncwarp();
     }
     for (int p = n - 1; p >= 0; --p) {         // L^T v = y
         const T vp = s[p] * LT[p * n + p];
         __syncwarp();
         if (lane == 0) s[p] = vp;
-        for (int q = e.env[p] + lane; q < p; q += 32) s[q] -= LT[p * n + q] * vp;
+        warp_axpy_neg(s, 1, LT + p * n, 1, e.env[p], p, vp);
         __syncwarp();
     }
 }
@@ -797,9 +843,11 @@ __device__ __forceinline__ void warp_chol_solve(const T *LT, T *s, int n, const 
 // solves.  With an FP32 factor: a solve, then one step of iterative refinement with the
 // residual b + J^T w - K v formed in FP64 from A (kept in od_L) and J:
 // K v = A v + beta J^T (J v).
+// `fast` (may be null): per-warp shared memory of fast_len T values; the FP32 solves of a
+// subsystem with n <= fast_len run on a copy there instead of on the global scratch vector.
 template <typename T, typename Dist>
 __device__ void recover_v(const StepParams &P, const SceneDesc &S, const View<T> &V, const T *w,
-                          const Dist &d)
+                          const Dist &d, T *fast = nullptr, int fast_len = 0)
 {
     constexpr bool MIXED = sizeof(T) == 4;
     const int lane = threadIdx.x & 31;
@@ -820,20 +868,20 @@ __device__ void recover_v(const StepParams &P, const SceneDesc &S, const View<T>
                 const double yp = v[p] * idg[p];
                 __syncwarp();
                 if (lane == 0) v[p] = yp;
-                for (int q = p + 1 + lane; q <= e.lastr[p]; q += 32) v[q] -= Lf[q * n + p] * yp;
+                warp_axpy_neg(v, 1, Lf + p, n, p + 1, e.lastr[p] + 1, yp);
                 __syncwarp();
             }
             for (int p = n - 1; p >= 0; --p) {     // L^T v = y
                 const double vp = v[p] * idg[p];
                 __syncwarp();
                 if (lane == 0) v[p] = vp;
-                for (int q = e.env[p] + lane; q < p; q += 32) v[q] -= Lf[p * n + q] * vp;
+                warp_axpy_neg(v, 1, Lf + p * n, 1, e.env[p], p, vp);
                 __syncwarp();
             }
             continue;
         }
         const T *LT = V.stb + u.ot_L;
-        T *s = V.stb + u.ot_s;
+        T *s = (fast && n <= fast_len) ? fast : V.stb + u.ot_s;
         double *rhs = idg;                          // (unused by the mixed factor)
         double *t = V.sdb + u.od_t;
         const double beta = V.db[S.od_beta + i];
