@@ -228,8 +228,8 @@ int sim_step_learned(sim_t s, struct wsn_s *net, int n_steps);
 int sim_grid_threshold(sim_t s, int side_rows);
 
 /* Grid kernel: with enable != 0 (the default) each warp of the warp-per-side-row v-step
- * stages its D rows in shared memory by bulk asynchronous copies (two stages per warp, the
- * next row in flight while the current one is used), when that leaves the launch its
+ * stages its D rows in shared memory by bulk asynchronous copies (two stages per warp,
+ * the next row in flight while the current one is used), when that leaves the launch its
  * blocks per SM; with 0 the rows are read from global memory directly.  The results are
  * the same either way (the same products in the same order).  Takes effect at the next
  * sim_step. */

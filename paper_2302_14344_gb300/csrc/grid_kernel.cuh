@@ -100,14 +100,14 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 2) grid_step_kernel(StepParam
     T *INVS = V.tb + S.ot_invs, *KF = V.tb + S.ot_kf, *AL = V.tb + S.ot_al;
     T *MU = V.tb + S.ot_mu;
     T *const W0 = V.tb + S.ot_w0, *const W1 = V.tb + S.ot_w1;
-    // staged D rows: two row buffers per warp (dynamic shared memory), each with an mbarrier
-    // that completes when its bulk copy has landed
+    // staged D rows: grid_nstage row buffers per warp (dynamic shared memory), each with an
+    // mbarrier that completes when its bulk copy has landed
     extern __shared__ __align__(128) unsigned char stage_raw[];
-    __shared__ __align__(8) unsigned long long stage_bar[SUBADMM_WARPS][2];
+    __shared__ __align__(8) unsigned long long stage_bar[SUBADMM_WARPS][4];
     const int wl = threadIdx.x >> 5;
+    const int nst = P.grid_nstage;
     if (P.grid_stage > 0 && lane == 0) {
-        mbar_init(&stage_bar[wl][0], 1);
-        mbar_init(&stage_bar[wl][1], 1);
+        for (int k = 0; k < nst; ++k) mbar_init(&stage_bar[wl][k], 1);
         mbar_init_fence();
     }
     __syncthreads();
@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 2) grid_step_kernel(StepParam
             }
         }
         // staged rows: every row of the warp starts 16-byte aligned and fits a stage
-        unsigned char *const stg = stage_raw + (size_t)wl * 2 * (size_t)P.grid_stage;
+        unsigned char *const stg = stage_raw + (size_t)wl * nst * (size_t)P.grid_stage;
         bool staged = false;
         if (P.grid_stage > 0 && rowcache && stage_ok) {
             const bool fits = r_len == 0 ||
@@ -192,16 +192,16 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 2) grid_step_kernel(StepParam
                 T tpart = (T)0;
                 constexpr int CH = VN == 4 ? 6 : 8;     // chunks per lane per pass
                 if (staged) {
-                    // warp per row, the warp's rows in order through two shared-memory stages:
-                    // row k + 2 is copied into row k's stage once the warp has read it, so a
-                    // copy is in flight while a row is used
+                    // warp per row, the warp's rows in order through nst shared-memory stages:
+                    // row k + nst is copied into row k's stage once the warp has read it, so
+                    // nst - 1 copies are in flight while a row is used
                     T own_c = (T)0, own_lam = (T)0, own_y = (T)0;
                     if (r_len > 0) {
                         own_c = V.htb[r_coff];
                         own_lam = LAM[r_row];
                         own_y = Y[xg + lane * groups];
                     }
-                    for (int k = 0; k < 2 && k < trips; ++k) {
+                    for (int k = 0; k < nst && k < trips; ++k) {
                         const int len = __shfl_sync(0xffffffffu, r_len, k);
                         const int drow = __shfl_sync(0xffffffffu, r_drow, k);
                         if (lane == 0 && len > 0)
@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 2) grid_step_kernel(StepParam
                                           (unsigned)((len + VN - 1) / VN * 16), &stage_bar[wl][k]);
                     }
                     for (int k = 0; k < trips; ++k) {
-                        const int s = k & 1;
+                        const int s = k % nst;
                         const int len = __shfl_sync(0xffffffffu, r_len, k);
                         const int wbk = __shfl_sync(0xffffffffu, r_wb, k);
                         T acc = (T)0;
@@ -240,9 +240,9 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 2) grid_step_kernel(StepParam
                             }
                         }
                         __syncwarp();
-                        if (k + 2 < trips) {
-                            const int len2 = __shfl_sync(0xffffffffu, r_len, k + 2);
-                            const int drow2 = __shfl_sync(0xffffffffu, r_drow, k + 2);
+                        if (k + nst < trips) {
+                            const int len2 = __shfl_sync(0xffffffffu, r_len, k + nst);
+                            const int drow2 = __shfl_sync(0xffffffffu, r_drow, k + nst);
                             if (staged && lane == 0 && len2 > 0)
                                 bulk_row_load(stg + (size_t)s * P.grid_stage, V.htb + drow2,
                                               (unsigned)((len2 + VN - 1) / VN * 16), &stage_bar[wl][s]);
@@ -487,7 +487,7 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 2) grid_step_kernel(StepParam
             // the warp's stage buffers (idle outside the v-step) hold the solves' vector
             recover_v<T>(P, S, V, last_par ? W1 : W0, d,
                          P.grid_stage > 0 ? reinterpret_cast<T *>(stg) : nullptr,
-                         P.grid_stage > 0 ? 2 * P.grid_stage / (int)sizeof(T) : 0);
+                         P.grid_stage > 0 ? nst * P.grid_stage / (int)sizeof(T) : 0);
             d.sync();
             if (MIXED && conv && primal_stop && status == ST_OK) {
                 // FP64 primal residual max |J v - z|; on a miss, refine c by the FP64 - FP32

@@ -143,8 +143,9 @@ struct StepParams {
                            // fallbacks of the learned start
     long long *phase;      // 8 per scene (or null): SM clock cycles per phase, see PHASE_*
     GridScratch *grid;     // grid kernel scratch
-    int grid_stage;        // grid kernel: bytes per staged D row in shared memory (two
-                           // stages per warp, filled by bulk copies), 0: rows read directly
+    int grid_stage;        // grid kernel: bytes per staged D row in shared memory (filled
+                           // by bulk copies), 0: rows read directly
+    int grid_nstage;       // grid kernel: staged rows per warp (2 to 4)
     int nscenes;           // scenes of this launch
     int n_steps;
     double h, g0, g1, g2, gamma, rho, tol, theta_th;

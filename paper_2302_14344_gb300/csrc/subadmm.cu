@@ -1125,27 +1125,33 @@ int launch_grid_class(sim_t s, LaunchClass &c, StepParams P, cudaStream_t st, in
     const int blocks = std::max(1, per_sm * sms);
     c.max_smem = 0;                 // reported: the largest stage buffers of the class's launches
     for (size_t i = 0; i < c.scenes.size(); ++i) {
-        // D rows staged in shared memory by bulk copies (two stages per warp, the warp-per-row
-        // v-step only) when that keeps the blocks per SM of the launch without it
+        // D rows staged in shared memory by bulk copies (the warp-per-row v-step only), two
+        // stages per warp if that keeps the blocks per SM of the launch without them.  (The
+        // kernel takes up to 4; on the FEM beam 3 and 4 measured slower than 2: the larger
+        // shared memory leaves less L1 for the w that each row is multiplied with.)
         const SceneDesc &S = s->scenes[c.scenes[i]];
         int stage = (s->grid_staging && split == 32) ? S.row_bytes : 0;
-        size_t dyn = (size_t)stage * 2 * SUBADMM_WARPS;
-        if (stage > 0) {
+        int nst = 0;
+        size_t dyn = 0;
+        for (int k = 2; k >= 2 && stage > 0 && nst == 0; --k) {
+            const size_t want = (size_t)stage * k * SUBADMM_WARPS;
             int per_sm_dyn = 0;
             if (cudaFuncSetAttribute((const void *)kf, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)dyn) != cudaSuccess ||
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_dyn, kf, SUBADMM_THREADS, dyn) !=
-                    cudaSuccess ||
-                per_sm_dyn < per_sm) {
-                cudaGetLastError();
-                stage = 0;
-                dyn = 0;
+                                     (int)want) == cudaSuccess &&
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_dyn, kf, SUBADMM_THREADS, want) ==
+                    cudaSuccess &&
+                per_sm_dyn >= per_sm) {
+                nst = k;
+                dyn = want;
             }
+            cudaGetLastError();
         }
+        if (nst == 0) stage = 0;
         CK(cudaMemsetAsync(s->d_grid, 0, sizeof(GridScratch), st), "grid scratch");
         P.scene_ids = s->d_scene_ids + c.ids_off + (int)i;
         P.nscenes = 1;
         P.grid_stage = stage;
+        P.grid_nstage = nst;
         c.max_smem = std::max(c.max_smem, (int)dyn);
         void *args[] = {&P};
         CK(cudaLaunchCooperativeKernel((const void *)kf, dim3(blocks), dim3(SUBADMM_THREADS), args, dyn, st),
