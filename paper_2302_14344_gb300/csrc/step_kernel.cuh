@@ -212,31 +212,32 @@ __device__ __forceinline__ unsigned long long global_ns()
     return t;
 }
 
-// Barrier over the `expected` blocks of a cooperative launch.  Thread 0 of each block
-// arrives on a counter; the last arrival resets it and advances the generation the others
-// wait on.  A wait longer than limit_ns, or an error raised by another block, sets / sees
-// the error flag and returns at once, here and at every later barrier, so the grid always
-// runs to its end.
+// Barrier over the `expected` blocks of a cooperative launch.  Thread 0 of each block adds
+// one to a counter that only grows (zeroed before the launch); the barrier of round r is
+// complete when the counter reaches (r + 1) expected, which each block reads off its own
+// arrival (arrivals of round r fall in [r expected, (r + 1) expected)).  The waiters poll
+// the counter itself, so the last arrival completes the barrier with its one atomic.  A
+// wait longer than limit_ns, or an error raised by another block, sets / sees the error
+// flag and returns at once, here and at every later barrier, so the grid always runs to its
+// end.  (`gen` is unused: kept for the scratch layout.)
 __device__ __noinline__ void grid_barrier(unsigned *count, unsigned *gen, int *err,
                                           unsigned expected, unsigned long long limit_ns)
 {
+    (void)gen;
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned *vgen = gen;
+        volatile unsigned *vcount = count;
         volatile int *verr = err;
         if (!*verr) {
-            const unsigned my = *vgen;
             __threadfence();
-            if (atomicAdd(count, 1u) == expected - 1) {
-                atomicExch(count, 0u);
-                __threadfence();
-                atomicAdd(gen, 1u);
-            } else {
+            const unsigned my = atomicAdd(count, 1u);
+            const unsigned target = (my / expected + 1u) * expected;
+            if ((int)(*vcount - target) < 0) {
                 const unsigned long long t0 = global_ns();
-                while (*vgen == my) {
+                while ((int)(*vcount - target) < 0) {
                     if (*verr) break;
                     if (global_ns() - t0 > limit_ns) { atomicExch(err, 1); break; }
-                    __nanosleep(64);
+                    __nanosleep(32);
                 }
             }
             __threadfence();
