@@ -161,24 +161,39 @@ def kernel_source_hash() -> str:
     return h.hexdigest()
 
 
-def recorded_traffic(steps_per_launch: int):
-    """DRAM bytes per launch from the committed ncu summary, scaled to this launch length
-    (the per-step traffic is constant: descriptors and states are re-read every step), or
-    None when the kernel sources changed since the capture."""
-    path = os.path.join(ROOT, "profiles", "step_kernel_robots64_traffic.md")
+def _recorded(name: str):
+    """key: value lines of a committed ncu summary, or None when it is missing or the kernel
+    sources changed since its capture."""
     try:
-        txt = open(path).read()
+        txt = open(os.path.join(ROOT, "profiles", name)).read()
     except OSError:
         return None
     vals = {}
     for line in txt.splitlines():
-        if ":" in line and line.split(":")[0] in ("traffic_bytes_per_launch", "steps_per_launch",
-                                                 "source_sha256"):
+        if ":" in line and not line.startswith(" "):
             k, v = line.split(":", 1)
             vals[k.strip()] = v.strip()
-    if vals.get("source_sha256") != kernel_source_hash():
+    return vals if vals.get("source_sha256") == kernel_source_hash() else None
+
+
+def recorded_traffic(steps_per_launch: int):
+    """DRAM bytes per launch of the step kernel (robots) from the committed ncu summary,
+    scaled to this launch length (the per-step traffic is constant: descriptors and states
+    are re-read every step), or None."""
+    vals = _recorded("step_kernel_robots64_traffic.md")
+    if not vals:
         return None
     return float(vals["traffic_bytes_per_launch"]) / float(vals["steps_per_launch"]) * steps_per_launch
+
+
+def recorded_traffic_fem(iters_per_launch: float):
+    """DRAM bytes per launch of the grid kernel (FEM beam): the summary's bytes per iteration
+    (D streamed once per iteration dominates) times this run's iterations per launch, or
+    None."""
+    vals = _recorded("grid_step_kernel_fem_beam_traffic.md")
+    if not vals:
+        return None
+    return float(vals["traffic_bytes_per_iteration"]) * iters_per_launch
 
 
 def measured_peaks():
@@ -468,9 +483,11 @@ def main():
         d_bytes = float(sum(w[2] for w in work)) * tsize
         hbm = measured_peaks().get("hbm_gbs")
         achieved_gbs = d_bytes * total_iters / (t_ms / 1e3) / 1e9
+        launches = (K + spl - 1) // spl
         roofline = {"bound": "hbm", "achieved": achieved_gbs,
                     "peak": hbm if hbm else 6800.0, "unit": "GB/s",
-                    "frac": achieved_gbs / (hbm if hbm else 6800.0), "traffic": None,
+                    "frac": achieved_gbs / (hbm if hbm else 6800.0),
+                    "traffic": recorded_traffic_fem(total_iters / launches),
                     "note": f"algorithmic bytes: D of every subsystem once per iteration "
                             f"({d_bytes / 1e6:.1f} MB) x iterations / whole-step time (setup and "
                             f"exit included, so a lower bound on the stream rate); peak = "
