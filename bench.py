@@ -487,14 +487,18 @@ def main():
         roofline = {"bound": "hbm", "achieved": achieved_gbs,
                     "peak": hbm if hbm else 6800.0, "unit": "GB/s",
                     "frac": achieved_gbs / (hbm if hbm else 6800.0),
-                    "traffic": recorded_traffic_fem(total_iters / launches),
+                    "traffic": (recorded_traffic_fem(total_iters / launches)
+                                if args.form == "mixed" else None),
                     "note": f"algorithmic bytes: D of every subsystem once per iteration "
                             f"({d_bytes / 1e6:.1f} MB) x iterations / whole-step time (setup and "
                             f"exit included, so a lower bound on the stream rate); peak = "
                             f"{'measured copy bandwidth' if hbm else 'fallback'}"}
     else:
         roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": recorded_traffic(spl),
+                    "frac": achieved / peak,
+                    # the recorded capture is of the 64-robot batch in the mixed form
+                    "traffic": (recorded_traffic(spl) if args.workload == "robots" and
+                                args.robots == 64 and args.form == "mixed" else None),
                     "note": f"{pipe} non-tensor pipe (iterations; the mixed form's per-step "
                             f"setup is FP64); peak = 152 SMs x lanes x 2 flops x 2.07 GHz; "
                             f"algorithmic flops of the triangular-solve form, "
