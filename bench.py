@@ -360,6 +360,35 @@ def whole_job_rate(world: int, steps: int, t_ms_max: float) -> float:
     return world * steps / (t_ms_max / 1e3)
 
 
+def time_refactor_every_step(subadmm, p, stream, dev, local, flush, steps: int = 3):
+    """The plain FP64 form with every block factorised again every step (Algorithm 1 as
+    stated; by default a constant block's factor, the same matrix, is computed once):
+    `steps` steps after one warm-up step, one launch each, L2 flushed before each."""
+    import torch
+    sim = subadmm.Simulation(p, stream=stream.cuda_stream, device=local,
+                             precision=subadmm.SIM_FP64)
+    sim.keep_factors(False)
+    sim.step(1)
+    sim.sync()
+    sim.iteration_stats()   # clear counters
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    torch.cuda.synchronize(dev)
+    for a, b in ev:
+        flush.zero_()
+        a.record(stream)
+        sim.step(1)
+        b.record(stream)
+    torch.cuda.synchronize(dev)
+    t = float(sum(a.elapsed_time(b) for a, b in ev))
+    st = sim.iteration_stats()
+    sim.close()
+    return {"value": steps / (t / 1e3), "unit": "steps/s", "ms_per_step": t / steps,
+            "steps": steps, "mean_iterations": st["total_iters"] / max(st["scene_steps"], 1),
+            "note": "every block refactorised every step (sim_keep_factors(0)); timed segment "
+                    "right after the first step, heuristic kernel variant, no graph"}
+
+
 def time_form(subadmm, p, precision, args, stream, dev, local, dist, flush, sample_clocks):
     """Warm-up W steps, then K timed steps in launches of ``--steps-per-launch`` steps (the
     scenes are independent, so one launch advances every scene by that many steps without a
@@ -514,6 +543,9 @@ def main():
                    "not_converged": st2["not_converged"],
                    "chosen_over_plain": (world * K / (t_ms / 1e3)) / (world * K / (t2 / 1e3))}
         sim2.close()
+    refactor = None
+    if args.workload == "fem_beam" and not args.no_compare and world == 1:
+        refactor = time_refactor_every_step(subadmm, p, stream, dev, local, flush)
 
     learned_line = None
     if args.workload == "robots" and not args.no_learned and world == 1:
@@ -570,6 +602,7 @@ def main():
                            "scene_steps": stats["scene_steps"]},
             "interface_updates_per_s": n_if * total_iters * world / (t_ms / 1e3),
             "plain_fp64": compare,
+            "plain_fp64_refactor_every_step": refactor,
             "learned_warm_start": learned_line,
             "roofline": roofline,
             "e2e": e2e,

@@ -235,6 +235,14 @@ int sim_grid_threshold(sim_t s, int side_rows);
  * sim_step. */
 int sim_grid_staging(sim_t s, int enable);
 
+/* A linear block's K_i = A_i + beta_i J_i^T J_i is constant (Sec. II-B: its A_i and its
+ * node-selector rows are), so by default (enable != 0) its factor, W and D are computed at
+ * its first step and kept.  With 0 every step factorises every block again, as Algorithm 1
+ * states it: the same matrix, so the results agree to rounding (with a kept factor
+ * g = L^-1 b is formed by the single-vector solve, otherwise as the last column of W).
+ * Takes effect at the next sim_step. */
+int sim_keep_factors(sim_t s, int enable);
+
 /* Self-test of the grid barrier's time limit (failure detection without a fault): a
  * cooperative launch of `blocks` blocks (all resident, else SIM_EINVAL) in which every block
  * waits once at a barrier that needs `expected` arrivals, for at most limit_s seconds

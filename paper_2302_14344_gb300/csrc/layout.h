@@ -130,6 +130,7 @@ struct StepParams {
     double *nodes;         // 6 doubles per node of linear blocks (state in and out)
     const int *ipool;      // integer constant data (sparse K of linear blocks, profiles)
     int *subflag;          // per subsystem: bit 0 its kept factor is valid, bit 1 it is FP64
+    int keep_factors;      // 0: refactor constant blocks every step too (Algorithm 1 literally)
     double *vhat;          // per DOF
     double *lam;           // per row: lambda of the last step (warm start state)
     const double *lam0;    // per row: learned initial lambda of this step (NULL: not learned)

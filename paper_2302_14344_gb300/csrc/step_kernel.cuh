@@ -333,11 +333,12 @@ __device__ __forceinline__ SubEnv sub_env(const StepParams &P, const SubDesc &u)
 }
 
 // A constant K_i whose factor from an earlier step is still held: in the workspace (it
-// outlives the launch) or in shared memory from an earlier step of this launch.
+// outlives the launch) or in shared memory from an earlier step of this launch.  With
+// keep_factors 0 every step refactors (the same matrix; results agree to rounding).
 __device__ __forceinline__ bool factor_kept(const StepParams &P, const SceneDesc &S,
                                             const SubDesc &u, int gsub, int step)
 {
-    return u.cst && (step > 0 || S.sub_global) && (P.subflag[gsub] & 1);
+    return P.keep_factors && u.cst && (step > 0 || S.sub_global) && (P.subflag[gsub] & 1);
 }
 
 // K += beta J^T J on the lower triangle (row-major n x n), one J row at a time over the

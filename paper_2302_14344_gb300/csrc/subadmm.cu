@@ -102,6 +102,7 @@ struct sim_s {
     int smem_full = 0;             // dynamic shared memory a block may use
     int grid_side_rows = kGridSideRows;
     int grid_staging = 1;          // grid kernel: stage D rows in shared memory by bulk copies
+    int keep_factors = 1;          // keep the factors of constant blocks across steps
     // graph replay of sim_step
     bool use_graph = false;
     int graph_steps = 0;
@@ -1075,6 +1076,7 @@ StepParams step_params(const sim_t s, int n_steps)
     P.nodes = s->d_nodes;
     P.ipool = s->d_ipool;
     P.subflag = s->d_subflag;
+    P.keep_factors = s->keep_factors;
     P.beta = s->d_beta; P.res = s->d_res; P.stats = s->d_stats; P.phase = s->d_phase;
     P.nscenes = s->nscenes;
     P.n_steps = n_steps;
@@ -1574,6 +1576,13 @@ int sim_grid_staging(sim_t s, int enable)
 {
     if (!s) return SIM_EINVAL;
     s->grid_staging = enable ? 1 : 0;
+    return SIM_OK;
+}
+
+int sim_keep_factors(sim_t s, int enable)
+{
+    if (!s) return SIM_EINVAL;
+    s->keep_factors = enable ? 1 : 0;
     return SIM_OK;
 }
 

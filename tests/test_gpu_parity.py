@@ -457,6 +457,34 @@ def test_small_fem_beam_fp64_fixed_iterations(sa, grid):
         _compare_states(sim, orcs, TOL)
 
 
+@pytest.mark.parametrize("grid", [False, True])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_refactoring_every_step_matches_the_kept_factors(sa, grid, precision):
+    """Constant (linear) blocks keep their factor, W and D across steps by default; with
+    sim_keep_factors(0) every step computes them again, as Algorithm 1 states it.  The
+    matrix is the same; g = L^-1 b comes from the multi-column solve instead of the
+    single-vector one, so the two agree to rounding.  FP64: both match the oracle (which
+    refactors every step) to 1e-9; mixed: they agree with each other to FP32 rounding
+    (1e-5 relative after 30 iterations a step)."""
+    prec = sa.SIM_FP64 if precision == "fp64" else sa.SIM_MIXED
+    p = _small_beam(tol_primal=-1, max_iters=30)
+    a = sa.Simulation(p, precision=prec, grid_side_rows=1 if grid else None)
+    b = sa.Simulation(p, precision=prec, grid_side_rows=1 if grid else None)
+    b.keep_factors(False)
+    orcs = [oracle.OracleScene(sc, p.options) for sc in p.scenes] if precision == "fp64" else []
+    for _ in range(3):
+        a.step(1)
+        b.step(1)
+        for o in orcs:
+            o.step()
+        if orcs:
+            _compare(a, orcs, p)
+            _compare(b, orcs, p)
+        else:
+            for x, y in zip(_batch_state(a, 1), _batch_state(b, 1)):
+                assert rel(y, x) < 1e-5
+
+
 def _staged_and_direct(sa, p, prec):
     a = sa.Simulation(p, precision=prec, grid_side_rows=1)
     b = sa.Simulation(p, precision=prec, grid_side_rows=1)
