@@ -28,7 +28,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "sim steps/sec at primal residual ≤1e-6, chosen form vs plain FP64, 1 GB300"
-FP64_NOMINAL_TFLOPS = 1.25     # GB300 FP64 (non-tensor) rate quoted for this pool
+FP64_NOMINAL_TFLOPS = 1.25     # GB300 nominal FP64 (non-tensor) rate
 FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # 152 SMs x 128 FP32 lanes x FMA x clock
 L2_FLUSH_BYTES = 512 << 20     # > 129 MB L2
 
