@@ -1,25 +1,37 @@
-"""Benchmark: simulation steps per second of the 64-legged-robot batch, every step iterated
-to primal residual <= 1e-6, on GB300 through libsubadmm (the C ABI in include/subadmm.h).
+"""Benchmark: simulation steps per second, every step iterated to primal residual <= 1e-6,
+on GB300 through libsubadmm (the C ABI in include/subadmm.h).
 
-One benchmark step = one time step of the whole batch: assembly, beta, factorisation, the
-ADMM loop to the stop rule, v-hat and the state update, all in the step kernel.
+One benchmark step = one time step of every scene of the workload: assembly, beta,
+factorisation, the ADMM loop to the stop rule, v-hat and the state update, all in the
+library's kernels.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload batched|robots|fem_beam|chain] [--no-sub]
 
-Prints one JSON line (rank 0).  Under torchrun every rank simulates its own seeded batch
-(scenes are independent: weak scaling, no data-path collective).  --impl reference times
-the FP64 CPU oracle on the host cores instead.
+The headline line is the batched workload (4,096 uneven scenes in one launch per launch
+class): the chosen form (mixed precision, batched, graph replay, autotuned variants) and
+the plain FP64 form on the same scenes.  Every workload first runs an untimed pre-roll so
+that the timed steps lie in its contact phase (the scenes start above the plane).  With a
+single GPU the line also carries keyed sub-results for the other workloads: the 64 legged
+robots after landing (with the learned warm start), the FEM beam, and the 8-link chain at a
+fixed 100 iterations per step.
+
+Under torchrun every rank simulates its own seeded batch (scenes are independent: weak
+scaling, no data-path collective).  --impl reference times the FP64 CPU oracle on the host
+cores on the same workload and segment instead.
 """
 from __future__ import annotations
 
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
 import threading
 import time
+from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
 
@@ -32,8 +44,18 @@ FP64_NOMINAL_TFLOPS = 1.25     # GB300 nominal FP64 (non-tensor) rate
 FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # 152 SMs x 128 FP32 lanes x FMA x clock
 L2_FLUSH_BYTES = 512 << 20     # > 129 MB L2
 
+# per workload: time step, untimed pre-roll (steps before warm-up, so that the timed segment
+# lies in the contact phase), scene-sample size of the CPU oracle
+WORKLOADS = {
+    "batched": {"h": 1e-3, "preroll": 100, "cpu_scenes": 32},
+    "robots": {"h": 2e-3, "preroll": 150, "cpu_scenes": 64},
+    "fem_beam": {"h": 1e-3, "preroll": 0, "cpu_scenes": 1},
+    "chain": {"h": 1e-3, "preroll": 0, "cpu_scenes": 1},
+}
 
-def workload_desc(n_robots: int, h: float, workload: str = "robots", scenes: int = 0) -> str:
+
+def workload_desc(workload: str, n_robots: int = 64, scenes: int = 4096) -> str:
+    h = WORKLOADS[workload]["h"]
     if workload == "fem_beam":
         return (f"one linear-elastic tetrahedral beam 0.5 x 0.05 x 0.05 m (10 x 10 nodes x 137 "
                 f"planes, Kuhn split, E=1e5 Pa, nu=0.45, rho=1000) cut into 64 slabs of 900/1200 "
@@ -42,22 +64,45 @@ def workload_desc(n_robots: int, h: float, workload: str = "robots", scenes: int
                 f"ball joints; h={h:g} s; each step iterated to r_p<=1e-6 with the previous "
                 f"step's warm start")
     if workload == "batched":
-        return (f"{scenes} independent uneven scenes of 2-32 subsystems each: rigid chains of "
-                f"1-8 bodies and linear spring-lattice blocks of 6-240 DOF, tree + chord ball "
-                f"joints, node plane contacts mu=0.5; h={h:g} s; each step iterated to "
-                f"r_p<=1e-6 with the previous step's warm start")
+        return (f"{scenes} independent uneven scenes of 2-32 subsystems each: floating rigid "
+                f"chains of 1-40 bodies and 2x2xk spring-lattice blocks (a stand-in for small "
+                f"FEM blocks) of 12-240 DOF, random tree + chord ball joints, 0-64 point "
+                f"contacts per scene with the plane z=0, mu uniform in [0.3, 1.0]; h={h:g} s; "
+                f"each step iterated to r_p<=1e-6 with the previous step's warm start")
+    if workload == "chain":
+        return ("serial chain of 8 rigid links (box 0.1x0.02x0.02 m, density 1000), ball "
+                "joints, first link pinned, gravity; 4 subsystems of 2 links; h=1e-3 s, "
+                "rho=1e3 fixed, exactly 100 ADMM iterations per step")
     return (f"{n_robots} independent legged robots (6-DOF trunk + 4 legs x 3 revolute joints, "
             f"one subsystem per leg and one for the trunk, PD drives as soft rows, 4 point-foot "
             f"plane contacts mu=0.8), dropped from 0.3-0.5 m; h={h:g} s; each step iterated to "
             f"r_p<=1e-6 with the previous step's warm start")
 
 
+def make_problem(workload: str, rank: int = 0, n_robots: int = 64, scenes: int = 4096):
+    """The scenes a rank simulates: an independent seeded batch per rank (weak scaling; the
+    scenes never exchange data, so the ranks share no data-path collective)."""
+    import scenegen as sg
+    h = WORKLOADS[workload]["h"]
+    if workload == "batched":
+        return sg.batched(seed=rank, n_scenes=scenes, h=h, tol_primal=1e-6, max_iters=1000)
+    if workload == "fem_beam":
+        return sg.fem_beam(seed=rank, h=h, tol_primal=1e-6, max_iters=1000)
+    if workload == "chain":
+        return sg.chain(rank, max_iters=100, tol_primal=-1, rho=1e3)
+    return sg.robots(seed=rank, n_robots=n_robots, h=h, tol_primal=1e-6, max_iters=1000)
+
+
+def whole_job_rate(world: int, steps: int, t_ms_max: float) -> float:
+    """Steps of every rank's batch per second over the slowest rank's time."""
+    return world * steps / (t_ms_max / 1e3)
+
+
 def algorithmic_work(problem):
     """Per-scene algorithmic FLOPs of the method (triangular-solve form of Eq. admm-1i):
     per iteration and subsystem 2 n^2 (two triangular solves) + 4 nnz(J_i) (J^T w and J v)
     + 20 m_i (projection, updates, residuals); per step and subsystem n^3/3 (Cholesky)
-    + 2 sum_rows nnz(row)^2 (K = A + beta J^T J)."""
-    import numpy as np
+    + 2 sum_rows nnz(row)^2 (K = A + beta J^T J).  Also sum_i m_i^2 (entries of D)."""
     out = []
     for sc in problem.scenes:
         n = [s.n for s in sc.subs]
@@ -196,6 +241,15 @@ def recorded_traffic_fem(iters_per_launch: float):
     return float(vals["traffic_bytes_per_iteration"]) * iters_per_launch
 
 
+def recorded_traffic_batched(steps_per_launch: int, scenes: int):
+    """DRAM bytes per launch of the batched workload's step kernels from the committed ncu
+    summary (a smaller batch of the same generator), scaled per scene and per step, or None."""
+    vals = _recorded("step_kernel_batched_traffic.md")
+    if not vals:
+        return None
+    return (float(vals["traffic_bytes_per_scene_step"]) * scenes * steps_per_launch)
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -204,118 +258,310 @@ def measured_peaks():
         return {}
 
 
-def cpu_baseline(problem, seconds: float, sample_scenes: int = 64):
-    """Time the FP64 CPU oracle, as it stands, on a bounded sample of the same workload: the
-    first steps of the first ``sample_scenes`` scenes of the batch (all of them when the batch
-    is no larger; the scenes are drawn independently, so a prefix is a random sample), until
-    ``seconds`` have elapsed.  The rate is scaled to whole-batch steps per second."""
+def host_cpu() -> dict:
+    """Host CPU model and core count (the oracle baselines' machine)."""
+    model = platform.processor() or platform.machine()
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k = line.split(":", 1)
+                if len(k) == 2 and k[0].strip() in ("model name", "Model name", "CPU part"):
+                    model = k[1].strip()
+                    if k[0].strip() != "CPU part":
+                        break
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"model": model, "arch": platform.machine(), "nproc": os.cpu_count() or 1}
+
+
+# ---------------------------------------------------------------------------------------------
+# CPU oracle (test infrastructure; timed here as the reported baseline only)
+
+def oracle_rate(workload: str, problem, preroll: int, warmup: int, steps: int,
+                threads: int, seconds: float, n_scenes: int):
+    """Time the FP64 CPU oracle, as it stands, on a bounded sample of the workload: the first
+    ``n_scenes`` scenes (scenes are drawn independently, so a prefix is a random sample), run
+    through the same pre-roll and warm-up as the GPU (untimed), then up to ``steps`` timed
+    steps or ``seconds``.  Scenes run on ``threads`` host threads (ctypes releases the GIL);
+    a single scene runs on the OpenMP build (subsystems and constraints over the threads).
+    The rate is scaled to whole-workload steps per second."""
     import oracle
     n_all = len(problem.scenes)
-    scs = [oracle.OracleScene(sc, problem.options) for sc in problem.scenes[:sample_scenes]]
+    n = min(n_scenes, n_all)
+    omp = n == 1 and threads > 1
+    if omp:
+        os.environ["OMP_NUM_THREADS"] = str(threads)
+    scs = [oracle.OracleScene(sc, problem.options, openmp=omp) for sc in problem.scenes[:n]]
+    pool = ThreadPoolExecutor(max_workers=threads) if (threads > 1 and n > 1) else None
+
+    def step_all():
+        if pool is None:
+            for o in scs:
+                o.step()
+        else:
+            list(pool.map(lambda o: o.step(), scs))
+    for _ in range(preroll + warmup):
+        step_all()
     t0 = time.perf_counter()
-    steps = 0
-    iters = 0
-    while True:
-        for o in scs:
-            o.step()
-            iters += o.residuals()["iters"]
-        steps += 1
-        if time.perf_counter() - t0 >= seconds or steps >= 500:
+    k, iters = 0, 0
+    while k < steps:
+        step_all()
+        k += 1
+        iters += sum(o.residuals()["iters"] for o in scs)
+        if time.perf_counter() - t0 >= seconds:
             break
     dt = time.perf_counter() - t0
-    frac = len(scs) / n_all
-    which = (f"all {n_all} scenes" if len(scs) == n_all else
-             f"the first {len(scs)} of {n_all} scenes, rate scaled by {len(scs)}/{n_all}")
-    return {"value": steps / dt * frac, "unit": "steps/s", "cores": 1, "kind": "oracle",
-            "sample": f"first {steps} steps of {which} (whole sample per step), "
-                      f"single-threaded plain C -O2, {iters / max(steps * len(scs), 1):.1f} "
-                      f"iterations per scene-step",
-            "seconds": dt}
+    if pool is not None:
+        pool.shutdown()
+    which = (f"all {n_all} scenes" if n == n_all else
+             f"the first {n} of {n_all} scenes, rate scaled by {n}/{n_all}")
+    how = (f"OpenMP build on {threads} threads (subsystems and constraints)" if omp else
+           f"{threads} host threads over scenes" if pool is not None else "single thread")
+    return {"value": k / dt * n / n_all, "unit": "steps/s", "cores": threads if (omp or pool) else 1,
+            "kind": "oracle",
+            "sample": f"steps {preroll + warmup}..{preroll + warmup + k} of {which} (whole sample "
+                      f"per step, after an untimed pre-roll and warm-up like the GPU's); plain C "
+                      f"-O2 FP64, {how}; {iters / max(k * n, 1):.1f} iterations per scene-step",
+            "seconds": round(dt, 2), "cpu": host_cpu()}
 
 
-def cpu_baseline_one_scene(args, h: float, mean_iters: float):
-    """The FP64 CPU oracle, as it stands, on one large scene: one step takes minutes, so the
-    first step is timed at 1 and at 4 ADMM iterations; their difference gives the time per
-    iteration, the rest the per-step assembly and factorisation; the rate is extrapolated
-    to the GPU run's mean iterations per step."""
+def oracle_fem_rate(threads: int):
+    """The FP64 CPU oracle on the FEM beam: one step takes minutes single-threaded, so the
+    first step is timed at 1 and at 4 ADMM iterations on the OpenMP build; their difference
+    gives the time per iteration, the rest the per-step assembly and factorisation."""
     import oracle
     import scenegen as sg
+    os.environ["OMP_NUM_THREADS"] = str(threads)
     times = {}
     for k in (1, 4):
-        p = sg.fem_beam(seed=0, h=h, tol_primal=-1, max_iters=k)
-        o = oracle.OracleScene(p.scenes[0], p.options)
+        p = sg.fem_beam(seed=0, h=1e-3, tol_primal=-1, max_iters=k)
+        o = oracle.OracleScene(p.scenes[0], p.options, openmp=True)
         t0 = time.perf_counter()
         o.step()
         times[k] = time.perf_counter() - t0
     per_iter = (times[4] - times[1]) / 3.0
-    setup = times[1] - per_iter
-    step_s = setup + per_iter * mean_iters
-    return {"value": 1.0 / step_s, "unit": "steps/s", "cores": 1, "kind": "oracle",
-            "sample": f"first step at 1 and 4 iterations ({times[1]:.1f} s, {times[4]:.1f} s): "
-                      f"{setup:.1f} s assembly and factorisation + {per_iter * 1e3:.0f} ms per "
-                      f"iteration, extrapolated to {mean_iters:.0f} iterations per step; "
-                      f"single-threaded plain C -O2",
-            "seconds": times[1] + times[4]}
+    return {"setup_s": times[1] - per_iter, "per_iter_s": per_iter, "times": times}
 
 
 def run_reference(args, rank: int, world: int):
-    """The reference arm: the FP64 CPU oracle, as it stands, on the same workload (rank 0
-    only); for a batch larger than ``--reference-scenes`` a prefix of that many scenes is
-    stepped and the rate scaled to whole-batch steps."""
+    """The reference arm: the FP64 CPU oracle, as it stands, on the same workload, segment,
+    metric and unit as this arm's line (rank 0 only)."""
     if rank != 0:
         return 0
-    import oracle
-    h = 2e-3 if args.workload == "robots" else 1e-3
+    wl = WORKLOADS[args.workload]
+    threads = os.cpu_count() or 1
     if args.workload == "fem_beam":
-        cb = cpu_baseline_one_scene(args, h, 500.0)
-        line = {"metric": METRIC, "value": cb["value"], "unit": "steps/s", "n_gpus": world,
-                "steps": 1, "warmup": 0, "ms_per_step": 1e3 / cb["value"],
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                "data": "synthetic", "impl": "reference",
-                "config": {"workload": workload_desc(args.robots, h, args.workload),
-                           "form": "FP64 CPU oracle"},
-                "cpu_baseline": cb,
-                "e2e": {"value": cb["value"], "unit": "steps/s", "h2d_bytes_per_step": 0,
-                        "d2h_bytes_per_step": 0}}
-        print(json.dumps(line), flush=True)
-        return 0
-    p = batch_for_rank(0, args.robots, h, args.workload, args.scenes)
-    n_all = len(p.scenes)
-    scs = [oracle.OracleScene(sc, p.options) for sc in p.scenes[:args.reference_scenes]]
-    # warm-up steps, then time K steps bounded to a few minutes
-    for _ in range(args.warmup):
-        for o in scs:
-            o.step()
-    t0 = time.perf_counter()
-    k = 0
-    for k in range(1, args.steps + 1):
-        for o in scs:
-            o.step()
-        if time.perf_counter() - t0 > args.reference_seconds:
-            break
-    dt = time.perf_counter() - t0
-    frac = len(scs) / n_all
-    val = k / dt * frac
-    which = (f"all {n_all} scenes" if len(scs) == n_all else
-             f"the first {len(scs)} of {n_all} scenes, rate scaled by {len(scs)}/{n_all}")
-    line = {"metric": METRIC, "value": val, "unit": "steps/s", "n_gpus": world, "steps": k,
+        r = oracle_fem_rate(threads)
+        mean_iters = 600.0
+        val = 1.0 / (r["setup_s"] + r["per_iter_s"] * mean_iters)
+        cb = {"value": val, "unit": "steps/s", "cores": threads, "kind": "oracle",
+              "sample": f"first step at 1 and 4 iterations: {r['setup_s']:.1f} s assembly and "
+                        f"factorisation + {r['per_iter_s'] * 1e3:.0f} ms per iteration, "
+                        f"extrapolated to {mean_iters:.0f} iterations per step; OpenMP build on "
+                        f"{threads} threads", "cpu": host_cpu()}
+        steps = 1
+    else:
+        p = make_problem(args.workload, 0, args.robots, args.scenes)
+        cb = oracle_rate(args.workload, p, wl["preroll"] + 1, args.warmup, args.steps, threads,
+                         args.reference_seconds, args.reference_scenes or wl["cpu_scenes"])
+        val = cb["value"]
+        steps = args.steps
+    line = {"metric": METRIC, "value": val, "unit": "steps/s", "n_gpus": world, "steps": steps,
             "warmup": args.warmup, "ms_per_step": 1e3 / val, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": workload_desc(args.robots, h, args.workload, args.scenes),
-                       "robots": args.robots, "form": "FP64 CPU oracle"},
-            "cpu_baseline": {"value": val, "unit": "steps/s", "cores": 1, "kind": "oracle",
-                             "sample": f"steps {args.warmup}..{args.warmup + k} of {which}"},
+            "config": {"workload": workload_desc(args.workload, args.robots, args.scenes),
+                       "form": "FP64 CPU oracle", "preroll_steps": wl["preroll"]},
+            "cpu_baseline": cb,
             "e2e": {"value": val, "unit": "steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
-def learned_comparison(args, p) -> dict:
-    """The learned warm start against the previous-step warm start on this workload: the
-    network is trained on robots of two other seeds after landing (steps 200-400), then
-    both starts run the timed segment (mixed form, one launch per step, graph replay)."""
+# ---------------------------------------------------------------------------------------------
+# GPU timing
+
+class Ctx:
+    def __init__(self, subadmm, stream, dev, local, dist, flush):
+        self.subadmm, self.stream, self.dev, self.local = subadmm, stream, dev, local
+        self.dist, self.flush = dist, flush
+
+
+def time_form(ctx, p, precision, steps: int, warmup: int, preroll: int, spl: int,
+              autotune: bool = True, graph: bool = True, sample_clocks: bool = False,
+              keep_factors: bool = True):
+    """Pre-roll (untimed, so the timed segment lies in the contact phase), autotune the
+    kernel variants on that state (restored afterwards), W warm-up steps, then K timed steps
+    in launches of ``spl`` steps (the scenes are independent, so one launch advances every
+    scene by that many steps without a device-wide wait per step).  The L2 is flushed before
+    every timed launch; CUDA events on the launching stream; max over ranks."""
+    import torch
+    sa = ctx.subadmm
+    sim = sa.Simulation(p, stream=ctx.stream.cuda_stream, device=ctx.local, precision=precision)
+    if not keep_factors:
+        sim.keep_factors(False)
+    sim.step(1)
+    left = preroll
+    while left > 0:
+        n = min(left, 50)
+        sim.step(n)
+        left -= n
+    tuned = sim.autotune(steps=3) if autotune else sim.launch_classes()
+    if graph:
+        sim.use_graph(True)
+    for _ in range(warmup):
+        sim.step(1)
+    sim.sync()
+    sim.iteration_stats()   # clear counters
+    chunks = [spl] * (steps // spl) + ([steps % spl] if steps % spl else [])
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in chunks]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in chunks]
+    if ctx.dist is not None:
+        ctx.dist.barrier()
+    torch.cuda.synchronize(ctx.dev)
+    clk = ClockSampler(ctx.local) if sample_clocks else None
+    if clk:
+        clk.__enter__()
+    for k, n in enumerate(chunks):
+        ctx.flush.zero_()                  # L2 flushed between timed launches
+        ev0[k].record(ctx.stream)
+        sim.step(n)
+        ev1[k].record(ctx.stream)
+    torch.cuda.synchronize(ctx.dev)
+    if clk:
+        clk.__exit__()
+    if ctx.dist is not None:
+        ctx.dist.barrier()
+    launch_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+    t_ms = float(sum(launch_ms))
+    if ctx.dist is not None:
+        tt = torch.tensor([t_ms], device=ctx.dev)
+        ctx.dist.all_reduce(tt, op=ctx.dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    stats = sim.iteration_stats(per_scene=True)
+    return {"sim": sim, "t_ms": t_ms, "launch_ms": launch_ms, "stats": stats, "classes": tuned,
+            "clocks": clk.summary() if clk else None, "chunks": chunks}
+
+
+def iter_summary(stats) -> dict:
+    return {"mean_per_scene_step": stats["total_iters"] / max(stats["scene_steps"], 1),
+            "max": stats["max_iters"], "not_converged": stats["not_converged"],
+            "not_converged_frac": stats["not_converged"] / max(stats["scene_steps"], 1),
+            "scene_steps": stats["scene_steps"]}
+
+
+def alu_roofline(p, work, stats, t_ms, mixed: bool, steps: int, traffic=None):
+    it_flops = np.array([w[0] for w in work])
+    st_flops = float(sum(w[1] for w in work))
+    flops = float(it_flops @ stats["per_scene"][:, 0]) + st_flops * steps
+    achieved = flops / (t_ms / 1e3) / 1e12
+    peak, pipe = (FP32_NOMINAL_TFLOPS, "FP32") if mixed else (FP64_NOMINAL_TFLOPS, "FP64")
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": traffic,
+            "note": f"{pipe} non-tensor pipe; peak nominal, derived from unit counts and clock "
+                    f"({'152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz' if mixed else 'GB300 FP64 rate'});"
+                    f" algorithmic flops of the triangular-solve form, {it_flops.mean():.0f} per "
+                    f"scene-iteration (mean over scenes) and {st_flops / len(p.scenes):.0f} per "
+                    f"scene-step, times the iterations each scene ran"}
+
+
+def e2e_rate(ctx, sim, steps: int, world: int):
+    """End to end through the C ABI with host buffers: the state in from pinned host memory,
+    one step, the state out to pinned host memory, every step (host wall clock)."""
+    import torch
+    sa = ctx.subadmm
+    sizes = sim.sizes()
+    nstate = 13 * sizes["bodies"] + 6 * sizes["nodes"]
+    hbuf = torch.empty(nstate, dtype=torch.float64).pin_memory()
+    sa.sim_read_state(sim.h, hbuf.data_ptr())
+    torch.cuda.synchronize(ctx.dev)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        sa.sim_write_state(sim.h, hbuf.data_ptr())
+        sim.step(1)
+        sa.sim_read_state(sim.h, hbuf.data_ptr())
+    dt = time.perf_counter() - t0
+    if ctx.dist is not None:
+        tt = torch.tensor([dt], device=ctx.dev)
+        ctx.dist.all_reduce(tt, op=ctx.dist.ReduceOp.MAX)
+        dt = float(tt.item())
+    return {"value": world * steps / dt, "unit": "steps/s", "h2d_bytes_per_step": 8 * nstate,
+            "d2h_bytes_per_step": 8 * nstate, "steps": steps, "timer": "host wall clock"}
+
+
+def barrier_floor(ctx) -> dict:
+    """Cycles of one __syncthreads_count round of a 256-thread block (one block per SM):
+    the floor under one iteration of the block kernel, which has one such barrier."""
+    return ctx.subadmm.sim_barrier_floor(ctx.local, 20000)
+
+
+# ---------------------------------------------------------------------------------------------
+# sub-results (single GPU only)
+
+def sub_robots(ctx, args, threads: int) -> dict:
+    """64 legged robots, timed after landing (pre-roll 150 steps: the feet touch down near
+    step 120); mixed and plain FP64; the learned warm start against the previous-step start
+    on the same segment; microseconds per iteration against the barrier floor."""
+    import torch
+    sa = ctx.subadmm
+    wl = WORKLOADS["robots"]
+    p = make_problem("robots", 0, args.robots)
+    K = max(args.steps, 100)
+    work = algorithmic_work(p)
+    r = time_form(ctx, p, sa.SIM_MIXED, K, args.warmup, wl["preroll"], 50)
+    f = time_form(ctx, p, sa.SIM_FP64, K, args.warmup, wl["preroll"], 50)
+    out = {"workload": workload_desc("robots", args.robots),
+           "timed_segment": f"steps {wl['preroll'] + 1 + args.warmup}..{wl['preroll'] + 1 + args.warmup + K} "
+                            f"(after landing)",
+           "value": K / (r["t_ms"] / 1e3), "unit": "steps/s", "form": "mixed",
+           "iterations": iter_summary(r["stats"]),
+           "plain_fp64": {"value": K / (f["t_ms"] / 1e3), "unit": "steps/s",
+                          "iterations": iter_summary(f["stats"])},
+           "roofline": alu_roofline(p, work, r["stats"], r["t_ms"], True, K,
+                                    recorded_traffic(50) if K % 50 == 0 else None),
+           "launch_classes": r["classes"]}
+    out["chosen_over_plain"] = out["value"] / out["plain_fp64"]["value"]
+    # cycles per iteration (phase tracer, a separate short run) against the barrier floor
+    sim = r["sim"]
+    sim.use_graph(False)
+    sa.sim_phase_trace(sim.h, True)
+    sim.step(20)
+    sim.sync()
+    ph = sa.sim_phase_trace(sim.h, False)
+    fl = barrier_floor(ctx)
+    per_it = (ph["v_step"] + ph["z_step"]) / max(ph["iterations"], 1)
+    out["cycles_per_iteration"] = {"iteration": per_it, "barrier_floor": fl["cycles"],
+                                   "ratio": per_it / max(fl["cycles"], 1e-9),
+                                   "setup_and_recovery_per_scene_step":
+                                       (ph["assemble"] + ph["factor"] + ph["recover"] + ph["exit"])
+                                       / max(ph["scene_steps"], 1),
+                                   "note": "SM cycles seen by each scene's first thread (phase "
+                                           "tracer, 20 steps after the timed segment); floor = "
+                                           "one __syncthreads_count round of a 256-thread block"}
+    sim.close()
+    f["sim"].close()
+    if not args.no_learned:
+        try:
+            out["learned_warm_start"] = learned_comparison(args, p, K)
+        except Exception as e:                       # reported, not fatal to the line
+            out["learned_warm_start"] = {"error": repr(e)}
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = oracle_rate("robots", p, wl["preroll"] + 1, args.warmup, K,
+                                          threads, 8.0, 64)
+    return out
+
+
+def learned_comparison(args, p, steps: int) -> dict:
+    """The learned warm start against the previous-step warm start on the robots after
+    landing: the network is trained on robots of two other seeds after landing (steps
+    200-400), then both starts run the same segment (mixed form, one launch per step by
+    graph replay)."""
     import scenegen as sg
     import torch
     from paper_2302_14344_gb300 import learned as lr
@@ -327,142 +573,115 @@ def learned_comparison(args, p) -> dict:
     net = lr.init_network(seed=1)
     losses = lr.train(net, X, T, M, epochs=8)
     train_s = time.perf_counter() - t0
-    res = lr.compare(p, net, steps=args.steps, warmup=args.warmup)
+    res = lr.compare(p, net, steps=steps, warmup=WORKLOADS["robots"]["preroll"] + args.warmup)
     pl, le = res["plain"], res["learned"]
     return {"value": 1e3 / le["ms_per_step"], "unit": "steps/s",
             "previous_step_start": 1e3 / pl["ms_per_step"],
             "learned_over_previous": pl["ms_per_step"] / le["ms_per_step"],
             "iterations_per_scene_step": {"learned": le["iters_per_scene_step"],
                                           "previous_step": pl["iters_per_scene_step"]},
-            "fallbacks": le["fallbacks"], "scene_steps": args.steps * len(p.scenes),
+            "not_converged": {"learned": le["not_converged"], "previous_step": pl["not_converged"]},
+            "fallbacks": le["fallbacks"], "scene_steps": steps * len(p.scenes),
             "training": {"samples": int(X.shape[0]), "epochs": 8,
                          "loss_first_last": [losses[0], losses[-1]],
                          "seconds": round(train_s, 1)},
-            "note": "both starts stepped one launch per step (graph replay), timed segment "
-                    "of this run; the network adds features + a 32-256-256-256-7 BF16 MLP "
-                    "per step"}
+            "note": "both starts stepped one launch per step (graph replay) over the same "
+                    "post-landing segment; the network adds features + a 32-256-256-256-7 BF16 "
+                    "MLP per step"}
 
 
-def batch_for_rank(rank: int, n_robots: int, h: float, workload: str = "robots",
-                   scenes: int = 4096):
-    """The scenes a rank simulates: an independent seeded batch per rank (weak scaling; the
-    scenes never exchange data, so the ranks share no data-path collective)."""
-    import scenegen as sg
-    if workload == "batched":
-        return sg.batched(seed=rank, n_scenes=scenes, h=h, tol_primal=1e-6, max_iters=1000)
-    if workload == "fem_beam":
-        return sg.fem_beam(seed=rank, h=h, tol_primal=1e-6, max_iters=1000)
-    return sg.robots(seed=rank, n_robots=n_robots, h=h, tol_primal=1e-6, max_iters=1000)
-
-
-def whole_job_rate(world: int, steps: int, t_ms_max: float) -> float:
-    """Steps of every rank's batch per second over the slowest rank's time."""
-    return world * steps / (t_ms_max / 1e3)
-
-
-def time_refactor_every_step(subadmm, p, stream, dev, local, flush, steps: int = 3):
-    """The plain FP64 form with every block factorised again every step (Algorithm 1 as
-    stated; by default a constant block's factor, the same matrix, is computed once):
-    `steps` steps after one warm-up step, one launch each, L2 flushed before each."""
-    import torch
-    sim = subadmm.Simulation(p, stream=stream.cuda_stream, device=local,
-                             precision=subadmm.SIM_FP64)
-    sim.keep_factors(False)
-    sim.step(1)
-    sim.sync()
-    sim.iteration_stats()   # clear counters
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(steps)]
-    torch.cuda.synchronize(dev)
-    for a, b in ev:
-        flush.zero_()
-        a.record(stream)
-        sim.step(1)
-        b.record(stream)
-    torch.cuda.synchronize(dev)
-    t = float(sum(a.elapsed_time(b) for a, b in ev))
-    st = sim.iteration_stats()
-    sim.close()
-    return {"value": steps / (t / 1e3), "unit": "steps/s", "ms_per_step": t / steps,
-            "steps": steps, "mean_iterations": st["total_iters"] / max(st["scene_steps"], 1),
-            "note": "every block refactorised every step (sim_keep_factors(0)); timed segment "
-                    "right after the first step, heuristic kernel variant, no graph"}
-
-
-def time_form(subadmm, p, precision, args, stream, dev, local, dist, flush, sample_clocks):
-    """Warm-up W steps, then K timed steps in launches of ``--steps-per-launch`` steps (the
-    scenes are independent, so one launch advances every scene by that many steps without a
-    device-wide wait per step).  The L2 is flushed before every timed launch."""
-    import torch
-    sim = subadmm.Simulation(p, stream=stream.cuda_stream, device=local, precision=precision)
-    sim.step(1)
-    tuned = sim.launch_classes() if args.no_autotune else sim.autotune(steps=3)
-    if not args.no_graph:
-        sim.use_graph(True)
-    for _ in range(args.warmup - 1):
-        sim.step(1)
-    sim.sync()
-    sim.iteration_stats()   # clear counters
+def sub_fem_beam(ctx, args, threads: int) -> dict:
+    """The FEM beam (one scene over the whole GPU): mixed, plain FP64, and plain FP64 with
+    every block refactorised every step (Algorithm 1 literally)."""
+    sa = ctx.subadmm
+    p = make_problem("fem_beam")
+    work = algorithmic_work(p)
     K = args.steps
-    spl = max(1, min(args.steps_per_launch, K))
-    chunks = [spl] * (K // spl) + ([K % spl] if K % spl else [])
-    ev0 = [torch.cuda.Event(enable_timing=True) for _ in chunks]
-    ev1 = [torch.cuda.Event(enable_timing=True) for _ in chunks]
-    if dist is not None:
-        dist.barrier()
-    torch.cuda.synchronize(dev)
-    clk = ClockSampler(local) if sample_clocks else None
-    if clk:
-        clk.__enter__()
-    for k, n in enumerate(chunks):
-        flush.zero_()                      # L2 flushed between timed launches
-        ev0[k].record(stream)
-        sim.step(n)
-        ev1[k].record(stream)
-    torch.cuda.synchronize(dev)
-    if clk:
-        clk.__exit__()
-    if dist is not None:
-        dist.barrier()
-    launch_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
-    t_ms = float(sum(launch_ms))
-    if dist is not None:
-        tt = torch.tensor([t_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
-    stats = sim.iteration_stats(per_scene=True)
-    stats["classes"] = tuned
-    return sim, t_ms, launch_ms, stats, (clk.summary() if clk else None)
+    r = time_form(ctx, p, sa.SIM_MIXED, K, args.warmup, 0, 50, autotune=True, graph=False)
+    f = time_form(ctx, p, sa.SIM_FP64, K, args.warmup, 0, 50, autotune=False, graph=False)
+    rf = time_form(ctx, p, sa.SIM_FP64, min(K, 5), 1, 0, 1, autotune=False, graph=False,
+                   keep_factors=False)
+    d_bytes = float(sum(w[2] for w in work)) * 4
+    hbm = measured_peaks().get("hbm_gbs")
+    st = r["stats"]
+    gbs = d_bytes * st["total_iters"] / (r["t_ms"] / 1e3) / 1e9
+    launches = len(r["chunks"])
+    out = {"workload": workload_desc("fem_beam"), "value": K / (r["t_ms"] / 1e3),
+           "unit": "steps/s", "form": "mixed", "iterations": iter_summary(st),
+           "timed_segment": f"steps {1 + args.warmup}..{1 + args.warmup + K}",
+           "plain_fp64": {"value": K / (f["t_ms"] / 1e3), "unit": "steps/s",
+                          "iterations": iter_summary(f["stats"])},
+           "plain_fp64_refactor_every_step": {
+               "value": len(rf["launch_ms"]) / (rf["t_ms"] / 1e3), "unit": "steps/s",
+               "steps": len(rf["launch_ms"]), "iterations": iter_summary(rf["stats"]),
+               "note": "every block refactorised every step (sim_keep_factors(0)), one launch "
+                       "per step, L2 flushed before each"},
+           "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm or 6800.0, "unit": "GB/s",
+                        "frac": gbs / (hbm or 6800.0),
+                        "traffic": recorded_traffic_fem(st["total_iters"] / launches),
+                        "note": f"algorithmic bytes: D of every subsystem once per iteration "
+                                f"({d_bytes / 1e6:.1f} MB, FP32) x iterations / whole-step time "
+                                f"(setup and exit included: a lower bound on the stream rate); "
+                                f"peak = {'measured copy bandwidth' if hbm else 'fallback'}"}}
+    out["chosen_over_plain"] = out["value"] / out["plain_fp64"]["value"]
+    for x in (r, f, rf):
+        x["sim"].close()
+    if not args.no_cpu_baseline:
+        fr = oracle_fem_rate(threads)
+        mi = out["iterations"]["mean_per_scene_step"]
+        out["cpu_baseline"] = {
+            "value": 1.0 / (fr["setup_s"] + fr["per_iter_s"] * mi), "unit": "steps/s",
+            "cores": threads, "kind": "oracle",
+            "sample": f"first step at 1 and 4 iterations on the OpenMP build ({threads} threads): "
+                      f"{fr['setup_s']:.1f} s assembly and factorisation + "
+                      f"{fr['per_iter_s'] * 1e3:.0f} ms per iteration, extrapolated to "
+                      f"{mi:.0f} iterations per step", "cpu": host_cpu()}
+    return out
+
+
+def sub_chain(ctx, args) -> dict:
+    """The 8-link chain at exactly 100 iterations per step with rho = 1e3 (FP64 and mixed)."""
+    sa = ctx.subadmm
+    p = make_problem("chain")
+    K = max(args.steps, 200)
+    f = time_form(ctx, p, sa.SIM_FP64, K, args.warmup, 0, 50, autotune=False)
+    r = time_form(ctx, p, sa.SIM_MIXED, K, args.warmup, 0, 50, autotune=False)
+    out = {"workload": workload_desc("chain"), "value": K / (f["t_ms"] / 1e3),
+           "unit": "steps/s", "form": "plain FP64", "iterations": iter_summary(f["stats"]),
+           "mixed": {"value": K / (r["t_ms"] / 1e3), "unit": "steps/s"},
+           "us_per_iteration_fp64": f["t_ms"] * 1e3 / (K * 100)}
+    f["sim"].close()
+    r["sim"].close()
+    return out
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--robots", type=int, default=64)
-    ap.add_argument("--workload", default="robots", choices=["robots", "batched", "fem_beam"],
-                    help="robots: 64 legged robots (the headline workload); batched: many "
-                         "uneven scenes of rigid chains and spring blocks in one launch; "
-                         "fem_beam: one tetrahedral FEM beam of 64 slabs held by a 7-R arm")
+    ap.add_argument("--workload", default="batched", choices=list(WORKLOADS),
+                    help="batched: 4096 uneven scenes in one launch per class (the headline); "
+                         "robots: 64 legged robots; fem_beam: one tetrahedral FEM beam of 64 "
+                         "slabs held by a 7-R arm; chain: the 8-link chain at 100 iterations")
     ap.add_argument("--scenes", type=int, default=4096, help="scenes of the batched workload")
-    ap.add_argument("--reference-scenes", type=int, default=64,
-                    help="scenes the reference arm steps (a prefix of the batch)")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--preroll", type=int, default=-1,
+                    help="untimed steps before warm-up (default: per workload)")
+    ap.add_argument("--reference-scenes", type=int, default=0,
+                    help="scenes the CPU oracle steps (a prefix of the batch; 0: per workload)")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--reference-seconds", type=float, default=120.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--form", default="mixed", choices=["mixed", "fp64"],
-                    help="mixed: FP32 iterations with FP64 setup and residual check (the "
-                         "chosen form); fp64: the plain FP64 form")
     ap.add_argument("--steps-per-launch", type=int, default=50)
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the heuristic kernel variants instead of timing them first")
     ap.add_argument("--no-graph", action="store_true", help="launch directly, not by graph replay")
-    ap.add_argument("--no-learned", action="store_true",
-                    help="skip the learned warm start comparison (robots workload)")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned warm start")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip timing the plain FP64 form next to the chosen one")
+    ap.add_argument("--no-sub", action="store_true", help="headline workload only")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -474,7 +693,6 @@ def main():
         return run_reference(args, rank, world)
 
     import torch
-    import scenegen as sg
     from paper_2302_14344_gb300 import subadmm
 
     torch.cuda.set_device(local)
@@ -484,94 +702,68 @@ def main():
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    h = 2e-3 if args.workload == "robots" else 1e-3
-    p = batch_for_rank(rank, args.robots, h, args.workload, args.scenes)
-    work = algorithmic_work(p)
-    it_flops = np.array([w[0] for w in work])
-    st_flops = float(sum(w[1] for w in work))
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    forms = {"mixed": subadmm.SIM_MIXED, "fp64": subadmm.SIM_FP64}
+    ctx = Ctx(subadmm, stream, dev, local, dist, flush)
+    wl = WORKLOADS[args.workload]
+    preroll = wl["preroll"] if args.preroll < 0 else args.preroll
+    threads = os.cpu_count() or 1
 
-    sim, t_ms, launch_ms, stats, clocks = time_form(subadmm, p, forms[args.form], args, stream,
-                                                  dev, local, dist, flush, True)
+    p = make_problem(args.workload, rank, args.robots, args.scenes)
+    work = algorithmic_work(p)
     K = args.steps
+    spl = max(1, min(args.steps_per_launch, K))
+    mixed_form = args.workload != "chain"
+    prec = subadmm.SIM_MIXED if mixed_form else subadmm.SIM_FP64
+    grid_scene = args.workload == "fem_beam"
+    r = time_form(ctx, p, prec, K, args.warmup, preroll, spl, autotune=not args.no_autotune,
+                  graph=not (args.no_graph or grid_scene), sample_clocks=True)
+    sim, t_ms, stats = r["sim"], r["t_ms"], r["stats"]
     sizes = sim.sizes()
     value = whole_job_rate(world, K, t_ms)
-    total_iters = stats["total_iters"]
-    flops = float(it_flops @ stats["per_scene"][:, 0]) + st_flops * K
-    achieved = flops / (t_ms / 1e3) / 1e12
-    if args.form == "mixed":
-        peak, pipe = FP32_NOMINAL_TFLOPS, "FP32"
-    else:
-        peak, pipe = FP64_NOMINAL_TFLOPS, "FP64"
-    spl = max(1, min(args.steps_per_launch, K))
     if args.workload == "fem_beam":
-        # one scene over the whole GPU: every iteration streams each subsystem's D (m_i x m_i)
-        # from HBM (125 MB in FP32, more than L2 holds), so the bound is HBM bandwidth
-        tsize = 4 if args.form == "mixed" else 8
+        tsize = 4
         d_bytes = float(sum(w[2] for w in work)) * tsize
         hbm = measured_peaks().get("hbm_gbs")
-        achieved_gbs = d_bytes * total_iters / (t_ms / 1e3) / 1e9
-        launches = (K + spl - 1) // spl
-        roofline = {"bound": "hbm", "achieved": achieved_gbs,
-                    "peak": hbm if hbm else 6800.0, "unit": "GB/s",
-                    "frac": achieved_gbs / (hbm if hbm else 6800.0),
-                    "traffic": (recorded_traffic_fem(total_iters / launches)
-                                if args.form == "mixed" else None),
-                    "note": f"algorithmic bytes: D of every subsystem once per iteration "
-                            f"({d_bytes / 1e6:.1f} MB) x iterations / whole-step time (setup and "
-                            f"exit included, so a lower bound on the stream rate); peak = "
-                            f"{'measured copy bandwidth' if hbm else 'fallback'}"}
+        gbs = d_bytes * stats["total_iters"] / (t_ms / 1e3) / 1e9
+        roofline = {"bound": "hbm", "achieved": gbs, "peak": hbm or 6800.0, "unit": "GB/s",
+                    "frac": gbs / (hbm or 6800.0),
+                    "traffic": recorded_traffic_fem(stats["total_iters"] / len(r["chunks"])),
+                    "note": "D of every subsystem once per iteration x iterations / whole-step "
+                            "time; peak = " + ("measured copy bandwidth" if hbm else "fallback")}
     else:
-        roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak,
-                    # the recorded capture is of the 64-robot batch in the mixed form
-                    "traffic": (recorded_traffic(spl) if args.workload == "robots" and
-                                args.robots == 64 and args.form == "mixed" else None),
-                    "note": f"{pipe} non-tensor pipe (iterations; the mixed form's per-step "
-                            f"setup is FP64); peak = 152 SMs x lanes x 2 flops x 2.07 GHz; "
-                            f"algorithmic flops of the triangular-solve form, "
-                            f"{it_flops.mean():.0f} per scene-iteration (mean over scenes) and "
-                            f"{st_flops / len(p.scenes):.0f} per scene-step"}
+        traffic = None
+        if args.workload == "robots" and args.robots == 64:
+            traffic = recorded_traffic(spl)
+        elif args.workload == "batched":
+            traffic = recorded_traffic_batched(spl, len(p.scenes))
+        roofline = alu_roofline(p, work, stats, t_ms, mixed_form, K, traffic)
 
     compare = None
-    if not args.no_compare and args.form != "fp64":
-        sim2, t2, sm2, st2, _ = time_form(subadmm, p, subadmm.SIM_FP64, args, stream, dev, local,
-                                          dist, flush, False)
-        compare = {"value": world * K / (t2 / 1e3), "unit": "steps/s", "ms_per_step": t2 / K,
-                   "mean_iterations": st2["total_iters"] / max(st2["scene_steps"], 1),
-                   "not_converged": st2["not_converged"],
-                   "chosen_over_plain": (world * K / (t_ms / 1e3)) / (world * K / (t2 / 1e3))}
-        sim2.close()
-    refactor = None
-    if args.workload == "fem_beam" and not args.no_compare and world == 1:
-        refactor = time_refactor_every_step(subadmm, p, stream, dev, local, flush)
+    if not args.no_compare and mixed_form:
+        f = time_form(ctx, p, subadmm.SIM_FP64, K, args.warmup, preroll, spl,
+                      autotune=not args.no_autotune, graph=not (args.no_graph or grid_scene))
+        compare = {"value": whole_job_rate(world, K, f["t_ms"]), "unit": "steps/s",
+                   "ms_per_step": f["t_ms"] / K, "iterations": iter_summary(f["stats"])}
+        compare["chosen_over_plain"] = value / compare["value"]
+        f["sim"].close()
 
-    learned_line = None
-    if args.workload == "robots" and not args.no_learned and world == 1:
-        learned_line = learned_comparison(args, p)
+    e2e = e2e_rate(ctx, sim, min(K, 200), world)
+    e2e["segment"] = (f"steps {1 + preroll + args.warmup + K}.."
+                      f"{1 + preroll + args.warmup + K + e2e['steps']} of the run")
+    sim.close()
 
-    # end to end through the C ABI with host buffers: state in from pinned host memory,
-    # one step, state out to pinned host memory, every step
-    nstate = 13 * sizes["bodies"] + 6 * sizes["nodes"]
-    hbuf = torch.empty(nstate, dtype=torch.float64).pin_memory()
-    subadmm.sim_read_state(sim.h, hbuf.data_ptr())
-    e2e_steps = min(K, 200)
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        subadmm.sim_write_state(sim.h, hbuf.data_ptr())
-        sim.step(1)
-        subadmm.sim_read_state(sim.h, hbuf.data_ptr())
-    e2e_dt = time.perf_counter() - t0
-    if dist is not None:
-        tt = torch.tensor([e2e_dt], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_dt = float(tt.item())
-    e2e = {"value": world * e2e_steps / e2e_dt, "unit": "steps/s",
-           "h2d_bytes_per_step": 8 * nstate, "d2h_bytes_per_step": 8 * nstate,
-           "steps": e2e_steps, "timer": "host wall clock",
-           "segment": f"steps {args.warmup + K}..{args.warmup + K + e2e_steps} of the run"}
+    subs = {}
+    if not args.no_sub and world == 1:
+        jobs = {"robots_after_landing": lambda: sub_robots(ctx, args, threads),
+                "fem_beam": lambda: sub_fem_beam(ctx, args, threads),
+                "chain_fixed_100_iterations": lambda: sub_chain(ctx, args)}
+        for name, fn in jobs.items():
+            if name.startswith(args.workload):
+                continue
+            try:
+                subs[name] = fn()
+            except Exception as e:                   # reported, not fatal to the line
+                subs[name] = {"error": repr(e)}
 
     if rank == 0:
         n_if = sum(len(sc.ifs) for sc in p.scenes) / max(len(p.scenes), 1)
@@ -579,49 +771,56 @@ def main():
             "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": t_ms / K, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32" if args.form == "mixed" else "f64", "data": "synthetic",
-            "config": {"workload": workload_desc(args.robots, h, args.workload, args.scenes),
-                       "form": ("mixed: FP64 assembly, factorisation and residual check, "
-                                "FP32 iterations") if args.form == "mixed" else "plain FP64",
-                       "robots": args.robots, "scenes_per_gpu": sizes["scenes"],
+            "dtype": "f32" if mixed_form else "f64", "data": "synthetic",
+            "config": {"workload": workload_desc(args.workload, args.robots, args.scenes),
+                       "form": ("chosen: mixed precision (FP64 assembly, beta and final residual "
+                                "check; FP32 factor for non-stiff blocks, FP64 for stiff ones; "
+                                "FP32 iterations), batched, graph replay, autotuned")
+                               if mixed_form else "plain FP64",
+                       "scenes_per_gpu": sizes["scenes"],
                        "subsystems": sizes["subsystems"], "dof": sizes["dof"],
                        "interfaces": sizes["interfaces"], "rows": sizes["rows"],
                        "side_rows": sizes["side_rows"], "parallelism": f"scenes x{world}",
-                       "l2": "flushed between timed steps (512 MiB write)",
-                       "launch": f"step kernel, {min(args.steps_per_launch, K)} steps per launch, "
-                                 f"one block of 256 threads per scene, one launch per class of "
-                                 f"scenes (classes on forked streams)"
-                                 + ("" if args.no_graph else ", replayed as a CUDA graph"),
-                       "launch_classes": stats["classes"],
+                       "l2": "flushed between timed launches (512 MiB write)",
+                       "launch": f"{spl} steps per launch, one launch per class of scenes "
+                                 f"(classes on forked streams)"
+                                 + ("" if (args.no_graph or grid_scene) else
+                                    ", replayed as a CUDA graph"),
+                       "launch_classes": r["classes"],
                        "kernel_variants": "heuristic" if args.no_autotune else
-                                          "autotuned (sim_autotune, 3 steps per variant)",
-                       "timed_segment": f"steps {args.warmup}..{args.warmup + K} of a run from "
-                                        f"the drop"},
-            "iterations": {"mean_per_scene_step": total_iters / max(stats["scene_steps"], 1),
-                           "max": stats["max_iters"], "not_converged": stats["not_converged"],
-                           "scene_steps": stats["scene_steps"]},
-            "interface_updates_per_s": n_if * total_iters * world / (t_ms / 1e3),
+                                          "autotuned on the pre-rolled state (sim_autotune, "
+                                          "3 steps per variant, state restored)",
+                       "preroll_steps": preroll,
+                       "timed_segment": f"steps {1 + preroll + args.warmup}.."
+                                        f"{1 + preroll + args.warmup + K} of a run from rest "
+                                        f"(1 first step, {preroll} untimed pre-roll, "
+                                        f"{args.warmup} warm-up)"},
+            "iterations": iter_summary(stats),
+            "interface_updates_per_s": n_if * stats["total_iters"] * world / (t_ms / 1e3),
             "plain_fp64": compare,
-            "plain_fp64_refactor_every_step": refactor,
-            "learned_warm_start": learned_line,
             "roofline": roofline,
             "e2e": e2e,
-            "gpu_launches": len(launch_ms) * len(stats["classes"]),
-            "clocks": clocks,
-            "launch_ms": {"mean": statistics.mean(launch_ms),
-                          "median": statistics.median(launch_ms),
-                          "min": min(launch_ms), "max": max(launch_ms)},
+            "gpu_launches": len(r["launch_ms"]) * len(r["classes"]),
+            "clocks": r["clocks"],
+            "launch_ms": {"mean": statistics.mean(r["launch_ms"]),
+                          "median": statistics.median(r["launch_ms"]),
+                          "min": min(r["launch_ms"]), "max": max(r["launch_ms"])},
         }
         if not args.no_cpu_baseline and world == 1:
             if args.workload == "fem_beam":
-                line["cpu_baseline"] = cpu_baseline_one_scene(
-                    args, h, total_iters / max(stats["scene_steps"], 1))
+                fr = oracle_fem_rate(threads)
+                mi = line["iterations"]["mean_per_scene_step"]
+                line["cpu_baseline"] = {
+                    "value": 1.0 / (fr["setup_s"] + fr["per_iter_s"] * mi), "unit": "steps/s",
+                    "cores": threads, "kind": "oracle", "cpu": host_cpu(),
+                    "sample": f"first step at 1 and 4 iterations, OpenMP build, extrapolated "
+                              f"to {mi:.0f} iterations per step"}
             else:
-                line["cpu_baseline"] = cpu_baseline(batch_for_rank(0, args.robots, h,
-                                                                   args.workload, args.scenes),
-                                                    args.cpu_seconds)
+                line["cpu_baseline"] = oracle_rate(args.workload, p, preroll + 1, args.warmup,
+                                                   K, threads, args.cpu_seconds,
+                                                   args.reference_scenes or wl["cpu_scenes"])
+        line["sub_results"] = subs or None
         print(json.dumps(line), flush=True)
-    sim.close()
     if dist is not None:
         dist.destroy_process_group()
     return 0

@@ -70,8 +70,10 @@ extern "C" {
 #define SIM_STOP_PRIMAL 0     /* stop when max|x - z| <= tol and max|z^{l+1}-z^l| <= tol    */
 #define SIM_STOP_THETA 1      /* stop when theta < theta_th after the v-step (Eq. residual) */
 #define SIM_FP64 0            /* every step in double precision                             */
-#define SIM_MIXED 1           /* FP64 assembly, beta, factorisation and final residual check;
-                                 FP32 iterations (resumed if the FP64 check misses the tol.) */
+#define SIM_MIXED 1           /* FP64 assembly, beta and final residual check; K_i factorised
+                                 in FP32, or in FP64 when the block is stiff (spread of K_i's
+                                 diagonal above 1e3); FP32 iterations (resumed with a refined
+                                 c if the FP64 check misses the tolerance)                 */
 
 /* what sim_get() reads */
 #define SIM_GET_VHAT 0        /* id = subsystem: n doubles, v-hat of the last step          */
@@ -235,6 +237,12 @@ int sim_grid_threshold(sim_t s, int side_rows);
  * sim_step. */
 int sim_grid_staging(sim_t s, int enable);
 
+/* Grid kernel: run the cooperative launch with `blocks` blocks (at most the resident count;
+ * 0, the default, takes every resident block: 2 per SM).  Fewer blocks give each warp more
+ * side-rows, subsystems and items; the results do not depend on it.  Takes effect at the
+ * next sim_step; SIM_EINVAL for blocks < 0. */
+int sim_grid_blocks(sim_t s, int blocks);
+
 /* A linear block's K_i = A_i + beta_i J_i^T J_i is constant (Sec. II-B: its A_i and its
  * node-selector rows are), so by default (enable != 0) its factor, W and D are computed at
  * its first step and kept.  With 0 every step factorises every block again, as Algorithm 1
@@ -250,6 +258,14 @@ int sim_keep_factors(sim_t s, int enable);
  * out, raises the error flag and returns.  Writes out[0] the error flag (1 if a wait ran
  * out), out[1] the blocks that left the barrier.  Synchronises the device. */
 int sim_probe_barrier(int device, int blocks, int expected, double limit_s, int out[2]);
+
+/* Floor of one iteration of the block kernel (a measurement aid, no counterpart in the
+ * paper): launches one 256-thread block per SM on `device` that runs `iters` rounds of the
+ * block barrier (__syncthreads_count) the block kernel ends every iteration with, nothing
+ * else between them.  Writes out[0] SM clock cycles per round (mean over blocks), out[1]
+ * nanoseconds per round of the whole launch (CUDA events).  Synchronises the device;
+ * allocates (and frees) a small device buffer.  SIM_EINVAL for iters outside 1..1e7. */
+int sim_barrier_floor(int device, int iters, double out[2]);
 
 /* CUDA-graph replay of sim_step (off by default).  When enabled, the first sim_step with a
  * given n_steps captures its launches (one per launch class of scenes, forked across streams

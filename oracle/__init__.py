@@ -18,8 +18,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
+_LIB_PATH_OMP = os.path.join(_HERE, "_build", "liboracle_omp.so")
 _lock = threading.Lock()
-_lib = None
+_libs = {}
 
 D = C.c_double
 PD = C.POINTER(C.c_double)
@@ -30,22 +31,23 @@ VP = C.c_void_p
 T_CODES = {0: 0, 1: 1, 2: 2, 3: 3}
 
 
-def build(force: bool = False) -> str:
-    """Compile oracle.c with plain gcc (no FMA contraction) into oracle/_build/."""
-    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
-        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile oracle.c with plain gcc (no FMA contraction) into oracle/_build/.  With
+    ``openmp`` the same source is built with -fopenmp (the multi-core timing baseline)."""
+    path = _LIB_PATH_OMP if openmp else _LIB_PATH
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    if force or not os.path.exists(path) or os.path.getmtime(path) < os.path.getmtime(_SRC):
+        tmp = path + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-std=c99", "-shared", "-fPIC",
-                               _SRC, "-o", tmp, "-lm"])
-        os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+                               *(["-fopenmp"] if openmp else []), _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, path)
+    return path
 
 
-def lib():
-    global _lib
+def lib(openmp: bool = False):
     with _lock:
-        if _lib is None:
-            L = C.CDLL(build())
+        if openmp not in _libs:
+            L = C.CDLL(build(openmp=openmp))
             sig = {
                 "orc_new": (VP, [PD]),
                 "orc_add_generic": (C.c_int, [VP, C.c_int, PD, PD]),
@@ -75,6 +77,7 @@ def lib():
                 "orc_get_body": (None, [VP, C.c_int, C.c_int, PD]),
                 "orc_set_body": (None, [VP, C.c_int, C.c_int, PD]),
                 "orc_set_generic": (None, [VP, C.c_int, PD, PD]),
+                "orc_set_warm": (None, [VP, C.c_int, PD, PD]),
                 "orc_residuals": (None, [VP, PD]),
                 "orc_chol_solve": (C.c_int, [C.c_int, PD, PD, PD]),
                 "orc_project": (None, [C.c_int, C.c_int, C.c_int, PD, PD, PD, D, D, D, PD]),
@@ -84,8 +87,8 @@ def lib():
                 f = getattr(L, name)
                 f.restype = res
                 f.argtypes = args
-            _lib = L
-    return _lib
+            _libs[openmp] = L
+    return _libs[openmp]
 
 
 def _p(a: np.ndarray):
@@ -116,8 +119,8 @@ def joint_params(j) -> np.ndarray:
 class OracleScene:
     """One scene held by the oracle (subsystems and constraints in scene order)."""
 
-    def __init__(self, scene, options):
-        L = lib()
+    def __init__(self, scene, options, openmp: bool = False):
+        L = lib(openmp)
         self.L = L
         ov = options_vector(options)
         self.h = L.orc_new(_p(ov))
@@ -263,6 +266,11 @@ class OracleScene:
     def set_body(self, i, k, rec):
         rec = _f64(rec)
         self.L.orc_set_body(self.h, i, k, _p(rec))
+
+    def set_warm(self, j, lam, z):
+        """Constraint j's warm-start state (lambda per row, z per side and row)."""
+        lam, z = _f64(lam), _f64(z)
+        self.L.orc_set_warm(self.h, j, _p(lam), _p(z.ravel()))
 
     def set_generic(self, i, A=None, b=None):
         Aa = _f64(A) if A is not None else None

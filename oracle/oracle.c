@@ -39,6 +39,12 @@
  *     open gap, gamma gap/h for penetration; tangential e = 0.
  *
  * Rounding: build with -O2 -ffp-contract=off (no fused multiply-add).
+ *
+ * Threads: the plain build is single-threaded.  Built with -fopenmp (the benchmark's
+ * multi-core timing baseline only, as the paper times its own solver with OpenMP) the
+ * factorisation and v-step run one subsystem per thread and the constraint loops one
+ * constraint per thread; every per-element result is the same, only the order of theta's
+ * sum differs.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -607,7 +613,10 @@ int orc_step(orc_scene *S)
         }
         u->beta = trJ > 0.0 ? trA / trJ : 1.0;
     }
-    /* factorise K_i = A_i + beta_i J_ci^T J_ci */
+    /* factorise K_i = A_i + beta_i J_ci^T J_ci (subsystems are independent: the OpenMP
+       build of the timing baseline runs them on separate threads) */
+    int notspd = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : notspd)
     for (int i = 0; i < S->nsub; i++) {
         sub_t *u = &S->subs[i];
         int n = u->n;
@@ -626,8 +635,9 @@ int orc_step(orc_scene *S)
         }
         int rc = cholesky(n, K, u->L);
         free(K);
-        if (rc) { S->status = -3; return -3; }
+        if (rc) notspd = 1;
     }
+    if (notspd) { S->status = -3; return -3; }
     /* initial z, u (cold: zeros; warm: previous step's z and -lambda) */
     for (int j = 0; j < S->ncon; j++) {
         con_t *c = &S->cons[j];
@@ -650,29 +660,29 @@ int orc_step(orc_scene *S)
     S->r_p = INFINITY; S->r_d = INFINITY; S->theta = INFINITY;
     int L = S->max_iters;
     for (int l = 0; l < L; l++) {
-        /* v-step: rhs_i = b_i + J_ci^T (beta_i z_i - u_i); K_i v_i = rhs_i */
+        /* v-step: rhs_i = b_i + J_ci^T (beta_i z_i - u_i); K_i v_i = rhs_i.  Each subsystem
+           gathers its constraints' terms in constraint order (independent per subsystem) */
+#pragma omp parallel for schedule(dynamic, 1)
         for (int i = 0; i < S->nsub; i++) {
             sub_t *u = &S->subs[i];
             memcpy(u->rhs, u->b, sizeof(double) * u->n);
-        }
-        for (int j = 0; j < S->ncon; j++) {
-            con_t *c = &S->cons[j];
-            for (int s = 0; s < c->ns; s++) {
-                sub_t *u = &S->subs[c->sub[s]];
-                for (int r = 0; r < c->rows; r++) {
-                    int q = s * c->rows + r;
-                    double w = u->beta * c->z[q] - c->u[q];
-                    for (int p = 0; p < u->n; p++) u->rhs[p] += c->J[s][r * u->n + p] * w;
+            for (int j = 0; j < S->ncon; j++) {
+                con_t *c = &S->cons[j];
+                for (int s = 0; s < c->ns; s++) {
+                    if (c->sub[s] != i) continue;
+                    for (int r = 0; r < c->rows; r++) {
+                        int q = s * c->rows + r;
+                        double w = u->beta * c->z[q] - c->u[q];
+                        for (int p = 0; p < u->n; p++) u->rhs[p] += c->J[s][r * u->n + p] * w;
+                    }
                 }
             }
-        }
-        for (int i = 0; i < S->nsub; i++) {
-            sub_t *u = &S->subs[i];
             memcpy(u->v, u->rhs, sizeof(double) * u->n);
             chol_solve(u->n, u->L, u->v);
         }
         /* x_i = J_ci v_i ; y_i = beta_i x_i + u_i ; theta */
         double theta = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : theta)
         for (int j = 0; j < S->ncon; j++) {
             con_t *c = &S->cons[j];
             for (int s = 0; s < c->ns; s++) {
@@ -698,8 +708,9 @@ int orc_step(orc_scene *S)
             }
             break;
         }
-        /* z-step per constraint, then u-step, then residuals */
+        /* z-step per constraint, then u-step, then residuals (independent per constraint) */
         double rp = 0.0, rd = 0.0, rz = 0.0;
+#pragma omp parallel for schedule(static) reduction(max : rp, rd, rz)
         for (int j = 0; j < S->ncon; j++) {
             con_t *c = &S->cons[j];
             double beta[MAXSIDES];
@@ -878,6 +889,16 @@ void orc_set_body(orc_scene *S, int i, int k, const double *in)
     memcpy(B->q, in + 7, 4 * sizeof(double));
     memcpy(B->v, in + 11, 3 * sizeof(double));
     memcpy(B->w, in + 14, 3 * sizeof(double));
+}
+
+/* Sets constraint j's warm-start state, as a finished step leaves it: lambda (rows) and z
+   (sides x rows).  Lets a test start the oracle from a state reached elsewhere. */
+void orc_set_warm(orc_scene *S, int j, const double *lam, const double *z)
+{
+    con_t *c = &S->cons[j];
+    memcpy(c->lamprev, lam, sizeof(double) * c->rows);
+    memcpy(c->zprev, z, sizeof(double) * c->rows * c->ns);
+    c->has_prev = 1;
 }
 
 void orc_set_generic(orc_scene *S, int i, const double *A, const double *b)

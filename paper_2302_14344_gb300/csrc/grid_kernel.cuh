@@ -79,6 +79,24 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned pari
     }
 }
 
+// After a stage's copy missed its wait: wait once more, bounded, for every copy the warp
+// still has in flight (bit s of *pend: stage s's copy was issued and not yet waited for), so
+// that no bulk copy lands in the block's shared memory after the block stops expecting it.
+// Stages whose copy completes are cleared from *pend (their parity advances); a copy that
+// never completes stays in *pend, and the caller no longer uses the stage buffers at all.
+__device__ __forceinline__ void drain_stages(unsigned long long *bars, unsigned *pend,
+                                             unsigned *ph, int nst)
+{
+    for (int s = 0; s < nst; ++s) {
+        if (!((*pend >> s) & 1u)) continue;
+        const bool got = __all_sync(0xffffffffu, mbar_wait(&bars[s], (*ph >> s) & 1u, 2000000000ull));
+        if (got) {
+            *ph ^= 1u << s;
+            *pend &= ~(1u << s);
+        }
+    }
+}
+
 template <typename T, int SPLIT>
 __global__ void __launch_bounds__(SUBADMM_THREADS, 2) grid_step_kernel(StepParams P)
 {
@@ -112,6 +130,7 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 2) grid_step_kernel(StepParam
     }
     __syncthreads();
     unsigned ph = 0;            // parity of the next completion of each stage's barrier
+    unsigned pend = 0;          // stages whose issued copy has not been waited for yet
     bool stage_ok = true;       // false after a copy that did not complete in time
     for (int q = d.tid; q < S.ot_lam - S.ot_x; q += d.nthreads) V.tb[S.ot_x + q] = (T)0;
     scene_tables<T>(P, S, V, d);
@@ -207,6 +226,7 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 2) grid_step_kernel(StepParam
                         if (lane == 0 && len > 0)
                             bulk_row_load(stg + (size_t)k * P.grid_stage, V.htb + drow,
                                           (unsigned)((len + VN - 1) / VN * 16), &stage_bar[wl][k]);
+                        if (len > 0) pend |= 1u << k;
                     }
                     for (int k = 0; k < trips; ++k) {
                         const int s = k % nst;
@@ -216,14 +236,18 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 2) grid_step_kernel(StepParam
                         if (len > 0 && staged) {
                             const bool got = __all_sync(0xffffffffu,
                                                         mbar_wait(&stage_bar[wl][s], (ph >> s) & 1u, 2000000000ull));
-                            ph ^= 1u << s;
-                            if (!got) {
+                            if (got) {
+                                ph ^= 1u << s;
+                                pend &= ~(1u << s);
+                            } else {
                                 // the copy did not complete: flag the launch (as a barrier
                                 // time-out does, so the grid runs to its end and the step
-                                // reports it) and stop staging rows
+                                // reports it), stop staging rows and wait, bounded, for the
+                                // copies still in flight
                                 if (lane == 0) atomicExch(&G->err, 1);
                                 staged = false;
                                 stage_ok = false;
+                                drain_stages(stage_bar[wl], &pend, &ph, nst);
                             }
                             const VT *Ds = reinterpret_cast<const VT *>(stg + (size_t)s * P.grid_stage);
                             const VT *wv = reinterpret_cast<const VT *>(w + wbk);
@@ -246,6 +270,7 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 2) grid_step_kernel(StepParam
                             if (staged && lane == 0 && len2 > 0)
                                 bulk_row_load(stg + (size_t)s * P.grid_stage, V.htb + drow2,
                                               (unsigned)((len2 + VN - 1) / VN * 16), &stage_bar[wl][s]);
+                            if (staged && len2 > 0) pend |= 1u << s;
                         }
 #pragma unroll
                         for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -484,10 +509,12 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 2) grid_step_kernel(StepParam
                 continue;
             }
             if (lead) G->chk = 0ull;
-            // the warp's stage buffers (idle outside the v-step) hold the solves' vector
+            // the warp's stage buffers (idle outside the v-step) hold the solves' vector,
+            // unless a copy into them may still be in flight (after a missed wait)
+            const bool stg_free = P.grid_stage > 0 && __all_sync(0xffffffffu, pend == 0u);
             recover_v<T>(P, S, V, last_par ? W1 : W0, d,
-                         P.grid_stage > 0 ? reinterpret_cast<T *>(stg) : nullptr,
-                         P.grid_stage > 0 ? nst * P.grid_stage / (int)sizeof(T) : 0);
+                         stg_free ? reinterpret_cast<T *>(stg) : nullptr,
+                         stg_free ? nst * P.grid_stage / (int)sizeof(T) : 0);
             d.sync();
             if (MIXED && conv && primal_stop && status == ST_OK) {
                 // FP64 primal residual max |J v - z|; on a miss, refine c by the FP64 - FP32
@@ -582,6 +609,8 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 2) grid_step_kernel(StepParam
             st[4] += fallbacks;
         }
     }
+    // a copy still in flight after a missed wait: wait for it (bounded) before the block exits
+    if (pend) drain_stages(stage_bar[wl], &pend, &ph, nst);
 }
 
 // Self-test of the barrier's time limit: every block waits once for `expected` arrivals and

@@ -17,6 +17,7 @@
 #include "grid_kernel.cuh"
 #include "features.cuh"
 #include "warmstart.h"
+#include "device_guard.h"
 
 namespace {
 
@@ -102,6 +103,7 @@ struct sim_s {
     int smem_full = 0;             // dynamic shared memory a block may use
     int grid_side_rows = kGridSideRows;
     int grid_staging = 1;          // grid kernel: stage D rows in shared memory by bulk copies
+    int grid_blocks = 0;           // grid kernel: blocks of the cooperative launch (0: all resident)
     int keep_factors = 1;          // keep the factors of constant blocks across steps
     // graph replay of sim_step
     bool use_graph = false;
@@ -197,6 +199,22 @@ __global__ void unpack_state(double *bodies, double *nodes, const double *in, lo
     }
 }
 
+#define ON_DEVICE(dev)                                                  \
+    subadmm::DeviceGuard device_guard_(dev);                                     \
+    if (device_guard_.err != cudaSuccess) return cuda_fail(s, device_guard_.err, "cudaSetDevice")
+
+// Drops the captured graphs of sim_step and sim_step_learned: their launches hold the kernel
+// arguments (variants, flags, tracer pointer) of their capture, so they are captured again.
+void drop_graphs(sim_t s)
+{
+    if (s->graph) cudaGraphExecDestroy(s->graph);
+    s->graph = nullptr;
+    s->graph_steps = 0;
+    if (s->graph_learned) cudaGraphExecDestroy(s->graph_learned);
+    s->graph_learned = nullptr;
+    s->graph_learned_net = nullptr;
+}
+
 long long state_doubles(const sim_t s) { return 13 * s->nbodies + SUBADMM_NODE * s->nnodes; }
 
 void free_device(sim_t s)
@@ -227,12 +245,7 @@ void free_device(sim_t s)
     s->classes.clear();
     if (s->ev_fork) cudaEventDestroy(s->ev_fork);
     s->ev_fork = nullptr;
-    if (s->graph) cudaGraphExecDestroy(s->graph);
-    s->graph = nullptr;
-    s->graph_steps = 0;
-    if (s->graph_learned) cudaGraphExecDestroy(s->graph_learned);
-    s->graph_learned = nullptr;
-    s->graph_learned_net = nullptr;
+    drop_graphs(s);
     if (s->graph_stream) cudaStreamDestroy(s->graph_stream);
     s->graph_stream = nullptr;
     s->d_nodes = nullptr; s->d_ipool = nullptr; s->d_subflag = nullptr;
@@ -267,7 +280,7 @@ int zeros(sim_t s, double **dst, size_t count, const char *what)
 int finalize(sim_t s)
 {
     if (s->finalized) return SIM_OK;
-    CK(cudaSetDevice(s->opt.device), "cudaSetDevice");
+    ON_DEVICE(s->opt.device);
     const int nsubs = (int)s->subs.size(), ncons = (int)s->cons.size();
     int nscenes = 0;
     for (auto &u : s->subs) nscenes = std::max(nscenes, u.scene + 1);
@@ -890,8 +903,11 @@ int sim_create(const sim_options *opt, sim_t *out)
     cudaError_t e = cudaGetDeviceCount(&ndev);
     if (e != cudaSuccess) return fail(nullptr, SIM_ECUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
     if (o.device < 0 || o.device >= ndev) return fail(nullptr, SIM_EINVAL, "device ordinal out of range");
-    e = cudaSetDevice(o.device);
-    if (e != cudaSuccess) return fail(nullptr, SIM_ECUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+    {
+        subadmm::DeviceGuard on_device(o.device);
+        if (on_device.err != cudaSuccess)
+            return fail(nullptr, SIM_ECUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(on_device.err));
+    }
     sim_t s = new (std::nothrow) sim_s();
     if (!s) return fail(nullptr, SIM_ENOMEM, "host allocation failed");
     s->opt = o;
@@ -903,9 +919,11 @@ int sim_create(const sim_options *opt, sim_t *out)
 void sim_destroy(sim_t s)
 {
     if (!s) return;
-    cudaSetDevice(s->opt.device);
-    cudaStreamSynchronize(s->stream);
-    free_device(s);
+    {
+        subadmm::DeviceGuard on_device(s->opt.device);
+        cudaStreamSynchronize(s->stream);
+        free_device(s);
+    }
     delete s;
 }
 
@@ -1042,6 +1060,7 @@ int sim_add_interface(sim_t s, int scene, int kind, int rows, int n_sides, const
 int sim_set_generic(sim_t s, int sub, const double *A, const double *b)
 {
     if (!s) return SIM_EINVAL;
+    ON_DEVICE(s->opt.device);
     if (sub < 0 || sub >= (int)s->subs.size() || s->subs[sub].kind != KIND_GENERIC)
         return fail(s, SIM_EINVAL, "not a generic subsystem");
     HostSub &u = s->subs[sub];
@@ -1065,6 +1084,17 @@ int sim_set_generic(sim_t s, int sub, const double *A, const double *b)
 namespace {
 
 using KernFn = void (*)(StepParams);
+
+// `iters` rounds of the block barrier that ends every iteration of the block kernel
+// (__syncthreads_count), with nothing else between them: the floor of one iteration
+__global__ void barrier_floor_kernel(int iters, long long *cycles)
+{
+    const long long t0 = clock64();
+    int acc = 0;
+    for (int k = 0; k < iters; ++k) acc += __syncthreads_count((int)threadIdx.x == (k & 255));
+    const long long t1 = clock64();
+    if (threadIdx.x == 0) cycles[blockIdx.x] = (t1 - t0) + (acc < 0 ? 1 : 0);
+}
 
 // kernel parameters of a step launch (scene list filled in per class)
 StepParams step_params(const sim_t s, int n_steps)
@@ -1124,7 +1154,8 @@ int launch_grid_class(sim_t s, LaunchClass &c, StepParams P, cudaStream_t st, in
     int per_sm = 0, sms = 0;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kf, SUBADMM_THREADS, 0), "occupancy");
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->opt.device), "attribute");
-    const int blocks = std::max(1, per_sm * sms);
+    const int resident = std::max(1, per_sm * sms);
+    const int blocks = s->grid_blocks > 0 ? std::min(s->grid_blocks, resident) : resident;
     c.max_smem = 0;                 // reported: the largest stage buffers of the class's launches
     for (size_t i = 0; i < c.scenes.size(); ++i) {
         // D rows staged in shared memory by bulk copies (the warp-per-row v-step only), two
@@ -1207,7 +1238,7 @@ int sim_step(sim_t s, int n_steps)
     int rc = finalize(s);
     if (rc) return rc;
     if (s->nscenes == 0) return SIM_OK;
-    CK(cudaSetDevice(s->opt.device), "cudaSetDevice");
+    ON_DEVICE(s->opt.device);
     StepParams P = step_params(s, n_steps);
     // the attribute is per function (shared by every simulation of the process): allow the
     // full budget; each launch requests its class's own size, which sets its occupancy
@@ -1260,16 +1291,7 @@ int sim_use_graph(sim_t s, int enable)
 {
     if (!s) return SIM_EINVAL;
     s->use_graph = enable != 0;
-    if (!s->use_graph && s->graph) {
-        cudaGraphExecDestroy(s->graph);
-        s->graph = nullptr;
-        s->graph_steps = 0;
-    }
-    if (!s->use_graph && s->graph_learned) {
-        cudaGraphExecDestroy(s->graph_learned);
-        s->graph_learned = nullptr;
-        s->graph_learned_net = nullptr;
-    }
+    if (!s->use_graph) drop_graphs(s);
     return SIM_OK;
 }
 
@@ -1302,6 +1324,7 @@ void class_rows(const sim_t s, int max_classes, long long *out, const std::vecto
 int sim_launch_classes(sim_t s, int max_classes, long long *out)
 {
     if (!s || (max_classes > 0 && !out)) return SIM_EINVAL;
+    ON_DEVICE(s->opt.device);
     int rc = finalize(s);
     if (rc) return rc;
     class_rows(s, max_classes, out, nullptr);
@@ -1311,10 +1334,10 @@ int sim_launch_classes(sim_t s, int max_classes, long long *out)
 int sim_autotune(sim_t s, int steps, int max_classes, long long *out)
 {
     if (!s || steps < 1 || (max_classes > 0 && !out)) return SIM_EINVAL;
+    ON_DEVICE(s->opt.device);
     int rc = finalize(s);
     if (rc) return rc;
     if (s->nscenes == 0) return 0;
-    CK(cudaSetDevice(s->opt.device), "cudaSetDevice");
     CK(cudaStreamSynchronize(s->stream), "stream synchronize");
     // snapshot of everything a step writes
     struct Arr { void *p; size_t bytes; };
@@ -1419,16 +1442,7 @@ int sim_autotune(sim_t s, int steps, int max_classes, long long *out)
     cudaEventDestroy(e1);
     cudaFree(snap);
     if (err != cudaSuccess) return cuda_fail(s, err, "autotune");
-    if (s->graph) {            // the captured launches used the old variants
-        cudaGraphExecDestroy(s->graph);
-        s->graph = nullptr;
-        s->graph_steps = 0;
-    }
-    if (s->graph_learned) {
-        cudaGraphExecDestroy(s->graph_learned);
-        s->graph_learned = nullptr;
-        s->graph_learned_net = nullptr;
-    }
+    drop_graphs(s);            // the captured launches used the old variants
     class_rows(s, max_classes, out, &best_ns);
     return (int)s->classes.size();
 }
@@ -1458,7 +1472,7 @@ int sim_interface_features(sim_t s, float *x_dev)
     if (rc) return rc;
     const int nif = (int)s->cons.size();
     if (nif == 0) return SIM_OK;
-    CK(cudaSetDevice(s->opt.device), "cudaSetDevice");
+    ON_DEVICE(s->opt.device);
     subadmm::interface_features_kernel<<<grid_of(nif), 128, 0, s->stream>>>(
         step_params(s, 1), s->d_pub2dev, s->d_con_scene, nif, x_dev);
     CK(cudaGetLastError(), "features launch");
@@ -1471,7 +1485,7 @@ int sim_interface_targets(sim_t s, const float *x_dev, float *t_dev, float *mask
     if (!s->finalized) return fail(s, SIM_EINVAL, "no step has run");
     const int nif = (int)s->cons.size();
     if (nif == 0) return SIM_OK;
-    CK(cudaSetDevice(s->opt.device), "cudaSetDevice");
+    ON_DEVICE(s->opt.device);
     subadmm::interface_targets_kernel<<<grid_of(nif), 128, 0, s->stream>>>(
         step_params(s, 1), s->d_pub2dev, s->d_con_scene, nif, x_dev, t_dev, mask_dev);
     CK(cudaGetLastError(), "targets launch");
@@ -1489,7 +1503,7 @@ int sim_step_learned(sim_t s, wsn_t net, int n_steps)
     if (rc) return rc;
     if (s->nscenes == 0) return SIM_OK;
     if ((rc = interface_buffers(s))) return rc;
-    CK(cudaSetDevice(s->opt.device), "cudaSetDevice");
+    ON_DEVICE(s->opt.device);
     const int nif = (int)s->cons.size();
     StepParams P = step_params(s, 1);
     for (const LaunchClass &c : s->classes)
@@ -1579,17 +1593,29 @@ int sim_grid_staging(sim_t s, int enable)
     return SIM_OK;
 }
 
+int sim_grid_blocks(sim_t s, int blocks)
+{
+    if (!s) return SIM_EINVAL;
+    if (blocks < 0) return fail(s, SIM_EINVAL, "blocks must be >= 0");
+    s->grid_blocks = blocks;
+    return SIM_OK;
+}
+
 int sim_keep_factors(sim_t s, int enable)
 {
     if (!s) return SIM_EINVAL;
-    s->keep_factors = enable ? 1 : 0;
+    const int k = enable ? 1 : 0;
+    // the flag is a kernel argument: a graph captured with the old value must not replay
+    if (k != s->keep_factors) drop_graphs(s);
+    s->keep_factors = k;
     return SIM_OK;
 }
 
 int sim_probe_barrier(int device, int blocks, int expected, double limit_s, int out[2])
 {
     if (!out || blocks < 1 || expected < 1 || !(limit_s > 0.0) || limit_s > 10.0) return SIM_EINVAL;
-    if (cudaSetDevice(device) != cudaSuccess) return SIM_ECUDA;
+    subadmm::DeviceGuard on_device(device);
+    if (on_device.err != cudaSuccess) return SIM_ECUDA;
     int per_sm = 0, sms = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, subadmm::barrier_probe_kernel, 32, 0) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
@@ -1615,9 +1641,43 @@ int sim_probe_barrier(int device, int blocks, int expected, double limit_s, int 
     return SIM_OK;
 }
 
+int sim_barrier_floor(int device, int iters, double out[2])
+{
+    if (!out || iters < 1 || iters > 10000000) return SIM_EINVAL;
+    subadmm::DeviceGuard on_device(device);
+    if (on_device.err != cudaSuccess) return SIM_ECUDA;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
+        return SIM_ECUDA;
+    long long *cyc = nullptr;
+    if (cudaMalloc((void **)&cyc, sizeof(long long) * sms) != cudaSuccess) return SIM_ENOMEM;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    barrier_floor_kernel<<<sms, SUBADMM_THREADS>>>(iters, cyc);     // warm-up
+    cudaEventRecord(e0, 0);
+    barrier_floor_kernel<<<sms, SUBADMM_THREADS>>>(iters, cyc);
+    cudaEventRecord(e1, 0);
+    cudaError_t e = cudaEventSynchronize(e1);
+    std::vector<long long> host(sms, 0);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e == cudaSuccess) e = cudaMemcpy(host.data(), cyc, sizeof(long long) * sms, cudaMemcpyDeviceToHost);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(cyc);
+    if (e != cudaSuccess) return SIM_ECUDA;
+    double sum = 0.0;
+    for (long long c : host) sum += (double)c;
+    out[0] = sum / sms / iters;
+    out[1] = (double)ms * 1e6 / iters;
+    return SIM_OK;
+}
+
 int sim_sync(sim_t s)
 {
     if (!s) return SIM_EINVAL;
+    ON_DEVICE(s->opt.device);
     CK(cudaStreamSynchronize(s->stream), "stream synchronize");
     return SIM_OK;
 }
@@ -1625,6 +1685,7 @@ int sim_sync(sim_t s)
 int sim_residuals(sim_t s, int scene, double out[6])
 {
     if (!s || !out) return SIM_EINVAL;
+    ON_DEVICE(s->opt.device);
     if (!s->finalized) return fail(s, SIM_EINVAL, "no step has run");
     if (scene < 0 || scene >= s->nscenes) return fail(s, SIM_EINVAL, "scene out of range");
     CK(cudaStreamSynchronize(s->stream), "stream synchronize");
@@ -1640,6 +1701,7 @@ int sim_residuals(sim_t s, int scene, double out[6])
 int sim_get(sim_t s, int what, int id, double *dst)
 {
     if (!s || !dst) return SIM_EINVAL;
+    ON_DEVICE(s->opt.device);
     if (!s->finalized) return fail(s, SIM_EINVAL, "no step has run");
     CK(cudaStreamSynchronize(s->stream), "stream synchronize");
     if (what == SIM_GET_VHAT || what == SIM_GET_BODIES || what == SIM_GET_BETA) {
@@ -1683,6 +1745,7 @@ int sim_get(sim_t s, int what, int id, double *dst)
 int sim_read_state(sim_t s, double *dst)
 {
     if (!s || !dst) return SIM_EINVAL;
+    ON_DEVICE(s->opt.device);
     int rc = finalize(s);
     if (rc) return rc;
     const long long nd = state_doubles(s);
@@ -1715,6 +1778,7 @@ extern "C" {
 int sim_read_state_noalloc(sim_t s, double *dst)
 {
     if (!s || !dst) return SIM_EINVAL;
+    ON_DEVICE(s->opt.device);
     if (!s->finalized)
         return fail(s, SIM_EINVAL, "sim_read_state_noalloc needs a simulation whose device memory "
                                    "is laid out (after its first sim_step)");
@@ -1725,7 +1789,6 @@ int sim_read_state_noalloc(sim_t s, double *dst)
                                    "(1 MiB staging)");
     const int dev = s->opt.device;
     if (dev < 0 || dev >= kNoallocMaxDevices) return fail(s, SIM_EINVAL, "device ordinal too large");
-    CK(cudaSetDevice(dev), "cudaSetDevice");
     double *stage = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_noalloc_mutex);
@@ -1748,6 +1811,7 @@ int sim_read_state_noalloc(sim_t s, double *dst)
 int sim_write_state(sim_t s, const double *src)
 {
     if (!s || !src) return SIM_EINVAL;
+    ON_DEVICE(s->opt.device);
     int rc = finalize(s);
     if (rc) return rc;
     const long long nd = state_doubles(s);
@@ -1779,6 +1843,7 @@ int sim_sizes(sim_t s, long long out[9])
 int sim_scene_info(sim_t s, int scene, long long out[4])
 {
     if (!s || !out) return SIM_EINVAL;
+    ON_DEVICE(s->opt.device);
     int rc = finalize(s);
     if (rc) return rc;
     if (scene < 0 || scene >= s->nscenes) return fail(s, SIM_EINVAL, "scene out of range");
@@ -1793,6 +1858,7 @@ int sim_scene_info(sim_t s, int scene, long long out[4])
 int sim_iteration_stats(sim_t s, long long out[5], long long *per_scene)
 {
     if (!s || !out) return SIM_EINVAL;
+    ON_DEVICE(s->opt.device);
     if (!s->finalized) return fail(s, SIM_EINVAL, "no step has run");
     CK(cudaStreamSynchronize(s->stream), "stream synchronize");
     std::vector<long long> st((size_t)5 * std::max(1, s->nscenes));
@@ -1813,6 +1879,7 @@ int sim_iteration_stats(sim_t s, long long out[5], long long *per_scene)
 int sim_phase_trace(sim_t s, int enable, long long out[8])
 {
     if (!s) return SIM_EINVAL;
+    ON_DEVICE(s->opt.device);
     int rc = finalize(s);
     if (rc) return rc;
     const size_t bytes = sizeof(long long) * 8 * std::max(1, s->nscenes);
@@ -1829,12 +1896,7 @@ int sim_phase_trace(sim_t s, int enable, long long out[8])
     // a captured graph holds the tracer pointer of its capture: capture again
     if (s->graph || s->graph_learned) {
         CK(cudaStreamSynchronize(s->stream), "stream synchronize");
-        if (s->graph) cudaGraphExecDestroy(s->graph);
-        if (s->graph_learned) cudaGraphExecDestroy(s->graph_learned);
-        s->graph = nullptr;
-        s->graph_steps = 0;
-        s->graph_learned = nullptr;
-        s->graph_learned_net = nullptr;
+        drop_graphs(s);
     }
     if (enable && !s->d_phase) {
         cudaError_t e = cudaMalloc((void **)&s->d_phase, bytes);

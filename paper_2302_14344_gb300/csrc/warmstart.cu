@@ -12,6 +12,7 @@
 #include "subadmm.h"
 #include "warmstart.h"
 #include "mlp.cuh"
+#include "device_guard.h"
 
 struct wsn_s {
     int device = 0;
@@ -168,7 +169,8 @@ int wsn_create(int device, int n_layers, const int *sizes, wsn_t *out)
     *out = nullptr;
     for (int l = 0; l <= n_layers; ++l)
         if (sizes[l] < 1 || sizes[l] > 1024) return SIM_EINVAL;
-    if (cudaSetDevice(device) != cudaSuccess) return SIM_ECUDA;
+    subadmm::DeviceGuard on_device(device);
+    if (on_device.err != cudaSuccess) return SIM_ECUDA;
     wsn_t w = new wsn_s();
     w->device = device;
     w->sizes.assign(sizes, sizes + n_layers + 1);
@@ -206,7 +208,7 @@ int wsn_create(int device, int n_layers, const int *sizes, wsn_t *out)
 void wsn_destroy(wsn_t w)
 {
     if (!w) return;
-    cudaSetDevice(w->device);
+    subadmm::DeviceGuard on_device(w->device);
     free_ws(w);
     cudaFree(w->p); cudaFree(w->g); cudaFree(w->m); cudaFree(w->v); cudaFree(w->pb);
     cudaFree(w->mean); cudaFree(w->inv_std); cudaFree(w->scale);
@@ -230,7 +232,8 @@ int wsn_shape(wsn_t w, int shape[2])
 int wsn_set_params(wsn_t w, const float *params)
 {
     if (!w || !params) return SIM_EINVAL;
-    WCK(cudaSetDevice(w->device), "cudaSetDevice");
+    subadmm::DeviceGuard on_device(w->device);
+    WCK(on_device.err, "cudaSetDevice");
     const size_t bytes = sizeof(float) * (size_t)w->nparams;
     WCK(cudaMemcpy(w->p, params, bytes, cudaMemcpyHostToDevice), "params");
     WCK(cudaMemset(w->m, 0, bytes), "adam state");
@@ -245,7 +248,8 @@ int wsn_set_params(wsn_t w, const float *params)
 int wsn_get_params(wsn_t w, float *params)
 {
     if (!w || !params) return SIM_EINVAL;
-    WCK(cudaSetDevice(w->device), "cudaSetDevice");
+    subadmm::DeviceGuard on_device(w->device);
+    WCK(on_device.err, "cudaSetDevice");
     WCK(cudaDeviceSynchronize(), "synchronize");
     WCK(cudaMemcpy(params, w->p, sizeof(float) * (size_t)w->nparams, cudaMemcpyDeviceToHost), "params");
     return SIM_OK;
@@ -261,7 +265,8 @@ int wsn_set_normalization(wsn_t w, const float *mean_in, const float *std_in,
         if (!(std_in[d] > 0.0f)) return werr(w, SIM_EINVAL, "std_in must be > 0");
         inv[d] = 1.0f / std_in[d];
     }
-    WCK(cudaSetDevice(w->device), "cudaSetDevice");
+    subadmm::DeviceGuard on_device(w->device);
+    WCK(on_device.err, "cudaSetDevice");
     WCK(cudaMemcpy(w->mean, mean_in, sizeof(float) * D, cudaMemcpyHostToDevice), "mean");
     WCK(cudaMemcpy(w->inv_std, inv.data(), sizeof(float) * D, cudaMemcpyHostToDevice), "std");
     WCK(cudaMemcpy(w->scale, scale_out, sizeof(float) * N, cudaMemcpyHostToDevice), "scale");
@@ -273,7 +278,8 @@ int wsn_get_normalization(wsn_t w, float *mean_in, float *std_in, float *scale_o
     if (!w || !mean_in || !std_in || !scale_out) return SIM_EINVAL;
     const int D = w->sizes[0], N = w->sizes.back();
     std::vector<float> inv(D);
-    WCK(cudaSetDevice(w->device), "cudaSetDevice");
+    subadmm::DeviceGuard on_device(w->device);
+    WCK(on_device.err, "cudaSetDevice");
     WCK(cudaDeviceSynchronize(), "synchronize");
     WCK(cudaMemcpy(mean_in, w->mean, sizeof(float) * D, cudaMemcpyDeviceToHost), "mean");
     WCK(cudaMemcpy(inv.data(), w->inv_std, sizeof(float) * D, cudaMemcpyDeviceToHost), "std");
@@ -286,7 +292,8 @@ int wsn_fit_normalization(wsn_t w, const float *x_dev, long long ldx, const floa
                           int batch, void *stream)
 {
     if (!w || !x_dev || !t_dev || batch < 1 || ldx < w->sizes[0]) return SIM_EINVAL;
-    WCK(cudaSetDevice(w->device), "cudaSetDevice");
+    subadmm::DeviceGuard on_device(w->device);
+    WCK(on_device.err, "cudaSetDevice");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int D = w->sizes[0], N = w->sizes.back();
     wsn::column_stats_kernel<<<D, 256, 0, st>>>(x_dev, ldx, batch, D, w->mean, w->inv_std, 1);
@@ -300,7 +307,8 @@ int wsn_forward(wsn_t w, const float *x_dev, long long ldx, int batch, float *y_
 {
     if (!w || !x_dev || !y_dev || batch < 0 || ldx < w->sizes[0]) return SIM_EINVAL;
     if (batch == 0) return SIM_OK;
-    WCK(cudaSetDevice(w->device), "cudaSetDevice");
+    subadmm::DeviceGuard on_device(w->device);
+    WCK(on_device.err, "cudaSetDevice");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int rc = forward(w, x_dev, ldx, batch, true, st);
     if (rc) return rc;
@@ -315,7 +323,8 @@ int wsn_gradients(wsn_t w, const float *x_dev, long long ldx, const float *t_dev
 {
     if (!w || !x_dev || !t_dev || !mask_dev || !grad_dev || batch < 1 || ldx < w->sizes[0])
         return SIM_EINVAL;
-    WCK(cudaSetDevice(w->device), "cudaSetDevice");
+    subadmm::DeviceGuard on_device(w->device);
+    WCK(on_device.err, "cudaSetDevice");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int rc = forward(w, x_dev, ldx, batch, false, st);
     if (rc) return rc;

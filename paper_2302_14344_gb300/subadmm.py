@@ -32,9 +32,10 @@ EXPORTS = ("sim_default_options", "sim_create", "sim_destroy", "sim_add_subsyste
            "sim_add_interface", "sim_set_generic", "sim_step", "sim_residuals", "sim_get",
            "sim_read_state", "sim_read_state_noalloc", "sim_write_state", "sim_sizes",
            "sim_iteration_stats", "sim_scene_info", "sim_use_graph", "sim_launch_classes",
-           "sim_autotune", "sim_grid_threshold", "sim_grid_staging", "sim_keep_factors", "sim_probe_barrier", "sim_interface_features",
-           "sim_interface_targets", "sim_step_learned",
-           "sim_phase_trace", "sim_sync", "sim_last_error")
+           "sim_autotune", "sim_grid_threshold", "sim_grid_staging", "sim_grid_blocks", "sim_keep_factors",
+           "sim_probe_barrier", "sim_barrier_floor", "sim_interface_features",
+           "sim_interface_targets", "sim_step_learned", "sim_phase_trace", "sim_sync",
+           "sim_last_error")
 
 
 class sim_options(C.Structure):
@@ -98,10 +99,12 @@ def load(build_if_missing: bool = True):
             "sim_grid_threshold": (C.c_int, [VP, C.c_int]),
             "sim_grid_staging": (C.c_int, [VP, C.c_int]),
             "sim_keep_factors": (C.c_int, [VP, C.c_int]),
+            "sim_grid_blocks": (C.c_int, [VP, C.c_int]),
             "sim_interface_features": (C.c_int, [VP, VP]),
             "sim_interface_targets": (C.c_int, [VP, VP, VP, VP]),
             "sim_step_learned": (C.c_int, [VP, VP, C.c_int]),
             "sim_probe_barrier": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_double, PI]),
+            "sim_barrier_floor": (C.c_int, [C.c_int, C.c_int, PD]),
             "sim_phase_trace": (C.c_int, [VP, C.c_int, PL]),
             "sim_sync": (C.c_int, [VP]),
             "sim_last_error": (C.c_char_p, [VP]),
@@ -231,6 +234,10 @@ def sim_grid_staging(h, enable: bool) -> None:
     _check(h, load().sim_grid_staging(h, 1 if enable else 0))
 
 
+def sim_grid_blocks(h, blocks: int) -> None:
+    _check(h, load().sim_grid_blocks(h, blocks))
+
+
 def sim_keep_factors(h, enable: bool) -> None:
     _check(h, load().sim_keep_factors(h, 1 if enable else 0))
 
@@ -241,6 +248,16 @@ def sim_probe_barrier(device: int, blocks: int, expected: int, limit_s: float) -
     if rc < 0:
         raise SimError(rc, "sim_probe_barrier failed")
     return dict(timed_out=bool(out[0]), passed=int(out[1]))
+
+
+def sim_barrier_floor(device: int, iters: int = 20000) -> dict:
+    """Cycles and nanoseconds of one block-barrier round (the block kernel's per-iteration
+    floor)."""
+    out = (C.c_double * 2)()
+    rc = load().sim_barrier_floor(device, iters, out)
+    if rc < 0:
+        raise SimError(rc, "sim_barrier_floor failed")
+    return {"cycles": out[0], "ns": out[1]}
 
 
 def sim_use_graph(h, enable: bool) -> None:
@@ -430,6 +447,9 @@ class Simulation:
 
     def grid_staging(self, enable: bool = True) -> None:
         sim_grid_staging(self.h, enable)
+
+    def grid_blocks(self, blocks: int) -> None:
+        sim_grid_blocks(self.h, blocks)
 
     def keep_factors(self, enable: bool = True) -> None:
         sim_keep_factors(self.h, enable)

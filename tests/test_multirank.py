@@ -24,7 +24,7 @@ def _worker(rank, world, port, out):
     import oracle
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     dist.init_process_group("gloo", rank=rank, world_size=world)
-    p = bench.batch_for_rank(rank, 2, 2e-3)
+    p = bench.make_problem("batched", rank, scenes=2)
     o = oracle.OracleScene(p.scenes[0], p.options)
     o.step()
     first_body = o.bodies_all()[0, 4:7].copy()
@@ -56,6 +56,7 @@ def test_two_ranks_shard_independent_batches():
 def test_reference_arm_runs_on_rank_zero_only(capsys):
     import argparse
     import bench
-    args = argparse.Namespace(robots=1, warmup=3, steps=1, reference_seconds=1.0)
+    args = argparse.Namespace(workload="batched", robots=1, scenes=2, warmup=3, steps=1,
+                              reference_seconds=1.0, reference_scenes=0)
     assert bench.run_reference(args, rank=1, world=2) == 0
     assert capsys.readouterr().out == ""

@@ -258,3 +258,25 @@ def test_same_seed_is_bitwise_deterministic():
     for x, y in zip(a, b):
         assert np.array_equal(x.bodies_all(), y.bodies_all())
         assert np.array_equal(x.lam_all(), y.lam_all())
+
+
+def test_state_and_warm_duals_determine_the_next_step():
+    """Bodies plus each constraint's warm-start lambda and z are the whole state a step
+    starts from: a fresh oracle scene given them (set_body, set_warm) takes the same next
+    step, bit for bit, as the scene that reached them."""
+    p = sg.robots(5, n_robots=1, tol_primal=1e-6, max_iters=1000)
+    sc = p.scenes[0]
+    a = oracle.OracleScene(sc, p.options)
+    for _ in range(30):
+        a.step()
+    b = oracle.OracleScene(sc, p.options)
+    for i, sub in enumerate(sc.subs):
+        for k in range(len(sub.bodies)):
+            b.set_body(i, k, a.body(i, k))
+    for j in range(a.ncon):
+        b.set_warm(j, a.lam(j), a.side(j, "z"))
+    a.step()
+    b.step()
+    assert np.array_equal(a.bodies_all(), b.bodies_all())
+    assert np.array_equal(a.lam_all(), b.lam_all())
+    assert a.residuals()["iters"] == b.residuals()["iters"]
