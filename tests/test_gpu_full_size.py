@@ -4,7 +4,7 @@ library's graph, device and measurement services.
 * FEM slabs of the full beam's size (10 x 10 nodes per plane: n = 1200 and 900 DOF) on the
   grid kernel with a launch small enough that every warp stages many D rows through its two
   shared-memory buffers: FP64 against the oracle (1e-9) and bit-equal to direct reads.
-* The 64-robot batch after landing, stepped 130 steps in the benchmark's launch structure
+* The 64-robot batch after landing, stepped 200 steps in the benchmark's launch structure
   (graph replay, autotuned variants, 50 steps per launch): sampled scenes are loaded into the
   oracle (bodies and warm-start duals) and the next step of both is compared (FP64 to 1e-9;
   the mixed form's error against the FP64 oracle is stated)."""
@@ -86,17 +86,18 @@ def _load_oracle(sim, p, k):
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_full_size_robot_batch_after_landing_sampled(sa, precision, capsys):
-    """The 64-robot workload in the benchmark's launch configuration, 130 steps (the feet
-    land near step 120); then scenes 0, 31 and 63 continue on the oracle from the device's
-    state and the next step of both is compared: FP64 to 1e-9 with iteration counts within
-    one; the mixed form's v-hat error against the FP64 oracle is stated and bounded."""
+    """The 64-robot workload in the benchmark's launch configuration, 200 steps (drops of
+    0.3-0.5 m land between steps 125 and 160); then scenes 0, 31 and 63 continue on the
+    oracle from the device's state and the next step of both is compared: FP64 to 1e-9 with
+    iteration counts within one; the mixed form's v-hat error against the FP64 oracle is
+    stated and bounded."""
     prec = sa.SIM_FP64 if precision == "fp64" else sa.SIM_MIXED
     p = sg.robots(0, n_robots=64, tol_primal=1e-6, max_iters=1000)
     sim = sa.Simulation(p, precision=prec)
     sim.step(1)
     sim.autotune(steps=3)
     sim.use_graph(True)
-    for n in (50, 50, 29):
+    for n in (50, 50, 50, 49):
         sim.step(n)
     orcs = {k: _load_oracle(sim, p, k) for k in (0, 31, 63)}
     sim.step(1)
@@ -115,7 +116,7 @@ def test_full_size_robot_batch_after_landing_sampled(sa, precision, capsys):
             assert r["r_p"] <= 1e-6 or not r["converged"]
             assert err < 1e-3
     # the contact phase: every sampled robot carries its weight through its feet
-    assert max(np.max(np.abs(o.lam_all())) for o in orcs.values()) > 1.0
+    assert min(np.max(np.abs(o.lam_all())) for o in orcs.values()) > 0.5
     with capsys.disabled():
         print(f"\n[64 robots after landing, {precision}] next step from the device state: "
               f"v-hat rel err against the FP64 oracle {worst:.3e}")
