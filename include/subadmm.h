@@ -267,6 +267,19 @@ int sim_probe_barrier(int device, int blocks, int expected, double limit_s, int 
  * allocates (and frees) a small device buffer.  SIM_EINVAL for iters outside 1..1e7. */
 int sim_barrier_floor(int device, int iters, double out[2]);
 
+/* Gram matrices G_j = W_j^T W_j on the tensor cores (tcgen05, split-TF32: FP32-class
+ * accuracy), the kernel that forms the per-step map of each subsystem (D = W^T W and
+ * c = W^T g with W = L^-1 [J^T b], Algorithm 1's factorise step carried to the constraint
+ * space).  This entry runs it standalone on `njobs` matrices, for testing and measurement:
+ * W[j] (device, n[j] rows of ldw[j] floats: W[j][p * ldw[j] + t], t < cols[j]) gives
+ * G[j] (device, cols[j] x cols[j], both triangles, G[j][t * ldg[j] + u]).  Runs `reps` times
+ * on the legacy default stream (the first untimed) and writes the mean time of the others
+ * to *ms_per_run (0 if reps == 1; ms_per_run may be NULL).  Allocates (and frees) its
+ * transposed operand buffers; synchronises the device.  Returns SIM_OK, SIM_EINVAL,
+ * SIM_ENOMEM, SIM_ECUDA, or SIM_ETIMEOUT if a wait of the kernel ran out (1 s). */
+int sim_gram_tc(int device, int njobs, const float *const *W, const int *n, const int *cols,
+                const int *ldw, float *const *G, const int *ldg, int reps, float *ms_per_run);
+
 /* CUDA-graph replay of sim_step (off by default).  When enabled, the first sim_step with a
  * given n_steps captures its launches (one per launch class of scenes, forked across streams
  * and joined back to the simulation's stream) into a graph, and later calls with the same

@@ -361,21 +361,26 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
             const bool got = gram_wait(&acc_full, tph, &abort_flag);
             if (!__all_sync(0xffffffffu, got)) { abort_flag = 1; atomicExch(err, 1); break; }
             gram_fence_after();
+            // a diagonal tile stores its upper triangle and mirrors it (the MMA forms (i, j)
+            // and (j, i) with the split's two correction terms in swapped order, so they may
+            // differ in the last bit); an off-diagonal tile is mirrored whole
             const int r = bi * kGramTile + warp * 32 + lane;
-            const bool mirror = bi != bj;
+            const bool diag = bi == bj;
             for (int cb = 0; cb < kGramTile; cb += 32) {
                 float v[32];
                 gram_tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb, v);
                 const int c0 = bj * kGramTile + cb;
                 if (c0 >= J.rows) continue;
 #pragma unroll
-                for (int k = 0; k < 32; ++k) gram_store(J, r, c0 + k, v[k], mirror);
+                for (int k = 0; k < 32; ++k)
+                    if (!diag || c0 + k >= r) gram_store(J, r, c0 + k, v[k], c0 + k != r);
             }
             gram_fence_before();
             gram_arrive(&acc_empty);
         }
     }
     // all roles done (or stopped): the MMA issuer's last commit marks every MMA complete
+    __syncwarp();
     __syncthreads();
     if (warp == 5 && lane == 0) {
         // parity of the teardown commit: one completion per tile plus the teardown's own

@@ -33,7 +33,7 @@ EXPORTS = ("sim_default_options", "sim_create", "sim_destroy", "sim_add_subsyste
            "sim_read_state", "sim_read_state_noalloc", "sim_write_state", "sim_sizes",
            "sim_iteration_stats", "sim_scene_info", "sim_use_graph", "sim_launch_classes",
            "sim_autotune", "sim_grid_threshold", "sim_grid_staging", "sim_grid_blocks", "sim_keep_factors",
-           "sim_probe_barrier", "sim_barrier_floor", "sim_interface_features",
+           "sim_probe_barrier", "sim_barrier_floor", "sim_gram_tc", "sim_interface_features",
            "sim_interface_targets", "sim_step_learned", "sim_phase_trace", "sim_sync",
            "sim_last_error")
 
@@ -105,6 +105,8 @@ def load(build_if_missing: bool = True):
             "sim_step_learned": (C.c_int, [VP, VP, C.c_int]),
             "sim_probe_barrier": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_double, PI]),
             "sim_barrier_floor": (C.c_int, [C.c_int, C.c_int, PD]),
+            "sim_gram_tc": (C.c_int, [C.c_int, C.c_int, C.POINTER(VP), PI, PI, PI,
+                                      C.POINTER(VP), PI, C.c_int, C.POINTER(C.c_float)]),
             "sim_phase_trace": (C.c_int, [VP, C.c_int, PL]),
             "sim_sync": (C.c_int, [VP]),
             "sim_last_error": (C.c_char_p, [VP]),
@@ -258,6 +260,20 @@ def sim_barrier_floor(device: int, iters: int = 20000) -> dict:
     if rc < 0:
         raise SimError(rc, "sim_barrier_floor failed")
     return {"cycles": out[0], "ns": out[1]}
+
+
+def sim_gram_tc(device: int, W_ptrs, n, cols, ldw, G_ptrs, ldg, reps: int = 1) -> float:
+    """G_j = W_j^T W_j on the tensor cores for device arrays W_j (n_j x ldw_j floats) into
+    G_j (cols_j x ldg_j floats); returns the mean ms per run over reps - 1 timed runs."""
+    k = len(W_ptrs)
+    arr = lambda t, v: (t * k)(*v)
+    ms = C.c_float(0.0)
+    rc = load().sim_gram_tc(device, k, arr(VP, W_ptrs), arr(C.c_int, n), arr(C.c_int, cols),
+                            arr(C.c_int, ldw), arr(VP, G_ptrs), arr(C.c_int, ldg), reps,
+                            C.byref(ms))
+    if rc < 0:
+        raise SimError(rc, "sim_gram_tc failed")
+    return float(ms.value)
 
 
 def sim_use_graph(h, enable: bool) -> None:
