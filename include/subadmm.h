@@ -237,6 +237,15 @@ int sim_grid_threshold(sim_t s, int side_rows);
  * sim_step. */
 int sim_grid_staging(sim_t s, int enable);
 
+/* Tensor cores for the per-step map of large blocks (mixed form, grid kernel scenes; on by
+ * default).  A step that factorises such a block (n >= 128 DOF, m >= 16 side-rows) anew --
+ * every step with sim_keep_factors(0), else the first -- runs as three launches: the grid
+ * kernel up to W = L^-1 [J^T b] (its columns solved in 32-wide chunks over every warp), the
+ * tcgen05 Gram kernel forming D = W^T W and c = W^T g (see sim_gram_tc), and the grid kernel
+ * from the initial duals on.  With 0 the grid kernel forms D and c itself (one warp per
+ * block, FP32 CUDA cores).  Must be called before the first sim_step (SIM_EINVAL after). */
+int sim_tensor_cores(sim_t s, int enable);
+
 /* Grid kernel: run the cooperative launch with `blocks` blocks (at most the resident count;
  * 0, the default, takes every resident block: 2 per SM).  Fewer blocks give each warp more
  * side-rows, subsystems and items; the results do not depend on it.  Takes effect at the

@@ -7,7 +7,7 @@
 #include <vector>
 
 #include "subadmm.h"
-#include "gram.h"
+#include "gram_tc.cuh"
 #include "device_guard.h"
 
 namespace subadmm {
@@ -100,7 +100,7 @@ cudaError_t gram_plan_build(GramPlan &P, std::vector<GramJob> jobs)
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kGramSmem);
 }
 
-cudaError_t gram_plan_run(const GramPlan &P, cudaStream_t st)
+cudaError_t gram_plan_run(const GramPlan &P, cudaStream_t st, int *err)
 {
     if (P.njobs == 0) return cudaSuccess;
     gram_prep_kernel<<<P.prep_blocks, 256, 0, st>>>(P.d_jobs, P.njobs, P.d_prep_prefix, P.hi,
@@ -108,7 +108,8 @@ cudaError_t gram_plan_run(const GramPlan &P, cudaStream_t st)
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     gram_tc_kernel<<<P.grid, kGramThreads, kGramSmem, st>>>(P.map_hi, P.map_lo, P.d_jobs,
-                                                            P.njobs, P.ntiles, P.d_err);
+                                                            P.njobs, P.ntiles,
+                                                            err ? err : P.d_err);
     return cudaGetLastError();
 }
 

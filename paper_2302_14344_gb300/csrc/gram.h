@@ -6,11 +6,39 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <stdint.h>
+
 #include <vector>
 
-#include "gram_tc.cuh"
-
 namespace subadmm {
+
+constexpr int kGramTile = 128;          // M = N of one MMA and one output tile
+constexpr int kGramKChunk = 32;         // FP32 elements of K per stage (128 bytes)
+constexpr int kGramStages = 3;          // shared-memory ring depth
+constexpr int kGramPanelBytes = kGramTile * kGramKChunk * 4;      // 16 KB
+constexpr int kGramStageBytes = 4 * kGramPanelBytes;             // A hi, A lo, B hi, B lo
+constexpr int kGramSmem = kGramStages * kGramStageBytes + 1024;  // + alignment slack
+constexpr int kGramThreads = 192;       // warps 0-3 epilogue, 4 TMA, 5 MMA
+constexpr int kGramAcc = 4;             // accumulators in tensor memory (K chunk kc adds into
+                                        // accumulator kc % 4; the epilogue sums them)
+constexpr unsigned long long kGramWaitNs = 1000000000ull;       // 1 s per wait
+
+// One Gram matrix of the batch.
+struct GramJob {
+    const float *W;   // W[p * ldw + t], p < k (DOF), t < rows (= m + 1 columns, last = g)
+    int ldw;
+    int rows;         // m + 1
+    int k;            // n
+    int row_off;      // first row of this job in the stacked buffer (a multiple of 128)
+    int tile0;        // first upper-triangle tile of this job in the launch's numbering
+    float *D;         // G[t][u] for t, u < m at D[t * ldd + u] (null: not stored)
+    int ldd;
+    int mpad;         // D rows are zero-padded from m to mpad
+    float *c;         // G[t][m] for t < m at c[t] (null: not stored)
+    float *G;         // the whole (m + 1) x (m + 1) matrix at G[t * ldg + u] (null: not stored)
+    int ldg;
+};
+
 
 struct GramPlan {
     int device = -1;
@@ -32,8 +60,9 @@ struct GramPlan {
 // Returns cudaSuccess or the first error.
 cudaError_t gram_plan_build(GramPlan &P, std::vector<GramJob> jobs);
 
-// Enqueues the transpose and the Gram kernel on `st`.
-cudaError_t gram_plan_run(const GramPlan &P, cudaStream_t st);
+// Enqueues the transpose and the Gram kernel on `st`; a wait that runs out raises *err
+// (the plan's own error word when err is null).
+cudaError_t gram_plan_run(const GramPlan &P, cudaStream_t st, int *err = nullptr);
 
 // Reads (and clears) the plan's error word: 1 if a wait of the last runs ran out.
 cudaError_t gram_plan_error(const GramPlan &P, int *out);

@@ -17,10 +17,13 @@
 //                     stages 32-wide K chunks of the tile's row panels (hi and lo of both
 //                     operands, 128-byte swizzled) into a ring of shared-memory stages; an
 //                     MMA warp issues tcgen05.mma kind::tf32 (M = N = 128, K = 8) with the
-//                     accumulator in tensor memory: hi*hi + hi*lo + lo*hi per K step, the
-//                     split-TF32 product, whose error is about 2^-20 relative per term, FP32
-//                     class; four epilogue warps read the accumulator (tcgen05.ld) and store
-//                     D, c and the mirrored tile.
+//                     accumulators in tensor memory: hi*hi + hi*lo + lo*hi per K step, the
+//                     split-TF32 product, whose error is about 2^-21 relative per term.  The
+//                     tensor core's own FP32 accumulation truncates, so the K chunks go round
+//                     robin into four accumulators (all 512 columns of tensor memory), each
+//                     summing a quarter of K at a quarter of the magnitude; four epilogue warps
+//                     read them (tcgen05.ld), add them in FP32, and store D, c and the
+//                     mirrored tile.
 //
 // All waits are bounded: a wait that runs out raises the launch's error word and the roles
 // stop; the kernel then waits (bounded) for its own copies and MMAs and frees its tensor
@@ -31,32 +34,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "gram.h"
+
 namespace subadmm {
-
-constexpr int kGramTile = 128;          // M = N of one MMA and one output tile
-constexpr int kGramKChunk = 32;         // FP32 elements of K per stage (128 bytes)
-constexpr int kGramStages = 3;          // shared-memory ring depth
-constexpr int kGramPanelBytes = kGramTile * kGramKChunk * 4;      // 16 KB
-constexpr int kGramStageBytes = 4 * kGramPanelBytes;             // A hi, A lo, B hi, B lo
-constexpr int kGramSmem = kGramStages * kGramStageBytes + 1024;  // + alignment slack
-constexpr int kGramThreads = 192;       // warps 0-3 epilogue, 4 TMA, 5 MMA
-constexpr unsigned long long kGramWaitNs = 1000000000ull;       // 1 s per wait
-
-// One Gram matrix of the batch.
-struct GramJob {
-    const float *W;   // W[p * ldw + t], p < k (DOF), t < rows (= m + 1 columns, last = g)
-    int ldw;
-    int rows;         // m + 1
-    int k;            // n
-    int row_off;      // first row of this job in the stacked buffer (a multiple of 128)
-    int tile0;        // first upper-triangle tile of this job in the launch's numbering
-    float *D;         // G[t][u] for t, u < m at D[t * ldd + u] (null: not stored)
-    int ldd;
-    int mpad;         // D rows are zero-padded from m to mpad
-    float *c;         // G[t][m] for t < m at c[t] (null: not stored)
-    float *G;         // the whole (m + 1) x (m + 1) matrix at G[t * ldg + u] (null: not stored)
-    int ldg;
-};
 
 __device__ __forceinline__ uint32_t gram_smem_u32(const void *p)
 {
@@ -277,7 +257,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     ::"r"(gram_smem_u32(&tmem_base)), "r"(kGramTile) : "memory");
+                     ::"r"(gram_smem_u32(&tmem_base)), "r"(kGramAcc * kGramTile) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     gram_fence_before();
@@ -336,12 +316,13 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
                     const uint64_t ah = gram_desc(st), al = gram_desc(st + kGramPanelBytes);
                     const uint64_t bh = gram_desc(st + 2 * kGramPanelBytes);
                     const uint64_t bl = gram_desc(st + 3 * kGramPanelBytes);
+                    const uint32_t acc = tmem + (uint32_t)((kc % kGramAcc) * kGramTile);
 #pragma unroll
                     for (int k = 0; k < kGramKChunk / 8; ++k) {
                         const uint64_t dk = (uint64_t)(2 * k);   // 32 bytes of K per step
-                        gram_mma(tmem, ah + dk, bh + dk, (kc > 0 || k > 0) ? 1u : 0u);
-                        gram_mma(tmem, ah + dk, bl + dk, 1u);
-                        gram_mma(tmem, al + dk, bh + dk, 1u);
+                        gram_mma(acc, ah + dk, bh + dk, (kc >= kGramAcc || k > 0) ? 1u : 0u);
+                        gram_mma(acc, ah + dk, bl + dk, 1u);
+                        gram_mma(acc, al + dk, bh + dk, 1u);
                     }
                     gram_commit(&empty[s]);            // the stage is free once these finish
                 }
@@ -366,9 +347,18 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
             // differ in the last bit); an off-diagonal tile is mirrored whole
             const int r = bi * kGramTile + warp * 32 + lane;
             const bool diag = bi == bj;
+            const int nk = (J.k + kGramKChunk - 1) / kGramKChunk;
+            const int nacc = nk < kGramAcc ? nk : kGramAcc;      // accumulators written
             for (int cb = 0; cb < kGramTile; cb += 32) {
                 float v[32];
-                gram_tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb, v);
+                const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb;
+                gram_tmem_ld32(ta, v);
+                for (int a = 1; a < nacc; ++a) {
+                    float w[32];
+                    gram_tmem_ld32(ta + (uint32_t)(a * kGramTile), w);
+#pragma unroll
+                    for (int k = 0; k < 32; ++k) v[k] += w[k];
+                }
                 const int c0 = bj * kGramTile + cb;
                 if (c0 >= J.rows) continue;
 #pragma unroll
@@ -394,7 +384,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
     gram_fence_after();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
-                     ::"r"(tmem), "r"(kGramTile) : "memory");
+                     ::"r"(tmem), "r"(kGramAcc * kGramTile) : "memory");
 }
 
 }  // namespace subadmm

@@ -132,13 +132,17 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 2) grid_step_kernel(StepParam
     unsigned ph = 0;            // parity of the next completion of each stage's barrier
     unsigned pend = 0;          // stages whose issued copy has not been waited for yet
     bool stage_ok = true;       // false after a copy that did not complete in time
-    for (int q = d.tid; q < S.ot_lam - S.ot_x; q += d.nthreads) V.tb[S.ot_x + q] = (T)0;
+    // tc_phase 2 continues the step that a tc_phase 1 launch set up (its per-side-row
+    // constants and status are kept; the Gram kernel formed D and c in between)
+    const int tc_phase = P.tc_phase;
+    if (tc_phase != 2)
+        for (int q = d.tid; q < S.ot_lam - S.ot_x; q += d.nthreads) V.tb[S.ot_x + q] = (T)0;
     scene_tables<T>(P, S, V, d);
     d.sync();
 
     for (int step = 0; step < P.n_steps; ++step) {
         if (lead) {
-            G->status = ST_OK;
+            if (tc_phase != 2) G->status = ST_OK;
             G->tsum = 0.0;
             G->pmax = 0ull;
             G->dmax = 0ull;
@@ -146,15 +150,19 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 2) grid_step_kernel(StepParam
         }
         d.sync();
         PhaseClock pc((P.phase && blockIdx.x == 0) ? P.phase + 8 * sc : nullptr);
-        pc.mark_at(PHASE_ASSEMBLE, scene_setup<T>(P, S, V, &G->status, step, d));
+        if (tc_phase != 2) pc.mark_at(PHASE_ASSEMBLE, scene_setup<T>(P, S, V, &G->status, step, d));
         pc.mark(PHASE_FACTOR);
         const int status0 = vload(&G->status);
         if (status0 != ST_OK) {
-            if (lead) {
+            if (lead && tc_phase != 2) {
                 double *o = P.res + 6 * sc;
                 o[0] = o[1] = o[2] = __longlong_as_double(0x7ff8000000000000LL);
                 o[3] = 0.0; o[4] = 0.0; o[5] = (double)status0;
             }
+            d.sync();
+            continue;
+        }
+        if (tc_phase == 1) {
             d.sync();
             continue;
         }

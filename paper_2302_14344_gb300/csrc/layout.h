@@ -82,6 +82,8 @@ struct SubDesc {
     int ot_s;              // T region: solve vector of the mixed recovery (n)
     int ot_D, ot_c;        // iteration region: D (m rows of mpad, ldd apart), c (m)
     int v_off;             // global offset of v-hat
+    int tc;                // grid scenes, mixed form: when refactorised, W's columns are solved
+                           // by all warps and D, c formed by the tensor-core Gram kernel
 };
 
 struct ConDesc {
@@ -131,6 +133,8 @@ struct StepParams {
     const int *ipool;      // integer constant data (sparse K of linear blocks, profiles)
     int *subflag;          // per subsystem: bit 0 its kept factor is valid, bit 1 it is FP64
     int keep_factors;      // 0: refactor constant blocks every step too (Algorithm 1 literally)
+    int tc_phase;          // grid kernel: 0 the whole step; 1 up to the map's W (the Gram
+                           // kernel forms D, c of the tc subsystems next); 2 from the duals on
     double *vhat;          // per DOF
     double *lam;           // per row: lambda of the last step (warm start state)
     const double *lam0;    // per row: learned initial lambda of this step (NULL: not learned)

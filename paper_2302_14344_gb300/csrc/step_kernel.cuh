@@ -334,10 +334,13 @@ __device__ __forceinline__ SubEnv sub_env(const StepParams &P, const SubDesc &u)
 
 // A constant K_i whose factor from an earlier step is still held: in the workspace (it
 // outlives the launch) or in shared memory from an earlier step of this launch.  With
-// keep_factors 0 every step refactors (the same matrix; results agree to rounding).
+// keep_factors 0 every step refactors (the same matrix; results agree to rounding).  A
+// tc_phase 1 launch (the host issues it only for steps that refactor) refactors every tc
+// subsystem.
 __device__ __forceinline__ bool factor_kept(const StepParams &P, const SceneDesc &S,
                                             const SubDesc &u, int gsub, int step)
 {
+    if (P.tc_phase == 1 && u.tc) return false;
     return P.keep_factors && u.cst && (step > 0 || S.sub_global) && (P.subflag[gsub] & 1);
 }
 
@@ -766,6 +769,8 @@ __device__ long long scene_setup(const StepParams &P, const SceneDesc &S, const 
             W[q] = t < m ? (T)J[t * n + p] : t == m ? (T)b[p] : (T)0;
         }
         __syncwarp();
+        if (P.tc_phase == 1 && u.tc) continue;     // solved by column chunks below; D, c by
+                                                   // the tensor-core Gram kernel
         env_forward_cols<T>(LT, W, n, ldw, m + 1, e.env);
         __syncwarp();
         form_D<T>(W, n, m, mp, u.ldd, ldw, e.jlo, D);
@@ -773,6 +778,31 @@ __device__ long long scene_setup(const StepParams &P, const SceneDesc &S, const 
         __syncwarp();
     }
     d.sync();
+    if (P.tc_phase == 1) {
+        // W <- L^-1 W for the refactorised tc subsystems, in chunks of 32 columns (a lane per
+        // column) spread over every warp of the grid
+        int total = 0;
+        for (int i = 0; i < S.nsub; ++i) {
+            const SubDesc &u = P.subs[S.sub0 + i];
+            if (u.tc) total += (u.m + 1 + 31) / 32;
+        }
+        for (int w = d.warp; w < total; w += d.nwarps) {
+            int k = w, i = 0;
+            for (; i < S.nsub; ++i) {
+                const SubDesc &u = P.subs[S.sub0 + i];
+                if (!u.tc) continue;
+                const int ch = (u.m + 1 + 31) / 32;
+                if (k < ch) break;
+                k -= ch;
+            }
+            const SubDesc &u = P.subs[S.sub0 + i];
+            const int ldw = (u.m + 1 + 3) / 4 * 4, c0 = 32 * k;
+            const int cols = u.m + 1 - c0 < 32 ? u.m + 1 - c0 : 32;
+            const SubEnv e = sub_env(P, u);
+            env_forward_cols<T>(stb + u.ot_L, stb + u.ot_W + c0, u.n, ldw, cols, e.env);
+        }
+        d.sync();
+    }
     // per-step z-step constants: 1/s, soft gain k/(1 + s alpha k), alpha, mu (per row);
     // beta and 1/beta per side-row
     T *INVS = tb + S.ot_invs, *KF = tb + S.ot_kf, *AL = tb + S.ot_al, *MU = tb + S.ot_mu;

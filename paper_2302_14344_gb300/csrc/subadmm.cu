@@ -18,6 +18,7 @@
 #include "features.cuh"
 #include "warmstart.h"
 #include "device_guard.h"
+#include "gram.h"
 
 namespace {
 
@@ -105,6 +106,9 @@ struct sim_s {
     int grid_staging = 1;          // grid kernel: stage D rows in shared memory by bulk copies
     int grid_blocks = 0;           // grid kernel: blocks of the cooperative launch (0: all resident)
     int keep_factors = 1;          // keep the factors of constant blocks across steps
+    int tensor_cores = 1;          // grid scenes, mixed form: D, c by the tcgen05 Gram kernel
+    std::vector<subadmm::GramPlan> gram;   // per scene: Gram jobs of its tc subsystems
+    std::vector<char> grid_factored;       // per scene: its tc subsystems hold kept factors
     // graph replay of sim_step
     bool use_graph = false;
     int graph_steps = 0;
@@ -246,6 +250,9 @@ void free_device(sim_t s)
     if (s->ev_fork) cudaEventDestroy(s->ev_fork);
     s->ev_fork = nullptr;
     drop_graphs(s);
+    for (auto &g : s->gram) subadmm::gram_plan_free(g);
+    s->gram.clear();
+    s->grid_factored.clear();
     if (s->graph_stream) cudaStreamDestroy(s->graph_stream);
     s->graph_stream = nullptr;
     s->d_nodes = nullptr; s->d_ipool = nullptr; s->d_subflag = nullptr;
@@ -684,6 +691,13 @@ int finalize(sim_t s)
         S.g_scene = -1;
         const bool grid_scene = s->classes[sc_class[sc]].grid;
         if (grid_scene) {
+            // large blocks of the mixed form have their map formed on the tensor cores
+            // whenever they are refactorised
+            for (int i = 0; i < S.nsub; ++i) {
+                SubDesc &u = s->sdesc[S.sub0 + i];
+                u.tc = (s->tensor_cores && s->opt.precision == SIM_MIXED && u.n >= 128 &&
+                        u.m >= 16) ? 1 : 0;
+            }
             // everything in the workspace: the per-subsystem arrays, then the scene arrays
             S.sub_global = 1; S.hot_global = 1;
             S.g_base = work_bytes;
@@ -1123,6 +1137,7 @@ StepParams step_params(const sim_t s, int n_steps)
     P.scene_ids = s->d_scene_ids;
     P.grid = s->d_grid;
     P.lam0 = nullptr;
+    P.tc_phase = 0;
     P.ref10 = s->d_ref10;
     P.learn_skip = s->d_learn_skip;
     return P;
@@ -1148,6 +1163,40 @@ KernFn grid_kernel_for(bool mixed, int split)
 
 // One cooperative launch per scene of a grid class, in turn on `st`, each after zeroing the
 // grid scratch; as many blocks as fit on the GPU at once.
+// The Gram plan of grid scene sc (its tc subsystems' W -> D, c), built on first use.
+int gram_plan_of(sim_t s, int sc)
+{
+    if ((int)s->gram.size() < s->nscenes) {
+        s->gram.resize(s->nscenes);
+        s->grid_factored.assign(s->nscenes, 0);
+    }
+    subadmm::GramPlan &G = s->gram[sc];
+    if (G.device >= 0) return SIM_OK;
+    const SceneDesc &S = s->scenes[sc];
+    std::vector<subadmm::GramJob> jobs;
+    unsigned char *tbase = reinterpret_cast<unsigned char *>(s->d_work) + S.g_base + S.g_tbase;
+    float *stb = reinterpret_cast<float *>(tbase);
+    for (int i = 0; i < S.nsub; ++i) {
+        const SubDesc &u = s->sdesc[S.sub0 + i];
+        if (!u.tc) continue;
+        subadmm::GramJob J{};
+        J.W = stb + u.ot_W;
+        J.ldw = (u.m + 1 + 3) / 4 * 4;
+        J.rows = u.m + 1;
+        J.k = u.n;
+        J.D = stb + u.ot_D;
+        J.ldd = u.ldd;
+        J.mpad = u.mpad;
+        J.c = stb + u.ot_c;
+        jobs.push_back(J);
+    }
+    cudaError_t e = subadmm::gram_plan_build(G, jobs);
+    if (e == cudaSuccess && jobs.empty()) e = cudaGetDevice(&G.device);
+    if (e == cudaErrorMemoryAllocation) return fail(s, SIM_ENOMEM, "Gram plan allocation");
+    CK(e, "Gram plan");
+    return SIM_OK;
+}
+
 int launch_grid_class(sim_t s, LaunchClass &c, StepParams P, cudaStream_t st, int split)
 {
     KernFn kf = grid_kernel_for(s->opt.precision == SIM_MIXED, split);
@@ -1180,13 +1229,38 @@ int launch_grid_class(sim_t s, LaunchClass &c, StepParams P, cudaStream_t st, in
             cudaGetLastError();
         }
         if (nst == 0) stage = 0;
-        CK(cudaMemsetAsync(s->d_grid, 0, sizeof(GridScratch), st), "grid scratch");
         P.scene_ids = s->d_scene_ids + c.ids_off + (int)i;
         P.nscenes = 1;
         P.grid_stage = stage;
         P.grid_nstage = nst;
         c.max_smem = std::max(c.max_smem, (int)dyn);
-        void *args[] = {&P};
+        const int sc = c.scenes[i];
+        int rc = gram_plan_of(s, sc);
+        if (rc) return rc;
+        // steps that refactorise tc subsystems: setup launch, Gram kernel, iteration launch
+        int left = P.n_steps;
+        while (left > 0 && s->gram[sc].njobs > 0 && (!s->keep_factors || !s->grid_factored[sc])) {
+            StepParams Q = P;
+            Q.n_steps = 1;
+            Q.tc_phase = 1;
+            void *a1[] = {&Q};
+            CK(cudaMemsetAsync(s->d_grid, 0, sizeof(GridScratch), st), "grid scratch");
+            CK(cudaLaunchCooperativeKernel((const void *)kf, dim3(blocks), dim3(SUBADMM_THREADS), a1, dyn, st),
+               "grid kernel launch (setup)");
+            CK(subadmm::gram_plan_run(s->gram[sc], st, &s->d_grid->err), "Gram kernel launch");
+            Q.tc_phase = 2;
+            // the barrier counter restarts; the step's status and error word carry over
+            CK(cudaMemsetAsync(s->d_grid, 0, 2 * sizeof(unsigned), st), "grid barrier");
+            CK(cudaLaunchCooperativeKernel((const void *)kf, dim3(blocks), dim3(SUBADMM_THREADS), a1, dyn, st),
+               "grid kernel launch (iterations)");
+            if (s->keep_factors) s->grid_factored[sc] = 1;
+            --left;
+        }
+        if (left == 0) continue;
+        StepParams R = P;
+        R.n_steps = left;
+        CK(cudaMemsetAsync(s->d_grid, 0, sizeof(GridScratch), st), "grid scratch");
+        void *args[] = {&R};
         CK(cudaLaunchCooperativeKernel((const void *)kf, dim3(blocks), dim3(SUBADMM_THREADS), args, dyn, st),
            "grid kernel launch");
     }
@@ -1384,6 +1458,7 @@ int sim_autotune(sim_t s, int steps, int max_classes, long long *out)
     cudaEventCreate(&e1);
     std::vector<double> best_ns(s->classes.size(), 0.0);
     cudaError_t err = copy_all(true);
+    const std::vector<char> grid_factored = s->grid_factored;   // restored with the snapshot
     for (size_t k = 0; k < s->classes.size() && err == cudaSuccess; ++k) {
         LaunchClass &c = s->classes[k];
         P.scene_ids = s->d_scene_ids + c.ids_off;
@@ -1438,6 +1513,7 @@ int sim_autotune(sim_t s, int steps, int max_classes, long long *out)
     }
     if (err == cudaSuccess) err = copy_all(false);
     if (err == cudaSuccess) err = cudaStreamSynchronize(s->stream);
+    s->grid_factored = grid_factored;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(snap);
@@ -1598,6 +1674,14 @@ int sim_grid_blocks(sim_t s, int blocks)
     if (!s) return SIM_EINVAL;
     if (blocks < 0) return fail(s, SIM_EINVAL, "blocks must be >= 0");
     s->grid_blocks = blocks;
+    return SIM_OK;
+}
+
+int sim_tensor_cores(sim_t s, int enable)
+{
+    if (!s) return SIM_EINVAL;
+    if (s->finalized) return fail(s, SIM_EINVAL, "the layout is fixed after the first sim_step");
+    s->tensor_cores = enable ? 1 : 0;
     return SIM_OK;
 }
 

@@ -32,7 +32,7 @@ EXPORTS = ("sim_default_options", "sim_create", "sim_destroy", "sim_add_subsyste
            "sim_add_interface", "sim_set_generic", "sim_step", "sim_residuals", "sim_get",
            "sim_read_state", "sim_read_state_noalloc", "sim_write_state", "sim_sizes",
            "sim_iteration_stats", "sim_scene_info", "sim_use_graph", "sim_launch_classes",
-           "sim_autotune", "sim_grid_threshold", "sim_grid_staging", "sim_grid_blocks", "sim_keep_factors",
+           "sim_autotune", "sim_grid_threshold", "sim_grid_staging", "sim_grid_blocks", "sim_tensor_cores", "sim_keep_factors",
            "sim_probe_barrier", "sim_barrier_floor", "sim_gram_tc", "sim_interface_features",
            "sim_interface_targets", "sim_step_learned", "sim_phase_trace", "sim_sync",
            "sim_last_error")
@@ -100,6 +100,7 @@ def load(build_if_missing: bool = True):
             "sim_grid_staging": (C.c_int, [VP, C.c_int]),
             "sim_keep_factors": (C.c_int, [VP, C.c_int]),
             "sim_grid_blocks": (C.c_int, [VP, C.c_int]),
+            "sim_tensor_cores": (C.c_int, [VP, C.c_int]),
             "sim_interface_features": (C.c_int, [VP, VP]),
             "sim_interface_targets": (C.c_int, [VP, VP, VP, VP]),
             "sim_step_learned": (C.c_int, [VP, VP, C.c_int]),
@@ -238,6 +239,10 @@ def sim_grid_staging(h, enable: bool) -> None:
 
 def sim_grid_blocks(h, blocks: int) -> None:
     _check(h, load().sim_grid_blocks(h, blocks))
+
+
+def sim_tensor_cores(h, enable: bool) -> None:
+    _check(h, load().sim_tensor_cores(h, 1 if enable else 0))
 
 
 def sim_keep_factors(h, enable: bool) -> None:
@@ -466,6 +471,9 @@ class Simulation:
 
     def grid_blocks(self, blocks: int) -> None:
         sim_grid_blocks(self.h, blocks)
+
+    def tensor_cores(self, enable: bool = True) -> None:
+        sim_tensor_cores(self.h, enable)
 
     def keep_factors(self, enable: bool = True) -> None:
         sim_keep_factors(self.h, enable)
