@@ -136,6 +136,57 @@ def algorithmic_work(problem):
     return out
 
 
+def sub_sizes(scene):
+    """(n_i, m_i) of every subsystem of a scene: DOF and side-rows (rows of J_ci)."""
+    n = [s.n for s in scene.subs]
+    m = [0] * len(n)
+    for itf in scene.ifs:
+        if hasattr(itf, "J"):
+            for s in itf.subs:
+                m[s] += itf.rows
+            continue
+        rows = {1: 3, 2: 5, 3: 1, 4: 3}[itf.kind]
+        sides = {itf.a[0]} | ({itf.b[0]} if itf.b is not None else set())
+        for s in sides:
+            m[s] += rows
+    return list(zip(n, m))
+
+
+def gram_roofline(ctx, scene, reps: int = 20) -> dict:
+    """The tcgen05 Gram kernel on the shapes of a scene's large blocks (W: n x (m + 1), the
+    map's right-hand sides), timed standalone with CUDA events over ``reps`` runs.  Algorithmic
+    work: the symmetric product, n (m + 1)(m + 2) flops per block; executed: three TF32 MMAs
+    per product (split-TF32) over the padded upper-triangle tiles."""
+    import torch
+    jobs = [(n, m + 1) for n, m in sub_sizes(scene) if n >= 128 and m >= 16]
+    if not jobs:
+        return None
+    g = torch.Generator(device="cuda").manual_seed(0)
+    Ws = [torch.randn(n, (c + 3) // 4 * 4, device=ctx.dev, generator=g) for n, c in jobs]
+    Gs = [torch.empty(c, c, device=ctx.dev) for _, c in jobs]
+    ms = ctx.subadmm.sim_gram_tc(ctx.local, [w.data_ptr() for w in Ws], [n for n, _ in jobs],
+                                 [c for _, c in jobs], [w.shape[1] for w in Ws],
+                                 [x.data_ptr() for x in Gs], [c for _, c in jobs], reps=reps)
+    alg = float(sum(n * c * (c + 1) for n, c in jobs))
+    tiles = sum(((c + 127) // 128) * ((c + 127) // 128 + 1) // 2 for _, c in jobs)
+    kpad = {n: (n + 31) // 32 * 32 for n, _ in jobs}
+    exe = float(sum(3 * 2 * kpad[n] * 128 * 128 * (((c + 127) // 128) * ((c + 127) // 128 + 1) // 2)
+                    for n, c in jobs))
+    bf16 = measured_peaks().get("bf16_tflops")
+    tf32 = (bf16 or 1900.0) / 2.0
+    ach = alg / (ms / 1e3) / 1e12
+    return {"bound": "tensor", "achieved": ach, "peak": tf32 / 3.0, "unit": "TFLOP/s",
+            "frac": ach / (tf32 / 3.0), "traffic": None,
+            "mma_tflops": exe / (ms / 1e3) / 1e12, "tf32_peak": tf32,
+            "mma_frac": exe / (ms / 1e3) / 1e12 / tf32, "ms_per_launch": ms,
+            "blocks": len(jobs), "tiles": tiles,
+            "note": f"tcgen05 Gram kernel alone on the scene's {len(jobs)} blocks of >= 128 DOF "
+                    f"(random W of their shapes), CUDA events over {reps - 1} launches; achieved = "
+                    f"algorithmic flops n (m+1)(m+2) per block / time; peak = TF32 (measured bf16 "
+                    f"{'burst' if bf16 else 'fallback'} x 1/2, the nominal ratio) / 3 (split-TF32 "
+                    f"issues three MMAs per product); mma_* count every issued MMA flop"}
+
+
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
 
@@ -606,6 +657,8 @@ def sub_fem_beam(ctx, args, threads: int) -> dict:
     f = time_form(ctx, p, sa.SIM_FP64, K, args.warmup, 0, 50, autotune=True, graph=False)
     rf = time_form(ctx, p, sa.SIM_FP64, min(K, 5), 1, 0, 1, autotune=False, graph=False,
                    keep_factors=False)
+    rm = time_form(ctx, p, sa.SIM_MIXED, K, args.warmup, 0, 1, autotune=False, graph=False,
+                   keep_factors=False)
     d_bytes = float(sum(w[2] for w in work)) * 4
     hbm = measured_peaks().get("hbm_gbs")
     st = r["stats"]
@@ -621,6 +674,13 @@ def sub_fem_beam(ctx, args, threads: int) -> dict:
                "steps": len(rf["launch_ms"]), "iterations": iter_summary(rf["stats"]),
                "note": "every block refactorised every step (sim_keep_factors(0)), one launch "
                        "per step, L2 flushed before each"},
+           "mixed_refactor_every_step": {
+               "value": len(rm["launch_ms"]) / (rm["t_ms"] / 1e3), "unit": "steps/s",
+               "steps": len(rm["launch_ms"]), "iterations": iter_summary(rm["stats"]),
+               "note": "every block refactorised every step, as Algorithm 1 states it: per step "
+                       "the grid kernel up to W = L^-1 [J^T b], the tcgen05 Gram kernel for "
+                       "D and c, the grid kernel's iterations; L2 flushed before each step"},
+           "gram_tensor_roofline": gram_roofline(ctx, p.scenes[0]),
            "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm or 6800.0, "unit": "GB/s",
                         "frac": gbs / (hbm or 6800.0),
                         "traffic": recorded_traffic_fem(st["total_iters"] / launches),
@@ -629,7 +689,7 @@ def sub_fem_beam(ctx, args, threads: int) -> dict:
                                 f"(setup and exit included: a lower bound on the stream rate); "
                                 f"peak = {'measured copy bandwidth' if hbm else 'fallback'}"}}
     out["chosen_over_plain"] = out["value"] / out["plain_fp64"]["value"]
-    for x in (r, f, rf):
+    for x in (r, f, rf, rm):
         x["sim"].close()
     if not args.no_cpu_baseline:
         fr = oracle_fem_rate(threads)

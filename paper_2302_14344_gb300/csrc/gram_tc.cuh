@@ -238,7 +238,8 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
                const GramJob *jobs, int njobs, int ntiles, int *err)
 {
     extern __shared__ unsigned char gram_raw[];
-    __shared__ __align__(8) uint64_t full[kGramStages], empty[kGramStages], acc_full, acc_empty;
+    __shared__ __align__(8) uint64_t full[kGramStages], empty[kGramStages], acc_full, acc_empty,
+        mma_done;
     __shared__ uint32_t tmem_base;
     __shared__ volatile int abort_flag;
     unsigned char *smem = reinterpret_cast<unsigned char *>(
@@ -252,6 +253,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
         }
         gram_mbar_init(&acc_full, 1);
         gram_mbar_init(&acc_empty, 128);
+        gram_mbar_init(&mma_done, 1);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -329,8 +331,10 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
                 if (!ok) { abort_flag = 1; atomicExch(err, 1); break; }
                 gram_commit(&acc_full);                // the tile's accumulator is complete
             }
-            // teardown: wait for every MMA issued so far (bounded)
-            gram_commit(&acc_full);
+            // teardown: a barrier of its own marks every MMA issued so far complete (on
+            // acc_full it could complete a second phase right after the last tile's, which
+            // an epilogue warp still polling that tile's parity might then never see)
+            gram_commit(&mma_done);
         }
     } else {
         // ---- epilogue (warps 0-3): accumulator -> D, c (row r = the thread's TMEM lane)
@@ -373,11 +377,8 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
     __syncwarp();
     __syncthreads();
     if (warp == 5 && lane == 0) {
-        // parity of the teardown commit: one completion per tile plus the teardown's own
-        unsigned n = 0;
-        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) ++n;
         volatile int never = 0;
-        gram_wait(&acc_full, n & 1u, &never);
+        gram_wait(&mma_done, 0u, &never);
     }
     gram_fence_before();
     __syncthreads();

@@ -66,3 +66,13 @@ def test_gram_repeated_runs_agree(sa):
     (G1,), (R,), ms = _run(sa, [(1000, 701, 704)], seed=5, reps=3)
     (G2,), _, _ = _run(sa, [(1000, 701, 704)], seed=5, reps=1)
     assert np.array_equal(G1, G2) and ms > 0.0
+
+
+def test_gram_many_tiles_per_block(sa):
+    """More tiles than blocks (the launch has one block per SM): each block runs several tiles
+    through its accumulators, nine at most here (64 jobs of the FEM beam's slab shape)."""
+    shapes = [(1000, 701, 704)] * 20 + [(1200, 691, 692)] * 44
+    Gs, Rs, _ = _run(sa, shapes, seed=11)
+    for G, R in zip(Gs, Rs):
+        assert np.all(np.isfinite(G))
+        assert _err(G, R) < 1e-5
