@@ -747,6 +747,10 @@ def main():
     ap.add_argument("--no-compare", action="store_true",
                     help="skip timing the plain FP64 form next to the chosen one")
     ap.add_argument("--no-sub", action="store_true", help="headline workload only")
+    ap.add_argument("--subs", default="robots,fem_beam,chain",
+                    help="comma-separated sub-results to run (robots, fem_beam, chain)")
+    ap.add_argument("--sub-only", action="store_true",
+                    help="skip the headline workload's GPU timing (sub-results only)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -822,8 +826,9 @@ def main():
         jobs = {"robots_after_landing": lambda: sub_robots(ctx, args, threads),
                 "fem_beam": lambda: sub_fem_beam(ctx, args, threads),
                 "chain_fixed_100_iterations": lambda: sub_chain(ctx, args)}
+        wanted = [w.strip() for w in args.subs.split(",") if w.strip()]
         for name, fn in jobs.items():
-            if name.startswith(args.workload):
+            if name.startswith(args.workload) or not any(name.startswith(w) for w in wanted):
                 continue
             try:
                 subs[name] = fn()

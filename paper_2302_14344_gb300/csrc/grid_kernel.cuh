@@ -164,6 +164,7 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 2) grid_step_kernel(StepParam
         }
         if (tc_phase == 1) {
             d.sync();
+            pc.flush(0, 0);         // the setup's cycles; the iteration launch counts the step
             continue;
         }
         // initial z, u = -lambda; a learned start is checked after 10 iterations against the

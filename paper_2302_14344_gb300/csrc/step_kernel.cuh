@@ -142,11 +142,11 @@ struct PhaseClock {
             t = when;
         }
     }
-    __device__ __forceinline__ void flush(int iters)
+    __device__ __forceinline__ void flush(int iters, int steps = 1)
     {
         if (out) {
             a[PHASE_ITERS] = iters;
-            a[PHASE_STEPS] = 1;
+            a[PHASE_STEPS] = steps;
 #pragma unroll
             for (int q = 0; q < 8; ++q) out[q] += a[q];
         }
