@@ -583,6 +583,22 @@ def sub_robots(ctx, args, threads: int) -> dict:
                                     recorded_traffic(50) if K % 50 == 0 else None),
            "launch_classes": r["classes"]}
     out["chosen_over_plain"] = out["value"] / out["plain_fp64"]["value"]
+    # the paper's full-system ADMM comparator (Sec. IV-B, FADMM): each robot merged into one
+    # subsystem, the same solver and segment
+    import scenegen as sg
+    pm = sg.merged(p)
+    fm = time_form(ctx, pm, sa.SIM_MIXED, K, args.warmup, wl["preroll"], 50)
+    ff = time_form(ctx, pm, sa.SIM_FP64, K, args.warmup, wl["preroll"], 50)
+    out["full_system_admm"] = {
+        "value": K / (fm["t_ms"] / 1e3), "unit": "steps/s", "form": "mixed",
+        "iterations": iter_summary(fm["stats"]),
+        "plain_fp64": {"value": K / (ff["t_ms"] / 1e3), "unit": "steps/s",
+                       "iterations": iter_summary(ff["stats"])},
+        "subsystem_over_full": out["value"] / (K / (fm["t_ms"] / 1e3)),
+        "note": "each robot merged into one subsystem of 78 DOF (every constraint its own "
+                "z-variable, one factorisation per robot and step), same kernels and segment"}
+    fm["sim"].close()
+    ff["sim"].close()
     # cycles per iteration (phase tracer, a separate short run) against the barrier floor
     sim = r["sim"]
     sim.use_graph(False)

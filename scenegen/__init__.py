@@ -828,3 +828,46 @@ def problem_sizes(p: Problem) -> dict:
             side_rows += r * ns
     return dict(scenes=len(p.scenes), subsystems=n_sub, dof=dof, interfaces=n_if, rows=rows,
                 side_rows=side_rows)
+
+
+def merged(problem: Problem) -> Problem:
+    """The same scenes with every scene's subsystems merged into one: the full-system ADMM
+    that the paper compares against (Sec. IV-B, "FADMM": one factorisation of the whole
+    system per step, every constraint its own z-variable), run by the same solver.  Rigid
+    scenes become one rigid subsystem (bodies concatenated), generic scenes one
+    block-diagonal block; interfaces keep their rows, re-addressed to the merged subsystem.
+    Scenes that mix kinds (or hold linear blocks) are rejected."""
+    scenes = []
+    for sc in problem.scenes:
+        kinds = {type(s) for s in sc.subs}
+        if kinds == {RigidSub}:
+            off = np.cumsum([0] + [len(s.bodies) for s in sc.subs])
+            sub = RigidSub([b for s in sc.subs for b in s.bodies])
+            ifs = []
+            for itf in sc.ifs:
+                if not isinstance(itf, JointIf):
+                    raise ValueError("explicit rows on rigid subsystems are not merged")
+                a = (0, int(off[itf.a[0]] + itf.a[1]))
+                b = None if itf.b is None else (0, int(off[itf.b[0]] + itf.b[1]))
+                ifs.append(JointIf(**{**itf.__dict__, "a": a, "b": b}))
+            scenes.append(Scene([sub], ifs))
+        elif kinds == {GenericSub}:
+            sizes = [s.n for s in sc.subs]
+            off = np.cumsum([0] + sizes)
+            N = int(off[-1])
+            A = np.zeros((N, N))
+            b = np.zeros(N)
+            for s, o in zip(sc.subs, off):
+                A[o:o + s.n, o:o + s.n] = s.A
+                b[o:o + s.n] = s.b
+            ifs = []
+            for itf in sc.ifs:
+                J = np.zeros((itf.rows, N))
+                for s, Js in zip(itf.subs, itf.J):
+                    J[:, off[s]:off[s] + sizes[s]] += np.asarray(Js)
+                ifs.append(RowsIf(itf.type, [0], [J], np.asarray(itf.e).copy(), itf.k,
+                                  itf.alpha, itf.mu))
+            scenes.append(Scene([GenericSub(A, b)], ifs))
+        else:
+            raise ValueError("only all-rigid or all-generic scenes are merged")
+    return Problem(scenes, problem.options, name=problem.name + "_merged")

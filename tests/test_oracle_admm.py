@@ -222,3 +222,33 @@ def test_planar_contact_matches_enumeration(seed):
     assert sols, "the enumeration always has a solution here"
     err = min(np.max(np.abs(v - s)) / max(np.max(np.abs(s)), 1e-12) for s in sols)
     assert err < 1e-8, (v, sols)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_full_system_admm_converges_to_the_same_kkt_solve(seed):
+    """The full-system ADMM comparator (Sec. IV-B, FADMM) is the same iteration on the scene
+    merged into one subsystem: its fixed point is the same KKT solution as the split
+    scene's, and its one block is the block-diagonal A of the full system."""
+    rng = np.random.default_rng(40 + seed)
+    sc = sg.generic_scene(rng, n_sub=3 + seed, n_range=(6, 10), types=(sg.EQUALITY,), extra=2)
+    A, b, J, e = _full_system(sc)
+    m, n = J.shape
+    KKT = np.block([[A, -J.T], [J, np.zeros((m, m))]])
+    v_ref = np.linalg.solve(KKT, np.concatenate([b, -e]))[:n]
+    p = sg.Problem([sc], sg.Options(gravity=(0, 0, 0), warm="cold", tol_primal=1e-13,
+                                    max_iters=200000))
+    q = sg.merged(p)
+    assert len(q.scenes[0].subs) == 1 and np.array_equal(q.scenes[0].subs[0].A, A)
+    o = oracle.run(q)[0]
+    assert o.residuals()["converged"]
+    assert np.max(np.abs(o.vhat_all() - v_ref)) / np.max(np.abs(v_ref)) < 1e-9
+
+
+def test_merged_rigid_chain_matches_the_split_chain():
+    """A bilateral rigid chain merged into one subsystem steps to the same state as the
+    chain split into four (both converged tightly: the same KKT solution per step)."""
+    p = sg.chain(0, tol_primal=1e-12, max_iters=200000, rho=1e3)
+    a = oracle.run(p, steps=3)[0]
+    b = oracle.run(sg.merged(p), steps=3)[0]
+    assert len(sg.merged(p).scenes[0].subs) == 1
+    assert np.max(np.abs(a.bodies_all()[:, 4:] - b.bodies_all()[:, 4:])) < 1e-7
