@@ -78,6 +78,7 @@ def lib(openmp: bool = False):
                 "orc_set_body": (None, [VP, C.c_int, C.c_int, PD]),
                 "orc_set_generic": (None, [VP, C.c_int, PD, PD]),
                 "orc_set_warm": (None, [VP, C.c_int, PD, PD]),
+                "orc_set_beta_scale": (None, [VP, C.c_int, D]),
                 "orc_residuals": (None, [VP, PD]),
                 "orc_chol_solve": (C.c_int, [C.c_int, PD, PD, PD]),
                 "orc_project": (None, [C.c_int, C.c_int, C.c_int, PD, PD, PD, D, D, D, PD]),
@@ -266,6 +267,10 @@ class OracleScene:
     def set_body(self, i, k, rec):
         rec = _f64(rec)
         self.L.orc_set_body(self.h, i, k, _p(rec))
+
+    def set_beta_scale(self, i, scale: float):
+        """beta_i = scale x (trace rule or rho) from the next step on."""
+        self.L.orc_set_beta_scale(self.h, i, float(scale))
 
     def set_warm(self, j, lam, z):
         """Constraint j's warm-start state (lambda per row, z per side and row)."""

@@ -10,7 +10,8 @@
  * What it computes, in the paper's order (Algorithm 1), for one scene:
  *   construct A_i, b_i                         (Eq. ddyn -> Eq. sdyn; rigid bodies below)
  *   construct e_j, J_j                         (Sec. II-A: soft, hard, contact rows)
- *   beta_i = Tr(A_i) / Tr(J_ci^T J_ci)         (Sec. III-D), or a fixed rho
+ *   beta_i = Tr(A_i) / Tr(J_ci^T J_ci)         (Sec. III-D), or a fixed rho, times a
+ *                                              per-subsystem scale (input, default 1)
  *   factorise K_i = A_i + beta_i J_ci^T J_ci   (plain Cholesky, no pivoting)
  *   loop l = 0 .. l_max-1
  *     v-step   K_i v_i = b_i + J_ci^T (beta_i z_i - u_i)      (Eq. admm-1i)
@@ -70,6 +71,7 @@ typedef struct {
     double *v;       /* v-hat */
     double *rhs;
     double beta;
+    double beta_scale;         /* multiplies the trace rule's (or the fixed) beta; 1 default */
 } sub_t;
 
 typedef struct {
@@ -194,6 +196,7 @@ static sub_t *new_sub(orc_scene *S)
     }
     sub_t *u = &S->subs[S->nsub++];
     memset(u, 0, sizeof(*u));
+    u->beta_scale = 1.0;
     return u;
 }
 
@@ -598,10 +601,11 @@ int orc_step(orc_scene *S)
     /* construct e_j, J_j */
     for (int j = 0; j < S->ncon; j++)
         if (S->cons[j].src != SRC_ROWS) assemble_joint(S, &S->cons[j]);
-    /* beta_i (Sec. III-D) */
+    /* beta_i (Sec. III-D): the trace rule, or a fixed rho; times the subsystem's scale (an
+       input: 1 unless a learned rho sets it) */
     for (int i = 0; i < S->nsub; i++) {
         sub_t *u = &S->subs[i];
-        if (S->beta_fixed) { u->beta = S->rho; continue; }
+        if (S->beta_fixed) { u->beta = S->rho * u->beta_scale; continue; }
         double trA = 0.0, trJ = 0.0;
         for (int d = 0; d < u->n; d++) trA += u->A[d * u->n + d];
         for (int j = 0; j < S->ncon; j++) {
@@ -611,7 +615,7 @@ int orc_step(orc_scene *S)
                 for (int q = 0; q < c->rows * u->n; q++) trJ += c->J[s][q] * c->J[s][q];
             }
         }
-        u->beta = trJ > 0.0 ? trA / trJ : 1.0;
+        u->beta = (trJ > 0.0 ? trA / trJ : 1.0) * u->beta_scale;
     }
     /* factorise K_i = A_i + beta_i J_ci^T J_ci (subsystems are independent: the OpenMP
        build of the timing baseline runs them on separate threads) */
@@ -797,6 +801,9 @@ int orc_n(orc_scene *S, int i) { return S->subs[i].n; }
 int orc_rows(orc_scene *S, int j) { return S->cons[j].rows; }
 int orc_nsides(orc_scene *S, int j) { return S->cons[j].ns; }
 double orc_beta(orc_scene *S, int i) { return S->subs[i].beta; }
+
+/* Scales subsystem i's beta (from the next step on): beta_i = scale * trace rule (or rho). */
+void orc_set_beta_scale(orc_scene *S, int i, double scale) { S->subs[i].beta_scale = scale; }
 
 void orc_get_vhat(orc_scene *S, int i, double *out) { memcpy(out, S->subs[i].v, sizeof(double) * S->subs[i].n); }
 

@@ -252,3 +252,43 @@ def test_merged_rigid_chain_matches_the_split_chain():
     b = oracle.run(sg.merged(p), steps=3)[0]
     assert len(sg.merged(p).scenes[0].subs) == 1
     assert np.max(np.abs(a.bodies_all()[:, 4:] - b.bodies_all()[:, 4:])) < 1e-7
+
+
+def test_beta_scale_multiplies_the_trace_rule_and_rho():
+    """A per-subsystem scale s_i gives beta_i = s_i Tr(A_i) / Tr(J_ci^T J_ci) (Sec. III-D's
+    rule, computed here by hand), and s_i rho in the fixed mode."""
+    rng = np.random.default_rng(7)
+    A0, A1 = np.diag([1.0, 2.0, 3.0]), np.diag([4.0, 5.0])
+    J0, J1 = rng.standard_normal((2, 3)), rng.standard_normal((2, 2))
+    ifs = [sg.RowsIf(sg.EQUALITY, [0, 1], [J0, J1], np.zeros(2))]
+    subs = [sg.GenericSub(A0, np.zeros(3)), sg.GenericSub(A1, np.zeros(2))]
+    o = oracle.OracleScene(sg.Scene(subs, ifs), sg.Options(max_iters=1, tol_primal=-1))
+    o.set_beta_scale(0, 0.25)
+    o.set_beta_scale(1, 8.0)
+    o.step()
+    assert np.isclose(o.beta(0), 0.25 * 6.0 / np.sum(J0 ** 2), rtol=1e-14)
+    assert np.isclose(o.beta(1), 8.0 * 9.0 / np.sum(J1 ** 2), rtol=1e-14)
+    f = oracle.OracleScene(sg.Scene(subs, ifs), sg.Options(max_iters=1, tol_primal=-1,
+                                                           beta_mode="fixed", rho=3.0))
+    f.set_beta_scale(1, 0.5)
+    f.step()
+    assert f.beta(0) == 3.0 and f.beta(1) == 1.5
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_fixed_point_does_not_depend_on_beta_scales(seed):
+    """Any positive beta_i leaves the ADMM fixed point unchanged: equality-only systems with
+    random per-subsystem scales in [1/8, 8] still converge to the full KKT solution."""
+    rng = np.random.default_rng(60 + seed)
+    sc = sg.generic_scene(rng, n_sub=4, n_range=(6, 10), types=(sg.EQUALITY,), extra=2)
+    A, b, J, e = _full_system(sc)
+    m, n = J.shape
+    KKT = np.block([[A, -J.T], [J, np.zeros((m, m))]])
+    v_ref = np.linalg.solve(KKT, np.concatenate([b, -e]))[:n]
+    o = oracle.OracleScene(sc, sg.Options(gravity=(0, 0, 0), warm="cold", tol_primal=1e-13,
+                                          max_iters=400000))
+    for i in range(len(sc.subs)):
+        o.set_beta_scale(i, float(2.0 ** rng.uniform(-3, 3)))
+    o.step()
+    assert o.residuals()["converged"]
+    assert np.max(np.abs(o.vhat_all() - v_ref)) / np.max(np.abs(v_ref)) < 1e-9
