@@ -205,12 +205,15 @@ int sim_autotune(sim_t s, int steps, int max_classes, long long *out);
  * sim_interface_targets, after a sim_step whose start features are in x_dev, writes the
  * training targets of each interface: t_dev[7 i + r] = lambda*_r - lambda_prev,r for its
  * first 6 rows (lambda* the step's final duals, lambda_prev read from the features), 0
- * elsewhere; mask_dev 1 on those rows and 0 elsewhere (column 6, the network's seventh
- * output, is unused: beta stays the trace rule of Sec. III-D).
+ * elsewhere; mask_dev 1 on those rows and 0 elsewhere; column 6 (log2 of the beta scale)
+ * target 0, mask 1: the trace rule, unless the caller writes the scale a search found.
  *
  * sim_step_learned runs n_steps steps, each as: features, the network (32 inputs, 7
  * outputs; see warmstart.h), lambda^0 = lambda_prev + output (first 6 rows of each
- * interface), and one step started from lambda^0 (z^0 from the previous step).  After 10
+ * interface), the beta scales (output 7 is log2 of a scale proposed per interface; each
+ * subsystem takes the mean over its interfaces, rounded to an integer k in [-3, 3], and
+ * scale 2^k; see sim_set_beta_scale), and one step started from lambda^0 (z^0 from the
+ * previous step).  After 10
  * iterations a scene compares its residual max(|x - z|, |dz|) with the one its last plain
  * (previous-step) start had after 10 iterations; if the learned start is behind, the scene
  * restarts the step from the plain start and records that run's residual as the new
@@ -236,6 +239,15 @@ int sim_grid_threshold(sim_t s, int side_rows);
  * the same either way (the same products in the same order).  Takes effect at the next
  * sim_step. */
 int sim_grid_staging(sim_t s, int enable);
+
+/* Per-subsystem beta scales (host array, one per subsystem id): from the next step on,
+ * beta_i = scale[i] x (the trace rule of Sec. III-D, or rho).  The default is 1.  The ADMM
+ * fixed point does not depend on beta, its speed does: this is the input a learned rho sets
+ * (sim_step_learned does so from the network's seventh output).  A block whose factor is
+ * kept (sim_keep_factors) is factorised again when its scale changes.  SIM_EINVAL for a
+ * scale that is not positive and finite.  Lays the simulation out if needed; waits for the
+ * copy. */
+int sim_set_beta_scale(sim_t s, const double *scale);
 
 /* Tensor cores for the per-step map of large blocks (mixed form, grid kernel scenes; on by
  * default).  A step that factorises such a block (n >= 128 DOF, m >= 16 side-rows) anew --

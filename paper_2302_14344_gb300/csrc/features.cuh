@@ -15,7 +15,7 @@
 namespace subadmm {
 
 constexpr int kFeatures = 32;
-constexpr int kDualOut = 7;       // network outputs: 6 dual corrections, 1 unused
+constexpr int kDualOut = 7;       // network outputs: 6 dual corrections, log2 beta scale
 constexpr int kDualRows = 6;
 
 __device__ __forceinline__ void quat_conj_mul(const double *a, const double *b, double *o)
@@ -113,7 +113,8 @@ __global__ void interface_features_kernel(const StepParams P, const int *pub2dev
 }
 
 // training targets after a step: t = lambda* - lambda_prev (the previous lambda read back from
-// the features taken before the step), mask 1 on the interface's rows (first 6), 0 elsewhere
+// the features taken before the step), mask 1 on the interface's rows (first 6), 0 elsewhere;
+// column 6 (log2 beta scale) 0 with mask 1
 __global__ void interface_targets_kernel(const StepParams P, const int *pub2dev,
                                          const int *con_scene, int nif, const float *X,
                                          float *T, float *M)
@@ -122,11 +123,15 @@ __global__ void interface_targets_kernel(const StepParams P, const int *pub2dev,
         const int j = pub2dev[i];
         const ConDesc &c = P.cons[j];
         const int rg = P.scenes[con_scene[j]].row_g0 + c.row0;
-        for (int r = 0; r < kDualOut; ++r) {
-            const bool on = r < c.rows && r < kDualRows;
+        for (int r = 0; r < kDualRows; ++r) {
+            const bool on = r < c.rows;
             T[(size_t)i * kDualOut + r] = on ? (float)(P.lam[rg + r] - (double)X[(size_t)i * kFeatures + 17 + r]) : 0.0f;
             M[(size_t)i * kDualOut + r] = on ? 1.0f : 0.0f;
         }
+        // the seventh output, log2 of the beta scale: 0 (the trace rule) unless the caller
+        // writes the best scale a search found
+        T[(size_t)i * kDualOut + kDualRows] = 0.0f;
+        M[(size_t)i * kDualOut + kDualRows] = 1.0f;
     }
 }
 
@@ -141,6 +146,38 @@ __global__ void learned_duals_kernel(const StepParams P, const int *pub2dev, con
         const int rg = P.scenes[con_scene[j]].row_g0 + c.row0;
         for (int r = 0; r < c.rows; ++r)
             lam0[rg + r] = P.lam[rg + r] + (r < kDualRows ? (double)Y[(size_t)i * kDualOut + r] : 0.0);
+    }
+}
+
+// learned beta scale, accumulation: every interface adds the network's seventh output (log2
+// of the scale it proposes) to each of its sides' subsystem sums; acc holds nsub sums, then
+// nsub counts, zeroed before
+__global__ void learned_beta_accumulate_kernel(const StepParams P, const int *pub2dev,
+                                               const int *con_scene, int nif, const float *Y,
+                                               float *acc, int nsub)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nif; i += gridDim.x * blockDim.x) {
+        const int j = pub2dev[i];
+        const ConDesc &c = P.cons[j];
+        const int sub0 = P.scenes[con_scene[j]].sub0;
+        const float y = Y[(size_t)i * kDualOut + kDualRows];
+        for (int q = 0; q < c.ns; ++q) {
+            atomicAdd(&acc[sub0 + c.sub[q]], isfinite(y) ? y : 0.0f);
+            atomicAdd(&acc[nsub + sub0 + c.sub[q]], 1.0f);
+        }
+    }
+}
+
+// learned beta scale per subsystem: 2^k with k the mean proposal of its interfaces rounded to
+// an integer in [-3, 3] (whole powers of two, so a kept factor is refactorised only when the
+// proposal moves by a whole step); 1 for a subsystem without interfaces
+__global__ void learned_beta_scale_kernel(const float *acc, int nsub, double *scale)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nsub; i += gridDim.x * blockDim.x) {
+        const float n = acc[nsub + i];
+        float k = n > 0.0f ? rintf(acc[i] / n) : 0.0f;
+        k = fminf(3.0f, fmaxf(-3.0f, k));
+        scale[i] = exp2((double)k);
     }
 }
 

@@ -143,6 +143,8 @@ struct StepParams {
     int *learn_skip;       // per scene: steps left to start plain, and the fallback streak
     double *z;             // per side-row: z of the last step (warm start state)
     double *beta;          // per subsystem
+    const double *beta_scale;  // per subsystem: beta = scale x (trace rule or rho)
+    double *beta_used;     // per subsystem: the scale a kept factor was computed with
     double *res;           // 6 per scene
     long long *stats;      // 5 per scene: sum iters, max iters, not converged, steps,
                            // fallbacks of the learned start

@@ -335,13 +335,14 @@ __device__ __forceinline__ SubEnv sub_env(const StepParams &P, const SubDesc &u)
 // A constant K_i whose factor from an earlier step is still held: in the workspace (it
 // outlives the launch) or in shared memory from an earlier step of this launch.  With
 // keep_factors 0 every step refactors (the same matrix; results agree to rounding).  A
-// tc_phase 1 launch (the host issues it only for steps that refactor) refactors every tc
+// changed beta scale refactors too (K_i = A_i + beta_i J^T J changed).  A tc_phase 1 launch (the host issues it only for steps that refactor) refactors every tc
 // subsystem.
 __device__ __forceinline__ bool factor_kept(const StepParams &P, const SceneDesc &S,
                                             const SubDesc &u, int gsub, int step)
 {
     if (P.tc_phase == 1 && u.tc) return false;
-    return P.keep_factors && u.cst && (step > 0 || S.sub_global) && (P.subflag[gsub] & 1);
+    return P.keep_factors && u.cst && (step > 0 || S.sub_global) && (P.subflag[gsub] & 1) &&
+           P.beta_scale[gsub] == P.beta_used[gsub];
 }
 
 // K += beta J^T J on the lower triangle (row-major n x n), one J row at a time over the
@@ -715,9 +716,11 @@ __device__ long long scene_setup(const StepParams &P, const SceneDesc &S, const 
             }
             beta = (double)(P.beta_fixed ? (T)P.rho : (trJ > (T)0 ? trA / trJ : (T)1));
         }
+        beta *= P.beta_scale[gsub];
         if (lane == 0) {
             db[S.od_beta + i] = beta;
             P.beta[gsub] = beta;
+            P.beta_used[gsub] = P.beta_scale[gsub];
         }
         bool stiff = true;
         if (MIXED) {

@@ -126,6 +126,9 @@ struct sim_s {
     double *d_nodes = nullptr;     // node states of linear blocks
     int *d_ipool = nullptr;        // integer constant data
     int *d_subflag = nullptr;      // per subsystem: kept-factor flags
+    double *d_beta_scale = nullptr;   // per subsystem: beta = scale x (trace rule or rho)
+    double *d_beta_used = nullptr;    // per subsystem: the scale of the kept factor
+    float *d_bacc = nullptr;          // learned beta: per-subsystem sums and counts
     long long nnodes = 0;
     long long work_bytes = 0;
     size_t pool_size = 0;
@@ -233,6 +236,8 @@ void free_device(sim_t s)
     cudaFree(s->d_work);
     s->d_work = nullptr;
     cudaFree(s->d_nodes); cudaFree(s->d_ipool); cudaFree(s->d_subflag);
+    cudaFree(s->d_beta_scale); cudaFree(s->d_beta_used); cudaFree(s->d_bacc);
+    s->d_beta_scale = nullptr; s->d_beta_used = nullptr; s->d_bacc = nullptr;
     cudaFree(s->d_scene_ids);
     s->d_scene_ids = nullptr;
     cudaFree(s->d_grid);
@@ -824,6 +829,17 @@ int finalize(sim_t s)
     if ((rc = upload(s, &s->d_nodes, nodes, "nodes"))) return rc;
     if ((rc = upload(s, &s->d_ipool, ipool, "integer pool"))) return rc;
     {
+        {
+            const std::vector<double> ones(std::max(1, nsubs), 1.0);
+            if (cudaMalloc((void **)&s->d_beta_scale, ones.size() * sizeof(double)) != cudaSuccess ||
+                cudaMalloc((void **)&s->d_beta_used, ones.size() * sizeof(double)) != cudaSuccess ||
+                cudaMalloc((void **)&s->d_bacc, 2 * ones.size() * sizeof(float)) != cudaSuccess)
+                return fail(s, SIM_ENOMEM, "cudaMalloc beta scale");
+            CK(cudaMemcpy(s->d_beta_scale, ones.data(), ones.size() * sizeof(double),
+                          cudaMemcpyHostToDevice), "beta scale");
+            CK(cudaMemcpy(s->d_beta_used, ones.data(), ones.size() * sizeof(double),
+                          cudaMemcpyHostToDevice), "beta scale");
+        }
         cudaError_t e = cudaMalloc((void **)&s->d_subflag, std::max(1, nsubs) * sizeof(int));
         if (e != cudaSuccess) return fail(s, SIM_ENOMEM, "cudaMalloc subsystem flags");
         CK(cudaMemsetAsync(s->d_subflag, 0, std::max(1, nsubs) * sizeof(int), s->stream), "memset flags");
@@ -1120,6 +1136,8 @@ StepParams step_params(const sim_t s, int n_steps)
     P.nodes = s->d_nodes;
     P.ipool = s->d_ipool;
     P.subflag = s->d_subflag;
+    P.beta_scale = s->d_beta_scale;
+    P.beta_used = s->d_beta_used;
     P.keep_factors = s->keep_factors;
     P.beta = s->d_beta; P.res = s->d_res; P.stats = s->d_stats; P.phase = s->d_phase;
     P.nscenes = s->nscenes;
@@ -1428,6 +1446,7 @@ int sim_autotune(sim_t s, int steps, int max_classes, long long *out)
         {s->d_ref10, sizeof(unsigned long long) * (size_t)s->nscenes},
         {s->d_learn_skip, sizeof(int) * 2 * (size_t)s->nscenes},
         {s->d_subflag, sizeof(int) * nsub},
+        {s->d_beta_used, sizeof(double) * nsub},
         {s->d_phase, s->d_phase ? sizeof(long long) * 8 * (size_t)s->nscenes : 0}};
     size_t total = 0;
     for (auto &a : arrs) total += (a.p ? (a.bytes + 255) / 256 * 256 : 0);
@@ -1597,6 +1616,14 @@ int sim_step_learned(sim_t s, wsn_t net, int n_steps)
             subadmm::learned_duals_kernel<<<grid_of(nif), 128, 0, st>>>(
                 P, s->d_pub2dev, s->d_con_scene, nif, s->d_netout, s->d_lam0);
             CK(cudaGetLastError(), "learned duals launch");
+            const int nsub = (int)s->sdesc.size();
+            CK(cudaMemsetAsync(s->d_bacc, 0, 2 * sizeof(float) * nsub, st), "learned beta clear");
+            subadmm::learned_beta_accumulate_kernel<<<grid_of(nif), 128, 0, st>>>(
+                P, s->d_pub2dev, s->d_con_scene, nif, s->d_netout, s->d_bacc, nsub);
+            CK(cudaGetLastError(), "learned beta launch");
+            subadmm::learned_beta_scale_kernel<<<grid_of(nsub), 128, 0, st>>>(
+                s->d_bacc, nsub, s->d_beta_scale);
+            CK(cudaGetLastError(), "learned beta scale launch");
         }
         StepParams Q = P;
         Q.lam0 = nif > 0 ? s->d_lam0 : nullptr;
@@ -1666,6 +1693,25 @@ int sim_grid_staging(sim_t s, int enable)
 {
     if (!s) return SIM_EINVAL;
     s->grid_staging = enable ? 1 : 0;
+    return SIM_OK;
+}
+
+int sim_set_beta_scale(sim_t s, const double *scale)
+{
+    if (!s || !scale) return SIM_EINVAL;
+    ON_DEVICE(s->opt.device);
+    int rc = finalize(s);
+    if (rc) return rc;
+    const int nsub = (int)s->subs.size();
+    std::vector<double> dev(std::max(1, nsub), 1.0);
+    for (int i = 0; i < nsub; ++i) {
+        if (!(scale[i] > 0.0) || !std::isfinite(scale[i]))
+            return fail(s, SIM_EINVAL, "beta scales must be positive and finite");
+        dev[s->sub_dev[i]] = scale[i];
+    }
+    CK(cudaMemcpyAsync(s->d_beta_scale, dev.data(), sizeof(double) * dev.size(),
+                       cudaMemcpyHostToDevice, s->stream), "beta scale");
+    CK(cudaStreamSynchronize(s->stream), "beta scale");
     return SIM_OK;
 }
 

@@ -33,6 +33,7 @@ EXPORTS = ("sim_default_options", "sim_create", "sim_destroy", "sim_add_subsyste
            "sim_read_state", "sim_read_state_noalloc", "sim_write_state", "sim_sizes",
            "sim_iteration_stats", "sim_scene_info", "sim_use_graph", "sim_launch_classes",
            "sim_autotune", "sim_grid_threshold", "sim_grid_staging", "sim_grid_blocks", "sim_tensor_cores", "sim_keep_factors",
+           "sim_set_beta_scale",
            "sim_probe_barrier", "sim_barrier_floor", "sim_gram_tc", "sim_interface_features",
            "sim_interface_targets", "sim_step_learned", "sim_phase_trace", "sim_sync",
            "sim_last_error")
@@ -101,6 +102,7 @@ def load(build_if_missing: bool = True):
             "sim_keep_factors": (C.c_int, [VP, C.c_int]),
             "sim_grid_blocks": (C.c_int, [VP, C.c_int]),
             "sim_tensor_cores": (C.c_int, [VP, C.c_int]),
+            "sim_set_beta_scale": (C.c_int, [VP, PD]),
             "sim_interface_features": (C.c_int, [VP, VP]),
             "sim_interface_targets": (C.c_int, [VP, VP, VP, VP]),
             "sim_step_learned": (C.c_int, [VP, VP, C.c_int]),
@@ -239,6 +241,11 @@ def sim_grid_staging(h, enable: bool) -> None:
 
 def sim_grid_blocks(h, blocks: int) -> None:
     _check(h, load().sim_grid_blocks(h, blocks))
+
+
+def sim_set_beta_scale(h, scale) -> None:
+    a = _f64(scale)
+    _check(h, load().sim_set_beta_scale(h, _dp(a)))
 
 
 def sim_tensor_cores(h, enable: bool) -> None:
@@ -471,6 +478,10 @@ class Simulation:
 
     def grid_blocks(self, blocks: int) -> None:
         sim_grid_blocks(self.h, blocks)
+
+    def set_beta_scale(self, scale) -> None:
+        """One scale per subsystem id (sub_ids order): beta_i = scale x trace rule (or rho)."""
+        sim_set_beta_scale(self.h, scale)
 
     def tensor_cores(self, enable: bool = True) -> None:
         sim_tensor_cores(self.h, enable)

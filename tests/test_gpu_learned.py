@@ -75,7 +75,8 @@ def test_targets_are_the_dual_change_on_the_interface_rows(mods):
     row = 0
     for i in range(nif):
         rows = sim.if_rows[i]
-        assert m[i].sum() == min(rows, 6) and m[i, 6] == 0
+        # the dual rows, plus column 6 (log2 beta scale): target 0, the trace rule
+        assert m[i, :6].sum() == min(rows, 6) and m[i, 6] == 1 and t[i, 6] == 0
         for r in range(min(rows, 6)):
             want = lam[row + r] - np.float32(lam_prev[row + r])
             assert abs(t[i, r] - want) <= 1e-6 * max(1.0, abs(lam[row + r]))
