@@ -56,9 +56,23 @@ int wsn_get_normalization(wsn_t w, float *mean_in, float *std_in, float *scale_o
 int wsn_fit_normalization(wsn_t w, const float *x_dev, long long ldx, const float *t_dev,
                           int batch, void *stream);
 
-/* Inference: y (batch x out, FP32) = scale_out * net((x - mean_in) / std_in). */
+/* Inference: y (batch x out, FP32) = scale_out * net((x - mean_in) / std_in).  For the
+ * warm-start shape (32 -> 256 -> 256 -> 256 -> 7) all four layers run in one fused launch on
+ * the tcgen05 tensor cores (the BF16 weights packed K-major on every call, activations in
+ * shared memory between layers, accumulators in tensor memory); other shapes run layer by
+ * layer.  Both compute the same arithmetic (BF16 weights and activations, FP32 accumulation,
+ * exact GELU) and differ only in the order of the FP32 sums. */
 int wsn_forward(wsn_t w, const float *x_dev, long long ldx, int batch, float *y_dev,
                 void *stream);
+
+/* The layer-by-layer inference (one tensor-core GEMM launch per layer) for any shape: the
+ * reference the fused path is tested against. */
+int wsn_forward_layers(wsn_t w, const float *x_dev, long long ldx, int batch, float *y_dev,
+                       void *stream);
+
+/* Reads and clears the fused inference kernel's error word: *out = 1 if one of its waits
+ * ran out (1 s) since the last call (its outputs are then undefined).  Synchronous. */
+int wsn_fused_error(wsn_t w, int *out);
 
 /* Gradients of the masked mean-squared loss L = sum mask (net(x) - t / scale_out)^2 / (2 batch)
  * (the targets t in output units, divided by scale_out inside), written to grad_dev in the

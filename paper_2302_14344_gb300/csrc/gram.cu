@@ -3,51 +3,22 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
-#include <mutex>
 #include <vector>
 
 #include "subadmm.h"
 #include "gram_tc.cuh"
+#include "tmap.h"
 #include "device_guard.h"
 
 namespace subadmm {
 
 namespace {
 
-using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
-                                 const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
-                                 const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
-                                 CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-// the driver's tensor-map encoder, through the runtime (no link against libcuda)
-EncodeTiled encoder()
-{
-    static std::once_flag once;
-    static EncodeTiled fn = nullptr;
-    std::call_once(once, [] {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
-                                             cudaEnableDefault, &q) == cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<EncodeTiled>(p);
-    });
-    return fn;
-}
-
 // a 2-D FP32 tensor of `rows` rows of `ld` elements, boxes of 32 x 128, 128-byte swizzle
 cudaError_t encode(CUtensorMap *map, float *base, int ld, int rows)
 {
-    EncodeTiled fn = encoder();
-    if (!fn) return cudaErrorNotSupported;
-    const cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)rows};
-    const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(float)};
-    const cuuint32_t box[2] = {(cuuint32_t)kGramKChunk, (cuuint32_t)kGramTile};
-    const cuuint32_t estr[2] = {1, 1};
-    const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr,
-                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+    return tmap_encode_2d(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, sizeof(float), base, ld, rows,
+                          kGramKChunk, kGramTile);
 }
 
 int round_up(int x, int a) { return (x + a - 1) / a * a; }

@@ -12,6 +12,8 @@
 #include "subadmm.h"
 #include "warmstart.h"
 #include "mlp.cuh"
+#include "mlp_tc.cuh"
+#include "tmap.h"
 #include "device_guard.h"
 
 struct wsn_s {
@@ -31,6 +33,12 @@ struct wsn_s {
     std::vector<float *> pre;          // pre[l]: pre-activation of hidden layer l (B x sizes[l+1])
     float *y = nullptr;                // network output (B x out)
     __nv_bfloat16 *g0 = nullptr, *g1 = nullptr;   // layer gradients (B x max width)
+    // fused tensor-core inference (the 32-256-256-256-7 warm-start shape): packed BF16
+    // weights (K-major per layer), their tensor maps, the kernel's error word
+    __nv_bfloat16 *wpack[4] = {nullptr, nullptr, nullptr, nullptr};
+    CUtensorMap wmap[4];
+    int *ferr = nullptr;
+    bool fused_ready = false;
     std::string err;
 };
 
@@ -161,6 +169,55 @@ int backward(wsn_t w, const float *t, const float *mask, int batch, float *grad,
 
 }  // namespace
 
+namespace {
+
+bool fused_shape(const wsn_t w)
+{
+    return w->sizes.size() == 5 && w->sizes[0] == wsn::kMlpIn && w->sizes[1] == wsn::kMlpHidden &&
+           w->sizes[2] == wsn::kMlpHidden && w->sizes[3] == wsn::kMlpHidden &&
+           w->sizes[4] == wsn::kMlpOut;
+}
+
+// the warm-start shape: pack the current BF16 weights (every call, so that a captured graph
+// sees parameters trained after its capture) and run all four layers in one launch
+int fused_forward(wsn_t w, const float *x, long long ldx, int batch, float *y, cudaStream_t st)
+{
+    using namespace wsn;
+    if (!w->fused_ready) {
+        const size_t n[4] = {(size_t)kMlpHidden * kMlpInPad, (size_t)kMlpHidden * kMlpHidden,
+                             (size_t)kMlpHidden * kMlpHidden, (size_t)kMlpOutPad * kMlpHidden};
+        const int inner[4] = {kMlpInPad, kMlpHidden, kMlpHidden, kMlpHidden};
+        const int rows[4] = {kMlpHidden, kMlpHidden, kMlpHidden, kMlpOutPad};
+        for (int l = 0; l < 4; ++l) {
+            WCK(cudaMalloc((void **)&w->wpack[l], sizeof(__nv_bfloat16) * n[l]), "cudaMalloc packed weights");
+            WCK(subadmm::tmap_encode_2d(&w->wmap[l], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                                        sizeof(__nv_bfloat16), w->wpack[l], inner[l], rows[l], 64,
+                                        rows[l]), "tensor map");
+        }
+        WCK(cudaMalloc((void **)&w->ferr, sizeof(int)), "cudaMalloc error word");
+        WCK(cudaMemset(w->ferr, 0, sizeof(int)), "error word");
+        WCK(cudaFuncSetAttribute((const void *)mlp_fused_kernel,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kMlpSmem), "attribute");
+        w->fused_ready = true;
+    }
+    mlp_pack_kernel<<<256, 256, 0, st>>>(w->pb, w->w_off[0], w->w_off[1], w->w_off[2], w->w_off[3],
+                                         w->wpack[0], w->wpack[1], w->wpack[2], w->wpack[3]);
+    WCK(cudaGetLastError(), "pack launch");
+    MlpArgs a;
+    a.x = x; a.ldx = ldx; a.batch = batch; a.mean = w->mean; a.inv_std = w->inv_std;
+    for (int l = 0; l < 4; ++l) a.bias[l] = w->p + w->b_off[l];
+    a.scale = w->scale; a.y = y; a.err = w->ferr;
+    int sms = 0;
+    WCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, w->device), "attribute");
+    const int tiles = (batch + kMlpRows - 1) / kMlpRows;
+    mlp_fused_kernel<<<std::max(1, std::min(tiles, sms)), kMlpThreads, kMlpSmem, st>>>(
+        w->wmap[0], w->wmap[1], w->wmap[2], w->wmap[3], a);
+    WCK(cudaGetLastError(), "fused forward launch");
+    return SIM_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 int wsn_create(int device, int n_layers, const int *sizes, wsn_t *out)
@@ -210,6 +267,8 @@ void wsn_destroy(wsn_t w)
     if (!w) return;
     subadmm::DeviceGuard on_device(w->device);
     free_ws(w);
+    for (auto *q : w->wpack) cudaFree(q);
+    cudaFree(w->ferr);
     cudaFree(w->p); cudaFree(w->g); cudaFree(w->m); cudaFree(w->v); cudaFree(w->pb);
     cudaFree(w->mean); cudaFree(w->inv_std); cudaFree(w->scale);
     delete w;
@@ -303,6 +362,33 @@ int wsn_fit_normalization(wsn_t w, const float *x_dev, long long ldx, const floa
     return SIM_OK;
 }
 
+int wsn_fused_error(wsn_t w, int *out)
+{
+    if (!w || !out) return SIM_EINVAL;
+    *out = 0;
+    if (!w->ferr) return SIM_OK;
+    subadmm::DeviceGuard on_device(w->device);
+    WCK(on_device.err, "cudaSetDevice");
+    WCK(cudaMemcpy(out, w->ferr, sizeof(int), cudaMemcpyDeviceToHost), "error word");
+    WCK(cudaMemset(w->ferr, 0, sizeof(int)), "error word");
+    return SIM_OK;
+}
+
+int wsn_forward_layers(wsn_t w, const float *x_dev, long long ldx, int batch,
+                                  float *y_dev, void *stream)
+{
+    if (!w || !x_dev || !y_dev || batch < 0 || ldx < w->sizes[0]) return SIM_EINVAL;
+    if (batch == 0) return SIM_OK;
+    subadmm::DeviceGuard on_device(w->device);
+    WCK(on_device.err, "cudaSetDevice");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = forward(w, x_dev, ldx, batch, true, st);
+    if (rc) return rc;
+    WCK(cudaMemcpyAsync(y_dev, w->y, sizeof(float) * (size_t)batch * w->sizes.back(),
+                        cudaMemcpyDeviceToDevice, st), "output copy");
+    return SIM_OK;
+}
+
 int wsn_forward(wsn_t w, const float *x_dev, long long ldx, int batch, float *y_dev, void *stream)
 {
     if (!w || !x_dev || !y_dev || batch < 0 || ldx < w->sizes[0]) return SIM_EINVAL;
@@ -310,6 +396,7 @@ int wsn_forward(wsn_t w, const float *x_dev, long long ldx, int batch, float *y_
     subadmm::DeviceGuard on_device(w->device);
     WCK(on_device.err, "cudaSetDevice");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (fused_shape(w)) return fused_forward(w, x_dev, ldx, batch, y_dev, st);
     int rc = forward(w, x_dev, ldx, batch, true, st);
     if (rc) return rc;
     WCK(cudaMemcpyAsync(y_dev, w->y, sizeof(float) * (size_t)batch * w->sizes.back(),

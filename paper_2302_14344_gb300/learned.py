@@ -41,6 +41,80 @@ def collect(problem, steps: int, warmup: int = 5, precision: int = sa.SIM_MIXED,
     return torch.cat(xs), torch.cat(ts), torch.cat(ms)
 
 
+SCALES = [2.0 ** k for k in range(-3, 4)]    # candidate beta scales of the rho search
+REF = 3                                       # index of scale 1 (the trace rule)
+
+
+def _replicate(problem, copies: int):
+    import scenegen as sg
+    return sg.Problem([sc for _ in range(copies) for sc in problem.scenes], problem.options,
+                      name=f"{problem.name}x{copies}")
+
+
+def collect_rho(problem, steps: int, warmup: int = 5, precision: int = sa.SIM_MIXED,
+                device: int = 0):
+    """Samples from the plain simulator, with the best beta scale of each scene-step as the
+    label of the network's seventh output.  Every scene runs in seven copies, copy k with
+    every subsystem's beta scaled by 2^(k-3) (k = 3: the trace rule, Sec. III-D); after each
+    step the copies' iteration counts give each scene's best scale (fewest iterations to the
+    stop rule, ties to the scale nearest 1) and every copy is reset to the trace-rule copy's
+    state, so that all copies start each step from the plain trajectory.  Features and dual
+    targets are the trace-rule copy's.  Returns device tensors (X, T, M) like collect()."""
+    import torch
+    nsc = len(problem.scenes)
+    rep = _replicate(problem, len(SCALES))
+    sim = sa.Simulation(rep, device=device, precision=precision)
+    nsub_copy = sum(len(sc.subs) for sc in problem.scenes)
+    sim.set_beta_scale([SCALES[c] for c in range(len(SCALES)) for _ in range(nsub_copy)])
+    sz = sim.sizes()
+    nb = sz["bodies"] // len(SCALES)
+    nn = sz["nodes"] // len(SCALES)
+    state = torch.empty(13 * sz["bodies"] + 6 * sz["nodes"], dtype=torch.float64).pin_memory()
+
+    def sync_copies():
+        sa.sim_read_state(sim.h, state.data_ptr())
+        bodies = state[: 13 * sz["bodies"]].view(len(SCALES), 13 * nb)
+        nodes = state[13 * sz["bodies"]:].view(len(SCALES), 6 * nn)
+        bodies[:] = bodies[REF].clone()
+        nodes[:] = nodes[REF].clone()
+        sa.sim_write_state(sim.h, state.data_ptr())
+
+    for _ in range(warmup):
+        sim.step(1)
+        sync_copies()
+    nif = sz["interfaces"]
+    nif0 = nif // len(SCALES)
+    per_scene_if = torch.tensor([len(sc.ifs) for sc in problem.scenes], device=f"cuda:{device}")
+    order = sorted(range(len(SCALES)), key=lambda k: abs(k - REF))
+    sim.iteration_stats()
+    xs, ts, ms = [], [], []
+    for _ in range(steps):
+        x = torch.empty((nif, FEATURES), device=f"cuda:{device}")
+        t = torch.empty((nif, OUTPUTS), device=f"cuda:{device}")
+        m = torch.empty((nif, OUTPUTS), device=f"cuda:{device}")
+        sa.sim_interface_features(sim.h, x.data_ptr())
+        sim.step(1)
+        sa.sim_interface_targets(sim.h, x.data_ptr(), t.data_ptr(), m.data_ptr())
+        st = sim.iteration_stats(per_scene=True)["per_scene"]
+        it = np.asarray(st[:, 0]).reshape(len(SCALES), nsc)
+        nc = np.asarray(st[:, 2]).reshape(len(SCALES), nsc)
+        best = np.zeros(nsc)
+        for sc in range(nsc):
+            cand = [k for k in order if nc[k, sc] == 0] or [REF]
+            kb = min(cand, key=lambda k: (it[k, sc], abs(k - REF)))
+            best[sc] = kb - REF
+        lo, hi = REF * nif0, (REF + 1) * nif0
+        label = torch.repeat_interleave(torch.tensor(best, dtype=torch.float32,
+                                                     device=f"cuda:{device}"), per_scene_if)
+        t_ref = t[lo:hi].clone()
+        t_ref[:, OUTPUTS - 1] = label
+        xs.append(x[lo:hi].clone()); ts.append(t_ref); ms.append(m[lo:hi].clone())
+        sync_copies()
+    sim.sync()
+    sim.close()
+    return torch.cat(xs), torch.cat(ts), torch.cat(ms)
+
+
 def init_network(seed: int = 0, device: int = 0) -> Network:
     """He-initialised weights (drawn on the host from a seeded generator), zero biases."""
     rng = np.random.default_rng(seed)
@@ -75,7 +149,7 @@ def train(net: Network, X, T, M, epochs: int = 3, batch: int = 4096, lr: float =
 
 
 def compare(problem, net: Network, steps: int, warmup: int = 5,
-            precision: int = sa.SIM_MIXED, device: int = 0) -> dict:
+            precision: int = sa.SIM_MIXED, device: int = 0, learned_warmup: int = 0) -> dict:
     """The same start, stepped with the previous-step warm start and with the learned one:
     iterations per scene-step of each, fallbacks of the learned start, and the wall time
     of the device work (CUDA events)."""
@@ -86,9 +160,9 @@ def compare(problem, net: Network, steps: int, warmup: int = 5,
         sim.step(warmup)
         sim.use_graph(True)
         if name == "learned":                   # first (direct) learned step and capture
-            sim.step_learned(net, 1)
+            sim.step_learned(net, 1 + learned_warmup)
         else:
-            sim.step(1)
+            sim.step(1 + learned_warmup)
         sim.sync()
         sim.iteration_stats()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -21,7 +21,8 @@ EXPORTS = ("wsn_create", "wsn_destroy", "wsn_last_error", "wsn_num_params", "wsn
            "wsn_workspace_generation",
            "wsn_set_params",
            "wsn_get_params", "wsn_set_normalization", "wsn_get_normalization",
-           "wsn_fit_normalization", "wsn_forward", "wsn_gradients", "wsn_train_step")
+           "wsn_fit_normalization", "wsn_forward", "wsn_forward_layers", "wsn_fused_error",
+           "wsn_gradients", "wsn_train_step")
 
 _sigs = {
     "wsn_create": (C.c_int, [C.c_int, C.c_int, PI, C.POINTER(VP)]),
@@ -36,6 +37,8 @@ _sigs = {
     "wsn_get_normalization": (C.c_int, [VP, PF, PF, PF]),
     "wsn_fit_normalization": (C.c_int, [VP, VP, C.c_longlong, VP, C.c_int, VP]),
     "wsn_forward": (C.c_int, [VP, VP, C.c_longlong, C.c_int, VP, VP]),
+    "wsn_forward_layers": (C.c_int, [VP, VP, C.c_longlong, C.c_int, VP, VP]),
+    "wsn_fused_error": (C.c_int, [VP, PI]),
     "wsn_gradients": (C.c_int, [VP, VP, C.c_longlong, VP, VP, C.c_int, VP, VP, VP]),
     "wsn_train_step": (C.c_int, [VP, VP, C.c_longlong, VP, VP, C.c_int, C.c_float, VP, VP]),
 }
@@ -127,6 +130,16 @@ class Network:
     def forward(self, x, y) -> None:
         self._check(lib().wsn_forward(self.h, _dev(x), x.shape[1], x.shape[0], _dev(y),
                                       VP(self.stream)))
+
+    def forward_layers(self, x, y) -> None:
+        """The layer-by-layer inference (any shape)."""
+        self._check(lib().wsn_forward_layers(self.h, _dev(x), x.shape[1], x.shape[0], _dev(y),
+                                             VP(self.stream)))
+
+    def fused_error(self) -> int:
+        out = (C.c_int * 1)()
+        self._check(lib().wsn_fused_error(self.h, out))
+        return int(out[0])
 
     def gradients(self, x, t, mask, grad, loss=None) -> None:
         self._check(lib().wsn_gradients(self.h, _dev(x), x.shape[1], _dev(t), _dev(mask),

@@ -635,7 +635,8 @@ def fem_beam(seed: int = 0, ny: int = 10, nz: int = 10, planes: int = 137, slabs
              length: float = 0.5, width: float = 0.05, height: float = 0.05, E: float = 1e5,
              nu: float = 0.45, rho: float = 1000.0, mu: float = 0.5, drop: float = 0.002,
              with_gripper: bool = True, h: float = 1e-3, tol_primal: float = 1e-6,
-             max_iters: int = 1000, warm: str = "prev", kp: float = 50.0, kd: float = 1.0):
+             max_iters: int = 1000, warm: str = "prev", kp: float = 50.0, kd: float = 1.0,
+             vary: bool = False):
     """A linear-elastic tetrahedral beam (planes x ny x nz nodes, Kuhn split of every grid
     cell) cut into ``slabs`` subsystems: slab g holds 4 node planes when g is a multiple of
     8 and 3 otherwise, neighbouring slabs duplicate the cut plane, and each duplicated node
@@ -643,8 +644,15 @@ def fem_beam(seed: int = 0, ny: int = 10, nz: int = 10, planes: int = 137, slabs
     has a speculative contact with the plane z = 0 (friction mu); the beam starts ``drop``
     above it.  With the gripper, a 7-R arm (one rigid subsystem, PD drives holding its
     pose) holds the beam's x = 0 end by ball joints between its two paddles and the
-    nearest side-face nodes."""
+    nearest side-face nodes.  With ``vary`` the seed draws a member of the workload's
+    distribution: drop height U[1, 4] mm, friction U[0.3, 0.7], Young's modulus E 2^U[-1/2, 1/2]
+    and PD gains kp 2^U[-1/2, 1/2]; otherwise the beam is the same for every seed."""
     rng = np.random.default_rng(seed)
+    if vary:
+        drop = float(rng.uniform(0.001, 0.004))
+        mu = float(rng.uniform(0.3, 0.7))
+        E = float(E * 2.0 ** rng.uniform(-0.5, 0.5))
+        kp = float(kp * 2.0 ** rng.uniform(-0.5, 0.5))
     ks = [4 if g % 8 == 0 else 3 for g in range(slabs)]
     if sum(k - 1 for k in ks) != planes - 1:
         raise ValueError("slab plane counts do not tile the beam")

@@ -120,3 +120,41 @@ def test_training_reduces_the_loss_of_a_smooth_regression(ws, capsys):
         print(f"\n[warm-start network training, smooth regression] loss {losses[0]:.3e} -> "
               f"{np.mean(losses[-10:]):.3e}")
     assert np.mean(losses[-10:]) < 0.1 * losses[0]
+
+
+@pytest.mark.parametrize("B", [1, 127, 128, 129, 1000, 70001])
+def test_fused_tensor_core_forward_equals_the_layered_forward(ws, B):
+    """All four layers in one tcgen05 launch (tiles of 128 interfaces, ragged last tile)
+    against the layer-by-layer kernels, with a fitted input normalisation and output scale:
+    the same BF16/FP32 arithmetic, so they agree to the order of the FP32 sums (an
+    activation may round to the neighbouring BF16 value)."""
+    import torch
+    net, params, _, _, _, dev = _setup(ws, seed=4, B=8)
+    g = torch.Generator(device="cuda").manual_seed(B)
+    x = torch.randn(B, SIZES[0], device="cuda", generator=g) * 3.0 + 1.0
+    t = torch.randn(B, SIZES[-1], device="cuda", generator=g) * 5.0
+    net.fit_normalization(x, t)
+    y = torch.full((B, SIZES[-1]), float("nan"), device="cuda")
+    z = torch.empty((B, SIZES[-1]), device="cuda")
+    net.forward(x, y)
+    net.forward_layers(x, z)
+    torch.cuda.synchronize()
+    assert net.fused_error() == 0
+    assert torch.isfinite(y).all()
+    err = float((y - z).norm() / z.norm())
+    assert err < 3e-3, err
+
+
+def test_fused_forward_follows_training(ws):
+    """The fused path packs the current BF16 weights on every call: after Adam steps its
+    outputs follow the layer-by-layer path's."""
+    import torch
+    net, params, x, t, mask, dev = _setup(ws, seed=6)
+    for _ in range(3):
+        net.train_step(dev(x), dev(t), dev(mask), 1e-2)
+    y = torch.empty((x.shape[0], SIZES[-1]), device="cuda")
+    z = torch.empty_like(y)
+    net.forward(dev(x), y)
+    net.forward_layers(dev(x), z)
+    torch.cuda.synchronize()
+    assert float((y - z).norm() / z.norm()) < 3e-3
