@@ -208,21 +208,22 @@ int sim_autotune(sim_t s, int steps, int max_classes, long long *out);
  * elsewhere; mask_dev 1 on those rows and 0 elsewhere; column 6 (log2 of the beta scale)
  * target 0, mask 1: the trace rule, unless the caller writes the scale a search found.
  *
- * sim_step_learned runs n_steps steps, each as: features, the network (32 inputs, 7
- * outputs; see warmstart.h), lambda^0 = lambda_prev + output (first 6 rows of each
- * interface), the beta scales (output 7 is log2 of a scale proposed per interface; each
- * subsystem takes the mean over its interfaces, rounded to an integer k in [-3, 3], and
- * scale 2^k; see sim_set_beta_scale), and one step started from lambda^0 (z^0 from the
- * previous step).  After 10
- * iterations a scene compares its residual max(|x - z|, |dz|) with the one its last plain
- * (previous-step) start had after 10 iterations; if the learned start is behind, the scene
- * restarts the step from the plain start and records that run's residual as the new
- * reference; it then starts plain for the next 2^f - 1 steps, f its run of consecutive
- * fallbacks (at most 5); a kept learned start ends the run.  The iterations of abandoned
- * learned starts count in sim_iteration_stats.
- * With sim_use_graph on (and no grid scene), one learned step is captured as a graph after
- * a first direct step (once per network handle) and replayed n times; the network's
- * parameters are read at replay time, so training between calls needs no recapture. */
+ * sim_step_learned evaluates the network once and then runs n_steps steps (one launch per
+ * launch class): the features of the current state, the network (32 inputs, 7 outputs; see
+ * warmstart.h), lambda^0 = lambda_prev + output (first 6 rows of each interface), and the
+ * beta scales (output 7 is log2 of a scale proposed per interface; each subsystem takes the
+ * mean over its interfaces, rounded to an integer k in [-3, 3], and scale 2^k; see
+ * sim_set_beta_scale).  The first step starts from lambda^0 (z^0 from the previous step),
+ * the others from the previous step's duals; the scales hold for all n_steps (and after,
+ * until changed).  After 10 iterations of the first step a scene compares its residual
+ * max(|x - z|, |dz|) with the one its last plain (previous-step) start had after 10
+ * iterations; if the learned start is behind, the scene restarts the step from the plain
+ * start and records that run's residual as the new reference; it then starts plain for the
+ * next 2^f - 1 calls (f its run of consecutive fallbacks, at most 5); a kept learned start
+ * ends the run.  The iterations of abandoned learned starts count in sim_iteration_stats.
+ * With sim_use_graph on (and no grid scene), the first call with a network and step count
+ * runs directly and captures a graph that later calls replay; the network's parameters
+ * are read at replay time, so training between calls needs no recapture. */
 struct wsn_s;
 int sim_interface_features(sim_t s, float *x_dev);
 int sim_interface_targets(sim_t s, const float *x_dev, float *t_dev, float *mask_dev);

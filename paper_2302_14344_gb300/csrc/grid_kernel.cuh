@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 2) grid_step_kernel(StepParam
         }
         // initial z, u = -lambda; a learned start is checked after 10 iterations against the
         // plain start's residual there, and replaced by the plain start if worse
-        const bool learned_mode = P.lam0 != nullptr;
+        const bool learned_mode = P.lam0 != nullptr && step == 0;    // the launch's first step
         const int skip0 = learned_mode ? vload(&P.learn_skip[2 * sc]) : 0;
         bool learned = learned_mode && skip0 == 0;
         const unsigned long long ref10 = learned_mode ? vload(&P.ref10[sc]) : 0ull;

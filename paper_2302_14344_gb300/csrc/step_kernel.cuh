@@ -1240,9 +1240,10 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, CACHED ? 1 : 2) step_kernel(S
                 __syncthreads();
                 continue;
             }
-            // initial z, u = -lambda; a learned start is checked after 10 iterations against
-            // the plain start's residual there, and replaced by the plain start if worse
-            const bool learned_mode = P.lam0 != nullptr;
+            // initial z, u = -lambda; a learned start (the launch's first step) is checked
+            // after 10 iterations against the plain start's residual there, and replaced by
+            // the plain start if worse
+            const bool learned_mode = P.lam0 != nullptr && step == 0;
             const int skip0 = learned_mode ? P.learn_skip[2 * sc] : 0;
             bool learned = learned_mode && skip0 == 0;
             const unsigned long long ref10 = learned_mode ? P.ref10[sc] : 0ull;

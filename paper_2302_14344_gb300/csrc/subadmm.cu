@@ -116,6 +116,7 @@ struct sim_s {
     cudaGraphExec_t graph_learned = nullptr;   // one learned step, captured for one network
     void *graph_learned_net = nullptr;
     long long graph_learned_ws = -1;           // the network workspace it was captured with
+    int graph_learned_steps = 0;               // and its step count
     cudaStream_t graph_stream = nullptr;   // capture and replay stream when the simulation's
                                            // stream is the legacy default stream
     double *d_pool = nullptr, *d_bodies = nullptr, *d_vhat = nullptr, *d_lam = nullptr;
@@ -1600,12 +1601,13 @@ int sim_step_learned(sim_t s, wsn_t net, int n_steps)
     if ((rc = interface_buffers(s))) return rc;
     ON_DEVICE(s->opt.device);
     const int nif = (int)s->cons.size();
-    StepParams P = step_params(s, 1);
+    StepParams P = step_params(s, n_steps);
     for (const LaunchClass &c : s->classes)
         CK(cudaFuncSetAttribute(kernel_for(s->opt.precision == SIM_MIXED, c.cached, c.split),
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, s->smem_full),
            "shared memory attribute");
-    // one learned step: features, the network, lambda^0, the step's launches
+    // one network evaluation: features, the network, lambda^0 and the beta scales, then the
+    // launches of n_steps steps, the first started from lambda^0
     auto enqueue = [&](cudaStream_t st) -> int {
         if (nif > 0) {
             subadmm::interface_features_kernel<<<grid_of(nif), 128, 0, st>>>(
@@ -1633,11 +1635,7 @@ int sim_step_learned(sim_t s, wsn_t net, int n_steps)
     for (const LaunchClass &c : s->classes) has_grid = has_grid || c.grid;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     CK(cudaStreamIsCapturing(s->stream, &cs), "capture status");
-    if (!s->use_graph || has_grid || cs != cudaStreamCaptureStatusNone) {
-        for (int k = 0; k < n_steps; ++k)
-            if ((rc = enqueue(s->stream))) return rc;
-        return SIM_OK;
-    }
+    if (!s->use_graph || has_grid || cs != cudaStreamCaptureStatusNone) return enqueue(s->stream);
     // graph replay: capture one learned step once per network (the network's workspace is
     // reserved by a first direct step, so the capture allocates nothing)
     cudaStream_t gs = s->stream;
@@ -1645,14 +1643,13 @@ int sim_step_learned(sim_t s, wsn_t net, int n_steps)
         if (!s->graph_stream) CK(cudaStreamCreate(&s->graph_stream), "graph stream");
         gs = s->graph_stream;
     }
-    int k = 0;
-    // the direct first step reserves the network's workspace for this batch
+    // the first call runs directly (it reserves the network's workspace for this batch) and
+    // then captures; later calls with the same network and step count replay
     if (!s->graph_learned || s->graph_learned_net != (void *)net ||
-        s->graph_learned_ws != wsn_workspace_generation(net)) {
+        s->graph_learned_ws != wsn_workspace_generation(net) || s->graph_learned_steps != n_steps) {
         if (s->graph_learned) cudaGraphExecDestroy(s->graph_learned);
         s->graph_learned = nullptr;
         if ((rc = enqueue(s->stream))) return rc;
-        ++k;
         if (gs != s->stream) {
             CK(cudaEventRecord(s->ev_fork, s->stream), "graph fork");
             CK(cudaStreamWaitEvent(gs, s->ev_fork, 0), "graph fork wait");
@@ -1668,11 +1665,14 @@ int sim_step_learned(sim_t s, wsn_t net, int n_steps)
         CK(ei, "graph instantiate");
         s->graph_learned_net = (void *)net;
         s->graph_learned_ws = wsn_workspace_generation(net);
-    } else if (gs != s->stream) {
+        s->graph_learned_steps = n_steps;
+        return SIM_OK;                 // this call's steps ran directly
+    }
+    if (gs != s->stream) {
         CK(cudaEventRecord(s->ev_fork, s->stream), "graph fork");
         CK(cudaStreamWaitEvent(gs, s->ev_fork, 0), "graph fork wait");
     }
-    for (; k < n_steps; ++k) CK(cudaGraphLaunch(s->graph_learned, gs), "graph launch");
+    CK(cudaGraphLaunch(s->graph_learned, gs), "graph launch");
     if (gs != s->stream) {
         CK(cudaEventRecord(s->ev_fork, gs), "graph join");
         CK(cudaStreamWaitEvent(s->stream, s->ev_fork, 0), "graph join wait");

@@ -149,29 +149,35 @@ def train(net: Network, X, T, M, epochs: int = 3, batch: int = 4096, lr: float =
 
 
 def compare(problem, net: Network, steps: int, warmup: int = 5,
-            precision: int = sa.SIM_MIXED, device: int = 0, learned_warmup: int = 0) -> dict:
-    """The same start, stepped with the previous-step warm start and with the learned one:
-    iterations per scene-step of each, fallbacks of the learned start, and the wall time
-    of the device work (CUDA events)."""
+            precision: int = sa.SIM_MIXED, device: int = 0, learned_warmup: int = 0,
+            per_launch: int = 1) -> dict:
+    """The same start, stepped with the previous-step warm start and with the learned one,
+    both in launches of ``per_launch`` steps (graph replay; the learned form evaluates the
+    network once per launch): iterations per scene-step of each, fallbacks of the learned
+    start, and the wall time of the device work (CUDA events).  ``learned_warmup`` launches
+    of each form run untimed first (a changed beta scale refactorises kept blocks once)."""
     import torch
+    if steps % per_launch:
+        raise ValueError("steps must be a multiple of per_launch")
     res = {}
     for name in ("plain", "learned"):
         sim = sa.Simulation(problem, device=device, precision=precision)
         sim.step(warmup)
         sim.use_graph(True)
-        if name == "learned":                   # first (direct) learned step and capture
-            sim.step_learned(net, 1 + learned_warmup)
-        else:
-            sim.step(1 + learned_warmup)
+        for _ in range(1 + learned_warmup):     # the first call captures the graph
+            if name == "learned":
+                sim.step_learned(net, per_launch)
+            else:
+                sim.step(per_launch)
         sim.sync()
         sim.iteration_stats()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        if name == "plain":
-            for _ in range(steps):
-                sim.step(1)
-        else:
-            sim.step_learned(net, steps)
+        for _ in range(steps // per_launch):
+            if name == "plain":
+                sim.step(per_launch)
+            else:
+                sim.step_learned(net, per_launch)
         e1.record()
         torch.cuda.synchronize()
         st = sim.iteration_stats()

@@ -118,7 +118,7 @@ def test_learned_steps_by_graph_replay_equal_direct_ones(mods):
     a = sa.Simulation(p, precision=sa.SIM_MIXED)
     b = sa.Simulation(p, precision=sa.SIM_MIXED)
     b.use_graph(True)
-    for n in (1, 3, 2):
+    for n in (2, 2, 2, 3, 3, 1):     # captures at each new count, replays the repeats
         a.step_learned(net, n)
         b.step_learned(net, n)
     for k in range(6):
@@ -150,3 +150,26 @@ def test_trained_network_against_the_previous_step_warm_start(mods, capsys):
     assert losses[-1] < losses[0]
     assert (res["learned"]["iters_per_scene_step"]
             <= res["plain"]["iters_per_scene_step"] + 10.0)
+
+
+def test_learned_rho_on_uneven_batched_scenes(mods, capsys):
+    """The learned beta scale where the trace rule of Sec. III-D is far from the best one:
+    uneven batched scenes.  Training samples come from a rho search on 128 scenes (each scene
+    in seven copies, beta scaled 2^-3 .. 2^3, the fewest iterations labelling the step);
+    evaluation on 512 other scenes after 100 steps, 20 steps in one launch for both forms:
+    the learned start needs at least 5% fewer iterations per scene-step and leaves fewer
+    scene-steps at the iteration limit."""
+    sa, ws, lr = mods
+    X, T, M = lr.collect_rho(sg.batched(201, n_scenes=128), steps=20, warmup=100)
+    net = lr.init_network(seed=3)
+    losses = lr.train(net, X, T, M, epochs=6)
+    res = lr.compare(sg.batched(202, n_scenes=512), net, steps=20, warmup=100, per_launch=20)
+    pl, le = res["plain"], res["learned"]
+    with capsys.disabled():
+        print(f"\n[learned rho, batched scenes, {X.shape[0]} samples] iterations per scene-step "
+              f"{pl['iters_per_scene_step']:.1f} -> {le['iters_per_scene_step']:.1f}; at the "
+              f"limit {pl['not_converged']} -> {le['not_converged']}; ms per step "
+              f"{pl['ms_per_step']:.2f} -> {le['ms_per_step']:.2f}")
+    assert losses[-1] < losses[0]
+    assert le["iters_per_scene_step"] < 0.95 * pl["iters_per_scene_step"]
+    assert le["not_converged"] < pl["not_converged"]
