@@ -211,9 +211,9 @@ int sim_autotune(sim_t s, int steps, int max_classes, long long *out);
  * sim_step_learned evaluates the network once and then runs n_steps steps (one launch per
  * launch class): the features of the current state, the network (32 inputs, 7 outputs; see
  * warmstart.h), lambda^0 = lambda_prev + output (first 6 rows of each interface), and the
- * beta scales (output 7 is log2 of a scale proposed per interface; each subsystem takes the
- * mean over its interfaces, rounded to an integer k in [-3, 3], and scale 2^k; see
- * sim_set_beta_scale).  The first step starts from lambda^0 (z^0 from the previous step),
+ * beta scales (output 7 is log2 of a scale proposed per interface; every subsystem of a
+ * scene takes scale 2^k, k the mean over the scene's interfaces rounded to an integer in
+ * [-3, 3]; see sim_set_beta_scale).  The first step starts from lambda^0 (z^0 from the previous step),
  * the others from the previous step's duals; the scales hold for all n_steps (and after,
  * until changed).  After 10 iterations of the first step a scene compares its residual
  * max(|x - z|, |dz|) with the one its last plain (previous-step) start had after 10

@@ -150,34 +150,32 @@ __global__ void learned_duals_kernel(const StepParams P, const int *pub2dev, con
 }
 
 // learned beta scale, accumulation: every interface adds the network's seventh output (log2
-// of the scale it proposes) to each of its sides' subsystem sums; acc holds nsub sums, then
-// nsub counts, zeroed before
-__global__ void learned_beta_accumulate_kernel(const StepParams P, const int *pub2dev,
-                                               const int *con_scene, int nif, const float *Y,
-                                               float *acc, int nsub)
+// of the scale it proposes) to its scene's sum; acc holds nscenes sums, then nscenes counts,
+// zeroed before
+__global__ void learned_beta_accumulate_kernel(const int *con_scene, int nif, const int *pub2dev,
+                                               const float *Y, float *acc, int nscenes)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nif; i += gridDim.x * blockDim.x) {
-        const int j = pub2dev[i];
-        const ConDesc &c = P.cons[j];
-        const int sub0 = P.scenes[con_scene[j]].sub0;
+        const int sc = con_scene[pub2dev[i]];
         const float y = Y[(size_t)i * kDualOut + kDualRows];
-        for (int q = 0; q < c.ns; ++q) {
-            atomicAdd(&acc[sub0 + c.sub[q]], isfinite(y) ? y : 0.0f);
-            atomicAdd(&acc[nsub + sub0 + c.sub[q]], 1.0f);
-        }
+        atomicAdd(&acc[sc], isfinite(y) ? y : 0.0f);
+        atomicAdd(&acc[nscenes + sc], 1.0f);
     }
 }
 
-// learned beta scale per subsystem: 2^k with k the mean proposal of its interfaces rounded to
-// an integer in [-3, 3] (whole powers of two, so a kept factor is refactorised only when the
-// proposal moves by a whole step); 1 for a subsystem without interfaces
-__global__ void learned_beta_scale_kernel(const float *acc, int nsub, double *scale)
+// learned beta scale of every subsystem of a scene: 2^k with k the mean proposal of the
+// scene's interfaces rounded to an integer in [-3, 3] (whole powers of two, so a kept factor
+// is refactorised only when the proposal moves by a whole step; one scale per scene, as the
+// rho search that labels the training data picks one per scene); 1 without interfaces
+__global__ void learned_beta_scale_kernel(const SceneDesc *scenes, const float *acc, int nscenes,
+                                          double *scale)
 {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nsub; i += gridDim.x * blockDim.x) {
-        const float n = acc[nsub + i];
-        float k = n > 0.0f ? rintf(acc[i] / n) : 0.0f;
+    for (int sc = blockIdx.x * blockDim.x + threadIdx.x; sc < nscenes; sc += gridDim.x * blockDim.x) {
+        const float n = acc[nscenes + sc];
+        float k = n > 0.0f ? rintf(acc[sc] / n) : 0.0f;
         k = fminf(3.0f, fmaxf(-3.0f, k));
-        scale[i] = exp2((double)k);
+        const double s = exp2((double)k);
+        for (int i = 0; i < scenes[sc].nsub; ++i) scale[scenes[sc].sub0 + i] = s;
     }
 }
 

@@ -129,7 +129,7 @@ struct sim_s {
     int *d_subflag = nullptr;      // per subsystem: kept-factor flags
     double *d_beta_scale = nullptr;   // per subsystem: beta = scale x (trace rule or rho)
     double *d_beta_used = nullptr;    // per subsystem: the scale of the kept factor
-    float *d_bacc = nullptr;          // learned beta: per-subsystem sums and counts
+    float *d_bacc = nullptr;          // learned beta: per-scene sums and counts
     long long nnodes = 0;
     long long work_bytes = 0;
     size_t pool_size = 0;
@@ -834,7 +834,7 @@ int finalize(sim_t s)
             const std::vector<double> ones(std::max(1, nsubs), 1.0);
             if (cudaMalloc((void **)&s->d_beta_scale, ones.size() * sizeof(double)) != cudaSuccess ||
                 cudaMalloc((void **)&s->d_beta_used, ones.size() * sizeof(double)) != cudaSuccess ||
-                cudaMalloc((void **)&s->d_bacc, 2 * ones.size() * sizeof(float)) != cudaSuccess)
+                cudaMalloc((void **)&s->d_bacc, 2 * std::max<size_t>(1, s->nscenes) * sizeof(float)) != cudaSuccess)
                 return fail(s, SIM_ENOMEM, "cudaMalloc beta scale");
             CK(cudaMemcpy(s->d_beta_scale, ones.data(), ones.size() * sizeof(double),
                           cudaMemcpyHostToDevice), "beta scale");
@@ -1618,13 +1618,13 @@ int sim_step_learned(sim_t s, wsn_t net, int n_steps)
             subadmm::learned_duals_kernel<<<grid_of(nif), 128, 0, st>>>(
                 P, s->d_pub2dev, s->d_con_scene, nif, s->d_netout, s->d_lam0);
             CK(cudaGetLastError(), "learned duals launch");
-            const int nsub = (int)s->sdesc.size();
-            CK(cudaMemsetAsync(s->d_bacc, 0, 2 * sizeof(float) * nsub, st), "learned beta clear");
+            const int nsc = s->nscenes;
+            CK(cudaMemsetAsync(s->d_bacc, 0, 2 * sizeof(float) * nsc, st), "learned beta clear");
             subadmm::learned_beta_accumulate_kernel<<<grid_of(nif), 128, 0, st>>>(
-                P, s->d_pub2dev, s->d_con_scene, nif, s->d_netout, s->d_bacc, nsub);
+                s->d_con_scene, nif, s->d_pub2dev, s->d_netout, s->d_bacc, nsc);
             CK(cudaGetLastError(), "learned beta launch");
-            subadmm::learned_beta_scale_kernel<<<grid_of(nsub), 128, 0, st>>>(
-                s->d_bacc, nsub, s->d_beta_scale);
+            subadmm::learned_beta_scale_kernel<<<grid_of(nsc), 128, 0, st>>>(
+                s->d_scenes, s->d_bacc, nsc, s->d_beta_scale);
             CK(cudaGetLastError(), "learned beta scale launch");
         }
         StepParams Q = P;
