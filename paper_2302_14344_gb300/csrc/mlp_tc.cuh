@@ -170,7 +170,7 @@ mlp_fused_kernel(const __grid_constant__ CUtensorMap m0, const __grid_constant__
     unsigned char *act[2] = {smem, smem + kMlpActBytes};
     unsigned char *stage[2] = {smem + 2 * kMlpActBytes, smem + 2 * kMlpActBytes + kMlpStageBytes};
     const CUtensorMap *maps[4] = {&m0, &m1, &m2, &m3};
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tid = threadIdx.x, warp = tid >> 5;
 
     if (tid == 0) {
         for (int s = 0; s < 2; ++s) {

@@ -488,16 +488,25 @@ __device__ void env_forward_vec(const F *LT, F *y, int n, int ldy, const int *la
     }
 }
 
-// D = W^T W over the m columns of W (rows ldd apart, padded with zeros to mp); W column t
-// is zero above row jlo[t].  A lane computes a 4 x 4 block of D (lower triangle of blocks,
-// mirrored): per row p of W it loads 4 + 4 values for 16 FMAs.  ldw is a multiple of 4 and
-// the columns of W past m are zero, so a block never reads past its row of W.
-template <typename F>
-__device__ void form_D(const F *W, int n, int m, int mp, int ldd, int ldw, const int *jlo, F *D)
+// One work item of the map D = W^T W, c = W^T g of a subsystem (W = L^-1 [J^T b], column m
+// is g; W column t is zero above row jlo[t]; D rows ldd apart, zero-padded from m to mp), for
+// items spread over many threads: item k < nb (nb + 1) / 2 is the 4 x 4 block k of D's lower
+// triangle (mirrored; per row p of W a thread loads 4 + 4 values for 16 FMAs); item
+// nb (nb + 1) / 2 + q gives c and the zero padding of D for rows 4q .. 4q + 3.  map_items()
+// is the item count of a subsystem of m side-rows.
+__device__ __forceinline__ int map_items(int m)
 {
-    const int lane = threadIdx.x & 31;
     const int nb = (m + 3) / 4;
-    for (int k = lane; k < nb * (nb + 1) / 2; k += 32) {
+    return nb * (nb + 1) / 2 + nb;
+}
+
+template <typename F>
+__device__ void map_item(const F *W, int n, int m, int mp, int ldd, int ldw, const int *jlo,
+                         F *D, F *cc, int k, bool with_D)
+{
+    const int nb = (m + 3) / 4, ntri = nb * (nb + 1) / 2;
+    if (k < ntri) {
+        if (!with_D) return;
         int bi, bj;
         tri_index(k, bi, bj);
         const int r0 = 4 * bi, s0 = 4 * bj;
@@ -532,21 +541,10 @@ __device__ void form_D(const F *W, int n, int m, int mp, int ldd, int ldw, const
                 }
             }
         }
+        return;
     }
-    if (mp > m) {
-        for (int q = lane; q < m * (mp - m); q += 32) {
-            const int r = q / (mp - m);
-            D[r * ldd + m + (q - r * (mp - m))] = (F)0;
-        }
-    }
-}
-
-// c = W^T g, g = column m of W
-template <typename F>
-__device__ void form_c(const F *W, int n, int m, int ldw, const int *jlo, F *cc)
-{
-    const int lane = threadIdx.x & 31;
-    for (int r = lane; r < m; r += 32) {
+    const int q0 = 4 * (k - ntri);
+    for (int r = q0; r < q0 + 4 && r < m; ++r) {
         F a0 = (F)0, a1 = (F)0;
         int p = jlo[r];
         for (; p + 1 < n; p += 2) {
@@ -555,6 +553,8 @@ __device__ void form_c(const F *W, int n, int m, int ldw, const int *jlo, F *cc)
         }
         if (p < n) a0 += W[p * ldw + r] * W[p * ldw + m];
         cc[r] = a0 + a1;
+        if (with_D)
+            for (int t = m; t < mp; ++t) D[r * ldd + t] = (F)0;
     }
 }
 
@@ -677,11 +677,11 @@ __device__ long long scene_setup(const StepParams &P, const SceneDesc &S, const 
     for (int i = d.warp; i < S.nsub; i += d.nwarps) {
         const SubDesc &u = P.subs[S.sub0 + i];
         const int gsub = S.sub0 + i;
-        // W's leading dimension: m + 1 columns rounded up to 4 (form_D reads 4-column blocks)
-        const int n = u.n, m = u.m, mp = u.mpad, ldw = (m + 1 + 3) / 4 * 4;
+        // W's leading dimension: m + 1 columns rounded up to 4 (map_item reads 4-column blocks)
+        const int n = u.n, m = u.m, ldw = (m + 1 + 3) / 4 * 4;
         const SubEnv e = sub_env(P, u);
         double *J = sdb + u.od_J, *K = sdb + u.od_L, *b = sdb + u.od_b, *idg = sdb + u.od_id;
-        T *LT = stb + u.ot_L, *W = stb + u.ot_W, *D = htb + u.ot_D, *cc = htb + u.ot_c;
+        T *LT = stb + u.ot_L, *W = stb + u.ot_W;
         if (factor_kept(P, S, u, gsub, step)) {
             // constant K_i: only g = L^-1 b and c change (and D when the launch lost it)
             if (step == 0 && lane == 0) {
@@ -691,8 +691,8 @@ __device__ long long scene_setup(const StepParams &P, const SceneDesc &S, const 
             for (int p = lane; p < n; p += 32) W[p * ldw + m] = (T)b[p];
             __syncwarp();
             env_forward_vec<T>(LT, W + m, n, ldw, e.lastr);
-            if (step == 0 && !S.hot_global) form_D<T>(W, n, m, mp, u.ldd, ldw, e.jlo, D);
-            form_c<T>(W, n, m, ldw, e.jlo, cc);
+            // c (and D if the launch lost it) below, over every thread of the scene
+            if (lane == 0) P.pending[gsub] = (step == 0 && !S.hot_global) ? 2 : 1;
             __syncwarp();
             continue;
         }
@@ -762,6 +762,7 @@ __device__ long long scene_setup(const StepParams &P, const SceneDesc &S, const 
             ok = env_cholesky<T, true>(LT, n, e, nullptr);
         }
         if (u.cst && lane == 0) P.subflag[gsub] = ok ? (1 | (stiff ? 2 : 0)) : 0;
+        if (lane == 0) P.pending[gsub] = 0;
         if (!ok) {
             if (lane == 0) *s_status = ST_NOTSPD;
             continue;
@@ -776,9 +777,34 @@ __device__ long long scene_setup(const StepParams &P, const SceneDesc &S, const 
                                                    // the tensor-core Gram kernel
         env_forward_cols<T>(LT, W, n, ldw, m + 1, e.env);
         __syncwarp();
-        form_D<T>(W, n, m, mp, u.ldd, ldw, e.jlo, D);
-        form_c<T>(W, n, m, ldw, e.jlo, cc);
+        if (lane == 0) P.pending[gsub] = 2;           // D and c below
         __syncwarp();
+    }
+    d.sync();
+    // the maps D = W^T W and c = W^T g of this step (pending 2: D and c, 1: c only), their
+    // items (4 x 4 blocks of D, 4 rows of c) spread over every thread of the scene rather
+    // than one warp per subsystem, which left a block waiting on its largest subsystem
+    {
+        int total = 0;
+        for (int i = 0; i < S.nsub; ++i) {
+            const SubDesc &u = P.subs[S.sub0 + i];
+            if (P.pending[S.sub0 + i] && !(P.tc_phase == 1 && u.tc)) total += map_items(u.m);
+        }
+        for (int w = d.tid; w < total; w += d.nthreads) {
+            int k = w, i = 0;
+            for (; i < S.nsub; ++i) {
+                const SubDesc &u = P.subs[S.sub0 + i];
+                if (!P.pending[S.sub0 + i] || (P.tc_phase == 1 && u.tc)) continue;
+                const int c = map_items(u.m);
+                if (k < c) break;
+                k -= c;
+            }
+            const SubDesc &u = P.subs[S.sub0 + i];
+            const int ldw = (u.m + 1 + 3) / 4 * 4;
+            const SubEnv e = sub_env(P, u);
+            map_item<T>(stb + u.ot_W, u.n, u.m, u.mpad, u.ldd, ldw, e.jlo, htb + u.ot_D,
+                        htb + u.ot_c, k, P.pending[S.sub0 + i] == 2);
+        }
     }
     d.sync();
     if (P.tc_phase == 1) {

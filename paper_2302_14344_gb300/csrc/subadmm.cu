@@ -127,6 +127,7 @@ struct sim_s {
     double *d_nodes = nullptr;     // node states of linear blocks
     int *d_ipool = nullptr;        // integer constant data
     int *d_subflag = nullptr;      // per subsystem: kept-factor flags
+    int *d_pending = nullptr;      // per subsystem: map formation of the current step
     double *d_beta_scale = nullptr;   // per subsystem: beta = scale x (trace rule or rho)
     double *d_beta_used = nullptr;    // per subsystem: the scale of the kept factor
     float *d_bacc = nullptr;          // learned beta: per-scene sums and counts
@@ -238,6 +239,8 @@ void free_device(sim_t s)
     s->d_work = nullptr;
     cudaFree(s->d_nodes); cudaFree(s->d_ipool); cudaFree(s->d_subflag);
     cudaFree(s->d_beta_scale); cudaFree(s->d_beta_used); cudaFree(s->d_bacc);
+    cudaFree(s->d_pending);
+    s->d_pending = nullptr;
     s->d_beta_scale = nullptr; s->d_beta_used = nullptr; s->d_bacc = nullptr;
     cudaFree(s->d_scene_ids);
     s->d_scene_ids = nullptr;
@@ -841,6 +844,9 @@ int finalize(sim_t s)
             CK(cudaMemcpy(s->d_beta_used, ones.data(), ones.size() * sizeof(double),
                           cudaMemcpyHostToDevice), "beta scale");
         }
+        if (cudaMalloc((void **)&s->d_pending, std::max(1, nsubs) * sizeof(int)) != cudaSuccess)
+            return fail(s, SIM_ENOMEM, "cudaMalloc map flags");
+        CK(cudaMemset(s->d_pending, 0, std::max(1, nsubs) * sizeof(int)), "map flags");
         cudaError_t e = cudaMalloc((void **)&s->d_subflag, std::max(1, nsubs) * sizeof(int));
         if (e != cudaSuccess) return fail(s, SIM_ENOMEM, "cudaMalloc subsystem flags");
         CK(cudaMemsetAsync(s->d_subflag, 0, std::max(1, nsubs) * sizeof(int), s->stream), "memset flags");
@@ -1137,6 +1143,7 @@ StepParams step_params(const sim_t s, int n_steps)
     P.nodes = s->d_nodes;
     P.ipool = s->d_ipool;
     P.subflag = s->d_subflag;
+    P.pending = s->d_pending;
     P.beta_scale = s->d_beta_scale;
     P.beta_used = s->d_beta_used;
     P.keep_factors = s->keep_factors;
