@@ -631,6 +631,90 @@ def gripper(anchor_w: np.ndarray, reach: float = 0.12, rho: float = 1000.0):
     return bodies, joints, paddles
 
 
+def _arm(gs: int, anchor_w: np.ndarray, kp: float, kd: float):
+    """The 7-R arm stand-in of ``gripper`` as one rigid subsystem (index ``gs``) whose
+    paddles hang down to ``anchor_w``: the subsystem, its revolute joints and PD drives
+    (holding the initial pose), and the first paddle's body index."""
+    bodies, joints, paddles = gripper(anchor_w)
+    ifs = []
+    ex = np.array([1.0, 0, 0])
+    for (pa, ch, jw, ax) in joints:
+        ref = np.array([0.0, 0, 1.0]) if abs(ax[2]) < 0.5 else ex
+        bc = bodies[ch]
+        if pa < 0:
+            ifs.append(JointIf(REVOLUTE, a=(gs, ch), b=None, anchor_a=jw - bc.p, anchor_b=jw.copy(),
+                               axis_a=ax.copy(), axis_b=ax.copy(), ref_a=ref.copy(),
+                               ref_b=ref.copy()))
+            continue
+        bp = bodies[pa]
+        ifs.append(JointIf(REVOLUTE, a=(gs, pa), b=(gs, ch), anchor_a=jw - bp.p,
+                           anchor_b=jw - bc.p, axis_a=ax.copy(), axis_b=ax.copy(),
+                           ref_a=ref.copy(), ref_b=ref.copy()))
+        ifs.append(JointIf(ANGLE_PD, a=(gs, pa), b=(gs, ch), axis_a=ax.copy(), axis_b=ax.copy(),
+                           ref_a=ref.copy(), ref_b=ref.copy(), kp=kp, kd=kd, target=0.0))
+    return RigidSub(bodies), ifs, paddles[0]
+
+
+def cable(seed: int = 0, segments: int = 640, per_sub: int = 4, seg_len: float = 0.01,
+          radius: float = 0.005, rho: float = 1200.0, bend_kp: float = 2e-3,
+          twist_kp: float = 1e-3, damping: float = 2e-5, mu: float = 0.5, arms: bool = True,
+          h: float = 1e-3, tol_primal: float = 1e-6, max_iters: int = 1000,
+          warm: str = "prev") -> Problem:
+    """A cable held by two arms, shaped like the paper's cable scene (Sec. IV-A: a Cosserat
+    cable handled by two manipulators, 162 subsystems): ``segments`` rigid capsule segments
+    along x, lying on the plane z = 0, joined end to end by ball joints, with the rod's
+    bending (two axes normal to the segment) and twist (about it) as PD soft rows holding the
+    straight rest shape -- a discrete elastic rod in maximal coordinates.  ``per_sub``
+    consecutive segments form a subsystem; each segment has a speculative contact with the
+    plane (friction mu).  With ``arms`` two 7-R arm stand-ins (as in the FEM beam scene) hold
+    the cable's ends by ball joints between a paddle and the end segment.  The seed draws
+    small initial lateral velocities of the segments (up to 2 cm/s).  The arms' and the
+    cable's models are stand-ins: the paper's manipulator and cable models are not public."""
+    rng = np.random.default_rng(seed)
+    m = np.pi * radius ** 2 * seg_len * rho
+    I = np.array([0.5 * m * radius ** 2, m * (3 * radius ** 2 + seg_len ** 2) / 12.0,
+                  m * (3 * radius ** 2 + seg_len ** 2) / 12.0])
+    q0 = np.array([1.0, 0.0, 0.0, 0.0])
+    bodies = []
+    for k in range(segments):
+        c = np.array([(k + 0.5) * seg_len, 0.0, radius])
+        v = np.array([0.0, rng.uniform(-0.02, 0.02), rng.uniform(0.0, 0.02)])
+        bodies.append(Body(m, I.copy(), c, q0.copy(), v, np.zeros(3)))
+    if segments % per_sub:
+        raise ValueError("segments must be a multiple of per_sub")
+    nsub = segments // per_sub
+    subs = [RigidSub(bodies[s * per_sub:(s + 1) * per_sub]) for s in range(nsub)]
+
+    def ref(k):
+        return (k // per_sub, k % per_sub)
+
+    ex, ey, ez = np.eye(3)
+    half = np.array([seg_len / 2, 0.0, 0.0])
+    ifs = []
+    for k in range(1, segments):
+        a, b = ref(k - 1), ref(k)
+        ifs.append(JointIf(BALL, a=a, b=b, anchor_a=half.copy(), anchor_b=-half))
+        for axis, rf, kp in ((ey, ex, bend_kp), (ez, ex, bend_kp), (ex, ey, twist_kp)):
+            ifs.append(JointIf(ANGLE_PD, a=a, b=b, axis_a=axis.copy(), axis_b=axis.copy(),
+                               ref_a=rf.copy(), ref_b=rf.copy(), kp=kp, kd=damping / seg_len,
+                               target=0.0))
+    for k in range(segments):
+        ifs.append(JointIf(PLANE_CONTACT, a=ref(k), anchor_a=np.array([0.0, 0.0, -radius]),
+                           plane_z=0.0, mu=mu))
+    if arms:
+        for end, k in ((0, 0), (1, segments - 1)):
+            gs = len(subs)
+            tip = bodies[k].p + (half if end else -half)
+            arm, arm_ifs, paddle = _arm(gs, tip, kp=50.0, kd=1.0)
+            subs.append(arm)
+            ifs.extend(arm_ifs)
+            pb = arm.bodies[paddle]
+            ifs.append(JointIf(BALL, a=(gs, paddle), b=ref(k), anchor_a=tip - pb.p,
+                               anchor_b=(half if end else -half)))
+    opts = Options(h=h, beta_mode="trace", warm=warm, tol_primal=tol_primal, max_iters=max_iters)
+    return Problem([Scene(subs, ifs)], opts, name=f"cable{segments}")
+
+
 def fem_beam(seed: int = 0, ny: int = 10, nz: int = 10, planes: int = 137, slabs: int = 64,
              length: float = 0.5, width: float = 0.05, height: float = 0.05, E: float = 1e5,
              nu: float = 0.45, rho: float = 1000.0, mu: float = 0.5, drop: float = 0.002,

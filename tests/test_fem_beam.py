@@ -107,3 +107,22 @@ def test_tet_count_of_the_full_beam():
     for k in ks:
         total += 6 * 9 * 9 * (k - 1)
     assert total == 66096
+
+
+def test_cable_scene_shape():
+    """The cable workload: 640 segments in 160 subsystems of 4 plus two arms (162
+    subsystems, 3,840 cable DOF), a ball joint and three PD rows between neighbouring
+    segments, a plane contact per segment, and the straight rest shape (every PD target and
+    every joint anchor pair coincide at t = 0)."""
+    p = sg.cable(0)
+    sc = p.scenes[0]
+    assert len(sc.subs) == 162
+    assert sum(s.n for s in sc.subs[:160]) == 3840
+    kinds = [f.kind for f in sc.ifs]
+    assert kinds.count(sg.PLANE_CONTACT) == 640
+    assert kinds.count(sg.ANGLE_PD) >= 3 * 639
+    for f in sc.ifs:
+        if f.kind == sg.BALL and f.b is not None and f.a[0] < 160 and f.b[0] < 160:
+            ba = sc.subs[f.a[0]].bodies[f.a[1]]
+            bb = sc.subs[f.b[0]].bodies[f.b[1]]
+            assert np.allclose(ba.p + f.anchor_a, bb.p + f.anchor_b, atol=1e-12)

@@ -47,3 +47,20 @@ def test_full_system_admm_generic_converged(sa):
         assert r["converged"] == ro["converged"]
         assert abs(r["iters"] - ro["iters"]) <= 1
         assert rel(sim.scene_vhat(k), o.vhat_all()) < 1e-6
+
+
+@pytest.mark.parametrize("grid", [False, True])
+def test_cable_fp64_fixed_iterations(sa, grid):
+    """The cable scene (discrete rod: ball joints and PD bending / twist rows between
+    segments, plane contacts, two arm stand-ins holding the ends), shortened to 24 segments in
+    6 subsystems: FP64 at a fixed 60 iterations per step against the oracle, block and grid
+    kernel."""
+    p = sg.cable(0, segments=24, tol_primal=-1, max_iters=60)
+    orcs = [oracle.OracleScene(sc, p.options) for sc in p.scenes]
+    sim = sa.Simulation(p, grid_side_rows=1 if grid else None)
+    for _ in range(3):
+        sim.step(1)
+        for o in orcs:
+            o.step()
+        assert rel(sim.scene_vhat(0), orcs[0].vhat_all()) < 1e-9
+        assert rel(sim.scene_bodies(0)[:, 4:], orcs[0].bodies_all()[:, 4:]) < 1e-9
