@@ -79,6 +79,8 @@ def lib(openmp: bool = False):
                 "orc_set_generic": (None, [VP, C.c_int, PD, PD]),
                 "orc_set_warm": (None, [VP, C.c_int, PD, PD]),
                 "orc_set_beta_scale": (None, [VP, C.c_int, D]),
+                "orc_set_corot": (C.c_int, [VP, C.c_int, C.c_int, PI, PD]),
+                "orc_elastic": (None, [VP, C.c_int, PD, PD]),
                 "orc_residuals": (None, [VP, PD]),
                 "orc_chol_solve": (C.c_int, [C.c_int, PD, PD, PD]),
                 "orc_project": (None, [C.c_int, C.c_int, C.c_int, PD, PD, PD, D, D, D, PD]),
@@ -134,6 +136,12 @@ class OracleScene:
                 data = _f64(np.concatenate([sub.mass, sub.K_dense().ravel(), sub.f, sub.X0,
                                             sub.x, sub.v]))
                 rc = L.orc_add_linear(self.h, sub.nodes, _p(data))
+                if rc >= 0 and getattr(sub, "corot", False):
+                    tets = np.ascontiguousarray(np.asarray(sub.tets, dtype=np.int32).ravel())
+                    Ke = _f64(np.asarray(sub.Ke).ravel())
+                    if L.orc_set_corot(self.h, rc, len(sub.tets), tets.ctypes.data_as(PI),
+                                       _p(Ke)) < 0:
+                        raise ValueError("oracle rejected the co-rotational elements")
             else:
                 A, b = _f64(sub.A), _f64(sub.b)
                 rc = L.orc_add_generic(self.h, sub.n, _p(A), _p(b))
@@ -267,6 +275,16 @@ class OracleScene:
     def set_body(self, i, k, rec):
         rec = _f64(rec)
         self.L.orc_set_body(self.h, i, k, _p(rec))
+
+    def elastic(self, i):
+        """(elastic force at the current positions, stiffness) of linear block i."""
+        n = self.n(i)
+        f, K = np.zeros(n), np.zeros((n, n))
+        self.L.orc_elastic(self.h, i, _p(f), _p(K))
+        return f, K
+
+    def set_node(self, i, k, rec):
+        self.L.orc_set_node(self.h, i, k, _p(_f64(rec)))
 
     def set_beta_scale(self, i, scale: float):
         """beta_i = scale x (trace rule or rho) from the next step on."""

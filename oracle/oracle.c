@@ -72,6 +72,9 @@ typedef struct {
     double *rhs;
     double beta;
     double beta_scale;         /* multiplies the trace rule's (or the fixed) beta; 1 default */
+    int ne;                    /* co-rotational linear block: elements (0: linear model) */
+    int *tets;                 /* 4 node indices per element */
+    double *Ke;                /* rest stiffness per element (12 x 12, row-major) */
 } sub_t;
 
 typedef struct {
@@ -244,6 +247,44 @@ int orc_add_rigid(orc_scene *S, int nb, const double *rec)
 
 /* linear elastic block of nn nodes (3 DOF each): data = mass (nn), K (n x n row-major),
  * f (n), rest positions X0 (n), positions x (n), velocities v (n), n = 3 nn */
+static void assemble_corot(orc_scene *S, sub_t *u);
+
+/* Makes linear block i co-rotational: ne elements of 4 node indices (tets) with their rest
+   stiffness matrices (Ke, 144 per element); its K and elastic force are assembled from them
+   at every step (assemble_corot) instead of from the constant K. */
+int orc_set_corot(orc_scene *S, int i, int ne, const int *tets, const double *Ke)
+{
+    sub_t *u = &S->subs[i];
+    if (u->kind != SUB_LINEAR || ne < 1) return -1;
+    for (int q = 0; q < 4 * ne; q++)
+        if (tets[q] < 0 || tets[q] >= u->nb) return -1;
+    u->ne = ne;
+    u->tets = (int *)xcalloc((size_t)4 * ne, sizeof(int));
+    u->Ke = (double *)xcalloc((size_t)144 * ne, sizeof(double));
+    memcpy(u->tets, tets, sizeof(int) * 4 * (size_t)ne);
+    memcpy(u->Ke, Ke, sizeof(double) * 144 * (size_t)ne);
+    return 0;
+}
+
+/* Elastic force of a linear block at its current positions (n doubles) and its stiffness
+   (n x n): the assembly's own terms, for tests.  */
+void orc_elastic(orc_scene *S, int i, double *f, double *K)
+{
+    sub_t *u = &S->subs[i];
+    int n = u->n;
+    if (u->ne > 0) {
+        assemble_corot(S, u);
+        memcpy(f, u->rhs, sizeof(double) * n);
+    } else {
+        for (int p = 0; p < n; p++) {
+            double kx = 0.0;
+            for (int q = 0; q < n; q++) kx += u->Kel[p * n + q] * (u->x[q] - u->X0[q]);
+            f[p] = -kx;
+        }
+    }
+    memcpy(K, u->Kel, sizeof(double) * (size_t)n * n);
+}
+
 int orc_add_linear(orc_scene *S, int nn, const double *data)
 {
     if (nn <= 0) return -1;
@@ -387,8 +428,124 @@ static void assemble_rigid(orc_scene *S, sub_t *u)
 
 /* Linear elastic block (Eq. ddyn with the elastic force at the midpoint):
  * A = (2/h) M + (h/2) K ;  b = (2/h) M v_k - K (x_k - X0) + f + M g */
+/* Rotation part of F (polar decomposition F = R S, S symmetric positive definite) by
+   Newton's iteration R <- (R + R^-T) / 2 from R = F (Higham), to convergence. */
+static void polar_rotation(const double F[9], double R[9])
+{
+    memcpy(R, F, 9 * sizeof(double));
+    for (int it = 0; it < 60; it++) {
+        /* R^-T = cofactor(R) / det(R) */
+        double c[9];
+        c[0] = R[4] * R[8] - R[5] * R[7];
+        c[1] = R[5] * R[6] - R[3] * R[8];
+        c[2] = R[3] * R[7] - R[4] * R[6];
+        c[3] = R[2] * R[7] - R[1] * R[8];
+        c[4] = R[0] * R[8] - R[2] * R[6];
+        c[5] = R[1] * R[6] - R[0] * R[7];
+        c[6] = R[1] * R[5] - R[2] * R[4];
+        c[7] = R[2] * R[3] - R[0] * R[5];
+        c[8] = R[0] * R[4] - R[1] * R[3];
+        double det = R[0] * c[0] + R[1] * c[1] + R[2] * c[2];
+        double d = 0.0, nrm = 0.0;
+        for (int k = 0; k < 9; k++) {
+            double nk = 0.5 * (R[k] + c[k] / det);
+            d += (nk - R[k]) * (nk - R[k]);
+            nrm += nk * nk;
+            R[k] = nk;
+        }
+        if (d <= 1e-30 * nrm) break;
+    }
+}
+
+/* Co-rotational linear elasticity (the paper's beam model, Sec. IV-A): per element the
+   rotation R of its deformation gradient F = D_s D_m^-1 (edge matrices of the current and
+   rest positions), the rotated stiffness R K_e R^T (R on each node's 3 x 3 block) and the
+   elastic force -R K_e (R^T x_e - X_e); the stiffness is that of the step's start, like the
+   linear block's (A = (2/h) M + (h/2) K, b = (2/h) M v_k + f_el + f + M g). */
+static void assemble_corot(orc_scene *S, sub_t *u)
+{
+    int n = u->n;
+    double c2h = 2.0 / S->h;
+    memset(u->Kel, 0, sizeof(double) * (size_t)n * n);
+    double *fel = u->rhs;                     /* scratch: elastic force (n) */
+    memset(fel, 0, sizeof(double) * n);
+    for (int e = 0; e < u->ne; e++) {
+        const int *t = u->tets + 4 * e;
+        const double *K = u->Ke + 144 * e;
+        double Dm[9], Ds[9];                  /* columns: node k - node 0, k = 1..3 */
+        for (int k = 0; k < 3; k++)
+            for (int d = 0; d < 3; d++) {
+                Dm[3 * d + k] = u->X0[3 * t[k + 1] + d] - u->X0[3 * t[0] + d];
+                Ds[3 * d + k] = u->x[3 * t[k + 1] + d] - u->x[3 * t[0] + d];
+            }
+        /* F = Ds Dm^-1 */
+        double c[9], Mi[9], F[9], R[9];
+        c[0] = Dm[4] * Dm[8] - Dm[5] * Dm[7];
+        c[1] = Dm[5] * Dm[6] - Dm[3] * Dm[8];
+        c[2] = Dm[3] * Dm[7] - Dm[4] * Dm[6];
+        c[3] = Dm[2] * Dm[7] - Dm[1] * Dm[8];
+        c[4] = Dm[0] * Dm[8] - Dm[2] * Dm[6];
+        c[5] = Dm[1] * Dm[6] - Dm[0] * Dm[7];
+        c[6] = Dm[1] * Dm[5] - Dm[2] * Dm[4];
+        c[7] = Dm[2] * Dm[3] - Dm[0] * Dm[5];
+        c[8] = Dm[0] * Dm[4] - Dm[1] * Dm[3];
+        double det = Dm[0] * c[0] + Dm[1] * c[1] + Dm[2] * c[2];
+        for (int a = 0; a < 3; a++)                 /* inverse = cofactor^T / det */
+            for (int b = 0; b < 3; b++) Mi[3 * a + b] = c[3 * b + a] / det;
+        for (int a = 0; a < 3; a++)
+            for (int b = 0; b < 3; b++) {
+                double acc = 0.0;
+                for (int k = 0; k < 3; k++) acc += Ds[3 * a + k] * Mi[3 * k + b];
+                F[3 * a + b] = acc;
+            }
+        polar_rotation(F, R);
+        /* w = R^T x_e - X_e ; g = K w ; force -R g */
+        double w[12], g[12];
+        for (int a = 0; a < 4; a++)
+            for (int d = 0; d < 3; d++) {
+                double acc = 0.0;
+                for (int k = 0; k < 3; k++) acc += R[3 * k + d] * u->x[3 * t[a] + k];
+                w[3 * a + d] = acc - u->X0[3 * t[a] + d];
+            }
+        for (int i = 0; i < 12; i++) {
+            double acc = 0.0;
+            for (int j = 0; j < 12; j++) acc += K[12 * i + j] * w[j];
+            g[i] = acc;
+        }
+        for (int a = 0; a < 4; a++)
+            for (int d = 0; d < 3; d++) {
+                double acc = 0.0;
+                for (int k = 0; k < 3; k++) acc += R[3 * d + k] * g[3 * a + k];
+                fel[3 * t[a] + d] -= acc;
+            }
+        /* Kel block (a, b) += R K_ab R^T */
+        for (int a = 0; a < 4; a++)
+            for (int b = 0; b < 4; b++) {
+                double T[9];
+                for (int i = 0; i < 3; i++)
+                    for (int j = 0; j < 3; j++) {
+                        double acc = 0.0;
+                        for (int k = 0; k < 3; k++) acc += R[3 * i + k] * K[12 * (3 * a + k) + 3 * b + j];
+                        T[3 * i + j] = acc;
+                    }
+                for (int i = 0; i < 3; i++)
+                    for (int j = 0; j < 3; j++) {
+                        double acc = 0.0;
+                        for (int k = 0; k < 3; k++) acc += T[3 * i + k] * R[3 * j + k];
+                        u->Kel[(size_t)(3 * t[a] + i) * n + 3 * t[b] + j] += acc;
+                    }
+            }
+    }
+    for (int p = 0; p < n; p++) {
+        for (int q = 0; q < n; q++) u->A[p * n + q] = 0.5 * S->h * u->Kel[p * n + q];
+        u->A[p * n + p] += c2h * u->mass[p / 3];
+        u->b[p] = c2h * u->mass[p / 3] * u->vel[p] + fel[p] + u->fext[p] + u->mass[p / 3] * S->g[p % 3];
+    }
+}
+
 static void assemble_linear(orc_scene *S, sub_t *u)
 {
+    if (u->ne > 0) { assemble_corot(S, u); return; }
     int n = u->n;
     double c2h = 2.0 / S->h;
     for (int p = 0; p < n; p++) {
@@ -939,6 +1096,7 @@ void orc_free(orc_scene *S)
         sub_t *u = &S->subs[i];
         free(u->A); free(u->b); free(u->L); free(u->v); free(u->rhs); free(u->bodies);
         free(u->mass); free(u->Kel); free(u->fext); free(u->X0); free(u->x); free(u->vel);
+        free(u->tets); free(u->Ke);
     }
     for (int j = 0; j < S->ncon; j++) {
         con_t *c = &S->cons[j];

@@ -83,6 +83,9 @@ class LinearSub:
     X0: np.ndarray
     x: np.ndarray
     v: np.ndarray
+    tets: Optional[np.ndarray] = None   # elements (T x 4 node indices), when known
+    Ke: Optional[np.ndarray] = None     # their rest stiffness matrices (T x 12 x 12)
+    corot: bool = False                 # co-rotational: K and force from the elements
 
     @property
     def nodes(self) -> int:
@@ -592,7 +595,7 @@ def fem_slab(planes_x: np.ndarray, ny: int, nz: int, width: float, height: float
     np.add.at(mass, tets.ravel(), np.repeat(rho * vol / 4.0, 4))
     nn = X.shape[0]
     sub = LinearSub(mass, Ki, Kj, vals, np.zeros(3 * nn), X.ravel().copy(), X.ravel().copy(),
-                    np.zeros(3 * nn))
+                    np.zeros(3 * nn), tets=tets.astype(np.int64), Ke=Ke)
     return sub, nid, tets
 
 
@@ -720,7 +723,7 @@ def fem_beam(seed: int = 0, ny: int = 10, nz: int = 10, planes: int = 137, slabs
              nu: float = 0.45, rho: float = 1000.0, mu: float = 0.5, drop: float = 0.002,
              with_gripper: bool = True, h: float = 1e-3, tol_primal: float = 1e-6,
              max_iters: int = 1000, warm: str = "prev", kp: float = 50.0, kd: float = 1.0,
-             vary: bool = False):
+             vary: bool = False, corotational: bool = False):
     """A linear-elastic tetrahedral beam (planes x ny x nz nodes, Kuhn split of every grid
     cell) cut into ``slabs`` subsystems: slab g holds 4 node planes when g is a multiple of
     8 and 3 otherwise, neighbouring slabs duplicate the cut plane, and each duplicated node
@@ -730,7 +733,9 @@ def fem_beam(seed: int = 0, ny: int = 10, nz: int = 10, planes: int = 137, slabs
     pose) holds the beam's x = 0 end by ball joints between its two paddles and the
     nearest side-face nodes.  With ``vary`` the seed draws a member of the workload's
     distribution: drop height U[1, 4] mm, friction U[0.3, 0.7], Young's modulus E 2^U[-1/2, 1/2]
-    and PD gains kp 2^U[-1/2, 1/2]; otherwise the beam is the same for every seed."""
+    and PD gains kp 2^U[-1/2, 1/2]; otherwise the beam is the same for every seed.  With
+    ``corotational`` the slabs are co-rotational (the paper's beam model, Sec. IV-A): their
+    stiffness and elastic force come from the rotated elements at every step."""
     rng = np.random.default_rng(seed)
     if vary:
         drop = float(rng.uniform(0.001, 0.004))
@@ -745,6 +750,7 @@ def fem_beam(seed: int = 0, ny: int = 10, nz: int = 10, planes: int = 137, slabs
     p0 = 0
     for g in range(slabs):
         sub, nid, _ = fem_slab(xs[p0:p0 + ks[g]], ny, nz, width, height, E, nu, rho, z0=drop)
+        sub.corot = corotational
         subs.append(sub)
         nids.append(nid)
         if g > 0:
