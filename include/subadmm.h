@@ -241,6 +241,16 @@ int sim_grid_threshold(sim_t s, int side_rows);
  * sim_step. */
 int sim_grid_staging(sim_t s, int enable);
 
+/* Makes linear subsystem `subsystem` co-rotational (the paper's beam model, Sec. IV-A):
+ * `ne` tetrahedra, tets[4e .. 4e + 3] their node indices (inside the block), Ke[144 e ..] their
+ * rest stiffness matrices (12 x 12 row-major, DOF order node-major).  Every step then
+ * assembles, per element, the rotation R of its deformation gradient F = Ds Dm^-1 (polar
+ * decomposition), the stiffness R K_e R^T and the force -R K_e (R^T x_e - X_e): A_i =
+ * (2/h) M + (h/2) sum_e R K_e R^T and b_i = (2/h) M v_k + sum_e f_e + f + M g (the block's own
+ * K triplets give only the pattern, which must contain every element's node pairs).  Its
+ * factor changes every step, so it is never kept.  Before the first sim_step only. */
+int sim_set_corotational(sim_t s, int subsystem, int ne, const int *tets, const double *Ke);
+
 /* Per-subsystem beta scales (host array, one per subsystem id): from the next step on,
  * beta_i = scale[i] x (the trace rule of Sec. III-D, or rho).  The default is 1.  The ADMM
  * fixed point does not depend on beta, its speed does: this is the input a learned rho sets

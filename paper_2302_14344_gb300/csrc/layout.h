@@ -82,6 +82,9 @@ struct SubDesc {
     int ot_s;              // T region: solve vector of the mixed recovery (n)
     int ot_D, ot_c;        // iteration region: D (m rows of mpad, ldd apart), c (m)
     int v_off;             // global offset of v-hat
+    int ne, tet_off, ke_off;   // co-rotational linear block: elements, ipool offset of their
+                               // 4 node indices each, pool offset of their 12 x 12 rest
+                               // stiffness matrices (ne = 0: the constant linear model)
     int tc;                // grid scenes, mixed form: when refactorised, W's columns are solved
                            // by all warps and D, c formed by the tensor-core Gram kernel
 };

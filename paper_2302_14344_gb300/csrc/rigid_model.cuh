@@ -217,6 +217,89 @@ __device__ __forceinline__ double linear_b(int p, const double *mass, const doub
     return (2.0 / h) * m * nodes[(p / 3) * SUBADMM_NODE + 3 + p % 3] - (k0 + k1) + f[p] + m * g[p % 3];
 }
 
+// Co-rotational tetrahedron (the beam model of Sec. IV-A): R, the rotation of the element's
+// deformation gradient F = Ds Dm^-1 (Ds, Dm: edge matrices of the current and rest positions)
+// by Newton's polar iteration R <- (R + R^-T) / 2 from R = F; then (h/2) R K_e R^T (R on every
+// node's 3 x 3 block) is added into the block's K and -R K_e (R^T x_e - X_e) into b.  K row-
+// major n x n, full symmetric band; atomics, since elements share nodes.
+__device__ __forceinline__ void inv3_cof(const double *M, double *c, double &det)
+{
+    c[0] = M[4] * M[8] - M[5] * M[7];
+    c[1] = M[5] * M[6] - M[3] * M[8];
+    c[2] = M[3] * M[7] - M[4] * M[6];
+    c[3] = M[2] * M[7] - M[1] * M[8];
+    c[4] = M[0] * M[8] - M[2] * M[6];
+    c[5] = M[1] * M[6] - M[0] * M[7];
+    c[6] = M[1] * M[5] - M[2] * M[4];
+    c[7] = M[2] * M[3] - M[0] * M[5];
+    c[8] = M[0] * M[4] - M[1] * M[3];
+    det = M[0] * c[0] + M[1] * c[1] + M[2] * c[2];
+}
+
+__device__ void corot_element(const int *tet, const double *Ke, const double *X0,
+                              const double *nodes, double h, int n, double *K, double *b)
+{
+    double Dm[9], Ds[9];
+    for (int k = 0; k < 3; ++k)
+        for (int d = 0; d < 3; ++d) {
+            Dm[3 * d + k] = X0[3 * tet[k + 1] + d] - X0[3 * tet[0] + d];
+            Ds[3 * d + k] = nodes[tet[k + 1] * SUBADMM_NODE + d] - nodes[tet[0] * SUBADMM_NODE + d];
+        }
+    double c[9], det;
+    inv3_cof(Dm, c, det);
+    double F[9], R[9];
+    for (int a = 0; a < 3; ++a)
+        for (int q = 0; q < 3; ++q) {
+            double acc = 0.0;
+            for (int k = 0; k < 3; ++k) acc += Ds[3 * a + k] * c[3 * q + k];
+            F[3 * a + q] = acc / det;
+        }
+    for (int k = 0; k < 9; ++k) R[k] = F[k];
+    for (int it = 0; it < 60; ++it) {
+        double rd;
+        inv3_cof(R, c, rd);
+        double dd = 0.0, nrm = 0.0;
+        for (int k = 0; k < 9; ++k) {
+            const double nk = 0.5 * (R[k] + c[k] / rd);
+            dd += (nk - R[k]) * (nk - R[k]);
+            nrm += nk * nk;
+            R[k] = nk;
+        }
+        if (dd <= 1e-30 * nrm) break;
+    }
+    double w[12], g[12];
+    for (int a = 0; a < 4; ++a)
+        for (int d = 0; d < 3; ++d) {
+            const double *xa = nodes + tet[a] * SUBADMM_NODE;
+            w[3 * a + d] = R[d] * xa[0] + R[3 + d] * xa[1] + R[6 + d] * xa[2] - X0[3 * tet[a] + d];
+        }
+    for (int i = 0; i < 12; ++i) {
+        double acc = 0.0;
+        for (int j = 0; j < 12; ++j) acc += Ke[12 * i + j] * w[j];
+        g[i] = acc;
+    }
+    for (int a = 0; a < 4; ++a)
+        for (int d = 0; d < 3; ++d)
+            atomicAdd(&b[3 * tet[a] + d],
+                      -(R[3 * d] * g[3 * a] + R[3 * d + 1] * g[3 * a + 1] + R[3 * d + 2] * g[3 * a + 2]));
+    const double hh = 0.5 * h;
+    for (int a = 0; a < 4; ++a)
+        for (int q = 0; q < 4; ++q) {
+            double T[9];
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) {
+                    double acc = 0.0;
+                    for (int k = 0; k < 3; ++k) acc += R[3 * i + k] * Ke[12 * (3 * a + k) + 3 * q + j];
+                    T[3 * i + j] = acc;
+                }
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) {
+                    const double v = T[3 * i] * R[3 * j] + T[3 * i + 1] * R[3 * j + 1] + T[3 * i + 2] * R[3 * j + 2];
+                    atomicAdd(&K[(size_t)(3 * tet[a] + i) * n + 3 * tet[q] + j], hh * v);
+                }
+        }
+}
+
 // v_{k+1} = 2 v-hat - v_k; p += h v-hat; q <- q (x) Exp(h w-hat), renormalised.
 __device__ __forceinline__ void body_update(double *B, const double *vh, double h)
 {

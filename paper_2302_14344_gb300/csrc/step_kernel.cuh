@@ -593,6 +593,18 @@ __device__ long long scene_setup(const StepParams &P, const SceneDesc &S, const 
             const int *rowp = P.ipool + u.csr_off, *col = rowp + u.n + 1;
             const double gv[3] = {P.g0, P.g1, P.g2};
             const double *nodes = P.nodes + (size_t)u.body0 * SUBADMM_NODE;
+            if (u.ne > 0) {
+                // co-rotational: (2/h) M on the diagonal and b without the elastic force here;
+                // the elements add (h/2) R K_e R^T and their forces in the pass below
+                for (int p = lane; p < u.n; p += 32) {
+                    const double m = mass[p / 3];
+                    K[p * u.n + p] = (2.0 / P.h) * m;
+                    sdb[u.od_b + p] = (2.0 / P.h) * m * nodes[(p / 3) * SUBADMM_NODE + 3 + p % 3] +
+                                      f[p] + m * gv[p % 3];
+                }
+                __syncwarp();
+                continue;
+            }
             double *ux = sdb + u.od_v;               // x - X0 (v-hat is rewritten later)
             for (int p = lane; p < u.n; p += 32) ux[p] = nodes[(p / 3) * SUBADMM_NODE + p % 3] - X0[p];
             if (!keep) {
@@ -610,6 +622,25 @@ __device__ long long scene_setup(const StepParams &P, const SceneDesc &S, const 
         }
     }
     d.sync();
+    // co-rotational blocks: every element's rotated stiffness and force, the elements of all
+    // such blocks of the scene spread over every thread
+    {
+        int total = 0;
+        for (int i = 0; i < S.nsub; ++i) total += P.subs[S.sub0 + i].ne;
+        for (int w = d.tid; w < total; w += d.nthreads) {
+            int el = w, i = 0;
+            for (; i < S.nsub; ++i) {
+                const int ne = P.subs[S.sub0 + i].ne;
+                if (el < ne) break;
+                el -= ne;
+            }
+            const SubDesc &u = P.subs[S.sub0 + i];
+            const double *X0 = P.pool + u.gen_off + u.nb + u.n;
+            corot_element(P.ipool + u.tet_off + 4 * el, P.pool + u.ke_off + 144 * (size_t)el, X0,
+                          P.nodes + (size_t)u.body0 * SUBADMM_NODE, P.h, u.n, sdb + u.od_L,
+                          sdb + u.od_b);
+        }
+    }
     // rigid bodies: diagonal A = (2/h) M and b (lane per body)
     for (int i = d.warp; i < S.nsub; i += d.nwarps) {
         const SubDesc &u = P.subs[S.sub0 + i];

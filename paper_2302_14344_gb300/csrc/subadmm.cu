@@ -33,6 +33,9 @@ struct HostSub {
     std::vector<double> lin;     // linear: mass (nb), f (n), X0 (n), K values (CSR)
     std::vector<int> csr;        // linear: K row pointers (n+1), then column indices
     std::vector<double> nodes;   // linear: nb records of 6 (x[3], v[3])
+    int ne = 0;                  // co-rotational linear block: elements
+    std::vector<int> tets;       // 4 node indices per element
+    std::vector<double> Ke;      // 12 x 12 rest stiffness per element
 };
 
 struct LaunchClass {
@@ -368,6 +371,13 @@ int finalize(sim_t s)
             u.gen_off = (int)pool.size();
             if (h.kind == KIND_GENERIC) pool.insert(pool.end(), h.Ab.begin(), h.Ab.end());
             if (h.kind == KIND_LINEAR) pool.insert(pool.end(), h.lin.begin(), h.lin.end());
+            u.ne = h.ne;
+            if (h.ne > 0) {
+                u.tet_off = (int)ipool.size();
+                ipool.insert(ipool.end(), h.tets.begin(), h.tets.end());
+                u.ke_off = (int)pool.size();
+                pool.insert(pool.end(), h.Ke.begin(), h.Ke.end());
+            }
             u.v_off = (int)dof;
             dof += h.n;
         }
@@ -454,8 +464,21 @@ int finalize(sim_t s)
                     }
             }
             // A of a linear block is constant, and every row on it is a constant selector or
-            // an explicit row, so its K_i (and factor) is the same at every step
-            u.cst = u.kind == KIND_LINEAR ? 1 : 0;
+            // an explicit row, so its K_i (and factor) is the same at every step; a
+            // co-rotational block's A changes with its elements' rotations
+            u.cst = (u.kind == KIND_LINEAR && u.ne == 0) ? 1 : 0;
+            // every element's node pairs must lie inside the envelope of K's pattern (they are
+            // scattered there each step)
+            for (int el = 0; el < u.ne; ++el)
+                for (int a = 0; a < 4; ++a)
+                    for (int b2 = 0; b2 < 4; ++b2) {
+                        const int na = hs.tets[4 * el + a], nb2 = hs.tets[4 * el + b2];
+                        const int hi = 3 * std::max(na, nb2), lo = 3 * std::min(na, nb2);
+                        for (int r = 0; r < 3; ++r)
+                            if (env[hi + r] > lo)
+                                return fail(s, SIM_EINVAL, "an element couples nodes outside the "
+                                                           "stiffness pattern of its linear block");
+                    }
             auto span = [&](int lr, int a, int b) {
                 if (b <= a) return;
                 if (jlo[lr] == n) { jlo[lr] = a; jhi[lr] = b; }
@@ -1265,7 +1288,14 @@ int launch_grid_class(sim_t s, LaunchClass &c, StepParams P, cudaStream_t st, in
         if (rc) return rc;
         // steps that refactorise tc subsystems: setup launch, Gram kernel, iteration launch
         int left = P.n_steps;
-        while (left > 0 && s->gram[sc].njobs > 0 && (!s->keep_factors || !s->grid_factored[sc])) {
+        // (blocks whose K changes every step, co-rotational ones, refactorise every step)
+        bool changing = false;
+        for (int q = 0; q < S.nsub; ++q) {
+            const SubDesc &u = s->sdesc[S.sub0 + q];
+            changing = changing || (u.tc && !u.cst);
+        }
+        while (left > 0 && s->gram[sc].njobs > 0 &&
+               (changing || !s->keep_factors || !s->grid_factored[sc])) {
             StepParams Q = P;
             Q.n_steps = 1;
             Q.tc_phase = 1;
@@ -1700,6 +1730,25 @@ int sim_grid_staging(sim_t s, int enable)
 {
     if (!s) return SIM_EINVAL;
     s->grid_staging = enable ? 1 : 0;
+    return SIM_OK;
+}
+
+int sim_set_corotational(sim_t s, int subsystem, int ne, const int *tets, const double *Ke)
+{
+    if (!s || !tets || !Ke) return SIM_EINVAL;
+    if (s->finalized) return fail(s, SIM_EINVAL, "the layout is fixed after the first sim_step");
+    if (subsystem < 0 || subsystem >= (int)s->subs.size())
+        return fail(s, SIM_EINVAL, "no such subsystem");
+    HostSub &h = s->subs[subsystem];
+    if (h.kind != KIND_LINEAR) return fail(s, SIM_EINVAL, "not a linear subsystem");
+    if (ne < 1) return fail(s, SIM_EINVAL, "ne must be >= 1");
+    for (long long q = 0; q < 4LL * ne; ++q)
+        if (tets[q] < 0 || tets[q] >= h.nb) return fail(s, SIM_EINVAL, "element node out of range");
+    for (long long q = 0; q < 144LL * ne; ++q)
+        if (!std::isfinite(Ke[q])) return fail(s, SIM_EINVAL, "non-finite element stiffness");
+    h.ne = ne;
+    h.tets.assign(tets, tets + 4LL * ne);
+    h.Ke.assign(Ke, Ke + 144LL * ne);
     return SIM_OK;
 }
 

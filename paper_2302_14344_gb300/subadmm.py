@@ -33,7 +33,7 @@ EXPORTS = ("sim_default_options", "sim_create", "sim_destroy", "sim_add_subsyste
            "sim_read_state", "sim_read_state_noalloc", "sim_write_state", "sim_sizes",
            "sim_iteration_stats", "sim_scene_info", "sim_use_graph", "sim_launch_classes",
            "sim_autotune", "sim_grid_threshold", "sim_grid_staging", "sim_grid_blocks", "sim_tensor_cores", "sim_keep_factors",
-           "sim_set_beta_scale",
+           "sim_set_beta_scale", "sim_set_corotational",
            "sim_probe_barrier", "sim_barrier_floor", "sim_gram_tc", "sim_interface_features",
            "sim_interface_targets", "sim_step_learned", "sim_phase_trace", "sim_sync",
            "sim_last_error")
@@ -103,6 +103,7 @@ def load(build_if_missing: bool = True):
             "sim_grid_blocks": (C.c_int, [VP, C.c_int]),
             "sim_tensor_cores": (C.c_int, [VP, C.c_int]),
             "sim_set_beta_scale": (C.c_int, [VP, PD]),
+            "sim_set_corotational": (C.c_int, [VP, C.c_int, C.c_int, PI, PD]),
             "sim_interface_features": (C.c_int, [VP, VP]),
             "sim_interface_targets": (C.c_int, [VP, VP, VP, VP]),
             "sim_step_learned": (C.c_int, [VP, VP, C.c_int]),
@@ -241,6 +242,12 @@ def sim_grid_staging(h, enable: bool) -> None:
 
 def sim_grid_blocks(h, blocks: int) -> None:
     _check(h, load().sim_grid_blocks(h, blocks))
+
+
+def sim_set_corotational(h, sub: int, tets, Ke) -> None:
+    t = np.ascontiguousarray(np.asarray(tets, dtype=np.int32).ravel())
+    k = _f64(np.asarray(Ke).ravel())
+    _check(h, load().sim_set_corotational(h, sub, len(t) // 4, t.ctypes.data_as(PI), _dp(k)))
 
 
 def sim_set_beta_scale(h, scale) -> None:
@@ -415,6 +422,8 @@ class Simulation:
                     data = np.concatenate([sub.mass, sub.f, sub.X0, sub.x, sub.v,
                                            [float(len(sub.Kv))], trip])
                     sid = sim_add_subsystem(self.h, sc_i, SIM_SUB_LINEAR, sub.nodes, data)
+                    if getattr(sub, "corot", False):
+                        sim_set_corotational(self.h, sid, sub.tets, sub.Ke)
                     self.linear_subs.append((sid, sub.nodes))
                 else:
                     data = np.concatenate([np.asarray(sub.A, float).ravel(),
