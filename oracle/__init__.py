@@ -115,7 +115,17 @@ def body_record(b) -> np.ndarray:
 
 
 def joint_params(j) -> np.ndarray:
-    return _f64(np.concatenate([j.anchor_a, j.anchor_b, j.axis_a, j.axis_b, j.ref_a, j.ref_b,
+    """The oracle's 23 parameters of a model constraint: a plane contact carries its normal
+    in the axis_b slot and its radius in ref_a[0], a sphere contact its radii in ref_a[0] and
+    ref_b[0]."""
+    axis_b, ref_a, ref_b = j.axis_b, j.ref_a, j.ref_b
+    if int(j.kind) == 4:
+        axis_b = j.normal
+        ref_a = [j.radius_a, 0.0, 0.0]
+    elif int(j.kind) == 5:
+        ref_a = [j.radius_a, 0.0, 0.0]
+        ref_b = [j.radius_b, 0.0, 0.0]
+    return _f64(np.concatenate([j.anchor_a, j.anchor_b, j.axis_a, axis_b, ref_a, ref_b,
                                 [j.kp, j.kd, j.target, j.plane_z, j.mu]]))
 
 

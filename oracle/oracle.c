@@ -54,7 +54,8 @@
 #define MAXSIDES 8
 
 enum { T_EQUALITY = 0, T_HARD = 1, T_SOFT = 2, T_CONTACT = 3 };
-enum { SRC_ROWS = 0, SRC_BALL = 1, SRC_REVOLUTE = 2, SRC_ANGLE_PD = 3, SRC_PLANE = 4 };
+enum { SRC_ROWS = 0, SRC_BALL = 1, SRC_REVOLUTE = 2, SRC_ANGLE_PD = 3, SRC_PLANE = 4,
+       SRC_SPHERE = 5 };
 enum { SUB_GENERIC = 0, SUB_RIGID = 1, SUB_LINEAR = 2 };
 
 typedef struct {
@@ -362,11 +363,15 @@ int orc_add_rows(orc_scene *S, int type, int rows, int ns, const int *subs, cons
 }
 
 /* rigid-model constraint.  p: anchor_a[3] anchor_b[3] axis_a[3] axis_b[3] ref_a[3]
- * ref_b[3] kp kd target plane_z mu   (23 doubles).  sb < 0 means the world. */
+ * ref_b[3] kp kd target plane_z mu   (23 doubles).  sb < 0 means the world.
+ * PLANE: axis_b is the plane's world normal (any length > 0; stored normalised); a sphere
+ * of radius ref_a[0] (>= 0; 0 for a point) about anchor_a touches the plane.
+ * SPHERE: anchor_a / anchor_b are the sphere centres in a's / b's frame (b: a world point
+ * for the world), ref_a[0] and ref_b[0] the radii (>= 0). */
 int orc_add_joint(orc_scene *S, int kind, int sa, int ba, int sb, int bb, const double *p)
 {
-    /* a node of a linear block may be a side of a ball joint or a plane contact */
-    const int node_ok = (kind == SRC_BALL || kind == SRC_PLANE);
+    /* a node of a linear block may be a side of a ball joint or a contact */
+    const int node_ok = (kind == SRC_BALL || kind == SRC_PLANE || kind == SRC_SPHERE);
     if (sa < 0 || sa >= S->nsub || S->subs[sa].kind == SUB_GENERIC) return -1;
     if (S->subs[sa].kind == SUB_LINEAR && !node_ok) return -1;
     if (ba < 0 || ba >= S->subs[sa].nb) return -1;
@@ -393,8 +398,16 @@ int orc_add_joint(orc_scene *S, int kind, int sa, int ba, int sb, int bb, const 
     case SRC_REVOLUTE: c->rows = 5; c->type = T_EQUALITY; break;
     case SRC_ANGLE_PD: c->rows = 1; c->type = T_SOFT; break;
     case SRC_PLANE: c->rows = 3; c->type = T_CONTACT; break;
+    case SRC_SPHERE: c->rows = 3; c->type = T_CONTACT; break;
     default: S->ncon--; return -1;
     }
+    if (kind == SRC_PLANE) {
+        double len = sqrt(dot3(c->ax_b, c->ax_b));
+        if (!(len > 0.0)) { S->ncon--; return -1; }
+        for (int d = 0; d < 3; d++) c->ax_b[d] /= len;
+    }
+    if (kind == SRC_PLANE && !(c->ref_a[0] >= 0.0)) { S->ncon--; return -1; }
+    if (kind == SRC_SPHERE && !(c->ref_a[0] >= 0.0 && c->ref_b[0] >= 0.0)) { S->ncon--; return -1; }
     c->ns = 1;
     c->sub[0] = sa;
     if (sb >= 0 && sb != sa) { c->ns = 2; c->sub[1] = sb; }
@@ -602,6 +615,20 @@ static void side_row(const side_t *sd, const double dir[3], const double anc[3],
     point_row(dir, sd->R, anc, row);
 }
 
+/* Contact frame of a unit normal n: rows (n, t1, t2) with t1 the world x axis (the y axis
+ * when n is within ~25 degrees of x) made orthogonal to n and normalised, t2 = n x t1.  For
+ * n = +z this is (z, x, y). */
+static void contact_frame(const double n[3], double F[3][3])
+{
+    double e[3] = {1.0, 0.0, 0.0};
+    if (fabs(n[0]) > 0.9) { e[0] = 0.0; e[1] = 1.0; }
+    double en = dot3(e, n), t1[3];
+    for (int d = 0; d < 3; d++) t1[d] = e[d] - en * n[d];
+    double len = sqrt(dot3(t1, t1));
+    for (int d = 0; d < 3; d++) { t1[d] /= len; F[0][d] = n[d]; F[1][d] = t1[d]; }
+    cross3(n, t1, F[2]);
+}
+
 /* phi (rows) and the blocks Ja, Jb (rows x 6, of which the first 3 columns are used for a
  * node side) of a model constraint */
 static void joint_rows(orc_scene *S, con_t *c, double *phi, double *Ja, double *Jb)
@@ -662,12 +689,47 @@ static void joint_rows(orc_scene *S, con_t *c, double *phi, double *Ja, double *
             for (int q = 0; q < 3; q++) Jb[3 + q] = jb[q];
         }
     } else if (c->src == SRC_PLANE) {
-        double pa[3];
+        /* the plane {x : n . x = plane_z}; the gap along n of the sphere of radius r about
+         * point a; rows of the velocity of its surface point a - r n */
+        double pa[3], F[3][3], ca[3], tmp[3];
+        const double *n = c->ax_b, r = c->ref_a[0];
         side_point(&sa, c->anc_a, pa);
-        phi[0] = pa[2] - c->plane_z;   /* gap along the normal +z */
+        phi[0] = dot3(n, pa) - c->plane_z - r;
         phi[1] = 0.0; phi[2] = 0.0;
-        static const double dirs[3][3] = {{0, 0, 1}, {1, 0, 0}, {0, 1, 0}};
-        for (int d = 0; d < 3; d++) side_row(&sa, dirs[d], c->anc_a, Ja + 6 * d);
+        contact_frame(n, F);
+        rowtimesR(n, Ra, tmp);
+        for (int d = 0; d < 3; d++) ca[d] = c->anc_a[d] - r * tmp[d];
+        for (int d = 0; d < 3; d++) side_row(&sa, F[d], ca, Ja + 6 * d);
+    } else if (c->src == SRC_SPHERE) {
+        /* spheres of radii r_a, r_b about the centres P_a, P_b: normal n = (P_a - P_b)/|.|
+         * (+z for coincident centres), gap |P_a - P_b| - r_a - r_b; rows of the relative
+         * velocity of the two surface points P_a - r_a n and P_b + r_b n */
+        double Pa[3], Pb[3], dv[3], n[3] = {0.0, 0.0, 1.0}, F[3][3];
+        side_point(&sa, c->anc_a, Pa);
+        if (hasb) side_point(&sbd, c->anc_b, Pb);
+        else { for (int d = 0; d < 3; d++) Pb[d] = c->anc_b[d]; }
+        for (int d = 0; d < 3; d++) dv[d] = Pa[d] - Pb[d];
+        double dist = sqrt(dot3(dv, dv));
+        if (dist > 0.0) for (int d = 0; d < 3; d++) n[d] = dv[d] / dist;
+        const double ra = c->ref_a[0], rb = c->ref_b[0];
+        phi[0] = dist - ra - rb;
+        phi[1] = 0.0; phi[2] = 0.0;
+        contact_frame(n, F);
+        /* surface points as offsets in each body's frame: anchor + R^T (-/+ r n) */
+        double ca[3], cb[3] = {c->anc_b[0], c->anc_b[1], c->anc_b[2]}, tmp[3];
+        rowtimesR(n, Ra, tmp);
+        for (int d = 0; d < 3; d++) ca[d] = c->anc_a[d] - ra * tmp[d];
+        if (hasb && !sbd.node) {
+            rowtimesR(n, Rb, tmp);
+            for (int d = 0; d < 3; d++) cb[d] = c->anc_b[d] + rb * tmp[d];
+        }
+        for (int d = 0; d < 3; d++) {
+            side_row(&sa, F[d], ca, Ja + 6 * d);
+            if (hasb) {
+                side_row(&sbd, F[d], cb, Jb + 6 * d);
+                for (int q = 0; q < 6; q++) Jb[6 * d + q] = -Jb[6 * d + q];
+            }
+        }
     }
 }
 
@@ -695,7 +757,7 @@ static void assemble_joint(orc_scene *S, con_t *c)
         c->e[0] = phi[0] - c->target;
         c->k = c->kp;
         c->alpha = c->kd / c->kp + 0.5 * h;
-    } else if (c->src == SRC_PLANE) {
+    } else if (c->src == SRC_PLANE || c->src == SRC_SPHERE) {
         double gap = phi[0];
         c->e[0] = gap >= 0.0 ? gap / h : S->gamma * gap / h;
         c->e[1] = 0.0; c->e[2] = 0.0;

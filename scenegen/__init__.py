@@ -24,7 +24,7 @@ TYPE_NAMES = {EQUALITY: "equality", HARD: "hard", SOFT: "soft", CONTACT: "contac
 
 # Interface sources: explicit rows, or a rigid-body model constraint whose rows are built
 # from the bodies' state every step.
-ROWS, BALL, REVOLUTE, ANGLE_PD, PLANE_CONTACT = 0, 1, 2, 3, 4
+ROWS, BALL, REVOLUTE, ANGLE_PD, PLANE_CONTACT, SPHERE_CONTACT = 0, 1, 2, 3, 4, 5
 
 WORLD = -1
 
@@ -182,7 +182,11 @@ class JointIf:
     kind REVOLUTE:      + axis_a, ref_a (a frame, ref_a orthogonal to axis_a),
                         axis_b (b frame)                                         5 rows
     kind ANGLE_PD:      axis_a, ref_a (a frame), ref_b (b frame), kp, kd, target 1 soft row
-    kind PLANE_CONTACT: anchor_a = contact point in a's frame, plane_z, mu        3 rows
+    kind PLANE_CONTACT: a sphere of radius radius_a (0: a point) about anchor_a (a frame)
+                        against the plane {x : normal . x = plane_z} (normal: world,
+                        default +z), mu                                         3 rows
+    kind SPHERE_CONTACT: spheres about anchor_a (a frame) and anchor_b (b frame, or a
+                        world point) of radii radius_a, radius_b; mu             3 rows
     """
 
     kind: int
@@ -199,6 +203,9 @@ class JointIf:
     target: float = 0.0
     plane_z: float = 0.0
     mu: float = 0.0
+    normal: np.ndarray = field(default_factory=lambda: np.array([0.0, 0.0, 1.0]))
+    radius_a: float = 0.0
+    radius_b: float = 0.0
 
 
 @dataclass
@@ -920,7 +927,8 @@ def problem_sizes(p: Problem) -> dict:
             if isinstance(itf, RowsIf):
                 r, ns = itf.rows, len(itf.subs)
             else:
-                r = {BALL: 3, REVOLUTE: 5, ANGLE_PD: 1, PLANE_CONTACT: 3}[itf.kind]  # noqa
+                r = {BALL: 3, REVOLUTE: 5, ANGLE_PD: 1, PLANE_CONTACT: 3,  # noqa
+                     SPHERE_CONTACT: 3}[itf.kind]
                 ns = 1 if (itf.b is None or itf.b[0] == itf.a[0]) else 2
             rows += r
             side_rows += r * ns
