@@ -818,6 +818,54 @@ def sub_cable(ctx, args) -> dict:
     return out
 
 
+STIR_PAPER_MS = {30: 3.489, 60: 5.940, 90: 8.705}   # Table I, SubADMM, 4-core CPU
+
+
+def sub_stir(ctx, args) -> dict:
+    """The granular stirring scene (216 spheres and a 7-R arm stand-in, 217 subsystems) at the
+    paper's fixed 30 / 60 / 90 iterations per step (Table I), mixed and FP64, one scene over
+    the whole GPU (grid kernel); the oracle's time per step on all host cores beside each,
+    and the paper's own times (another machine, a CPU: context only)."""
+    import scenegen as sg
+    sa = ctx.subadmm
+    K = args.steps
+    out = {"workload": "stir: 216 spheres (r 1 cm, 4 g) on a 6x6x6 lattice in a box, one "
+                       "subsystem each, sphere-sphere contacts between initial neighbours "
+                       "(< 1.5 diameters), floor and wall contacts, a 7-R arm stand-in sweeping "
+                       "a tool sphere through the top layers (217 subsystems, 1,338 DOF); "
+                       "mu=0.5, h=1e-2 s; exactly 30 / 60 / 90 ADMM iterations per step",
+           "paper_ms_per_step": {str(k): v for k, v in STIR_PAPER_MS.items()}}
+    for iters in (30, 60, 90):
+        p = sg.stir(0, tol_primal=-1, max_iters=iters)
+        row = {}
+        for name, prec in (("mixed", sa.SIM_MIXED), ("plain_fp64", sa.SIM_FP64)):
+            r = time_form(ctx, p, prec, K, args.warmup, 0, 50, autotune=True, graph=False,
+                          grid_rows=1)
+            res = r["sim"].residuals(0)
+            row[name] = {"ms_per_step": r["t_ms"] / K,
+                         "us_per_iteration": r["t_ms"] * 1e3 / (K * iters),
+                         "r_p_after": res["r_p"]}
+            r["sim"].close()
+        if not args.no_cpu_baseline:                 # sub-results run at N = 1 only
+            row["oracle_ms_per_step"] = oracle_stir_ms(p, steps=5)
+        row["paper_over_mixed"] = STIR_PAPER_MS[iters] / row["mixed"]["ms_per_step"]
+        out[str(iters)] = row
+    out["value"] = 1e3 / out["90"]["mixed"]["ms_per_step"]
+    out["unit"] = "steps/s at 90 iterations"
+    return out
+
+
+def oracle_stir_ms(p, steps: int) -> float:
+    """The oracle (OpenMP build, all host cores) stepping the stir scene: ms per step."""
+    import oracle
+    o = oracle.OracleScene(p.scenes[0], p.options, openmp=True)
+    o.step()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        o.step()
+    return (time.perf_counter() - t0) * 1e3 / steps
+
+
 def sub_chain(ctx, args) -> dict:
     """The 8-link chain at exactly 100 iterations per step with rho = 1e3 (FP64 and mixed)."""
     sa = ctx.subadmm
@@ -861,8 +909,9 @@ def main():
     ap.add_argument("--no-compare", action="store_true",
                     help="skip timing the plain FP64 form next to the chosen one")
     ap.add_argument("--no-sub", action="store_true", help="headline workload only")
-    ap.add_argument("--subs", default="robots,fem_beam,chain,cable",
-                    help="comma-separated sub-results to run (robots, fem_beam, chain, cable)")
+    ap.add_argument("--subs", default="robots,fem_beam,chain,cable,stir",
+                    help="comma-separated sub-results to run (robots, fem_beam, chain, cable, "
+                         "stir)")
     ap.add_argument("--sub-only", action="store_true",
                     help="skip the headline workload's GPU timing (sub-results only)")
     args = ap.parse_args()
@@ -957,7 +1006,8 @@ def main():
         jobs = {"robots_after_landing": lambda: sub_robots(ctx, args, threads),
                 "fem_beam": lambda: sub_fem_beam(ctx, args, threads),
                 "chain_fixed_100_iterations": lambda: sub_chain(ctx, args),
-                "cable_fixed_90_iterations": lambda: sub_cable(ctx, args)}
+                "cable_fixed_90_iterations": lambda: sub_cable(ctx, args),
+                "stir_fixed_30_60_90_iterations": lambda: sub_stir(ctx, args)}
         wanted = [w.strip() for w in args.subs.split(",") if w.strip()]
         for name, fn in jobs.items():
             if name.startswith(args.workload) or not any(name.startswith(w) for w in wanted):

@@ -60,7 +60,8 @@ extern "C" {
 #define SIM_IF_BALL 4         /* 3 equality rows: point of a == point of b                  */
 #define SIM_IF_REVOLUTE 5     /* 5 equality rows: ball + two axis-alignment rows            */
 #define SIM_IF_ANGLE_PD 6     /* 1 soft row: PD drive of the relative angle about an axis   */
-#define SIM_IF_PLANE_CONTACT 7/* 3 contact rows: body point against the plane z = plane_z  */
+#define SIM_IF_PLANE_CONTACT 7/* 3 contact rows: a sphere (or point) of a against a plane    */
+#define SIM_IF_SPHERE_CONTACT 8/* 3 contact rows: a sphere of a against a sphere of b       */
 
 /* option values */
 #define SIM_BETA_TRACE 0      /* beta_i = Tr(A_i) / Tr(J_ci^T J_ci)  (Sec. III-D)           */
@@ -134,10 +135,11 @@ int sim_add_subsystem(sim_t s, int scene, int kind, int count, const double *dat
  *   the same scene; J = for each side in order, a rows x n_side row-major block; e = rows
  *   values; params = {k, alpha, mu} (k, alpha for SOFT; mu for CONTACT; may be NULL
  *   otherwise).  J and e are constant for the life of the simulation.
- * Rigid-model kinds (SIM_IF_BALL, SIM_IF_REVOLUTE, SIM_IF_ANGLE_PD, SIM_IF_PLANE_CONTACT):
+ * Rigid-model kinds (SIM_IF_BALL, SIM_IF_REVOLUTE, SIM_IF_ANGLE_PD, SIM_IF_PLANE_CONTACT,
+ * SIM_IF_SPHERE_CONTACT):
  *   rows and n_sides are ignored; sides = {sub_a, body_a, sub_b, body_b}: (subsystem id, body
  *   index inside it) of bodies a and b, sub_b = -1 for the world (PLANE_CONTACT uses a only);
- *   for BALL and PLANE_CONTACT a side may also be (linear subsystem id, node index): the
+ *   for BALL and the two contacts a side may also be (linear subsystem id, node index): the
  *   node's position takes the place of the anchored body point;
  *   J and e must be NULL; params = 23 doubles:
  *     anchor_a[3] (a frame), anchor_b[3] (b frame, or a world point), axis_a[3], axis_b[3],
@@ -147,8 +149,18 @@ int sim_add_subsystem(sim_t s, int scene, int kind, int count, const double *dat
  *   REVOLUTE: BALL rows plus t_k . (R_b axis_b) for t_1 = R_a ref_a, t_2 = R_a (axis_a x ref_a).
  *   ANGLE_PD: angle theta of R_b ref_b from R_a ref_a about R_a axis_a; soft row with
  *     k = kp, alpha = kd/kp + h/2, e = theta - target.
- *   PLANE_CONTACT: rows (z, x, y) of the velocity of point anchor_a; e_n = gap/h for
- *     gap >= 0, baumgarte gap/h otherwise; friction coefficient mu.
+ *   Contact frame of a unit normal n: rows (n, t1, t2), t1 = the world x axis (the y axis
+ *     when |n_x| > 0.9) made orthogonal to n and normalised, t2 = n x t1; for n = +z the
+ *     rows are (z, x, y).  Both contacts: e_n = gap/h for gap >= 0, baumgarte gap/h
+ *     otherwise, e_t = 0; friction coefficient mu >= 0.
+ *   PLANE_CONTACT: axis_b = the plane's world normal n (any length > 0, normalised here),
+ *     ref_a[0] = r >= 0: the sphere of radius r about the point P = p_a + R_a anchor_a
+ *     against the plane {x : n . x = plane_z}; gap = n . P - plane_z - r; rows of the
+ *     velocity of the material point P - r n (r = 0: the point P itself).
+ *   SPHERE_CONTACT: spheres of radii ref_a[0], ref_b[0] >= 0 about P_a = p_a + R_a anchor_a
+ *     and P_b = p_b + R_b anchor_b (anchor_b a world point for the world); n = (P_a - P_b) /
+ *     |P_a - P_b| (+z when the centres coincide), gap = |P_a - P_b| - r_a - r_b; rows of the
+ *     relative velocity of the material points P_a - r_a n (of a) and P_b + r_b n (of b).
  * Two bodies of the same subsystem give an intra-subsystem constraint (|S_j| = 1). */
 int sim_add_interface(sim_t s, int scene, int kind, int rows, int n_sides, const int *sides,
                       const double *J, const double *e, const double *params, int *out_id);
@@ -194,7 +206,8 @@ int sim_autotune(sim_t s, int steps, int max_classes, long long *out);
  * sim_interface_features writes 32 features per interface from the current state (the
  * state a next sim_step starts from): [0:4] projection type one-hot (equality, hard, soft,
  * contact); [4:7] anchor point of side a minus that of side b (world; the world side is
- * its anchor, a plane contact's the point's projection on the plane); [7:11] relative
+ * its anchor, a plane contact's the foot of a's point on the plane, a sphere contact's
+ * the centre of b's sphere); [7:11] relative
  * orientation q_a^-1 q_b (w, x, y, z; identity for nodes and the world); [11:14] and
  * [14:17] anchor velocity and angular velocity of a minus those of b (world); [17:23] the
  * last step's lambda (first 6 rows); [23:26] the error terms e (first 3 rows); [26] mu;
@@ -277,7 +290,9 @@ int sim_grid_blocks(sim_t s, int blocks);
 
 /* A linear block's K_i = A_i + beta_i J_i^T J_i is constant (Sec. II-B: its A_i and its
  * node-selector rows are), so by default (enable != 0) its factor, W and D are computed at
- * its first step and kept.  With 0 every step factorises every block again, as Algorithm 1
+ * its first step and kept.  Not kept: co-rotational blocks (A_i changes) and blocks with a
+ * node in a SPHERE_CONTACT (the rows turn with the normal, so D does).  With 0 every step
+ * factorises every block again, as Algorithm 1
  * states it: the same matrix, so the results agree to rounding (with a kept factor
  * g = L^-1 b is formed by the single-vector solve, otherwise as the last column of W).
  * Takes effect at the next sim_step. */

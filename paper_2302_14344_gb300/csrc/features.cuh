@@ -96,9 +96,16 @@ __global__ void interface_features_kernel(const StepParams P, const int *pub2dev
                 side_motion(0, nullptr, prm + 3, pb, vb, wb, qb);
             }
             if (c.src == SRC_PLANE) {
-                pb[0] = pa[0]; pb[1] = pa[1]; pb[2] = prm[21];
+                // b is the foot of a's centre on the plane n . x = plane_z
+                const double *n = prm + 9;
+                const double off = n[0] * pa[0] + n[1] * pa[1] + n[2] * pa[2] - prm[21];
+                for (int d = 0; d < 3; ++d) pb[d] = pa[d] - off * n[d];
                 f[26] = (float)prm[22];
-                f[28] = (float)(pa[2] - prm[21]);
+                f[28] = (float)(off - prm[12]);
+            } else if (c.src == SRC_SPHERE) {
+                const double d[3] = {pa[0] - pb[0], pa[1] - pb[1], pa[2] - pb[2]};
+                f[26] = (float)prm[22];
+                f[28] = (float)(sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) - prm[12] - prm[15]);
             }
             quat_conj_mul(qa, qb, qr);
             for (int d = 0; d < 3; ++d) {

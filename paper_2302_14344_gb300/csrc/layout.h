@@ -12,7 +12,7 @@
 
 // constraint sources (how the rows are obtained) -- values of the public SIM_IF_* kinds
 enum { SRC_EQUALITY = 0, SRC_HARD = 1, SRC_SOFT = 2, SRC_CONTACT = 3, SRC_BALL = 4,
-       SRC_REVOLUTE = 5, SRC_ANGLE_PD = 6, SRC_PLANE = 7 };
+       SRC_REVOLUTE = 5, SRC_ANGLE_PD = 6, SRC_PLANE = 7, SRC_SPHERE = 8 };
 // projection types (Sec. III-C)
 enum { TYPE_EQUALITY = 0, TYPE_HARD = 1, TYPE_SOFT = 2, TYPE_CONTACT = 3 };
 // subsystem kinds

@@ -59,6 +59,20 @@ __device__ __forceinline__ void point_row(const double *d, const Rot &R, const d
     cross(r, Rd, row + 3);
 }
 
+// Contact frame of a unit normal n: rows n, t1, t2 with t1 the world x axis (y when
+// |n_x| > 0.9) with its n component removed, normalised, and t2 = n x t1; for n = +z the
+// frame is (z, x, y).
+__device__ __forceinline__ void contact_frame(const double *n, double F[3][3])
+{
+    const bool near_x = fabs(n[0]) > 0.9;
+    const double ex = near_x ? 0.0 : 1.0, ey = near_x ? 1.0 : 0.0;
+    const double en = ex * n[0] + ey * n[1];
+    double t[3] = {ex - en * n[0], ey - en * n[1], -en * n[2]};
+    const double inv = 1.0 / sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
+    for (int q = 0; q < 3; ++q) { t[q] *= inv; F[0][q] = n[q]; F[1][q] = t[q]; }
+    cross(n, t, F[2]);
+}
+
 // A side of a model constraint: a rigid body (its point p + R anchor, rows of 6 columns
 // [v, w]) or a node of a linear block (its position, rows of 3 columns: its velocity).
 struct Side {
@@ -166,12 +180,45 @@ __device__ void model_rows(const ConDesc &c, const double *prm, const double *bo
         e[0] = theta - prm[20];
         *k_out = kp;
         *alpha_out = kd / kp + 0.5 * h;
-    } else if (c.src == SRC_PLANE) {
-        double pa[3];
+    } else if (c.src == SRC_PLANE || c.src == SRC_SPHERE) {
+        // a sphere of radius ref_a[0] about point a against the plane n . x = plane_z (n =
+        // axis_b, unit), or against the sphere of radius ref_b[0] about point b (n from b's
+        // centre to a's, +z for coincident centres); rows of the relative velocity of the
+        // two surface points along the contact frame of n
+        double pa[3], n[3], gap;
+        const double ra = ref_a[0];
         side_point(sa, anc_a, pa);
-        const double gap = pa[2] - prm[21];
-        const double dirs[3][3] = {{0.0, 0.0, 1.0}, {1.0, 0.0, 0.0}, {0.0, 1.0, 0.0}};
-        for (int d = 0; d < 3; ++d) side_row(sa, dirs[d], anc_a, Ja + 6 * d);
+        if (c.src == SRC_PLANE) {
+            n[0] = ax_b[0]; n[1] = ax_b[1]; n[2] = ax_b[2];
+            gap = dot(n, pa) - prm[21] - ra;
+        } else {
+            double pb[3];
+            if (hasb) side_point(sb, anc_b, pb);
+            else { pb[0] = anc_b[0]; pb[1] = anc_b[1]; pb[2] = anc_b[2]; }
+            const double d[3] = {pa[0] - pb[0], pa[1] - pb[1], pa[2] - pb[2]};
+            const double dist = sqrt(dot(d, d));
+            n[0] = 0.0; n[1] = 0.0; n[2] = 1.0;
+            if (dist > 0.0) { n[0] = d[0] / dist; n[1] = d[1] / dist; n[2] = d[2] / dist; }
+            gap = dist - ra - ref_b[0];
+        }
+        double F[3][3];
+        contact_frame(n, F);
+        double ca[3], cb[3], rn[3];
+        mulT(Ra, n, rn);
+        for (int q = 0; q < 3; ++q) ca[q] = anc_a[q] - ra * rn[q];
+        if (c.src == SRC_SPHERE && hasb && !sb.node) {
+            mulT(sb.R, n, rn);
+            for (int q = 0; q < 3; ++q) cb[q] = anc_b[q] + ref_b[0] * rn[q];
+        } else {
+            for (int q = 0; q < 3; ++q) cb[q] = anc_b[q];
+        }
+        for (int d = 0; d < 3; ++d) {
+            side_row(sa, F[d], ca, Ja + 6 * d);
+            if (c.src == SRC_SPHERE && hasb) {
+                side_row(sb, F[d], cb, Jb + 6 * d);
+                for (int q = 0; q < 6; ++q) Jb[6 * d + q] = -Jb[6 * d + q];
+            }
+        }
         e[0] = gap >= 0.0 ? gap * ih : gamma * gap * ih;
         e[1] = 0.0;
         e[2] = 0.0;

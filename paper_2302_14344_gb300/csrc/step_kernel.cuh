@@ -301,7 +301,7 @@ __device__ __forceinline__ void con_params(const ConDesc &c, const double *pool,
         k = p[0]; alpha = p[1]; mu = p[2];
     } else if (c.src == SRC_ANGLE_PD) {
         k = p[18]; alpha = p[19] / p[18] + 0.5 * h;
-    } else if (c.src == SRC_PLANE) {
+    } else if (c.src == SRC_PLANE || c.src == SRC_SPHERE) {
         mu = p[22];
     }
 }

@@ -165,6 +165,7 @@ int model_rows_of(int src)
     case SRC_REVOLUTE: return 5;
     case SRC_ANGLE_PD: return 1;
     case SRC_PLANE: return 3;
+    case SRC_SPHERE: return 3;
     default: return 0;
     }
 }
@@ -174,6 +175,7 @@ int model_type_of(int src)
     switch (src) {
     case SRC_ANGLE_PD: return TYPE_SOFT;
     case SRC_PLANE: return TYPE_CONTACT;
+    case SRC_SPHERE: return TYPE_CONTACT;
     default: return TYPE_EQUALITY;
     }
 }
@@ -465,8 +467,18 @@ int finalize(sim_t s)
             }
             // A of a linear block is constant, and every row on it is a constant selector or
             // an explicit row, so its K_i (and factor) is the same at every step; a
-            // co-rotational block's A changes with its elements' rotations
-            u.cst = (u.kind == KIND_LINEAR && u.ne == 0) ? 1 : 0;
+            // co-rotational block's A changes with its elements' rotations, and a sphere
+            // contact on one of its nodes turns its rows with the contact normal (K_i stays,
+            // as the frame is orthonormal, but the map D = J K^-1 J^T does not)
+            bool turning_rows = false;
+            for (int j = 0; j < S.ncon; ++j) {
+                const ConDesc &c = s->cdesc[S.con0 + j];
+                if (c.src != SRC_SPHERE) continue;
+                if ((c.node_a && c.sub[0] == i) ||
+                    (c.node_b && c.side_b >= 0 && c.sub[c.side_b] == i))
+                    turning_rows = true;
+            }
+            u.cst = (u.kind == KIND_LINEAR && u.ne == 0 && !turning_rows) ? 1 : 0;
             // every element's node pairs must lie inside the envelope of K's pattern (they are
             // scattered there each step)
             for (int el = 0; el < u.ne; ++el)
@@ -552,7 +564,7 @@ int finalize(sim_t s)
         // assembly slots: constraints grouped by how their rows are built (explicit rows, or
         // one model kind), each group padded to whole warps
         S.asm_g0 = (int)asm_order.size();
-        for (int grp = 0; grp < 5; ++grp) {
+        for (int grp = 0; grp <= SRC_SPHERE - SRC_CONTACT; ++grp) {
             int cnt = 0;
             for (int j = 0; j < S.ncon; ++j) {
                 const int src = s->cdesc[S.con0 + j].src;
@@ -1074,25 +1086,26 @@ int sim_add_interface(sim_t s, int scene, int kind, int rows, int n_sides, const
         if (rc) return rc;
         for (int q = 0; q < n_sides; ++q)
             if (s->subs[sides[q]].scene != scene) return fail(s, SIM_EINVAL, "a side belongs to another scene");
-    } else if (kind >= SIM_IF_BALL && kind <= SIM_IF_PLANE_CONTACT) {
+    } else if (kind >= SIM_IF_BALL && kind <= SIM_IF_SPHERE_CONTACT) {
         if (!sides || !params) return fail(s, SIM_EINVAL, "sides and params are required");
         if (J || e) return fail(s, SIM_EINVAL, "model interfaces take no J or e");
         const int sa = sides[0], ba = sides[1];
         int sb = sides[2], bb = sides[3];
         if (kind == SIM_IF_PLANE_CONTACT) { sb = -1; bb = 0; }
-        // a node of a linear block may be a side of a ball joint or a plane contact
-        const bool node_ok = kind == SIM_IF_BALL || kind == SIM_IF_PLANE_CONTACT;
+        // a node of a linear block may be a side of a ball joint or a contact
+        const bool node_ok = kind == SIM_IF_BALL || kind == SIM_IF_PLANE_CONTACT ||
+                             kind == SIM_IF_SPHERE_CONTACT;
         auto side_kind_ok = [&](int sub) {
             const int kd = s->subs[sub].kind;
             return kd == KIND_RIGID || (kd == KIND_LINEAR && node_ok);
         };
         if (sa < 0 || sa >= (int)s->subs.size() || !side_kind_ok(sa))
-            return fail(s, SIM_EINVAL, "side a must be a rigid subsystem (or a linear one for BALL / PLANE_CONTACT)");
+            return fail(s, SIM_EINVAL, "side a must be a rigid subsystem (or a linear one for BALL and the contacts)");
         if (ba < 0 || ba >= s->subs[sa].nb) return fail(s, SIM_EINVAL, "body a out of range");
         if (s->subs[sa].scene != scene) return fail(s, SIM_EINVAL, "body a belongs to another scene");
         if (sb >= 0) {
             if (sb >= (int)s->subs.size() || !side_kind_ok(sb))
-                return fail(s, SIM_EINVAL, "side b must be a rigid subsystem (or a linear one for BALL), or -1");
+                return fail(s, SIM_EINVAL, "side b must be a rigid subsystem (or a linear one for BALL and the contacts), or -1");
             if (bb < 0 || bb >= s->subs[sb].nb) return fail(s, SIM_EINVAL, "body b out of range");
             if (sb == sa && bb == ba) return fail(s, SIM_EINVAL, "a body cannot be joined to itself");
             if (s->subs[sb].scene != scene) return fail(s, SIM_EINVAL, "body b belongs to another scene");
@@ -1101,14 +1114,25 @@ int sim_add_interface(sim_t s, int scene, int kind, int rows, int n_sides, const
             if (!std::isfinite(params[q])) return fail(s, SIM_EINVAL, "non-finite parameter");
         if (kind == SIM_IF_ANGLE_PD && !(params[18] > 0.0))
             return fail(s, SIM_EINVAL, "ANGLE_PD needs kp > 0");
-        if (kind == SIM_IF_PLANE_CONTACT && !(params[22] >= 0.0))
-            return fail(s, SIM_EINVAL, "PLANE_CONTACT needs mu >= 0");
+        const bool contact = kind == SIM_IF_PLANE_CONTACT || kind == SIM_IF_SPHERE_CONTACT;
+        if (contact && !(params[22] >= 0.0)) return fail(s, SIM_EINVAL, "a contact needs mu >= 0");
+        if (contact && !(params[12] >= 0.0)) return fail(s, SIM_EINVAL, "a contact radius is negative");
+        if (kind == SIM_IF_SPHERE_CONTACT && !(params[15] >= 0.0))
+            return fail(s, SIM_EINVAL, "a contact radius is negative");
+        double nrm = 0.0;
+        if (kind == SIM_IF_PLANE_CONTACT) {
+            nrm = std::sqrt(params[9] * params[9] + params[10] * params[10] + params[11] * params[11]);
+            if (!(nrm > 0.0) || !std::isfinite(nrm))
+                return fail(s, SIM_EINVAL, "PLANE_CONTACT needs a nonzero normal (axis_b)");
+        }
         c.src = kind; c.type = model_type_of(kind); c.rows = model_rows_of(kind);
         c.sa = sa; c.ba = ba; c.sb = sb; c.bb = bb;
         c.side_sub[0] = sa;
         c.ns = 1;
         if (sb >= 0 && sb != sa) { c.ns = 2; c.side_sub[1] = sb; }
         c.data.assign(params, params + SUBADMM_PARAMS);
+        if (kind == SIM_IF_PLANE_CONTACT)
+            for (int d = 0; d < 3; ++d) c.data[9 + d] = params[9 + d] / nrm;
     } else {
         return fail(s, SIM_EINVAL, "unknown interface kind");
     }

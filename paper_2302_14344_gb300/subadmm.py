@@ -21,6 +21,7 @@ SIM_EINVAL, SIM_ENOMEM, SIM_ENOTSPD, SIM_ENAN, SIM_ECUDA = -1, -2, -3, -4, -5
 SIM_SUB_GENERIC, SIM_SUB_RIGID, SIM_SUB_LINEAR = 0, 1, 2
 SIM_IF_EQUALITY, SIM_IF_HARD, SIM_IF_SOFT, SIM_IF_CONTACT = 0, 1, 2, 3
 SIM_IF_BALL, SIM_IF_REVOLUTE, SIM_IF_ANGLE_PD, SIM_IF_PLANE_CONTACT = 4, 5, 6, 7
+SIM_IF_SPHERE_CONTACT = 8
 SIM_BETA_TRACE, SIM_BETA_FIXED = 0, 1
 SIM_WARM_COLD, SIM_WARM_PREV = 0, 1
 SIM_STOP_PRIMAL, SIM_STOP_THETA = 0, 1
@@ -367,7 +368,22 @@ def sim_last_error(h) -> str:
 # --- convenience: a simulation built from a scene description ---------------------------
 
 _KIND = {0: SIM_IF_EQUALITY, 1: SIM_IF_HARD, 2: SIM_IF_SOFT, 3: SIM_IF_CONTACT}
-_MODEL = {1: SIM_IF_BALL, 2: SIM_IF_REVOLUTE, 3: SIM_IF_ANGLE_PD, 4: SIM_IF_PLANE_CONTACT}
+_MODEL = {1: SIM_IF_BALL, 2: SIM_IF_REVOLUTE, 3: SIM_IF_ANGLE_PD, 4: SIM_IF_PLANE_CONTACT,
+          5: SIM_IF_SPHERE_CONTACT}
+
+
+def model_params(itf) -> np.ndarray:
+    """The 23 parameters of a rigid-model interface: a plane contact carries its normal in
+    the axis_b slot and its radius in ref_a[0], a sphere contact its radii in ref_a[0] and
+    ref_b[0]."""
+    kind = _MODEL[int(itf.kind)]
+    axis_b, ref_a, ref_b = itf.axis_b, itf.ref_a, itf.ref_b
+    if kind == SIM_IF_PLANE_CONTACT:
+        axis_b, ref_a = itf.normal, [itf.radius_a, 0.0, 0.0]
+    elif kind == SIM_IF_SPHERE_CONTACT:
+        ref_a, ref_b = [itf.radius_a, 0.0, 0.0], [itf.radius_b, 0.0, 0.0]
+    return np.concatenate([itf.anchor_a, itf.anchor_b, itf.axis_a, axis_b, ref_a, ref_b,
+                           [itf.kp, itf.kd, itf.target, itf.plane_z, itf.mu]]).astype(np.float64)
 
 
 def options_from(o, stream: int = 0, device: int = 0, precision: int = SIM_FP64) -> sim_options:
@@ -444,14 +460,12 @@ class Simulation:
                     self.if_nsides.append(len(sides))
                 else:
                     sb, bb = (ids[itf.b[0]], itf.b[1]) if itf.b is not None else (-1, 0)
-                    prm = np.concatenate([itf.anchor_a, itf.anchor_b, itf.axis_a, itf.axis_b,
-                                          itf.ref_a, itf.ref_b,
-                                          [itf.kp, itf.kd, itf.target, itf.plane_z, itf.mu]])
+                    prm = model_params(itf)
                     kind = _MODEL[int(itf.kind)]
                     iid = sim_add_interface(self.h, sc_i, kind, 0, 0,
                                             [ids[itf.a[0]], itf.a[1], sb, bb], None, None, prm)
                     rows = {SIM_IF_BALL: 3, SIM_IF_REVOLUTE: 5, SIM_IF_ANGLE_PD: 1,
-                            SIM_IF_PLANE_CONTACT: 3}[kind]
+                            SIM_IF_PLANE_CONTACT: 3, SIM_IF_SPHERE_CONTACT: 3}[kind]
                     self.if_rows.append(rows)
                     same = itf.b is None or itf.b[0] == itf.a[0]
                     self.if_nsides.append(1 if same else 2)

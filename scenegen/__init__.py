@@ -641,10 +641,12 @@ def gripper(anchor_w: np.ndarray, reach: float = 0.12, rho: float = 1000.0):
     return bodies, joints, paddles
 
 
-def _arm(gs: int, anchor_w: np.ndarray, kp: float, kd: float):
+def _arm(gs: int, anchor_w: np.ndarray, kp: float, kd: float, base_drive=None):
     """The 7-R arm stand-in of ``gripper`` as one rigid subsystem (index ``gs``) whose
     paddles hang down to ``anchor_w``: the subsystem, its revolute joints and PD drives
-    (holding the initial pose), and the first paddle's body index."""
+    (holding the initial pose), and the first paddle's body index.  ``base_drive`` =
+    (kp, kd, angle) adds a PD drive of the base about the vertical that turns it by
+    ``angle`` from its initial pose."""
     bodies, joints, paddles = gripper(anchor_w)
     ifs = []
     ex = np.array([1.0, 0, 0])
@@ -655,6 +657,13 @@ def _arm(gs: int, anchor_w: np.ndarray, kp: float, kd: float):
             ifs.append(JointIf(REVOLUTE, a=(gs, ch), b=None, anchor_a=jw - bc.p, anchor_b=jw.copy(),
                                axis_a=ax.copy(), axis_b=ax.copy(), ref_a=ref.copy(),
                                ref_b=ref.copy()))
+            if base_drive is not None:
+                bkp, bkd, angle = base_drive
+                # the angle of the world's ref from the base's ref about the base's axis is
+                # minus the base's turn
+                ifs.append(JointIf(ANGLE_PD, a=(gs, ch), b=None, axis_a=ax.copy(),
+                                   axis_b=ax.copy(), ref_a=ref.copy(), ref_b=ref.copy(),
+                                   kp=bkp, kd=bkd, target=-angle))
             continue
         bp = bodies[pa]
         ifs.append(JointIf(REVOLUTE, a=(gs, pa), b=(gs, ch), anchor_a=jw - bp.p,
@@ -805,6 +814,100 @@ def fem_beam(seed: int = 0, ny: int = 10, nz: int = 10, planes: int = 137, slabs
             ifs.append(JointIf(BALL, a=(gs, pb), b=(sg_, node), anchor_a=Xn[node] - bodies[pb].p))
     opts = Options(h=h, beta_mode="trace", warm=warm, tol_primal=tol_primal, max_iters=max_iters)
     return Problem([Scene(subs, ifs)], opts, name=f"fem_beam{slabs}")
+
+
+def stir(seed: int = 0, n_side: int = 6, layers: int = 6, radius: float = 0.01,
+         mass: float = 0.004, gap: float = 5e-4, mu: float = 0.5, tool_radius: float = 0.008,
+         tool_offset: float = 0.03, sweep: float = 1.5, drive=(0.02, 0.002),
+         arm: bool = True, neighbor: float = 1.5, h: float = 1e-2, tol_primal: float = 1e-6,
+         max_iters: int = 1000, warm: str = "prev") -> Problem:
+    """Granular stirring, shaped like the paper's stir scene (Sec. IV-A: 216 spheres of
+    radius 1 cm and 4 g in a box, stirred by an arm's end effector; each sphere and the arm
+    one subsystem, 217 in all; h = 10 ms as in the paper's experiments).
+
+    ``n_side`` x ``n_side`` x ``layers`` spheres (one rigid subsystem each) start on a
+    lattice of spacing 2 radius + gap above the floor z = 0, inside four walls, with seeded
+    jitter (at most 0.2 gap per axis, so no two overlap), random orientations and small
+    random velocities (up to 1 cm/s).  Contacts (friction mu), all speculative (an open one
+    projects to zero): sphere-sphere for every pair whose centres start closer than
+    ``neighbor`` diameters; the floor for the bottom layer and the facing wall for every
+    sphere on the lattice's boundary (plane contacts with the sphere's radius).  With
+    ``arm``, the 7-R arm stand-in (as in the cable and beam scenes) hangs from a world
+    pivot ``tool_offset`` beside the box's axis and carries a tool sphere (``tool_radius``)
+    in the top layer's central hollow; a PD drive (``drive`` = kp, kd) turns its base by
+    ``sweep`` radians, sweeping the tool through the top layers, and the tool has a
+    speculative contact with every sphere of the two top layers within reach of its
+    circle.  The arm's model is a stand-in: the paper's manipulator model is not public."""
+    rng = np.random.default_rng(seed)
+    spacing = 2.0 * radius + gap
+    I = 0.4 * mass * radius * radius
+    half = 0.5 * (n_side - 1) * spacing
+    centres, bodies = [], []
+    for k in range(layers):
+        for iy in range(n_side):
+            for ix in range(n_side):
+                c = np.array([ix * spacing - half, iy * spacing - half,
+                              radius + 0.5 * gap + k * spacing])
+                c = c + rng.uniform(-0.2 * gap, 0.2 * gap, 3)
+                q = _random_rotation(rng)
+                v = rng.uniform(-0.01, 0.01, 3)
+                centres.append(c)
+                bodies.append(Body(mass, np.array([I, I, I]), c, q, v, np.zeros(3)))
+    subs = [RigidSub([b]) for b in bodies]
+    N = len(bodies)
+    P = np.array(centres)
+    ifs = []
+    cut = neighbor * 2.0 * radius
+    for a in range(N):
+        d = np.linalg.norm(P[a + 1:] - P[a], axis=1)
+        for b in np.nonzero(d < cut)[0] + a + 1:
+            ifs.append(JointIf(SPHERE_CONTACT, a=(a, 0), b=(int(b), 0), radius_a=radius,
+                               radius_b=radius, mu=mu))
+    wall = half + radius + gap
+    for a in range(N):
+        k, rem = divmod(a, n_side * n_side)
+        iy, ix = divmod(rem, n_side)
+        planes = []
+        if k == 0:
+            planes.append((np.array([0.0, 0.0, 1.0]), 0.0))
+        if ix == 0:
+            planes.append((np.array([1.0, 0.0, 0.0]), -wall))
+        if ix == n_side - 1:
+            planes.append((np.array([-1.0, 0.0, 0.0]), -wall))
+        if iy == 0:
+            planes.append((np.array([0.0, 1.0, 0.0]), -wall))
+        if iy == n_side - 1:
+            planes.append((np.array([0.0, -1.0, 0.0]), -wall))
+        for nrm, off in planes:
+            ifs.append(JointIf(PLANE_CONTACT, a=(a, 0), radius_a=radius, normal=nrm,
+                               plane_z=off, mu=mu))
+    if arm:
+        ztop = radius + 0.5 * gap + (layers - 1) * spacing
+        reach = radius + tool_radius + gap
+        if n_side % 2 == 0:       # the central hollow between four top spheres
+            dz = np.sqrt(max(reach * reach - 0.5 * spacing * spacing, 0.0))
+        else:                     # on top of the central sphere
+            dz = reach
+        tool = np.array([0.0, 0.0, ztop + dz])
+        axis_xy = np.array([-tool_offset, 0.0])
+        gs = len(subs)
+        arm_sub, arm_ifs, paddle = _arm(gs, np.array([axis_xy[0], 0.0, tool[2] + 0.02]),
+                                        kp=50.0, kd=1.0,
+                                        base_drive=(drive[0], drive[1], sweep))
+        subs.append(arm_sub)
+        ifs.extend(arm_ifs)
+        pb = arm_sub.bodies[paddle]
+        Rr = np.hypot(*(tool[:2] - axis_xy))
+        band = radius + tool_radius + spacing
+        for a in range(N):
+            if P[a, 2] < ztop - spacing - 0.5 * gap:
+                continue
+            if abs(np.hypot(*(P[a, :2] - axis_xy)) - Rr) > band:
+                continue
+            ifs.append(JointIf(SPHERE_CONTACT, a=(gs, paddle), b=(a, 0), anchor_a=tool - pb.p,
+                               radius_a=tool_radius, radius_b=radius, mu=mu))
+    opts = Options(h=h, beta_mode="trace", warm=warm, tol_primal=tol_primal, max_iters=max_iters)
+    return Problem([Scene(subs, ifs)], opts, name=f"stir{N}")
 
 
 def _random_rotation(rng) -> np.ndarray:
