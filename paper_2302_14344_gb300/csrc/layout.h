@@ -42,6 +42,9 @@ struct SceneDesc {
     int row_bytes;
     int item_g0, list_g0;  // global offsets of the scene's item / list tables
     int nasm, asm_g0;      // assembly slots (constraint indices grouped by kind, -1 = idle)
+    // ipool offset of three prefix sums over the subsystems (nsub + 1 each): chunks of 32
+    // columns of W, items of c, items of D (the setup's scene-wide work lists)
+    int pre_off;
     int sr_g0, row_g0;     // global offset of the scene's side-rows / rows (z, lambda state)
     // double region
     int od_beta;           // beta per subsystem

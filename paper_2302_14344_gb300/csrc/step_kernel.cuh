@@ -364,8 +364,11 @@ __device__ void add_jtj(F *K, int n, const double *J, int m, const SubEnv &e, F 
 }
 
 // Right-looking Cholesky inside the envelope, in place on the lower triangle of K (one
-// warp).  Column k below the diagonal is scaled, then the rows it reaches are updated a row
-// at a time, lanes across the columns (coalesced).  INV_DIAG: the diagonal ends as 1/L_kk
+// warp).  Column k below the diagonal is scaled, then the triangle k < q <= r <= lastr[k]
+// it reaches is updated with the lanes across its entries: a band of width w costs
+// w (w + 1) / 64 warp instructions per column rather than w (on GB300 an FP64 warp
+// instruction occupies its pipe however few lanes are active).  Every entry receives the
+// same updates in the same order (k ascending).  INV_DIAG: the diagonal ends as 1/L_kk
 // (the T factor); otherwise as L_kk with 1/L_kk in idg.  False on a non-positive pivot.
 template <typename F, bool INV_DIAG>
 __device__ bool env_cholesky(F *K, int n, const SubEnv &e, double *idg)
@@ -387,45 +390,71 @@ __device__ bool env_cholesky(F *K, int n, const SubEnv &e, double *idg)
             }
         }
         __syncwarp();
-        for (int c0 = k + 1; c0 <= R; c0 += 32) {
-            const int q = c0 + lane;
-            const F lq = q <= R ? K[q * n + k] : (F)0;
-            F *Kq = K + q;
-#pragma unroll 4
-            for (int r = c0; r <= R; ++r) {
-                const F lrk = (r - c0 < 32) ? __shfl_sync(0xffffffffu, lq, r - c0) : K[r * n + k];
-                if (q <= r) Kq[r * n] -= lrk * lq;
-            }
+        const int w = R - k, tri = w * (w + 1) / 2;
+        for (int t = lane; t < tri; t += 32) {
+            int a, b;
+            tri_index(t, a, b);
+            const int r = k + 1 + a, q = k + 1 + b;
+            K[r * n + q] -= K[r * n + k] * K[q * n + k];
         }
         __syncwarp();
     }
     return true;
 }
 
-// X <- L^-1 X for the nrhs columns of X (column t at X[p ldx + t]), a lane per column, each
-// row inside the envelope; the diagonal of LT holds 1/L_pp
+// Columns c0 .. c0 + 31 of W = L^-1 [J^T b] (column-major, W[p ldw + t]; a lane per
+// column): column t < m is row t of J, column m is b, columns m < t < ldw are padding
+// (zero).  Row t of J is zero outside its span [jlo[t], jhi[t]), so column t of W is zero
+// above jlo[t]: the warp starts at the first such row among its columns and reads J's span
+// directly (no separate transposed fill).  Rows above that start are written as zeros only
+// when `whole` (a reader that takes W whole: the tensor-core Gram kernel); the map's
+// items skip them.  The diagonal of LT holds 1/L_pp.
 template <typename F>
-__device__ void env_forward_cols(const F *LT, F *X, int n, int ldx, int nrhs, const int *env)
+__device__ void solve_w_chunk(const F *LT, F *W, const double *J, const double *b, int n,
+                              int m, int ldw, int c0, const SubEnv &e, bool whole)
 {
     const int lane = threadIdx.x & 31;
-    for (int t0 = 0; t0 < nrhs; t0 += 32) {
-        const int t = t0 + lane;
-        const bool act = t < nrhs;
-        F *x = X + (act ? t : nrhs - 1);
-        for (int p = 0; p < n; ++p) {
-            const F *Lp = LT + (size_t)p * n;
-            F s0 = x[p * ldx], s1 = (F)0, s2 = (F)0, s3 = (F)0;
-            int q = env[p];
-            for (; q + 3 < p; q += 4) {
-                s0 -= Lp[q] * x[q * ldx];
-                s1 -= Lp[q + 1] * x[(q + 1) * ldx];
-                s2 -= Lp[q + 2] * x[(q + 2) * ldx];
-                s3 -= Lp[q + 3] * x[(q + 3) * ldx];
-            }
-            for (; q < p; ++q) s0 -= Lp[q] * x[q * ldx];
-            if (act) x[p * ldx] = ((s0 + s1) + (s2 + s3)) * Lp[p];
+    const int t = c0 + lane;
+    const bool act = t <= m;                       // a column of J^T or b
+    const bool pad = t > m && t < ldw;             // zero padding
+    const int lo = !act ? n : (t == m ? 0 : e.jlo[t]);
+    const int hi = !act ? n : (t == m ? n : e.jhi[t]);
+    int p0 = lo;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) p0 = min(p0, __shfl_xor_sync(0xffffffffu, p0, o));
+    if (pad)
+        for (int p = 0; p < n; ++p) W[(size_t)p * ldw + t] = (F)0;
+    if (whole && act)
+        for (int p = 0; p < p0; ++p) W[(size_t)p * ldw + t] = (F)0;
+    F *x = W + (act ? t : c0);                     // idle lanes read column c0, write nothing
+    const double *Jt = J + (size_t)(act && t < m ? t : 0) * n;
+    for (int p = p0; p < n; ++p) {
+        const F *Lp = LT + (size_t)p * n;
+        F s0 = (F)0, s1 = (F)0, s2 = (F)0, s3 = (F)0;
+        if (p >= lo && p < hi) s0 = (F)(t == m ? b[p] : Jt[p]);
+        int q = max(e.env[p], p0);                 // x[q] = 0 above p0
+        for (; q + 3 < p; q += 4) {
+            s0 -= Lp[q] * x[(size_t)q * ldw];
+            s1 -= Lp[q + 1] * x[(size_t)(q + 1) * ldw];
+            s2 -= Lp[q + 2] * x[(size_t)(q + 2) * ldw];
+            s3 -= Lp[q + 3] * x[(size_t)(q + 3) * ldw];
         }
+        for (; q < p; ++q) s0 -= Lp[q] * x[(size_t)q * ldw];
+        if (act) x[(size_t)p * ldw] = ((s0 + s1) + (s2 + s3)) * Lp[p];
     }
+}
+
+// The range of a prefix table pre[0 .. nsub] (pre[0] = 0, nondecreasing) that holds item w
+// < pre[nsub]: the i with pre[i] <= w < pre[i + 1]
+__device__ __forceinline__ int pre_find(const int *pre, int nsub, int w)
+{
+    int lo = 0, hi = nsub;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(pre + mid) <= w) lo = mid;
+        else hi = mid;
+    }
+    return lo;
 }
 
 // x[q ldx] -= a[q lda] f for q0 <= q < q1 (warp, lanes across q).  Whole passes of 8 x 32
@@ -492,13 +521,7 @@ __device__ void env_forward_vec(const F *LT, F *y, int n, int ldy, const int *la
 // is g; W column t is zero above row jlo[t]; D rows ldd apart, zero-padded from m to mp), for
 // items spread over many threads: item k < nb (nb + 1) / 2 is the 4 x 4 block k of D's lower
 // triangle (mirrored; per row p of W a thread loads 4 + 4 values for 16 FMAs); item
-// nb (nb + 1) / 2 + q gives c and the zero padding of D for rows 4q .. 4q + 3.  map_items()
-// is the item count of a subsystem of m side-rows.
-__device__ __forceinline__ int map_items(int m)
-{
-    const int nb = (m + 3) / 4;
-    return nb * (nb + 1) / 2 + nb;
-}
+// nb (nb + 1) / 2 + q gives c and the zero padding of D for rows 4q .. 4q + 3.
 
 template <typename F>
 __device__ void map_item(const F *W, int n, int m, int mp, int ldd, int ldw, const int *jlo,
@@ -793,76 +816,54 @@ __device__ long long scene_setup(const StepParams &P, const SceneDesc &S, const 
             ok = env_cholesky<T, true>(LT, n, e, nullptr);
         }
         if (u.cst && lane == 0) P.subflag[gsub] = ok ? (1 | (stiff ? 2 : 0)) : 0;
-        if (lane == 0) P.pending[gsub] = 0;
         if (!ok) {
-            if (lane == 0) *s_status = ST_NOTSPD;
+            if (lane == 0) { P.pending[gsub] = 0; *s_status = ST_NOTSPD; }
             continue;
         }
-        // W = [J^T b] in T (column-major), then W <- L^-1 W; D = W^T W, c = W^T g
-        for (int q = lane; q < n * ldw; q += 32) {
-            const int p = q / ldw, t = q - p * ldw;
-            W[q] = t < m ? (T)J[t * n + p] : t == m ? (T)b[p] : (T)0;
-        }
-        __syncwarp();
-        if (P.tc_phase == 1 && u.tc) continue;     // solved by column chunks below; D, c by
-                                                   // the tensor-core Gram kernel
-        env_forward_cols<T>(LT, W, n, ldw, m + 1, e.env);
-        __syncwarp();
-        if (lane == 0) P.pending[gsub] = 2;           // D and c below
+        if (lane == 0) P.pending[gsub] = 3;       // W, then D and c, below
         __syncwarp();
     }
     d.sync();
-    // the maps D = W^T W and c = W^T g of this step (pending 2: D and c, 1: c only), their
-    // items (4 x 4 blocks of D, 4 rows of c) spread over every thread of the scene rather
-    // than one warp per subsystem, which left a block waiting on its largest subsystem
+    // W = L^-1 [J^T b] of the refactorised subsystems (pending 3) in chunks of 32 columns, a
+    // warp per chunk over every warp of the scene, so that one large subsystem does not hold
+    // a single warp (and the scene) for all of its columns
     {
-        int total = 0;
-        for (int i = 0; i < S.nsub; ++i) {
-            const SubDesc &u = P.subs[S.sub0 + i];
-            if (P.pending[S.sub0 + i] && !(P.tc_phase == 1 && u.tc)) total += map_items(u.m);
-        }
-        for (int w = d.tid; w < total; w += d.nthreads) {
-            int k = w, i = 0;
-            for (; i < S.nsub; ++i) {
-                const SubDesc &u = P.subs[S.sub0 + i];
-                if (!P.pending[S.sub0 + i] || (P.tc_phase == 1 && u.tc)) continue;
-                const int c = map_items(u.m);
-                if (k < c) break;
-                k -= c;
-            }
+        const int *wpre = P.ipool + S.pre_off;
+        const int total = __ldg(wpre + S.nsub);
+        for (int w = d.warp; w < total; w += d.nwarps) {
+            const int i = pre_find(wpre, S.nsub, w);
+            if (P.pending[S.sub0 + i] != 3) continue;
             const SubDesc &u = P.subs[S.sub0 + i];
             const int ldw = (u.m + 1 + 3) / 4 * 4;
-            const SubEnv e = sub_env(P, u);
-            map_item<T>(stb + u.ot_W, u.n, u.m, u.mpad, u.ldd, ldw, e.jlo, htb + u.ot_D,
-                        htb + u.ot_c, k, P.pending[S.sub0 + i] == 2);
+            solve_w_chunk<T>(stb + u.ot_L, stb + u.ot_W, sdb + u.od_J, sdb + u.od_b, u.n, u.m,
+                             ldw, 32 * (w - __ldg(wpre + i)), sub_env(P, u),
+                             P.tc_phase == 1 && u.tc);
         }
     }
     d.sync();
-    if (P.tc_phase == 1) {
-        // W <- L^-1 W for the refactorised tc subsystems, in chunks of 32 columns (a lane per
-        // column) spread over every warp of the grid
-        int total = 0;
-        for (int i = 0; i < S.nsub; ++i) {
+    // the maps D = W^T W and c = W^T g of this step (pending >= 2: D and c, 1: c only), their
+    // items (rows of c, then 4 x 4 blocks of D) spread over every thread of the scene and
+    // found through the scene's prefix tables; the tensor-core Gram kernel forms them for
+    // the tc subsystems in the first launch of a three-launch step
+    {
+        const int *cpre = P.ipool + S.pre_off + (S.nsub + 1), *dpre = cpre + (S.nsub + 1);
+        const int ctot = __ldg(cpre + S.nsub), total = ctot + __ldg(dpre + S.nsub);
+        for (int w = d.tid; w < total; w += d.nthreads) {
+            const bool cpart = w < ctot;
+            const int wl = cpart ? w : w - ctot;
+            const int i = pre_find(cpart ? cpre : dpre, S.nsub, wl);
+            const int pend = P.pending[S.sub0 + i];
+            if (pend == 0 || (!cpart && pend < 2)) continue;
             const SubDesc &u = P.subs[S.sub0 + i];
-            if (u.tc) total += (u.m + 1 + 31) / 32;
+            if (P.tc_phase == 1 && u.tc) continue;
+            const int nb = (u.m + 3) / 4;
+            const int k = (cpart ? nb * (nb + 1) / 2 : 0) + wl - __ldg((cpart ? cpre : dpre) + i);
+            const int ldw = (u.m + 1 + 3) / 4 * 4;
+            map_item<T>(stb + u.ot_W, u.n, u.m, u.mpad, u.ldd, ldw, sub_env(P, u).jlo,
+                        htb + u.ot_D, htb + u.ot_c, k, pend >= 2);
         }
-        for (int w = d.warp; w < total; w += d.nwarps) {
-            int k = w, i = 0;
-            for (; i < S.nsub; ++i) {
-                const SubDesc &u = P.subs[S.sub0 + i];
-                if (!u.tc) continue;
-                const int ch = (u.m + 1 + 31) / 32;
-                if (k < ch) break;
-                k -= ch;
-            }
-            const SubDesc &u = P.subs[S.sub0 + i];
-            const int ldw = (u.m + 1 + 3) / 4 * 4, c0 = 32 * k;
-            const int cols = u.m + 1 - c0 < 32 ? u.m + 1 - c0 : 32;
-            const SubEnv e = sub_env(P, u);
-            env_forward_cols<T>(stb + u.ot_L, stb + u.ot_W + c0, u.n, ldw, cols, e.env);
-        }
-        d.sync();
     }
+    d.sync();
     // per-step z-step constants: 1/s, soft gain k/(1 + s alpha k), alpha, mu (per row);
     // beta and 1/beta per side-row
     T *INVS = tb + S.ot_invs, *KF = tb + S.ot_kf, *AL = tb + S.ot_al, *MU = tb + S.ot_mu;

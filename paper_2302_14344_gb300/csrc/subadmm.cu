@@ -537,6 +537,19 @@ int finalize(sim_t s)
             ipool.insert(ipool.end(), jlo.begin(), jlo.end());
             ipool.insert(ipool.end(), jhi.begin(), jhi.end());
         }
+        // work of the setup's scene-wide passes, as prefix sums over the scene's subsystems:
+        // chunks of 32 columns of W = L^-1 [J^T b] (m + 1 columns), then the map's items of
+        // c (one per 4 rows) and of D (4 x 4 blocks of its lower triangle)
+        S.pre_off = (int)ipool.size();
+        for (int tab = 0; tab < 3; ++tab) {
+            int acc = 0;
+            ipool.push_back(0);
+            for (int i = 0; i < S.nsub; ++i) {
+                const int m = s->sdesc[S.sub0 + i].m, nb = (m + 3) / 4;
+                acc += tab == 0 ? (m + 1 + 31) / 32 : tab == 1 ? nb : nb * (nb + 1) / 2;
+                ipool.push_back(acc);
+            }
+        }
         // z-step items: one per row of an equality / hard / soft constraint, one per contact;
         // ordered by type so that neighbouring threads run the same projection
         S.item_g0 = (int)items.size();
