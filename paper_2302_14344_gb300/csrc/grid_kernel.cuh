@@ -122,6 +122,11 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 2) grid_step_kernel(StepParam
     // mbarrier that completes when its bulk copy has landed
     extern __shared__ __align__(128) unsigned char stage_raw[];
     __shared__ __align__(8) unsigned long long stage_bar[SUBADMM_WARPS][4];
+    // per-warp partials of the iteration's reductions: a block combines its warps' values
+    // and adds one atomic to the grid-wide slot (one per block rather than one per warp:
+    // atomics on one address serialise at its L2 slice)
+    __shared__ unsigned long long s_umax[SUBADMM_WARPS];
+    __shared__ double s_theta[SUBADMM_WARPS];
     const int wl = threadIdx.x >> 5;
     const int nst = P.grid_nstage;
     if (P.grid_stage > 0 && lane == 0) {
@@ -166,6 +171,22 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 2) grid_step_kernel(StepParam
             d.sync();
             pc.flush(0, 0);         // the setup's cycles; the iteration launch counts the step
             continue;
+        }
+        // z-step items in registers for the whole step when the scene has at most one item
+        // per thread (an item's tables are constant within a step): each iteration then loads
+        // only its y, x and z, in one round trip, instead of a chain of table loads; items of
+        // more than two sides stay on the generic path
+        // Items go by the block-interleaved warp numbering (item group g of 32, one type each,
+        // to warp g, i.e. warp g / blocks of block g % blocks), so that a scene with few
+        // items spreads them over the SMs rather than filling the first blocks.
+        const int ix = 32 * d.warp + lane;
+        const bool icache = S.nitem <= d.nthreads;
+        RegItem<T, false> ri;
+        bool igeneric = false;
+        if (icache && ix < S.nitem) {
+            const Item it = V.item[ix];
+            if (it.ns <= 2) ri.load(V.item, V.list, ix, INVB, E, INVS, KF, AL, MU, Z);
+            else igeneric = it.type >= 0;
         }
         // initial z, u = -lambda; a learned start is checked after 10 iterations against the
         // plain start's residual there, and replaced by the plain start if worse
@@ -409,7 +430,13 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 2) grid_step_kernel(StepParam
                 if (P.stop_theta) {
 #pragma unroll
                     for (int o = 16; o; o >>= 1) tpart += __shfl_xor_sync(0xffffffffu, tpart, o);
-                    if (lane == 0 && tpart != (T)0) atomicAdd(&G->theta[(l + wasted) % 3], (double)tpart);
+                    if (lane == 0) s_theta[wl] = (double)tpart;
+                    __syncthreads();
+                    if (threadIdx.x == 0) {
+                        double tb = 0.0;
+                        for (int k = 0; k < SUBADMM_WARPS; ++k) tb += s_theta[k];
+                        if (tb != 0.0) atomicAdd(&G->theta[(l + wasted) % 3], tb);
+                    }
                 }
                 d.sync();
                 pc.mark(PHASE_VSTEP);
@@ -427,8 +454,8 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 2) grid_step_kernel(StepParam
                 }
                 // ---- z-step (Sec. III-C); u = -lambda; max(|x - z|, |dz|) as bits
                 T *wn = par ? W0 : W1;
-                U mloc = 0;
-                for (int i = d.tid; i < S.nitem; i += d.nthreads) {
+                U mloc = icache ? ri.project(Y, X, LAM, wn, Z, ZO) : (U)0;
+                for (int i = icache && !igeneric ? S.nitem : ix; i < S.nitem; i += d.nthreads) {
                     const Item it = V.item[i];
                     if (it.type < 0) continue;
                     const int *ls = V.list + it.lo;
@@ -485,9 +512,16 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 2) grid_step_kernel(StepParam
                             wn[t] = yv + (T)2 * lv;
                         }
                     }
+                    if (icache) break;                  // this thread's one item
                 }
                 mloc = warp_umax(mloc);
-                if (lane == 0 && mloc) atomicMax(&G->umax[(l + wasted) % 3], (unsigned long long)mloc);
+                if (lane == 0) s_umax[wl] = (unsigned long long)mloc;
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    unsigned long long mb = 0ull;
+                    for (int k = 0; k < SUBADMM_WARPS; ++k) mb = umax(mb, s_umax[k]);
+                    if (mb) atomicMax(&G->umax[(l + wasted) % 3], mb);
+                }
                 d.sync();
                 const U mx = (U)vload(&G->umax[(l + wasted) % 3]);
                 par ^= 1;

@@ -76,6 +76,8 @@ struct SubDesc {
                            // X0 (n), K values (linear)
     int csr_off;           // linear: ipool offset of the K row pointers (n+1), then columns
     int env_off;           // ipool offset of the profile of K_i: env (n), lastr (n), jlo (m), jhi (m)
+    int grp_off, ngrp;     // ipool offset of the row groups of J_ci: maximal runs of consecutive
+                           // rows with one column span, as ngrp + 1 first rows (the last = m)
     int cst;               // 1 if K_i is the same at every step (its factor may be kept)
     int od_J, od_L, od_b;  // double region: J_ci rows (m x n), K then its factor L (n x n), b (n)
     int od_v, od_id;       // double region: v-hat (n); 1 / L_pp (FP64 factor) or rhs (mixed) (n)

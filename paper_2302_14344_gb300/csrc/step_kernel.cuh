@@ -320,6 +320,8 @@ __device__ __forceinline__ void tri_index(int t, int &r, int &s)
 // last row whose envelope reaches column k, [jlo[t], jhi[t]) the columns of J row t.
 struct SubEnv {
     const int *env, *lastr, *jlo, *jhi;
+    const int *grp;        // first rows of the row groups (ngrp + 1 entries)
+    int ngrp;
 };
 
 __device__ __forceinline__ SubEnv sub_env(const StepParams &P, const SubDesc &u)
@@ -329,6 +331,8 @@ __device__ __forceinline__ SubEnv sub_env(const StepParams &P, const SubDesc &u)
     e.lastr = e.env + u.n;
     e.jlo = e.lastr + u.n;
     e.jhi = e.jlo + u.m;
+    e.grp = P.ipool + u.grp_off;
+    e.ngrp = u.ngrp;
     return e;
 }
 
@@ -345,19 +349,24 @@ __device__ __forceinline__ bool factor_kept(const StepParams &P, const SceneDesc
            P.beta_scale[gsub] == P.beta_used[gsub];
 }
 
-// K += beta J^T J on the lower triangle (row-major n x n), one J row at a time over the
-// row's column span (rows share entries, so they are added in turn)
+// K += beta J^T J on the lower triangle (row-major n x n), a row group at a time (rows
+// with one column span [lo, lo + w)): lanes across the span's triangle entries, each summing
+// its products over the group's rows with independent loads, then one update of K per
+// entry and group (groups share entries, so they are added in turn)
 template <typename F>
-__device__ void add_jtj(F *K, int n, const double *J, int m, const SubEnv &e, F beta)
+__device__ void add_jtj(F *K, int n, const double *J, const SubEnv &e, F beta)
 {
     const int lane = threadIdx.x & 31;
-    for (int t = 0; t < m; ++t) {
-        const int lo = e.jlo[t], w = e.jhi[t] - lo;
-        const double *Jr = J + (size_t)t * n + lo;
+    for (int g = 0; g < e.ngrp; ++g) {
+        const int r0 = e.grp[g], r1 = e.grp[g + 1];
+        const int lo = e.jlo[r0], w = e.jhi[r0] - lo;
+        const double *J0 = J + (size_t)r0 * n + lo;
         for (int k = lane; k < w * (w + 1) / 2; k += 32) {
             int a, b;
             tri_index(k, a, b);
-            K[(lo + a) * n + lo + b] += beta * (F)Jr[a] * (F)Jr[b];
+            F acc = (F)0;
+            for (int t = 0; t < r1 - r0; ++t) acc += (F)J0[(size_t)t * n + a] * (F)J0[(size_t)t * n + b];
+            K[(lo + a) * n + lo + b] += beta * acc;
         }
         __syncwarp();
     }
@@ -801,7 +810,7 @@ __device__ long long scene_setup(const StepParams &P, const SceneDesc &S, const 
         }
         bool ok;
         if (stiff) {
-            add_jtj<double>(K, n, J, m, e, beta);
+            add_jtj<double>(K, n, J, e, beta);
             ok = env_cholesky<double, false>(K, n, e, idg);
             if (ok) {
                 for (int p = 0; p < n; ++p)
@@ -812,7 +821,7 @@ __device__ long long scene_setup(const StepParams &P, const SceneDesc &S, const 
             for (int p = 0; p < n; ++p)
                 for (int q = e.env[p] + lane; q <= p; q += 32) LT[p * n + q] = (T)K[p * n + q];
             __syncwarp();
-            add_jtj<T>(LT, n, J, m, e, (T)beta);
+            add_jtj<T>(LT, n, J, e, (T)beta);
             ok = env_cholesky<T, true>(LT, n, e, nullptr);
         }
         if (u.cst && lane == 0) P.subflag[gsub] = ok ? (1 | (stiff ? 2 : 0)) : 0;
@@ -894,17 +903,21 @@ __device__ long long scene_setup(const StepParams &P, const SceneDesc &S, const 
     return t_asm;
 }
 
-// out += J^T w (FP64) over the column span of each J row, a row at a time (lanes across the
-// span), in row order: deterministic, and O(sum of spans) instead of O(m n)
+// out += J^T w (FP64) over the column span of each row group (lanes across the span, each
+// summing over the group's rows, then one update of out per group), in row order:
+// deterministic, and O(sum of spans) instead of O(m n)
 template <typename W>
-__device__ __forceinline__ void add_jt(double *out, const double *J, int n, int m,
-                                       const SubEnv &e, const W *w)
+__device__ __forceinline__ void add_jt(double *out, const double *J, int n, const SubEnv &e,
+                                       const W *w)
 {
     const int lane = threadIdx.x & 31;
-    for (int r = 0; r < m; ++r) {
-        const double wr = (double)w[r];
-        const double *Jr = J + (size_t)r * n;
-        for (int p = e.jlo[r] + lane; p < e.jhi[r]; p += 32) out[p] += Jr[p] * wr;
+    for (int g = 0; g < e.ngrp; ++g) {
+        const int r0 = e.grp[g], r1 = e.grp[g + 1];
+        for (int p = e.jlo[r0] + lane; p < e.jhi[r0]; p += 32) {
+            double acc = 0.0;
+            for (int r = r0; r < r1; ++r) acc += J[(size_t)r * n + p] * (double)w[r];
+            out[p] += acc;
+        }
         __syncwarp();
     }
 }
@@ -956,7 +969,7 @@ __device__ void recover_v(const StepParams &P, const SceneDesc &S, const View<T>
         if (!MIXED || V.db[S.od_flag + i] != 0.0) {
             for (int p = lane; p < n; p += 32) v[p] = b[p];
             __syncwarp();
-            add_jt(v, J, n, m, e, wi);
+            add_jt(v, J, n, e, wi);
             for (int p = 0; p < n; ++p) {          // L y = rhs (column-oriented)
                 const double yp = v[p] * idg[p];
                 __syncwarp();
@@ -980,7 +993,7 @@ __device__ void recover_v(const StepParams &P, const SceneDesc &S, const View<T>
         const double beta = V.db[S.od_beta + i];
         for (int p = lane; p < n; p += 32) rhs[p] = b[p];
         __syncwarp();
-        add_jt(rhs, J, n, m, e, wi);
+        add_jt(rhs, J, n, e, wi);
         for (int p = lane; p < n; p += 32) s[p] = (T)rhs[p];
         __syncwarp();
         warp_chol_solve<T>(LT, s, n, e);
@@ -997,7 +1010,7 @@ __device__ void recover_v(const StepParams &P, const SceneDesc &S, const View<T>
         for (int r = lane; r < m; r += 32) t[r] *= -beta;
         __syncwarp();
         // s = rhs - A v - beta J^T t, with J^T (-beta t) added into the FP64 rhs copy
-        add_jt(rhs, J, n, m, e, t);
+        add_jt(rhs, J, n, e, t);
         for (int p = lane; p < n; p += 32) {
             double acc = rhs[p];
             for (int q = e.env[p]; q <= e.lastr[p]; ++q) acc -= Lf[p * n + q] * v[q];     // A v

@@ -536,6 +536,15 @@ int finalize(sim_t s)
             ipool.insert(ipool.end(), lastr.begin(), lastr.end());
             ipool.insert(ipool.end(), jlo.begin(), jlo.end());
             ipool.insert(ipool.end(), jhi.begin(), jhi.end());
+            // row groups: J^T J and J^T w sum a group's rows before touching K or the vector
+            u.grp_off = (int)ipool.size();
+            u.ngrp = 0;
+            for (int t = 0; t < m; ++t)
+                if (t == 0 || jlo[t] != jlo[t - 1] || jhi[t] != jhi[t - 1]) {
+                    ipool.push_back(t);
+                    ++u.ngrp;
+                }
+            ipool.push_back(m);
         }
         // work of the setup's scene-wide passes, as prefix sums over the scene's subsystems:
         // chunks of 32 columns of W = L^-1 [J^T b] (m + 1 columns), then the map's items of
