@@ -60,6 +60,7 @@ def lib(openmp: bool = False):
                 "orc_step": (C.c_int, [VP]),
                 "orc_assemble": (None, [VP]),
                 "orc_set_trace": (None, [VP, PD, C.c_int]),
+                "orc_set_pj": (C.c_int, [VP, C.c_int, D]),
                 "orc_nsub": (C.c_int, [VP]),
                 "orc_ncon": (C.c_int, [VP]),
                 "orc_n": (C.c_int, [VP, C.c_int]),
@@ -171,6 +172,9 @@ class OracleScene:
                 rc = L.orc_add_joint(self.h, int(itf.kind), itf.a[0], itf.a[1], sb, bb, _p(prm))
             if rc < 0:
                 raise ValueError("oracle rejected an interface")
+        if getattr(options, "solver", "admm") == "pj":
+            if L.orc_set_pj(self.h, 1, float(options.pj_omega)) < 0:
+                raise ValueError("oracle rejected the Projected Jacobi settings")
         self._trace = None
 
     def __del__(self):

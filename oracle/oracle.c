@@ -97,6 +97,8 @@ typedef struct {
 typedef struct orc_scene {
     double h, g[3], gamma, rho, tol, theta_th;
     int beta_fixed, warm_prev, stop_theta, max_iters;
+    int pj;                    /* 1: the step runs Projected Jacobi instead of ADMM */
+    double pj_omega;           /* its relaxation factor */
     int nsub, ncon, capsub, capcon;
     sub_t *subs;
     con_t *cons;
@@ -809,17 +811,29 @@ static double beta_of(orc_scene *S, int i)
     return S->subs[i].beta;
 }
 
-int orc_step(orc_scene *S)
+/* v_i = A_i^-1 (b_i + sum_j J_ij^T lambda_j) for every subsystem (A_i's factor in L) */
+static void pj_velocities(orc_scene *S)
 {
-    S->status = 0;
-    /* construct A_i, b_i */
+#pragma omp parallel for schedule(dynamic, 1)
     for (int i = 0; i < S->nsub; i++) {
-        if (S->subs[i].kind == SUB_RIGID) assemble_rigid(S, &S->subs[i]);
-        else if (S->subs[i].kind == SUB_LINEAR) assemble_linear(S, &S->subs[i]);
+        sub_t *u = &S->subs[i];
+        memcpy(u->v, u->b, sizeof(double) * u->n);
+        for (int j = 0; j < S->ncon; j++) {
+            con_t *c = &S->cons[j];
+            for (int s = 0; s < c->ns; s++) {
+                if (c->sub[s] != i) continue;
+                for (int r = 0; r < c->rows; r++)
+                    for (int p = 0; p < u->n; p++) u->v[p] += c->J[s][r * u->n + p] * c->lam[r];
+            }
+        }
+        chol_solve(u->n, u->L, u->v);
     }
-    /* construct e_j, J_j */
-    for (int j = 0; j < S->ncon; j++)
-        if (S->cons[j].src != SRC_ROWS) assemble_joint(S, &S->cons[j]);
+}
+
+/* The subsystem-based ADMM loop of one step (Algorithm 1) on the assembled A_i, b_i, J, e:
+ * leaves v-hat in each subsystem and lambda, z in each constraint. */
+static int admm_solve(orc_scene *S)
+{
     /* beta_i (Sec. III-D): the trace rule, or a fixed rho; times the subsystem's scale (an
        input: 1 unless a learned rho sets it) */
     for (int i = 0; i < S->nsub; i++) {
@@ -964,6 +978,143 @@ int orc_step(orc_scene *S)
         }
         if (!isfinite(rp) || !isfinite(theta)) { S->status = -4; break; }
     }
+    return S->status;
+}
+
+/* Projected Jacobi on the same step (the comparison solver of Sec. IV-B, written from the
+ * standard method, as its details are not printed): the dual problem over the impulses
+ * lambda with the subsystems' own A_i (no penalty term), v_i = A_i^-1 (b_i + J_i^T lambda).
+ *   delta_r = sum_i J_ir A_i^-1 J_ir^T   (the diagonal of the Delassus operator, per row)
+ *   loop l = 0 .. l_max - 1 (a fixed count: the step has no stop rule)
+ *     v_i = A_i^-1 (b_i + sum_j J_ij^T lambda_j);  x_r = sum_i J_ir v_i;  c_r = x_r + e_r
+ *     every row at once from these values, with relaxation omega:
+ *       equality  lambda_r -= omega c_r / delta_r
+ *       hard      lambda_r = max(0, lambda_r - omega c_r / delta_r)
+ *       soft      lambda*_r = -k (e_r + alpha (x_r - delta_r lambda_r)) / (1 + k alpha delta_r)
+ *                 (the soft law with x_r linearised in its own lambda), then
+ *                 lambda_r += omega (lambda*_r - lambda_r)
+ *       contact   lambda_n = max(0, lambda_n - omega c_n / delta_n); both tangent rows
+ *                 lambda_t -= omega c_t / delta_t with one delta_t = max(delta_t1, delta_t2)
+ *                 (an isotropic step, so that a sliding contact's exact impulse, on the
+ *                 cone's edge against the slip, is a fixed point), then (lambda_t1,
+ *                 lambda_t2) scaled onto the disk of radius mu lambda_n when outside it
+ *     r_p = max_r |lambda_r^{l+1} - lambda_r^l| delta_r / omega (the natural residual, in
+ *     constraint-velocity units)
+ *   v-hat = A^-1 (b + J^T lambda) with the last lambda.
+ * Starts from the previous step's lambda (warm) or zero. */
+static int pj_solve(orc_scene *S)
+{
+    int notspd = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : notspd)
+    for (int i = 0; i < S->nsub; i++) {
+        sub_t *u = &S->subs[i];
+        u->beta = 0.0;
+        if (cholesky(u->n, u->A, u->L)) notspd = 1;
+    }
+    if (notspd) { S->status = -3; return -3; }
+    /* delta per row: J_r A^-1 J_r^T summed over the sides */
+    double **delta = (double **)xcalloc(S->ncon, sizeof(double *));
+    for (int j = 0; j < S->ncon; j++) {
+        con_t *c = &S->cons[j];
+        delta[j] = (double *)xcalloc(c->rows, sizeof(double));
+        for (int s = 0; s < c->ns; s++) {
+            sub_t *u = &S->subs[c->sub[s]];
+            double *y = (double *)xcalloc(u->n, sizeof(double));
+            for (int r = 0; r < c->rows; r++) {
+                memcpy(y, c->J[s] + (size_t)r * u->n, sizeof(double) * u->n);
+                chol_solve(u->n, u->L, y);
+                double acc = 0.0;
+                for (int p = 0; p < u->n; p++) acc += c->J[s][r * u->n + p] * y[p];
+                delta[j][r] += acc;
+            }
+            free(y);
+        }
+    }
+    for (int j = 0; j < S->ncon; j++) {
+        con_t *c = &S->cons[j];
+        for (int r = 0; r < c->rows; r++)
+            c->lam[r] = (S->warm_prev && c->has_prev) ? c->lamprev[r] : 0.0;
+    }
+    const double om = S->pj_omega;
+    S->iters = 0; S->converged = 0;
+    S->r_p = INFINITY; S->r_d = 0.0; S->theta = 0.0;
+    for (int l = 0; l < S->max_iters; l++) {
+        pj_velocities(S);
+        double rp = 0.0;
+        for (int j = 0; j < S->ncon; j++) {
+            con_t *c = &S->cons[j];
+            double *x = (double *)xcalloc(c->rows, sizeof(double));
+            double *lo = (double *)xcalloc(c->rows, sizeof(double));
+            for (int r = 0; r < c->rows; r++) {
+                x[r] = 0.0;
+                for (int s = 0; s < c->ns; s++) {
+                    sub_t *u = &S->subs[c->sub[s]];
+                    for (int p = 0; p < u->n; p++) x[r] += c->J[s][r * u->n + p] * u->v[p];
+                }
+                lo[r] = c->lam[r];
+            }
+            double *dl = delta[j];
+            if (c->type == T_EQUALITY) {
+                for (int r = 0; r < c->rows; r++) c->lam[r] = lo[r] - om * (x[r] + c->e[r]) / dl[r];
+            } else if (c->type == T_HARD) {
+                for (int r = 0; r < c->rows; r++) {
+                    double t = lo[r] - om * (x[r] + c->e[r]) / dl[r];
+                    c->lam[r] = t > 0.0 ? t : 0.0;
+                }
+            } else if (c->type == T_SOFT) {
+                for (int r = 0; r < c->rows; r++) {
+                    double ka = c->k * c->alpha;
+                    double ls = -c->k * (c->e[r] + c->alpha * (x[r] - dl[r] * lo[r])) / (1.0 + ka * dl[r]);
+                    c->lam[r] = lo[r] + om * (ls - lo[r]);
+                }
+            } else {
+                double ln = lo[0] - om * (x[0] + c->e[0]) / dl[0];
+                ln = ln > 0.0 ? ln : 0.0;
+                const double dt = dl[1] > dl[2] ? dl[1] : dl[2];
+                dl[1] = dt;
+                dl[2] = dt;
+                double l1 = lo[1] - om * (x[1] + c->e[1]) / dt;
+                double l2 = lo[2] - om * (x[2] + c->e[2]) / dt;
+                double lim = c->mu * ln, t2 = l1 * l1 + l2 * l2;
+                if (t2 > lim * lim) {
+                    double f = lim / sqrt(t2);
+                    l1 *= f; l2 *= f;
+                }
+                c->lam[0] = ln; c->lam[1] = l1; c->lam[2] = l2;
+            }
+            for (int r = 0; r < c->rows; r++) {
+                double a = fabs(c->lam[r] - lo[r]) * dl[r] / om;
+                if (a > rp) rp = a;
+            }
+            free(x);
+            free(lo);
+        }
+        S->r_p = rp;
+        S->iters = l + 1;
+        if (S->trace && l < S->trace_cap) {
+            S->trace[3 * l] = 0.0; S->trace[3 * l + 1] = rp; S->trace[3 * l + 2] = 0.0;
+        }
+        if (!isfinite(rp)) { S->status = -4; break; }
+    }
+    pj_velocities(S);
+    for (int j = 0; j < S->ncon; j++) free(delta[j]);
+    free(delta);
+    return S->status;
+}
+
+int orc_step(orc_scene *S)
+{
+    S->status = 0;
+    /* construct A_i, b_i */
+    for (int i = 0; i < S->nsub; i++) {
+        if (S->subs[i].kind == SUB_RIGID) assemble_rigid(S, &S->subs[i]);
+        else if (S->subs[i].kind == SUB_LINEAR) assemble_linear(S, &S->subs[i]);
+    }
+    /* construct e_j, J_j */
+    for (int j = 0; j < S->ncon; j++)
+        if (S->cons[j].src != SRC_ROWS) assemble_joint(S, &S->cons[j]);
+    int rc = S->pj ? pj_solve(S) : admm_solve(S);
+    if (rc == -3) return rc;
     /* keep lambda and z for the next step's warm start */
     for (int j = 0; j < S->ncon; j++) {
         con_t *c = &S->cons[j];
@@ -1014,6 +1165,14 @@ int orc_step(orc_scene *S)
 /* accessors                                                                             */
 
 void orc_set_trace(orc_scene *S, double *buf, int cap) { S->trace = buf; S->trace_cap = cap; }
+/* Projected Jacobi instead of ADMM for every later step (on != 0), relaxation omega > 0 */
+int orc_set_pj(orc_scene *S, int on, double omega)
+{
+    if (on && !(omega > 0.0)) return -1;
+    S->pj = on ? 1 : 0;
+    S->pj_omega = omega;
+    return 0;
+}
 int orc_nsub(orc_scene *S) { return S->nsub; }
 int orc_ncon(orc_scene *S) { return S->ncon; }
 int orc_n(orc_scene *S, int i) { return S->subs[i].n; }

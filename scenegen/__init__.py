@@ -228,6 +228,9 @@ class Options:
     tol_primal: float = 1e-6      # <= 0 runs exactly max_iters iterations
     theta_th: float = 1e-12
     max_iters: int = 1000
+    solver: str = "admm"          # "admm" (the method) or "pj" (Projected Jacobi, the paper's
+                                  # comparison solver: always exactly max_iters iterations)
+    pj_omega: float = 1.0         # Projected Jacobi's relaxation factor
 
 
 @dataclass
