@@ -819,6 +819,8 @@ def sub_cable(ctx, args) -> dict:
 
 
 STIR_PAPER_MS = {30: 3.489, 60: 5.940, 90: 8.705}   # Table I, SubADMM, 4-core CPU
+STIR_PAPER_PJ_MS = {30: 3.235, 60: 5.688, 90: 9.425}  # Table I, PJ, same machine
+STIR_PJ_OMEGA = 0.3                                   # Projected Jacobi's relaxation here
 
 
 def sub_stir(ctx, args) -> dict:
@@ -849,6 +851,16 @@ def sub_stir(ctx, args) -> dict:
         if not args.no_cpu_baseline:                 # sub-results run at N = 1 only
             row["oracle_ms_per_step"] = oracle_stir_ms(p, steps=5)
         row["paper_over_mixed"] = STIR_PAPER_MS[iters] / row["mixed"]["ms_per_step"]
+        # the paper's Projected Jacobi comparison solver on the same scene (sim_set_solver)
+        q = sg.stir(0, tol_primal=-1, max_iters=iters)
+        q.options.solver, q.options.pj_omega = "pj", STIR_PJ_OMEGA
+        r = time_form(ctx, q, sa.SIM_MIXED, K, args.warmup, 0, 50, autotune=True, graph=False,
+                      grid_rows=1)
+        row["projected_jacobi_mixed"] = {
+            "ms_per_step": r["t_ms"] / K, "omega": STIR_PJ_OMEGA,
+            "natural_residual_after": r["sim"].residuals(0)["r_p"],
+            "paper_ms_per_step": STIR_PAPER_PJ_MS[iters]}
+        r["sim"].close()
         out[str(iters)] = row
     out["value"] = 1e3 / out["90"]["mixed"]["ms_per_step"]
     out["unit"] = "steps/s at 90 iterations"

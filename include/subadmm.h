@@ -282,6 +282,26 @@ int sim_set_beta_scale(sim_t s, const double *scale);
  * block, FP32 CUDA cores).  Must be called before the first sim_step (SIM_EINVAL after). */
 int sim_tensor_cores(sim_t s, int enable);
 
+/* The solver of every step (Sec. IV-B compares the method with other solvers on the same
+ * scenes; Projected Jacobi is one of them):
+ *   SIM_SOLVER_ADMM (default): subsystem-based ADMM, Algorithm 1.
+ *   SIM_SOLVER_PJ: Projected Jacobi on the step's dual problem, relaxation omega > 0.  With
+ *     A_i's own factor (no penalty term): D_i = J_i A_i^-1 J_i^T, c_i = J_i A_i^-1 b_i, the
+ *     diagonal delta_r = sum over the row's sides of D_i's entry; every iteration forms
+ *     each side's x = c + D lambda and updates every row at once: equality
+ *     lambda -= omega (x + e) / delta; hard the same clamped at 0; soft lambda += omega
+ *     (lambda* - lambda) with lambda* = -k (e + alpha (x - delta lambda)) / (1 + k alpha
+ *     delta); contact: normal as hard, both tangents with delta_t = max of theirs, then
+ *     scaled onto the disk of radius mu lambda_n.  Exactly max_iters iterations per step
+ *     (tol_primal and the stop rule are ignored); v-hat = A^-1 (b + J^T lambda).  The
+ *     reported r_p is the last iteration's natural residual max |d lambda| delta / omega;
+ *     r_d and theta are 0.  The learned warm start and the tensor-core map are not used.
+ * Must be called before the first sim_step (SIM_EINVAL after); SIM_EINVAL for an unknown
+ * solver or omega <= 0. */
+#define SIM_SOLVER_ADMM 0
+#define SIM_SOLVER_PJ 1
+int sim_set_solver(sim_t s, int solver, double omega);
+
 /* Grid kernel: run the cooperative launch with `blocks` blocks (at most the resident count;
  * 0, the default, takes every resident block: 2 per SM).  Fewer blocks give each warp more
  * side-rows, subsystems and items; the results do not depend on it.  Takes effect at the

@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 2) grid_step_kernel(StepParam
         // to warp g, i.e. warp g / blocks of block g % blocks), so that a scene with few
         // items spreads them over the SMs rather than filling the first blocks.
         const int ix = 32 * d.warp + lane;
-        const bool icache = S.nitem <= d.nthreads;
+        const bool icache = S.nitem <= d.nthreads && !P.pj;
         RegItem<T, false> ri;
         bool igeneric = false;
         if (icache && ix < S.nitem) {
@@ -459,6 +459,11 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 2) grid_step_kernel(StepParam
                     const Item it = V.item[i];
                     if (it.type < 0) continue;
                     const int *ls = V.list + it.lo;
+                    if (P.pj) {
+                        mloc = pj_item<T, U>(it, ls, X, E, INVS, KF, AL, MU, LAM, Z, ZO, wn,
+                                             (T)P.pj_omega, mloc);
+                        continue;
+                    }
                     if (it.type == TYPE_CONTACT) {
                         T q0 = (T)0, q1 = (T)0, q2 = (T)0;
                         for (int s = 0; s < it.ns; ++s) {
@@ -555,7 +560,10 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 2) grid_step_kernel(StepParam
             // the warp's stage buffers (idle outside the v-step) hold the solves' vector,
             // unless a copy into them may still be in flight (after a missed wait)
             const bool stg_free = P.grid_stage > 0 && __all_sync(0xffffffffu, pend == 0u);
-            recover_v<T>(P, S, V, last_par ? W1 : W0, d,
+            // v-hat from the last v-step's w (ADMM), or from the last z-step's lambda
+            // (Projected Jacobi: v-hat = A^-1 (b + J^T lambda) with the impulses it reports)
+            const int wpar = P.pj ? par : last_par;
+            recover_v<T>(P, S, V, wpar ? W1 : W0, d,
                          stg_free ? reinterpret_cast<T *>(stg) : nullptr,
                          stg_free ? nst * P.grid_stage / (int)sizeof(T) : 0);
             d.sync();

@@ -127,6 +127,8 @@ struct GridScratch {
 };
 
 struct StepParams {
+    int pj;                // 1: Projected Jacobi (the comparison solver) instead of ADMM
+    double pj_omega;       // its relaxation factor
     const SceneDesc *scenes;
     const int *scene_ids;  // the scenes of this launch (indices into scenes)
     const SubDesc *subs;

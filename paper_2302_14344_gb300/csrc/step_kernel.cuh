@@ -780,6 +780,7 @@ __device__ long long scene_setup(const StepParams &P, const SceneDesc &S, const 
             beta = (double)(P.beta_fixed ? (T)P.rho : (trJ > (T)0 ? trA / trJ : (T)1));
         }
         beta *= P.beta_scale[gsub];
+        if (P.pj) beta = 0.0;                       // Projected Jacobi: K_i = A_i
         if (lane == 0) {
             db[S.od_beta + i] = beta;
             P.beta[gsub] = beta;
@@ -880,6 +881,42 @@ __device__ long long scene_setup(const StepParams &P, const SceneDesc &S, const 
     const double *BETA = db + S.od_beta;
     for (int j = d.tid; j < S.ncon; j += d.nthreads) {
         const ConDesc &c = P.cons[S.con0 + j];
+        if (P.pj) {
+            // Projected Jacobi: 1/delta per row, delta = the sum over its sides of D's diagonal
+            // entry (both tangents of a contact take the larger of theirs), soft gain
+            // k/(1 + k alpha delta); beta and 1/beta per side-row are zero
+            double kk, al, mu;
+            con_params(c, P.pool, P.h, kk, al, mu);
+            double dl[3] = {0.0, 0.0, 0.0};
+            for (int r = 0; r < c.rows; ++r) {
+                double dr = 0.0;
+                for (int q = 0; q < c.ns; ++q) {
+                    const SubDesc &u = P.subs[S.sub0 + c.sub[q]];
+                    const int lr = c.sr[q] + r - u.sr0;
+                    dr += (double)htb[u.ot_D + (size_t)lr * u.ldd + lr];
+                }
+                if (c.type == TYPE_CONTACT) dl[r] = dr;
+                else {
+                    INVS[c.row0 + r] = (T)(1.0 / dr);
+                    KF[c.row0 + r] = (T)(c.type == TYPE_SOFT ? kk / (1.0 + kk * al * dr) : 0.0);
+                }
+                AL[c.row0 + r] = (T)al;
+                MU[c.row0 + r] = (T)mu;
+            }
+            if (c.type == TYPE_CONTACT) {
+                const double dt = dl[1] > dl[2] ? dl[1] : dl[2];
+                INVS[c.row0] = (T)(1.0 / dl[0]);
+                INVS[c.row0 + 1] = (T)(1.0 / dt);
+                INVS[c.row0 + 2] = (T)(1.0 / dt);
+                for (int r = 0; r < 3; ++r) KF[c.row0 + r] = (T)0;
+            }
+            for (int q = 0; q < c.ns; ++q)
+                for (int r = 0; r < c.rows; ++r) {
+                    INVB[c.sr[q] + r] = (T)0;
+                    BT[c.sr[q] + r] = (T)0;
+                }
+            continue;
+        }
         double s = 0.0;
         for (int q = 0; q < c.ns; ++q) s += 1.0 / BETA[c.sub[q]];
         double kk, al, mu;
@@ -1062,6 +1099,54 @@ __device__ void init_duals(const StepParams &P, const SceneDesc &S, const View<T
         W0[t] = beta * z + l;
     }
     d.sync();
+}
+
+// One item of a Projected Jacobi iteration (the comparison solver of Sec. IV-B): the row's
+// (or contact's) constraint value from the x of its sides, the relaxed Jacobi update of its
+// impulse with 1/delta from INVS (soft rows: the soft law with x linearised in the row's own
+// lambda; contacts: normal clamped at 0, tangents scaled onto the friction disk), w =
+// lambda on every side for the next v-step, and the natural residual |d lambda| delta /
+// omega, written as x - z of the first side-row (z = x on the others) so that the step's
+// residuals report it; returns its bits
+template <typename T, typename U>
+__device__ __forceinline__ U pj_item(const Item &it, const int *ls, const T *X, const T *E,
+                                     const T *INVS, const T *KF, const T *AL, const T *MU,
+                                     T *LAM, T *Z, T *ZO, T *wn, T om, U mloc)
+{
+    const int nr = it.type == TYPE_CONTACT ? 3 : 1;
+    T xr[3] = {(T)0, (T)0, (T)0}, lo[3], ln[3], id[3];
+    for (int s = 0; s < it.ns; ++s)
+        for (int r = 0; r < nr; ++r) xr[r] += X[ls[s] + r];
+    for (int r = 0; r < nr; ++r) { lo[r] = LAM[it.row + r]; id[r] = INVS[it.row + r]; }
+    if (it.type == TYPE_CONTACT) {
+        T n = lo[0] - om * (xr[0] + E[it.row]) * id[0];
+        n = n > (T)0 ? n : (T)0;
+        T l1 = lo[1] - om * (xr[1] + E[it.row + 1]) * id[1];
+        T l2 = lo[2] - om * (xr[2] + E[it.row + 2]) * id[2];
+        const T lim = MU[it.row] * n, t2 = l1 * l1 + l2 * l2;
+        if (t2 > lim * lim) { const T f = lim * rsq(t2); l1 *= f; l2 *= f; }
+        ln[0] = n; ln[1] = l1; ln[2] = l2;
+    } else if (it.type == TYPE_SOFT) {
+        const T dl = (T)1 / id[0];
+        const T ls_ = -KF[it.row] * (E[it.row] + AL[it.row] * (xr[0] - dl * lo[0]));
+        ln[0] = lo[0] + om * (ls_ - lo[0]);
+    } else {
+        ln[0] = lo[0] - om * (xr[0] + E[it.row]) * id[0];
+        if (it.type == TYPE_HARD) ln[0] = ln[0] > (T)0 ? ln[0] : (T)0;
+    }
+    for (int r = 0; r < nr; ++r) {
+        LAM[it.row + r] = ln[r];
+        const T res = fabs(ln[r] - lo[r]) / (om * id[r]);
+        mloc = umax(mloc, rbits(res));
+        for (int s = 0; s < it.ns; ++s) {
+            const int t = ls[s] + r;
+            const T zv = s == 0 ? X[t] - res : X[t];
+            ZO[t] = zv;
+            Z[t] = zv;
+            wn[t] = ln[r];
+        }
+    }
+    return mloc;
 }
 
 // One z-step item held in a thread's registers for a whole step (items with at most two
@@ -1509,6 +1594,11 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, CACHED ? 1 : 2) step_kernel(S
                             const Item it = V.item[i];
                             if (it.type < 0) continue;
                             const int *ls = V.list + it.lo;
+                            if (P.pj) {
+                                mloc = pj_item<T, U>(it, ls, X, E, INVS, KF, AL, MU, LAM, Z, ZO,
+                                                     wn, (T)P.pj_omega, mloc);
+                                continue;
+                            }
                             if (it.type == TYPE_CONTACT) {
                                 T q0 = (T)0, q1 = (T)0, q2 = (T)0;
                                 for (int s = 0; s < it.ns; ++s) {
@@ -1621,7 +1711,9 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, CACHED ? 1 : 2) step_kernel(S
                     LAM[xrow] = lreg;
                 }
                 __syncthreads();
-                block_recover<T>(P, S, V, last_par ? W1 : W0);
+                // v-hat from the last v-step's w (ADMM), or from the last z-step's lambda
+                // (Projected Jacobi: v-hat = A^-1 (b + J^T lambda) with the reported impulses)
+                block_recover<T>(P, S, V, (P.pj ? par : last_par) ? W1 : W0);
                 __syncthreads();
                 if (MIXED && conv && primal_stop && status == ST_OK) {
                     // FP64 primal residual max |J v - z|; on a miss, refine c by the FP64 - FP32

@@ -109,6 +109,8 @@ struct sim_s {
     int grid_staging = 1;          // grid kernel: stage D rows in shared memory by bulk copies
     int grid_blocks = 0;           // grid kernel: blocks of the cooperative launch (0: all resident)
     int keep_factors = 1;          // keep the factors of constant blocks across steps
+    int pj = 0;                    // Projected Jacobi instead of ADMM (sim_set_solver)
+    double pj_omega = 1.0;
     int tensor_cores = 1;          // grid scenes, mixed form: D, c by the tcgen05 Gram kernel
     std::vector<subadmm::GramPlan> gram;   // per scene: Gram jobs of its tc subsystems
     std::vector<char> grid_factored;       // per scene: its tc subsystems hold kept factors
@@ -730,7 +732,7 @@ int finalize(sim_t s)
         }
         if (s->split_override > 0) split = s->split_override;
         const int si = split == 4 ? 2 : split == 2 ? 1 : 0;
-        const bool cached = !grid && s->opt.stop != SIM_STOP_THETA && (sc_fmap_ok[sc] >> si & 1) &&
+        const bool cached = !grid && !s->pj && s->opt.stop != SIM_STOP_THETA && (sc_fmap_ok[sc] >> si & 1) &&
                             sc_sides[sc] <= 2 && (sc_mpad[sc] + vn - 1) / vn <= chunks * split;
         const bool half = !grid && !cached && bytes_with(q, q.scd, q.sh + q.scene_t) <= half_budget;
         sc_budget[sc] = half ? half_budget : smem_budget;
@@ -761,7 +763,7 @@ int finalize(sim_t s)
             // whenever they are refactorised
             for (int i = 0; i < S.nsub; ++i) {
                 SubDesc &u = s->sdesc[S.sub0 + i];
-                u.tc = (s->tensor_cores && s->opt.precision == SIM_MIXED && u.n >= 128 &&
+                u.tc = (s->tensor_cores && !s->pj && s->opt.precision == SIM_MIXED && u.n >= 128 &&
                         u.m >= 16) ? 1 : 0;
             }
             // everything in the workspace: the per-subsystem arrays, then the scene arrays
@@ -1225,6 +1227,10 @@ StepParams step_params(const sim_t s, int n_steps)
     P.beta_fixed = s->opt.beta_mode == SIM_BETA_FIXED;
     P.warm_prev = s->opt.warm == SIM_WARM_PREV;
     P.stop_theta = s->opt.stop == SIM_STOP_THETA;
+    // Projected Jacobi: always exactly max_iters iterations
+    P.pj = s->pj;
+    P.pj_omega = s->pj_omega;
+    if (s->pj) { P.tol = -1.0; P.stop_theta = 0; }
     P.max_iters = s->opt.max_iters;
     P.items = s->d_items;
     P.lists = s->d_lists;
@@ -1591,7 +1597,7 @@ int sim_autotune(sim_t s, int steps, int max_classes, long long *out)
         for (int cached = 0; cached < 2 && err == cudaSuccess; ++cached) {
             for (int split = 1; split <= 4 && err == cudaSuccess; split *= 2) {
                 if (cached) {
-                    bool ok = true;
+                    bool ok = !s->pj && s->opt.stop != SIM_STOP_THETA;
                     for (int sc : c.scenes) ok = ok && cache_fits(s, sc, split);
                     if (!ok) continue;
                 }
@@ -1675,6 +1681,7 @@ int sim_step_learned(sim_t s, wsn_t net, int n_steps)
 {
     if (!s || !net) return SIM_EINVAL;
     if (n_steps < 1) return fail(s, SIM_EINVAL, "n_steps must be >= 1");
+    if (s->pj) return fail(s, SIM_EINVAL, "the learned warm start serves the ADMM solver only");
     int shape[2] = {0, 0};
     if (wsn_shape(net, shape) || shape[0] != subadmm::kFeatures || shape[1] != subadmm::kDualOut)
         return fail(s, SIM_EINVAL, "the network must map 32 features to 7 outputs");
@@ -1822,6 +1829,19 @@ int sim_grid_blocks(sim_t s, int blocks)
     if (!s) return SIM_EINVAL;
     if (blocks < 0) return fail(s, SIM_EINVAL, "blocks must be >= 0");
     s->grid_blocks = blocks;
+    return SIM_OK;
+}
+
+int sim_set_solver(sim_t s, int solver, double omega)
+{
+    if (!s) return SIM_EINVAL;
+    if (s->finalized) return fail(s, SIM_EINVAL, "the solver is fixed after the first sim_step");
+    if (solver != SIM_SOLVER_ADMM && solver != SIM_SOLVER_PJ)
+        return fail(s, SIM_EINVAL, "unknown solver");
+    if (solver == SIM_SOLVER_PJ && !(omega > 0.0 && std::isfinite(omega)))
+        return fail(s, SIM_EINVAL, "Projected Jacobi needs a finite omega > 0");
+    s->pj = solver == SIM_SOLVER_PJ ? 1 : 0;
+    s->pj_omega = s->pj ? omega : 1.0;
     return SIM_OK;
 }
 
