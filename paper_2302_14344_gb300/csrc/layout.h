@@ -45,6 +45,8 @@ struct SceneDesc {
     // ipool offset of three prefix sums over the subsystems (nsub + 1 each): chunks of 32
     // columns of W, items of c, items of D (the setup's scene-wide work lists)
     int pre_off;
+    int ord_off;           // ipool offset: the subsystems in decreasing order of per-warp setup
+                           // work (the order the per-warp loops take them in)
     int sr_g0, row_g0;     // global offset of the scene's side-rows / rows (z, lambda state)
     // double region
     int od_beta;           // beta per subsystem

@@ -737,7 +737,8 @@ __device__ long long scene_setup(const StepParams &P, const SceneDesc &S, const 
     // the map W = L^-1 [J^T b], D = W^T W, c.  The FP64 form and the stiff blocks of the mixed
     // form factorise K in FP64 (rounded into the T copy); the other mixed blocks factorise in
     // FP32, keeping the FP64 A, b and J for the recovery and refinement of v-hat.
-    for (int i = d.warp; i < S.nsub; i += d.nwarps) {
+    for (int k = d.warp; k < S.nsub; k += d.nwarps) {
+        const int i = __ldg(P.ipool + S.ord_off + k);          // largest first
         const SubDesc &u = P.subs[S.sub0 + i];
         const int gsub = S.sub0 + i;
         // W's leading dimension: m + 1 columns rounded up to 4 (map_item reads 4-column blocks)
@@ -994,7 +995,8 @@ __device__ void recover_v(const StepParams &P, const SceneDesc &S, const View<T>
 {
     constexpr bool MIXED = sizeof(T) == 4;
     const int lane = threadIdx.x & 31;
-    for (int i = d.warp; i < S.nsub; i += d.nwarps) {
+    for (int k = d.warp; k < S.nsub; k += d.nwarps) {
+        const int i = __ldg(P.ipool + S.ord_off + k);          // largest first
         const SubDesc &u = P.subs[S.sub0 + i];
         const int n = u.n, m = u.m;
         const SubEnv e = sub_env(P, u);

@@ -453,6 +453,7 @@ int finalize(sim_t s)
         // the envelope, lastr[k] = last row whose envelope reaches column k; and the column
         // span [jlo, jhi) of every J row (empty rows: jlo = jhi = n).  Cholesky fill stays
         // inside the envelope, so the factorisation and the solves skip everything outside.
+        std::vector<long long> setup_cost(S.nsub, 0);
         for (int i = 0; i < S.nsub; ++i) {
             SubDesc &u = s->sdesc[S.sub0 + i];
             const HostSub &hs = s->subs[sub_order[S.sub0 + i]];
@@ -547,6 +548,23 @@ int finalize(sim_t s)
                     ++u.ngrp;
                 }
             ipool.push_back(m);
+            // the subsystem's per-warp work in the setup and the recovery: the envelope
+            // Cholesky and solves (band width squared per column) and J^T J (span squared
+            // per row)
+            long long c = 0;
+            for (int p = 0; p < n; ++p) c += (long long)(p - env[p] + 1) * (p - env[p] + 1);
+            for (int t = 0; t < m; ++t) c += (long long)(jhi[t] - jlo[t]) * (jhi[t] - jlo[t]);
+            setup_cost[i] = c;
+        }
+        // the order in which warps take the subsystems in the per-warp loops (largest first,
+        // so that the largest ones go to different warps)
+        S.ord_off = (int)ipool.size();
+        {
+            std::vector<int> ord(S.nsub);
+            for (int i = 0; i < S.nsub; ++i) ord[i] = i;
+            std::stable_sort(ord.begin(), ord.end(),
+                             [&](int a, int b) { return setup_cost[a] > setup_cost[b]; });
+            ipool.insert(ipool.end(), ord.begin(), ord.end());
         }
         // work of the setup's scene-wide passes, as prefix sums over the scene's subsystems:
         // chunks of 32 columns of W = L^-1 [J^T b] (m + 1 columns), then the map's items of
