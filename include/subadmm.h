@@ -185,13 +185,16 @@ int sim_step(sim_t s, int n_steps);
  * scene at a time, and are never captured into a graph.
  * sim_launch_classes lays the simulation out if needed and writes, for each class k <
  * max_classes, five counts at out[5k]: scenes, kernel (0 generic, 1 register-cached, 2
- * grid), lanes per side-row (1, 2 or 4; 8, 16 or 32 for the grid kernel), dynamic shared
+ * grid, 3 generic with 512 threads per block: a class whose scenes take a whole SM's shared
+ * memory, so that a block has the whole register file and twice the warps), lanes per
+ * side-row (1, 2 or 4; 8, 16 or 32 for the grid kernel), dynamic shared
  * memory per block in bytes (for a grid class: its staged D-row buffers at its last launch,
  * 0 before the first or without staging, see sim_grid_staging), 0.  Returns the number
  * of classes, or a negative SIM_E* code.
  * sim_autotune times, for each class on its own, every kernel variant that is valid for all
- * its scenes (generic with 1, 2 or 4 lanes per side-row, register-cached where the scenes
- * fit; the grid kernel with 8, 16 or 32) over `steps` steps from the current state, keeps the fastest, and restores the state
+ * its scenes (generic with 1, 2 or 4 lanes per side-row and 256 or 512 threads per block,
+ * register-cached where the scenes fit; the grid kernel with 8, 16 or 32) over `steps`
+ * steps from the current state, keeps the fastest, and restores the state
  * (bodies, nodes, warm-start duals, outputs, counters) so that tuning leaves no trace.  It
  * waits for the stream, allocates a temporary snapshot, and writes the same rows as
  * sim_launch_classes with out[5k + 4] the chosen variant's time per step in nanoseconds.

@@ -5,6 +5,8 @@
 #define SUBADMM_MAXS 8          // most sides one constraint may have (|S_j|)
 #define SUBADMM_THREADS 256     // threads of one scene's block
 #define SUBADMM_WARPS (SUBADMM_THREADS / 32)
+#define SUBADMM_WIDE 512        // threads of the wide block-kernel variant (one block per SM)
+#define SUBADMM_MAXWARPS (SUBADMM_WIDE / 32)
 #define SUBADMM_MAXN 2048       // largest subsystem DOF
 #define SUBADMM_MAXM 2048       // largest side-row count of one subsystem
 #define SUBADMM_PARAMS 23       // doubles of a rigid-model constraint's parameters

@@ -98,8 +98,8 @@ __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
 
 // Sum (a) and maxima (b, c) of three per-thread doubles over the block.
-__device__ __forceinline__ void block_reduce3(double (*red)[SUBADMM_WARPS], double &a, double &b,
-                                              double &c)
+__device__ __forceinline__ void block_reduce3(double (*red)[SUBADMM_MAXWARPS], double &a,
+                                              double &b, double &c)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     a = warp_sum(a); b = warp_max(b); c = warp_max(c);
@@ -107,7 +107,7 @@ __device__ __forceinline__ void block_reduce3(double (*red)[SUBADMM_WARPS], doub
     if (lane == 0) { red[0][warp] = a; red[1][warp] = b; red[2][warp] = c; }
     __syncthreads();
     a = 0.0; b = 0.0; c = 0.0;
-    for (int q = 0; q < SUBADMM_WARPS; ++q) {
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
         a += red[0][q]; b = nanmax(b, red[1][q]); c = nanmax(c, red[2][q]);
     }
     __syncthreads();
@@ -1352,16 +1352,21 @@ struct RegItem {
     }
 };
 
-template <typename T, int SPLIT, bool CACHED>
-__global__ void __launch_bounds__(SUBADMM_THREADS, CACHED ? 1 : 2) step_kernel(StepParams P)
+// NT threads per block: SUBADMM_THREADS, or SUBADMM_WIDE for a generic variant of a class
+// whose scenes take a whole SM's shared memory (one block per SM), which then uses the whole
+// register file and twice the warps per scene
+template <typename T, int SPLIT, bool CACHED, int NT = SUBADMM_THREADS>
+__global__ void __launch_bounds__(NT, (CACHED || NT > SUBADMM_THREADS) ? 1 : 2) step_kernel(StepParams P)
 {
+    static_assert(!CACHED || NT == SUBADMM_THREADS, "the register-cached map is laid out for 256 threads");
+    constexpr int NW = NT / 32;
     using VT = typename VecOf<T>::V;
     using U = typename VecOf<T>::U;
     constexpr int VN = VecOf<T>::N;
     extern __shared__ __align__(16) unsigned char smraw[];
-    __shared__ double red[4][SUBADMM_WARPS];
-    __shared__ U ured[2][SUBADMM_WARPS];
-    __shared__ T tred[2][SUBADMM_WARPS];
+    __shared__ double red[4][SUBADMM_MAXWARPS];
+    __shared__ U ured[2][NW];
+    __shared__ T tred[2][NW];
     __shared__ int s_status;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr bool MIXED = sizeof(T) == 4;
@@ -1526,7 +1531,7 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, CACHED ? 1 : 2) step_kernel(S
                     } else {
                         // two side-rows per trip, two accumulators per row: independent
                         // load and FMA chains overlap
-                        constexpr int groups = SUBADMM_THREADS / SPLIT;
+                        constexpr int groups = NT / SPLIT;
                         const int trips = (S.nsr + groups - 1) / groups;
                         for (int k = 0; k < trips; k += 2) {
                             int tt[2], mm[2];
@@ -1584,7 +1589,7 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, CACHED ? 1 : 2) step_kernel(S
                     iters = l + 1;
                     if (!CACHED && P.stop_theta) {
                         T ths = (T)0;
-                        for (int q = 0; q < SUBADMM_WARPS; ++q) ths += tred[l & 1][q];
+                        for (int q = 0; q < NW; ++q) ths += tred[l & 1][q];
                         if (l >= 1 && ths < theta_thT) { th = (double)ths; conv = 1; break; }
                     }
                     // ---- z-step (Sec. III-C); u = -lambda; max(|x - z|, |dz|) as bits
@@ -1592,7 +1597,7 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, CACHED ? 1 : 2) step_kernel(S
                     if (CACHED) {
                         mloc = mfused;
                     } else {
-                        for (int i = tid; i < S.nitem; i += SUBADMM_THREADS) {
+                        for (int i = tid; i < S.nitem; i += NT) {
                             const Item it = V.item[i];
                             if (it.type < 0) continue;
                             const int *ls = V.list + it.lo;
@@ -1674,7 +1679,7 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, CACHED ? 1 : 2) step_kernel(S
                     __syncthreads();
                     U mx = 0;
 #pragma unroll
-                    for (int q = 0; q < SUBADMM_WARPS; ++q) mx = umax(mx, ured[l & 1][q]);
+                    for (int q = 0; q < NW; ++q) mx = umax(mx, ured[l & 1][q]);
                     par ^= 1;
                     pc.mark(PHASE_ZSTEP);
                     {
@@ -1768,7 +1773,7 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, CACHED ? 1 : 2) step_kernel(S
             if (status == ST_OK && !(isfinite(rp) && isfinite(rd))) { status = ST_NAN; conv = 0; }
             pc.mark(PHASE_EXIT);
             // v-hat out and state update of rigid bodies (Algorithm 1, after the loop)
-            for (int i = warp; i < S.nsub; i += SUBADMM_WARPS) {
+            for (int i = warp; i < S.nsub; i += NW) {
                 const SubDesc &u = P.subs[S.sub0 + i];
                 const double *v = V.sdb + u.od_v;
                 for (int p = lane; p < u.n; p += 32) P.vhat[u.v_off + p] = v[p];

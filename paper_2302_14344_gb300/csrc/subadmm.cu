@@ -43,6 +43,8 @@ struct LaunchClass {
     int split = 1;                 // lanes per side-row in the v-step mat-vec
     bool half = false;             // placed within half an SM's shared memory (two blocks/SM)
     bool grid = false;             // one scene at a time over the whole GPU (cooperative launch)
+    int nt = SUBADMM_THREADS;      // threads per block (SUBADMM_WIDE: a generic class whose
+                                   // scenes take a whole SM, one block per SM)
     int blocks = 0;                // grid class: blocks of the cooperative launch
     std::vector<int> scenes;
     int ids_off = 0;               // offset of the scene list in d_scene_ids
@@ -330,7 +332,8 @@ int finalize(sim_t s)
     int dev_max_smem = 0;
     CK(cudaDeviceGetAttribute(&dev_max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->opt.device),
        "attribute");
-    const int smem_budget = dev_max_smem - 1024;   // static shared memory of the kernel
+    // the kernels' static shared memory (the wide FP64 variant's reduction arrays: ~1 KB)
+    const int smem_budget = dev_max_smem - 2048;
     s->smem_full = smem_budget;
     int sm_smem = 0;
     CK(cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, s->opt.device),
@@ -761,6 +764,7 @@ int finalize(sim_t s)
         if (k == (int)s->classes.size()) {
             LaunchClass c;
             c.cached = cached; c.split = split; c.half = half; c.grid = grid;
+            c.nt = (!cached && !half && !grid) ? SUBADMM_WIDE : SUBADMM_THREADS;
             s->classes.push_back(c);
         }
         s->classes[k].scenes.push_back(sc);
@@ -1262,9 +1266,18 @@ StepParams step_params(const sim_t s, int n_steps)
     return P;
 }
 
-KernFn kernel_for(bool mixed, bool cached, int split)
+KernFn kernel_for(bool mixed, bool cached, int split, int nt = SUBADMM_THREADS)
 {
     using namespace subadmm;
+    if (!cached && nt == SUBADMM_WIDE) {
+        if (mixed)
+            return split == 4 ? step_kernel<float, 4, false, SUBADMM_WIDE>
+                 : split == 2 ? step_kernel<float, 2, false, SUBADMM_WIDE>
+                              : step_kernel<float, 1, false, SUBADMM_WIDE>;
+        return split == 4 ? step_kernel<double, 4, false, SUBADMM_WIDE>
+             : split == 2 ? step_kernel<double, 2, false, SUBADMM_WIDE>
+                          : step_kernel<double, 1, false, SUBADMM_WIDE>;
+    }
     if (mixed) {
         if (cached) return split == 4 ? step_kernel<float, 4, true> : split == 2 ? step_kernel<float, 2, true> : step_kernel<float, 1, true>;
         return split == 4 ? step_kernel<float, 4, false> : split == 2 ? step_kernel<float, 2, false> : step_kernel<float, 1, false>;
@@ -1417,7 +1430,7 @@ int launch_classes(sim_t s, StepParams P, cudaStream_t base)
         if (j > 0) CK(cudaStreamWaitEvent(st, s->ev_fork, 0), "fork wait");
         P.scene_ids = s->d_scene_ids + c.ids_off;
         P.nscenes = (int)c.scenes.size();
-        kernel_for(mixed, c.cached, c.split)<<<P.nscenes, SUBADMM_THREADS, c.max_smem, st>>>(P);
+        kernel_for(mixed, c.cached, c.split, c.nt)<<<P.nscenes, c.nt, c.max_smem, st>>>(P);
         CK(cudaGetLastError(), "step kernel launch");
         if (j > 0) {
             CK(cudaEventRecord(c.done, st), "join");
@@ -1443,7 +1456,7 @@ int sim_step(sim_t s, int n_steps)
     // the attribute is per function (shared by every simulation of the process): allow the
     // full budget; each launch requests its class's own size, which sets its occupancy
     for (const LaunchClass &c : s->classes)
-        CK(cudaFuncSetAttribute(kernel_for(s->opt.precision == SIM_MIXED, c.cached, c.split),
+        CK(cudaFuncSetAttribute(kernel_for(s->opt.precision == SIM_MIXED, c.cached, c.split, c.nt),
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, s->smem_full),
            "shared memory attribute");
     bool has_grid = false;
@@ -1512,7 +1525,7 @@ void class_rows(const sim_t s, int max_classes, long long *out, const std::vecto
     for (int k = 0; k < (int)s->classes.size() && k < max_classes; ++k) {
         const LaunchClass &c = s->classes[k];
         out[5 * k + 0] = (long long)c.scenes.size();
-        out[5 * k + 1] = c.grid ? 2 : c.cached ? 1 : 0;
+        out[5 * k + 1] = c.grid ? 2 : c.cached ? 1 : c.nt == SUBADMM_WIDE ? 3 : 0;
         out[5 * k + 2] = c.split;
         out[5 * k + 3] = c.max_smem;
         out[5 * k + 4] = ns ? (long long)(*ns)[k] : 0;
@@ -1575,9 +1588,10 @@ int sim_autotune(sim_t s, int steps, int max_classes, long long *out)
         return cudaSuccess;
     };
     StepParams P = step_params(s, steps);
-    for (int cached = 0; cached < 2; ++cached)
+    for (int variant = 0; variant < 3; ++variant)
         for (int split = 1; split <= 4; split *= 2)
-            CK(cudaFuncSetAttribute(kernel_for(s->opt.precision == SIM_MIXED, cached, split),
+            CK(cudaFuncSetAttribute(kernel_for(s->opt.precision == SIM_MIXED, variant == 1, split,
+                                               variant == 2 ? SUBADMM_WIDE : SUBADMM_THREADS),
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, s->smem_full),
                "shared memory attribute");
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1592,7 +1606,7 @@ int sim_autotune(sim_t s, int steps, int max_classes, long long *out)
         P.nscenes = (int)c.scenes.size();
         double best = 1e300;
         bool bc = c.cached;
-        int bs = c.split;
+        int bs = c.split, bt = c.nt;
         if (c.grid) {
             for (int split = 8; split <= 32 && err == cudaSuccess; split *= 2) {
                 float ms = 0.0f;
@@ -1612,30 +1626,34 @@ int sim_autotune(sim_t s, int steps, int max_classes, long long *out)
             best_ns[k] = best * 1e6 / steps;
             continue;
         }
-        for (int cached = 0; cached < 2 && err == cudaSuccess; ++cached) {
+        // variants: generic (256 threads), register-cached (256), generic wide (512 threads)
+        for (int variant = 0; variant < 3 && err == cudaSuccess; ++variant) {
+            const bool cached = variant == 1;
+            const int nt = variant == 2 ? SUBADMM_WIDE : SUBADMM_THREADS;
             for (int split = 1; split <= 4 && err == cudaSuccess; split *= 2) {
                 if (cached) {
                     bool ok = !s->pj && s->opt.stop != SIM_STOP_THETA;
                     for (int sc : c.scenes) ok = ok && cache_fits(s, sc, split);
                     if (!ok) continue;
                 }
-                KernFn kf = kernel_for(s->opt.precision == SIM_MIXED, cached, split);
+                KernFn kf = kernel_for(s->opt.precision == SIM_MIXED, cached, split, nt);
                 float ms = 0.0f;
                 for (int rep = 0; rep < 2 && err == cudaSuccess; ++rep) {   // warm, then timed
                     err = copy_all(false);
                     if (err != cudaSuccess) break;
                     cudaEventRecord(e0, s->stream);
-                    kf<<<P.nscenes, SUBADMM_THREADS, c.max_smem, s->stream>>>(P);
+                    kf<<<P.nscenes, nt, c.max_smem, s->stream>>>(P);
                     err = cudaGetLastError();
                     cudaEventRecord(e1, s->stream);
                     if (err == cudaSuccess) err = cudaEventSynchronize(e1);
                     if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
                 }
-                if (err == cudaSuccess && ms < best) { best = ms; bc = cached; bs = split; }
+                if (err == cudaSuccess && ms < best) { best = ms; bc = cached; bs = split; bt = nt; }
             }
         }
         c.cached = bc;
         c.split = bs;
+        c.nt = bt;
         best_ns[k] = best * 1e6 / steps;
     }
     if (err == cudaSuccess) err = copy_all(false);
@@ -1711,7 +1729,7 @@ int sim_step_learned(sim_t s, wsn_t net, int n_steps)
     const int nif = (int)s->cons.size();
     StepParams P = step_params(s, n_steps);
     for (const LaunchClass &c : s->classes)
-        CK(cudaFuncSetAttribute(kernel_for(s->opt.precision == SIM_MIXED, c.cached, c.split),
+        CK(cudaFuncSetAttribute(kernel_for(s->opt.precision == SIM_MIXED, c.cached, c.split, c.nt),
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, s->smem_full),
            "shared memory attribute");
     // one network evaluation: features, the network, lambda^0 and the beta scales, then the
