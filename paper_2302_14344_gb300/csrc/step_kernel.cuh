@@ -203,6 +203,7 @@ struct BlockDist {
     __device__ __forceinline__ BlockDist()
         : tid(threadIdx.x), nthreads(blockDim.x), warp(threadIdx.x >> 5), nwarps(blockDim.x >> 5) {}
     __device__ __forceinline__ void sync() const { __syncthreads(); }
+    __device__ __forceinline__ void fence() const { __threadfence_block(); }
 };
 
 __device__ __forceinline__ unsigned long long global_ns()
@@ -261,6 +262,7 @@ struct GridDist {
     {
         grid_barrier(count, gen, err, gridDim.x, 20000000000ull);
     }
+    __device__ __forceinline__ void fence() const { __threadfence(); }
 };
 
 template <typename T, typename Dist>
@@ -731,6 +733,8 @@ __device__ long long scene_setup(const StepParams &P, const SceneDesc &S, const 
             }
         }
     }
+    // factor-ready flags of this step (see the factor loop): -1 until a subsystem is done
+    for (int i = d.tid; i < S.nsub; i += d.nthreads) P.pending[S.sub0 + i] = -1;
     d.sync();
     const long long t_asm = clock64();
     // per subsystem (one warp each): beta, K = A + beta J^T J and its Cholesky factor, then
@@ -756,7 +760,11 @@ __device__ long long scene_setup(const StepParams &P, const SceneDesc &S, const 
             __syncwarp();
             env_forward_vec<T>(LT, W + m, n, ldw, e.lastr);
             // c (and D if the launch lost it) below, over every thread of the scene
-            if (lane == 0) P.pending[gsub] = (step == 0 && !S.hot_global) ? 2 : 1;
+            __syncwarp();
+            if (lane == 0) {
+                d.fence();
+                *(volatile int *)&P.pending[gsub] = (step == 0 && !S.hot_global) ? 2 : 1;
+            }
             __syncwarp();
             continue;
         }
@@ -827,27 +835,45 @@ __device__ long long scene_setup(const StepParams &P, const SceneDesc &S, const 
             ok = env_cholesky<T, true>(LT, n, e, nullptr);
         }
         if (u.cst && lane == 0) P.subflag[gsub] = ok ? (1 | (stiff ? 2 : 0)) : 0;
-        if (!ok) {
-            if (lane == 0) { P.pending[gsub] = 0; *s_status = ST_NOTSPD; }
-            continue;
+        __syncwarp();
+        if (lane == 0) {
+            d.fence();                            // the factor before its flag
+            *(volatile int *)&P.pending[gsub] = ok ? 3 : 0;    // 3: W, then D and c, below
+            if (!ok) *s_status = ST_NOTSPD;
         }
-        if (lane == 0) P.pending[gsub] = 3;       // W, then D and c, below
         __syncwarp();
     }
-    d.sync();
-    // W = L^-1 [J^T b] of the refactorised subsystems (pending 3) in chunks of 32 columns, a
-    // warp per chunk over every warp of the scene, so that one large subsystem does not hold
-    // a single warp (and the scene) for all of its columns
+    // W = L^-1 [J^T b] of the refactorised subsystems (flag 3) in chunks of 32 columns, a warp
+    // per chunk over every warp of the scene, so that one large subsystem does not hold a
+    // single warp (and the scene) for all of its columns.  No barrier after the factor loop:
+    // a chunk waits for its own subsystem's flag, and the chunks run smallest subsystem
+    // first (the largest are factorised first and take longest), so the chunks of the
+    // others overlap the largest factorisations.  Each warp ends its factor tasks before it
+    // takes a chunk, so every wait ends; it is bounded all the same (a wait that runs out
+    // marks the scene ST_TIMEOUT and skips the chunk).
     {
-        const int *wpre = P.ipool + S.pre_off;
+        const int *wpre = P.ipool + S.pre_off, *ord = P.ipool + S.ord_off;
         const int total = __ldg(wpre + S.nsub);
         for (int w = d.warp; w < total; w += d.nwarps) {
-            const int i = pre_find(wpre, S.nsub, w);
-            if (P.pending[S.sub0 + i] != 3) continue;
+            const int pos = pre_find(wpre, S.nsub, w);
+            const int i = __ldg(ord + S.nsub - 1 - pos);
+            int flag = 0;
+            if (lane == 0) {
+                volatile int *vf = &P.pending[S.sub0 + i];
+                flag = *vf;
+                for (long long spin = 0; flag == -1; ++spin) {
+                    if (spin > (1ll << 26)) { *s_status = ST_TIMEOUT; break; }
+                    __nanosleep(64);
+                    flag = *vf;
+                }
+                d.fence();                        // the factor after its flag
+            }
+            flag = __shfl_sync(0xffffffffu, flag, 0);
+            if (flag != 3) continue;
             const SubDesc &u = P.subs[S.sub0 + i];
             const int ldw = (u.m + 1 + 3) / 4 * 4;
             solve_w_chunk<T>(stb + u.ot_L, stb + u.ot_W, sdb + u.od_J, sdb + u.od_b, u.n, u.m,
-                             ldw, 32 * (w - __ldg(wpre + i)), sub_env(P, u),
+                             ldw, 32 * (w - __ldg(wpre + pos)), sub_env(P, u),
                              P.tc_phase == 1 && u.tc);
         }
     }

@@ -572,11 +572,14 @@ int finalize(sim_t s)
         // work of the setup's scene-wide passes, as prefix sums over the scene's subsystems:
         // chunks of 32 columns of W = L^-1 [J^T b] (m + 1 columns), then the map's items of
         // c (one per 4 rows) and of D (4 x 4 blocks of its lower triangle)
+        // (the chunks of W are listed smallest subsystem first: position k is subsystem
+        // ord[nsub - 1 - k])
         S.pre_off = (int)ipool.size();
         for (int tab = 0; tab < 3; ++tab) {
             int acc = 0;
             ipool.push_back(0);
-            for (int i = 0; i < S.nsub; ++i) {
+            for (int k = 0; k < S.nsub; ++k) {
+                const int i = tab == 0 ? ipool[S.ord_off + S.nsub - 1 - k] : k;
                 const int m = s->sdesc[S.sub0 + i].m, nb = (m + 3) / 4;
                 acc += tab == 0 ? (m + 1 + 31) / 32 : tab == 1 ? nb : nb * (nb + 1) / 2;
                 ipool.push_back(acc);
