@@ -648,6 +648,11 @@ def sub_robots(ctx, args, threads: int) -> dict:
     return out
 
 
+# the rho search labels a scene-step with the largest beta scale within 10% of its fewest
+# iterations (learned.collect_rho)
+RHO_LABEL_SLACK = 0.1
+
+
 def train_warmstart(seed: int = 1) -> tuple:
     """The learned warm start's network, trained on the GPU by the library's own kernels on
     samples the plain simulator generates (config 5): the uneven batched scenes, the legged
@@ -659,14 +664,16 @@ def train_warmstart(seed: int = 1) -> tuple:
     import torch
     from paper_2302_14344_gb300 import learned as lr
     t0 = time.perf_counter()
+    slack = RHO_LABEL_SLACK
     sources = [("batched", lambda: lr.collect_rho(sg.batched(101, n_scenes=512), steps=20,
-                                                  warmup=100)),
+                                                  warmup=100, slack=slack)),
                ("robots", lambda: lr.collect_rho(sg.robots(101, n_robots=64), steps=40,
-                                                 warmup=150)),
+                                                 warmup=150, slack=slack)),
                ("fem_beam", lambda: lr.collect_rho(sg.fem_beam(11, vary=True), steps=10,
-                                                   warmup=3)),
+                                                   warmup=3, slack=slack)),
                ("chain", lambda: lr.collect_rho(sg.chain(101, max_iters=1000, tol_primal=1e-6,
-                                                         rho=1e3), steps=50, warmup=3))]
+                                                         rho=1e3), steps=50, warmup=3,
+                                                slack=slack))]
     parts, counts = [], {}
     for name, fn in sources:
         q = fn()
@@ -678,6 +685,7 @@ def train_warmstart(seed: int = 1) -> tuple:
     net = lr.init_network(seed=seed)
     losses = lr.train(net, X, T, M, epochs=6)
     return net, {"samples": int(X.shape[0]), "by_workload": counts, "epochs": 6,
+                 "label": f"largest beta scale within {RHO_LABEL_SLACK:.0%} of the fewest iterations",
                  "loss_first_last": [losses[0], losses[-1]],
                  "collect_seconds": round(collect_s, 1),
                  "train_seconds": round(time.perf_counter() - t0 - collect_s, 1)}

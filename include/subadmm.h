@@ -215,8 +215,9 @@ int sim_autotune(sim_t s, int steps, int max_classes, long long *out);
  * [14:17] anchor velocity and angular velocity of a minus those of b (world); [17:23] the
  * last step's lambda (first 6 rows); [23:26] the error terms e (first 3 rows); [26] mu;
  * [27] s = sum of 1/beta over its sides (last step's beta; 0 before the first step); [28]
- * the contact gap; [29] beta_a / beta_b (1 for one side or before the first step); [30:32]
- * zero; a non-finite feature is written as 0.  x_dev holds 32 x interfaces floats.
+ * the contact gap; [29] beta_a / beta_b (1 for one side or before the first step); [30]
+ * log2(1 + side-rows of the scene); [31] log2(1 + DOF of side a's subsystem); a non-finite
+ * feature is written as 0.  x_dev holds 32 x interfaces floats.
  *
  * sim_interface_targets, after a sim_step whose start features are in x_dev, writes the
  * training targets of each interface: t_dev[7 i + r] = lambda*_r - lambda_prev,r for its

@@ -74,6 +74,10 @@ __global__ void interface_features_kernel(const StepParams P, const int *pub2dev
             s += b > 0.0 ? 1.0 / b : 0.0;
         }
         f[27] = (float)s;
+        // the sizes the best beta depends on (the rho search prefers larger scales for large
+        // scenes): the scene's side-rows and the DOF of side a's subsystem, as log2(1 + x)
+        f[30] = log2f(1.0f + (float)S.nsr);
+        f[31] = log2f(1.0f + (float)P.subs[S.sub0 + c.sub[0]].n);
         const double b0 = P.beta[S.sub0 + c.sub[0]], b1 = c.ns >= 2 ? P.beta[S.sub0 + c.sub[1]] : 0.0;
         f[29] = (b0 > 0.0 && b1 > 0.0) ? (float)(b0 / b1) : 1.0f;
         const double *prm = P.pool + c.par_off;

@@ -52,14 +52,17 @@ def _replicate(problem, copies: int):
 
 
 def collect_rho(problem, steps: int, warmup: int = 5, precision: int = sa.SIM_MIXED,
-                device: int = 0):
+                device: int = 0, slack: float = 0.0):
     """Samples from the plain simulator, with the best beta scale of each scene-step as the
     label of the network's seventh output.  Every scene runs in seven copies, copy k with
     every subsystem's beta scaled by 2^(k-3) (k = 3: the trace rule, Sec. III-D); after each
     step the copies' iteration counts give each scene's best scale (fewest iterations to the
     stop rule, ties to the scale nearest 1) and every copy is reset to the trace-rule copy's
-    state, so that all copies start each step from the plain trajectory.  Features and dual
-    targets are the trace-rule copy's.  Returns device tensors (X, T, M) like collect()."""
+    state, so that all copies start each step from the plain trajectory.  With ``slack`` > 0
+    the label is the largest scale within (1 + slack) of the fewest iterations: too small a
+    beta costs far more iterations than too large a one, so under an uncertain proposal the
+    larger of near-equal scales is the safer label.  Features and dual targets are the
+    trace-rule copy's.  Returns device tensors (X, T, M) like collect()."""
     import torch
     nsc = len(problem.scenes)
     rep = _replicate(problem, len(SCALES))
@@ -102,6 +105,8 @@ def collect_rho(problem, steps: int, warmup: int = 5, precision: int = sa.SIM_MI
         for sc in range(nsc):
             cand = [k for k in order if nc[k, sc] == 0] or [REF]
             kb = min(cand, key=lambda k: (it[k, sc], abs(k - REF)))
+            if slack > 0.0:
+                kb = max(k for k in cand if it[k, sc] <= (1.0 + slack) * it[kb, sc])
             best[sc] = kb - REF
         lo, hi = REF * nif0, (REF + 1) * nif0
         label = torch.repeat_interleave(torch.tensor(best, dtype=torch.float32,

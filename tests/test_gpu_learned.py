@@ -155,12 +155,13 @@ def test_trained_network_against_the_previous_step_warm_start(mods, capsys):
 def test_learned_rho_on_uneven_batched_scenes(mods, capsys):
     """The learned beta scale where the trace rule of Sec. III-D is far from the best one:
     uneven batched scenes.  Training samples come from a rho search on 128 scenes (each scene
-    in seven copies, beta scaled 2^-3 .. 2^3, the fewest iterations labelling the step);
+    in seven copies, beta scaled 2^-3 .. 2^3, the largest scale within 10% of the fewest
+    iterations labelling the step);
     evaluation on 512 other scenes after 100 steps, 20 steps in one launch for both forms:
     the learned start needs at least 5% fewer iterations per scene-step and leaves fewer
     scene-steps at the iteration limit."""
     sa, ws, lr = mods
-    X, T, M = lr.collect_rho(sg.batched(201, n_scenes=128), steps=20, warmup=100)
+    X, T, M = lr.collect_rho(sg.batched(201, n_scenes=128), steps=20, warmup=100, slack=0.1)
     net = lr.init_network(seed=3)
     losses = lr.train(net, X, T, M, epochs=6)
     res = lr.compare(sg.batched(202, n_scenes=512), net, steps=20, warmup=100, per_launch=20)
