@@ -199,6 +199,11 @@ __device__ View<T> scene_view(const StepParams &P, const SceneDesc &S, unsigned 
 // subsystems take a warp each, loops over rows and constraints a thread each; sync() is a
 // barrier over all of them.
 struct BlockDist {
+    // a scene's own block: its per-warp loops take the subsystems largest first, and the
+    // chunks of W wait on per-subsystem flags instead of a barrier after the factor loop (a
+    // scene over the whole grid has far more warps than subsystems, and its pollers would
+    // load the L2 that its factorisations run through)
+    static constexpr bool kSpread = true;
     int tid, nthreads, warp, nwarps;
     __device__ __forceinline__ BlockDist()
         : tid(threadIdx.x), nthreads(blockDim.x), warp(threadIdx.x >> 5), nwarps(blockDim.x >> 5) {}
@@ -251,6 +256,7 @@ __device__ __noinline__ void grid_barrier(unsigned *count, unsigned *gen, int *e
 // work (one warp each, FP64-bound in the setup and the recovery) then spreads over one warp
 // per block, i.e. over the SMs and their FP64 pipes, instead of filling the first blocks.
 struct GridDist {
+    static constexpr bool kSpread = false;
     int tid, nthreads, warp, nwarps;
     unsigned *count, *gen;
     int *err;
@@ -742,7 +748,7 @@ __device__ long long scene_setup(const StepParams &P, const SceneDesc &S, const 
     // form factorise K in FP64 (rounded into the T copy); the other mixed blocks factorise in
     // FP32, keeping the FP64 A, b and J for the recovery and refinement of v-hat.
     for (int k = d.warp; k < S.nsub; k += d.nwarps) {
-        const int i = __ldg(P.ipool + S.ord_off + k);          // largest first
+        const int i = Dist::kSpread ? __ldg(P.ipool + S.ord_off + k) : k;   // largest first
         const SubDesc &u = P.subs[S.sub0 + i];
         const int gsub = S.sub0 + i;
         // W's leading dimension: m + 1 columns rounded up to 4 (map_item reads 4-column blocks)
@@ -851,6 +857,7 @@ __device__ long long scene_setup(const StepParams &P, const SceneDesc &S, const 
     // others overlap the largest factorisations.  Each warp ends its factor tasks before it
     // takes a chunk, so every wait ends; it is bounded all the same (a wait that runs out
     // marks the scene ST_TIMEOUT and skips the chunk).
+    if (!Dist::kSpread) d.sync();
     {
         const int *wpre = P.ipool + S.pre_off, *ord = P.ipool + S.ord_off;
         const int total = __ldg(wpre + S.nsub);
@@ -858,7 +865,9 @@ __device__ long long scene_setup(const StepParams &P, const SceneDesc &S, const 
             const int pos = pre_find(wpre, S.nsub, w);
             const int i = __ldg(ord + S.nsub - 1 - pos);
             int flag = 0;
-            if (lane == 0) {
+            if (lane == 0 && !Dist::kSpread) {
+                flag = P.pending[S.sub0 + i];     // set before the barrier above
+            } else if (lane == 0) {
                 volatile int *vf = &P.pending[S.sub0 + i];
                 flag = *vf;
                 for (long long spin = 0; flag == -1; ++spin) {
@@ -1022,7 +1031,7 @@ __device__ void recover_v(const StepParams &P, const SceneDesc &S, const View<T>
     constexpr bool MIXED = sizeof(T) == 4;
     const int lane = threadIdx.x & 31;
     for (int k = d.warp; k < S.nsub; k += d.nwarps) {
-        const int i = __ldg(P.ipool + S.ord_off + k);          // largest first
+        const int i = Dist::kSpread ? __ldg(P.ipool + S.ord_off + k) : k;   // largest first
         const SubDesc &u = P.subs[S.sub0 + i];
         const int n = u.n, m = u.m;
         const SubEnv e = sub_env(P, u);
