@@ -126,3 +126,39 @@ def test_cable_scene_shape():
             ba = sc.subs[f.a[0]].bodies[f.a[1]]
             bb = sc.subs[f.b[0]].bodies[f.b[1]]
             assert np.allclose(ba.p + f.anchor_a, bb.p + f.anchor_b, atol=1e-12)
+
+
+def test_stir_scene_shape():
+    """The stir workload: 216 spheres (r 1 cm, 4 g) and the arm stand-in (217 subsystems,
+    1,296 sphere DOF), no two bodies overlapping at t = 0 (every sphere-sphere gap and every
+    wall / floor gap non-negative), candidate pairs closer than 1.5 diameters, and tool
+    contacts only with spheres of the two top layers."""
+    from scipy.spatial.transform import Rotation
+    p = sg.stir(0)
+    sc = p.scenes[0]
+    assert len(sc.subs) == 217 and sum(s.n for s in sc.subs[:216]) == 1296
+    assert p.options.h == 1e-2
+    centres = np.array([s.bodies[0].p for s in sc.subs[:216]])
+    r = 0.01
+    for s in sc.subs[:216]:
+        b = s.bodies[0]
+        assert np.isclose(b.m, 0.004) and np.allclose(b.I, 0.4 * b.m * r * r)
+    ztop = centres[:, 2].max()
+    arm = sc.subs[216]
+    for f in sc.ifs:
+        if f.kind == sg.SPHERE_CONTACT and f.a[0] < 216:
+            pa, pb = centres[f.a[0]], centres[f.b[0]]
+            d = np.linalg.norm(pa - pb)
+            assert d - f.radius_a - f.radius_b >= 0.0 and d < 1.5 * 2 * r
+        elif f.kind == sg.SPHERE_CONTACT:               # the tool
+            b = arm.bodies[f.a[1]]
+            R = Rotation.from_quat([b.q[1], b.q[2], b.q[3], b.q[0]]).as_matrix()
+            tool = b.p + R @ f.anchor_a
+            pb = centres[f.b[0]]
+            assert pb[2] >= ztop - 2.1 * r
+            assert np.linalg.norm(tool - pb) - f.radius_a - f.radius_b >= 0.0
+        elif f.kind == sg.PLANE_CONTACT:
+            n = f.normal / np.linalg.norm(f.normal)
+            assert n @ centres[f.a[0]] - f.plane_z - f.radius_a >= 0.0
+    kinds = [f.kind for f in sc.ifs]
+    assert kinds.count(sg.PLANE_CONTACT) == 180
