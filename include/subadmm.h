@@ -193,7 +193,8 @@ int sim_step(sim_t s, int n_steps);
  * of classes, or a negative SIM_E* code.
  * sim_autotune times, for each class on its own, every kernel variant that is valid for all
  * its scenes (generic with 1, 2 or 4 lanes per side-row and 256 or 512 threads per block,
- * register-cached where the scenes fit; the grid kernel with 8, 16 or 32) over `steps`
+ * register-cached where the scenes fit; the grid kernel with 8, 16 or 32 lanes per
+ * side-row and all resident blocks or half of them, unless sim_grid_blocks fixed the count) over `steps`
  * steps from the current state, keeps the fastest, and restores the state
  * (bodies, nodes, warm-start duals, outputs, counters) so that tuning leaves no trace.  It
  * waits for the stream, allocates a temporary snapshot, and writes the same rows as
@@ -285,6 +286,20 @@ int sim_set_beta_scale(sim_t s, const double *scale);
  * from the initial duals on.  With 0 the grid kernel forms D and c itself (one warp per
  * block, FP32 CUDA cores).  Must be called before the first sim_step (SIM_EINVAL after). */
 int sim_tensor_cores(sim_t s, int enable);
+
+/* Blocked factorisation of those blocks on the tensor cores (Algorithm 1, factorise; on by
+ * default; takes effect only where sim_tensor_cores is on).  A refactorised block that the
+ * mixed form factorises in FP32 (not stiff by the diagonal-spread test) is factorised after
+ * the setup launch instead of inside it: right-looking over panels of 128 columns, one launch
+ * per panel for the diagonal tile's factor and the rows below it (CUDA cores, FP32, a thread
+ * per row), and one tcgen05 launch per panel for the Schur update of the trailing tiles the
+ * panel reaches inside K_i's envelope (C -= P P^T, split-TF32, accumulators in tensor
+ * memory); a grid launch then solves those blocks' W before the Gram kernel.  Stiff blocks
+ * stay on the FP64 envelope factorisation.  With 0 every factor is formed inside the setup
+ * launch (one warp per block).  A non-positive pivot ends the step with SIM_ENOTSPD status
+ * like the one-warp factorisation.  May be called at any time; it applies from the next
+ * step that refactorises. */
+int sim_tc_factor(sim_t s, int enable);
 
 /* The solver of every step (Sec. IV-B compares the method with other solvers on the same
  * scenes; Projected Jacobi is one of them):

@@ -9,7 +9,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libsubadmm.so")
-SOURCES = [os.path.join(CSRC, f) for f in ("subadmm.cu", "warmstart.cu", "gram.cu")]
+SOURCES = [os.path.join(CSRC, f) for f in ("subadmm.cu", "warmstart.cu", "gram.cu", "chol.cu")]
 DEPENDS = SOURCES + [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [
     os.path.join(ROOT, "include", h) for h in ("subadmm.h", "warmstart.h")]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo",

@@ -25,7 +25,7 @@ int round_up(int x, int a) { return (x + a - 1) / a * a; }
 
 }  // namespace
 
-cudaError_t gram_plan_build(GramPlan &P, std::vector<GramJob> jobs)
+cudaError_t gram_plan_build(GramPlan &P, std::vector<GramJob> &jobs)
 {
     gram_plan_free(P);
     cudaError_t e = cudaGetDevice(&P.device);
@@ -34,6 +34,9 @@ cudaError_t gram_plan_build(GramPlan &P, std::vector<GramJob> jobs)
     if (P.njobs == 0) return cudaSuccess;
     int maxk = 1, rows = 0, tiles = 0;
     for (const GramJob &J : jobs) maxk = std::max(maxk, J.k);
+    P.prep = jobs[0].W != nullptr;
+    for (const GramJob &J : jobs)
+        if ((J.W != nullptr) != P.prep) return cudaErrorInvalidValue;
     P.ldt = round_up(maxk, kGramKChunk);
     std::vector<int> prefix;
     int prep = 0;
@@ -57,6 +60,10 @@ cudaError_t gram_plan_build(GramPlan &P, std::vector<GramJob> jobs)
     const size_t bytes = sizeof(float) * (size_t)rows * P.ldt;
     if ((e = cudaMalloc((void **)&P.hi, bytes)) != cudaSuccess) return e;
     if ((e = cudaMalloc((void **)&P.lo, bytes)) != cudaSuccess) return e;
+    if (!P.prep) {
+        if ((e = cudaMemset(P.hi, 0, bytes)) != cudaSuccess) return e;
+        if ((e = cudaMemset(P.lo, 0, bytes)) != cudaSuccess) return e;
+    }
     if ((e = cudaMalloc((void **)&P.d_jobs, sizeof(GramJob) * jobs.size())) != cudaSuccess) return e;
     if ((e = cudaMalloc((void **)&P.d_prep_prefix, sizeof(int) * prefix.size())) != cudaSuccess) return e;
     if ((e = cudaMalloc((void **)&P.d_err, sizeof(int))) != cudaSuccess) return e;
@@ -74,10 +81,12 @@ cudaError_t gram_plan_build(GramPlan &P, std::vector<GramJob> jobs)
 cudaError_t gram_plan_run(const GramPlan &P, cudaStream_t st, int *err)
 {
     if (P.njobs == 0) return cudaSuccess;
-    gram_prep_kernel<<<P.prep_blocks, 256, 0, st>>>(P.d_jobs, P.njobs, P.d_prep_prefix, P.hi,
-                                                    P.lo, P.ldt);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    if (P.prep) {
+        gram_prep_kernel<<<P.prep_blocks, 256, 0, st>>>(P.d_jobs, P.njobs, P.d_prep_prefix,
+                                                        P.hi, P.lo, P.ldt);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     gram_tc_kernel<<<P.grid, kGramThreads, kGramSmem, st>>>(P.map_hi, P.map_lo, P.d_jobs,
                                                             P.njobs, P.ntiles,
                                                             err ? err : P.d_err);

@@ -37,6 +37,13 @@ struct GramJob {
     float *c;         // G[t][m] for t < m at c[t] (null: not stored)
     float *G;         // the whole (m + 1) x (m + 1) matrix at G[t * ldg + u] (null: not stored)
     int ldg;
+    // Schur-update form (the blocked Cholesky's trailing update): S[u * lds + t] -= G[t][u]
+    // for t <= u, the lower triangle of a row-major matrix (null: not this form).  The operand
+    // rows are written into the plan's buffers by their producer (W is null: no transpose).
+    float *S;
+    int lds;
+    const int *gate;  // stores happen only while *gate == gate_val (null: always)
+    int gate_val;
 };
 
 
@@ -48,6 +55,8 @@ struct GramPlan {
     int ldt = 0;               // row length of the stacked buffers (a multiple of 32)
     int rows_total = 0;        // rows of the stacked buffers (each job padded to 128)
     int grid = 0;              // blocks of the Gram launch
+    bool prep = true;          // W given: the transpose kernel fills the buffers (else their
+                               // producer writes them; padding rows stay zero)
     float *hi = nullptr, *lo = nullptr;
     GramJob *d_jobs = nullptr;
     int *d_prep_prefix = nullptr;
@@ -57,8 +66,10 @@ struct GramPlan {
 
 // Lays out the jobs (W, ldw, rows, k and the outputs of each must be set; row_off and tile0
 // are filled in), allocates the buffers and encodes the tensor maps on the current device.
-// Returns cudaSuccess or the first error.
-cudaError_t gram_plan_build(GramPlan &P, std::vector<GramJob> jobs);
+// Either every job has its W or none (the Schur-update form: the buffers start zeroed and
+// job j's operand row t goes to row row_off + t of hi and lo).  Returns cudaSuccess or the
+// first error.
+cudaError_t gram_plan_build(GramPlan &P, std::vector<GramJob> &jobs);
 
 // Enqueues the transpose and the Gram kernel on `st`; a wait that runs out raises *err
 // (the plan's own error word when err is null).

@@ -217,6 +217,10 @@ __device__ __forceinline__ void gram_tile_of(const GramJob *jobs, int njobs, int
 
 __device__ __forceinline__ void gram_store(const GramJob &J, int r, int c, float v, bool mirror)
 {
+    if (J.S) {                                  // Schur update: lower triangle, row c
+        if (r < J.rows && c < J.rows) J.S[(size_t)c * J.lds + r] -= v;
+        return;
+    }
     const int m = J.rows - 1;
     if (J.G) {
         if (r < J.rows && c < J.rows) {
@@ -351,6 +355,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
             // differ in the last bit); an off-diagonal tile is mirrored whole
             const int r = bi * kGramTile + warp * 32 + lane;
             const bool diag = bi == bj;
+            const bool live = !J.gate || *(volatile const int *)J.gate == J.gate_val;
             const int nk = (J.k + kGramKChunk - 1) / kGramKChunk;
             const int nacc = nk < kGramAcc ? nk : kGramAcc;      // accumulators written
             for (int cb = 0; cb < kGramTile; cb += 32) {
@@ -364,7 +369,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
                     for (int k = 0; k < 32; ++k) v[k] += w[k];
                 }
                 const int c0 = bj * kGramTile + cb;
-                if (c0 >= J.rows) continue;
+                if (c0 >= J.rows || !live) continue;
 #pragma unroll
                 for (int k = 0; k < 32; ++k)
                     if (!diag || c0 + k >= r) gram_store(J, r, c0 + k, v[k], c0 + k != r);

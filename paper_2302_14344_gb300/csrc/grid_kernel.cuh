@@ -138,16 +138,19 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 2) grid_step_kernel(StepParam
     unsigned pend = 0;          // stages whose issued copy has not been waited for yet
     bool stage_ok = true;       // false after a copy that did not complete in time
     // tc_phase 2 continues the step that a tc_phase 1 launch set up (its per-side-row
-    // constants and status are kept; the Gram kernel formed D and c in between)
+    // constants and status are kept; the Gram kernel formed D and c in between); tc_phase 3,
+    // between the two, solves W for the subsystems that the blocked tensor-core
+    // factorisation factorised after tc_phase 1
     const int tc_phase = P.tc_phase;
-    if (tc_phase != 2)
+    const bool fresh = tc_phase == 0 || tc_phase == 1;     // a launch that starts the step
+    if (fresh)
         for (int q = d.tid; q < S.ot_lam - S.ot_x; q += d.nthreads) V.tb[S.ot_x + q] = (T)0;
     scene_tables<T>(P, S, V, d);
     d.sync();
 
     for (int step = 0; step < P.n_steps; ++step) {
         if (lead) {
-            if (tc_phase != 2) G->status = ST_OK;
+            if (fresh) G->status = ST_OK;
             G->tsum = 0.0;
             G->pmax = 0ull;
             G->dmax = 0ull;
@@ -155,7 +158,11 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 2) grid_step_kernel(StepParam
         }
         d.sync();
         PhaseClock pc((P.phase && blockIdx.x == 0) ? P.phase + 8 * sc : nullptr);
-        if (tc_phase != 2) pc.mark_at(PHASE_ASSEMBLE, scene_setup<T>(P, S, V, &G->status, step, d));
+        if (fresh) pc.mark_at(PHASE_ASSEMBLE, scene_setup<T>(P, S, V, &G->status, step, d));
+        if (tc_phase == 3) {
+            w_chunks<T>(P, S, V, &G->status, d, 4);
+            d.sync();
+        }
         pc.mark(PHASE_FACTOR);
         const int status0 = vload(&G->status);
         if (status0 != ST_OK) {
@@ -167,7 +174,7 @@ __global__ void __launch_bounds__(SUBADMM_THREADS, 2) grid_step_kernel(StepParam
             d.sync();
             continue;
         }
-        if (tc_phase == 1) {
+        if (tc_phase == 1 || tc_phase == 3) {
             d.sync();
             pc.flush(0, 0);         // the setup's cycles; the iteration launch counts the step
             continue;

@@ -150,7 +150,10 @@ struct StepParams {
                            // c, 0 neither (set by the factorisation loop of the setup)
     int keep_factors;      // 0: refactor constant blocks every step too (Algorithm 1 literally)
     int tc_phase;          // grid kernel: 0 the whole step; 1 up to the map's W (the Gram
-                           // kernel forms D, c of the tc subsystems next); 2 from the duals on
+                           // kernel forms D, c of the tc subsystems next); 2 from the duals on;
+                           // 3 only the W of the subsystems whose factor was deferred
+    int tc_factor;         // tc_phase 1: the FP32 factors of the tc subsystems are left to the
+                           // blocked tensor-core factorisation (step flag 4), run before phase 3
     double *vhat;          // per DOF
     double *lam;           // per row: lambda of the last step (warm start state)
     const double *lam0;    // per row: learned initial lambda of this step (NULL: not learned)

@@ -598,6 +598,52 @@ __device__ void map_item(const F *W, int n, int m, int mp, int ldd, int ldw, con
     }
 }
 
+// W = L^-1 [J^T b] of the subsystems whose step flag is `want` (3: factorised by the setup;
+// 4: by the blocked tensor-core factorisation), in chunks of 32 columns, a warp per chunk over
+// every warp of the scene, so that one large subsystem does not hold a single warp (and the
+// scene) for all of its columns.  With flags still being set (want 3 in the setup, the spread
+// distribution: no barrier after the factor loop) a chunk waits for its own subsystem's flag,
+// and the chunks run smallest subsystem first (the largest are factorised first and take
+// longest), so the chunks of the others overlap the largest factorisations.  Each warp ends
+// its factor tasks before it takes a chunk, so every wait ends; it is bounded all the same (a
+// wait that runs out marks the scene ST_TIMEOUT and skips the chunk).
+template <typename T, typename Dist>
+__device__ void w_chunks(const StepParams &P, const SceneDesc &S, const View<T> &V,
+                         int *s_status, const Dist &d, int want)
+{
+    const int lane = threadIdx.x & 31;
+    const double *sdb = V.sdb;
+    T *stb = V.stb;
+    {
+        const int *wpre = P.ipool + S.pre_off, *ord = P.ipool + S.ord_off;
+        const int total = __ldg(wpre + S.nsub);
+        for (int w = d.warp; w < total; w += d.nwarps) {
+            const int pos = pre_find(wpre, S.nsub, w);
+            const int i = __ldg(ord + S.nsub - 1 - pos);
+            int flag = 0;
+            if (lane == 0 && !Dist::kSpread) {
+                flag = P.pending[S.sub0 + i];     // set before the barrier above
+            } else if (lane == 0) {
+                volatile int *vf = &P.pending[S.sub0 + i];
+                flag = *vf;
+                for (long long spin = 0; flag == -1; ++spin) {
+                    if (spin > (1ll << 26)) { *s_status = ST_TIMEOUT; break; }
+                    __nanosleep(64);
+                    flag = *vf;
+                }
+                d.fence();                        // the factor after its flag
+            }
+            flag = __shfl_sync(0xffffffffu, flag, 0);
+            if (flag != want) continue;
+            const SubDesc &u = P.subs[S.sub0 + i];
+            const int ldw = (u.m + 1 + 3) / 4 * 4;
+            solve_w_chunk<T>(stb + u.ot_L, stb + u.ot_W, sdb + u.od_J, sdb + u.od_b, u.n, u.m,
+                             ldw, 32 * (w - __ldg(wpre + pos)), sub_env(P, u),
+                             (P.tc_phase == 1 || P.tc_phase == 3) && u.tc);
+        }
+    }
+}
+
 // assemble .. factor .. map, and the per-step constants of the z-step
 template <typename T, typename Dist>
 __device__ long long scene_setup(const StepParams &P, const SceneDesc &S, const View<T> &V,
@@ -825,6 +871,7 @@ __device__ long long scene_setup(const StepParams &P, const SceneDesc &S, const 
             if (lane == 0) db[S.od_flag + i] = stiff ? 1.0 : 0.0;
         }
         bool ok;
+        const bool defer = MIXED && !stiff && P.tc_factor && P.tc_phase == 1 && u.tc;
         if (stiff) {
             add_jtj<double>(K, n, J, e, beta);
             ok = env_cholesky<double, false>(K, n, e, idg);
@@ -833,6 +880,18 @@ __device__ long long scene_setup(const StepParams &P, const SceneDesc &S, const 
                     for (int q = e.env[p] + lane; q <= p; q += 32)
                         LT[p * n + q] = (q == p) ? (T)idg[p] : (T)K[p * n + q];
             }
+        } else if (defer) {
+            // K in FP32 for the blocked tensor-core factorisation that follows this launch:
+            // the lower triangle from the first column of the envelope's tile of each tile
+            // row on, zeros left of the envelope (the blocked factorisation reads whole tiles)
+            for (int p = 0; p < n; ++p) {
+                const int q0 = e.env[p & ~127] & ~127;
+                for (int q = q0 + lane; q <= p; q += 32)
+                    LT[p * n + q] = q < e.env[p] ? (T)0 : (T)K[p * n + q];
+            }
+            __syncwarp();
+            add_jtj<T>(LT, n, J, e, (T)beta);
+            ok = true;
         } else {
             for (int p = 0; p < n; ++p)
                 for (int q = e.env[p] + lane; q <= p; q += 32) LT[p * n + q] = (T)K[p * n + q];
@@ -844,48 +903,15 @@ __device__ long long scene_setup(const StepParams &P, const SceneDesc &S, const 
         __syncwarp();
         if (lane == 0) {
             d.fence();                            // the factor before its flag
-            *(volatile int *)&P.pending[gsub] = ok ? 3 : 0;    // 3: W, then D and c, below
+            // 3: W, then D and c, below; 4: factor, W, D and c after this launch
+            *(volatile int *)&P.pending[gsub] = ok ? (defer ? 4 : 3) : 0;
             if (!ok) *s_status = ST_NOTSPD;
         }
         __syncwarp();
     }
-    // W = L^-1 [J^T b] of the refactorised subsystems (flag 3) in chunks of 32 columns, a warp
-    // per chunk over every warp of the scene, so that one large subsystem does not hold a
-    // single warp (and the scene) for all of its columns.  No barrier after the factor loop:
-    // a chunk waits for its own subsystem's flag, and the chunks run smallest subsystem
-    // first (the largest are factorised first and take longest), so the chunks of the
-    // others overlap the largest factorisations.  Each warp ends its factor tasks before it
-    // takes a chunk, so every wait ends; it is bounded all the same (a wait that runs out
-    // marks the scene ST_TIMEOUT and skips the chunk).
+    // W = L^-1 [J^T b] of the subsystems factorised above (flag 3)
     if (!Dist::kSpread) d.sync();
-    {
-        const int *wpre = P.ipool + S.pre_off, *ord = P.ipool + S.ord_off;
-        const int total = __ldg(wpre + S.nsub);
-        for (int w = d.warp; w < total; w += d.nwarps) {
-            const int pos = pre_find(wpre, S.nsub, w);
-            const int i = __ldg(ord + S.nsub - 1 - pos);
-            int flag = 0;
-            if (lane == 0 && !Dist::kSpread) {
-                flag = P.pending[S.sub0 + i];     // set before the barrier above
-            } else if (lane == 0) {
-                volatile int *vf = &P.pending[S.sub0 + i];
-                flag = *vf;
-                for (long long spin = 0; flag == -1; ++spin) {
-                    if (spin > (1ll << 26)) { *s_status = ST_TIMEOUT; break; }
-                    __nanosleep(64);
-                    flag = *vf;
-                }
-                d.fence();                        // the factor after its flag
-            }
-            flag = __shfl_sync(0xffffffffu, flag, 0);
-            if (flag != 3) continue;
-            const SubDesc &u = P.subs[S.sub0 + i];
-            const int ldw = (u.m + 1 + 3) / 4 * 4;
-            solve_w_chunk<T>(stb + u.ot_L, stb + u.ot_W, sdb + u.od_J, sdb + u.od_b, u.n, u.m,
-                             ldw, 32 * (w - __ldg(wpre + pos)), sub_env(P, u),
-                             P.tc_phase == 1 && u.tc);
-        }
-    }
+    w_chunks<T>(P, S, V, s_status, d, 3);
     d.sync();
     // the maps D = W^T W and c = W^T g of this step (pending >= 2: D and c, 1: c only), their
     // items (rows of c, then 4 x 4 blocks of D) spread over every thread of the scene and

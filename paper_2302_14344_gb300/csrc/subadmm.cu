@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <mutex>
 #include <cstdio>
 #include <cstring>
@@ -19,6 +20,7 @@
 #include "warmstart.h"
 #include "device_guard.h"
 #include "gram.h"
+#include "chol.h"
 
 namespace {
 
@@ -46,6 +48,8 @@ struct LaunchClass {
     int nt = SUBADMM_THREADS;      // threads per block (SUBADMM_WIDE: a generic class whose
                                    // scenes take a whole SM, one block per SM)
     int blocks = 0;                // grid class: blocks of the cooperative launch
+    int block_div = 1;             // grid class: the launch takes the resident blocks / this
+                                   // (autotuned: fewer blocks make cheaper grid barriers)
     std::vector<int> scenes;
     int ids_off = 0;               // offset of the scene list in d_scene_ids
     int max_smem = 0;
@@ -115,6 +119,10 @@ struct sim_s {
     double pj_omega = 1.0;
     int tensor_cores = 1;          // grid scenes, mixed form: D, c by the tcgen05 Gram kernel
     std::vector<subadmm::GramPlan> gram;   // per scene: Gram jobs of its tc subsystems
+    int tc_factor = 1;             // refactorised tc subsystems' FP32 factors by the blocked
+                                   // Cholesky with tensor-core Schur updates
+    std::vector<subadmm::CholPlan> chol;   // per scene: the blocked factorisation's panels
+    std::vector<int> h_ipool;      // host copy of the integer pool (envelopes)
     std::vector<char> grid_factored;       // per scene: its tc subsystems hold kept factors
     // graph replay of sim_step
     bool use_graph = false;
@@ -270,6 +278,8 @@ void free_device(sim_t s)
     drop_graphs(s);
     for (auto &g : s->gram) subadmm::gram_plan_free(g);
     s->gram.clear();
+    for (auto &c : s->chol) subadmm::chol_plan_free(c);
+    s->chol.clear();
     s->grid_factored.clear();
     if (s->graph_stream) cudaStreamDestroy(s->graph_stream);
     s->graph_stream = nullptr;
@@ -916,6 +926,7 @@ int finalize(sim_t s)
     if ((rc = upload(s, &s->d_bodies, bodies, "bodies"))) return rc;
     if ((rc = upload(s, &s->d_nodes, nodes, "nodes"))) return rc;
     if ((rc = upload(s, &s->d_ipool, ipool, "integer pool"))) return rc;
+    s->h_ipool = ipool;
     {
         {
             const std::vector<double> ones(std::max(1, nsubs), 1.0);
@@ -1264,6 +1275,7 @@ StepParams step_params(const sim_t s, int n_steps)
     P.grid = s->d_grid;
     P.lam0 = nullptr;
     P.tc_phase = 0;
+    P.tc_factor = 0;
     P.ref10 = s->d_ref10;
     P.learn_skip = s->d_learn_skip;
     return P;
@@ -1332,6 +1344,35 @@ int gram_plan_of(sim_t s, int sc)
     return SIM_OK;
 }
 
+// The blocked factorisation plan of grid scene sc (its tc subsystems' K_i), built on first use.
+int chol_plan_of(sim_t s, int sc)
+{
+    if ((int)s->chol.size() < s->nscenes) s->chol.resize(s->nscenes);
+    subadmm::CholPlan &C = s->chol[sc];
+    if (C.device >= 0) return SIM_OK;
+    const SceneDesc &S = s->scenes[sc];
+    std::vector<subadmm::CholMatrix> mats;
+    unsigned char *tbase = reinterpret_cast<unsigned char *>(s->d_work) + S.g_base + S.g_tbase;
+    float *stb = reinterpret_cast<float *>(tbase);
+    for (int i = 0; i < S.nsub; ++i) {
+        const SubDesc &u = s->sdesc[S.sub0 + i];
+        if (!u.tc) continue;
+        subadmm::CholMatrix M;
+        M.L = stb + u.ot_L;
+        M.n = u.n;
+        M.env.assign(s->h_ipool.begin() + u.env_off, s->h_ipool.begin() + u.env_off + u.n);
+        M.pending = s->d_pending + S.sub0 + i;
+        M.subflag = u.cst ? s->d_subflag + S.sub0 + i : nullptr;
+        mats.push_back(std::move(M));
+    }
+    int *status = reinterpret_cast<int *>(reinterpret_cast<char *>(s->d_grid) +
+                                          offsetof(GridScratch, status));
+    cudaError_t e = subadmm::chol_plan_build(C, mats, status, ST_NOTSPD);
+    if (e == cudaErrorMemoryAllocation) return fail(s, SIM_ENOMEM, "blocked factorisation plan");
+    CK(e, "blocked factorisation plan");
+    return SIM_OK;
+}
+
 int launch_grid_class(sim_t s, LaunchClass &c, StepParams P, cudaStream_t st, int split)
 {
     KernFn kf = grid_kernel_for(s->opt.precision == SIM_MIXED, split);
@@ -1339,7 +1380,8 @@ int launch_grid_class(sim_t s, LaunchClass &c, StepParams P, cudaStream_t st, in
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kf, SUBADMM_THREADS, 0), "occupancy");
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->opt.device), "attribute");
     const int resident = std::max(1, per_sm * sms);
-    const int blocks = s->grid_blocks > 0 ? std::min(s->grid_blocks, resident) : resident;
+    const int blocks = s->grid_blocks > 0 ? std::min(s->grid_blocks, resident)
+                                          : std::max(1, resident / std::max(1, c.block_div));
     c.max_smem = 0;                 // reported: the largest stage buffers of the class's launches
     for (size_t i = 0; i < c.scenes.size(); ++i) {
         // D rows staged in shared memory by bulk copies (the warp-per-row v-step only), two
@@ -1372,6 +1414,8 @@ int launch_grid_class(sim_t s, LaunchClass &c, StepParams P, cudaStream_t st, in
         const int sc = c.scenes[i];
         int rc = gram_plan_of(s, sc);
         if (rc) return rc;
+        const bool blocked = s->tc_factor && s->gram[sc].njobs > 0;
+        if (blocked && (rc = chol_plan_of(s, sc))) return rc;
         // steps that refactorise tc subsystems: setup launch, Gram kernel, iteration launch
         int left = P.n_steps;
         // (blocks whose K changes every step, co-rotational ones, refactorise every step)
@@ -1385,10 +1429,21 @@ int launch_grid_class(sim_t s, LaunchClass &c, StepParams P, cudaStream_t st, in
             StepParams Q = P;
             Q.n_steps = 1;
             Q.tc_phase = 1;
+            Q.tc_factor = blocked ? 1 : 0;
             void *a1[] = {&Q};
             CK(cudaMemsetAsync(s->d_grid, 0, sizeof(GridScratch), st), "grid scratch");
             CK(cudaLaunchCooperativeKernel((const void *)kf, dim3(blocks), dim3(SUBADMM_THREADS), a1, dyn, st),
                "grid kernel launch (setup)");
+            if (blocked) {
+                // the deferred FP32 factors: panel kernels and tensor-core Schur updates, then
+                // W of those subsystems
+                CK(subadmm::chol_plan_run(s->chol[sc], st, &s->d_grid->err),
+                   "blocked factorisation launch");
+                Q.tc_phase = 3;
+                CK(cudaMemsetAsync(s->d_grid, 0, 2 * sizeof(unsigned), st), "grid barrier");
+                CK(cudaLaunchCooperativeKernel((const void *)kf, dim3(blocks), dim3(SUBADMM_THREADS), a1, dyn, st),
+                   "grid kernel launch (W of the blocked factors)");
+            }
             CK(subadmm::gram_plan_run(s->gram[sc], st, &s->d_grid->err), "Gram kernel launch");
             Q.tc_phase = 2;
             // the barrier counter restarts; the step's status and error word carry over
@@ -1611,7 +1666,14 @@ int sim_autotune(sim_t s, int steps, int max_classes, long long *out)
         bool bc = c.cached;
         int bs = c.split, bt = c.nt;
         if (c.grid) {
+            // lanes per side-row, and all resident blocks or half of them (unless the caller
+            // fixed the block count)
+            // (half the blocks must win by 3% over all of them: the short timing is noisy)
+            double best_div[3] = {1e300, 1e300, 1e300};
+            int split_div[3] = {c.split, c.split, c.split};
+            for (int div = 1; div <= (s->grid_blocks > 0 ? 1 : 2) && err == cudaSuccess; ++div)
             for (int split = 8; split <= 32 && err == cudaSuccess; split *= 2) {
+                c.block_div = div;
                 float ms = 0.0f;
                 for (int rep = 0; rep < 2 && err == cudaSuccess; ++rep) {   // warm, then timed
                     err = copy_all(false);
@@ -1623,9 +1685,13 @@ int sim_autotune(sim_t s, int steps, int max_classes, long long *out)
                     err = cudaEventSynchronize(e1);
                     if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
                 }
-                if (err == cudaSuccess && ms < best) { best = ms; bs = split; }
+                if (err == cudaSuccess && ms < best_div[div]) { best_div[div] = ms; split_div[div] = split; }
             }
+            const int bd = best_div[2] < 0.97 * best_div[1] ? 2 : 1;
+            best = best_div[bd];
+            bs = split_div[bd];
             c.split = bs;
+            c.block_div = bd;
             best_ns[k] = best * 1e6 / steps;
             continue;
         }
@@ -1889,6 +1955,13 @@ int sim_tensor_cores(sim_t s, int enable)
     if (!s) return SIM_EINVAL;
     if (s->finalized) return fail(s, SIM_EINVAL, "the layout is fixed after the first sim_step");
     s->tensor_cores = enable ? 1 : 0;
+    return SIM_OK;
+}
+
+int sim_tc_factor(sim_t s, int enable)
+{
+    if (!s) return SIM_EINVAL;
+    s->tc_factor = enable ? 1 : 0;
     return SIM_OK;
 }
 

@@ -33,7 +33,7 @@ EXPORTS = ("sim_default_options", "sim_create", "sim_destroy", "sim_add_subsyste
            "sim_add_interface", "sim_set_generic", "sim_step", "sim_residuals", "sim_get",
            "sim_read_state", "sim_read_state_noalloc", "sim_write_state", "sim_sizes",
            "sim_iteration_stats", "sim_scene_info", "sim_use_graph", "sim_launch_classes",
-           "sim_autotune", "sim_grid_threshold", "sim_grid_staging", "sim_grid_blocks", "sim_tensor_cores", "sim_set_solver", "sim_keep_factors",
+           "sim_autotune", "sim_grid_threshold", "sim_grid_staging", "sim_grid_blocks", "sim_tensor_cores", "sim_tc_factor", "sim_set_solver", "sim_keep_factors",
            "sim_set_beta_scale", "sim_set_corotational",
            "sim_probe_barrier", "sim_barrier_floor", "sim_gram_tc", "sim_interface_features",
            "sim_interface_targets", "sim_step_learned", "sim_phase_trace", "sim_sync",
@@ -103,6 +103,7 @@ def load(build_if_missing: bool = True):
             "sim_keep_factors": (C.c_int, [VP, C.c_int]),
             "sim_grid_blocks": (C.c_int, [VP, C.c_int]),
             "sim_tensor_cores": (C.c_int, [VP, C.c_int]),
+            "sim_tc_factor": (C.c_int, [VP, C.c_int]),
             "sim_set_solver": (C.c_int, [VP, C.c_int, C.c_double]),
             "sim_set_beta_scale": (C.c_int, [VP, PD]),
             "sim_set_corotational": (C.c_int, [VP, C.c_int, C.c_int, PI, PD]),
@@ -259,6 +260,10 @@ def sim_set_beta_scale(h, scale) -> None:
 
 def sim_tensor_cores(h, enable: bool) -> None:
     _check(h, load().sim_tensor_cores(h, 1 if enable else 0))
+
+
+def sim_tc_factor(h, enable: bool) -> None:
+    _check(h, load().sim_tc_factor(h, 1 if enable else 0))
 
 
 SIM_SOLVER_ADMM, SIM_SOLVER_PJ = 0, 1
@@ -518,6 +523,10 @@ class Simulation:
 
     def tensor_cores(self, enable: bool = True) -> None:
         sim_tensor_cores(self.h, enable)
+
+    def tc_factor(self, enable: bool = True) -> None:
+        """Blocked Cholesky with tensor-core Schur updates for the refactorised large blocks."""
+        sim_tc_factor(self.h, enable)
 
     def keep_factors(self, enable: bool = True) -> None:
         sim_keep_factors(self.h, enable)
