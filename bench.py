@@ -452,7 +452,7 @@ class Ctx:
 
 def time_form(ctx, p, precision, steps: int, warmup: int, preroll: int, spl: int,
               autotune: bool = True, graph: bool = True, sample_clocks: bool = False,
-              keep_factors: bool = True, net=None, grid_rows=None):
+              keep_factors: bool = True, net=None, grid_rows=None, tc_factor: bool = True):
     """Pre-roll (untimed, so the timed segment lies in the contact phase), autotune the
     kernel variants on that state (restored afterwards), W warm-up steps, then K timed steps
     in launches of ``spl`` steps (the scenes are independent, so one launch advances every
@@ -472,6 +472,8 @@ def time_form(ctx, p, precision, steps: int, warmup: int, preroll: int, spl: int
             sim.step_learned(net, n)
     if not keep_factors:
         sim.keep_factors(False)
+    if not tc_factor:
+        sim.tc_factor(False)
     sim.step(1)
     left = preroll
     while left > 0:
@@ -725,6 +727,8 @@ def sub_fem_beam(ctx, args, threads: int) -> dict:
                    keep_factors=False)
     rm = time_form(ctx, p, sa.SIM_MIXED, K, args.warmup, 0, 1, autotune=False, graph=False,
                    keep_factors=False)
+    rw = time_form(ctx, p, sa.SIM_MIXED, K, args.warmup, 0, 1, autotune=False, graph=False,
+                   keep_factors=False, tc_factor=False)
     d_bytes = float(sum(w[2] for w in work)) * 4
     hbm = measured_peaks().get("hbm_gbs")
     st = r["stats"]
@@ -744,8 +748,15 @@ def sub_fem_beam(ctx, args, threads: int) -> dict:
                "value": len(rm["launch_ms"]) / (rm["t_ms"] / 1e3), "unit": "steps/s",
                "steps": len(rm["launch_ms"]), "iterations": iter_summary(rm["stats"]),
                "note": "every block refactorised every step, as Algorithm 1 states it: per step "
-                       "the grid kernel up to W = L^-1 [J^T b], the tcgen05 Gram kernel for "
-                       "D and c, the grid kernel's iterations; L2 flushed before each step"},
+                       "the grid kernel up to K = A + beta J^T J, the blocked factorisation "
+                       "(per 128-column panel a CUDA-core panel kernel and a tcgen05 Schur "
+                       "update), the grid kernel for W = L^-1 [J^T b], the tcgen05 Gram kernel "
+                       "for D and c, the grid kernel's iterations; L2 flushed before each step",
+               "one_warp_factor": {
+                   "value": len(rw["launch_ms"]) / (rw["t_ms"] / 1e3), "unit": "steps/s",
+                   "iterations": iter_summary(rw["stats"]),
+                   "note": "the same with every factor formed inside the setup launch by one "
+                           "warp per slab (sim_tc_factor(0))"}},
            "gram_tensor_roofline": gram_roofline(ctx, p.scenes[0]),
            "corotational": corotational_beam(ctx, args),
            "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm or 6800.0, "unit": "GB/s",
@@ -756,7 +767,7 @@ def sub_fem_beam(ctx, args, threads: int) -> dict:
                                 f"(setup and exit included: a lower bound on the stream rate); "
                                 f"peak = {'measured copy bandwidth' if hbm else 'fallback'}"}}
     out["chosen_over_plain"] = out["value"] / out["plain_fp64"]["value"]
-    for x in (r, f, rf, rm):
+    for x in (r, f, rf, rm, rw):
         x["sim"].close()
     if ctx.net is not None:
         try:
@@ -782,8 +793,9 @@ def sub_fem_beam(ctx, args, threads: int) -> dict:
 
 def corotational_beam(ctx, args) -> dict:
     """The beam with co-rotational slabs (the paper's beam model): every step assembles the
-    elements' rotations and refactorises every slab; the mixed form forms the slabs' maps on
-    the tensor cores (three launches per step), plain FP64 on the CUDA cores."""
+    elements' rotations and refactorises every slab; the mixed form factorises the slabs by
+    the blocked factorisation (tensor-core Schur updates) and forms their maps on the tensor
+    cores, plain FP64 does both on the CUDA cores."""
     import scenegen as sg
     sa = ctx.subadmm
     p = sg.fem_beam(0, corotational=True, tol_primal=1e-6, max_iters=1000)

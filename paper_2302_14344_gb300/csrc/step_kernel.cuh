@@ -598,6 +598,53 @@ __device__ void map_item(const F *W, int n, int m, int mp, int ldd, int ldw, con
     }
 }
 
+// K_i = A_i + beta_i J_i^T J_i in FP32 for the blocks whose factorisation is left to the
+// blocked tensor-core factorisation (step flag 4, set before the barrier that precedes this),
+// a warp per row over every warp of the scene: the lower triangle from the first column of
+// the envelope's tile of the row's tile row on (zeros left of the envelope: that
+// factorisation reads whole tiles), then, for every row group whose span holds the row's
+// column p (ascending), the group's products summed over its rows and added times beta: the
+// arithmetic of add_jtj, entry by entry.
+template <typename T, typename Dist>
+__device__ void deferred_fill(const StepParams &P, const SceneDesc &S, const View<T> &V,
+                              const Dist &d)
+{
+    const int lane = threadIdx.x & 31;
+    for (int i = 0; i < S.nsub; ++i) {
+        if (P.pending[S.sub0 + i] != 4) continue;
+        const SubDesc &u = P.subs[S.sub0 + i];
+        const int n = u.n;
+        const SubEnv e = sub_env(P, u);
+        const double *K = V.sdb + u.od_L, *J = V.sdb + u.od_J;
+        T *LT = V.stb + u.ot_L;
+        const T beta = (T)V.db[S.od_beta + i];
+        for (int p = d.warp; p < n; p += d.nwarps) {
+            const int ep = e.env[p], q0 = e.env[p & ~127] & ~127;
+            T *Lp = LT + (size_t)p * n;
+            for (int q = q0 + lane; q <= p; q += 32) Lp[q] = q < ep ? (T)0 : (T)K[(size_t)p * n + q];
+            __syncwarp();
+            for (int g0 = 0; g0 < e.ngrp; g0 += 32) {
+                bool cov = false;
+                if (g0 + lane < e.ngrp) {
+                    const int r0 = e.grp[g0 + lane];
+                    cov = e.jlo[r0] <= p && p < e.jhi[r0];
+                }
+                for (unsigned mask = __ballot_sync(0xffffffffu, cov); mask; mask &= mask - 1) {
+                    const int g = g0 + __ffs(mask) - 1;
+                    const int r0 = e.grp[g], r1 = e.grp[g + 1], lo = e.jlo[r0];
+                    for (int q = lo + lane; q <= p; q += 32) {
+                        T acc = (T)0;
+                        for (int r = r0; r < r1; ++r)
+                            acc += (T)J[(size_t)r * n + p] * (T)J[(size_t)r * n + q];
+                        Lp[q] += beta * acc;
+                    }
+                    __syncwarp();
+                }
+            }
+        }
+    }
+}
+
 // W = L^-1 [J^T b] of the subsystems whose step flag is `want` (3: factorised by the setup;
 // 4: by the blocked tensor-core factorisation), in chunks of 32 columns, a warp per chunk over
 // every warp of the scene, so that one large subsystem does not hold a single warp (and the
@@ -658,7 +705,13 @@ __device__ long long scene_setup(const StepParams &P, const SceneDesc &S, const 
         const SubEnv e = sub_env(P, u);
         const bool keep = factor_kept(P, S, u, S.sub0 + i, step);
         double *J = sdb + u.od_J, *K = sdb + u.od_L;
-        for (int q = lane; q < u.m * u.n; q += 32) J[q] = 0.0;
+        // J's rows are read only inside their column spans (model rows are written there,
+        // explicit rows whole): zero the spans
+        for (int g = 0; g < e.ngrp; ++g) {
+            const int r0 = e.grp[g], r1 = e.grp[g + 1], lo = e.jlo[r0], w = e.jhi[r0] - lo;
+            for (int k = lane; k < (r1 - r0) * w; k += 32)
+                J[(size_t)(r0 + k / w) * u.n + lo + k % w] = 0.0;
+        }
         if (u.kind == KIND_GENERIC) {
             const double *A = P.pool + u.gen_off;
             for (int q = lane; q < u.n * u.n; q += 32) K[q] = A[q];
@@ -825,14 +878,26 @@ __device__ long long scene_setup(const StepParams &P, const SceneDesc &S, const 
         if (!MIXED) {
             double trA = 0.0, trJ = 0.0;
             for (int q = lane; q < n; q += 32) trA += K[q * n + q];
-            for (int q = lane; q < m * n; q += 32) trJ += J[q] * J[q];
+            for (int g = 0; g < e.ngrp; ++g) {            // J's rows inside their spans
+                const int r0 = e.grp[g], r1 = e.grp[g + 1], lo = e.jlo[r0], w = e.jhi[r0] - lo;
+                for (int k = lane; k < (r1 - r0) * w; k += 32) {
+                    const double x = J[(size_t)(r0 + k / w) * n + lo + k % w];
+                    trJ += x * x;
+                }
+            }
             trA = warp_sum(trA);
             trJ = warp_sum(trJ);
             beta = P.beta_fixed ? P.rho : (trJ > 0.0 ? trA / trJ : 1.0);
         } else {
             T trA = (T)0, trJ = (T)0;
             for (int q = lane; q < n; q += 32) trA += (T)K[q * n + q];
-            for (int q = lane; q < m * n; q += 32) { const T jq = (T)J[q]; trJ += jq * jq; }
+            for (int g = 0; g < e.ngrp; ++g) {
+                const int r0 = e.grp[g], r1 = e.grp[g + 1], lo = e.jlo[r0], w = e.jhi[r0] - lo;
+                for (int k = lane; k < (r1 - r0) * w; k += 32) {
+                    const T jq = (T)J[(size_t)(r0 + k / w) * n + lo + k % w];
+                    trJ += jq * jq;
+                }
+            }
 #pragma unroll
             for (int o = 16; o; o >>= 1) {
                 trA += __shfl_xor_sync(0xffffffffu, trA, o);
@@ -854,8 +919,15 @@ __device__ long long scene_setup(const StepParams &P, const SceneDesc &S, const 
             const T bt = (T)beta;
             T dmax = (T)0, dmin = (T)3.0e38;
             for (int p = lane; p < n; p += 32) {
-                T cs = (T)0;
-                for (int r = 0; r < m; ++r) { const T jr = (T)J[r * n + p]; cs += jr * jr; }
+                T cs = (T)0;                       // rows whose span holds column p, in order
+                for (int g = 0; g < e.ngrp; ++g) {
+                    const int r0 = e.grp[g];
+                    if (p < e.jlo[r0] || p >= e.jhi[r0]) continue;
+                    for (int r = r0; r < e.grp[g + 1]; ++r) {
+                        const T jr = (T)J[r * n + p];
+                        cs += jr * jr;
+                    }
+                }
                 const T dk = (T)K[p * n + p] + bt * cs;
                 dmax = dk > dmax ? dk : dmax;
                 dmin = dk < dmin ? dk : dmin;
@@ -881,17 +953,7 @@ __device__ long long scene_setup(const StepParams &P, const SceneDesc &S, const 
                         LT[p * n + q] = (q == p) ? (T)idg[p] : (T)K[p * n + q];
             }
         } else if (defer) {
-            // K in FP32 for the blocked tensor-core factorisation that follows this launch:
-            // the lower triangle from the first column of the envelope's tile of each tile
-            // row on, zeros left of the envelope (the blocked factorisation reads whole tiles)
-            for (int p = 0; p < n; ++p) {
-                const int q0 = e.env[p & ~127] & ~127;
-                for (int q = q0 + lane; q <= p; q += 32)
-                    LT[p * n + q] = q < e.env[p] ? (T)0 : (T)K[p * n + q];
-            }
-            __syncwarp();
-            add_jtj<T>(LT, n, J, e, (T)beta);
-            ok = true;
+            ok = true;                            // K in FP32 by deferred_fill, below
         } else {
             for (int p = 0; p < n; ++p)
                 for (int q = e.env[p] + lane; q <= p; q += 32) LT[p * n + q] = (T)K[p * n + q];
@@ -909,8 +971,9 @@ __device__ long long scene_setup(const StepParams &P, const SceneDesc &S, const 
         }
         __syncwarp();
     }
-    // W = L^-1 [J^T b] of the subsystems factorised above (flag 3)
+    // W = L^-1 [J^T b] of the subsystems factorised above (flag 3); K of the deferred ones
     if (!Dist::kSpread) d.sync();
+    if (P.tc_factor && P.tc_phase == 1) deferred_fill<T>(P, S, V, d);
     w_chunks<T>(P, S, V, s_status, d, 3);
     d.sync();
     // the maps D = W^T W and c = W^T g of this step (pending >= 2: D and c, 1: c only), their
