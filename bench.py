@@ -941,6 +941,9 @@ def main():
     ap.add_argument("--no-compare", action="store_true",
                     help="skip timing the plain FP64 form next to the chosen one")
     ap.add_argument("--no-sub", action="store_true", help="headline workload only")
+    ap.add_argument("--refactor", action="store_true",
+                    help="refactorise every block every step (sim_keep_factors(0), Algorithm 1 "
+                         "as stated) in the headline workload's timing")
     ap.add_argument("--subs", default="robots,fem_beam,chain,cable,stir",
                     help="comma-separated sub-results to run (robots, fem_beam, chain, cable, "
                          "stir)")
@@ -995,7 +998,7 @@ def main():
         rp["sim"].close()
     r = time_form(ctx, p, prec, K, args.warmup, preroll, spl, autotune=not args.no_autotune,
                   graph=not (args.no_graph or grid_scene), sample_clocks=True,
-                  net=ctx.net if learned else None)
+                  net=ctx.net if learned else None, keep_factors=not args.refactor)
     sim, t_ms, stats = r["sim"], r["t_ms"], r["stats"]
     sizes = sim.sizes()
     value = whole_job_rate(world, K, t_ms)
@@ -1020,7 +1023,8 @@ def main():
     compare = None
     if not args.no_compare and mixed_form:
         f = time_form(ctx, p, subadmm.SIM_FP64, K, args.warmup, preroll, spl,
-                      autotune=not args.no_autotune, graph=not (args.no_graph or grid_scene))
+                      autotune=not args.no_autotune, graph=not (args.no_graph or grid_scene),
+                      keep_factors=not args.refactor)
         compare = {"value": whole_job_rate(world, K, f["t_ms"]), "unit": "steps/s",
                    "ms_per_step": f["t_ms"] / K, "iterations": iter_summary(f["stats"])}
         compare["chosen_over_plain"] = value / compare["value"]
@@ -1078,6 +1082,8 @@ def main():
                        "kernel_variants": "heuristic" if args.no_autotune else
                                           "autotuned on the pre-rolled state (sim_autotune, "
                                           "3 steps per variant, state restored)",
+                       "factors": ("every block refactorised every step" if args.refactor
+                                   else "constant blocks' factors kept across steps"),
                        "preroll_steps": preroll,
                        "timed_segment": f"steps {1 + preroll + args.warmup}.."
                                         f"{1 + preroll + args.warmup + K} of a run from rest "
@@ -1092,6 +1098,8 @@ def main():
             "e2e": e2e,
             # kernels per timed launch: one per launch class, plus features, weight packing,
             # the fused network, learned duals and the two beta-scale kernels when learned
+            # (a refactorising grid scene adds its blocked factorisation's and Gram kernel's
+            # launches, which this count leaves out)
             "gpu_launches": len(r["launch_ms"]) * (len(r["classes"]) + (6 if learned else 0)),
             "clocks": r["clocks"],
             "launch_ms": {"mean": statistics.mean(r["launch_ms"]),

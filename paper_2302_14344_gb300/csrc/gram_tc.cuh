@@ -25,6 +25,12 @@
 //                     read them (tcgen05.ld), add them in FP32, and store D, c and the
 //                     mirrored tile.
 //
+// The same kernel is the Schur update of the blocked Cholesky factorisation (chol.cu): the
+// panel kernel writes the panel's rows below its diagonal tile as TF32 pairs straight into
+// the stacked buffers (no transpose), and the epilogue subtracts the Gram matrix of those
+// rows from the lower triangle of the trailing tiles, C -= P P^T, while the block's step flag
+// says that its factorisation is the blocked one.
+//
 // All waits are bounded: a wait that runs out raises the launch's error word and the roles
 // stop; the kernel then waits (bounded) for its own copies and MMAs and frees its tensor
 // memory before it returns.

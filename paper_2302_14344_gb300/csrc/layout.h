@@ -146,8 +146,10 @@ struct StepParams {
     double *nodes;         // 6 doubles per node of linear blocks (state in and out)
     const int *ipool;      // integer constant data (sparse K of linear blocks, profiles)
     int *subflag;          // per subsystem: bit 0 its kept factor is valid, bit 1 it is FP64
-    int *pending;          // per subsystem, this step: 2 its map D, c is to be formed, 1 only
-                           // c, 0 neither (set by the factorisation loop of the setup)
+    int *pending;          // per subsystem, this step (set by the factorisation loop of the
+                           // setup): 4 its factor is left to the blocked factorisation, then
+                           // W, D and c; 3 W, D and c are to be formed; 2 D and c; 1 only c;
+                           // 0 none (or a failed factorisation); -1 not set yet
     int keep_factors;      // 0: refactor constant blocks every step too (Algorithm 1 literally)
     int tc_phase;          // grid kernel: 0 the whole step; 1 up to the map's W (the Gram
                            // kernel forms D, c of the tc subsystems next); 2 from the duals on;

@@ -23,7 +23,9 @@
 // T is the iteration type.  T = double: the map and the iterations in FP64.  T = float (the
 // mixed form): assembly stays FP64; K and its Cholesky factor are FP32 for well-conditioned
 // blocks and FP64 for stiff or high-mass-ratio ones (spread of diag K above 1e3); W, g, D,
-// c are formed in FP32 and the iterations run in FP32.  When the FP32 stop test
+// c are formed in FP32 and the iterations run in FP32.  (In a grid scene, the FP32 factor of
+// a refactorised block of >= 128 DOF is left to the blocked factorisation with tensor-core
+// Schur updates that runs between the grid kernel's launches.)  When the FP32 stop test
 // passes, v-hat is recovered in FP64 and the primal residual re-evaluated as
 // max |J v-hat - z| in FP64; if that misses the tolerance, c is corrected by the FP64 - FP32
 // difference of x at the current iterate (iterative refinement) and the iterations resume.

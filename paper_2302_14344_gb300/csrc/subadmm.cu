@@ -1416,7 +1416,8 @@ int launch_grid_class(sim_t s, LaunchClass &c, StepParams P, cudaStream_t st, in
         if (rc) return rc;
         const bool blocked = s->tc_factor && s->gram[sc].njobs > 0;
         if (blocked && (rc = chol_plan_of(s, sc))) return rc;
-        // steps that refactorise tc subsystems: setup launch, Gram kernel, iteration launch
+        // steps that refactorise tc subsystems: setup launch, (the blocked factorisation's
+        // panels and the W launch,) Gram kernel, iteration launch
         int left = P.n_steps;
         // (blocks whose K changes every step, co-rotational ones, refactorise every step)
         bool changing = false;
@@ -1667,8 +1668,8 @@ int sim_autotune(sim_t s, int steps, int max_classes, long long *out)
         int bs = c.split, bt = c.nt;
         if (c.grid) {
             // lanes per side-row, and all resident blocks or half of them (unless the caller
-            // fixed the block count)
-            // (half the blocks must win by 3% over all of them: the short timing is noisy)
+            // fixed the block count); half the blocks must win by 3% over all of them, as the
+            // short timing is noisy
             double best_div[3] = {1e300, 1e300, 1e300};
             int split_div[3] = {c.split, c.split, c.split};
             for (int div = 1; div <= (s->grid_blocks > 0 ? 1 : 2) && err == cudaSuccess; ++div)
