@@ -723,7 +723,7 @@ def sub_fem_beam(ctx, args, threads: int) -> dict:
     K = args.steps
     r = time_form(ctx, p, sa.SIM_MIXED, K, args.warmup, 0, 50, autotune=True, graph=False)
     f = time_form(ctx, p, sa.SIM_FP64, K, args.warmup, 0, 50, autotune=True, graph=False)
-    rf = time_form(ctx, p, sa.SIM_FP64, min(K, 5), 1, 0, 1, autotune=False, graph=False,
+    rf = time_form(ctx, p, sa.SIM_FP64, min(K, 10), 2, 0, 1, autotune=False, graph=False,
                    keep_factors=False)
     rm = time_form(ctx, p, sa.SIM_MIXED, K, args.warmup, 0, 1, autotune=False, graph=False,
                    keep_factors=False)
@@ -802,7 +802,7 @@ def corotational_beam(ctx, args) -> dict:
     K = min(args.steps, 10)
     out = {"workload": "the FEM beam with co-rotational slabs (66,096 elements rotated and "
                        "assembled every step, every slab refactorised every step)"}
-    for name, prec, k in (("mixed", sa.SIM_MIXED, K), ("plain_fp64", sa.SIM_FP64, min(K, 3))):
+    for name, prec, k in (("mixed", sa.SIM_MIXED, K), ("plain_fp64", sa.SIM_FP64, min(K, 5))):
         r = time_form(ctx, p, prec, k, 2, 0, 1, autotune=False, graph=False)
         out[name] = {"value": k / (r["t_ms"] / 1e3), "unit": "steps/s", "steps": k,
                      "iterations": iter_summary(r["stats"])}

@@ -114,3 +114,28 @@ def test_blocked_factor_converged_against_fp64_oracle(sa, capsys):
         print(f"\n[blocked tensor-core factor, refactorised every step, r_p<=1e-6] v-hat rel "
               f"err to the exact step {err:.3e}; FP64 oracle at the same tolerance {spread:.3e}")
     assert err <= 3 * spread + 1e-6
+
+
+def test_blocked_factor_reports_not_spd(sa):
+    """An indefinite block whose diagonal spread passes the stiffness test (so the blocked
+    factorisation, not the FP64 one, meets the non-positive pivot): the step ends with
+    SIM_ENOTSPD status, with the blocked factorisation and with the one-warp one alike."""
+    rng = np.random.default_rng(3)
+    n = 160
+    A = np.eye(n)
+    A[0, 1] = A[1, 0] = 2.0                 # eigenvalue -1: pivot 1 - 4 < 0
+    ifs = []
+    for k in range(6):                      # 18 side-rows on the block, away from DOF 0 and 1
+        J = np.zeros((3, n))
+        J[:, 10 + 20 * k: 10 + 20 * k + 8] = rng.standard_normal((3, 8))
+        ifs.append(sg.RowsIf(sg.EQUALITY, [0], [J], np.zeros(3)))
+    p = sg.Problem([sg.Scene([sg.GenericSub(A, np.ones(n))], ifs)],
+                   sg.Options(gravity=(0, 0, 0), max_iters=5))
+    for blocked in (True, False):
+        sim = sa.Simulation(p, precision=sa.SIM_MIXED, grid_side_rows=1)
+        sim.tc_factor(blocked)
+        sim.step(1)
+        with pytest.raises(sa.SimError) as ei:
+            sim.residuals(0)
+        assert ei.value.code == sa.SIM_ENOTSPD
+        sim.close()
