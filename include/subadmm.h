@@ -72,9 +72,11 @@ extern "C" {
 #define SIM_STOP_THETA 1      /* stop when theta < theta_th after the v-step (Eq. residual) */
 #define SIM_FP64 0            /* every step in double precision                             */
 #define SIM_MIXED 1           /* FP64 assembly, beta and final residual check; K_i factorised
-                                 in FP32, or in FP64 when the block is stiff (spread of K_i's
-                                 diagonal above 1e3); FP32 iterations (resumed with a refined
-                                 c if the FP64 check misses the tolerance)                 */
+                                 in FP32 (a large block of a grid scene by the blocked
+                                 factorisation, see sim_tc_factor), or in FP64 when the block
+                                 is stiff (spread of K_i's diagonal above 1e3); FP32
+                                 iterations (resumed with a refined c if the FP64 check
+                                 misses the tolerance)                                      */
 
 /* what sim_get() reads */
 #define SIM_GET_VHAT 0        /* id = subsystem: n doubles, v-hat of the last step          */
