@@ -285,8 +285,10 @@ int sim_set_beta_scale(sim_t s, const double *scale);
  * every step with sim_keep_factors(0), else the first -- runs as three launches: the grid
  * kernel up to W = L^-1 [J^T b] (its columns solved in 32-wide chunks over every warp), the
  * tcgen05 Gram kernel forming D = W^T W and c = W^T g (see sim_gram_tc), and the grid kernel
- * from the initial duals on.  With 0 the grid kernel forms D and c itself (one warp per
- * block, FP32 CUDA cores).  Must be called before the first sim_step (SIM_EINVAL after). */
+ * from the initial duals on (with sim_tc_factor, the default, those blocks' factorisation
+ * and a W launch come between the first two).  With 0 the grid kernel forms D and c itself
+ * (one warp per block, FP32 CUDA cores).  Must be called before the first sim_step
+ * (SIM_EINVAL after). */
 int sim_tensor_cores(sim_t s, int enable);
 
 /* Blocked factorisation of those blocks on the tensor cores (Algorithm 1, factorise; on by

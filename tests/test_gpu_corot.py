@@ -56,7 +56,8 @@ def test_corotational_fp64_against_oracle(sa, grid):
 
 def test_corotational_mixed_tensor_core_map_against_oracle(sa, capsys):
     """Slabs of >= 128 DOF in the mixed form on the grid kernel: every step takes the
-    three-launch path (setup with the element pass, tcgen05 Gram, iterations)."""
+    tensor-core path (setup with the element pass, the blocked factorisation, tcgen05 Gram,
+    iterations)."""
     p = _tilted(_beam(ny=8, nz=8, tol_primal=-1, max_iters=30, with_gripper=False))
     assert all(s.n >= 128 for s in p.scenes[0].subs)
     o = oracle.OracleScene(p.scenes[0], p.options)

@@ -2,7 +2,8 @@
 
 A step that factorises a block of >= 128 DOF anew runs as three launches: the grid kernel up
 to W = L^-1 [J^T b] (columns solved in chunks over every warp), the tcgen05 Gram kernel
-(D = W^T W, c = W^T g, split-TF32), and the grid kernel from the initial duals on.  With
+(D = W^T W, c = W^T g, split-TF32), and the grid kernel from the initial duals on (the
+blocked factorisation's launches, on by default, come between the first two).  With
 sim_tensor_cores(0) the grid kernel forms D and c on the CUDA cores instead.
 
 * Fixed iteration counts: both maps are FP32 approximations of the FP64 oracle's step (the
